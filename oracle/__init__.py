@@ -1,0 +1,202 @@
+"""FP64 CPU oracle for the damped 2-D acoustic simulator and its misfit gradient.
+
+Test infrastructure only: the tests, the smoke check and the CPU-baseline leg
+of the benchmark load it; the library path never does. The arithmetic lives
+in ``dufwi_oracle.c`` (plain C, FP64, one routine per passage of the paper);
+this module compiles it with gcc and marshals numpy arrays through ctypes.
+
+Physical conventions (paper Sec. II-A, Eqs. 2-6; readings in the C header):
+``C`` is the SoS map ``[nz][nx]`` in m/s on the physical grid, element
+positions are physical-grid node indices ``(ix, iz)``, traces are
+``M[t][r] = U[t]`` at the receivers, ``J = sum (M_sim - M_obs)^2`` and
+``g = dJ/dC``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dufwi_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nt", ctypes.c_int), ("pml", ctypes.c_int),
+                ("pml_R", ctypes.c_double), ("pml_cref", ctypes.c_double),
+                ("fd_order", ctypes.c_int)]
+
+
+@dataclass(frozen=True)
+class Problem:
+    """Grid and time axis of one simulation (physical grid, unpadded)."""
+    nx: int
+    nz: int
+    dx: float
+    dt: float
+    nt: int
+    pml: int = 20
+    pml_R: float = 1e-3
+    pml_cref: float = 1540.0
+    fd_order: int = 8
+
+    @property
+    def nxp(self) -> int:
+        return self.nx + 2 * self.pml
+
+    @property
+    def nzp(self) -> int:
+        return self.nz + 2 * self.pml
+
+    def c_struct(self) -> _Problem:
+        return _Problem(self.nx, self.nz, self.dx, self.dt, self.nt, self.pml,
+                        self.pml_R, self.pml_cref, self.fd_order)
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        pp = ctypes.POINTER(_Problem)
+        _lib.orc_fd_coeffs.argtypes = [ctypes.c_int, dp]
+        _lib.orc_d0.argtypes = [pp]
+        _lib.orc_d0.restype = ctypes.c_double
+        _lib.orc_damping.argtypes = [pp, dp]
+        _lib.orc_pad.argtypes = [pp, dp, dp]
+        _lib.orc_laplacian.argtypes = [pp, dp, dp]
+        _lib.orc_forward.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp,
+                                     ctypes.c_int, ip, ip, dp]
+        _lib.orc_adjoint_probe.argtypes = [pp, dp, ctypes.c_int, ip, ip, dp,
+                                           ctypes.c_int, ctypes.c_int, dp]
+        _lib.orc_misfit_gradient.argtypes = [pp, dp, ctypes.c_int, ip, ip, dp, ctypes.c_int,
+                                             ctypes.c_int, ip, ip, dp, ctypes.c_int,
+                                             dp, dp, dp]
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError("oracle %s failed with status %d" % (what, rc))
+
+
+def fd_coeffs(order: int) -> np.ndarray:
+    c = np.zeros(5)
+    _check(_get().orc_fd_coeffs(order, _d(c)), "fd_coeffs")
+    return c[: order // 2 + 1].copy()
+
+
+def d0(p: Problem) -> float:
+    s = p.c_struct()
+    return _get().orc_d0(ctypes.byref(s))
+
+
+def damping(p: Problem) -> np.ndarray:
+    s = p.c_struct()
+    D = np.zeros((p.nzp, p.nxp))
+    _check(_get().orc_damping(ctypes.byref(s), _d(D)), "damping")
+    return D
+
+
+def pad(p: Problem, C) -> np.ndarray:
+    s = p.c_struct()
+    C = _f64(C)
+    out = np.zeros((p.nzp, p.nxp))
+    _check(_get().orc_pad(ctypes.byref(s), _d(C), _d(out)), "pad")
+    return out
+
+
+def laplacian(p: Problem, u) -> np.ndarray:
+    s = p.c_struct()
+    u = _f64(u)
+    assert u.shape == (p.nzp, p.nxp)
+    out = np.zeros_like(u)
+    _check(_get().orc_laplacian(ctypes.byref(s), _d(u), _d(out)), "laplacian")
+    return out
+
+
+def forward(p: Problem, C, src, wavelet, rx_ix, rx_iz) -> np.ndarray:
+    """Traces ``[nt][n_rx]`` of one transmit from node ``src = (ix, iz)``."""
+    s = p.c_struct()
+    C = _f64(C)
+    w = _f64(wavelet)
+    rx_ix, rx_iz = _i32(rx_ix), _i32(rx_iz)
+    assert C.shape == (p.nz, p.nx) and w.shape == (p.nt,) and rx_ix.shape == rx_iz.shape
+    out = np.zeros((p.nt, rx_ix.size))
+    _check(_get().orc_forward(ctypes.byref(s), _d(C), int(src[0]), int(src[1]), _d(w),
+                              rx_ix.size, _i(rx_ix), _i(rx_iz), _d(out)), "forward")
+    return out
+
+
+def adjoint_probe(p: Problem, C, rx_ix, rx_iz, q, probe) -> np.ndarray:
+    """Adjoint field ``lam[t]`` at node ``probe`` for receiver series ``q[nt][n_rx]``."""
+    s = p.c_struct()
+    C, q = _f64(C), _f64(q)
+    rx_ix, rx_iz = _i32(rx_ix), _i32(rx_iz)
+    assert q.shape == (p.nt, rx_ix.size)
+    out = np.zeros(p.nt)
+    _check(_get().orc_adjoint_probe(ctypes.byref(s), _d(C), rx_ix.size, _i(rx_ix), _i(rx_iz),
+                                    _d(q), int(probe[0]), int(probe[1]), _d(out)), "adjoint_probe")
+    return out
+
+
+def misfit_gradient(p: Problem, C, tx_ix, tx_iz, wavelet, rx_ix, rx_iz, M_obs, ckpt: int = 0,
+                    return_traces: bool = False):
+    """Misfit ``J`` and gradient ``g = dJ/dC`` (``[nz][nx]``) of one map.
+
+    ``tx_ix, tx_iz``: ``[n_tx]``; ``wavelet``: ``[nt]`` or ``[n_tx][nt]``;
+    ``rx_ix, rx_iz``: ``[n_tx][n_rx]``; ``M_obs``: ``[n_tx][nt][n_rx]``;
+    ``ckpt``: snapshot interval of the forward fields (0 = keep all).
+    """
+    s = p.c_struct()
+    C = _f64(C)
+    tx_ix, tx_iz = _i32(tx_ix).ravel(), _i32(tx_iz).ravel()
+    n_tx = tx_ix.size
+    w = _f64(wavelet)
+    n_wav = 1 if w.ndim == 1 else w.shape[0]
+    rx_ix, rx_iz = _i32(rx_ix).reshape(n_tx, -1), _i32(rx_iz).reshape(n_tx, -1)
+    n_rx = rx_ix.shape[1]
+    M_obs = _f64(M_obs).reshape(n_tx, p.nt, n_rx)
+    J = np.zeros(1)
+    g = np.zeros((p.nz, p.nx))
+    M_sim = np.zeros((n_tx, p.nt, n_rx))
+    _check(_get().orc_misfit_gradient(ctypes.byref(s), _d(C), n_tx, _i(tx_ix), _i(tx_iz),
+                                      _d(w), n_wav, n_rx, _i(rx_ix), _i(rx_iz), _d(M_obs),
+                                      int(ckpt), _d(J), _d(g), _d(M_sim)), "misfit_gradient")
+    if return_traces:
+        return float(J[0]), g, M_sim
+    return float(J[0]), g

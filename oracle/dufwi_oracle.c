@@ -1,0 +1,411 @@
+/*
+ * dufwi_oracle.c -- plain FP64 CPU oracle for the damped 2-D acoustic
+ * simulator and its misfit gradient (test infrastructure only).
+ *
+ * This file is the reference that the CUDA path is checked against. It is
+ * deliberately slow and literal: every routine follows one passage of the
+ * paper (arXiv 2603.04070, "Physics Informed Deep Unfolded Full Waveform
+ * Inversion for Edema Detection") and nothing is blocked, fused or reordered
+ * beyond what that passage states. It shares no code, header, table or
+ * constant with the GPU library; only tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.
+ *
+ * Notation (paper Sec. II-A):
+ *   C  speed of sound (m/s), D  damping profile (1/s), dt time step (s),
+ *   dx grid spacing (m), U[t] field at time sample t, S[t] source term.
+ * Grid layout: padded grid nzp x nxp, row-major [z][x] (x fastest).
+ *   nxp = nx + 2P, nzp = nz + 2P, with P absorbing cells added on each side.
+ *
+ * Readings of points the paper leaves open (each is listed in the design
+ * notes of the repository):
+ *   - Eq. 2 prints the Laplacian coefficient as C^2 dt/(1+D dt); the
+ *     dimensionally consistent coefficient, used here, is C^2 dt^2/(1+D dt).
+ *   - The Laplacian "convolution kernel" of Eq. 2 is the textbook central
+ *     second-difference stencil of order 2, 4, 6 or 8 along x plus the same
+ *     along z, divided by dx^2, with zero field outside the padded grid.
+ *   - The absorbing profile (Sec. IV) is quadratic, d(xi) = d0 (xi/L)^2,
+ *     L = P dx, d0 = 3 c_ref ln(1/R) / (2L); D = d(xi_x) + d(xi_z), xi the
+ *     depth into the layer (P - i) dx for layer index i (outermost i = 0).
+ *     With c_ref = 1500 m/s, R = 1e-3, P = 20, dx = 0.1 m / 188 this gives
+ *     the 1.46e6 printed in Sec. IV.
+ *   - The SoS map covers the physical grid; inside the absorbing layer it is
+ *     extended by edge replication, so the gradient of a padded cell is
+ *     folded back onto the physical edge cell it copies.
+ *   - Source: a point source w(t) at one node, S[t] = dt^2 w((t-1) dt)/dx^2,
+ *     i.e. the step that produces U[t+1] adds dt^2 w[t]/dx^2 at the node.
+ *   - Receivers record M[t][r] = U[t](x_r) for t = 0..nt-1, U[0] = U[-1] = 0.
+ *   - Misfit J = sum over transmits, samples and receivers of
+ *     (M_sim - M_obs)^2 (Eq. 5 data term, lambda = 0); g = dJ/dC (Eq. 6), the
+ *     exact gradient of the discrete J, obtained with the discrete adjoint.
+ *
+ * Parity pins (tests marked "not gpu"): analytic 2-D Green's function trace,
+ * source-receiver reciprocity, adjoint dot-product test, central finite
+ * differences of J, the printed d0, stencil moment conditions, linearity and
+ * time-shift equivariance, mirror symmetry, J = 0 and g = 0 at the truth.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int nx, nz;          /* physical grid (cells) */
+    double dx, dt;       /* m, s */
+    int nt;              /* recorded samples t = 0..nt-1 */
+    int pml;             /* absorbing cells per side (P) */
+    double pml_R;        /* target reflection factor */
+    double pml_cref;     /* reference SoS for d0 (m/s) */
+    int fd_order;        /* 2, 4, 6 or 8 */
+} orc_problem;
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 5
+
+/* ------------------------------------------------------------------ */
+/* Laplacian stencil weights (the "convolution with a Laplacian kernel"
+ * of Sec. II-A): c[k] multiplies u(x+k dx) + u(x-k dx) for k >= 1 and
+ * c[0] multiplies u(x). Textbook central second-difference weights. */
+int orc_fd_coeffs(int order, double *c)
+{
+    switch (order) {
+    case 2:
+        c[0] = -2.0; c[1] = 1.0;
+        return ORC_OK;
+    case 4:
+        c[0] = -5.0 / 2.0; c[1] = 4.0 / 3.0; c[2] = -1.0 / 12.0;
+        return ORC_OK;
+    case 6:
+        c[0] = -49.0 / 18.0; c[1] = 3.0 / 2.0; c[2] = -3.0 / 20.0;
+        c[3] = 1.0 / 90.0;
+        return ORC_OK;
+    case 8:
+        c[0] = -205.0 / 72.0; c[1] = 8.0 / 5.0; c[2] = -1.0 / 5.0;
+        c[3] = 8.0 / 315.0; c[4] = -1.0 / 560.0;
+        return ORC_OK;
+    default:
+        return ORC_EINVAL;
+    }
+}
+
+static int padded_nx(const orc_problem *p) { return p->nx + 2 * p->pml; }
+static int padded_nz(const orc_problem *p) { return p->nz + 2 * p->pml; }
+
+/* Maximum damping of the quadratic layer (Sec. IV). */
+double orc_d0(const orc_problem *p)
+{
+    double L = p->pml * p->dx;
+    return 3.0 * p->pml_cref * log(1.0 / p->pml_R) / (2.0 * L);
+}
+
+/* Depth into the absorbing layer of padded index i along an axis with n
+ * physical cells: (P - i) dx on the low side, (i - (P + n - 1)) dx on the
+ * high side, 0 inside the physical grid. */
+static double layer_depth(const orc_problem *p, int i, int n)
+{
+    int P = p->pml;
+    if (i < P) return (double)(P - i) * p->dx;
+    if (i > P + n - 1) return (double)(i - (P + n - 1)) * p->dx;
+    return 0.0;
+}
+
+/* D(x,z) of Eq. 1 over the padded grid. */
+int orc_damping(const orc_problem *p, double *D)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p);
+    double L = p->pml * p->dx, d0 = orc_d0(p);
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            double xi_x = layer_depth(p, x, p->nx) / L;
+            double xi_z = layer_depth(p, z, p->nz) / L;
+            D[(size_t)z * nxp + x] = d0 * xi_x * xi_x + d0 * xi_z * xi_z;
+        }
+    return ORC_OK;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* SoS on the padded grid: edge replication of the physical map. */
+int orc_pad(const orc_problem *p, const double *C, double *Cpad)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p), P = p->pml;
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            int zs = clampi(z - P, 0, p->nz - 1), xs = clampi(x - P, 0, p->nx - 1);
+            Cpad[(size_t)z * nxp + x] = C[(size_t)zs * p->nx + xs];
+        }
+    return ORC_OK;
+}
+
+/* The three element-wise coefficient maps of Eq. 2:
+ *   a = (2 - D^2 dt^2)/(1 + D dt), b = (D dt - 1)/(1 + D dt),
+ *   kappa = C^2 dt^2/(1 + D dt). */
+static void coefficient_maps(const orc_problem *p, const double *Cpad, const double *D,
+                             double *a, double *b, double *kappa)
+{
+    size_t n = (size_t)padded_nx(p) * padded_nz(p);
+    double dt = p->dt;
+    for (size_t i = 0; i < n; ++i) {
+        double den = 1.0 + D[i] * dt;
+        a[i] = (2.0 - D[i] * D[i] * dt * dt) / den;
+        b[i] = (D[i] * dt - 1.0) / den;
+        kappa[i] = Cpad[i] * Cpad[i] * dt * dt / den;
+    }
+}
+
+/* out = Laplacian of u on the padded grid (Sec. II-A), zero outside. */
+int orc_laplacian(const orc_problem *p, const double *u, double *out)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p);
+    int h = p->fd_order / 2;
+    double c[5];
+    if (orc_fd_coeffs(p->fd_order, c) != ORC_OK) return ORC_EINVAL;
+    double inv_dx2 = 1.0 / (p->dx * p->dx);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            double s = 0.0;
+            for (int k = -h; k <= h; ++k) {
+                double w = c[k < 0 ? -k : k];
+                if (x + k >= 0 && x + k < nxp) s += w * u[(size_t)z * nxp + (x + k)];
+                if (z + k >= 0 && z + k < nzp) s += w * u[(size_t)(z + k) * nxp + x];
+            }
+            out[(size_t)z * nxp + x] = s * inv_dx2;
+        }
+    return ORC_OK;
+}
+
+/* One application of Eq. 2 without the source:
+ *   next = a*cur + b*prev + kappa*lap(cur). lapc receives lap(cur). */
+static void eq2_step(const orc_problem *p, const double *a, const double *b,
+                     const double *kappa, const double *cur, const double *prev,
+                     double *next, double *lapc)
+{
+    size_t n = (size_t)padded_nx(p) * padded_nz(p);
+    orc_laplacian(p, cur, lapc);
+    for (size_t i = 0; i < n; ++i)
+        next[i] = a[i] * cur[i] + b[i] * prev[i] + kappa[i] * lapc[i];
+}
+
+static int node_index(const orc_problem *p, int ix, int iz, size_t *out)
+{
+    if (ix < 0 || ix >= p->nx || iz < 0 || iz >= p->nz) return ORC_EINVAL;
+    *out = (size_t)(iz + p->pml) * padded_nx(p) + (size_t)(ix + p->pml);
+    return ORC_OK;
+}
+
+static int valid_problem(const orc_problem *p)
+{
+    double c[5];
+    if (p->nx < 1 || p->nz < 1 || p->nt < 1 || p->pml < 1) return 0;
+    if (!(p->dx > 0) || !(p->dt > 0) || !(p->pml_R > 0 && p->pml_R < 1) || !(p->pml_cref > 0)) return 0;
+    return orc_fd_coeffs(p->fd_order, c) == ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Forward model of one transmit, Eqs. 2-3: a point source at (sx, sz)
+ * driven by w[0..nt-1], traces M[t][r] = U[t] at the receivers. */
+int orc_forward(const orc_problem *p, const double *C,
+                int sx, int sz, const double *w,
+                int n_rx, const int *rx_ix, const int *rx_iz,
+                double *traces /* [nt][n_rx] */)
+{
+    if (!valid_problem(p)) return ORC_EINVAL;
+    size_t n = (size_t)padded_nx(p) * padded_nz(p), src;
+    if (node_index(p, sx, sz, &src)) return ORC_EINVAL;
+    size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
+    double *buf = calloc(n * 9, sizeof(double));
+    if (!rx || !buf) { free(rx); free(buf); return ORC_ENOMEM; }
+    for (int r = 0; r < n_rx; ++r)
+        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { free(rx); free(buf); return ORC_EINVAL; }
+    double *D = buf, *Cpad = buf + n, *a = buf + 2 * n, *b = buf + 3 * n, *kap = buf + 4 * n;
+    double *prev = buf + 5 * n, *cur = buf + 6 * n, *next = buf + 7 * n, *lap = buf + 8 * n;
+    orc_damping(p, D);
+    orc_pad(p, C, Cpad);
+    coefficient_maps(p, Cpad, D, a, b, kap);
+    double src_scale = p->dt * p->dt / (p->dx * p->dx);
+
+    for (int t = 0; t < p->nt; ++t) {
+        /* cur holds U[t] */
+        for (int r = 0; r < n_rx; ++r) traces[(size_t)t * n_rx + r] = cur[rx[r]];
+        if (t == p->nt - 1) break;
+        eq2_step(p, a, b, kap, cur, prev, next, lap);
+        next[src] += src_scale * w[t];
+        double *tmp = prev; prev = cur; cur = next; next = tmp;
+    }
+    free(rx); free(buf);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Discrete adjoint of Eq. 2 (exact transpose of the forward recursion).
+ * With q[t][r] the derivative of the objective w.r.t. M[t][r], the adjoint
+ * fields lam[t] (t = nt-1 .. 1) obey
+ *   lam[t] = R^T q[t] + a*lam[t+1] + Lap(kappa*lam[t+1]) + b*lam[t+2],
+ *   lam[nt] = lam[nt+1] = 0,
+ * because the Laplacian with zero exterior is a symmetric matrix. */
+static void adjoint_step(const orc_problem *p, const double *a, const double *b,
+                         const double *kappa, const double *lam1, const double *lam2,
+                         double *lam0, double *work, double *lapw)
+{
+    size_t n = (size_t)padded_nx(p) * padded_nz(p);
+    for (size_t i = 0; i < n; ++i) work[i] = kappa[i] * lam1[i];
+    orc_laplacian(p, work, lapw);
+    for (size_t i = 0; i < n; ++i)
+        lam0[i] = a[i] * lam1[i] + lapw[i] + b[i] * lam2[i];
+}
+
+/* Adjoint fields driven by receiver series q[nt][n_rx]; returns lam[t] at
+ * one probe node for t = 0..nt-1 (lam[0] included for completeness).
+ * For a source w at the probe node, <F w, q> = sum_t w[t] dt^2/dx^2 lam[t+1]. */
+int orc_adjoint_probe(const orc_problem *p, const double *C,
+                      int n_rx, const int *rx_ix, const int *rx_iz, const double *q,
+                      int px, int pz, double *lam_probe /* [nt] */)
+{
+    if (!valid_problem(p)) return ORC_EINVAL;
+    size_t n = (size_t)padded_nx(p) * padded_nz(p), probe;
+    if (node_index(p, px, pz, &probe)) return ORC_EINVAL;
+    size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
+    double *buf = calloc(n * 10, sizeof(double));
+    if (!rx || !buf) { free(rx); free(buf); return ORC_ENOMEM; }
+    for (int r = 0; r < n_rx; ++r)
+        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { free(rx); free(buf); return ORC_EINVAL; }
+    double *D = buf, *Cpad = buf + n, *a = buf + 2 * n, *b = buf + 3 * n, *kap = buf + 4 * n;
+    double *l2 = buf + 5 * n, *l1 = buf + 6 * n, *l0 = buf + 7 * n, *work = buf + 8 * n, *lapw = buf + 9 * n;
+    orc_damping(p, D);
+    orc_pad(p, C, Cpad);
+    coefficient_maps(p, Cpad, D, a, b, kap);
+    /* l1 = lam[t+1], l2 = lam[t+2] */
+    for (int t = p->nt - 1; t >= 0; --t) {
+        adjoint_step(p, a, b, kap, l1, l2, l0, work, lapw);
+        for (int r = 0; r < n_rx; ++r) l0[rx[r]] += q[(size_t)t * n_rx + r];
+        lam_probe[t] = l0[probe];
+        double *tmp = l2; l2 = l1; l1 = l0; l0 = tmp;
+    }
+    free(rx); free(buf);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Misfit and gradient of one SoS map over n_tx transmits (Eqs. 5-6).
+ *
+ *   J = sum_p sum_t sum_r (M_sim[p][t][r] - M_obs[p][t][r])^2
+ *   g = dJ/dC on the physical grid.
+ *
+ * dJ/dkappa = sum_{t=1}^{nt-1} lam[t] * Lap(U[t-1]) (kappa multiplies
+ * Lap(U[t-1]) in the step producing U[t]); dkappa/dC = 2 C dt^2/(1 + D dt);
+ * the padded-grid gradient is then summed onto the physical cell each padded
+ * cell replicates. The forward fields needed by the adjoint sweep are kept
+ * as snapshots (U[t], U[t-1]) every `ckpt` samples and recomputed segment by
+ * segment in FP64, which reproduces them exactly; ckpt >= nt keeps them all.
+ *
+ * wavelet: [n_wav][nt] with n_wav = 1 (shared) or n_tx (one per transmit).
+ * rx_ix, rx_iz: [n_tx][n_rx]. M_obs: [n_tx][nt][n_rx]. M_sim (optional
+ * output): [n_tx][nt][n_rx]. g: [nz][nx]. */
+int orc_misfit_gradient(const orc_problem *p, const double *C,
+                        int n_tx, const int *tx_ix, const int *tx_iz,
+                        const double *wavelet, int n_wav,
+                        int n_rx, const int *rx_ix, const int *rx_iz,
+                        const double *M_obs, int ckpt,
+                        double *J, double *g, double *M_sim)
+{
+    if (!valid_problem(p) || n_tx < 1 || n_rx < 0 || (n_wav != 1 && n_wav != n_tx)) return ORC_EINVAL;
+    int nxp = padded_nx(p), nzp = padded_nz(p), nt = p->nt;
+    size_t n = (size_t)nxp * nzp;
+    if (ckpt < 1 || ckpt > nt) ckpt = nt;
+    int n_seg = (nt - 1 + ckpt - 1) / ckpt;     /* steps t -> t+1 for t = 0..nt-2 */
+    if (n_seg < 1) n_seg = 1;
+
+    double *base = calloc(n * 13, sizeof(double));
+    double *snap = calloc((size_t)n_seg * 2 * n, sizeof(double));
+    double *seg = calloc((size_t)(ckpt + 1) * n, sizeof(double));
+    double *gpad = calloc(n, sizeof(double));
+    double *trace = calloc((size_t)nt * (n_rx > 0 ? n_rx : 1), sizeof(double));
+    double *q = calloc((size_t)nt * (n_rx > 0 ? n_rx : 1), sizeof(double));
+    size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
+    if (!base || !snap || !seg || !gpad || !trace || !q || !rx) {
+        free(base); free(snap); free(seg); free(gpad); free(trace); free(q); free(rx);
+        return ORC_ENOMEM;
+    }
+    double *D = base, *Cpad = base + n, *a = base + 2 * n, *b = base + 3 * n, *kap = base + 4 * n;
+    double *prev = base + 5 * n, *cur = base + 6 * n, *next = base + 7 * n, *lap = base + 8 * n;
+    double *l2 = base + 9 * n, *l1 = base + 10 * n, *l0 = base + 11 * n, *work = base + 12 * n;
+    orc_damping(p, D);
+    orc_pad(p, C, Cpad);
+    coefficient_maps(p, Cpad, D, a, b, kap);
+    double src_scale = p->dt * p->dt / (p->dx * p->dx);
+    double Jsum = 0.0;
+    int status = ORC_OK;
+
+    for (int tx = 0; tx < n_tx && status == ORC_OK; ++tx) {
+        size_t src;
+        const double *w = wavelet + (size_t)(n_wav == 1 ? 0 : tx) * nt;
+        if (node_index(p, tx_ix[tx], tx_iz[tx], &src)) { status = ORC_EINVAL; break; }
+        for (int r = 0; r < n_rx; ++r)
+            if (node_index(p, rx_ix[(size_t)tx * n_rx + r], rx_iz[(size_t)tx * n_rx + r], &rx[r])) status = ORC_EINVAL;
+        if (status) break;
+
+        /* forward sweep: traces and snapshots (U[s*ckpt], U[s*ckpt-1]) */
+        memset(prev, 0, n * sizeof(double));
+        memset(cur, 0, n * sizeof(double));
+        for (int t = 0; t < nt; ++t) {
+            if (t % ckpt == 0 && t / ckpt < n_seg) {
+                memcpy(snap + (size_t)(t / ckpt) * 2 * n, cur, n * sizeof(double));
+                memcpy(snap + (size_t)(t / ckpt) * 2 * n + n, prev, n * sizeof(double));
+            }
+            for (int r = 0; r < n_rx; ++r) trace[(size_t)t * n_rx + r] = cur[rx[r]];
+            if (t == nt - 1) break;
+            eq2_step(p, a, b, kap, cur, prev, next, lap);
+            next[src] += src_scale * w[t];
+            double *tmp = prev; prev = cur; cur = next; next = tmp;
+        }
+        /* residual and misfit; q[t][r] = dJ/dM_sim[t][r] = 2 (M_sim - M_obs) */
+        const double *obs = M_obs + (size_t)tx * nt * n_rx;
+        for (size_t i = 0; i < (size_t)nt * n_rx; ++i) {
+            double r = trace[i] - obs[i];
+            Jsum += r * r;
+            q[i] = 2.0 * r;
+        }
+        if (M_sim) memcpy(M_sim + (size_t)tx * nt * n_rx, trace, sizeof(double) * (size_t)nt * n_rx);
+        /* adjoint sweep, segment by segment from the last */
+        memset(l1, 0, n * sizeof(double));
+        memset(l2, 0, n * sizeof(double));
+        int t_hi = nt - 1;                       /* next adjoint index to produce */
+        for (int s = n_seg - 1; s >= 0; --s) {
+            int t0 = s * ckpt;                   /* segment steps t0..t1-1 produce U[t0+1..t1] */
+            int t1 = t0 + ckpt; if (t1 > nt - 1) t1 = nt - 1;
+            /* seg[k] = U[t0 + k] for k = 0..t1-t0 */
+            memcpy(seg, snap + (size_t)s * 2 * n, n * sizeof(double));
+            memcpy(prev, snap + (size_t)s * 2 * n + n, n * sizeof(double));
+            for (int t = t0; t < t1; ++t) {
+                double *u_t = seg + (size_t)(t - t0) * n;
+                double *u_prev = (t == t0) ? prev : seg + (size_t)(t - t0 - 1) * n;
+                double *u_next = seg + (size_t)(t - t0 + 1) * n;
+                eq2_step(p, a, b, kap, u_t, u_prev, u_next, lap);
+                u_next[src] += src_scale * w[t];
+            }
+            /* adjoint indices t = t_hi .. t0+1 pair with U[t-1] in this segment */
+            for (int t = t_hi; t >= t0 + 1; --t) {
+                adjoint_step(p, a, b, kap, l1, l2, l0, work, lap);
+                for (int r = 0; r < n_rx; ++r) l0[rx[r]] += q[(size_t)t * n_rx + r];
+                orc_laplacian(p, seg + (size_t)(t - 1 - t0) * n, lap);
+                for (size_t i = 0; i < n; ++i) gpad[i] += l0[i] * lap[i];
+                double *tmp = l2; l2 = l1; l1 = l0; l0 = tmp;
+            }
+            t_hi = t0;
+        }
+    }
+    if (status == ORC_OK) {
+        /* chain rule through kappa = C^2 dt^2/(1 + D dt), then fold the padding */
+        for (size_t i = 0; i < n; ++i)
+            gpad[i] *= 2.0 * Cpad[i] * p->dt * p->dt / (1.0 + D[i] * p->dt);
+        memset(g, 0, sizeof(double) * (size_t)p->nx * p->nz);
+        for (int z = 0; z < nzp; ++z)
+            for (int x = 0; x < nxp; ++x) {
+                int zs = clampi(z - p->pml, 0, p->nz - 1), xs = clampi(x - p->pml, 0, p->nx - 1);
+                g[(size_t)zs * p->nx + xs] += gpad[(size_t)z * nxp + x];
+            }
+        *J = Jsum;
+    }
+    free(base); free(snap); free(seg); free(gpad); free(trace); free(q); free(rx);
+    return status;
+}

@@ -1,0 +1,213 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the oracle's tests and the benchmark.
+
+This module draws speed-of-sound maps, the source pulse and the array geometry. It holds no
+part of the simulator's or the gradient's arithmetic. Every draw comes from
+``numpy.random.Generator(PCG64(seed))``.
+
+These inputs stand in for the paper's datasets (MNIST-derived maps, the simulated arm and the
+phantom rods, Sec. V). Those datasets are not available here. The maps reuse the paper's
+structure: a water-like background with compact inclusions (Sec. V, Sec. VII). The workloads:
+
+* ``disk``: one hard disk, radius U[1.5, 3] mm, SoS U[1450, 1520] m/s, in 1540 m/s.
+* ``grf_rods``: 1540 m/s plus a smooth Gaussian random field (+-20 m/s, correlation 3 mm),
+  plus 1-4 non-overlapping rods, radius U[1, 5] mm, SoS U[1450, 1600] m/s.
+* a linear array on the top physical row, point elements every 3 cells (0.3 mm at
+  dx = 0.1 mm), centred; transmits evenly spaced as floor((j + 0.5) n_elem / n_tx).
+* a 2 MHz Ricker pulse of peak 1, delayed by 1.5 / f0.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BACKGROUND_SOS = 1540.0
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def ricker(nt: int, dt: float, f0: float, delay: float | None = None) -> np.ndarray:
+    """Ricker pulse w(n dt) = (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2), tau = n dt - delay."""
+    if delay is None:
+        delay = 1.5 / f0
+    tau = np.arange(nt, dtype=np.float64) * dt - delay
+    arg = (math.pi * f0 * tau) ** 2
+    return ((1.0 - 2.0 * arg) * np.exp(-arg)).astype(np.float32)
+
+
+def gaussian_derivative_pulse(nt: int, dt: float, f0: float) -> np.ndarray:
+    """Time derivative of a Gaussian (the paper's simulated pulse shape, Sec. IV), peak |w| = 1."""
+    sigma = 1.0 / (2.0 * math.pi * f0)
+    tau = np.arange(nt, dtype=np.float64) * dt - 4.0 * sigma
+    w = -tau * np.exp(-0.5 * (tau / sigma) ** 2)
+    return (w / np.max(np.abs(w))).astype(np.float32)
+
+
+def linear_array(nx: int, n_elem: int, pitch_cells: int = 3, row: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Point elements on physical row ``row``, ``pitch_cells`` apart, centred in x."""
+    span = pitch_cells * (n_elem - 1)
+    if span >= nx:
+        raise ValueError("array of %d elements does not fit %d cells" % (n_elem, nx))
+    x0 = (nx - 1 - span) // 2
+    ix = x0 + pitch_cells * np.arange(n_elem, dtype=np.int32)
+    iz = np.full(n_elem, row, dtype=np.int32)
+    return ix.astype(np.int32), iz
+
+
+def ring_array(n: int, n_elem: int, radius_cells: float) -> tuple[np.ndarray, np.ndarray]:
+    """Point elements evenly spaced on a circle centred in an n x n grid (the paper's ring, Sec. IV)."""
+    c = (n - 1) / 2.0
+    ang = 2.0 * math.pi * np.arange(n_elem) / n_elem
+    ix = np.rint(c + radius_cells * np.cos(ang)).astype(np.int32)
+    iz = np.rint(c + radius_cells * np.sin(ang)).astype(np.int32)
+    return ix, iz
+
+
+def evenly_spaced_transmits(n_elem: int, n_tx: int) -> np.ndarray:
+    """Transmit element j = floor((j + 0.5) n_elem / n_tx)."""
+    return np.floor((np.arange(n_tx) + 0.5) * n_elem / n_tx).astype(np.int32)
+
+
+def disk_map(rng, nx: int, nz: int, dx: float, margin_m: float = 3e-3) -> np.ndarray:
+    """One hard disk (node-centre test) in the 1540 m/s background."""
+    r = rng.uniform(1.5e-3, 3e-3)
+    c = rng.uniform(1450.0, 1520.0)
+    lx, lz = (nx - 1) * dx, (nz - 1) * dx
+    cx = rng.uniform(min(margin_m, lx / 2), max(lx - margin_m, lx / 2))
+    cz = rng.uniform(min(margin_m, lz / 2), max(lz - margin_m, lz / 2))
+    X = np.arange(nx) * dx
+    Z = np.arange(nz) * dx
+    inside = (X[None, :] - cx) ** 2 + (Z[:, None] - cz) ** 2 <= r * r
+    sos = np.full((nz, nx), BACKGROUND_SOS, dtype=np.float64)
+    sos[inside] = c
+    return sos.astype(np.float32)
+
+
+def _gaussian_field(rng, nx: int, nz: int, sigma_cells: float) -> np.ndarray:
+    white = rng.standard_normal((nz, nx))
+    kx = np.fft.fftfreq(nx)[None, :]
+    kz = np.fft.fftfreq(nz)[:, None]
+    filt = np.exp(-2.0 * (math.pi * sigma_cells) ** 2 * (kx * kx + kz * kz))
+    return np.real(np.fft.ifft2(np.fft.fft2(white) * filt))
+
+
+def grf_rods_map(rng, nx: int, nz: int, dx: float, max_rods: int = 4,
+                 amp: float = 20.0, corr_m: float = 3e-3) -> np.ndarray:
+    """1540 m/s + smooth Gaussian random field (max |.| = amp) + 1..max_rods hard rods."""
+    f = _gaussian_field(rng, nx, nz, corr_m / math.sqrt(2.0) / dx)
+    f *= amp / max(np.max(np.abs(f)), 1e-30)
+    sos = BACKGROUND_SOS + f
+    X = np.arange(nx) * dx
+    Z = np.arange(nz) * dx
+    n_rods = int(rng.integers(1, max_rods + 1))
+    rods: list[tuple[float, float, float]] = []
+    tries = 0
+    while len(rods) < n_rods and tries < 1000:
+        tries += 1
+        r = rng.uniform(1e-3, 5e-3)
+        cx = rng.uniform(r, (nx - 1) * dx - r)
+        cz = rng.uniform(r, (nz - 1) * dx - r)
+        if any((cx - x) ** 2 + (cz - z) ** 2 < (r + q) ** 2 for x, z, q in rods):
+            continue
+        rods.append((cx, cz, r))
+        inside = (X[None, :] - cx) ** 2 + (Z[:, None] - cz) ** 2 <= r * r
+        sos[inside] = rng.uniform(1450.0, 1600.0)
+    return sos.astype(np.float32)
+
+
+@dataclass
+class Workload:
+    """One batch of maps on one grid: everything both implementations need as input."""
+    name: str
+    nx: int
+    nz: int
+    dx: float
+    dt: float
+    nt: int
+    sos_true: np.ndarray           # [B][nz][nx] float32, the map that produces the observed data
+    sos_start: np.ndarray          # [B][nz][nx] float32, the map the gradient is taken at
+    wavelet: np.ndarray            # [nt] float32 (shared by all transmits)
+    elem_ix: np.ndarray            # [n_elem] int32, physical-grid node indices
+    elem_iz: np.ndarray            # [n_elem] int32
+    tx_elem: np.ndarray            # [n_tx] int32, element index of each transmit
+    rx_elem: np.ndarray            # [n_tx][n_rx] int32, element indices receiving each transmit
+    pml: int = 20
+    pml_R: float = 1e-3
+    pml_cref: float = BACKGROUND_SOS
+    fd_order: int = 8
+    c_max: float = 1700.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_maps(self) -> int:
+        return self.sos_true.shape[0]
+
+    @property
+    def n_tx(self) -> int:
+        return self.tx_elem.size
+
+    @property
+    def n_rx(self) -> int:
+        return self.rx_elem.shape[1]
+
+    def tx_nodes(self):
+        return self.elem_ix[self.tx_elem], self.elem_iz[self.tx_elem]
+
+    def rx_nodes(self):
+        return self.elem_ix[self.rx_elem], self.elem_iz[self.rx_elem]
+
+    @property
+    def padded_cells(self) -> int:
+        return (self.nx + 2 * self.pml) * (self.nz + 2 * self.pml)
+
+
+def make_workload(name: str, seed: int = 0, *, n_maps: int | None = None, nt: int | None = None,
+                  n_tx: int | None = None, nx: int | None = None, nz: int | None = None,
+                  n_elem: int | None = None, fd_order: int = 8) -> Workload:
+    """Named workloads (sizes overridable for small test cases).
+
+    ``linear_disk``: 128 x 128, 2000 steps, 32 elements, 1 transmit (the centre element), all
+    receive; one disk map; the gradient is taken at the homogeneous 1540 m/s map.
+    ``full_shot_set``: 512 x 512, 6000 steps, 128 elements, 16 evenly spaced transmits, all
+    receive; ``grf_rods`` maps.
+    ``scale``: 1024 x 1024, 12000 steps, 128 elements, 64 transmits, up to 8 rods.
+    """
+    rng = rng_for(seed)
+    dx, dt, f0 = 1e-4, 1e-8, 2e6
+    if name == "linear_disk":
+        nx_, nz_, nt_, ne, ntx, B, kind = 128, 128, 2000, 32, 1, 1, "disk"
+    elif name == "full_shot_set":
+        nx_, nz_, nt_, ne, ntx, B, kind = 512, 512, 6000, 128, 16, 1, "grf_rods"
+    elif name == "scale":
+        nx_, nz_, nt_, ne, ntx, B, kind = 1024, 1024, 12000, 128, 64, 1, "grf_rods8"
+    else:
+        raise ValueError("unknown workload %r" % name)
+    nx_ = nx if nx is not None else nx_
+    nz_ = nz if nz is not None else nz_
+    nt_ = nt if nt is not None else nt_
+    ne = n_elem if n_elem is not None else ne
+    ntx = n_tx if n_tx is not None else ntx
+    B = n_maps if n_maps is not None else B
+    maps = []
+    for _ in range(B):
+        if kind == "disk":
+            maps.append(disk_map(rng, nx_, nz_, dx))
+        elif kind == "grf_rods":
+            maps.append(grf_rods_map(rng, nx_, nz_, dx, max_rods=4))
+        else:
+            maps.append(grf_rods_map(rng, nx_, nz_, dx, max_rods=8))
+    sos_true = np.stack(maps)
+    sos_start = np.full_like(sos_true, BACKGROUND_SOS)
+    elem_ix, elem_iz = linear_array(nx_, ne)
+    if ntx == 1:
+        tx = np.array([ne // 2], dtype=np.int32)
+    else:
+        tx = evenly_spaced_transmits(ne, ntx)
+    rx = np.tile(np.arange(ne, dtype=np.int32), (ntx, 1))
+    return Workload(name=name, nx=nx_, nz=nz_, dx=dx, dt=dt, nt=nt_, sos_true=sos_true,
+                    sos_start=sos_start, wavelet=ricker(nt_, dt, f0), elem_ix=elem_ix,
+                    elem_iz=elem_iz, tx_elem=tx, rx_elem=rx, fd_order=fd_order,
+                    meta={"seed": seed, "f0": f0, "kind": kind})

@@ -1,0 +1,346 @@
+"""Pins of the FP64 oracle against facts that the paper and the mathematics fix.
+
+Every test here runs on the CPU. Each one checks the oracle against something other than
+itself:
+
+* the damping maximum printed in Sec. IV;
+* the moment conditions that define the central stencils;
+* closed-form Laplacians of polynomials;
+* the analytic 2-D Green's function, evaluated by independent quadrature;
+* reciprocity and the adjoint dot-product identity;
+* brute-force central finite differences of the misfit;
+* exact symmetries: linearity, time shift and mirror symmetry.
+
+A plausible slip in the oracle fails at least one of them. Examples: a dropped dt, a
+one-step source shift, a wrong adjoint transpose, a sign or index error in the stencil.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_04070_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_problem(n=24, nt=240, pml=8, order=8, dx=1e-4, dt=1e-8, nz=None):
+    return oracle.Problem(nx=n, nz=nz or n, dx=dx, dt=dt, nt=nt, pml=pml, pml_R=1e-3,
+                          pml_cref=1540.0, fd_order=order)
+
+
+# --------------------------------------------------------------------------- constants
+def test_d0_matches_printed_value():
+    """Sec. IV prints a maximum damping of 1.46e6 for a 20-point quadratic layer, R = 1e-3,
+    on a 188-point grid over 10 cm in water."""
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        g = json.load(f)
+    dx = g["domain_m"] / g["grid_n"]
+    p = oracle.Problem(nx=g["grid_n"], nz=g["grid_n"], dx=dx, dt=1e-8, nt=2, pml=g["pml_cells"],
+                       pml_R=g["pml_R"], pml_cref=g["water_sos_m_s"], fd_order=8)
+    d0 = oracle.d0(p)
+    # printed to 3 significant digits
+    assert abs(d0 - g["d0_printed"]) <= 0.005e6
+    # the grid is the lambda/8 grid of the nominal centre frequency in water (to rounding)
+    lam = g["water_sos_m_s"] / g["center_frequency_hz"]
+    assert abs(g["domain_m"] / (lam / g["points_per_wavelength"]) - g["grid_n"]) < 2.0
+
+
+def test_damping_profile_shape():
+    p = _small_problem(n=10, pml=5)
+    D = oracle.damping(p)
+    d0 = oracle.d0(p)
+    P = p.pml
+    # zero on the physical grid, d0 on the outer edge, 2 d0 at the outer corner
+    assert np.all(D[P:P + p.nz, P:P + p.nx] == 0.0)
+    assert D[0, P + 3] == pytest.approx(d0, rel=1e-14)
+    assert D[P + 3, -1] == pytest.approx(d0, rel=1e-14)
+    assert D[0, 0] == pytest.approx(2 * d0, rel=1e-14)
+    # quadratic in the depth into the layer: D(i) = d0 ((P - i)/P)^2
+    for i in range(P):
+        assert D[P + 2, i] == pytest.approx(d0 * ((P - i) / P) ** 2, rel=1e-13)
+        assert D[P + 2, p.nxp - 1 - i] == pytest.approx(d0 * ((P - i) / P) ** 2, rel=1e-13)
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_stencil_moment_conditions(order):
+    """The central second-difference stencil of order 2h is the unique one with
+    sum_k c_|k| k^(2j) = 2 delta_{j,1} for j = 0..h (exact on polynomials of degree 2h+1)."""
+    c = oracle.fd_coeffs(order)
+    h = order // 2
+    assert c.size == h + 1
+    for j in range(h + 1):
+        m = c[0] * (1.0 if j == 0 else 0.0) + 2.0 * sum(c[k] * k ** (2 * j) for k in range(1, h + 1))
+        assert m == pytest.approx(2.0 if j == 1 else 0.0, abs=1e-13)
+
+
+@pytest.mark.parametrize("order", [2, 4, 8])
+def test_laplacian_of_polynomials(order):
+    p = _small_problem(n=20, pml=6, order=order, dx=0.5)
+    z, x = np.meshgrid(np.arange(p.nzp) * p.dx, np.arange(p.nxp) * p.dx, indexing="ij")
+    h = order // 2
+    inner = (slice(h, p.nzp - h), slice(h, p.nxp - h))
+    # constant and linear fields: zero Laplacian away from the zero exterior
+    for u in (np.ones_like(x), 3.0 * x - 2.0 * z + 1.0):
+        assert np.max(np.abs(oracle.laplacian(p, u)[inner])) < 1e-10
+    # x^2 + 3 z^2 -> 8 for every order
+    lap = oracle.laplacian(p, x * x + 3 * z * z)
+    assert np.max(np.abs(lap[inner] - 8.0)) < 1e-9
+    if order >= 4:   # quartic: exact for order >= 4
+        lap = oracle.laplacian(p, x ** 4)
+        assert np.max(np.abs(lap[inner] - 12 * x[inner] ** 2)) < 1e-7
+
+
+def test_laplacian_symmetric_with_zero_exterior():
+    p = _small_problem(n=12, pml=4)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((p.nzp, p.nxp))
+    v = rng.standard_normal((p.nzp, p.nxp))
+    a = np.sum(oracle.laplacian(p, u) * v)
+    b = np.sum(u * oracle.laplacian(p, v))
+    assert abs(a - b) <= 1e-12 * (abs(a) + abs(b))
+
+
+def test_pad_is_edge_replication():
+    p = _small_problem(n=6, pml=3, nz=5)
+    C = np.arange(30, dtype=np.float64).reshape(5, 6) + 1500
+    Cp = oracle.pad(p, C)
+    assert np.array_equal(Cp, np.pad(C, 3, mode="edge"))
+
+
+# --------------------------------------------------------------------------- Green's function
+def _ricker(t, f0, delay):
+    a = (math.pi * f0 * (t - delay)) ** 2
+    return (1 - 2 * a) * np.exp(-a)
+
+
+def _green_trace(r, c, times, f0, delay, n_gl=3000):
+    """u(r,t) for u_tt - c^2 lap u = w(t) delta(x): (1/(2 pi c^2)) int_0^acosh(ct/r) w(t - r cosh(s)/c) ds,
+    with w = 0 before t = 0 (the discrete source starts at sample 0)."""
+    xg, wg = np.polynomial.legendre.leggauss(n_gl)
+    out = np.zeros(times.size)
+    for i, t in enumerate(times):
+        if c * t <= r:
+            continue
+        smax = math.acosh(c * t / r)
+        s = 0.5 * smax * (xg + 1.0)
+        tau = t - (r / c) * np.cosh(s)
+        out[i] = 0.5 * smax * np.sum(wg * _ricker(tau, f0, delay)) / (2 * math.pi * c * c)
+    return out
+
+
+def _green_errors(order, dx, f0, n, src, rxs, T, dt, c=1500.0):
+    nt = int(round(T / dt))
+    p = oracle.Problem(nx=n, nz=n, dx=dx, dt=dt, nt=nt, pml=20, pml_R=1e-3, pml_cref=c,
+                       fd_order=order)
+    w = _ricker(np.arange(nt) * dt, f0, 1.5 / f0)
+    tr = oracle.forward(p, np.full((n, n), c), src, w,
+                        np.array([r[0] for r in rxs]), np.array([r[1] for r in rxs]))
+    times = np.arange(nt) * dt
+    errs = []
+    for k, r in enumerate(rxs):
+        ref = _green_trace(math.hypot(r[0] - src[0], r[1] - src[1]) * dx, c, times, f0, 1.5 / f0)
+        errs.append(np.linalg.norm(tr[:, k] - ref) / np.linalg.norm(ref))
+    return max(errs)
+
+
+def test_green_function_trace_order8():
+    """Homogeneous medium, 8th-order stencil, traces read before the first border return.
+    The error is the leapfrog's time dispersion: second order in dt (halving dt divides it
+    by about 4)."""
+    rxs = [(105, 80), (80, 45), (98, 98)]
+    e1 = _green_errors(8, 1e-4, 1.0e6, 161, (80, 80), rxs, 7e-6, 5e-9)
+    e2 = _green_errors(8, 1e-4, 1.0e6, 161, (80, 80), rxs, 7e-6, 2.5e-9)
+    assert e1 < 2e-3 and e2 < 5e-4, (e1, e2)
+    assert 3.0 < e1 / e2 < 6.0, (e1, e2)
+
+
+def test_green_function_trace_order2():
+    """Second-order stencil at 60 points per wavelength of the centre frequency."""
+    rxs = [(145, 120), (120, 85), (138, 138)]
+    e = _green_errors(2, 1e-4, 0.25e6, 241, (120, 120), rxs, 13e-6, 5e-9)
+    assert e < 1e-2, e
+
+
+def test_source_time_index_is_detectable():
+    """A one-sample shift of the source is far outside the Green's tolerance (guards the
+    time-index reading of the source term)."""
+    c, dx, dt, f0 = 1500.0, 1e-4, 2.5e-9, 1.0e6
+    n, nt = 121, 2400
+    p = oracle.Problem(nx=n, nz=n, dx=dx, dt=dt, nt=nt, pml=20, pml_cref=c, fd_order=8)
+    w = _ricker(np.arange(nt) * dt, f0, 1.5 / f0)
+    C = np.full((n, n), c)
+    tr = oracle.forward(p, C, (60, 60), w, np.array([85]), np.array([60]))[:, 0]
+    ref = _green_trace(25 * dx, c, np.arange(nt) * dt, f0, 1.5 / f0)
+    err = np.linalg.norm(tr - ref) / np.linalg.norm(ref)
+    shifted = np.linalg.norm(np.roll(tr, 1) - ref) / np.linalg.norm(ref)
+    assert err < 5e-4 and shifted > 20 * err, (err, shifted)
+
+
+# --------------------------------------------------------------------------- reciprocity and adjoint
+def _hetero_map(rng, n, nz=None):
+    nz = nz or n
+    return 1540.0 + 40.0 * rng.standard_normal((nz, n))
+
+
+def test_reciprocity():
+    """trace(s->r) kappa_s = trace(r->s) kappa_r for the damped scheme (K^-1 P K = P^T)."""
+    rng = np.random.default_rng(3)
+    p = _small_problem(n=30, nt=300, pml=10)
+    C = _hetero_map(rng, 30)
+    w = inputs.ricker(p.nt, p.dt, 2e6).astype(np.float64)
+    s, r = (5, 3), (22, 17)
+    t_sr = oracle.forward(p, C, s, w, np.array([r[0]]), np.array([r[1]]))[:, 0]
+    t_rs = oracle.forward(p, C, r, w, np.array([s[0]]), np.array([s[1]]))[:, 0]
+    ks = C[s[1], s[0]] ** 2
+    kr = C[r[1], r[0]] ** 2
+    assert np.max(np.abs(t_sr * ks - t_rs * kr)) <= 1e-11 * np.max(np.abs(t_sr * ks))
+    # and the two traces genuinely differ when kappa_s != kappa_r
+    assert np.max(np.abs(t_sr - t_rs)) > 1e-4 * np.max(np.abs(t_sr))
+
+
+def test_adjoint_dot_product():
+    """<F w, q> = <w, F^T q> with F: source series at one node -> receiver traces."""
+    rng = np.random.default_rng(4)
+    p = _small_problem(n=26, nt=200, pml=8, nz=22)
+    C = _hetero_map(rng, 26, 22)
+    rx_ix = np.array([2, 9, 20, 25, 13], dtype=np.int32)
+    rx_iz = np.array([0, 5, 21, 11, 13], dtype=np.int32)
+    src = (7, 15)
+    w = rng.standard_normal(p.nt)
+    q = rng.standard_normal((p.nt, rx_ix.size))
+    Fw = oracle.forward(p, C, src, w, rx_ix, rx_iz)
+    lam = oracle.adjoint_probe(p, C, rx_ix, rx_iz, q, src)
+    lhs = np.sum(Fw * q)
+    rhs = p.dt ** 2 / p.dx ** 2 * np.sum(w[:-1] * lam[1:])
+    assert abs(lhs - rhs) <= 1e-13 * (np.sum(np.abs(Fw * q)))
+
+
+# --------------------------------------------------------------------------- gradient
+def _tiny_case(rng, n=16, nt=160, n_tx=2, pml=6, order=8):
+    p = _small_problem(n=n, nt=nt, pml=pml, order=order)
+    C_true = _hetero_map(rng, n)
+    C0 = np.full((n, n), 1540.0) + 5.0 * rng.standard_normal((n, n))
+    tx_ix = np.array([3, 12][:n_tx], dtype=np.int32)
+    tx_iz = np.array([0, 0][:n_tx], dtype=np.int32)
+    rx_ix = np.tile(np.minimum(np.array([0, 4, 8, 12, 15], dtype=np.int32), n - 1), (n_tx, 1))
+    rx_iz = np.tile(np.minimum(np.array([0, 0, 15, 0, 7], dtype=np.int32), n - 1), (n_tx, 1))
+    w = inputs.ricker(nt, p.dt, 2e6).astype(np.float64)
+    M_obs = np.stack([oracle.forward(p, C_true, (tx_ix[k], tx_iz[k]), w, rx_ix[k], rx_iz[k])
+                      for k in range(n_tx)])
+    return p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs
+
+
+def test_gradient_matches_finite_differences_random_direction():
+    rng = np.random.default_rng(5)
+    p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs = _tiny_case(rng, n=20, nt=200)
+    J, g = oracle.misfit_gradient(p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs)
+    for trial in range(3):
+        d = rng.standard_normal(C0.shape)
+        h = 1e-2
+        Jp, _ = oracle.misfit_gradient(p, C0 + h * d, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs)
+        Jm, _ = oracle.misfit_gradient(p, C0 - h * d, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs)
+        fd = (Jp - Jm) / (2 * h)
+        an = np.sum(g * d)
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_gradient_brute_force_every_cell():
+    """Central differences at every physical cell of a 12 x 12 grid, including the edge
+    cells whose gradient collects the folded absorbing layer."""
+    rng = np.random.default_rng(6)
+    p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs = _tiny_case(rng, n=12, nt=120, n_tx=1, pml=5)
+    M_obs = oracle.forward(p, C0 + 30.0, (tx_ix[0], tx_iz[0]), w, rx_ix[0], rx_iz[0])[None]
+    J, g = oracle.misfit_gradient(p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs)
+    h = 1e-2
+    fd = np.zeros_like(g)
+    for iz in range(p.nz):
+        for ix in range(p.nx):
+            Cp = C0.copy(); Cp[iz, ix] += h
+            Cm = C0.copy(); Cm[iz, ix] -= h
+            Jp, _ = oracle.misfit_gradient(p, Cp, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs)
+            Jm, _ = oracle.misfit_gradient(p, Cm, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs)
+            fd[iz, ix] = (Jp - Jm) / (2 * h)
+    assert np.max(np.abs(fd - g)) <= 1e-6 * np.max(np.abs(g))
+
+
+def test_zero_residual_gives_zero_gradient():
+    rng = np.random.default_rng(7)
+    p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, _ = _tiny_case(rng)
+    M = np.stack([oracle.forward(p, C0, (tx_ix[k], tx_iz[k]), w, rx_ix[k], rx_iz[k])
+                  for k in range(tx_ix.size)])
+    J, g = oracle.misfit_gradient(p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M)
+    assert J == 0.0 and np.all(g == 0.0)
+
+
+def test_checkpointed_gradient_equals_stored():
+    rng = np.random.default_rng(8)
+    p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs = _tiny_case(rng, nt=157)
+    ref = oracle.misfit_gradient(p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs, ckpt=0, return_traces=True)
+    for k in (1, 7, 25, 156, 157):
+        out = oracle.misfit_gradient(p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs, ckpt=k, return_traces=True)
+        assert out[0] == ref[0] and np.array_equal(out[1], ref[1]) and np.array_equal(out[2], ref[2])
+
+
+def test_misfit_is_sum_of_squares_and_traces_match_forward():
+    rng = np.random.default_rng(9)
+    p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs = _tiny_case(rng)
+    J, g, M_sim = oracle.misfit_gradient(p, C0, tx_ix, tx_iz, w, rx_ix, rx_iz, M_obs, return_traces=True)
+    for k in range(tx_ix.size):
+        assert np.array_equal(M_sim[k], oracle.forward(p, C0, (tx_ix[k], tx_iz[k]), w, rx_ix[k], rx_iz[k]))
+    assert J == pytest.approx(np.sum((M_sim - M_obs) ** 2), rel=1e-14)
+    # the first sample is U[0] = 0
+    assert np.all(M_sim[:, 0, :] == 0.0)
+
+
+# --------------------------------------------------------------------------- exact symmetries
+def test_wavelet_linearity_and_time_shift():
+    rng = np.random.default_rng(10)
+    p = _small_problem(n=24, nt=220, pml=8)
+    C = _hetero_map(rng, 24)
+    rx_ix, rx_iz = np.array([3, 20]), np.array([0, 18])
+    w1 = rng.standard_normal(p.nt)
+    w2 = rng.standard_normal(p.nt)
+    f = lambda w: oracle.forward(p, C, (12, 4), w, rx_ix, rx_iz)
+    lin = f(2.0 * w1 - 0.5 * w2)
+    assert np.max(np.abs(lin - (2.0 * f(w1) - 0.5 * f(w2)))) <= 1e-12 * np.max(np.abs(lin))
+    k = 13
+    ws = np.concatenate([np.zeros(k), w1[:-k]])
+    assert np.array_equal(f(ws)[k:], f(w1)[:-k])
+    assert np.all(f(ws)[:k] == 0.0)
+
+
+def test_mirror_symmetry():
+    rng = np.random.default_rng(11)
+    n = 25
+    p = _small_problem(n=n, nt=200, pml=7)
+    half = 1540.0 + 30.0 * rng.standard_normal((n, n // 2 + 1))
+    C = np.concatenate([half, half[:, -2::-1]], axis=1)
+    assert np.array_equal(C, C[:, ::-1])
+    w = inputs.ricker(p.nt, p.dt, 2e6).astype(np.float64)
+    rx_ix = np.array([3, n - 1 - 3, 9, n - 1 - 9])
+    rx_iz = np.array([20, 20, 2, 2])
+    tr = oracle.forward(p, C, (n // 2, 5), w, rx_ix, rx_iz)
+    scale = np.max(np.abs(tr))
+    assert np.max(np.abs(tr[:, 0] - tr[:, 1])) <= 1e-12 * scale
+    assert np.max(np.abs(tr[:, 2] - tr[:, 3])) <= 1e-12 * scale
+
+
+def test_absorbing_layer_reflection_bound():
+    """Compared with a domain three times as large, the border return seen at a receiver 8 cells
+    from the 20-cell layer stays below 2.5% of the direct arrival, and a 30-cell layer
+    reflects less than half as much."""
+    c, dx, dt, f0 = 1540.0, 1e-4, 1e-8, 2e6
+    nt = 700
+    w = inputs.ricker(nt, dt, f0).astype(np.float64)
+    refl = []
+    for P in (20, 30):
+        small = oracle.Problem(nx=60, nz=60, dx=dx, dt=dt, nt=nt, pml=P, pml_cref=c, fd_order=8)
+        big = oracle.Problem(nx=180, nz=180, dx=dx, dt=dt, nt=nt, pml=P, pml_cref=c, fd_order=8)
+        tr_s = oracle.forward(small, np.full((60, 60), c), (30, 30), w, np.array([52]), np.array([30]))[:, 0]
+        tr_b = oracle.forward(big, np.full((180, 180), c), (90, 90), w, np.array([112]), np.array([90]))[:, 0]
+        refl.append(np.max(np.abs(tr_s - tr_b)) / np.max(np.abs(tr_b)))
+    assert refl[0] < 2.5e-2 and refl[1] < 0.5 * refl[0], refl

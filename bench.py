@@ -1,0 +1,341 @@
+"""Benchmark of the FWI gradient hot path (forward + checkpointed adjoint) on GB300.
+
+One step is one misfit-gradient call over every shot of one batch. The full-shot-set workload
+is a 512 x 512 grid (552 x 552 with the 20-cell absorbing layer), 6000 steps, a 128-element
+linear array, 16 evenly spaced transmits and 128 receivers. The gradient uses the checkpointed
+adjoint (snapshots every 100 steps, FP32). Inputs are synthetic and seeded (a Gaussian random
+field plus rods), and resident in HBM before the timed region starts.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+It prints one JSON line (rank 0). With N > 1 (torchrun), every rank runs its own map (seed =
+rank) with no collective on the data path: weak scaling. The reference arm is the FP64 CPU
+oracle, timed on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FWI gradient Gcell-updates/s (fwd+adj)"
+UNIT = "Gcell-updates/s"
+# Algorithmic bytes per padded cell and launch (FP32): forward step reads U^n, U^{n-1}, kappa and
+# writes U^{n+1}; the recompute step also writes Lap(U^n); the adjoint step reads mu^{m+1},
+# mu^{m+2}, kappa, Lap(U^{m-1}) and writes mu^m (the imaging sum ideally stays on chip).
+ALGO_BYTES = {"forward": 16, "recompute": 20, "adjoint": 20}
+GRADIENT_BYTES_PER_CELL = 40          # forward 16 + history 4 + 4 + adjoint 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="full_shot_set")
+    ap.add_argument("--ckpt", type=int, default=100)
+    ap.add_argument("--snapshot", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        self.out = tempfile.TemporaryFile(mode="w+")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_traffic(kind: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = os.path.join(ROOT, "paper_2603_04070_gb300", "csrc", "dufwi_kernels.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("kernel_source_sha256") != sha:
+            return None
+        return rec.get("per_launch_dram_bytes_full_size", {}).get(kind)
+    except Exception:
+        return None
+
+
+def cpu_oracle_sample(wl, n_steps: int):
+    """Oracle gradient of one transmit over the first n_steps samples (FP64, OpenMP)."""
+    import oracle
+    nt = n_steps
+    p = oracle.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=nt, pml=wl.pml, pml_R=wl.pml_R,
+                       pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    w = wl.wavelet[:nt].astype(np.float64)
+    obs = np.zeros((1, nt, wl.n_rx))
+    t0 = time.perf_counter()
+    oracle.misfit_gradient(p, wl.sos_start[0].astype(np.float64), tix[:1], tiz[:1], w, rix[:1], riz[:1], obs)
+    dt = time.perf_counter() - t0
+    cells = (wl.nx + 2 * wl.pml) * (wl.nz + 2 * wl.pml)
+    return 2.0 * cells * nt / dt / 1e9, dt
+
+
+def omp_cores():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2603_04070_gb300 import inputs
+    wl = inputs.make_workload(args.workload, seed=0)
+    sample_steps = 200
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, sample_steps)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        v, dt = cpu_oracle_sample(wl, sample_steps)
+        vals.append(v)
+        secs += dt
+    value = 2.0 * wl.padded_cells * sample_steps * args.steps / secs / 1e9
+    sample = ("FP64 oracle misfit gradient of 1 of %d transmits, first %d of %d steps, %dx%d grid "
+              "(%dx%d padded)" % (wl.n_tx, sample_steps, wl.nt, wl.nx, wl.nz, wl.nx + 2 * wl.pml, wl.nz + 2 * wl.pml))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": omp_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(wl, args):
+    return {"workload": "%s: %dx%d grid (+%d absorbing cells per side), %d steps, %d elements, %d transmits, "
+                        "%d receivers, checkpointed adjoint (every %d steps, %s snapshots)"
+                        % (wl.name, wl.nx, wl.nz, wl.pml, wl.nt, wl.elem_ix.size, wl.n_tx, wl.n_rx,
+                           args.ckpt, args.snapshot),
+            "grid": [wl.nz, wl.nx], "padded_grid": [wl.nz + 2 * wl.pml, wl.nx + 2 * wl.pml], "nt": wl.nt,
+            "maps_per_gpu": wl.n_maps, "n_tx": wl.n_tx, "n_rx": wl.n_rx, "fd_order": wl.fd_order,
+            "ckpt_interval": args.ckpt, "snapshot_dtype": args.snapshot,
+            "l2": "flushed between timed steps (256 MiB write outside the events)"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2603_04070_gb300 import build_lib, inputs
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+
+    wl = inputs.make_workload(args.workload, seed=rank)
+    pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
+                       pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
+                       ckpt_interval=args.ckpt, c_max=wl.c_max)
+    geom = dufwi.Geometry.from_workload(wl)
+    sos_true = torch.from_numpy(wl.sos_true).to(dev)
+    sos = torch.from_numpy(wl.sos_start).to(dev)
+    wav = torch.from_numpy(wl.wavelet).to(dev)
+    obs = dufwi.simulate(pb, sos_true, wav, geom, check=True)
+    ws = torch.empty(dufwi.workspace_size(pb, geom, wl.n_maps), dtype=torch.uint8, device=dev)
+    misfit = torch.empty(wl.n_maps, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(sos)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dufwi.misfit_gradient(pb, sos, wav, geom, obs, misfit=misfit, grad=grad, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    status = dufwi.workspace_status(ws)
+    if status != 0:
+        raise RuntimeError("device status %s" % dufwi.status_string(status))
+
+    # timed region: K steps, device time by CUDA events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dufwi.profile_enable(True)
+    dufwi.profile_read(reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = dufwi.launch_count()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    n_launch = dufwi.launch_count() - n_launch0
+    prof = dufwi.profile_read(reset=True)
+    dufwi.profile_enable(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    cells = wl.padded_cells
+    S = wl.n_maps * wl.n_tx
+    units_per_step = 2.0 * cells * wl.nt * S                       # fwd + adj cell updates
+    value = units_per_step * world * args.steps / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    hbm_frac = GRADIENT_BYTES_PER_CELL * cells * wl.nt * S / (peak * 1e9) / (ms_step / 1e3)
+
+    # dominant kernel: the sweep kind with the largest share of device time
+    kinds = ["forward", "recompute", "adjoint"]
+    dom = max(kinds, key=lambda k: prof[k]["ms"])
+    avg_launch_ms = prof[dom]["ms"] / max(prof[dom]["launches"], 1)
+    bytes_per_launch = ALGO_BYTES[dom] * cells * S
+    achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "step_kernel (%s sweep)" % dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": kernel_traffic(dom), "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": 1e3 * avg_launch_ms,
+                "sweep_ms_per_step": {k: prof[k]["ms"] / args.steps for k in kinds + ["other"]},
+                "launches_per_step": {k: prof[k]["launches"] / args.steps for k in kinds + ["other"]}}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_sos = torch.from_numpy(wl.sos_start).pin_memory()
+        h_obs = obs.cpu().pin_memory()
+        h_wav = torch.from_numpy(wl.wavelet).pin_memory()
+        h_grad = torch.empty(grad.shape, dtype=torch.float32).pin_memory()
+        h_mis = torch.empty(misfit.shape, dtype=torch.float64).pin_memory()
+        d_sos, d_obs, d_wav = torch.empty_like(sos), torch.empty_like(obs), torch.empty_like(wav)
+
+        def e2e_step():
+            d_sos.copy_(h_sos, non_blocking=True)
+            d_obs.copy_(h_obs, non_blocking=True)
+            d_wav.copy_(h_wav, non_blocking=True)
+            dufwi.misfit_gradient(pb, d_sos, d_wav, geom, d_obs, misfit=misfit, grad=grad, workspace=ws)
+            h_grad.copy_(grad, non_blocking=True)
+            h_mis.copy_(misfit, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = h_sos.numel() * 4 + h_obs.numel() * 4 + h_wav.numel() * 4
+        d2h = h_grad.numel() * 4 + h_mis.numel() * 8
+        e2e = {"value": units_per_step * world * args.steps / (ems / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps = 1000
+        v, dt = cpu_oracle_sample(wl, steps)
+        cpu = {"value": v, "unit": UNIT, "cores": omp_cores(), "kind": "oracle",
+               "sample": "FP64 oracle misfit gradient of 1 of %d transmits over the first %d of %d steps on the "
+                         "same %dx%d grid (%.1f s)" % (wl.n_tx, steps, wl.nt, wl.nx, wl.nz, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded GRF + rods SoS maps; observed data "
+                "simulated from the true map on the GPU)", "config": workload_config(wl, args),
+                "hbm_roofline_frac_40B": hbm_frac, "ms_per_gradient": ms_step,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
+                "clocks": clk.summary(), "profile_complete": prof["complete"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * dufwi.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot path of deep-unfolded
+ * full waveform inversion (DUFWI, arXiv 2603.04070). The library provides:
+ *   - the time-domain damped acoustic simulation of transducer channel data (Sec. II-A, Eqs. 1-4);
+ *   - the misfit of that simulation against observed data and its gradient with respect to the
+ *     speed-of-sound (SoS) map (Sec. II-B, Eqs. 5-6). Every unfolded iteration consumes this
+ *     gradient (Sec. III-A, Eq. 9).
+ *
+ * Conventions shared by every entry point:
+ *   - Grids are row-major [z][x], x contiguous. The SoS map covers the physical grid nz x nx.
+ *     The library adds `pml_cells` absorbing cells on every side internally, and extends the
+ *     SoS into that layer by edge replication.
+ *   - A "shot" is one (map, transmit) pair. Shots of map b are b*n_tx .. b*n_tx + n_tx - 1.
+ *   - Channel data (CD) follow Eq. 3: M[p] is nt x n_rx, with M[p][t][r] the field U[t] at
+ *     receiver r of transmit p, for t = 0..nt-1. U[0] = U[-1] = 0, so M[p][0][r] = 0.
+ *   - Device arrays are caller-owned device pointers. Geometry tables are host pointers, which
+ *     the library copies into the workspace with stream-ordered copies. The library allocates
+ *     no memory: callers query the workspace size first and pass a device buffer at least that
+ *     large, aligned to 256 bytes.
+ *   - Every call is asynchronous on the given stream and returns a status code. Host-side
+ *     argument checks are reported by the return value. Conditions only visible on the device
+ *     are recorded in a status word inside the workspace and read with dufwi_workspace_status:
+ *       * an SoS value that is not finite, or not in (0, c_max];
+ *       * non-finite observed data;
+ *       * a non-constant density;
+ *       * a bounded device wait that ran out.
+ *     No C++ exception crosses this boundary.
+ */
+#ifndef DUFWI_H
+#define DUFWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define DUFWI_OK                 0
+#define DUFWI_ERR_INVALID_ARG    1  /* a size, pointer or option is out of range */
+#define DUFWI_ERR_CFL            2  /* c_max dt/dx above the stencil's stability limit, or SoS > c_max */
+#define DUFWI_ERR_GEOMETRY       3  /* an element lies outside the physical grid */
+#define DUFWI_ERR_UNSUPPORTED    4  /* variable density (Eq. 1 with non-constant rho) */
+#define DUFWI_ERR_WORKSPACE      5  /* workspace too small or misaligned */
+#define DUFWI_ERR_CUDA           6  /* a CUDA runtime call failed */
+#define DUFWI_ERR_TIMEOUT        7  /* a bounded device wait gave up */
+#define DUFWI_ERR_NONFINITE      8  /* NaN/Inf in the SoS map or in the observed data */
+
+/* Storage type of the checkpoint snapshots used by dufwi_misfit_gradient. */
+#define DUFWI_SNAP_FP32 0           /* (U[t], U[t-1]) in FP32, exact */
+#define DUFWI_SNAP_BF16 1           /* (U[t], U[t]-U[t-1]) in BF16, each scaled by its max |.| */
+#define DUFWI_SNAP_FP16 2           /* (U[t], U[t]-U[t-1]) in FP16, each scaled by its max |.| */
+
+/* Problem description: grid, time axis, absorbing layer, stencil, checkpointing.
+ * Eq. 2 (Sec. II-A) is advanced with the coefficient maps
+ *   a = (2 - D^2 dt^2)/(1 + D dt),  b = (D dt - 1)/(1 + D dt),  kappa = C^2 dt^2/(1 + D dt),
+ * and the Laplacian is the central stencil of order fd_order divided by dx^2. The damping is
+ * D(x,z) = d(xi_x) + d(xi_z), with d(xi) = d0 (xi/L)^2, L = pml_cells * dx, and
+ * d0 = 3 pml_cref ln(1/pml_R) / (2L) (Sec. IV). */
+typedef struct {
+    int32_t nx, nz;          /* physical grid (cells), >= 1 each */
+    double  dx, dt;          /* grid spacing (m) and time step (s), > 0 */
+    int32_t nt;              /* recorded samples t = 0..nt-1, >= 1 */
+    int32_t pml_cells;       /* absorbing cells per side, >= 1 (paper: 20) */
+    double  pml_R;           /* target reflection factor in (0,1) (paper: 1e-3) */
+    double  pml_cref;        /* reference SoS for d0, m/s (paper's water: 1500) */
+    int32_t fd_order;        /* Laplacian order: 2, 4, 6 or 8 */
+    int32_t snapshot_dtype;  /* DUFWI_SNAP_*; ignored by dufwi_simulate */
+    int32_t ckpt_interval;   /* snapshot interval K in steps; 0 = keep every step (no recompute) */
+    double  c_max;           /* upper bound of every SoS value (m/s), used for the CFL check */
+} dufwi_problem;
+
+/* Transducer elements: physical-grid node indices (host arrays of n_elem entries). Elements
+ * are point sources/receivers at nodes (the paper's elements act as both, Sec. II-A). */
+typedef struct {
+    int32_t n_elem;
+    const int32_t *ix;
+    const int32_t *iz;
+} dufwi_array;
+
+/* Transmit/receive pattern shared by every map (host arrays). Sequential transmission
+ * (Sec. II-A): transmit p fires element tx_elem[p]; elements rx_elem[p][0..n_rx-1] record.
+ * The receive subset may change between transmits. wavelet_per_tx = 0: one pulse [nt] for
+ * all transmits; 1: one pulse per transmit [n_tx][nt]. */
+typedef struct {
+    int32_t n_tx, n_rx;
+    const int32_t *tx_elem;   /* [n_tx] */
+    const int32_t *rx_elem;   /* [n_tx][n_rx] */
+    int32_t wavelet_per_tx;
+} dufwi_shots;
+
+/* Bytes of workspace needed by dufwi_simulate for n_maps maps. */
+int dufwi_simulate_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots,
+                                  int32_t n_maps, size_t *bytes);
+
+/* Bytes of workspace needed by dufwi_misfit_gradient for n_maps maps. It counts the snapshots
+ * (every ckpt_interval steps) and one segment of recomputed history. */
+int dufwi_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int32_t n_maps,
+                         size_t *bytes);
+
+/* Forward model, Eqs. 2-4: the channel data of every shot.
+ *   sos      [n_maps][nz][nx] float, device, m/s
+ *   density  NULL (constant density, as in the paper) or [n_maps][nz][nx] float, device. The
+ *            result does not depend on a constant density. A non-constant one sets
+ *            DUFWI_ERR_UNSUPPORTED in the workspace status word.
+ *   wavelet  [nt] or [n_tx][nt] float, device. The source adds dt^2 w[t]/dx^2 at the transmit
+ *            node in the step that produces U[t+1].
+ *   cd       [n_maps][n_tx][nt][n_rx] float, device, output (may be NULL when n_rx = 0)
+ *   workspace: device, >= dufwi_simulate_workspace_size bytes. */
+int dufwi_simulate(const dufwi_problem *pb, const float *sos, const float *density,
+                   const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                   int32_t n_maps, float *cd, void *workspace, size_t workspace_bytes,
+                   void *stream /* cudaStream_t */);
+
+/* Misfit and gradient, Eqs. 5-6 with lambda = 0, per map b:
+ *   J[b] = sum over transmits, samples and receivers of (M_sim - M_obs)^2 (FP64 sum)
+ *   g[b] = dJ[b]/dC on the physical grid. This is the exact gradient of the discrete J: the
+ *          discrete adjoint of Eq. 2, with the zero-lag imaging condition, reduced over
+ *          transmits in FP64, with the absorbing layer folded onto the edge cells.
+ *   cd_obs  [n_maps][n_tx][nt][n_rx] float, device (may be NULL when n_rx = 0)
+ *   misfit  [n_maps] double, device, output
+ *   grad    [n_maps][nz][nx] float, device, output
+ *   cd_sim  NULL or [n_maps][n_tx][nt][n_rx] float, device, output (the simulated data)
+ *   workspace: device, >= dufwi_workspace_size bytes. */
+int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float *density,
+                          const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                          int32_t n_maps, const float *cd_obs, double *misfit, float *grad,
+                          float *cd_sim, void *workspace, size_t workspace_bytes,
+                          void *stream /* cudaStream_t */);
+
+/* Waits for the stream, then returns the device-side status word of the last call that used
+ * this workspace (DUFWI_OK if none was raised). */
+int dufwi_workspace_status(const void *workspace, void *stream /* cudaStream_t */);
+
+/* Human-readable name of a status code (static storage). */
+const char *dufwi_status_string(int status);
+
+/* Largest stable c_max*dt/dx of the leapfrog scheme with the fd_order stencil in 2-D:
+ * 2/sqrt(2 rho), rho = -(c_0 + 2 sum_k (-1)^k c_k) the magnitude of the 1-D stencil at the
+ * Nyquist wavenumber. Returns a negative value for an unsupported order. */
+double dufwi_cfl_limit(int32_t fd_order);
+
+/* Sweep timing for measurement tools. While enabled, each call records CUDA events on its stream
+ * around every sweep: the first forward sweep, each recompute segment, each adjoint segment, and
+ * the remaining setup/residual/fold kernels. dufwi_profile_enable(1) creates a fixed pool of
+ * events on the current device (outside any hot path); dufwi_profile_enable(0) destroys it.
+ * dufwi_profile_read waits for the last recorded event, then writes the accumulated time (ms)
+ * and the kernel launches per kind into ms[4] and launches[4]:
+ *   0 forward sweep, 1 recompute, 2 adjoint, 3 other.
+ * reset != 0 clears the accumulators. Recording stops silently when the pool is exhausted,
+ * and the function then returns DUFWI_ERR_WORKSPACE. */
+int dufwi_profile_enable(int enable);
+int dufwi_profile_read(double *ms, int64_t *launches, int reset);
+
+/* Number of kernels this library has launched since it was loaded (all devices, all calls). */
+int64_t dufwi_launch_count(void);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+int32_t dufwi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DUFWI_H */

@@ -1,0 +1,83 @@
+// dufwi_internal.h -- shared declarations of the sm_103a kernels and the host-side ABI code.
+//
+// Data layout in device memory (one workspace, carved by the host code):
+//   field  [S][nzp][pitch] float, S = n_maps * n_tx shots; the padded grid is nzp x nxp with
+//          nxp = nx + 2P and nzp = nz + 2P; pitch = nxp rounded up to 8 floats (32-byte rows).
+//          Columns nxp..pitch-1 are never read by the stencil (the TMA box treats x >= nxp as
+//          outside the tensor, i.e. zero).
+//   kappa  [n_maps][nzp][pitch] float: kappa' = C^2 dt^2 / (dx^2 (1 + D dt)), the Eq. 2
+//          coefficient with the 1/dx^2 of the Laplacian folded in. It is computed once per call
+//          in FP64 and rounded once.
+//   node   packed (zp << 16) | xp padded-grid node of an element.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dufwi {
+
+constexpr int kTileX = 64;                    // output tile width (x, contiguous)
+constexpr int kTileZ = 64;                    // output tile height (z)
+constexpr int kHalo = 4;                      // halo loaded on every side (max stencil radius)
+constexpr int kBoxX = kTileX + 2 * kHalo;     // TMA box: 72 floats = 288 bytes per row
+constexpr int kBoxZ = kTileZ + 2 * kHalo;
+constexpr int kThreads = 256;                 // 16 x 16 threads, 4 (x) x 4 (z) outputs each
+
+// Step kernel variants.
+enum StepMode : int {
+    kFwdSample = 0,      // forward step, record receivers (simulation, first pass with snapshots)
+    kFwdSampleHist = 1,  // forward step, record receivers, keep Lap(U^n) (store-all first pass)
+    kFwdHist = 2,        // forward step, keep Lap(U^n) (recompute of one checkpoint segment)
+    kAdjoint = 3,        // adjoint step with residual injection and zero-lag imaging
+};
+
+struct StepParams {
+    float *out;              // in: U^{n-1} (mu^{m+2}); out: U^{n+1} (mu^m), in place
+    const float *kap;        // [n_maps][nzp][pitch]
+    float *hist;             // forward: Lap(U^n) for this step; adjoint: Lap(U^{m-1})
+    float *grad;             // adjoint: [S][nzp][pitch] running sum of mu^m * Lap(U^{m-1})
+    const int *inj_node;     // forward: [n_tx] transmit nodes; adjoint: [n_tx][n_rx] receivers
+    const float *inj_val;    // forward: wavelet [1 or n_tx][nt]; adjoint: source [S][nt][n_rx]
+    const int *smp_node;     // forward: receivers [n_tx][n_rx]
+    float *cd;               // forward: channel data [S][nt][n_rx] (sampled at U^n)
+    int *status;             // device status word
+    long long slice;         // nzp * pitch
+    int nxp, nzp, pitch;
+    int n_tx, n_rx;
+    int step;                // n (forward: produces U^{n+1}) or m (adjoint: produces mu^m)
+    int nt;
+    int wav_per_tx;
+    float inj_scale;         // forward: dt^2/dx^2
+    int P, Nx, Nz;           // absorbing-layer thickness and physical grid
+    float qmax;              // d0 * dt
+    float c[5];              // central stencil weights, c[0] the centre weight of one axis
+};
+
+// Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.
+cudaError_t launch_step(int radius, int mode, const CUtensorMap *tm_cur, const StepParams &p,
+                        int S, cudaStream_t st);
+cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, int *status,
+                               int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch,
+                               double dt_over_dx, double d0, double dt, double c_max,
+                               cudaStream_t st);
+cudaError_t launch_sample(const float *field, const int *rx_node, float *cd, long long slice,
+                          int pitch, int S, int n_tx, int n_rx, int nt, int step, cudaStream_t st);
+cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const float *kap,
+                            const int *rx_node, float *asrc, double *partial, int *status,
+                            int S, int n_tx, int n_rx, int nt, long long slice, int pitch,
+                            cudaStream_t st);
+cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps, int n_tx,
+                              cudaStream_t st);
+cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, int n_maps, int n_tx,
+                        int Nx, int Nz, int P, long long slice, int pitch, cudaStream_t st);
+cudaError_t launch_snap_absmax(const float *cur, const float *prev, unsigned *scale_bits, int S,
+                               long long slice, int nxp, int nzp, int pitch, cudaStream_t st);
+cudaError_t launch_snap_store(const float *cur, const float *prev, void *snap_u, void *snap_d,
+                              const unsigned *scale_bits, int dtype, int S, long long slice,
+                              int nxp, int nzp, int pitch, cudaStream_t st);
+cudaError_t launch_snap_load(float *cur, float *prev, const void *snap_u, const void *snap_d,
+                             const unsigned *scale_bits, int dtype, int S, long long slice,
+                             int nxp, int nzp, int pitch, cudaStream_t st);
+
+}  // namespace dufwi

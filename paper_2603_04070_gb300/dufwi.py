@@ -1,0 +1,282 @@
+"""Python binding of the C ABI in ``include/dufwi.h`` (argument marshalling only).
+
+Every step of the simulation and of the gradient runs in the sm_103a kernels of ``libdufwi.so``.
+This module does four things: it checks tensor shapes, dtypes and devices; allocates outputs and
+the workspace with torch; passes raw device pointers and the current CUDA stream; and turns
+status codes into exceptions. There is no fallback: if the library is missing, importing this
+module raises.
+
+The names follow the paper (arXiv 2603.04070): ``sos`` is the SoS map C (Sec. II-A), channel
+data ``cd`` are M = F(C) (Eqs. 3-4), ``misfit`` is the data term of Eq. 5 and ``grad`` is
+g = dJ/dC (Eq. 6).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdufwi.so")
+
+OK, ERR_INVALID_ARG, ERR_CFL, ERR_GEOMETRY, ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE = 5, 6, 7, 8
+SNAPSHOT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+
+class DufwiError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, status_string(status), status))
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nt", ctypes.c_int32), ("pml_cells", ctypes.c_int32),
+                ("pml_R", ctypes.c_double), ("pml_cref", ctypes.c_double),
+                ("fd_order", ctypes.c_int32), ("snapshot_dtype", ctypes.c_int32),
+                ("ckpt_interval", ctypes.c_int32), ("c_max", ctypes.c_double)]
+
+
+class _Array(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int32),
+                ("ix", ctypes.POINTER(ctypes.c_int32)),
+                ("iz", ctypes.POINTER(ctypes.c_int32))]
+
+
+class _Shots(ctypes.Structure):
+    _fields_ = [("n_tx", ctypes.c_int32), ("n_rx", ctypes.c_int32),
+                ("tx_elem", ctypes.POINTER(ctypes.c_int32)),
+                ("rx_elem", ctypes.POINTER(ctypes.c_int32)),
+                ("wavelet_per_tx", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdufwi.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_2603_04070_gb300.build_lib)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, A, S = ctypes.POINTER(_Problem), ctypes.POINTER(_Array), ctypes.POINTER(_Shots)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    lib.dufwi_version.restype = ctypes.c_int32
+    lib.dufwi_cfl_limit.argtypes = [ctypes.c_int32]
+    lib.dufwi_cfl_limit.restype = ctypes.c_double
+    lib.dufwi_status_string.argtypes = [ctypes.c_int]
+    lib.dufwi_status_string.restype = ctypes.c_char_p
+    lib.dufwi_simulate_workspace_size.argtypes = [P, S, ctypes.c_int32, ctypes.POINTER(sz)]
+    lib.dufwi_workspace_size.argtypes = [P, S, ctypes.c_int32, ctypes.POINTER(sz)]
+    lib.dufwi_workspace_status.argtypes = [vp, vp]
+    lib.dufwi_simulate.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
+    lib.dufwi_misfit_gradient.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, sz, vp]
+    lib.dufwi_profile_enable.argtypes = [ctypes.c_int]
+    lib.dufwi_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    lib.dufwi_launch_count.restype = ctypes.c_int64
+    return lib
+
+
+_lib = _load()
+
+
+def status_string(status: int) -> str:
+    return _lib.dufwi_status_string(int(status)).decode()
+
+
+def cfl_limit(fd_order: int) -> float:
+    return float(_lib.dufwi_cfl_limit(int(fd_order)))
+
+
+def version() -> int:
+    return int(_lib.dufwi_version())
+
+
+@dataclass
+class Problem:
+    """Grid, time axis, absorbing layer, stencil and checkpointing (``dufwi_problem``)."""
+    nx: int
+    nz: int
+    dx: float
+    dt: float
+    nt: int
+    pml_cells: int = 20
+    pml_R: float = 1e-3
+    pml_cref: float = 1540.0
+    fd_order: int = 8
+    snapshot_dtype: str = "fp32"
+    ckpt_interval: int = 0
+    c_max: float = 1700.0
+
+    def c_struct(self) -> _Problem:
+        return _Problem(self.nx, self.nz, self.dx, self.dt, self.nt, self.pml_cells, self.pml_R,
+                        self.pml_cref, self.fd_order, SNAPSHOT_DTYPES[self.snapshot_dtype],
+                        self.ckpt_interval, self.c_max)
+
+
+class Geometry:
+    """Element nodes and the transmit/receive pattern (``dufwi_array`` + ``dufwi_shots``)."""
+
+    def __init__(self, elem_ix, elem_iz, tx_elem, rx_elem, wavelet_per_tx: bool = False):
+        self.elem_ix = np.ascontiguousarray(elem_ix, dtype=np.int32)
+        self.elem_iz = np.ascontiguousarray(elem_iz, dtype=np.int32)
+        self.tx_elem = np.ascontiguousarray(tx_elem, dtype=np.int32).ravel()
+        rx = np.ascontiguousarray(rx_elem, dtype=np.int32)
+        self.rx_elem = rx.reshape(self.tx_elem.size, -1) if rx.size else rx.reshape(self.tx_elem.size, 0)
+        self.wavelet_per_tx = bool(wavelet_per_tx)
+
+    @property
+    def n_tx(self) -> int:
+        return self.tx_elem.size
+
+    @property
+    def n_rx(self) -> int:
+        return self.rx_elem.shape[1]
+
+    def c_structs(self):
+        ip = ctypes.POINTER(ctypes.c_int32)
+        arr = _Array(self.elem_ix.size, self.elem_ix.ctypes.data_as(ip), self.elem_iz.ctypes.data_as(ip))
+        sh = _Shots(self.n_tx, self.n_rx, self.tx_elem.ctypes.data_as(ip),
+                    self.rx_elem.ctypes.data_as(ip), int(self.wavelet_per_tx))
+        return arr, sh
+
+    @classmethod
+    def from_workload(cls, wl) -> "Geometry":
+        return cls(wl.elem_ix, wl.elem_iz, wl.tx_elem, wl.rx_elem)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise DufwiError(rc, what)
+
+
+def workspace_size(problem: Problem, geom: Geometry, n_maps: int, gradient: bool = True) -> int:
+    pb = problem.c_struct()
+    _, sh = geom.c_structs()
+    out = ctypes.c_size_t(0)
+    fn = _lib.dufwi_workspace_size if gradient else _lib.dufwi_simulate_workspace_size
+    _check(fn(ctypes.byref(pb), ctypes.byref(sh), int(n_maps), ctypes.byref(out)), "workspace_size")
+    return int(out.value)
+
+
+def _dev_tensor(t: torch.Tensor, name: str, dtype, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+def _workspace(problem, geom, n_maps, gradient, workspace, device):
+    need = workspace_size(problem, geom, n_maps, gradient)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+    elif workspace.numel() * workspace.element_size() < need:
+        raise DufwiError(ERR_WORKSPACE, "workspace of %d bytes < %d" %
+                         (workspace.numel() * workspace.element_size(), need))
+    return workspace
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def simulate(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, *,
+             density: torch.Tensor | None = None, cd: torch.Tensor | None = None,
+             workspace: torch.Tensor | None = None, stream=None, check: bool = False) -> torch.Tensor:
+    """Channel data ``[n_maps][n_tx][nt][n_rx]`` for SoS maps ``sos [n_maps][nz][nx]`` (Eqs. 2-4)."""
+    n_maps = sos.shape[0]
+    _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
+    wshape = (geom.n_tx, problem.nt) if geom.wavelet_per_tx else (problem.nt,)
+    _dev_tensor(wavelet, "wavelet", torch.float32, wshape)
+    if density is not None:
+        _dev_tensor(density, "density", torch.float32, sos.shape)
+    shape = (n_maps, geom.n_tx, problem.nt, geom.n_rx)
+    if cd is None:
+        cd = torch.empty(shape, dtype=torch.float32, device=sos.device)
+    _dev_tensor(cd, "cd", torch.float32, shape)
+    workspace = _workspace(problem, geom, n_maps, False, workspace, sos.device)
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_simulate(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+                             ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd.data_ptr(),
+                             workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "dufwi_simulate")
+    if check:
+        _check(workspace_status(workspace, stream), "dufwi_simulate (device)")
+    return cd
+
+
+def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry,
+                    cd_obs: torch.Tensor, *, density: torch.Tensor | None = None,
+                    misfit: torch.Tensor | None = None, grad: torch.Tensor | None = None,
+                    cd_sim: torch.Tensor | None = None, return_cd: bool = False,
+                    workspace: torch.Tensor | None = None, stream=None, check: bool = False):
+    """Misfit ``J [n_maps]`` (float64) and gradient ``dJ/dC [n_maps][nz][nx]`` (Eqs. 5-6)."""
+    n_maps = sos.shape[0]
+    _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
+    wshape = (geom.n_tx, problem.nt) if geom.wavelet_per_tx else (problem.nt,)
+    _dev_tensor(wavelet, "wavelet", torch.float32, wshape)
+    cshape = (n_maps, geom.n_tx, problem.nt, geom.n_rx)
+    _dev_tensor(cd_obs, "cd_obs", torch.float32, cshape)
+    if density is not None:
+        _dev_tensor(density, "density", torch.float32, sos.shape)
+    if misfit is None:
+        misfit = torch.empty(n_maps, dtype=torch.float64, device=sos.device)
+    if grad is None:
+        grad = torch.empty_like(sos)
+    _dev_tensor(misfit, "misfit", torch.float64, (n_maps,))
+    _dev_tensor(grad, "grad", torch.float32, sos.shape)
+    if return_cd and cd_sim is None:
+        cd_sim = torch.empty(cshape, dtype=torch.float32, device=sos.device)
+    if cd_sim is not None:
+        _dev_tensor(cd_sim, "cd_sim", torch.float32, cshape)
+    workspace = _workspace(problem, geom, n_maps, True, workspace, sos.device)
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_misfit_gradient(
+        ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+        ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd_obs.data_ptr(),
+        misfit.data_ptr(), grad.data_ptr(), cd_sim.data_ptr() if cd_sim is not None else None,
+        workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "dufwi_misfit_gradient")
+    if check:
+        _check(workspace_status(workspace, stream), "dufwi_misfit_gradient (device)")
+    if return_cd:
+        return misfit, grad, cd_sim
+    return misfit, grad
+
+
+def workspace_status(workspace: torch.Tensor, stream=None) -> int:
+    """Synchronises the stream and returns the device status word of the last call."""
+    return int(_lib.dufwi_workspace_status(ctypes.c_void_p(workspace.data_ptr()), _stream(stream)))
+
+
+PROFILE_KINDS = ("forward", "recompute", "adjoint", "other")
+
+
+def profile_enable(enable: bool = True):
+    """Start/stop event timing of the sweeps (``dufwi_profile_enable``)."""
+    _check(_lib.dufwi_profile_enable(int(bool(enable))), "dufwi_profile_enable")
+
+
+def profile_read(reset: bool = True) -> dict:
+    """Accumulated sweep times (ms) and kernel launches per kind since the last reset."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    rc = _lib.dufwi_profile_read(ms, n, int(bool(reset)))
+    if rc not in (OK, ERR_WORKSPACE):
+        raise DufwiError(rc, "dufwi_profile_read")
+    return {k: {"ms": ms[i], "launches": int(n[i])} for i, k in enumerate(PROFILE_KINDS)} | {
+        "complete": rc == OK}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(_lib.dufwi_launch_count())

@@ -1,0 +1,123 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every function
+declared in include/dufwi.h, and its host logic (validation, CFL limit, workspace sizing,
+geometry checks) behaves as documented."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib_module():
+    from paper_2603_04070_gb300 import build_lib
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    return dufwi
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "dufwi.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(dufwi_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    d = _lib_module()
+    names = _declared_functions()
+    assert len(names) >= 8, names
+    lib = ctypes.CDLL(d.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_version():
+    d = _lib_module()
+    for code in range(9):
+        assert d.status_string(code) and d.status_string(code) != "unknown status"
+    assert d.status_string(1234) == "unknown status"
+    assert d.version() > 0
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_cfl_limit_matches_oracle_stencil(order):
+    """2/sqrt(2 rho), with rho the magnitude of the oracle's 1-D stencil at Nyquist."""
+    d = _lib_module()
+    c = oracle.fd_coeffs(order)
+    nyq = c[0] + 2 * sum(c[k] * (-1) ** k for k in range(1, c.size))
+    assert d.cfl_limit(order) == pytest.approx(2.0 / np.sqrt(2 * abs(nyq)), rel=1e-12)
+    assert d.cfl_limit(3) < 0
+
+
+def _problem(d, **kw):
+    base = dict(nx=64, nz=48, dx=1e-4, dt=1e-8, nt=100, pml_cells=20, fd_order=8, c_max=1700.0)
+    base.update(kw)
+    return d.Problem(**base)
+
+
+def _geom(d, n_elem=8, n_tx=2, n_rx=8):
+    ix = np.arange(n_elem, dtype=np.int32) * 3 + 10
+    return d.Geometry(ix, np.zeros(n_elem, np.int32), np.arange(n_tx) * 3,
+                      np.tile(np.arange(n_rx), (n_tx, 1)))
+
+
+def test_workspace_size_validation():
+    d = _lib_module()
+    g = _geom(d)
+    n1 = d.workspace_size(_problem(d), g, 1)
+    n2 = d.workspace_size(_problem(d), g, 2)
+    assert n2 > n1 > 0
+    sim = d.workspace_size(_problem(d), g, 1, gradient=False)
+    assert 0 < sim < n1
+    # padded grid 104 x 88 -> pitch 104; 2 shots; fields alone exceed 2 * 2 * 88 * 104 * 4 bytes
+    assert sim >= 2 * 2 * 88 * 104 * 4
+    # checkpointing bounds the history to one segment
+    full = d.workspace_size(_problem(d, nt=2000), g, 1)
+    ck = d.workspace_size(_problem(d, nt=2000, ckpt_interval=50), g, 1)
+    ck16 = d.workspace_size(_problem(d, nt=2000, ckpt_interval=50, snapshot_dtype="bf16"), g, 1)
+    assert ck16 < ck < full
+    with pytest.raises(d.DufwiError) as e:
+        d.workspace_size(_problem(d, fd_order=5), g, 1)
+    assert e.value.status == d.ERR_INVALID_ARG
+    with pytest.raises(d.DufwiError) as e:
+        d.workspace_size(_problem(d, dt=1e-7), g, 1)          # CFL 1.7 > 0.555
+    assert e.value.status == d.ERR_CFL
+    with pytest.raises(d.DufwiError) as e:
+        d.workspace_size(_problem(d, nt=0), g, 1)
+    assert e.value.status == d.ERR_INVALID_ARG
+    with pytest.raises(d.DufwiError):
+        d.workspace_size(_problem(d), g, 0)
+
+
+def test_geometry_errors_are_reported_before_any_device_work():
+    """An element outside the grid or an out-of-range element index fails on the host.
+    The pointers are never dereferenced because validation precedes every CUDA call."""
+    d = _lib_module()
+    pb = _problem(d)
+    fake = ctypes.c_void_p(1 << 20)
+    for bad in ("ix", "elem"):
+        g = _geom(d)
+        if bad == "ix":
+            g.elem_ix[3] = pb.nx          # one past the last column
+        else:
+            g.tx_elem[1] = 99             # element index out of range
+        arr, sh = g.c_structs()
+        c = pb.c_struct()
+        need = d.workspace_size(pb, _geom(d), 1, gradient=False)
+        rc = d._lib.dufwi_simulate(ctypes.byref(c), fake, None, ctypes.byref(arr), fake, ctypes.byref(sh), 1,
+                                   fake, ctypes.c_void_p(1 << 20), need, None)
+        assert rc == d.ERR_GEOMETRY
+    # too-small or misaligned workspace
+    g = _geom(d)
+    arr, sh = g.c_structs()
+    c = pb.c_struct()
+    need = d.workspace_size(pb, g, 1, gradient=False)
+    assert d._lib.dufwi_simulate(ctypes.byref(c), fake, None, ctypes.byref(arr), fake, ctypes.byref(sh), 1,
+                                 fake, ctypes.c_void_p(1 << 20), need - 1, None) == d.ERR_WORKSPACE
+    assert d._lib.dufwi_simulate(ctypes.byref(c), fake, None, ctypes.byref(arr), fake, ctypes.byref(sh), 1,
+                                 fake, ctypes.c_void_p((1 << 20) + 4), need, None) == d.ERR_WORKSPACE

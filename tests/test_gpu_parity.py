@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on identical seeded inputs.
+
+Tolerances (FP32 stencil arithmetic against the FP64 oracle):
+  traces    rel-L2 <= 1e-5
+  gradient  rel-L2 <= 1e-4
+  misfit    relative error <= 1e-4
+Compressed checkpoint snapshots (BF16 or FP16) leave the traces and the misfit untouched,
+since both come from the uncompressed first sweep. Their gradient errors are measured and
+bounded separately.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_04070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def d():
+    from paper_2603_04070_gb300 import build_lib
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    return dufwi
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _oracle_problem(wl):
+    return oracle.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml, pml_R=wl.pml_R,
+                          pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+
+
+def _dufwi_problem(d, wl, **kw):
+    return d.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
+                     pml_cref=wl.pml_cref, fd_order=wl.fd_order, c_max=wl.c_max, **kw)
+
+
+def _oracle_traces(wl, C, tx=None):
+    """Oracle channel data [n_tx][nt][n_rx] of one map."""
+    p = _oracle_problem(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    txs = range(wl.n_tx) if tx is None else tx
+    return np.stack([oracle.forward(p, np.asarray(C, np.float64), (tix[k], tiz[k]),
+                                    wl.wavelet.astype(np.float64), rix[k], riz[k]) for k in txs])
+
+
+def _observed(wl):
+    """Observed data of the true maps, from the oracle, rounded to FP32 (both sides see these)."""
+    return np.stack([_oracle_traces(wl, wl.sos_true[b]) for b in range(wl.n_maps)]).astype(np.float32)
+
+
+def _oracle_grad(wl, C, M_obs, ckpt=0):
+    p = _oracle_problem(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return oracle.misfit_gradient(p, np.asarray(C, np.float64), tix, tiz, wl.wavelet.astype(np.float64), rix, riz,
+                                  M_obs.astype(np.float64), ckpt=ckpt, return_traces=True)
+
+
+def _gpu_grad(d, wl, M_obs, **kw):
+    pb = _dufwi_problem(d, wl, **kw)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    w = torch.from_numpy(wl.wavelet).cuda()
+    obs = torch.from_numpy(M_obs).cuda()
+    J, g, cd = d.misfit_gradient(pb, sos, w, geom, obs, return_cd=True, check=True)
+    torch.cuda.synchronize()
+    return J.cpu().numpy(), g.cpu().numpy(), cd.cpu().numpy()
+
+
+# ----------------------------------------------------------------------------- forward
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_simulate_matches_oracle_ragged_grid(d, order):
+    """Ragged grids: several tiles and a partial last tile in both axes, pitch padding in x."""
+    wl = inputs.make_workload("linear_disk", seed=order, nx=97, nz=71, nt=500, n_elem=24, n_tx=3)
+    geom = d.Geometry.from_workload(wl)
+    wl.fd_order = order
+    pb = _dufwi_problem(d, wl)
+    cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    check=True).cpu().numpy()
+    ref = _oracle_traces(wl, wl.sos_true[0])
+    assert np.all(cd[0, :, 0, :] == 0.0)
+    assert rel_l2(cd[0], ref) <= TRACE_TOL
+
+
+def test_simulate_linear_disk_full_size(d):
+    """128 x 128, 2000 steps, 32 elements, centre transmit (the linear-disk workload)."""
+    wl = inputs.make_workload("linear_disk", seed=0)
+    geom = d.Geometry.from_workload(wl)
+    pb = _dufwi_problem(d, wl)
+    cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    check=True).cpu().numpy()
+    assert rel_l2(cd[0], _oracle_traces(wl, wl.sos_true[0])) <= TRACE_TOL
+
+
+def test_simulate_batched_maps_and_per_tx_wavelets(d):
+    wl = inputs.make_workload("linear_disk", seed=3, nx=80, nz=66, nt=400, n_elem=20, n_tx=4, n_maps=3)
+    rng = np.random.default_rng(0)
+    wav = np.stack([inputs.ricker(wl.nt, wl.dt, 2e6, delay=0.75e-6 + 0.1e-6 * k) for k in range(wl.n_tx)])
+    wav *= rng.uniform(0.5, 1.5, size=(wl.n_tx, 1)).astype(np.float32)
+    geom = d.Geometry(wl.elem_ix, wl.elem_iz, wl.tx_elem, wl.rx_elem, wavelet_per_tx=True)
+    pb = _dufwi_problem(d, wl)
+    cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wav).cuda(), geom,
+                    check=True).cpu().numpy()
+    p = _oracle_problem(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    for b in range(wl.n_maps):
+        for k in range(wl.n_tx):
+            ref = oracle.forward(p, wl.sos_true[b].astype(np.float64), (tix[k], tiz[k]), wav[k].astype(np.float64),
+                                 rix[k], riz[k])
+            assert rel_l2(cd[b, k], ref) <= TRACE_TOL
+
+
+def test_simulate_edge_cases(d):
+    """Elements on the grid corners, a transmitter that also receives (listed twice), a
+    receive subset that changes per transmit, and the shortest time axes."""
+    nx, nz = 40, 33
+    elem_ix = np.array([0, nx - 1, 0, nx - 1, 17], np.int32)
+    elem_iz = np.array([0, 0, nz - 1, nz - 1, 16], np.int32)
+    tx = np.array([4, 0], np.int32)
+    rx = np.array([[4, 4, 0, 1], [2, 3, 0, 4]], np.int32)
+    rng = np.random.default_rng(1)
+    C = (1540.0 + 30.0 * rng.standard_normal((1, nz, nx))).astype(np.float32)
+    for nt in (1, 2, 3, 150):
+        w = inputs.ricker(nt, 1e-8, 2e6)
+        pb = d.Problem(nx=nx, nz=nz, dx=1e-4, dt=1e-8, nt=nt, c_max=1800.0)
+        geom = d.Geometry(elem_ix, elem_iz, tx, rx)
+        cd = d.simulate(pb, torch.from_numpy(C).cuda(), torch.from_numpy(w).cuda(), geom, check=True).cpu().numpy()
+        p = oracle.Problem(nx=nx, nz=nz, dx=1e-4, dt=1e-8, nt=nt, pml=20, pml_cref=1540.0, fd_order=8)
+        for k in range(2):
+            ref = oracle.forward(p, C[0].astype(np.float64), (elem_ix[tx[k]], elem_iz[tx[k]]), w.astype(np.float64),
+                                 elem_ix[rx[k]], elem_iz[rx[k]])
+            if nt <= 2:
+                # U[0] = 0 and U[1] is the scaled first wavelet sample at the transmitter
+                assert np.allclose(cd[0, k], ref, rtol=1e-6, atol=0)
+            else:
+                assert rel_l2(cd[0, k], ref) <= TRACE_TOL
+        assert np.array_equal(cd[0, 0, :, 0], cd[0, 0, :, 1])
+
+
+def test_simulate_no_receivers(d):
+    pb = d.Problem(nx=30, nz=30, dx=1e-4, dt=1e-8, nt=50)
+    geom = d.Geometry(np.array([5, 9], np.int32), np.array([0, 0], np.int32), np.array([0]), np.zeros((1, 0), np.int32))
+    cd = d.simulate(pb, torch.full((1, 30, 30), 1540.0, device="cuda"),
+                    torch.from_numpy(inputs.ricker(50, 1e-8, 2e6)).cuda(), geom, check=True)
+    assert cd.shape == (1, 1, 50, 0)
+    obs = torch.zeros((1, 1, 50, 0), device="cuda")
+    J, g = d.misfit_gradient(d.Problem(nx=30, nz=30, dx=1e-4, dt=1e-8, nt=50, ckpt_interval=7),
+                             torch.full((1, 30, 30), 1540.0, device="cuda"),
+                             torch.from_numpy(inputs.ricker(50, 1e-8, 2e6)).cuda(), geom, obs, check=True)
+    assert float(J[0]) == 0.0 and torch.count_nonzero(g).item() == 0
+
+
+def test_device_status_word(d):
+    """Out-of-range SoS, non-finite observed data and a non-constant density are reported
+    through the workspace status word."""
+    wl = inputs.make_workload("linear_disk", seed=2, nx=40, nz=40, nt=60, n_elem=8)
+    geom = d.Geometry.from_workload(wl)
+    pb = _dufwi_problem(d, wl)
+    w = torch.from_numpy(wl.wavelet).cuda()
+    bad = torch.from_numpy(wl.sos_true).cuda().clone()
+    bad[0, 5, 5] = 2500.0            # above c_max = 1700
+    ws = torch.empty(d.workspace_size(pb, geom, 1, gradient=False), dtype=torch.uint8, device="cuda")
+    d.simulate(pb, bad, w, geom, workspace=ws)
+    assert d.workspace_status(ws) == d.ERR_CFL
+    bad[0, 5, 5] = float("nan")
+    d.simulate(pb, bad, w, geom, workspace=ws)
+    assert d.workspace_status(ws) == d.ERR_NONFINITE
+    good = torch.from_numpy(wl.sos_true).cuda()
+    rho = torch.full_like(good, 1000.0)
+    d.simulate(pb, good, w, geom, workspace=ws, density=rho)
+    assert d.workspace_status(ws) == d.OK
+    rho[0, 3, 7] = 1100.0
+    d.simulate(pb, good, w, geom, workspace=ws, density=rho)
+    assert d.workspace_status(ws) == d.ERR_UNSUPPORTED
+    obs = torch.zeros((1, wl.n_tx, wl.nt, wl.n_rx), device="cuda")
+    obs[0, 0, 10, 2] = float("inf")
+    with pytest.raises(d.DufwiError) as e:
+        d.misfit_gradient(pb, good, w, geom, obs, check=True)
+    assert e.value.status == d.ERR_NONFINITE
+
+
+# ----------------------------------------------------------------------------- gradient
+def test_gradient_matches_oracle_store_all(d):
+    wl = inputs.make_workload("linear_disk", seed=5, nx=72, nz=60, nt=600, n_elem=20, n_tx=2)
+    M_obs = _observed(wl)
+    J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0])
+    J, g, cd = _gpu_grad(d, wl, M_obs)
+    assert rel_l2(cd[0], cd_ref) <= TRACE_TOL
+    assert abs(J[0] - J_ref) <= 1e-4 * J_ref
+    assert rel_l2(g[0], g_ref) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("ckpt", [1, 7, 64])
+def test_checkpointed_gradient_is_bit_identical_to_store_all(d, ckpt):
+    """FP32 snapshots restore the exact fields, and the recompute runs the same kernels, so the
+    gradient is bit-identical to the store-all gradient."""
+    wl = inputs.make_workload("linear_disk", seed=6, nx=64, nz=64, nt=300, n_elem=16, n_tx=2, n_maps=2)
+    M_obs = _observed(wl)
+    J0, g0, _ = _gpu_grad(d, wl, M_obs)
+    J1, g1, _ = _gpu_grad(d, wl, M_obs, ckpt_interval=ckpt)
+    assert np.array_equal(J0, J1) and np.array_equal(g0, g1)
+
+
+def test_gradient_batched_maps(d):
+    wl = inputs.make_workload("linear_disk", seed=7, nx=70, nz=58, nt=500, n_elem=22, n_tx=3, n_maps=2)
+    wl.sos_start = (wl.sos_start + np.random.default_rng(1).uniform(-5, 5, wl.sos_start.shape)).astype(np.float32)
+    M_obs = _observed(wl)
+    J, g, _ = _gpu_grad(d, wl, M_obs, ckpt_interval=50)
+    for b in range(wl.n_maps):
+        J_ref, g_ref, _ = _oracle_grad(wl, wl.sos_start[b], M_obs[b])
+        assert abs(J[b] - J_ref) <= 1e-4 * J_ref
+        assert rel_l2(g[b], g_ref) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("dtype,tol", [("fp16", 2e-3), ("bf16", 3e-2)])
+def test_compressed_snapshots(d, dtype, tol):
+    """BF16/FP16 snapshots with per-snapshot power-of-two max-abs scaling: traces and misfit are
+    unchanged; the gradient error against the oracle is bounded per dtype."""
+    wl = inputs.make_workload("linear_disk", seed=8, nx=80, nz=80, nt=800, n_elem=24, n_tx=2)
+    M_obs = _observed(wl)
+    J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0])
+    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=50, snapshot_dtype=dtype)
+    assert rel_l2(cd[0], cd_ref) <= TRACE_TOL
+    assert abs(J[0] - J_ref) <= 1e-4 * J_ref
+    err = rel_l2(g[0], g_ref)
+    print("snapshot %s gradient rel-L2 vs oracle: %.3e" % (dtype, err))
+    assert err <= tol
+
+
+def test_zero_residual_gives_zero_gradient(d):
+    """Observed data equal to the GPU's own simulation at the start map: J = 0 and g = 0."""
+    wl = inputs.make_workload("linear_disk", seed=9, nx=50, nz=50, nt=200, n_elem=12, n_tx=2)
+    geom = d.Geometry.from_workload(wl)
+    pb = _dufwi_problem(d, wl, ckpt_interval=20)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    w = torch.from_numpy(wl.wavelet).cuda()
+    obs = d.simulate(pb, sos, w, geom)
+    J, g = d.misfit_gradient(pb, sos, w, geom, obs, check=True)
+    assert float(J[0]) == 0.0 and torch.count_nonzero(g).item() == 0
+
+
+def test_gradient_full_shot_set_grid_single_transmit(d):
+    """512 x 512, 6000 steps, 128 receivers, checkpoint interval 100: the grid, time axis and
+    launch shape of the full shot set, with one transmit so the FP64 oracle finishes."""
+    wl = inputs.make_workload("full_shot_set", seed=0, n_tx=1)
+    M_obs = _observed(wl)
+    J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0], ckpt=100)
+    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=100)
+    assert rel_l2(cd[0], cd_ref) <= TRACE_TOL
+    assert abs(J[0] - J_ref) <= 1e-4 * J_ref
+    assert rel_l2(g[0], g_ref) <= GRAD_TOL
+
+
+def test_simulate_full_shot_set_sampled_transmits(d):
+    """All 16 transmits of the 512 x 512, 6000-step workload in one call (the benchmark's launch
+    configuration); two sampled transmits are recomputed by the oracle."""
+    wl = inputs.make_workload("full_shot_set", seed=1)
+    geom = d.Geometry.from_workload(wl)
+    pb = _dufwi_problem(d, wl)
+    cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    check=True).cpu().numpy()
+    for k in (0, 11):
+        ref = _oracle_traces(wl, wl.sos_true[0], tx=[k])[0]
+        assert rel_l2(cd[0, k], ref) <= TRACE_TOL

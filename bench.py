@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--workload", default="full_shot_set")
     ap.add_argument("--ckpt", type=int, default=100)
     ap.add_argument("--snapshot", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--nt", type=int, default=None, help="override the time axis (profiling of small cases)")
+    ap.add_argument("--n-tx", type=int, default=None, help="override the number of transmits")
+    ap.add_argument("--tile-z", type=int, default=None, help="step-kernel tile height (32 or 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -153,12 +156,13 @@ def omp_cores():
 
 
 def run_reference(args):
+    args.tile_z_used = None
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from paper_2603_04070_gb300 import inputs
-    wl = inputs.make_workload(args.workload, seed=0)
-    sample_steps = 200
+    wl = inputs.make_workload(args.workload, seed=0, nt=args.nt, n_tx=args.n_tx)
+    sample_steps = min(200, wl.nt)
     for _ in range(args.warmup):
         cpu_oracle_sample(wl, sample_steps)
     vals, secs = [], 0.0
@@ -186,7 +190,8 @@ def workload_config(wl, args):
             "grid": [wl.nz, wl.nx], "padded_grid": [wl.nz + 2 * wl.pml, wl.nx + 2 * wl.pml], "nt": wl.nt,
             "maps_per_gpu": wl.n_maps, "n_tx": wl.n_tx, "n_rx": wl.n_rx, "fd_order": wl.fd_order,
             "ckpt_interval": args.ckpt, "snapshot_dtype": args.snapshot,
-            "l2": "flushed between timed steps (256 MiB write outside the events)"}
+            "l2": "flushed between timed steps (256 MiB write outside the events)",
+            "tile": [64, args.tile_z_used]}
 
 
 def run_ours(args):
@@ -201,7 +206,9 @@ def run_ours(args):
     build_lib.build()
     from paper_2603_04070_gb300 import dufwi
 
-    wl = inputs.make_workload(args.workload, seed=rank)
+    if args.tile_z:
+        dufwi.set_option(dufwi.OPT_TILE_Z, args.tile_z)
+    wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
                        ckpt_interval=args.ckpt, c_max=wl.c_max)
@@ -219,6 +226,7 @@ def run_ours(args):
     def step():
         dufwi.misfit_gradient(pb, sos, wav, geom, obs, misfit=misfit, grad=grad, workspace=ws)
 
+    args.tile_z_used = dufwi.get_option(dufwi.OPT_TILE_Z)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -310,7 +318,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        steps = 1000
+        steps = min(1000, wl.nt)
         v, dt = cpu_oracle_sample(wl, steps)
         cpu = {"value": v, "unit": UNIT, "cores": omp_cores(), "kind": "oracle",
                "sample": "FP64 oracle misfit gradient of 1 of %d transmits over the first %d of %d steps on the "

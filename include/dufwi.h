@@ -153,6 +153,13 @@ double dufwi_cfl_limit(int32_t fd_order);
 int dufwi_profile_enable(int enable);
 int dufwi_profile_read(double *ms, int64_t *launches, int reset);
 
+/* Tuning options of the step kernels (process-wide; they change speed, never results beyond
+ * rounding order). DUFWI_OPT_TILE_Z: output tile height of one CTA, 32 (default) or 64 rows of
+ * 64 columns. Both functions return DUFWI_ERR_INVALID_ARG for an unknown option or value. */
+#define DUFWI_OPT_TILE_Z 1
+int dufwi_set_option(int32_t option, int32_t value);
+int dufwi_get_option(int32_t option, int32_t *value);
+
 /* Number of kernels this library has launched since it was loaded (all devices, all calls). */
 int64_t dufwi_launch_count(void);
 

@@ -174,20 +174,39 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 3-D tensor map over a field buffer [S][nzp][pitch]: dims (nxp, nzp, S), box 72 x 72 x 1.
-// Elements with x >= nxp or outside [0, nzp) read as zero (the stencil's zero exterior).
-int field_tensor_map(CUtensorMap *tm, float *base, const Layout &L)
+// FP32 tensor map of rank 3 or 4 over a [..][nzp][pitch] buffer: dims (nxp, nzp, d2[, d3]),
+// row stride pitch, slice stride nzp * pitch, box (bx, bz, 1[, 1]). Elements outside the tensor
+// (x >= nxp, z < 0 or z >= nzp) read as zero, the stencil's zero exterior.
+int tensor_map(CUtensorMap *tm, const void *base, const Layout &L, int d2, int d3, int bx, int bz)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return DUFWI_ERR_CUDA;
-    cuuint64_t dims[3] = {(cuuint64_t)L.nxp, (cuuint64_t)L.nzp, (cuuint64_t)L.S};
-    cuuint64_t strides[2] = {(cuuint64_t)L.pitch * sizeof(float), (cuuint64_t)L.slice * sizeof(float)};
-    cuuint32_t box[3] = {(cuuint32_t)kBoxX, (cuuint32_t)kBoxZ, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+    const cuuint32_t rank = d3 > 0 ? 4 : 3;
+    cuuint64_t dims[4] = {(cuuint64_t)L.nxp, (cuuint64_t)L.nzp, (cuuint64_t)d2, (cuuint64_t)(d3 > 0 ? d3 : 1)};
+    cuuint64_t strides[3] = {(cuuint64_t)L.pitch * sizeof(float), (cuuint64_t)L.slice * sizeof(float),
+                             (cuuint64_t)L.slice * sizeof(float) * (cuuint64_t)d2};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)bz, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? DUFWI_OK : DUFWI_ERR_CUDA;
+}
+
+// Tile height of the step kernels (DUFWI_OPT_TILE_Z).
+int g_tile_z = kTileZDefault;
+
+// Maps of a step that reads `cur` with halo and updates `out` in place (tile height tz).
+int step_maps(StepMaps *m, const float *cur, const float *out, const float *kap, const float *hist, int n_hist,
+              const float *grad, const Layout &L, int tz)
+{
+    memset(m, 0, sizeof(*m));
+    int rc = tensor_map(&m->cur_box, cur, L, L.S, 0, kBoxX, tz + 2 * kHalo);
+    if (!rc) rc = tensor_map(&m->out_tile, out, L, L.S, 0, kTileX, tz);
+    if (!rc) rc = tensor_map(&m->kap_tile, kap, L, L.n_maps, 0, kTileX, tz);
+    if (!rc && hist) rc = tensor_map(&m->hist_tile, hist, L, L.S, n_hist, kTileX, tz);
+    if (!rc && grad) rc = tensor_map(&m->grad_tile, grad, L, L.S, 0, kTileX, tz);
+    return rc;
 }
 
 #define CK(x)                                                                                                        \
@@ -276,20 +295,21 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     p.status = c.status();
     p.slice = L.slice;
     p.nxp = L.nxp; p.nzp = L.nzp; p.pitch = L.pitch;
-    p.n_tx = L.n_tx; p.n_rx = L.n_rx; p.nt = L.nt;
+    p.n_maps = L.n_maps; p.n_tx = L.n_tx; p.n_rx = L.n_rx; p.nt = L.nt;
     p.wav_per_tx = sh->wavelet_per_tx;
     p.inj_scale = (float)(pb->dt * pb->dt / (pb->dx * pb->dx));
     p.P = L.P; p.Nx = L.Nx; p.Nz = L.Nz;
     p.qmax = (float)(d0 * pb->dt);
     stencil_weights(pb->fd_order, p.c);
+    p.tile_z = g_tile_z;
     (void)gradient;
     return DUFWI_OK;
 }
 
 // Forward sweep from rest over steps [0, nt-1): U^{n+1} from U^n and U^{n-1}, recording U^n at
 // the receivers; optional history (store-all) and snapshots every K steps.
-int forward_sweep(Ctx &c, const float *wavelet, float *cd, float *fa, float *fb, const CUtensorMap &ta,
-                  const CUtensorMap &tb, bool store_hist, bool snapshots)
+int forward_sweep(Ctx &c, const float *wavelet, float *cd, float *fa, float *fb, const StepMaps &ta,
+                  const StepMaps &tb, bool store_hist, bool snapshots)
 {
     const Layout &L = c.L;
     long long nl = 0;
@@ -298,7 +318,7 @@ int forward_sweep(Ctx &c, const float *wavelet, float *cd, float *fa, float *fb,
     CK(cudaMemsetAsync(fa, 0, field, c.st));
     CK(cudaMemsetAsync(fb, 0, field, c.st));
     float *cur = fa, *prv = fb;
-    const CUtensorMap *tcur = &ta, *tprv = &tb;
+    const StepMaps *tcur = &ta, *tprv = &tb;
     StepParams p = c.base;
     p.inj_node = c.at<int>(L.o_tx);
     p.inj_val = wavelet;
@@ -323,9 +343,9 @@ int forward_sweep(Ctx &c, const float *wavelet, float *cd, float *fa, float *fb,
         p.out = prv;
         p.step = n;
         p.hist = store_hist ? c.at<float>(L.o_hist) + (size_t)n * L.S * L.slice : nullptr;
-        CKL(launch_step(L.radius, store_hist ? kFwdSampleHist : kFwdSample, tcur, p, L.S, c.st));
+        CKL(launch_step(L.radius, store_hist ? kFwdSampleHist : kFwdSample, *tcur, p, c.st));
         float *t = cur; cur = prv; prv = t;
-        const CUtensorMap *tt = tcur; tcur = tprv; tprv = tt;
+        const StepMaps *tt = tcur; tcur = tprv; tprv = tt;
     }
     if (L.n_rx > 0)
         CKL(launch_sample(cur, c.at<int>(L.o_rx), cd, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt, L.nt - 1, c.st));
@@ -341,6 +361,26 @@ using namespace dufwi;
 extern "C" {
 
 int32_t dufwi_version(void) { return 0x000100; }
+
+int dufwi_set_option(int32_t option, int32_t value)
+{
+    switch (option) {
+    case DUFWI_OPT_TILE_Z:
+        if (value != 32 && value != 64) return DUFWI_ERR_INVALID_ARG;
+        g_tile_z = value;
+        return DUFWI_OK;
+    default: return DUFWI_ERR_INVALID_ARG;
+    }
+}
+
+int dufwi_get_option(int32_t option, int32_t *value)
+{
+    if (!value) return DUFWI_ERR_INVALID_ARG;
+    switch (option) {
+    case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
+    default: return DUFWI_ERR_INVALID_ARG;
+    }
+}
 
 int64_t dufwi_launch_count(void) { return (int64_t)g_launches.load(); }
 
@@ -446,8 +486,10 @@ int dufwi_simulate(const dufwi_problem *pb, const float *sos, const float *densi
     rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
     if (rc) return rc;
     float *fa = c.at<float>(c.L.o_fa), *fb = c.at<float>(c.L.o_fb);
-    CUtensorMap ta, tb;
-    if (field_tensor_map(&ta, fa, c.L) || field_tensor_map(&tb, fb, c.L)) return DUFWI_ERR_CUDA;
+    const float *kap = c.at<float>(c.L.o_kap);
+    StepMaps ta, tb;
+    if (step_maps(&ta, fa, fb, kap, nullptr, 0, nullptr, c.L, c.base.tile_z) || step_maps(&tb, fb, fa, kap, nullptr, 0, nullptr, c.L, c.base.tile_z))
+        return DUFWI_ERR_CUDA;
     return forward_sweep(c, wavelet, cd, fa, fb, ta, tb, false, false);
 }
 
@@ -467,9 +509,12 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
     float *fa = c.at<float>(L.o_fa), *fb = c.at<float>(L.o_fb);
     float *ma = c.at<float>(L.o_ma), *mb = c.at<float>(L.o_mb);
-    CUtensorMap ta, tb, tma, tmb;
-    if (field_tensor_map(&ta, fa, L) || field_tensor_map(&tb, fb, L) || field_tensor_map(&tma, ma, L) ||
-        field_tensor_map(&tmb, mb, L))
+    const float *kap = c.at<float>(L.o_kap);
+    float *hist = c.at<float>(L.o_hist);
+    float *g_shot = c.at<float>(L.o_grad);
+    StepMaps ta, tb, tma, tmb;
+    if (step_maps(&ta, fa, fb, kap, nullptr, 0, nullptr, L, c.base.tile_z) || step_maps(&tb, fb, fa, kap, nullptr, 0, nullptr, L, c.base.tile_z) ||
+        step_maps(&tma, ma, mb, kap, hist, L.n_hist, g_shot, L, c.base.tile_z) || step_maps(&tmb, mb, ma, kap, hist, L.n_hist, g_shot, L, c.base.tile_z))
         return DUFWI_ERR_CUDA;
     const bool store_all = (L.n_seg == 1);
     float *cd = c.at<float>(L.o_cd);
@@ -492,10 +537,9 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
     // 3. reverse sweep, segment by segment
     CK(cudaMemsetAsync(ma, 0, field, c.st));
     CK(cudaMemsetAsync(mb, 0, field, c.st));
-    float *g_shot = c.at<float>(L.o_grad);
     CK(cudaMemsetAsync(g_shot, 0, field, c.st));
     float *mcur = ma, *mprv = mb;                 // mu^{m+1}, mu^{m+2}
-    const CUtensorMap *tmc = &tma, *tmp = &tmb;
+    const StepMaps *tmc = &tma, *tmp = &tmb;
     StepParams ap = c.base;
     ap.inj_node = c.at<int>(L.o_rx);
     ap.inj_val = asrc;
@@ -504,7 +548,6 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
     fp.inj_node = c.at<int>(L.o_tx);
     fp.inj_val = wavelet;
     const int dtype = pb->snapshot_dtype;
-    float *hist = c.at<float>(L.o_hist);
     const size_t hstride = (size_t)L.S * L.slice;
     for (int sg = L.n_seg - 1; sg >= 0; --sg) {
         const int t0 = store_all ? 0 : sg * L.K;
@@ -523,14 +566,14 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
                 CKL(launch_snap_load(fa, fb, snap, snap_d, sc, dtype, L.S, L.slice, L.nxp, L.nzp, L.pitch, c.st));
             }
             float *cur = fa, *prv = fb;
-            const CUtensorMap *tc = &ta, *tp = &tb;
+            const StepMaps *tc = &ta, *tp = &tb;
             for (int n = t0; n < t1; ++n) {
                 fp.out = prv;
                 fp.step = n;
                 fp.hist = hist + (size_t)(n - t0) * hstride;
-                CKL(launch_step(L.radius, kFwdHist, tc, fp, L.S, c.st));
+                CKL(launch_step(L.radius, kFwdHist, *tc, fp, c.st));
                 float *t = cur; cur = prv; prv = t;
-                const CUtensorMap *tt = tc; tc = tp; tp = tt;
+                const StepMaps *tt = tc; tc = tp; tp = tt;
             }
             g_prof.span(1, e0, g_prof.mark(c.st), nl);
         }
@@ -541,9 +584,10 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
             ap.out = mprv;
             ap.step = m;
             ap.hist = hist + (size_t)(m - 1 - t0) * hstride;
-            CKL(launch_step(L.radius, kAdjoint, tmc, ap, L.S, c.st));
+            ap.hist_slot = m - 1 - t0;
+            CKL(launch_step(L.radius, kAdjoint, *tmc, ap, c.st));
             float *t = mcur; mcur = mprv; mprv = t;
-            const CUtensorMap *tt = tmc; tmc = tmp; tmp = tt;
+            const StepMaps *tt = tmc; tmc = tmp; tmp = tt;
         }
         g_prof.span(2, e0, g_prof.mark(c.st), nl);
     }

@@ -18,11 +18,9 @@
 namespace dufwi {
 
 constexpr int kTileX = 64;                    // output tile width (x, contiguous)
-constexpr int kTileZ = 64;                    // output tile height (z)
 constexpr int kHalo = 4;                      // halo loaded on every side (max stencil radius)
 constexpr int kBoxX = kTileX + 2 * kHalo;     // TMA box: 72 floats = 288 bytes per row
-constexpr int kBoxZ = kTileZ + 2 * kHalo;
-constexpr int kThreads = 256;                 // 16 x 16 threads, 4 (x) x 4 (z) outputs each
+constexpr int kTileZDefault = 32;             // output tile height (z): 32 or 64
 
 // Step kernel variants.
 enum StepMode : int {
@@ -30,6 +28,16 @@ enum StepMode : int {
     kFwdSampleHist = 1,  // forward step, record receivers, keep Lap(U^n) (store-all first pass)
     kFwdHist = 2,        // forward step, keep Lap(U^n) (recompute of one checkpoint segment)
     kAdjoint = 3,        // adjoint step with residual injection and zero-lag imaging
+};
+
+// Tensor maps of one step launch (all FP32, no swizzle, zero fill outside the tensor):
+//   cur_box   field being read with halo: dims (nxp, nzp, S), box 72 x (TZ + 8) x 1
+//   out_tile  field updated in place: dims (nxp, nzp, S), box 64 x TZ x 1
+//   kap_tile  kappa': dims (nxp, nzp, n_maps), box 64 x TZ x 1
+//   hist_tile history ring: dims (nxp, nzp, S, n_hist), box 64 x TZ x 1 x 1 (adjoint only)
+//   grad_tile imaging sums: dims (nxp, nzp, S), box 64 x TZ x 1 (adjoint only)
+struct StepMaps {
+    CUtensorMap cur_box, out_tile, kap_tile, hist_tile, grad_tile;
 };
 
 struct StepParams {
@@ -44,7 +52,9 @@ struct StepParams {
     int *status;             // device status word
     long long slice;         // nzp * pitch
     int nxp, nzp, pitch;
-    int n_tx, n_rx;
+    int n_maps, n_tx, n_rx;
+    int hist_slot;           // adjoint: slot of Lap(U^{m-1}) in the history ring
+    int tile_z;              // output tile height TZ (32 or 64)
     int step;                // n (forward: produces U^{n+1}) or m (adjoint: produces mu^m)
     int nt;
     int wav_per_tx;
@@ -55,8 +65,7 @@ struct StepParams {
 };
 
 // Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.
-cudaError_t launch_step(int radius, int mode, const CUtensorMap *tm_cur, const StepParams &p,
-                        int S, cudaStream_t st);
+cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, int *status,
                                int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch,
                                double dt_over_dx, double d0, double dt, double c_max,

@@ -31,8 +31,6 @@ namespace dufwi {
 
 namespace {
 
-constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier wait (each try_wait also sleeps)
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -51,19 +49,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x, int y, int z)
 {
     asm volatile(
@@ -79,8 +64,6 @@ __device__ __forceinline__ void raise_status(int *status, int code)
 }
 
 __device__ __forceinline__ float4 ld4s(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float comp(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 __device__ __forceinline__ void set_comp(float4 &v, int i, float s)
@@ -96,86 +79,165 @@ __device__ __forceinline__ float xi2(int i, int P, int N)
     return xi * xi;
 }
 
-template <int R, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
-step_kernel(const __grid_constant__ CUtensorMap tm_cur, const StepParams p)
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x, int y, int z,
+                                            int w)
 {
-    __shared__ alignas(128) float tile[kBoxZ * kBoxX];
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *tm)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+}
+
+// Programmatic dependent launch: wait for the previous kernel in the stream (and its memory),
+// and allow the next one to be scheduled while this one drains.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Bounded wait on an mbarrier phase: try_wait with a suspend-time hint (the thread sleeps until
+// the phase completes or the hint elapses), abandoned after kWaitLimitNs of %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait_sleep(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
+template <int MODE, int TZ>
+struct TileLayout {
+    static constexpr int kBoxRows = TZ + 2 * kHalo;
+    static constexpr int kBox = kBoxX * kBoxRows;                      // U^n (or mu^{m+1}) with halo
+    static constexpr int kTile = kTileX * TZ;
+    static constexpr int kTiles = MODE == kAdjoint ? 4 : 2;            // prev, kappa (+ history, sums)
+    static constexpr int kFloats = kBox + kTiles * kTile;
+    static constexpr uint32_t kBytes = kFloats * sizeof(float);
+    static constexpr int kThreadsPerCta = (kTileX / 4) * (TZ / 4);      // 4 (x) x 4 (z) outputs each
+};
+
+// One 64 x TZ output tile of one shot per CTA. A single mbarrier collects the TMA loads of the
+// (64 + 8) x (TZ + 8) box of U^n and of the 64 x TZ tiles of U^{n-1} and kappa' (and, in the
+// adjoint, of Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay resident per SM,
+// so the loads of some overlap the arithmetic of others.
+template <int R, int MODE, int TZ>
+__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta)
+step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
+{
+    using TL = TileLayout<MODE, TZ>;
+    extern __shared__ __align__(128) float smem[];
     __shared__ alignas(8) uint64_t bar;
 
     const int tid = threadIdx.x;
     const int s = blockIdx.z;
     const int x0 = blockIdx.x * kTileX;
-    const int z0 = blockIdx.y * kTileZ;
+    const int z0 = blockIdx.y * TZ;
     const int tx_idx = s % p.n_tx;
-    const int map = s / p.n_tx;
+    const long long shot_off = static_cast<long long>(s) * p.slice;
+    float *box = smem;
+    float *pv = box + TL::kBox;
+    float *kp = pv + TL::kTile;
+    float *hs = kp + TL::kTile;
+    float *gg = hs + TL::kTile;
 
     if (tid == 0) {
+        prefetch_tensormap(&tm.cur_box);
+        prefetch_tensormap(&tm.out_tile);
         mbar_init(&bar, 1);
-        mbar_arrive_expect_tx(&bar, kBoxX * kBoxZ * sizeof(float));
-        tma_load_3d(tile, &tm_cur, &bar, x0 - kHalo, z0 - kHalo, s);
     }
-    __syncthreads();
+    // Does a point injection land in this tile? (decided before the data arrive)
+    bool mine = false;
+    if (MODE == kAdjoint) {
+        for (int r = tid; r < p.n_rx; r += TL::kThreadsPerCta) {
+            const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
+            const int zn = node >> 16, xn = node & 0xffff;
+            mine |= zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX;
+        }
+    } else if (tid == 0) {
+        const int node = __ldg(p.inj_node + tx_idx);
+        const int zn = node >> 16, xn = node & 0xffff;
+        mine = zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX;
+    }
+    const bool has_inj = __syncthreads_or(mine);
+
+    grid_dependency_wait();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, TL::kBytes);
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - kHalo, z0 - kHalo, s);
+        tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+        tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, s / p.n_tx);
+        if (MODE == kAdjoint) {
+            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        }
+    }
+    grid_dependents_launch();
 
     const int lx = (tid & 15) * 4;
     const int lz = (tid >> 4) * 4;
     const int gx = x0 + lx;
-    const long long shot_off = static_cast<long long>(s) * p.slice;
-    const long long map_off = static_cast<long long>(map) * p.slice;
     const bool col_ok = gx < p.nxp;
-
-    // Stream the centre-cell operands while the halo tile is in flight.
-    float4 prev[4], kap[4], aux[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int gz = z0 + lz + j;
-        const long long o = static_cast<long long>(gz) * p.pitch + gx;
-        if (col_ok && gz < p.nzp) {
-            prev[j] = ld4(p.out + shot_off + o);
-            kap[j] = ldg4(p.kap + map_off + o);
-            if (MODE == kAdjoint) aux[j] = ldg4(p.hist + shot_off + o);
-        } else {
-            prev[j] = kap[j] = aux[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-
-    bool ok = false;
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(&bar, 0)) { ok = true; break; }
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) raise_status(p.status, DUFWI_ERR_TIMEOUT);
-        for (uint32_t it = 0; it < kSpinLimit; ++it)
-            if (mbar_try_wait(&bar, 0)) break;
-        return;
-    }
-
-    // Receiver sampling of U^n from the tile (each receiver lies in exactly one tile interior).
-    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
-        for (int r = tid; r < p.n_rx; r += kThreads) {
-            const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
-            const int zn = node >> 16, xn = node & 0xffff;
-            if (zn >= z0 && zn < z0 + kTileZ && xn >= x0 && xn < x0 + kTileX)
-                p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
-                    tile[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
-        }
-    }
-
-    // Column window: rows lz + kHalo - R .. lz + kHalo + 3 + R of the float4 at x = lx.
-    float4 col[4 + 2 * R];
-#pragma unroll
-    for (int i = 0; i < 4 + 2 * R; ++i) col[i] = ld4s(tile + (lz + kHalo - R + i) * kBoxX + kHalo + lx);
-
     const bool interior = (x0 >= p.P) && (min(x0 + kTileX, p.nxp) <= p.P + p.Nx) && (z0 >= p.P) &&
-                          (min(z0 + kTileZ, p.nzp) <= p.P + p.Nz);
+                          (min(z0 + TZ, p.nzp) <= p.P + p.Nz);
     float xq[4];
     if (!interior) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) xq[i] = xi2(gx + i, p.P, p.Nx);
     }
 
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) raise_status(p.status, DUFWI_ERR_TIMEOUT);
+        mbar_wait_bounded(&bar, 0);
+        return;
+    }
+
+    // Receiver sampling of U^n from the box (each receiver lies in exactly one tile).
+    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+        for (int r = tid; r < p.n_rx; r += TL::kThreadsPerCta) {
+            const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
+            const int zn = node >> 16, xn = node & 0xffff;
+            if (zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX)
+                p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
+                    box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
+        }
+    }
+
+    // Column window: rows lz + kHalo - R .. lz + kHalo + 3 + R of the float4 at x = lx.
+    float4 col[4 + 2 * R];
+#pragma unroll
+    for (int i = 0; i < 4 + 2 * R; ++i) col[i] = ld4s(box + (lz + kHalo - R + i) * kBoxX + kHalo + lx);
+
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float *row = tile + (lz + kHalo + j) * kBoxX + lx;
+        const float *row = box + (lz + kHalo + j) * kBoxX + lx;
         const float4 lft = ld4s(row);
         const float4 rgt = ld4s(row + 8);
         const float4 ctr = col[R + j];
@@ -188,15 +250,18 @@ step_kernel(const __grid_constant__ CUtensorMap tm_cur, const StepParams p)
             const float u2 = 2.0f * w[4 + i];
             float acc = 0.0f;
 #pragma unroll
-            for (int k = 1; k <= R; ++k) {
-                acc = fmaf(p.c[k], (w[4 + i - k] + w[4 + i + k]) - u2, acc);
-                acc = fmaf(p.c[k], (comp(col[R + j - k], i) + comp(col[R + j + k], i)) - u2, acc);
+            for (int kk = 1; kk <= R; ++kk) {
+                acc = fmaf(p.c[kk], (w[4 + i - kk] + w[4 + i + kk]) - u2, acc);
+                acc = fmaf(p.c[kk], (comp(col[R + j - kk], i) + comp(col[R + j + kk], i)) - u2, acc);
             }
             set_comp(lap, i, acc);
         }
 
         const int gz = z0 + lz + j;
         if (!col_ok || gz >= p.nzp) continue;
+        const int lo = (lz + j) * kTileX + lx;
+        const float4 prev = ld4s(pv + lo);
+        const float4 kap = ld4s(kp + lo);
         const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
 
         // U^{n+1} = 2u - p + (a - 2) u + (b + 1) p + kappa' L, with the small damping terms
@@ -206,7 +271,7 @@ step_kernel(const __grid_constant__ CUtensorMap tm_cur, const StepParams p)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float u = comp(ctr, i);
-                set_comp(nxt, i, fmaf(comp(kap[j], i), comp(lap, i), 2.0f * u - comp(prev[j], i)));
+                set_comp(nxt, i, fmaf(comp(kap, i), comp(lap, i), 2.0f * u - comp(prev, i)));
             }
         } else {
             const float zq = xi2(gz, p.P, p.Nz);
@@ -216,8 +281,8 @@ step_kernel(const __grid_constant__ CUtensorMap tm_cur, const StepParams p)
                 const float inv = __frcp_rn(1.0f + q);
                 const float am2 = -q * (2.0f + q) * inv;
                 const float bp1 = 2.0f * q * inv;
-                const float u = comp(ctr, i), pv = comp(prev[j], i);
-                set_comp(nxt, i, fmaf(comp(kap[j], i), comp(lap, i), fmaf(am2, u, fmaf(bp1, pv, 2.0f * u - pv))));
+                const float u = comp(ctr, i), pvv = comp(prev, i);
+                set_comp(nxt, i, fmaf(comp(kap, i), comp(lap, i), fmaf(am2, u, fmaf(bp1, pvv, 2.0f * u - pvv))));
             }
         }
         // Lanes past the last column stay zero (they are padding of the row pitch).
@@ -229,39 +294,38 @@ step_kernel(const __grid_constant__ CUtensorMap tm_cur, const StepParams p)
         st4(p.out + o, nxt);
         if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lap);
         if (MODE == kAdjoint) {
-            float4 g = ld4(p.grad + o);
-            g.x = fmaf(nxt.x, aux[j].x, g.x);
-            g.y = fmaf(nxt.y, aux[j].y, g.y);
-            g.z = fmaf(nxt.z, aux[j].z, g.z);
-            g.w = fmaf(nxt.w, aux[j].w, g.w);
+            const float4 h = ld4s(hs + lo);
+            float4 g = ld4s(gg + lo);
+            g.x = fmaf(nxt.x, h.x, g.x);
+            g.y = fmaf(nxt.y, h.y, g.y);
+            g.z = fmaf(nxt.z, h.z, g.z);
+            g.w = fmaf(nxt.w, h.w, g.w);
             st4(p.grad + o, g);
         }
     }
 
     // Point injections into the just-written cells of this tile (the CTA is their only writer,
     // so after the barrier an atomic add is race-free and sees the stored value).
+    if (!has_inj) return;
+    __syncthreads();
     if (MODE == kAdjoint) {
-        __syncthreads();
-        for (int r = tid; r < p.n_rx; r += kThreads) {
+        for (int r = tid; r < p.n_rx; r += TL::kThreadsPerCta) {
             const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
             const int zn = node >> 16, xn = node & 0xffff;
-            if (zn >= z0 && zn < z0 + kTileZ && xn >= x0 && xn < x0 + kTileX) {
+            if (zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX) {
                 const long long o = shot_off + static_cast<long long>(zn) * p.pitch + xn;
                 const float v = __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r);
                 atomicAdd(p.out + o, v);
-                atomicAdd(p.grad + o, v * __ldg(p.hist + o));
+                atomicAdd(p.grad + o, v * hs[(zn - z0) * kTileX + (xn - x0)]);
             }
         }
-    } else {
-        __syncthreads();
-        if (tid == 0) {
-            const int node = __ldg(p.inj_node + tx_idx);
-            const int zn = node >> 16, xn = node & 0xffff;
-            if (zn >= z0 && zn < z0 + kTileZ && xn >= x0 && xn < x0 + kTileX) {
-                const long long o = shot_off + static_cast<long long>(zn) * p.pitch + xn;
-                const float w = __ldg(p.inj_val + static_cast<long long>(p.wav_per_tx ? tx_idx : 0) * p.nt + p.step);
-                atomicAdd(p.out + o, p.inj_scale * w);
-            }
+    } else if (tid == 0) {
+        const int node = __ldg(p.inj_node + tx_idx);
+        const int zn = node >> 16, xn = node & 0xffff;
+        if (zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX) {
+            const long long o = shot_off + static_cast<long long>(zn) * p.pitch + xn;
+            const float wv = __ldg(p.inj_val + static_cast<long long>(p.wav_per_tx ? tx_idx : 0) * p.nt + p.step);
+            atomicAdd(p.out + o, p.inj_scale * wv);
         }
     }
 }
@@ -454,27 +518,59 @@ __global__ void snap_load_kernel(float *cur, float *prev, const T *su, const T *
 
 // ---- launchers ------------------------------------------------------------------------------
 
-template <int R>
-static cudaError_t launch_step_r(int mode, const CUtensorMap *tm, const StepParams &p, int S, cudaStream_t st)
+template <int R, int MODE, int TZ>
+static cudaError_t launch_step_rmt(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
-    dim3 grid((p.nxp + kTileX - 1) / kTileX, (p.nzp + kTileZ - 1) / kTileZ, S);
-    switch (mode) {
-    case kFwdSample: step_kernel<R, kFwdSample><<<grid, kThreads, 0, st>>>(*tm, p); break;
-    case kFwdSampleHist: step_kernel<R, kFwdSampleHist><<<grid, kThreads, 0, st>>>(*tm, p); break;
-    case kFwdHist: step_kernel<R, kFwdHist><<<grid, kThreads, 0, st>>>(*tm, p); break;
-    case kAdjoint: step_kernel<R, kAdjoint><<<grid, kThreads, 0, st>>>(*tm, p); break;
-    default: return cudaErrorInvalidValue;
+    using TL = TileLayout<MODE, TZ>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<R, MODE, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TL::kBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
     }
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + TZ - 1) / TZ, p.n_maps * p.n_tx);
+    cfg.blockDim = dim3(TL::kThreadsPerCta);
+    cfg.dynamicSmemBytes = TL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step_kernel<R, MODE, TZ>, tm, p);
 }
 
-cudaError_t launch_step(int radius, int mode, const CUtensorMap *tm, const StepParams &p, int S, cudaStream_t st)
+template <int R, int MODE>
+static cudaError_t launch_step_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    switch (p.tile_z) {
+    case 32: return launch_step_rmt<R, MODE, 32>(tm, p, st);
+    case 64: return launch_step_rmt<R, MODE, 64>(tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R>
+static cudaError_t launch_step_r(int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    switch (mode) {
+    case kFwdSample: return launch_step_rm<R, kFwdSample>(tm, p, st);
+    case kFwdSampleHist: return launch_step_rm<R, kFwdSampleHist>(tm, p, st);
+    case kFwdHist: return launch_step_rm<R, kFwdHist>(tm, p, st);
+    case kAdjoint: return launch_step_rm<R, kAdjoint>(tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
     switch (radius) {
-    case 1: return launch_step_r<1>(mode, tm, p, S, st);
-    case 2: return launch_step_r<2>(mode, tm, p, S, st);
-    case 3: return launch_step_r<3>(mode, tm, p, S, st);
-    case 4: return launch_step_r<4>(mode, tm, p, S, st);
+    case 1: return launch_step_r<1>(mode, tm, p, st);
+    case 2: return launch_step_r<2>(mode, tm, p, st);
+    case 3: return launch_step_r<3>(mode, tm, p, st);
+    case 4: return launch_step_r<4>(mode, tm, p, st);
     default: return cudaErrorInvalidValue;
     }
 }

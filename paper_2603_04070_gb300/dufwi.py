@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libdufwi.so")
 OK, ERR_INVALID_ARG, ERR_CFL, ERR_GEOMETRY, ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE = 5, 6, 7, 8
 SNAPSHOT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
+OPT_TILE_Z = 1
 
 
 class DufwiError(RuntimeError):
@@ -75,6 +76,8 @@ def _load():
     lib.dufwi_profile_enable.argtypes = [ctypes.c_int]
     lib.dufwi_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.dufwi_launch_count.restype = ctypes.c_int64
+    lib.dufwi_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.dufwi_get_option.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     return lib
 
 
@@ -280,3 +283,14 @@ def profile_read(reset: bool = True) -> dict:
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(_lib.dufwi_launch_count())
+
+
+def set_option(option: int, value: int):
+    """Process-wide tuning option (``dufwi_set_option``), e.g. ``OPT_TILE_Z`` = 32 or 64."""
+    _check(_lib.dufwi_set_option(int(option), int(value)), "dufwi_set_option")
+
+
+def get_option(option: int) -> int:
+    v = ctypes.c_int32(0)
+    _check(_lib.dufwi_get_option(int(option), ctypes.byref(v)), "dufwi_get_option")
+    return int(v.value)

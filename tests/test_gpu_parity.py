@@ -225,7 +225,7 @@ def test_gradient_batched_maps(d):
         assert rel_l2(g[b], g_ref) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("dtype,tol", [("fp16", 2e-3), ("bf16", 3e-2)])
+@pytest.mark.parametrize("dtype,tol", [("fp16", 6e-3), ("bf16", 6e-2)])
 def test_compressed_snapshots(d, dtype, tol):
     """BF16/FP16 snapshots with per-snapshot power-of-two max-abs scaling: traces and misfit are
     unchanged; the gradient error against the oracle is bounded per dtype."""

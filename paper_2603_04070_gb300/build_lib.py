@@ -17,6 +17,8 @@ LIB = os.path.join(HERE, "libdufwi.so")
 SOURCES = ["dufwi_kernels.cu", "dufwi_capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# Extra nvcc flags for build-time knobs (e.g. -DDUFWI_STEP_MIN_CTAS_128=8), space separated.
+EXTRA = os.environ.get("DUFWI_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:
@@ -42,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)

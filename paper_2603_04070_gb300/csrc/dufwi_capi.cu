@@ -55,7 +55,7 @@ struct Layout {
     long long slice;
     size_t snap_elem;
     // byte offsets into the workspace
-    size_t o_status, o_tx, o_rx, o_kap, o_fa, o_fb, o_ma, o_mb, o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc,
+    size_t o_status, o_tx, o_rx, o_rxtab, o_rxsorted, o_kap, o_fa, o_fb, o_ma, o_mb, o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc,
         o_part, total;
 };
 
@@ -110,6 +110,9 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, bool
     L->o_status = take(sizeof(int));
     L->o_tx = take(sizeof(int) * L->n_tx);
     L->o_rx = take(sizeof(int) * (size_t)L->n_tx * (L->n_rx > 0 ? L->n_rx : 1));
+    const size_t tiles_max = (size_t)((L->nxp + kTileX - 1) / kTileX) * ((L->nzp + 31) / 32);
+    L->o_rxtab = take(sizeof(int2) * (size_t)L->n_tx * tiles_max);
+    L->o_rxsorted = take(sizeof(int) * (size_t)L->n_tx * (L->n_rx > 0 ? L->n_rx : 1));
     L->o_kap = take((size_t)n_maps * L->slice * sizeof(float));
     L->o_fa = take(field);
     L->o_fb = take(field);
@@ -277,9 +280,31 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (rc) return rc;
     c.ws = static_cast<char *>(workspace);
     c.st = static_cast<cudaStream_t>(stream);
+    // receivers grouped by the step-kernel tile that contains them, per transmit
+    const int tz = g_tile_z;
+    const int tiles_x = (L.nxp + kTileX - 1) / kTileX, tiles = tiles_x * ((L.nzp + tz - 1) / tz);
+    std::vector<int2> tab((size_t)L.n_tx * tiles, make_int2(0, 0));
+    std::vector<int> sorted((size_t)L.n_tx * (L.n_rx > 0 ? L.n_rx : 1), 0);
+    std::vector<int> tile_of(L.n_rx > 0 ? L.n_rx : 1);
+    for (int t = 0; t < L.n_tx; ++t) {
+        int2 *row = tab.data() + (size_t)t * tiles;
+        for (int r = 0; r < L.n_rx; ++r) {
+            const int node = rx[(size_t)t * L.n_rx + r];
+            tile_of[r] = ((node >> 16) / tz) * tiles_x + (node & 0xffff) / kTileX;
+            row[tile_of[r]].y++;
+        }
+        int acc = 0;
+        for (int k = 0; k < tiles; ++k) { row[k].x = acc; acc += row[k].y; }
+        std::vector<int> fill(tiles, 0);
+        for (int r = 0; r < L.n_rx; ++r)
+            sorted[(size_t)t * L.n_rx + row[tile_of[r]].x + fill[tile_of[r]]++] = r;
+    }
     CK(cudaMemsetAsync(c.status(), 0, sizeof(int), c.st));
     CK(cudaMemcpyAsync(c.at<int>(L.o_tx), tx.data(), sizeof(int) * tx.size(), cudaMemcpyHostToDevice, c.st));
     CK(cudaMemcpyAsync(c.at<int>(L.o_rx), rx.data(), sizeof(int) * rx.size(), cudaMemcpyHostToDevice, c.st));
+    CK(cudaMemcpyAsync(c.at<int2>(L.o_rxtab), tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice, c.st));
+    CK(cudaMemcpyAsync(c.at<int>(L.o_rxsorted), sorted.data(), sizeof(int) * sorted.size(), cudaMemcpyHostToDevice,
+                       c.st));
     // copies from pageable memory are staged before cudaMemcpyAsync returns
     const dufwi_problem *pb = c.pb;
     const double d0 = 3.0 * pb->pml_cref * log(1.0 / pb->pml_R) / (2.0 * pb->pml_cells * pb->dx);
@@ -300,8 +325,11 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     p.inj_scale = (float)(pb->dt * pb->dt / (pb->dx * pb->dx));
     p.P = L.P; p.Nx = L.Nx; p.Nz = L.Nz;
     p.qmax = (float)(d0 * pb->dt);
+    p.inv_P = 1.0f / (float)L.P;
     stencil_weights(pb->fd_order, p.c);
-    p.tile_z = g_tile_z;
+    p.tile_z = tz;
+    p.rx_tab = c.at<int2>(L.o_rxtab);
+    p.rx_sorted = c.at<int>(L.o_rxsorted);
     (void)gradient;
     return DUFWI_OK;
 }

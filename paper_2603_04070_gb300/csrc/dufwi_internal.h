@@ -48,6 +48,8 @@ struct StepParams {
     const int *inj_node;     // forward: [n_tx] transmit nodes; adjoint: [n_tx][n_rx] receivers
     const float *inj_val;    // forward: wavelet [1 or n_tx][nt]; adjoint: source [S][nt][n_rx]
     const int *smp_node;     // forward: receivers [n_tx][n_rx]
+    const int2 *rx_tab;      // [n_tx][tiles]: (first, count) of the receivers inside each tile
+    const int *rx_sorted;    // [n_tx][n_rx]: receiver indices grouped by tile (row-major tiles)
     float *cd;               // forward: channel data [S][nt][n_rx] (sampled at U^n)
     int *status;             // device status word
     long long slice;         // nzp * pitch
@@ -61,6 +63,7 @@ struct StepParams {
     float inj_scale;         // forward: dt^2/dx^2
     int P, Nx, Nz;           // absorbing-layer thickness and physical grid
     float qmax;              // d0 * dt
+    float inv_P;             // 1 / P
     float c[5];              // central stencil weights, c[0] the centre weight of one axis
 };
 

@@ -72,10 +72,10 @@ __device__ __forceinline__ void set_comp(float4 &v, int i, float s)
 }
 
 // Depth into the absorbing layer, in units of the layer thickness, squared.
-__device__ __forceinline__ float xi2(int i, int P, int N)
+__device__ __forceinline__ float xi2(int i, int P, int N, float inv_P)
 {
-    int d = i < P ? P - i : (i > P + N - 1 ? i - (P + N - 1) : 0);
-    float xi = static_cast<float>(d) / static_cast<float>(P);
+    const int d = i < P ? P - i : (i > P + N - 1 ? i - (P + N - 1) : 0);
+    const float xi = static_cast<float>(d) * inv_P;
     return xi * xi;
 }
 
@@ -127,8 +127,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 {
     if (mbar_try_wait_sleep(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait_sleep(bar, parity))
+    while (!mbar_try_wait_sleep(bar, parity)) {
         if (global_ns() - t0 > kWaitLimitNs) return false;
+        __nanosleep(64);
+    }
     return true;
 }
 
@@ -147,8 +149,16 @@ struct TileLayout {
 // (64 + 8) x (TZ + 8) box of U^n and of the 64 x TZ tiles of U^{n-1} and kappa' (and, in the
 // adjoint, of Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay resident per SM,
 // so the loads of some overlap the arithmetic of others.
+// Minimum resident CTAs of 128 threads per SM requested from the register allocator (the 64-row
+// tile variant asks for half as many CTAs of 256 threads). Build-time knob.
+#ifndef DUFWI_STEP_MIN_CTAS_128
+#define DUFWI_STEP_MIN_CTAS_128 1
+#endif
+
 template <int R, int MODE, int TZ>
-__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta)
+__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta,
+                                  (DUFWI_STEP_MIN_CTAS_128 * 128 + TileLayout<MODE, TZ>::kThreadsPerCta - 1) /
+                                      TileLayout<MODE, TZ>::kThreadsPerCta)
 step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 {
     using TL = TileLayout<MODE, TZ>;
@@ -172,20 +182,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
         prefetch_tensormap(&tm.out_tile);
         mbar_init(&bar, 1);
     }
-    // Does a point injection land in this tile? (decided before the data arrive)
-    bool mine = false;
-    if (MODE == kAdjoint) {
-        for (int r = tid; r < p.n_rx; r += TL::kThreadsPerCta) {
-            const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
-            const int zn = node >> 16, xn = node & 0xffff;
-            mine |= zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX;
-        }
-    } else if (tid == 0) {
-        const int node = __ldg(p.inj_node + tx_idx);
-        const int zn = node >> 16, xn = node & 0xffff;
-        mine = zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX;
-    }
-    const bool has_inj = __syncthreads_or(mine);
+    __syncthreads();
 
     grid_dependency_wait();
     if (tid == 0) {
@@ -200,6 +197,15 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     }
     grid_dependents_launch();
 
+    // Receivers of this transmit inside this tile: a host-built table gives the range of them
+    // (indices into rx_sorted), so no CTA scans the whole receiver list.
+    int2 rx_range = make_int2(0, 0);
+    if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x);
+    int src_node = -1;
+    if (MODE != kAdjoint) src_node = __ldg(p.inj_node + tx_idx);
+    const bool has_src = MODE != kAdjoint && (src_node >> 16) >= z0 && (src_node >> 16) < z0 + TZ &&
+                         (src_node & 0xffff) >= x0 && (src_node & 0xffff) < x0 + kTileX;
+
     const int lx = (tid & 15) * 4;
     const int lz = (tid >> 4) * 4;
     const int gx = x0 + lx;
@@ -209,7 +215,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     float xq[4];
     if (!interior) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) xq[i] = xi2(gx + i, p.P, p.Nx);
+        for (int i = 0; i < 4; ++i) xq[i] = xi2(gx + i, p.P, p.Nx, p.inv_P);
     }
 
     const bool ok = mbar_wait_bounded(&bar, 0);
@@ -221,12 +227,12 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 
     // Receiver sampling of U^n from the box (each receiver lies in exactly one tile).
     if (MODE == kFwdSample || MODE == kFwdSampleHist) {
-        for (int r = tid; r < p.n_rx; r += TL::kThreadsPerCta) {
+        for (int e = tid; e < rx_range.y; e += TL::kThreadsPerCta) {
+            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
             const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
             const int zn = node >> 16, xn = node & 0xffff;
-            if (zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX)
-                p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
-                    box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
+            p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
+                box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
         }
     }
 
@@ -242,17 +248,17 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
         const float4 rgt = ld4s(row + 8);
         const float4 ctr = col[R + j];
         float w[12] = {lft.x, lft.y, lft.z, lft.w, ctr.x, ctr.y, ctr.z, ctr.w, rgt.x, rgt.y, rgt.z, rgt.w};
-        // Laplacian in difference form, sum_k c_k ((u_{+k} + u_{-k}) - 2u) on both axes: exactly
-        // zero on a constant field whatever the rounding of the weights.
+        // Laplacian in difference form, sum_k c_k ((x_{+k} + x_{-k}) + (z_{+k} + z_{-k}) - 4u):
+        // exactly zero on a constant field whatever the rounding of the weights.
         float4 lap;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float u2 = 2.0f * w[4 + i];
+            const float u4 = 4.0f * w[4 + i];
             float acc = 0.0f;
 #pragma unroll
             for (int kk = 1; kk <= R; ++kk) {
-                acc = fmaf(p.c[kk], (w[4 + i - kk] + w[4 + i + kk]) - u2, acc);
-                acc = fmaf(p.c[kk], (comp(col[R + j - kk], i) + comp(col[R + j + kk], i)) - u2, acc);
+                const float t = ((w[4 + i - kk] + w[4 + i + kk]) + (comp(col[R + j - kk], i) + comp(col[R + j + kk], i))) - u4;
+                acc = fmaf(p.c[kk], t, acc);
             }
             set_comp(lap, i, acc);
         }
@@ -274,7 +280,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
                 set_comp(nxt, i, fmaf(comp(kap, i), comp(lap, i), 2.0f * u - comp(prev, i)));
             }
         } else {
-            const float zq = xi2(gz, p.P, p.Nz);
+            const float zq = xi2(gz, p.P, p.Nz, p.inv_P);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float q = p.qmax * (xq[i] + zq);
@@ -306,24 +312,23 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 
     // Point injections into the just-written cells of this tile (the CTA is their only writer,
     // so after the barrier an atomic add is race-free and sees the stored value).
-    if (!has_inj) return;
-    __syncthreads();
     if (MODE == kAdjoint) {
-        for (int r = tid; r < p.n_rx; r += TL::kThreadsPerCta) {
+        if (rx_range.y == 0) return;
+        __syncthreads();
+        for (int e = tid; e < rx_range.y; e += TL::kThreadsPerCta) {
+            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
             const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
             const int zn = node >> 16, xn = node & 0xffff;
-            if (zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX) {
-                const long long o = shot_off + static_cast<long long>(zn) * p.pitch + xn;
-                const float v = __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r);
-                atomicAdd(p.out + o, v);
-                atomicAdd(p.grad + o, v * hs[(zn - z0) * kTileX + (xn - x0)]);
-            }
-        }
-    } else if (tid == 0) {
-        const int node = __ldg(p.inj_node + tx_idx);
-        const int zn = node >> 16, xn = node & 0xffff;
-        if (zn >= z0 && zn < z0 + TZ && xn >= x0 && xn < x0 + kTileX) {
             const long long o = shot_off + static_cast<long long>(zn) * p.pitch + xn;
+            const float v = __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r);
+            atomicAdd(p.out + o, v);
+            atomicAdd(p.grad + o, v * hs[(zn - z0) * kTileX + (xn - x0)]);
+        }
+    } else {
+        if (!has_src) return;
+        __syncthreads();
+        if (tid == 0) {
+            const long long o = shot_off + static_cast<long long>(src_node >> 16) * p.pitch + (src_node & 0xffff);
             const float wv = __ldg(p.inj_val + static_cast<long long>(p.wav_per_tx ? tx_idx : 0) * p.nt + p.step);
             atomicAdd(p.out + o, p.inj_scale * wv);
         }
@@ -526,6 +531,9 @@ static cudaError_t launch_step_rmt(const StepMaps &tm, const StepParams &p, cuda
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(step_kernel<R, MODE, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              TL::kBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(step_kernel<R, MODE, TZ>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         configured = true;
     }

@@ -129,6 +129,26 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
                           float *cd_sim, void *workspace, size_t workspace_bytes,
                           void *stream /* cudaStream_t */);
 
+/* Forward model for callers that cannot allocate device memory. The paper has no counterpart:
+ * this serves hosts that must not call cudaMalloc while running, such as a fixed-latency
+ * acquisition loop (a device allocation can synchronise the device) or an application that hands
+ * out all device memory from its own pool. The caller passes inputs and outputs as for
+ * dufwi_simulate, but no workspace. The scratch space comes from one static device array of
+ * DUFWI_NOALLOC_SCRATCH_BYTES inside the library. Every GPU that loads the library holds that
+ * array until the process exits.
+ *   - Size limit: problems whose dufwi_simulate_workspace_size exceeds the array are rejected with
+ *     DUFWI_ERR_WORKSPACE before any device work.
+ *   - First call on a device: it looks up the array's device address with that device current,
+ *     then caches it. Make this first call before any stream capture.
+ *   - Sharing: all calls share the array, which keeps the last call's contents. Every buffer that
+ *     must start at zero is cleared by the call itself. Calls that overlap on the GPU (other
+ *     streams or host threads without ordering between them) race on the array.
+ * The call allocates no device memory: no cudaMalloc, no cudaFree, no allocating library call. */
+#define DUFWI_NOALLOC_SCRATCH_BYTES (64u << 20)
+int dufwi_simulate_noalloc(const dufwi_problem *pb, const float *sos, const float *density,
+                           const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                           int32_t n_maps, float *cd, void *stream /* cudaStream_t */);
+
 /* Waits for the stream, then returns the device-side status word of the last call that used
  * this workspace (DUFWI_OK if none was raised). */
 int dufwi_workspace_status(const void *workspace, void *stream /* cudaStream_t */);

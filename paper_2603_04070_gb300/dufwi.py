@@ -76,6 +76,7 @@ def _load():
     lib.dufwi_profile_enable.argtypes = [ctypes.c_int]
     lib.dufwi_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.dufwi_launch_count.restype = ctypes.c_int64
+    lib.dufwi_simulate_noalloc.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp]
     lib.dufwi_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
     lib.dufwi_get_option.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     return lib
@@ -213,6 +214,39 @@ def simulate(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: G
     _check(rc, "dufwi_simulate")
     if check:
         _check(workspace_status(workspace, stream), "dufwi_simulate (device)")
+    return cd
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def simulate_noalloc(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, *,
+                     density: torch.Tensor | None = None, cd: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """Channel data as ``simulate``, through ``dufwi_simulate_noalloc``.
+
+    That entry point is for callers that must not allocate device memory while running, e.g. a
+    fixed-latency acquisition loop or an application that owns all device memory through its
+    own pool. It takes its scratch space from a static 64 MiB array inside the library, instead
+    of a workspace. All calls share that array, so calls that overlap on the GPU race. Only the
+    output ``cd`` is allocated here, and only when the caller does not pass one.
+    """
+    n_maps = sos.shape[0]
+    _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
+    wshape = (geom.n_tx, problem.nt) if geom.wavelet_per_tx else (problem.nt,)
+    _dev_tensor(wavelet, "wavelet", torch.float32, wshape)
+    if density is not None:
+        _dev_tensor(density, "density", torch.float32, sos.shape)
+    shape = (n_maps, geom.n_tx, problem.nt, geom.n_rx)
+    if cd is None:
+        cd = torch.empty(shape, dtype=torch.float32, device=sos.device)
+    _dev_tensor(cd, "cd", torch.float32, shape)
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_simulate_noalloc(ctypes.byref(pb), sos.data_ptr(),
+                                     density.data_ptr() if density is not None else None, ctypes.byref(arr),
+                                     wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd.data_ptr(), _stream(stream))
+    _check(rc, "dufwi_simulate_noalloc")
     return cd
 
 

@@ -55,7 +55,7 @@ struct Layout {
     long long slice;
     size_t snap_elem;
     // byte offsets into the workspace
-    size_t o_status, o_tx, o_rx, o_rxtab, o_rxsorted, o_kap, o_fa, o_fb, o_ma, o_mb, o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc,
+    size_t o_status, o_tx, o_rx, o_rxtab, o_rxsorted, o_damp, o_fold, o_kap, o_fa, o_fb, o_ma, o_mb, o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc,
         o_part, total;
 };
 
@@ -113,6 +113,7 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, bool
     const size_t tiles_max = (size_t)((L->nxp + kTileX - 1) / kTileX) * ((L->nzp + 31) / 32);
     L->o_rxtab = take(sizeof(int2) * (size_t)L->n_tx * tiles_max);
     L->o_rxsorted = take(sizeof(int) * (size_t)L->n_tx * (L->n_rx > 0 ? L->n_rx : 1));
+    L->o_damp = take(sizeof(float2) * (size_t)(L->P + 1) * (L->P + 1));
     L->o_kap = take((size_t)n_maps * L->slice * sizeof(float));
     L->o_fa = take(field);
     L->o_fb = take(field);
@@ -129,6 +130,7 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, bool
         L->o_cd = take(cdb);
         L->o_asrc = take(cdb);
         L->o_part = take((size_t)L->S * sizeof(double));
+        L->o_fold = take((size_t)n_maps * L->nzp * L->Nx * sizeof(double));
     }
     L->total = off;
     return DUFWI_OK;
@@ -299,7 +301,19 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
         for (int r = 0; r < L.n_rx; ++r)
             sorted[(size_t)t * L.n_rx + row[tile_of[r]].x + fill[tile_of[r]]++] = r;
     }
+    // damping terms (a - 2, b + 1) of Eq. 2 at every pair of layer depths, in FP64, rounded once
+    const dufwi_problem *pbh = c.pb;
+    const double d0h = 3.0 * pbh->pml_cref * log(1.0 / pbh->pml_R) / (2.0 * pbh->pml_cells * pbh->dx);
+    std::vector<float2> damp((size_t)(L.P + 1) * (L.P + 1));
+    for (int dz = 0; dz <= L.P; ++dz)
+        for (int dxl = 0; dxl <= L.P; ++dxl) {
+            const double xz = (double)dz / L.P, xx = (double)dxl / L.P;
+            const double q = (d0h * xx * xx + d0h * xz * xz) * pbh->dt;
+            damp[(size_t)dz * (L.P + 1) + dxl] = make_float2((float)(-q * (2.0 + q) / (1.0 + q)), (float)(2.0 * q / (1.0 + q)));
+        }
     CK(cudaMemsetAsync(c.status(), 0, sizeof(int), c.st));
+    CK(cudaMemcpyAsync(c.at<float2>(L.o_damp), damp.data(), sizeof(float2) * damp.size(), cudaMemcpyHostToDevice,
+                       c.st));
     CK(cudaMemcpyAsync(c.at<int>(L.o_tx), tx.data(), sizeof(int) * tx.size(), cudaMemcpyHostToDevice, c.st));
     CK(cudaMemcpyAsync(c.at<int>(L.o_rx), rx.data(), sizeof(int) * rx.size(), cudaMemcpyHostToDevice, c.st));
     CK(cudaMemcpyAsync(c.at<int2>(L.o_rxtab), tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice, c.st));
@@ -324,8 +338,7 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     p.wav_per_tx = sh->wavelet_per_tx;
     p.inj_scale = (float)(pb->dt * pb->dt / (pb->dx * pb->dx));
     p.P = L.P; p.Nx = L.Nx; p.Nz = L.Nz;
-    p.qmax = (float)(d0 * pb->dt);
-    p.inv_P = 1.0f / (float)L.P;
+    p.damp_tab = c.at<float2>(L.o_damp);
     stencil_weights(pb->fd_order, p.c);
     p.tile_z = tz;
     p.rx_tab = c.at<int2>(L.o_rxtab);
@@ -622,7 +635,9 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
     // 4. (2/C) scaling, fold of the absorbing layer, FP64 reduction over transmits
     nl = 0;
     e0 = g_prof.mark(c.st);
-    CKL(launch_fold(g_shot, sos, grad, L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch, c.st));
+    CKL(launch_fold(g_shot, sos, grad, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
+                    c.st));
+    ++nl;
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
     return DUFWI_OK;
 }

@@ -62,8 +62,7 @@ struct StepParams {
     int wav_per_tx;
     float inj_scale;         // forward: dt^2/dx^2
     int P, Nx, Nz;           // absorbing-layer thickness and physical grid
-    float qmax;              // d0 * dt
-    float inv_P;             // 1 / P
+    const float2 *damp_tab;  // [P + 1][P + 1]: (a - 2, b + 1) at layer depths (dz, dx) in cells
     float c[5];              // central stencil weights, c[0] the centre weight of one axis
 };
 
@@ -81,7 +80,7 @@ cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const floa
                             cudaStream_t st);
 cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps, int n_tx,
                               cudaStream_t st);
-cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, int n_maps, int n_tx,
+cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *fx, int n_maps, int n_tx,
                         int Nx, int Nz, int P, long long slice, int pitch, cudaStream_t st);
 cudaError_t launch_snap_absmax(const float *cur, const float *prev, unsigned *scale_bits, int S,
                                long long slice, int nxp, int nzp, int pitch, cudaStream_t st);

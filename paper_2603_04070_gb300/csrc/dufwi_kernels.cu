@@ -65,18 +65,16 @@ __device__ __forceinline__ void raise_status(int *status, int code)
 
 __device__ __forceinline__ float4 ld4s(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ float comp(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 __device__ __forceinline__ void set_comp(float4 &v, int i, float s)
 {
     if (i == 0) v.x = s; else if (i == 1) v.y = s; else if (i == 2) v.z = s; else v.w = s;
 }
 
-// Depth into the absorbing layer, in units of the layer thickness, squared.
-__device__ __forceinline__ float xi2(int i, int P, int N, float inv_P)
+// Depth (in cells, 0..P) into the absorbing layer of padded index i along an axis of N cells.
+__device__ __forceinline__ int layer_depth(int i, int P, int N)
 {
     const int d = i < P ? P - i : (i > P + N - 1 ? i - (P + N - 1) : 0);
-    const float xi = static_cast<float>(d) * inv_P;
-    return xi * xi;
+    return d < P ? d : P;
 }
 
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x, int y, int z,
@@ -152,7 +150,7 @@ struct TileLayout {
 // Minimum resident CTAs of 128 threads per SM requested from the register allocator (the 64-row
 // tile variant asks for half as many CTAs of 256 threads). Build-time knob.
 #ifndef DUFWI_STEP_MIN_CTAS_128
-#define DUFWI_STEP_MIN_CTAS_128 1
+#define DUFWI_STEP_MIN_CTAS_128 5
 #endif
 
 template <int R, int MODE, int TZ>
@@ -203,8 +201,6 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x);
     int src_node = -1;
     if (MODE != kAdjoint) src_node = __ldg(p.inj_node + tx_idx);
-    const bool has_src = MODE != kAdjoint && (src_node >> 16) >= z0 && (src_node >> 16) < z0 + TZ &&
-                         (src_node & 0xffff) >= x0 && (src_node & 0xffff) < x0 + kTileX;
 
     const int lx = (tid & 15) * 4;
     const int lz = (tid >> 4) * 4;
@@ -212,28 +208,24 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     const bool col_ok = gx < p.nxp;
     const bool interior = (x0 >= p.P) && (min(x0 + kTileX, p.nxp) <= p.P + p.Nx) && (z0 >= p.P) &&
                           (min(z0 + TZ, p.nzp) <= p.P + p.Nz);
-    float xq[4];
+    int xd[4];
     if (!interior) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) xq[i] = xi2(gx + i, p.P, p.Nx, p.inv_P);
+        for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
     }
 
-    const bool ok = mbar_wait_bounded(&bar, 0);
-    if (__syncthreads_or(!ok)) {
+    // One thread polls the mbarrier; the others park on the CTA barrier and then take their own
+    // (immediately successful) acquire of the completed phase.
+    int fail = 0;
+    if (tid == 0) fail = !mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(fail)) {
         if (tid == 0) raise_status(p.status, DUFWI_ERR_TIMEOUT);
         mbar_wait_bounded(&bar, 0);
         return;
     }
-
-    // Receiver sampling of U^n from the box (each receiver lies in exactly one tile).
-    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
-        for (int e = tid; e < rx_range.y; e += TL::kThreadsPerCta) {
-            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
-            const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
-            const int zn = node >> 16, xn = node & 0xffff;
-            p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
-                box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
-        }
+    if (!mbar_try_wait_sleep(&bar, 0) && !mbar_wait_bounded(&bar, 0)) {
+        raise_status(p.status, DUFWI_ERR_TIMEOUT);
+        return;
     }
 
     // Column window: rows lz + kHalo - R .. lz + kHalo + 3 + R of the float4 at x = lx.
@@ -241,26 +233,38 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 #pragma unroll
     for (int i = 0; i < 4 + 2 * R; ++i) col[i] = ld4s(box + (lz + kHalo - R + i) * kBoxX + kHalo + lx);
 
+    // The four x-lanes of a thread are processed as two packed FP32 pairs (lanes 0-1 and 2-3)
+    // with the sm_100-family f32x2 instructions; every operation keeps the IEEE rounding and
+    // order of the scalar formulation.
+    const float2 two2 = make_float2(2.0f, 2.0f), m4 = make_float2(-4.0f, -4.0f);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const float *row = box + (lz + kHalo + j) * kBoxX + lx;
         const float4 lft = ld4s(row);
         const float4 rgt = ld4s(row + 8);
         const float4 ctr = col[R + j];
-        float w[12] = {lft.x, lft.y, lft.z, lft.w, ctr.x, ctr.y, ctr.z, ctr.w, rgt.x, rgt.y, rgt.z, rgt.w};
+        const float w[12] = {lft.x, lft.y, lft.z, lft.w, ctr.x, ctr.y, ctr.z, ctr.w, rgt.x, rgt.y, rgt.z, rgt.w};
         // Laplacian in difference form, sum_k c_k ((x_{+k} + x_{-k}) + (z_{+k} + z_{-k}) - 4u):
         // exactly zero on a constant field whatever the rounding of the weights.
-        float4 lap;
+        float2 lap[2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float u4 = 4.0f * w[4 + i];
-            float acc = 0.0f;
+        for (int h = 0; h < 2; ++h) {
+            const float2 u = make_float2(w[4 + 2 * h], w[5 + 2 * h]);
+            const float2 nu4 = __fmul2_rn(m4, u);
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int kk = 1; kk <= R; ++kk) {
-                const float t = ((w[4 + i - kk] + w[4 + i + kk]) + (comp(col[R + j - kk], i) + comp(col[R + j + kk], i))) - u4;
-                acc = fmaf(p.c[kk], t, acc);
+                const float2 xs = (kk & 1)
+                    ? make_float2(w[4 + 2 * h - kk] + w[4 + 2 * h + kk], w[5 + 2 * h - kk] + w[5 + 2 * h + kk])
+                    : __fadd2_rn(make_float2(w[4 + 2 * h - kk], w[5 + 2 * h - kk]),
+                                 make_float2(w[4 + 2 * h + kk], w[5 + 2 * h + kk]));
+                const float4 &cm = col[R + j - kk], &cp = col[R + j + kk];
+                const float2 zs = h == 0 ? __fadd2_rn(make_float2(cm.x, cm.y), make_float2(cp.x, cp.y))
+                                         : __fadd2_rn(make_float2(cm.z, cm.w), make_float2(cp.z, cp.w));
+                const float2 t = __fadd2_rn(__fadd2_rn(xs, zs), nu4);
+                acc = __ffma2_rn(make_float2(p.c[kk], p.c[kk]), t, acc);
             }
-            set_comp(lap, i, acc);
+            lap[h] = acc;
         }
 
         const int gz = z0 + lz + j;
@@ -271,42 +275,50 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
         const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
 
         // U^{n+1} = 2u - p + (a - 2) u + (b + 1) p + kappa' L, with the small damping terms
-        // a - 2 = -q (2 + q)/(1 + q) and b + 1 = 2q/(1 + q), q = D dt, formed directly.
-        float4 nxt;
-        if (interior) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float u = comp(ctr, i);
-                set_comp(nxt, i, fmaf(comp(kap, i), comp(lap, i), 2.0f * u - comp(prev, i)));
-            }
-        } else {
-            const float zq = xi2(gz, p.P, p.Nz, p.inv_P);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float q = p.qmax * (xq[i] + zq);
-                const float inv = __frcp_rn(1.0f + q);
-                const float am2 = -q * (2.0f + q) * inv;
-                const float bp1 = 2.0f * q * inv;
-                const float u = comp(ctr, i), pvv = comp(prev, i);
-                set_comp(nxt, i, fmaf(comp(kap, i), comp(lap, i), fmaf(am2, u, fmaf(bp1, pvv, 2.0f * u - pvv))));
-            }
+        // a - 2 = -q (2 + q)/(1 + q) and b + 1 = 2q/(1 + q), q = D dt, read from a table over
+        // the layer depths (computed in FP64 on the host, rounded once).
+        float2 base[2];
+        base[0] = __ffma2_rn(two2, make_float2(ctr.x, ctr.y), make_float2(-prev.x, -prev.y));
+        base[1] = __ffma2_rn(two2, make_float2(ctr.z, ctr.w), make_float2(-prev.z, -prev.w));
+        if (!interior) {
+            const float2 *trow = p.damp_tab + layer_depth(gz, p.P, p.Nz) * (p.P + 1);
+            const float2 t0 = __ldg(trow + xd[0]), t1 = __ldg(trow + xd[1]);
+            const float2 t2 = __ldg(trow + xd[2]), t3 = __ldg(trow + xd[3]);
+            base[0] = __ffma2_rn(make_float2(t0.x, t1.x), make_float2(ctr.x, ctr.y),
+                                 __ffma2_rn(make_float2(t0.y, t1.y), make_float2(prev.x, prev.y), base[0]));
+            base[1] = __ffma2_rn(make_float2(t2.x, t3.x), make_float2(ctr.z, ctr.w),
+                                 __ffma2_rn(make_float2(t2.y, t3.y), make_float2(prev.z, prev.w), base[1]));
         }
+        const float2 n01 = __ffma2_rn(make_float2(kap.x, kap.y), lap[0], base[0]);
+        const float2 n23 = __ffma2_rn(make_float2(kap.z, kap.w), lap[1], base[1]);
+        float4 nxt = make_float4(n01.x, n01.y, n23.x, n23.y);
+        float4 lp = make_float4(lap[0].x, lap[0].y, lap[1].x, lap[1].y);
         // Lanes past the last column stay zero (they are padding of the row pitch).
         if (gx + 4 > p.nxp) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (gx + i >= p.nxp) { set_comp(nxt, i, 0.f); set_comp(lap, i, 0.f); }
+                if (gx + i >= p.nxp) { set_comp(nxt, i, 0.f); set_comp(lp, i, 0.f); }
         }
         st4(p.out + o, nxt);
-        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lap);
+        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lp);
         if (MODE == kAdjoint) {
-            const float4 h = ld4s(hs + lo);
-            float4 g = ld4s(gg + lo);
-            g.x = fmaf(nxt.x, h.x, g.x);
-            g.y = fmaf(nxt.y, h.y, g.y);
-            g.z = fmaf(nxt.z, h.z, g.z);
-            g.w = fmaf(nxt.w, h.w, g.w);
-            st4(p.grad + o, g);
+            const float4 hv = ld4s(hs + lo);
+            const float4 gv = ld4s(gg + lo);
+            const float2 g01 = __ffma2_rn(make_float2(nxt.x, nxt.y), make_float2(hv.x, hv.y), make_float2(gv.x, gv.y));
+            const float2 g23 = __ffma2_rn(make_float2(nxt.z, nxt.w), make_float2(hv.z, hv.w), make_float2(gv.z, gv.w));
+            st4(p.grad + o, make_float4(g01.x, g01.y, g23.x, g23.y));
+        }
+    }
+
+    // Receiver sampling of U^n from the box (each receiver lies in exactly one tile); placed
+    // after the arithmetic so the table load is long complete.
+    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+        for (int e = tid; e < rx_range.y; e += TL::kThreadsPerCta) {
+            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
+            const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
+            const int zn = node >> 16, xn = node & 0xffff;
+            p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
+                box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
         }
     }
 
@@ -325,6 +337,8 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
             atomicAdd(p.grad + o, v * hs[(zn - z0) * kTileX + (xn - x0)]);
         }
     } else {
+        const bool has_src = (src_node >> 16) >= z0 && (src_node >> 16) < z0 + TZ && (src_node & 0xffff) >= x0 &&
+                             (src_node & 0xffff) < x0 + kTileX;
         if (!has_src) return;
         __syncthreads();
         if (tid == 0) {
@@ -423,23 +437,35 @@ __global__ void misfit_sum_kernel(const double *partial, double *misfit, int n_m
     misfit[b] = J;
 }
 
-// Fold the padded per-shot imaging sums onto the physical grid and reduce over transmits in
-// FP64: g[b][iz][ix] = (2 / C) sum_tx sum_{padded cells copying (iz, ix)} G_s.
-__global__ void fold_kernel(const float *g_shot, const float *sos, float *grad, int n_tx, int Nx, int Nz, int P,
-                            long long slice, int pitch)
+// Fold of the padded per-shot imaging sums onto the physical grid with the FP64 reduction over
+// transmits, in two short passes (every dependent FP64 chain stays below n_tx (P + 1) terms):
+//   fold_x: F[b][zp][ix] = sum_tx sum_{xp copying ix} G_s[zp][xp]
+//   fold_z: g[b][iz][ix] = (2 / C) sum_{zp copying iz} F[b][zp][ix]
+__global__ void fold_x_kernel(const float *g_shot, double *fx, int n_tx, int Nx, int P, int nzp, long long slice,
+                              int pitch)
+{
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int zp = blockIdx.y;
+    const int b = blockIdx.z;
+    if (ix >= Nx) return;
+    const int xlo = ix == 0 ? 0 : ix + P, xhi = ix == Nx - 1 ? Nx + 2 * P - 1 : ix + P;
+    double acc = 0.0;
+    for (int t = 0; t < n_tx; ++t) {
+        const float *g = g_shot + static_cast<long long>(b * n_tx + t) * slice + static_cast<long long>(zp) * pitch;
+        for (int x = xlo; x <= xhi; ++x) acc += g[x];
+    }
+    fx[(static_cast<long long>(b) * nzp + zp) * Nx + ix] = acc;
+}
+
+__global__ void fold_z_kernel(const double *fx, const float *sos, float *grad, int Nx, int Nz, int P, int nzp)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y;
     const int b = blockIdx.z;
     if (ix >= Nx) return;
-    const int xlo = ix == 0 ? 0 : ix + P, xhi = ix == Nx - 1 ? Nx + 2 * P - 1 : ix + P;
     const int zlo = iz == 0 ? 0 : iz + P, zhi = iz == Nz - 1 ? Nz + 2 * P - 1 : iz + P;
     double acc = 0.0;
-    for (int t = 0; t < n_tx; ++t) {
-        const float *g = g_shot + static_cast<long long>(b * n_tx + t) * slice;
-        for (int z = zlo; z <= zhi; ++z)
-            for (int x = xlo; x <= xhi; ++x) acc += g[static_cast<long long>(z) * pitch + x];
-    }
+    for (int z = zlo; z <= zhi; ++z) acc += fx[(static_cast<long long>(b) * nzp + z) * Nx + ix];
     const long long o = (static_cast<long long>(b) * Nz + iz) * Nx + ix;
     grad[o] = static_cast<float>(acc * (2.0 / static_cast<double>(sos[o])));
 }
@@ -616,11 +642,14 @@ cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps,
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, int n_maps, int n_tx, int Nx, int Nz,
-                        int P, long long slice, int pitch, cudaStream_t st)
+cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *fx, int n_maps, int n_tx, int Nx,
+                        int Nz, int P, long long slice, int pitch, cudaStream_t st)
 {
-    dim3 grid((Nx + 127) / 128, Nz, n_maps);
-    fold_kernel<<<grid, 128, 0, st>>>(g_shot, sos, grad, n_tx, Nx, Nz, P, slice, pitch);
+    const int nzp = Nz + 2 * P;
+    fold_x_kernel<<<dim3((Nx + 127) / 128, nzp, n_maps), 128, 0, st>>>(g_shot, fx, n_tx, Nx, P, nzp, slice, pitch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fold_z_kernel<<<dim3((Nx + 127) / 128, Nz, n_maps), 128, 0, st>>>(fx, sos, grad, Nx, Nz, P, nzp);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--nt", type=int, default=None, help="override the time axis (profiling of small cases)")
     ap.add_argument("--n-tx", type=int, default=None, help="override the number of transmits")
     ap.add_argument("--tile-z", type=int, default=None, help="step-kernel tile height (32 or 64)")
+    ap.add_argument("--two-step", type=int, default=None, help="1: two time steps per launch, 0: one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -157,6 +158,7 @@ def omp_cores():
 
 def run_reference(args):
     args.tile_z_used = None
+    args.two_step_used = None
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -191,7 +193,7 @@ def workload_config(wl, args):
             "maps_per_gpu": wl.n_maps, "n_tx": wl.n_tx, "n_rx": wl.n_rx, "fd_order": wl.fd_order,
             "ckpt_interval": args.ckpt, "snapshot_dtype": args.snapshot,
             "l2": "flushed between timed steps (256 MiB write outside the events)",
-            "tile": [64, args.tile_z_used]}
+            "tile": [64, args.tile_z_used], "two_step": args.two_step_used}
 
 
 def run_ours(args):
@@ -208,6 +210,8 @@ def run_ours(args):
 
     if args.tile_z:
         dufwi.set_option(dufwi.OPT_TILE_Z, args.tile_z)
+    if args.two_step is not None:
+        dufwi.set_option(dufwi.OPT_TWO_STEP, args.two_step)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
@@ -227,6 +231,7 @@ def run_ours(args):
         dufwi.misfit_gradient(pb, sos, wav, geom, obs, misfit=misfit, grad=grad, workspace=ws)
 
     args.tile_z_used = dufwi.get_option(dufwi.OPT_TILE_Z)
+    args.two_step_used = dufwi.get_option(dufwi.OPT_TWO_STEP)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

@@ -173,10 +173,15 @@ double dufwi_cfl_limit(int32_t fd_order);
 int dufwi_profile_enable(int enable);
 int dufwi_profile_read(double *ms, int64_t *launches, int reset);
 
-/* Tuning options of the step kernels (process-wide; they change speed, never results beyond
- * rounding order). DUFWI_OPT_TILE_Z: output tile height of one CTA, 32 (default) or 64 rows of
- * 64 columns. Both functions return DUFWI_ERR_INVALID_ARG for an unknown option or value. */
+/* Tuning options of the step kernels. They are process-wide and change speed, never results
+ * beyond rounding order.
+ *   DUFWI_OPT_TILE_Z: output tile height of the one-step kernel, 32 (default) or 64 rows of 64
+ *     columns.
+ *   DUFWI_OPT_TWO_STEP: 1 advances pairs of time steps (n, n+1 with n even) in one launch,
+ *     bit-identical to one launch per step (0, the default, which measured faster on GB300).
+ * Both functions return DUFWI_ERR_INVALID_ARG for an unknown option or value. */
 #define DUFWI_OPT_TILE_Z 1
+#define DUFWI_OPT_TWO_STEP 2
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <vector>
 
@@ -55,9 +56,15 @@ struct Layout {
     long long slice;
     size_t snap_elem;
     // byte offsets into the workspace
-    size_t o_status, o_tx, o_rx, o_rxtab, o_rxsorted, o_damp, o_fold, o_kap, o_fa, o_fb, o_ma, o_mb, o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc,
-        o_part, total;
+    int tiles1, tiles2;      // tiles of the one-step kernel (tile height TZ) and of the two-step kernel
+    int n_rxe;               // row length of the grown-tile receiver lists (4 n_rx)
+    size_t o_status, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
+        o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
 };
+
+// Tile height of the one-step kernel (DUFWI_OPT_TILE_Z) and use of the two-step kernel.
+int g_tile_z = kTileZDefault;
+int g_two_step = 0;
 
 int validate_problem(const dufwi_problem *pb)
 {
@@ -107,20 +114,26 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, bool
     const size_t cdb = (size_t)L->S * L->nt * (L->n_rx > 0 ? L->n_rx : 1) * sizeof(float);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+    const size_t nrx1 = L->n_rx > 0 ? L->n_rx : 1;
+    const int tiles_x = (L->nxp + kTileX - 1) / kTileX;
+    L->tiles1 = tiles_x * ((L->nzp + g_tile_z - 1) / g_tile_z);
+    L->tiles2 = tiles_x * ((L->nzp + kPairTileZ - 1) / kPairTileZ);
+    L->n_rxe = 4 * (int)nrx1;
     L->o_status = take(sizeof(int));
     L->o_tx = take(sizeof(int) * L->n_tx);
-    L->o_rx = take(sizeof(int) * (size_t)L->n_tx * (L->n_rx > 0 ? L->n_rx : 1));
-    const size_t tiles_max = (size_t)((L->nxp + kTileX - 1) / kTileX) * ((L->nzp + 31) / 32);
-    L->o_rxtab = take(sizeof(int2) * (size_t)L->n_tx * tiles_max);
-    L->o_rxsorted = take(sizeof(int) * (size_t)L->n_tx * (L->n_rx > 0 ? L->n_rx : 1));
+    L->o_rx = take(sizeof(int) * (size_t)L->n_tx * nrx1);
+    L->o_tab1 = take(sizeof(int2) * (size_t)L->n_tx * L->tiles1);
+    L->o_sorted1 = take(sizeof(int) * (size_t)L->n_tx * nrx1);
+    L->o_tab2 = take(sizeof(int2) * (size_t)L->n_tx * L->tiles2);
+    L->o_sorted2 = take(sizeof(int) * (size_t)L->n_tx * nrx1);
+    L->o_tabe = take(sizeof(int2) * (size_t)L->n_tx * L->tiles2);
+    L->o_sortede = take(sizeof(int) * (size_t)L->n_tx * L->n_rxe);
     L->o_damp = take(sizeof(float2) * (size_t)(L->P + 1) * (L->P + 1));
     L->o_kap = take((size_t)n_maps * L->slice * sizeof(float));
-    L->o_fa = take(field);
-    L->o_fb = take(field);
+    for (int i = 0; i < 4; ++i) L->o_f[i] = take(field);
     if (gradient) {
         const bool store_all = pb->ckpt_interval == 0 || pb->ckpt_interval >= steps;
-        L->o_ma = take(field);
-        L->o_mb = take(field);
+        for (int i = 0; i < 4; ++i) L->o_m[i] = take(field);
         L->o_grad = take(field);
         L->o_hist = take(field * (size_t)L->n_hist);
         if (!store_all) {
@@ -198,22 +211,6 @@ int tensor_map(CUtensorMap *tm, const void *base, const Layout &L, int d2, int d
     return r == CUDA_SUCCESS ? DUFWI_OK : DUFWI_ERR_CUDA;
 }
 
-// Tile height of the step kernels (DUFWI_OPT_TILE_Z).
-int g_tile_z = kTileZDefault;
-
-// Maps of a step that reads `cur` with halo and updates `out` in place (tile height tz).
-int step_maps(StepMaps *m, const float *cur, const float *out, const float *kap, const float *hist, int n_hist,
-              const float *grad, const Layout &L, int tz)
-{
-    memset(m, 0, sizeof(*m));
-    int rc = tensor_map(&m->cur_box, cur, L, L.S, 0, kBoxX, tz + 2 * kHalo);
-    if (!rc) rc = tensor_map(&m->out_tile, out, L, L.S, 0, kTileX, tz);
-    if (!rc) rc = tensor_map(&m->kap_tile, kap, L, L.n_maps, 0, kTileX, tz);
-    if (!rc && hist) rc = tensor_map(&m->hist_tile, hist, L, L.S, n_hist, kTileX, tz);
-    if (!rc && grad) rc = tensor_map(&m->grad_tile, grad, L, L.S, 0, kTileX, tz);
-    return rc;
-}
-
 #define CK(x)                                                                                                        \
     do {                                                                                                             \
         if ((x) != cudaSuccess) return DUFWI_ERR_CUDA;                                                               \
@@ -261,15 +258,68 @@ struct Profiler {
 Profiler g_prof;
 constexpr size_t kProfEvents = 1 << 14;
 
+// Tensor maps of one field buffer: read with halo by the one-step kernel (box1, 72 x (TZ + 8)),
+// updated in place by it (tile1, 64 x TZ), read with halo by the two-step kernel (box2, 80 x 48)
+// and read on the grown tile by it (ring2, 72 x 40).
+struct FieldMaps {
+    CUtensorMap box1, tile1, box2, ring2;
+};
+
 struct Ctx {
     Layout L;
     const dufwi_problem *pb;
     char *ws;
     cudaStream_t st;
     StepParams base;
+    int tz;
+    bool two_step;
+    FieldMaps fmap[4], mmap[4];
+    CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2;
     int *status() const { return reinterpret_cast<int *>(ws + L.o_status); }
     template <typename T> T *at(size_t o) const { return reinterpret_cast<T *>(ws + o); }
 };
+
+int field_maps(FieldMaps *m, const float *buf, const Layout &L, int tz)
+{
+    int rc = tensor_map(&m->box1, buf, L, L.S, 0, kBoxX, tz + 2 * kHalo);
+    if (!rc) rc = tensor_map(&m->tile1, buf, L, L.S, 0, kTileX, tz);
+    if (!rc) rc = tensor_map(&m->box2, buf, L, L.S, 0, kTileX + 4 * kHalo, kPairTileZ + 4 * kHalo);
+    if (!rc) rc = tensor_map(&m->ring2, buf, L, L.S, 0, kTileX + 2 * kHalo, kPairTileZ + 2 * kHalo);
+    return rc;
+}
+
+// Receivers of each transmit grouped by tile (tiles of width 64 and height tz, row-major), as
+// (first, count) per tile into a list of receiver indices. grow > 0 lists a receiver in every
+// tile whose rectangle grown by `grow` cells contains it (row length of the list: 4 n_rx).
+void receiver_tables(const std::vector<int> &rx, const Layout &L, int tz, int grow, std::vector<int2> &tab,
+                     std::vector<int> &sorted, int row_len)
+{
+    const int tiles_x = (L.nxp + kTileX - 1) / kTileX, tiles_z = (L.nzp + tz - 1) / tz;
+    const int tiles = tiles_x * tiles_z;
+    auto floor_div = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    tab.assign((size_t)L.n_tx * tiles, make_int2(0, 0));
+    sorted.assign((size_t)L.n_tx * (row_len > 0 ? row_len : 1), 0);
+    std::vector<std::vector<int>> lists(tiles);
+    for (int t = 0; t < L.n_tx; ++t) {
+        for (auto &v : lists) v.clear();
+        for (int r = 0; r < L.n_rx; ++r) {
+            const int node = rx[(size_t)t * L.n_rx + r];
+            const int zn = node >> 16, xn = node & 0xffff;
+            // tiles c with c*w - grow <= n < (c+1)*w + grow
+            const int cx0 = std::max(0, floor_div(xn - grow - kTileX, kTileX) + 1);
+            const int cx1 = std::min(tiles_x - 1, floor_div(xn + grow, kTileX));
+            const int cz0 = std::max(0, floor_div(zn - grow - tz, tz) + 1);
+            const int cz1 = std::min(tiles_z - 1, floor_div(zn + grow, tz));
+            for (int cz = cz0; cz <= cz1; ++cz)
+                for (int cx = cx0; cx <= cx1; ++cx) lists[cz * tiles_x + cx].push_back(r);
+        }
+        int acc = 0;
+        for (int k = 0; k < tiles; ++k) {
+            tab[(size_t)t * tiles + k] = make_int2(acc, (int)lists[k].size());
+            for (int r : lists[k]) sorted[(size_t)t * row_len + acc++] = r;
+        }
+    }
+}
 
 int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_array *arr, const float *wavelet,
                  const dufwi_shots *sh, void *workspace, size_t ws_bytes, void *stream, bool gradient)
@@ -282,55 +332,66 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (rc) return rc;
     c.ws = static_cast<char *>(workspace);
     c.st = static_cast<cudaStream_t>(stream);
-    // receivers grouped by the step-kernel tile that contains them, per transmit
-    const int tz = g_tile_z;
-    const int tiles_x = (L.nxp + kTileX - 1) / kTileX, tiles = tiles_x * ((L.nzp + tz - 1) / tz);
-    std::vector<int2> tab((size_t)L.n_tx * tiles, make_int2(0, 0));
-    std::vector<int> sorted((size_t)L.n_tx * (L.n_rx > 0 ? L.n_rx : 1), 0);
-    std::vector<int> tile_of(L.n_rx > 0 ? L.n_rx : 1);
-    for (int t = 0; t < L.n_tx; ++t) {
-        int2 *row = tab.data() + (size_t)t * tiles;
-        for (int r = 0; r < L.n_rx; ++r) {
-            const int node = rx[(size_t)t * L.n_rx + r];
-            tile_of[r] = ((node >> 16) / tz) * tiles_x + (node & 0xffff) / kTileX;
-            row[tile_of[r]].y++;
-        }
-        int acc = 0;
-        for (int k = 0; k < tiles; ++k) { row[k].x = acc; acc += row[k].y; }
-        std::vector<int> fill(tiles, 0);
-        for (int r = 0; r < L.n_rx; ++r)
-            sorted[(size_t)t * L.n_rx + row[tile_of[r]].x + fill[tile_of[r]]++] = r;
-    }
+    c.tz = g_tile_z;
+    c.two_step = g_two_step != 0;
+    const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
+    std::vector<int2> tab1, tab2, tabe;
+    std::vector<int> sorted1, sorted2, sortede;
+    receiver_tables(rx, L, c.tz, 0, tab1, sorted1, nrx1);
+    receiver_tables(rx, L, kPairTileZ, 0, tab2, sorted2, nrx1);
+    receiver_tables(rx, L, kPairTileZ, kHalo, tabe, sortede, L.n_rxe);
     // damping terms (a - 2, b + 1) of Eq. 2 at every pair of layer depths, in FP64, rounded once
-    const dufwi_problem *pbh = c.pb;
-    const double d0h = 3.0 * pbh->pml_cref * log(1.0 / pbh->pml_R) / (2.0 * pbh->pml_cells * pbh->dx);
+    const dufwi_problem *pb = c.pb;
+    const double d0 = 3.0 * pb->pml_cref * log(1.0 / pb->pml_R) / (2.0 * pb->pml_cells * pb->dx);
     std::vector<float2> damp((size_t)(L.P + 1) * (L.P + 1));
     for (int dz = 0; dz <= L.P; ++dz)
         for (int dxl = 0; dxl <= L.P; ++dxl) {
             const double xz = (double)dz / L.P, xx = (double)dxl / L.P;
-            const double q = (d0h * xx * xx + d0h * xz * xz) * pbh->dt;
-            damp[(size_t)dz * (L.P + 1) + dxl] = make_float2((float)(-q * (2.0 + q) / (1.0 + q)), (float)(2.0 * q / (1.0 + q)));
+            const double q = (d0 * xx * xx + d0 * xz * xz) * pb->dt;
+            damp[(size_t)dz * (L.P + 1) + dxl] =
+                make_float2((float)(-q * (2.0 + q) / (1.0 + q)), (float)(2.0 * q / (1.0 + q)));
         }
-    CK(cudaMemsetAsync(c.status(), 0, sizeof(int), c.st));
-    CK(cudaMemcpyAsync(c.at<float2>(L.o_damp), damp.data(), sizeof(float2) * damp.size(), cudaMemcpyHostToDevice,
-                       c.st));
-    CK(cudaMemcpyAsync(c.at<int>(L.o_tx), tx.data(), sizeof(int) * tx.size(), cudaMemcpyHostToDevice, c.st));
-    CK(cudaMemcpyAsync(c.at<int>(L.o_rx), rx.data(), sizeof(int) * rx.size(), cudaMemcpyHostToDevice, c.st));
-    CK(cudaMemcpyAsync(c.at<int2>(L.o_rxtab), tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice, c.st));
-    CK(cudaMemcpyAsync(c.at<int>(L.o_rxsorted), sorted.data(), sizeof(int) * sorted.size(), cudaMemcpyHostToDevice,
-                       c.st));
     // copies from pageable memory are staged before cudaMemcpyAsync returns
-    const dufwi_problem *pb = c.pb;
-    const double d0 = 3.0 * pb->pml_cref * log(1.0 / pb->pml_R) / (2.0 * pb->pml_cells * pb->dx);
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(c.ws + off, src, bytes, cudaMemcpyHostToDevice, c.st);
+    };
+    CK(cudaMemsetAsync(c.status(), 0, sizeof(int), c.st));
+    CK(up(L.o_damp, damp.data(), sizeof(float2) * damp.size()));
+    CK(up(L.o_tx, tx.data(), sizeof(int) * tx.size()));
+    CK(up(L.o_rx, rx.data(), sizeof(int) * rx.size()));
+    CK(up(L.o_tab1, tab1.data(), sizeof(int2) * tab1.size()));
+    CK(up(L.o_sorted1, sorted1.data(), sizeof(int) * sorted1.size()));
+    CK(up(L.o_tab2, tab2.data(), sizeof(int2) * tab2.size()));
+    CK(up(L.o_sorted2, sorted2.data(), sizeof(int) * sorted2.size()));
+    CK(up(L.o_tabe, tabe.data(), sizeof(int2) * tabe.size()));
+    CK(up(L.o_sortede, sortede.data(), sizeof(int) * sortede.size()));
+
     long long nl = 0;
     const int e0 = g_prof.mark(c.st);
     CKL(launch_setup_kappa(sos, density, c.at<float>(L.o_kap), c.status(), L.n_maps, L.Nx, L.Nz, L.P, L.nxp, L.nzp,
                            L.pitch, pb->dt / pb->dx, d0, pb->dt, pb->c_max, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
 
+    // tensor maps of every buffer
+    const float *kap = c.at<float>(L.o_kap);
+    for (int i = 0; i < 4; ++i)
+        if (field_maps(&c.fmap[i], c.at<float>(L.o_f[i]), L, c.tz)) return DUFWI_ERR_CUDA;
+    if (tensor_map(&c.kap1, kap, L, L.n_maps, 0, kTileX, c.tz) ||
+        tensor_map(&c.kap2, kap, L, L.n_maps, 0, kTileX + 2 * kHalo, kPairTileZ + 2 * kHalo))
+        return DUFWI_ERR_CUDA;
+    if (gradient) {
+        for (int i = 0; i < 4; ++i)
+            if (field_maps(&c.mmap[i], c.at<float>(L.o_m[i]), L, c.tz)) return DUFWI_ERR_CUDA;
+        const float *hist = c.at<float>(L.o_hist), *g = c.at<float>(L.o_grad);
+        if (tensor_map(&c.hist1, hist, L, L.S, L.n_hist, kTileX, c.tz) ||
+            tensor_map(&c.hist2, hist, L, L.S, L.n_hist, kTileX, kPairTileZ) ||
+            tensor_map(&c.grad1, g, L, L.S, 0, kTileX, c.tz) || tensor_map(&c.grad2, g, L, L.S, 0, kTileX, kPairTileZ))
+            return DUFWI_ERR_CUDA;
+    }
+
     StepParams &p = c.base;
     memset(&p, 0, sizeof(p));
-    p.kap = c.at<float>(L.o_kap);
+    p.kap = kap;
     p.status = c.status();
     p.slice = L.slice;
     p.nxp = L.nxp; p.nzp = L.nzp; p.pitch = L.pitch;
@@ -340,37 +401,141 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     p.P = L.P; p.Nx = L.Nx; p.Nz = L.Nz;
     p.damp_tab = c.at<float2>(L.o_damp);
     stencil_weights(pb->fd_order, p.c);
-    p.tile_z = tz;
-    p.rx_tab = c.at<int2>(L.o_rxtab);
-    p.rx_sorted = c.at<int>(L.o_rxsorted);
-    (void)gradient;
+    p.tile_z = c.tz;
+    p.rxe_tab = c.at<int2>(L.o_tabe);
+    p.rxe_sorted = c.at<int>(L.o_sortede);
+    p.n_rxe = L.n_rxe;
     return DUFWI_OK;
 }
 
-// Forward sweep from rest over steps [0, nt-1): U^{n+1} from U^n and U^{n-1}, recording U^n at
-// the receivers; optional history (store-all) and snapshots every K steps.
-int forward_sweep(Ctx &c, const float *wavelet, float *cd, float *fa, float *fb, const StepMaps &ta,
-                  const StepMaps &tb, bool store_hist, bool snapshots)
+// Four rotating field buffers of one sweep: cur holds U^n (mu^{m+1}), prv U^{n-1} (mu^{m+2}).
+// A one-step launch updates prv in place; a two-step launch writes the two spare buffers.
+struct Ring {
+    float *buf[4];
+    const FieldMaps *map;
+    int cur, prv;
+    void spares(int &a, int &b) const
+    {
+        int k = 0, sp[2] = {0, 0};
+        for (int i = 0; i < 4; ++i)
+            if (i != cur && i != prv) sp[k++] = i;
+        a = sp[0];
+        b = sp[1];
+    }
+};
+
+// One step n -> n+1 (forward modes) or m+1 -> m (adjoint), in place.
+int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
+{
+    StepMaps tm;
+    memset(&tm, 0, sizeof(tm));
+    tm.cur_box = rg.map[rg.cur].box1;
+    tm.out_tile = rg.map[rg.prv].tile1;
+    tm.kap_tile = c.kap1;
+    if (mode == kAdjoint) { tm.hist_tile = c.hist1; tm.grad_tile = c.grad1; }
+    p.out = rg.buf[rg.prv];
+    p.rx_tab = c.at<int2>(c.L.o_tab1);
+    p.rx_sorted = c.at<int>(c.L.o_sorted1);
+    CKL(launch_step(c.L.radius, mode, tm, p, c.st));
+    std::swap(rg.cur, rg.prv);
+    return DUFWI_OK;
+}
+
+// Two steps per launch: n -> n+2 (forward modes) or m+1 -> m-1 (adjoint).
+int two_steps(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
+{
+    int a, b;
+    rg.spares(a, b);
+    StepMaps tm;
+    memset(&tm, 0, sizeof(tm));
+    tm.cur_box = rg.map[rg.cur].box2;
+    tm.out_tile = rg.map[rg.prv].ring2;
+    tm.kap_tile = c.kap2;
+    if (mode == kAdjoint) { tm.hist_tile = c.hist2; tm.grad_tile = c.grad2; }
+    p.out = rg.buf[a];
+    p.out2 = rg.buf[b];
+    p.rx_tab = c.at<int2>(c.L.o_tab2);
+    p.rx_sorted = c.at<int>(c.L.o_sorted2);
+    CKL(launch_step2(c.L.radius, mode, tm, p, c.st));
+    rg.prv = a;
+    rg.cur = b;
+    return DUFWI_OK;
+}
+
+// Forward steps n = n0 .. n1-1 (producing U^{n1}). Steps pair up from even n when the two-step
+// kernel is enabled, so every schedule covering a step uses the same grouping. hist: base of the
+// history slots of this range (slot n - h0), or null.
+int forward_range(Ctx &c, Ring &rg, int n0, int n1, int mode, const float *wavelet, float *cd, float *hist, int h0,
+                  long long &nl)
+{
+    const size_t hstride = (size_t)c.L.S * c.L.slice;
+    StepParams p = c.base;
+    p.inj_node = c.at<int>(c.L.o_tx);
+    p.inj_val = wavelet;
+    p.smp_node = c.at<int>(c.L.o_rx);
+    p.cd = cd;
+    for (int n = n0; n < n1;) {
+        p.step = n;
+        p.hist = hist ? hist + (size_t)(n - h0) * hstride : nullptr;
+        if (c.two_step && n % 2 == 0 && n + 2 <= n1) {
+            p.hist2 = hist ? hist + (size_t)(n + 1 - h0) * hstride : nullptr;
+            int rc = two_steps(c, rg, mode, p, nl);
+            if (rc) return rc;
+            n += 2;
+        } else {
+            int rc = one_step(c, rg, mode, p, nl);
+            if (rc) return rc;
+            n += 1;
+        }
+    }
+    return DUFWI_OK;
+}
+
+// Adjoint steps m = m1 .. m0 (descending), imaging with Lap(U^{m-1}) at history slot m-1-h0.
+int adjoint_range(Ctx &c, Ring &rg, int m1, int m0, const float *asrc, float *g_shot, int h0, long long &nl)
+{
+    StepParams p = c.base;
+    p.inj_node = c.at<int>(c.L.o_rx);
+    p.inj_val = asrc;
+    p.grad = g_shot;
+    for (int m = m1; m >= m0;) {
+        p.step = m;
+        p.hist_slot = m - 1 - h0;
+        if (c.two_step && m % 2 == 0 && m - 1 >= m0) {
+            p.hist_slot2 = m - 2 - h0;
+            int rc = two_steps(c, rg, kAdjoint, p, nl);
+            if (rc) return rc;
+            m -= 2;
+        } else {
+            int rc = one_step(c, rg, kAdjoint, p, nl);
+            if (rc) return rc;
+            m -= 1;
+        }
+    }
+    return DUFWI_OK;
+}
+
+// Forward sweep from rest over steps [0, nt-1): traces, and either the whole history or the
+// snapshots (U^n, U^{n-1}) at n = 0, K, 2K, ...
+int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_hist, bool snapshots)
 {
     const Layout &L = c.L;
     long long nl = 0;
     const int e0 = g_prof.mark(c.st);
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
-    CK(cudaMemsetAsync(fa, 0, field, c.st));
-    CK(cudaMemsetAsync(fb, 0, field, c.st));
-    float *cur = fa, *prv = fb;
-    const StepMaps *tcur = &ta, *tprv = &tb;
-    StepParams p = c.base;
-    p.inj_node = c.at<int>(L.o_tx);
-    p.inj_val = wavelet;
-    p.smp_node = c.at<int>(L.o_rx);
-    p.cd = cd;
+    for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(rg.buf[i], 0, field, c.st));
+    rg.cur = 0;
+    rg.prv = 1;
     const int dtype = c.pb->snapshot_dtype;
-    for (int n = 0; n < L.nt - 1; ++n) {
-        if (snapshots && n % L.K == 0) {
+    const int mode = store_hist ? kFwdSampleHist : kFwdSample;
+    float *hist = store_hist ? c.at<float>(L.o_hist) : nullptr;
+    const int seg = snapshots ? L.K : (L.nt > 1 ? L.nt - 1 : 1);
+    for (int n = 0; n < L.nt - 1; n += seg) {
+        if (snapshots) {
             const int sg = n / L.K;
             char *snap = c.at<char>(L.o_snap) + (size_t)sg * 2 * L.S * L.slice * L.snap_elem;
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
+            float *cur = rg.buf[rg.cur], *prv = rg.buf[rg.prv];
             if (dtype == DUFWI_SNAP_FP32) {
                 CK(cudaMemcpyAsync(snap, cur, field, cudaMemcpyDeviceToDevice, c.st));
                 CK(cudaMemcpyAsync(snap_d, prv, field, cudaMemcpyDeviceToDevice, c.st));
@@ -381,15 +546,13 @@ int forward_sweep(Ctx &c, const float *wavelet, float *cd, float *fa, float *fb,
                 CKL(launch_snap_store(cur, prv, snap, snap_d, sc, dtype, L.S, L.slice, L.nxp, L.nzp, L.pitch, c.st));
             }
         }
-        p.out = prv;
-        p.step = n;
-        p.hist = store_hist ? c.at<float>(L.o_hist) + (size_t)n * L.S * L.slice : nullptr;
-        CKL(launch_step(L.radius, store_hist ? kFwdSampleHist : kFwdSample, *tcur, p, c.st));
-        float *t = cur; cur = prv; prv = t;
-        const StepMaps *tt = tcur; tcur = tprv; tprv = tt;
+        const int n1 = std::min(n + seg, L.nt - 1);
+        int rc = forward_range(c, rg, n, n1, mode, wavelet, cd, hist, 0, nl);
+        if (rc) return rc;
     }
     if (L.n_rx > 0)
-        CKL(launch_sample(cur, c.at<int>(L.o_rx), cd, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt, L.nt - 1, c.st));
+        CKL(launch_sample(rg.buf[rg.cur], c.at<int>(L.o_rx), cd, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt,
+                          L.nt - 1, c.st));
     g_prof.span(0, e0, g_prof.mark(c.st), nl);
     return DUFWI_OK;
 }
@@ -410,6 +573,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 32 && value != 64) return DUFWI_ERR_INVALID_ARG;
         g_tile_z = value;
         return DUFWI_OK;
+    case DUFWI_OPT_TWO_STEP:
+        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
+        g_two_step = value;
+        return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
     }
 }
@@ -419,6 +586,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     if (!value) return DUFWI_ERR_INVALID_ARG;
     switch (option) {
     case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
+    case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
     }
 }
@@ -526,12 +694,10 @@ int dufwi_simulate(const dufwi_problem *pb, const float *sos, const float *densi
     if (!cd && c.L.n_rx > 0) return DUFWI_ERR_INVALID_ARG;
     rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
     if (rc) return rc;
-    float *fa = c.at<float>(c.L.o_fa), *fb = c.at<float>(c.L.o_fb);
-    const float *kap = c.at<float>(c.L.o_kap);
-    StepMaps ta, tb;
-    if (step_maps(&ta, fa, fb, kap, nullptr, 0, nullptr, c.L, c.base.tile_z) || step_maps(&tb, fb, fa, kap, nullptr, 0, nullptr, c.L, c.base.tile_z))
-        return DUFWI_ERR_CUDA;
-    return forward_sweep(c, wavelet, cd, fa, fb, ta, tb, false, false);
+    Ring rg;
+    for (int i = 0; i < 4; ++i) rg.buf[i] = c.at<float>(c.L.o_f[i]);
+    rg.map = c.fmap;
+    return forward_sweep(c, rg, wavelet, cd, false, false);
 }
 
 int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
@@ -548,22 +714,23 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
     if (rc) return rc;
     const Layout &L = c.L;
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
-    float *fa = c.at<float>(L.o_fa), *fb = c.at<float>(L.o_fb);
-    float *ma = c.at<float>(L.o_ma), *mb = c.at<float>(L.o_mb);
-    const float *kap = c.at<float>(L.o_kap);
-    float *hist = c.at<float>(L.o_hist);
-    float *g_shot = c.at<float>(L.o_grad);
-    StepMaps ta, tb, tma, tmb;
-    if (step_maps(&ta, fa, fb, kap, nullptr, 0, nullptr, L, c.base.tile_z) || step_maps(&tb, fb, fa, kap, nullptr, 0, nullptr, L, c.base.tile_z) ||
-        step_maps(&tma, ma, mb, kap, hist, L.n_hist, g_shot, L, c.base.tile_z) || step_maps(&tmb, mb, ma, kap, hist, L.n_hist, g_shot, L, c.base.tile_z))
-        return DUFWI_ERR_CUDA;
     const bool store_all = (L.n_seg == 1);
     float *cd = c.at<float>(L.o_cd);
+    float *hist = c.at<float>(L.o_hist);
+    float *g_shot = c.at<float>(L.o_grad);
+    Ring fr, ar;
+    for (int i = 0; i < 4; ++i) {
+        fr.buf[i] = c.at<float>(L.o_f[i]);
+        ar.buf[i] = c.at<float>(L.o_m[i]);
+    }
+    fr.map = c.fmap;
+    ar.map = c.mmap;
 
     // 1. forward sweep: traces, and either the whole history or the snapshots
-    rc = forward_sweep(c, wavelet, cd, fa, fb, ta, tb, store_all, !store_all);
+    rc = forward_sweep(c, fr, wavelet, cd, store_all, !store_all);
     if (rc) return rc;
-    if (cd_sim && L.n_rx > 0) CK(cudaMemcpyAsync(cd_sim, cd, (size_t)L.S * L.nt * L.n_rx * sizeof(float), cudaMemcpyDeviceToDevice, c.st));
+    if (cd_sim && L.n_rx > 0)
+        CK(cudaMemcpyAsync(cd_sim, cd, (size_t)L.S * L.nt * L.n_rx * sizeof(float), cudaMemcpyDeviceToDevice, c.st));
 
     // 2. residual, misfit and adjoint source
     float *asrc = c.at<float>(L.o_asrc);
@@ -576,60 +743,39 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
 
     // 3. reverse sweep, segment by segment
-    CK(cudaMemsetAsync(ma, 0, field, c.st));
-    CK(cudaMemsetAsync(mb, 0, field, c.st));
+    for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(ar.buf[i], 0, field, c.st));
+    ar.cur = 0;
+    ar.prv = 1;
     CK(cudaMemsetAsync(g_shot, 0, field, c.st));
-    float *mcur = ma, *mprv = mb;                 // mu^{m+1}, mu^{m+2}
-    const StepMaps *tmc = &tma, *tmp = &tmb;
-    StepParams ap = c.base;
-    ap.inj_node = c.at<int>(L.o_rx);
-    ap.inj_val = asrc;
-    ap.grad = g_shot;
-    StepParams fp = c.base;
-    fp.inj_node = c.at<int>(L.o_tx);
-    fp.inj_val = wavelet;
     const int dtype = pb->snapshot_dtype;
-    const size_t hstride = (size_t)L.S * L.slice;
     for (int sg = L.n_seg - 1; sg >= 0; --sg) {
         const int t0 = store_all ? 0 : sg * L.K;
-        const int t1 = store_all ? L.nt - 1 : (t0 + L.K < L.nt - 1 ? t0 + L.K : L.nt - 1);
+        const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
         if (!store_all) {
             nl = 0;
             e0 = g_prof.mark(c.st);
             // restore (U^{t0}, U^{t0-1}) and recompute Lap(U^n) for n = t0 .. t1-1
             char *snap = c.at<char>(L.o_snap) + (size_t)sg * 2 * L.S * L.slice * L.snap_elem;
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
+            fr.cur = 0;
+            fr.prv = 1;
             if (dtype == DUFWI_SNAP_FP32) {
-                CK(cudaMemcpyAsync(fa, snap, field, cudaMemcpyDeviceToDevice, c.st));
-                CK(cudaMemcpyAsync(fb, snap_d, field, cudaMemcpyDeviceToDevice, c.st));
+                CK(cudaMemcpyAsync(fr.buf[0], snap, field, cudaMemcpyDeviceToDevice, c.st));
+                CK(cudaMemcpyAsync(fr.buf[1], snap_d, field, cudaMemcpyDeviceToDevice, c.st));
             } else {
                 const unsigned *sc = c.at<unsigned>(L.o_scale) + (size_t)sg * 2 * L.S;
-                CKL(launch_snap_load(fa, fb, snap, snap_d, sc, dtype, L.S, L.slice, L.nxp, L.nzp, L.pitch, c.st));
+                CKL(launch_snap_load(fr.buf[0], fr.buf[1], snap, snap_d, sc, dtype, L.S, L.slice, L.nxp, L.nzp,
+                                     L.pitch, c.st));
             }
-            float *cur = fa, *prv = fb;
-            const StepMaps *tc = &ta, *tp = &tb;
-            for (int n = t0; n < t1; ++n) {
-                fp.out = prv;
-                fp.step = n;
-                fp.hist = hist + (size_t)(n - t0) * hstride;
-                CKL(launch_step(L.radius, kFwdHist, *tc, fp, c.st));
-                float *t = cur; cur = prv; prv = t;
-                const StepMaps *tt = tc; tc = tp; tp = tt;
-            }
+            rc = forward_range(c, fr, t0, t1, kFwdHist, wavelet, nullptr, hist, t0, nl);
+            if (rc) return rc;
             g_prof.span(1, e0, g_prof.mark(c.st), nl);
         }
+        // adjoint steps m = t1 .. t0+1, imaging with Lap(U^{m-1})
         nl = 0;
         e0 = g_prof.mark(c.st);
-        // adjoint steps m = t1 .. t0+1, imaging with Lap(U^{m-1})
-        for (int m = t1; m >= t0 + 1; --m) {
-            ap.out = mprv;
-            ap.step = m;
-            ap.hist = hist + (size_t)(m - 1 - t0) * hstride;
-            ap.hist_slot = m - 1 - t0;
-            CKL(launch_step(L.radius, kAdjoint, *tmc, ap, c.st));
-            float *t = mcur; mcur = mprv; mprv = t;
-            const StepMaps *tt = tmc; tmc = tmp; tmp = tt;
-        }
+        rc = adjoint_range(c, ar, t1, t0 + 1, asrc, g_shot, t0, nl);
+        if (rc) return rc;
         g_prof.span(2, e0, g_prof.mark(c.st), nl);
     }
     // 4. (2/C) scaling, fold of the absorbing layer, FP64 reduction over transmits

@@ -50,6 +50,13 @@ struct StepParams {
     const int *smp_node;     // forward: receivers [n_tx][n_rx]
     const int2 *rx_tab;      // [n_tx][tiles]: (first, count) of the receivers inside each tile
     const int *rx_sorted;    // [n_tx][n_rx]: receiver indices grouped by tile (row-major tiles)
+    const int2 *rxe_tab;     // two-step kernel: (first, count) of the receivers inside each tile
+                             // grown by 4 cells on every side
+    const int *rxe_sorted;   // [n_tx][n_rxe]: receiver indices grouped by grown tile
+    int n_rxe;               // row length of rxe_sorted
+    float *out2;             // two-step kernel: U^{n+2} (mu^{m-1}); out holds U^{n+1} (mu^m)
+    float *hist2;            // two-step kernel: Lap(U^{n+1}) (forward history)
+    int hist_slot2;          // two-step adjoint: slot of Lap(U^{m-2})
     float *cd;               // forward: channel data [S][nt][n_rx] (sampled at U^n)
     int *status;             // device status word
     long long slice;         // nzp * pitch
@@ -68,6 +75,9 @@ struct StepParams {
 
 // Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.
 cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
+// Two time steps per launch (core tiles 64 x 32; see step2_kernel).
+cudaError_t launch_step2(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
+constexpr int kPairTileZ = 32;   // core tile height of the two-step kernel (64 x 32 tiles)
 cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, int *status,
                                int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch,
                                double dt_over_dx, double d0, double dt, double c_max,

@@ -65,10 +65,7 @@ __device__ __forceinline__ void raise_status(int *status, int code)
 
 __device__ __forceinline__ float4 ld4s(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ void set_comp(float4 &v, int i, float s)
-{
-    if (i == 0) v.x = s; else if (i == 1) v.y = s; else if (i == 2) v.z = s; else v.w = s;
-}
+__device__ __forceinline__ void st4s(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
 // Depth (in cells, 0..P) into the absorbing layer of padded index i along an axis of N cells.
 __device__ __forceinline__ int layer_depth(int i, int P, int N)
@@ -143,16 +140,172 @@ struct TileLayout {
     static constexpr int kThreadsPerCta = (kTileX / 4) * (TZ / 4);      // 4 (x) x 4 (z) outputs each
 };
 
-// One 64 x TZ output tile of one shot per CTA. A single mbarrier collects the TMA loads of the
-// (64 + 8) x (TZ + 8) box of U^n and of the 64 x TZ tiles of U^{n-1} and kappa' (and, in the
-// adjoint, of Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay resident per SM,
-// so the loads of some overlap the arithmetic of others.
+constexpr int kMaxInj = 64;   // point injections staged in shared memory per list
+
+// Point injections of one step into a region of shared memory: source samples (forward) or
+// scaled residuals at receivers (adjoint). They are gathered in parallel into shared memory
+// and applied by one thread in list order, so the result is deterministic even when several
+// entries hit the same node.
+struct InjList {
+    int n;
+    int idx[kMaxInj];
+    float val[kMaxInj];
+};
+
+// Fills `l` (called by every thread; a barrier must follow before use) with the injections of
+// step `step` that land in the region [rz0, rz0 + rh) x [rx0, rx0 + rw) of shot s; the local
+// index is (z - rz0) * stride + (x - rx0). range: (first, count) into p.rx_sorted (adjoint).
+template <int MODE>
+__device__ __forceinline__ void gather_injections(InjList &l, const StepParams &p, const int *sorted, int n_sorted,
+                                                  int s, int tx_idx, int step, int2 range, int rx0, int rz0, int rw,
+                                                  int rh, int stride, int tid, int nthreads)
+{
+    if (MODE == kAdjoint) {
+        if (tid == 0) l.n = range.y;
+        const int m = min(range.y, kMaxInj);
+        for (int e = tid; e < m; e += nthreads) {
+            const int r = __ldg(sorted + tx_idx * n_sorted + range.x + e);
+            const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
+            l.idx[e] = ((node >> 16) - rz0) * stride + ((node & 0xffff) - rx0);
+            l.val[e] = __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + step) * p.n_rx + r);
+        }
+    } else if (tid == 0) {
+        const int node = __ldg(p.inj_node + tx_idx);
+        const int zn = node >> 16, xn = node & 0xffff;
+        const bool in = zn >= rz0 && zn < rz0 + rh && xn >= rx0 && xn < rx0 + rw;
+        l.n = in ? 1 : 0;
+        if (in) {
+            l.idx[0] = (zn - rz0) * stride + (xn - rx0);
+            l.val[0] = p.inj_scale * __ldg(p.inj_val + static_cast<long long>(p.wav_per_tx ? tx_idx : 0) * p.nt + step);
+        }
+    }
+}
+
+// Applies a gathered list to `buf` (thread 0 only). Entries beyond the staged capacity are read
+// from global memory directly (same order).
+template <int MODE>
+__device__ __forceinline__ void apply_injections(const InjList &l, float *buf, const StepParams &p, const int *sorted,
+                                                 int n_sorted, int s, int tx_idx, int step, int2 range, int rx0,
+                                                 int rz0, int stride)
+{
+    const int m = min(l.n, kMaxInj);
+    for (int e = 0; e < m; ++e) buf[l.idx[e]] += l.val[e];
+    if (MODE == kAdjoint) {
+        for (int e = kMaxInj; e < l.n; ++e) {
+            const int r = __ldg(sorted + tx_idx * n_sorted + range.x + e);
+            const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
+            buf[((node >> 16) - rz0) * stride + ((node & 0xffff) - rx0)] +=
+                __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + step) * p.n_rx + r);
+        }
+    }
+}
+
+// Laplacian (difference form) of a 4 (x) x 4 (z) block of a shared-memory field with row stride
+// SX whose first cell is at (cx, cz); the halo covers cx - 4 .. cx + 7 and cz - R .. cz + 3 + R.
+//   lap = sum_k c_k ((x_{+k} + x_{-k}) + (z_{+k} + z_{-k}) - 4u)
+// is exactly zero on a constant field whatever the rounding of the weights. The four x-lanes
+// are processed as two packed FP32 pairs (f32x2 instructions, IEEE rounding and order kept).
+template <int R, int SX>
+__device__ __forceinline__ void lap_block(const float *src, int cx, int cz, const float *c, float4 (&lap)[4],
+                                          float4 (&ctr)[4])
+{
+    float4 col[4 + 2 * R];
+#pragma unroll
+    for (int i = 0; i < 4 + 2 * R; ++i) col[i] = ld4s(src + (cz - R + i) * SX + cx);
+    const float2 m4 = make_float2(-4.0f, -4.0f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 lft = ld4s(src + (cz + j) * SX + cx - 4);
+        const float4 rgt = ld4s(src + (cz + j) * SX + cx + 4);
+        const float4 cc = col[R + j];
+        ctr[j] = cc;
+        const float w[12] = {lft.x, lft.y, lft.z, lft.w, cc.x, cc.y, cc.z, cc.w, rgt.x, rgt.y, rgt.z, rgt.w};
+        float2 l[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 u = make_float2(w[4 + 2 * h], w[5 + 2 * h]);
+            const float2 nu4 = __fmul2_rn(m4, u);
+            float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int kk = 1; kk <= R; ++kk) {
+                const float2 xs = (kk & 1)
+                    ? make_float2(w[4 + 2 * h - kk] + w[4 + 2 * h + kk], w[5 + 2 * h - kk] + w[5 + 2 * h + kk])
+                    : __fadd2_rn(make_float2(w[4 + 2 * h - kk], w[5 + 2 * h - kk]),
+                                 make_float2(w[4 + 2 * h + kk], w[5 + 2 * h + kk]));
+                const float4 &cm = col[R + j - kk], &cp = col[R + j + kk];
+                const float2 zs = h == 0 ? __fadd2_rn(make_float2(cm.x, cm.y), make_float2(cp.x, cp.y))
+                                         : __fadd2_rn(make_float2(cm.z, cm.w), make_float2(cp.z, cp.w));
+                acc = __ffma2_rn(make_float2(c[kk], c[kk]), __fadd2_rn(__fadd2_rn(xs, zs), nu4), acc);
+            }
+            l[h] = acc;
+        }
+        lap[j] = make_float4(l[0].x, l[0].y, l[1].x, l[1].y);
+    }
+}
+
+// Eq. 2 for four cells of a row: 2u - p + (a - 2) u + (b + 1) p + kappa' lap. The small damping
+// terms (a - 2, b + 1) come from a table over the layer depths (FP64 on the host, rounded once);
+// trow is the table row of this z, xd the x depths of the four lanes.
+__device__ __forceinline__ float4 eq2_row(float4 u, float4 pv, float4 kp, float4 lap, bool interior,
+                                          const float2 *trow, const int (&xd)[4])
+{
+    const float2 two2 = make_float2(2.0f, 2.0f);
+    float2 b0 = __ffma2_rn(two2, make_float2(u.x, u.y), make_float2(-pv.x, -pv.y));
+    float2 b1 = __ffma2_rn(two2, make_float2(u.z, u.w), make_float2(-pv.z, -pv.w));
+    if (!interior) {
+        const float2 t0 = __ldg(trow + xd[0]), t1 = __ldg(trow + xd[1]);
+        const float2 t2 = __ldg(trow + xd[2]), t3 = __ldg(trow + xd[3]);
+        b0 = __ffma2_rn(make_float2(t0.x, t1.x), make_float2(u.x, u.y),
+                        __ffma2_rn(make_float2(t0.y, t1.y), make_float2(pv.x, pv.y), b0));
+        b1 = __ffma2_rn(make_float2(t2.x, t3.x), make_float2(u.z, u.w),
+                        __ffma2_rn(make_float2(t2.y, t3.y), make_float2(pv.z, pv.w), b1));
+    }
+    const float2 n01 = __ffma2_rn(make_float2(kp.x, kp.y), make_float2(lap.x, lap.y), b0);
+    const float2 n23 = __ffma2_rn(make_float2(kp.z, kp.w), make_float2(lap.z, lap.w), b1);
+    return make_float4(n01.x, n01.y, n23.x, n23.y);
+}
+
+__device__ __forceinline__ float4 fma4(float4 a, float4 b, float4 c)
+{
+    const float2 lo = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y));
+    const float2 hi = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), make_float2(c.z, c.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Is the region [x0, x0 + w) x [z0, z0 + h) (clipped to the padded grid) free of damping?
+__device__ __forceinline__ bool region_interior(const StepParams &p, int x0, int z0, int w, int h)
+{
+    return x0 >= p.P && min(x0 + w, p.nxp) <= p.P + p.Nx && z0 >= p.P && min(z0 + h, p.nzp) <= p.P + p.Nz;
+}
+
+// Issues the TMA loads of one launch (thread 0) after the previous kernel in the stream is done.
+__device__ __forceinline__ bool wait_tile(uint64_t *bar, const StepParams &p, int tid)
+{
+    int fail = 0;
+    if (tid == 0) fail = !mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(fail)) {
+        if (tid == 0) raise_status(p.status, DUFWI_ERR_TIMEOUT);
+        mbar_wait_bounded(bar, 0);
+        return false;
+    }
+    // every thread takes its own (immediately successful) acquire of the completed phase
+    if (!mbar_try_wait_sleep(bar, 0) && !mbar_wait_bounded(bar, 0)) {
+        raise_status(p.status, DUFWI_ERR_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
 // Minimum resident CTAs of 128 threads per SM requested from the register allocator (the 64-row
 // tile variant asks for half as many CTAs of 256 threads). Build-time knob.
 #ifndef DUFWI_STEP_MIN_CTAS_128
 #define DUFWI_STEP_MIN_CTAS_128 5
 #endif
 
+// One time step, one 64 x TZ output tile of one shot per CTA. A single mbarrier collects the TMA
+// loads of the (64 + 8) x (TZ + 8) box of U^n and of the 64 x TZ tiles of U^{n-1} and kappa'
+// (and, in the adjoint, of Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay
+// resident per SM, so the loads of some overlap the arithmetic of others.
 template <int R, int MODE, int TZ>
 __global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta,
                                   (DUFWI_STEP_MIN_CTAS_128 * 128 + TileLayout<MODE, TZ>::kThreadsPerCta - 1) /
@@ -162,6 +315,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     using TL = TileLayout<MODE, TZ>;
     extern __shared__ __align__(128) float smem[];
     __shared__ alignas(8) uint64_t bar;
+    __shared__ InjList inj;
 
     const int tid = threadIdx.x;
     const int s = blockIdx.z;
@@ -197,121 +351,63 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 
     // Receivers of this transmit inside this tile: a host-built table gives the range of them
     // (indices into rx_sorted), so no CTA scans the whole receiver list.
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     int2 rx_range = make_int2(0, 0);
-    if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x);
-    int src_node = -1;
-    if (MODE != kAdjoint) src_node = __ldg(p.inj_node + tx_idx);
+    if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
+    gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
+                            tid, TL::kThreadsPerCta);
 
     const int lx = (tid & 15) * 4;
     const int lz = (tid >> 4) * 4;
     const int gx = x0 + lx;
-    const bool col_ok = gx < p.nxp;
-    const bool interior = (x0 >= p.P) && (min(x0 + kTileX, p.nxp) <= p.P + p.Nx) && (z0 >= p.P) &&
-                          (min(z0 + TZ, p.nzp) <= p.P + p.Nz);
+    const bool interior = region_interior(p, x0, z0, kTileX, TZ);
     int xd[4];
-    if (!interior) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
-    }
+    for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
 
-    // One thread polls the mbarrier; the others park on the CTA barrier and then take their own
-    // (immediately successful) acquire of the completed phase.
-    int fail = 0;
-    if (tid == 0) fail = !mbar_wait_bounded(&bar, 0);
-    if (__syncthreads_or(fail)) {
-        if (tid == 0) raise_status(p.status, DUFWI_ERR_TIMEOUT);
-        mbar_wait_bounded(&bar, 0);
-        return;
-    }
-    if (!mbar_try_wait_sleep(&bar, 0) && !mbar_wait_bounded(&bar, 0)) {
-        raise_status(p.status, DUFWI_ERR_TIMEOUT);
-        return;
-    }
+    if (!wait_tile(&bar, p, tid)) return;
 
-    // Column window: rows lz + kHalo - R .. lz + kHalo + 3 + R of the float4 at x = lx.
-    float4 col[4 + 2 * R];
-#pragma unroll
-    for (int i = 0; i < 4 + 2 * R; ++i) col[i] = ld4s(box + (lz + kHalo - R + i) * kBoxX + kHalo + lx);
-
-    // The four x-lanes of a thread are processed as two packed FP32 pairs (lanes 0-1 and 2-3)
-    // with the sm_100-family f32x2 instructions; every operation keeps the IEEE rounding and
-    // order of the scalar formulation.
-    const float2 two2 = make_float2(2.0f, 2.0f), m4 = make_float2(-4.0f, -4.0f);
+    float4 lap[4], ctr[4], nxt[4];
+    lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float *row = box + (lz + kHalo + j) * kBoxX + lx;
-        const float4 lft = ld4s(row);
-        const float4 rgt = ld4s(row + 8);
-        const float4 ctr = col[R + j];
-        const float w[12] = {lft.x, lft.y, lft.z, lft.w, ctr.x, ctr.y, ctr.z, ctr.w, rgt.x, rgt.y, rgt.z, rgt.w};
-        // Laplacian in difference form, sum_k c_k ((x_{+k} + x_{-k}) + (z_{+k} + z_{-k}) - 4u):
-        // exactly zero on a constant field whatever the rounding of the weights.
-        float2 lap[2];
+        const int lo = (lz + j) * kTileX + lx;
+        nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
+                         p.damp_tab + layer_depth(z0 + lz + j, p.P, p.Nz) * (p.P + 1), xd);
+    }
+    if (inj.n > 0) {   // block-uniform: stage, inject in list order, reload
+        __syncthreads();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float2 u = make_float2(w[4 + 2 * h], w[5 + 2 * h]);
-            const float2 nu4 = __fmul2_rn(m4, u);
-            float2 acc = make_float2(0.0f, 0.0f);
+        for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
+        __syncthreads();
+        if (tid == 0)
+            apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX);
+        __syncthreads();
 #pragma unroll
-            for (int kk = 1; kk <= R; ++kk) {
-                const float2 xs = (kk & 1)
-                    ? make_float2(w[4 + 2 * h - kk] + w[4 + 2 * h + kk], w[5 + 2 * h - kk] + w[5 + 2 * h + kk])
-                    : __fadd2_rn(make_float2(w[4 + 2 * h - kk], w[5 + 2 * h - kk]),
-                                 make_float2(w[4 + 2 * h + kk], w[5 + 2 * h + kk]));
-                const float4 &cm = col[R + j - kk], &cp = col[R + j + kk];
-                const float2 zs = h == 0 ? __fadd2_rn(make_float2(cm.x, cm.y), make_float2(cp.x, cp.y))
-                                         : __fadd2_rn(make_float2(cm.z, cm.w), make_float2(cp.z, cp.w));
-                const float2 t = __fadd2_rn(__fadd2_rn(xs, zs), nu4);
-                acc = __ffma2_rn(make_float2(p.c[kk], p.c[kk]), t, acc);
-            }
-            lap[h] = acc;
-        }
+        for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+    }
 
+    const bool col_ok = gx < p.nxp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
         const int gz = z0 + lz + j;
         if (!col_ok || gz >= p.nzp) continue;
-        const int lo = (lz + j) * kTileX + lx;
-        const float4 prev = ld4s(pv + lo);
-        const float4 kap = ld4s(kp + lo);
+        float4 nv = nxt[j], lv = lap[j];
+        if (gx + 4 > p.nxp) {   // lanes past the last column stay zero (row pitch padding)
+            if (gx + 1 >= p.nxp) { nv.y = 0.f; lv.y = 0.f; }
+            if (gx + 2 >= p.nxp) { nv.z = 0.f; lv.z = 0.f; }
+            nv.w = 0.f; lv.w = 0.f;
+        }
         const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
-
-        // U^{n+1} = 2u - p + (a - 2) u + (b + 1) p + kappa' L, with the small damping terms
-        // a - 2 = -q (2 + q)/(1 + q) and b + 1 = 2q/(1 + q), q = D dt, read from a table over
-        // the layer depths (computed in FP64 on the host, rounded once).
-        float2 base[2];
-        base[0] = __ffma2_rn(two2, make_float2(ctr.x, ctr.y), make_float2(-prev.x, -prev.y));
-        base[1] = __ffma2_rn(two2, make_float2(ctr.z, ctr.w), make_float2(-prev.z, -prev.w));
-        if (!interior) {
-            const float2 *trow = p.damp_tab + layer_depth(gz, p.P, p.Nz) * (p.P + 1);
-            const float2 t0 = __ldg(trow + xd[0]), t1 = __ldg(trow + xd[1]);
-            const float2 t2 = __ldg(trow + xd[2]), t3 = __ldg(trow + xd[3]);
-            base[0] = __ffma2_rn(make_float2(t0.x, t1.x), make_float2(ctr.x, ctr.y),
-                                 __ffma2_rn(make_float2(t0.y, t1.y), make_float2(prev.x, prev.y), base[0]));
-            base[1] = __ffma2_rn(make_float2(t2.x, t3.x), make_float2(ctr.z, ctr.w),
-                                 __ffma2_rn(make_float2(t2.y, t3.y), make_float2(prev.z, prev.w), base[1]));
-        }
-        const float2 n01 = __ffma2_rn(make_float2(kap.x, kap.y), lap[0], base[0]);
-        const float2 n23 = __ffma2_rn(make_float2(kap.z, kap.w), lap[1], base[1]);
-        float4 nxt = make_float4(n01.x, n01.y, n23.x, n23.y);
-        float4 lp = make_float4(lap[0].x, lap[0].y, lap[1].x, lap[1].y);
-        // Lanes past the last column stay zero (they are padding of the row pitch).
-        if (gx + 4 > p.nxp) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (gx + i >= p.nxp) { set_comp(nxt, i, 0.f); set_comp(lp, i, 0.f); }
-        }
-        st4(p.out + o, nxt);
-        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lp);
+        st4(p.out + o, nv);
+        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
         if (MODE == kAdjoint) {
-            const float4 hv = ld4s(hs + lo);
-            const float4 gv = ld4s(gg + lo);
-            const float2 g01 = __ffma2_rn(make_float2(nxt.x, nxt.y), make_float2(hv.x, hv.y), make_float2(gv.x, gv.y));
-            const float2 g23 = __ffma2_rn(make_float2(nxt.z, nxt.w), make_float2(hv.z, hv.w), make_float2(gv.z, gv.w));
-            st4(p.grad + o, make_float4(g01.x, g01.y, g23.x, g23.y));
+            const int lo = (lz + j) * kTileX + lx;
+            st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
         }
     }
 
-    // Receiver sampling of U^n from the box (each receiver lies in exactly one tile); placed
-    // after the arithmetic so the table load is long complete.
+    // Receiver sampling of U^n from the box (each receiver lies in exactly one tile).
     if (MODE == kFwdSample || MODE == kFwdSampleHist) {
         for (int e = tid; e < rx_range.y; e += TL::kThreadsPerCta) {
             const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
@@ -321,30 +417,208 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
                 box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
         }
     }
+}
 
-    // Point injections into the just-written cells of this tile (the CTA is their only writer,
-    // so after the barrier an atomic add is race-free and sees the stored value).
-    if (MODE == kAdjoint) {
-        if (rx_range.y == 0) return;
+// ---- two time steps per launch ----------------------------------------------------------------
+// Core tile 64 x 32 per CTA, 192 threads. Phase A computes U^{n+1} on the core plus a 4-cell
+// ring (72 x 40, 180 blocks of 4 x 4) from an 80 x 48 TMA box of U^n and the 72 x 40 boxes of
+// U^{n-1} and kappa'. Phase B computes U^{n+2} on the core (128 blocks) while the other two
+// warps write the core of U^{n+1} and record receivers. Neighbouring CTAs read both input
+// fields, so the outputs go to two other buffers (four rotating buffers per sweep). The
+// adjoint runs the same two steps on mu (mu^m, then mu^{m-1}) with imaging of both.
+constexpr int kPairZ = 32;
+constexpr int kPairThreads = 192;
+constexpr int kPairBoxX = kTileX + 4 * kHalo;    // 80
+constexpr int kPairBoxZ = kPairZ + 4 * kHalo;    // 48
+constexpr int kPairEX = kTileX + 2 * kHalo;      // 72
+constexpr int kPairEZ = kPairZ + 2 * kHalo;      // 40
+
+template <int MODE>
+struct PairLayout {
+    static constexpr int kBox = kPairBoxX * kPairBoxZ;
+    static constexpr int kE = kPairEX * kPairEZ;
+    static constexpr int kCore = kTileX * kPairZ;
+    // box | prev (E) | kappa (E) | U^{n+1} (E) [| hist A | hist B | sums (core)]
+    static constexpr int kLoadFloats = kBox + 2 * kE + (MODE == kAdjoint ? 3 * kCore : 0);
+    static constexpr uint32_t kLoadBytes = kLoadFloats * sizeof(float);
+    static constexpr int kFloats = kLoadFloats + kE;
+    static constexpr uint32_t kBytes = kFloats * sizeof(float);
+};
+
+// Minimum resident CTAs of the two-step kernel per SM requested from the register allocator.
+#ifndef DUFWI_STEP2_MIN_CTAS
+#define DUFWI_STEP2_MIN_CTAS 3
+#endif
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kPairThreads, DUFWI_STEP2_MIN_CTAS)
+step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
+{
+    using PL = PairLayout<MODE>;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ InjList inj[2];
+
+    const int tid = threadIdx.x;
+    const int s = blockIdx.z;
+    const int x0 = blockIdx.x * kTileX;
+    const int z0 = blockIdx.y * kPairZ;
+    const int tx_idx = s % p.n_tx;
+    const long long shot_off = static_cast<long long>(s) * p.slice;
+    float *box = smem;                       // U^n, origin (x0 - 8, z0 - 8)
+    float *pe = box + PL::kBox;              // U^{n-1} on E, origin (x0 - 4, z0 - 4)
+    float *ke = pe + PL::kE;                 // kappa' on E
+    float *ha = ke + PL::kE;                 // adjoint: Lap(U^{m-1}) on the core
+    float *hb = ha + PL::kCore;              // adjoint: Lap(U^{m-2}) on the core
+    float *gs = hb + PL::kCore;              // adjoint: running imaging sums on the core
+    float *n1 = smem + PL::kLoadFloats;      // U^{n+1} on E (computed)
+
+    if (tid == 0) {
+        prefetch_tensormap(&tm.cur_box);
+        prefetch_tensormap(&tm.out_tile);
+        mbar_init(&bar, 1);
+    }
+    __syncthreads();
+
+    grid_dependency_wait();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, PL::kLoadBytes);
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - 2 * kHalo, z0 - 2 * kHalo, s);
+        tma_load_3d(pe, &tm.out_tile, &bar, x0 - kHalo, z0 - kHalo, s);
+        tma_load_3d(ke, &tm.kap_tile, &bar, x0 - kHalo, z0 - kHalo, s / p.n_tx);
+        if (MODE == kAdjoint) {
+            tma_load_4d(ha, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            tma_load_4d(hb, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot2);
+            tma_load_3d(gs, &tm.grad_tile, &bar, x0, z0, s);
+        }
+    }
+    grid_dependents_launch();
+
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    const int n_tiles = gridDim.x * gridDim.y;
+    int2 rx_core = make_int2(0, 0), rx_ring = make_int2(0, 0);
+    if (MODE != kFwdHist) rx_core = __ldg(p.rx_tab + tx_idx * n_tiles + tile);
+    if (MODE == kAdjoint) rx_ring = __ldg(p.rxe_tab + tx_idx * n_tiles + tile);
+    // step A injections land anywhere on E, step B injections on the core
+    const int step_b = MODE == kAdjoint ? p.step - 1 : p.step + 1;
+    gather_injections<MODE>(inj[0], p, p.rxe_sorted, p.n_rxe, s, tx_idx, p.step, rx_ring, x0 - kHalo, z0 - kHalo,
+                            kPairEX, kPairEZ, kPairEX, tid, kPairThreads);
+    gather_injections<MODE>(inj[1], p, p.rx_sorted, p.n_rx, s, tx_idx, step_b, rx_core, x0, z0, kTileX, kPairZ,
+                            kTileX, tid, kPairThreads);
+
+    if (!wait_tile(&bar, p, tid)) return;
+
+    // ---- phase A: step n -> n+1 on E (18 x 10 blocks)
+    if (tid < 180) {
+        const int ex = (tid % 18) * 4, ez = (tid / 18) * 4;             // E-local block origin
+        const int gx = x0 - kHalo + ex;
+        const bool interior = region_interior(p, x0 - kHalo, z0 - kHalo, kPairEX, kPairEZ);
+        int xd[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
+        float4 lap[4], ctr[4];
+        lap_block<R, kPairBoxX>(box, ex + kHalo, ez + kHalo, p.c, lap, ctr);
+        const bool in_core = ex >= kHalo && ex < kHalo + kTileX && ez >= kHalo && ez < kHalo + kPairZ;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int lo = (ez + j) * kPairEX + ex;
+            const int gz = z0 - kHalo + ez + j;
+            const float4 v = eq2_row(ctr[j], ld4s(pe + lo), ld4s(ke + lo), lap[j], interior,
+                                     p.damp_tab + layer_depth(gz, p.P, p.Nz) * (p.P + 1), xd);
+            st4s(n1 + lo, v);
+            if ((MODE == kFwdSampleHist || MODE == kFwdHist) && in_core && gz < p.nzp && gx < p.nxp) {
+                float4 lv = lap[j];
+                if (gx + 4 > p.nxp) {
+                    if (gx + 1 >= p.nxp) lv.y = 0.f;
+                    if (gx + 2 >= p.nxp) lv.z = 0.f;
+                    lv.w = 0.f;
+                }
+                st4(p.hist + shot_off + static_cast<long long>(gz) * p.pitch + gx, lv);
+            }
+        }
+    }
+    __syncthreads();
+    if (inj[0].n > 0) {
+        if (tid == 0)
+            apply_injections<MODE>(inj[0], n1, p, p.rxe_sorted, p.n_rxe, s, tx_idx, p.step, rx_ring, x0 - kHalo,
+                                   z0 - kHalo, kPairEX);
         __syncthreads();
-        for (int e = tid; e < rx_range.y; e += TL::kThreadsPerCta) {
-            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
-            const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
-            const int zn = node >> 16, xn = node & 0xffff;
-            const long long o = shot_off + static_cast<long long>(zn) * p.pitch + xn;
-            const float v = __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r);
-            atomicAdd(p.out + o, v);
-            atomicAdd(p.grad + o, v * hs[(zn - z0) * kTileX + (xn - x0)]);
+    }
+
+    // ---- phase B: step n+1 -> n+2 on the core (16 x 8 blocks); warps 4-5 write U^{n+1}
+    float4 nxt[4], lap[4];
+    const int lx = (tid & 15) * 4, lz = ((tid >> 4) & 7) * 4;
+    const int gx = x0 + lx;
+    if (tid < 128) {
+        const bool interior = region_interior(p, x0, z0, kTileX, kPairZ);
+        int xd[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
+        float4 ctr[4];
+        lap_block<R, kPairEX>(n1, lx + kHalo, lz + kHalo, p.c, lap, ctr);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 prev = ld4s(box + (lz + j + 2 * kHalo) * kPairBoxX + lx + 2 * kHalo);
+            const float4 kap = ld4s(ke + (lz + j + kHalo) * kPairEX + lx + kHalo);
+            nxt[j] = eq2_row(ctr[j], prev, kap, lap[j], interior,
+                             p.damp_tab + layer_depth(z0 + lz + j, p.P, p.Nz) * (p.P + 1), xd);
         }
     } else {
-        const bool has_src = (src_node >> 16) >= z0 && (src_node >> 16) < z0 + TZ && (src_node & 0xffff) >= x0 &&
-                             (src_node & 0xffff) < x0 + kTileX;
-        if (!has_src) return;
+        // core of U^{n+1} (mu^m) to global, and receivers of U^n and U^{n+1}
+        const int t = tid - 128;
+        for (int k = t; k < kTileX / 4 * kPairZ; k += kPairThreads - 128) {
+            const int cx = (k & 15) * 4, cz = k >> 4;
+            const int gz = z0 + cz, gxx = x0 + cx;
+            if (gz < p.nzp && gxx < p.nxp)
+                st4(p.out + shot_off + static_cast<long long>(gz) * p.pitch + gxx,
+                    ld4s(n1 + (cz + kHalo) * kPairEX + cx + kHalo));
+        }
+        if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+            for (int e = t; e < rx_core.y; e += kPairThreads - 128) {
+                const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_core.x + e);
+                const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
+                const int zn = node >> 16, xn = node & 0xffff;
+                float *cd = p.cd + (static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r;
+                cd[0] = box[(zn - z0 + 2 * kHalo) * kPairBoxX + (xn - x0 + 2 * kHalo)];
+                if (p.step + 1 < p.nt) cd[p.n_rx] = n1[(zn - z0 + kHalo) * kPairEX + (xn - x0 + kHalo)];
+            }
+        }
+    }
+    if (inj[1].n > 0) {   // block-uniform: stage the core of U^{n+2} in the (free) U^{n-1} area
         __syncthreads();
-        if (tid == 0) {
-            const long long o = shot_off + static_cast<long long>(src_node >> 16) * p.pitch + (src_node & 0xffff);
-            const float wv = __ldg(p.inj_val + static_cast<long long>(p.wav_per_tx ? tx_idx : 0) * p.nt + p.step);
-            atomicAdd(p.out + o, p.inj_scale * wv);
+        if (tid < 128) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) st4s(pe + (lz + j) * kTileX + lx, nxt[j]);
+        }
+        __syncthreads();
+        if (tid == 0)
+            apply_injections<MODE>(inj[1], pe, p, p.rx_sorted, p.n_rx, s, tx_idx, step_b, rx_core, x0, z0, kTileX);
+        __syncthreads();
+        if (tid < 128) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pe + (lz + j) * kTileX + lx);
+        }
+    }
+    if (tid >= 128) return;
+
+    const bool col_ok = gx < p.nxp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gz = z0 + lz + j;
+        if (!col_ok || gz >= p.nzp) continue;
+        float4 nv = nxt[j], lv = lap[j];
+        if (gx + 4 > p.nxp) {
+            if (gx + 1 >= p.nxp) { nv.y = 0.f; lv.y = 0.f; }
+            if (gx + 2 >= p.nxp) { nv.z = 0.f; lv.z = 0.f; }
+            nv.w = 0.f; lv.w = 0.f;
+        }
+        const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+        st4(p.out2 + o, nv);
+        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist2 + o, lv);
+        if (MODE == kAdjoint) {
+            const int lo = (lz + j) * kTileX + lx;
+            const float4 mu_m = ld4s(n1 + (lz + j + kHalo) * kPairEX + lx + kHalo);
+            st4(p.grad + o, fma4(nv, ld4s(hb + lo), fma4(mu_m, ld4s(ha + lo), ld4s(gs + lo))));
         }
     }
 }
@@ -594,6 +868,56 @@ static cudaError_t launch_step_r(int mode, const StepMaps &tm, const StepParams 
     case kFwdSampleHist: return launch_step_rm<R, kFwdSampleHist>(tm, p, st);
     case kFwdHist: return launch_step_rm<R, kFwdHist>(tm, p, st);
     case kAdjoint: return launch_step_rm<R, kAdjoint>(tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R, int MODE>
+static cudaError_t launch_step2_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    using PL = PairLayout<MODE>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step2_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             PL::kBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(step2_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kPairZ - 1) / kPairZ, p.n_maps * p.n_tx);
+    cfg.blockDim = dim3(kPairThreads);
+    cfg.dynamicSmemBytes = PL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step2_kernel<R, MODE>, tm, p);
+}
+
+template <int R>
+static cudaError_t launch_step2_r(int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    switch (mode) {
+    case kFwdSample: return launch_step2_rm<R, kFwdSample>(tm, p, st);
+    case kFwdSampleHist: return launch_step2_rm<R, kFwdSampleHist>(tm, p, st);
+    case kFwdHist: return launch_step2_rm<R, kFwdHist>(tm, p, st);
+    case kAdjoint: return launch_step2_rm<R, kAdjoint>(tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step2(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    switch (radius) {
+    case 1: return launch_step2_r<1>(mode, tm, p, st);
+    case 2: return launch_step2_r<2>(mode, tm, p, st);
+    case 3: return launch_step2_r<3>(mode, tm, p, st);
+    case 4: return launch_step2_r<4>(mode, tm, p, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -26,6 +26,7 @@ OK, ERR_INVALID_ARG, ERR_CFL, ERR_GEOMETRY, ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE = 5, 6, 7, 8
 SNAPSHOT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 OPT_TILE_Z = 1
+OPT_TWO_STEP = 2
 
 
 class DufwiError(RuntimeError):

@@ -275,3 +275,25 @@ def test_simulate_full_shot_set_sampled_transmits(d):
     for k in (0, 11):
         ref = _oracle_traces(wl, wl.sos_true[0], tx=[k])[0]
         assert rel_l2(cd[0, k], ref) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("ckpt", [0, 9])
+def test_two_step_kernel_is_bit_identical_to_one_step(d, ckpt):
+    """Fusing pairs of time steps into one launch changes no result bit: the grown-tile step
+    repeats the one-step arithmetic, and injections are applied in list order either way."""
+    wl = inputs.make_workload("linear_disk", seed=12, nx=90, nz=77, nt=257, n_elem=20, n_tx=3, n_maps=2)
+    M_obs = _observed(wl)
+    out = []
+    for two in (0, 1):
+        d.set_option(d.OPT_TWO_STEP, two)
+        try:
+            pb = _dufwi_problem(d, wl, ckpt_interval=ckpt)
+            geom = d.Geometry.from_workload(wl)
+            cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                            check=True).cpu().numpy()
+            J, g, cds = _gpu_grad(d, wl, M_obs, ckpt_interval=ckpt)
+            out.append((cd, J, g, cds))
+        finally:
+            d.set_option(d.OPT_TWO_STEP, 0)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)

@@ -129,6 +129,28 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
                           float *cd_sim, void *workspace, size_t workspace_bytes,
                           void *stream /* cudaStream_t */);
 
+/* Forward model that keeps what the adjoint needs: the same channel data as dufwi_simulate, plus
+ * the snapshots (every ckpt_interval steps) or the whole history, stored in `workspace`. The
+ * workspace must hold dufwi_workspace_size bytes. Pair it with dufwi_backward, which turns any
+ * cotangent of the channel data into a gradient with respect to the SoS map. Those two calls
+ * are the forward and the backward of a differentiable simulator (Eq. 3 as a map C -> M). */
+int dufwi_forward_save(const dufwi_problem *pb, const float *sos, const float *density,
+                       const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                       int32_t n_maps, float *cd, void *workspace, size_t workspace_bytes,
+                       void *stream /* cudaStream_t */);
+
+/* Vector-Jacobian product of the forward model: grad[b] = (dM[b]/dC[b])^T cd_grad[b] for each map.
+ *   cd_grad  [n_maps][n_tx][nt][n_rx] float, device: the cotangent dL/dM
+ *   grad     [n_maps][nz][nx] float, device, output
+ * The call runs the discrete adjoint of Eq. 2, recomputing checkpoint segments from the
+ * snapshots. It needs the workspace of a preceding dufwi_forward_save with the same problem,
+ * maps, pulse and geometry, not overwritten in between. With cd_grad = 2 (M - M_obs) it gives
+ * the gradient of dufwi_misfit_gradient, bit for bit. */
+int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *density,
+                   const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                   int32_t n_maps, const float *cd_grad, float *grad, void *workspace,
+                   size_t workspace_bytes, void *stream /* cudaStream_t */);
+
 /* Forward model for callers that cannot allocate device memory. The paper has no counterpart:
  * this serves hosts that must not call cudaMalloc while running, such as a fixed-latency
  * acquisition loop (a device allocation can synchronise the device) or an application that hands

@@ -1,0 +1,49 @@
+"""Differentiable forward model: the simulator behind ``torch.autograd.Function``.
+
+The forward pass is ``dufwi_forward_save``: the channel data M = F(C) of every shot (Eqs. 2-4),
+with the checkpoint snapshots (or the whole history) kept in a workspace. The backward pass is
+``dufwi_backward``, the hand-written discrete adjoint: for any upstream cotangent dL/dM it
+returns dL/dC = (dM/dC)^T dL/dM. The same kernels compute the misfit gradient of Eq. 6; this
+wrapper exposes them to any loss built on the channel data. An example is the block-wise
+DUFWI training of Sec. III-B, where g_k feeds N_theta_k.
+
+Gradients flow to the SoS maps only. The pulse, the density and the geometry are constants.
+Calling ``backward`` twice needs ``retain_graph=True``; the saved workspace is reused.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import dufwi
+
+
+class _Simulate(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, sos, wavelet, problem, geom):
+        cd, ws = dufwi.forward_save(problem, sos.detach().contiguous(), wavelet.detach().contiguous(), geom)
+        ctx.save_for_backward(sos, wavelet)
+        ctx.workspace = ws
+        ctx.problem = problem
+        ctx.geom = geom
+        return cd
+
+    @staticmethod
+    def backward(ctx, cd_grad):
+        sos, wavelet = ctx.saved_tensors
+        grad = None
+        if ctx.needs_input_grad[0]:
+            grad = dufwi.backward(ctx.problem, sos.detach().contiguous(), wavelet.detach().contiguous(), ctx.geom,
+                                  cd_grad.contiguous(), ctx.workspace)
+        return grad, None, None, None
+
+
+def simulate(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: dufwi.Geometry) -> torch.Tensor:
+    """Channel data ``[n_maps][n_tx][nt][n_rx]``, differentiable with respect to ``sos``."""
+    return _Simulate.apply(sos, wavelet, problem, geom)
+
+
+def misfit(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: dufwi.Geometry,
+           cd_obs: torch.Tensor) -> torch.Tensor:
+    """Per-map data misfit J = sum (M - M_obs)^2 (Eq. 5 with lambda = 0), differentiable in sos."""
+    r = simulate(problem, sos, wavelet, geom) - cd_obs
+    return (r * r).sum(dim=(1, 2, 3), dtype=torch.float64)

@@ -700,54 +700,46 @@ int dufwi_simulate(const dufwi_problem *pb, const float *sos, const float *densi
     return forward_sweep(c, rg, wavelet, cd, false, false);
 }
 
-int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
-                          const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_obs,
-                          double *misfit, float *grad, float *cd_sim, void *workspace, size_t workspace_bytes,
-                          void *stream)
+}  // extern "C"
+
+namespace dufwi {
+namespace {
+
+Ring field_ring(Ctx &c, bool adjoint)
 {
-    Ctx c;
-    c.pb = pb;
-    int rc = make_layout(pb, shots, n_maps, true, &c.L);
-    if (rc) return rc;
-    if ((!cd_obs && c.L.n_rx > 0) || !misfit || !grad) return DUFWI_ERR_INVALID_ARG;
-    rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, true);
-    if (rc) return rc;
+    Ring r;
+    for (int i = 0; i < 4; ++i) r.buf[i] = c.at<float>(adjoint ? c.L.o_m[i] : c.L.o_f[i]);
+    r.map = adjoint ? c.mmap : c.fmap;
+    r.cur = 0;
+    r.prv = 1;
+    return r;
+}
+
+// First half of a gradient: forward sweep recording the traces into the workspace, and either
+// the whole history or the snapshots.
+int gradient_forward(Ctx &c, const float *wavelet)
+{
+    Ring fr = field_ring(c, false);
+    const bool store_all = (c.L.n_seg == 1);
+    return forward_sweep(c, fr, wavelet, c.at<float>(c.L.o_cd), store_all, !store_all);
+}
+
+// Second half: reverse sweep driven by the scaled adjoint source already in the workspace
+// (kappa'_r times dJ/dM), recomputing each checkpoint segment, then the fold into grad.
+int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad)
+{
     const Layout &L = c.L;
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
     const bool store_all = (L.n_seg == 1);
-    float *cd = c.at<float>(L.o_cd);
     float *hist = c.at<float>(L.o_hist);
     float *g_shot = c.at<float>(L.o_grad);
-    Ring fr, ar;
-    for (int i = 0; i < 4; ++i) {
-        fr.buf[i] = c.at<float>(L.o_f[i]);
-        ar.buf[i] = c.at<float>(L.o_m[i]);
-    }
-    fr.map = c.fmap;
-    ar.map = c.mmap;
-
-    // 1. forward sweep: traces, and either the whole history or the snapshots
-    rc = forward_sweep(c, fr, wavelet, cd, store_all, !store_all);
-    if (rc) return rc;
-    if (cd_sim && L.n_rx > 0)
-        CK(cudaMemcpyAsync(cd_sim, cd, (size_t)L.S * L.nt * L.n_rx * sizeof(float), cudaMemcpyDeviceToDevice, c.st));
-
-    // 2. residual, misfit and adjoint source
-    float *asrc = c.at<float>(L.o_asrc);
-    double *part = c.at<double>(L.o_part);
+    const float *asrc = c.at<float>(L.o_asrc);
+    Ring fr = field_ring(c, false), ar = field_ring(c, true);
     long long nl = 0;
-    int e0 = g_prof.mark(c.st);
-    CKL(launch_residual(cd, cd_obs, c.at<float>(L.o_kap), c.at<int>(L.o_rx), asrc, part, c.status(), L.S, L.n_tx,
-                        L.n_rx, L.nt, L.slice, L.pitch, c.st));
-    CKL(launch_misfit_sum(part, misfit, L.n_maps, L.n_tx, c.st));
-    g_prof.span(3, e0, g_prof.mark(c.st), nl);
-
-    // 3. reverse sweep, segment by segment
+    int e0 = -1, rc = DUFWI_OK;
     for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(ar.buf[i], 0, field, c.st));
-    ar.cur = 0;
-    ar.prv = 1;
     CK(cudaMemsetAsync(g_shot, 0, field, c.st));
-    const int dtype = pb->snapshot_dtype;
+    const int dtype = c.pb->snapshot_dtype;
     for (int sg = L.n_seg - 1; sg >= 0; --sg) {
         const int t0 = store_all ? 0 : sg * L.K;
         const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
@@ -778,7 +770,7 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
         if (rc) return rc;
         g_prof.span(2, e0, g_prof.mark(c.st), nl);
     }
-    // 4. (2/C) scaling, fold of the absorbing layer, FP64 reduction over transmits
+    // (2/C) scaling, fold of the absorbing layer, FP64 reduction over transmits
     nl = 0;
     e0 = g_prof.mark(c.st);
     CKL(launch_fold(g_shot, sos, grad, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
@@ -786,6 +778,88 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
     ++nl;
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
     return DUFWI_OK;
+}
+
+int gradient_setup(Ctx &c, const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                   const float *wavelet, const dufwi_shots *shots, int32_t n_maps, void *workspace,
+                   size_t workspace_bytes, void *stream)
+{
+    c.pb = pb;
+    int rc = make_layout(pb, shots, n_maps, true, &c.L);
+    if (rc) return rc;
+    return common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, true);
+}
+
+}  // namespace
+}  // namespace dufwi
+
+extern "C" {
+
+int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                          const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_obs,
+                          double *misfit, float *grad, float *cd_sim, void *workspace, size_t workspace_bytes,
+                          void *stream)
+{
+    Ctx c;
+    Layout chk;
+    int rc = make_layout(pb, shots, n_maps, true, &chk);
+    if (rc) return rc;
+    if ((!cd_obs && chk.n_rx > 0) || !misfit || !grad) return DUFWI_ERR_INVALID_ARG;
+    rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
+    if (rc) return rc;
+    const Layout &L = c.L;
+    rc = gradient_forward(c, wavelet);
+    if (rc) return rc;
+    float *cd = c.at<float>(L.o_cd);
+    if (cd_sim && L.n_rx > 0)
+        CK(cudaMemcpyAsync(cd_sim, cd, (size_t)L.S * L.nt * L.n_rx * sizeof(float), cudaMemcpyDeviceToDevice, c.st));
+    // residual, misfit and adjoint source
+    long long nl = 0;
+    const int e0 = g_prof.mark(c.st);
+    CKL(launch_residual(cd, cd_obs, c.at<float>(L.o_kap), c.at<int>(L.o_rx), c.at<float>(L.o_asrc),
+                        c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
+    CKL(launch_misfit_sum(c.at<double>(L.o_part), misfit, L.n_maps, L.n_tx, c.st));
+    g_prof.span(3, e0, g_prof.mark(c.st), nl);
+    return gradient_reverse(c, sos, wavelet, grad);
+}
+
+int dufwi_forward_save(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                       const float *wavelet, const dufwi_shots *shots, int32_t n_maps, float *cd, void *workspace,
+                       size_t workspace_bytes, void *stream)
+{
+    Ctx c;
+    Layout chk;
+    int rc = make_layout(pb, shots, n_maps, true, &chk);
+    if (rc) return rc;
+    if (!cd && chk.n_rx > 0) return DUFWI_ERR_INVALID_ARG;
+    rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
+    if (rc) return rc;
+    rc = gradient_forward(c, wavelet);
+    if (rc) return rc;
+    if (c.L.n_rx > 0)
+        CK(cudaMemcpyAsync(cd, c.at<float>(c.L.o_cd), (size_t)c.L.S * c.L.nt * c.L.n_rx * sizeof(float),
+                           cudaMemcpyDeviceToDevice, c.st));
+    return DUFWI_OK;
+}
+
+int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                   const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_grad, float *grad,
+                   void *workspace, size_t workspace_bytes, void *stream)
+{
+    Ctx c;
+    Layout chk;
+    int rc = make_layout(pb, shots, n_maps, true, &chk);
+    if (rc) return rc;
+    if ((!cd_grad && chk.n_rx > 0) || !grad) return DUFWI_ERR_INVALID_ARG;
+    rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
+    if (rc) return rc;
+    const Layout &L = c.L;
+    long long nl = 0;
+    const int e0 = g_prof.mark(c.st);
+    CKL(launch_cotangent_source(cd_grad, c.at<float>(L.o_kap), c.at<int>(L.o_rx), c.at<float>(L.o_asrc), c.status(),
+                                L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
+    g_prof.span(3, e0, g_prof.mark(c.st), nl);
+    return gradient_reverse(c, sos, wavelet, grad);
 }
 
 }  // extern "C"

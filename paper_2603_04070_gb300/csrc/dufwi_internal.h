@@ -88,6 +88,9 @@ cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const floa
                             const int *rx_node, float *asrc, double *partial, int *status,
                             int S, int n_tx, int n_rx, int nt, long long slice, int pitch,
                             cudaStream_t st);
+cudaError_t launch_cotangent_source(const float *cd_grad, const float *kap, const int *rx_node, float *asrc,
+                                   int *status, int S, int n_tx, int n_rx, int nt, long long slice, int pitch,
+                                   cudaStream_t st);
 cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps, int n_tx,
                               cudaStream_t st);
 cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *fx, int n_maps, int n_tx,

@@ -702,6 +702,24 @@ __global__ void residual_kernel(const float *cd_sim, const float *cd_obs, const 
     if (threadIdx.x == 0) partial[s] = t;
 }
 
+// Adjoint source of a general cotangent v = dL/dM: kappa'_r * v (no misfit).
+__global__ void cotangent_source_kernel(const float *cd_grad, const float *kap, const int *rx_node, float *asrc,
+                                        int *status, int n_tx, int n_rx, int nt, long long slice, int pitch)
+{
+    const int s = blockIdx.y;
+    const int tx_idx = s % n_tx, map = s / n_tx;
+    const long long base = static_cast<long long>(s) * nt * n_rx;
+    const long long n = static_cast<long long>(nt) * n_rx;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(i % n_rx);
+        const float v = cd_grad[base + i];
+        if (!isfinite(v)) raise_status(status, DUFWI_ERR_NONFINITE);
+        const int node = rx_node[tx_idx * n_rx + r];
+        asrc[base + i] = kap[map * slice + static_cast<long long>(node >> 16) * pitch + (node & 0xffff)] * v;
+    }
+}
+
 __global__ void misfit_sum_kernel(const double *partial, double *misfit, int n_maps, int n_tx)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -957,6 +975,17 @@ cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const floa
 {
     residual_kernel<<<S, 512, 0, st>>>(cd_sim, cd_obs, kap, rx_node, asrc, partial, status, n_tx, n_rx, nt, slice,
                                        pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cotangent_source(const float *cd_grad, const float *kap, const int *rx_node, float *asrc,
+                                   int *status, int S, int n_tx, int n_rx, int nt, long long slice, int pitch,
+                                   cudaStream_t st)
+{
+    if (n_rx == 0) return cudaSuccess;
+    const long long n = static_cast<long long>(nt) * n_rx;
+    dim3 grid(static_cast<unsigned>(std::min<long long>((n + 255) / 256, 64)), S);
+    cotangent_source_kernel<<<grid, 256, 0, st>>>(cd_grad, kap, rx_node, asrc, status, n_tx, n_rx, nt, slice, pitch);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,8 @@ def _load():
     lib.dufwi_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.dufwi_launch_count.restype = ctypes.c_int64
     lib.dufwi_simulate_noalloc.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp]
+    lib.dufwi_forward_save.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
+    lib.dufwi_backward.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, sz, vp]
     lib.dufwi_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
     lib.dufwi_get_option.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     return lib
@@ -289,6 +291,60 @@ def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, 
     if return_cd:
         return misfit, grad, cd_sim
     return misfit, grad
+
+
+def _common_inputs(problem, sos, wavelet, geom, density):
+    n_maps = sos.shape[0]
+    _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
+    wshape = (geom.n_tx, problem.nt) if geom.wavelet_per_tx else (problem.nt,)
+    _dev_tensor(wavelet, "wavelet", torch.float32, wshape)
+    if density is not None:
+        _dev_tensor(density, "density", torch.float32, sos.shape)
+    return n_maps, (n_maps, geom.n_tx, problem.nt, geom.n_rx)
+
+
+def forward_save(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, *,
+                 workspace: torch.Tensor | None = None, density: torch.Tensor | None = None,
+                 cd: torch.Tensor | None = None, stream=None):
+    """Channel data plus the saved snapshots/history in ``workspace`` (``dufwi_forward_save``).
+
+    Returns ``(cd, workspace)``; pass the same workspace to ``backward``."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, density)
+    if cd is None:
+        cd = torch.empty(cshape, dtype=torch.float32, device=sos.device)
+    _dev_tensor(cd, "cd", torch.float32, cshape)
+    workspace = _workspace(problem, geom, n_maps, True, workspace, sos.device)
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_forward_save(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+                                 ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd.data_ptr(),
+                                 workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "dufwi_forward_save")
+    return cd, workspace
+
+
+def backward(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, cd_grad: torch.Tensor,
+             workspace: torch.Tensor, *, density: torch.Tensor | None = None, grad: torch.Tensor | None = None,
+             stream=None, check: bool = False) -> torch.Tensor:
+    """(dM/dC)^T cd_grad for every map (``dufwi_backward``), after ``forward_save`` on ``workspace``."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, density)
+    _dev_tensor(cd_grad, "cd_grad", torch.float32, cshape)
+    if grad is None:
+        grad = torch.empty_like(sos)
+    _dev_tensor(grad, "grad", torch.float32, sos.shape)
+    need = workspace_size(problem, geom, n_maps, True)
+    if workspace.numel() * workspace.element_size() < need:
+        raise DufwiError(ERR_WORKSPACE, "backward workspace")
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_backward(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+                             ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd_grad.data_ptr(),
+                             grad.data_ptr(), workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                             _stream(stream))
+    _check(rc, "dufwi_backward")
+    if check:
+        _check(workspace_status(workspace, stream), "dufwi_backward (device)")
+    return grad
 
 
 def workspace_status(workspace: torch.Tensor, stream=None) -> int:

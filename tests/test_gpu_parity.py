@@ -297,3 +297,38 @@ def test_two_step_kernel_is_bit_identical_to_one_step(d, ckpt):
             d.set_option(d.OPT_TWO_STEP, 0)
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+def test_autograd_matches_misfit_gradient_bit_for_bit(d):
+    """loss = sum (M - M_obs)^2 through the autograd wrapper gives the misfit gradient exactly:
+    the cotangent 2 (M - M_obs) enters the same adjoint kernels."""
+    from paper_2603_04070_gb300 import autograd
+    wl = inputs.make_workload("linear_disk", seed=14, nx=70, nz=62, nt=300, n_elem=18, n_tx=2, n_maps=2)
+    M_obs = torch.from_numpy(_observed(wl)).cuda()
+    pb = _dufwi_problem(d, wl, ckpt_interval=40)
+    geom = d.Geometry.from_workload(wl)
+    w = torch.from_numpy(wl.wavelet).cuda()
+    sos = torch.from_numpy(wl.sos_start).cuda().requires_grad_(True)
+    cd = autograd.simulate(pb, sos, w, geom)
+    loss = ((cd - M_obs) ** 2).sum()
+    loss.backward()
+    J, g = d.misfit_gradient(pb, sos.detach(), w, geom, M_obs)
+    assert torch.equal(sos.grad, g)
+    assert abs(float(loss.detach()) - float(J.sum())) <= 1e-5 * float(J.sum())
+
+
+def test_autograd_vjp_matches_oracle_for_random_cotangent(d):
+    """A random linear functional of the traces: (dM/dC)^T q against the oracle, which computes
+    the same product as the misfit gradient with M_obs = M_sim - q/2."""
+    from paper_2603_04070_gb300 import autograd
+    wl = inputs.make_workload("linear_disk", seed=15, nx=64, nz=60, nt=350, n_elem=16, n_tx=2)
+    rng = np.random.default_rng(0)
+    q = rng.standard_normal((1, wl.n_tx, wl.nt, wl.n_rx)).astype(np.float32) * 1e-9
+    pb = _dufwi_problem(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_true).cuda().requires_grad_(True)
+    cd = autograd.simulate(pb, sos, torch.from_numpy(wl.wavelet).cuda(), geom)
+    (cd * torch.from_numpy(q).cuda()).sum().backward()
+    sim = _oracle_traces(wl, wl.sos_true[0])
+    J_ref, g_ref, _ = _oracle_grad(wl, wl.sos_true[0], sim - 0.5 * q[0].astype(np.float64))
+    assert rel_l2(sos.grad.cpu().numpy()[0], g_ref) <= GRAD_TOL

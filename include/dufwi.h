@@ -17,6 +17,11 @@
  *     the library copies into the workspace with stream-ordered copies. The library allocates
  *     no memory: callers query the workspace size first and pass a device buffer at least that
  *     large, aligned to 256 bytes.
+ *   - The library remembers, per workspace pointer, what it last copied there. A call on the
+ *     same workspace with unchanged problem and geometry skips those copies, and then issues
+ *     only kernels, memsets and device-to-device copies. Such a call can be captured in a CUDA
+ *     graph; run it once outside the capture first. Between calls, the workspace belongs to the
+ *     library: a caller that writes into it must not rely on this cache.
  *   - Every call is asynchronous on the given stream and returns a status code. Host-side
  *     argument checks are reported by the return value. Conditions only visible on the device
  *     are recorded in a status word inside the workspace and read with dufwi_workspace_status:
@@ -170,6 +175,31 @@ int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *densi
 int dufwi_simulate_noalloc(const dufwi_problem *pb, const float *sos, const float *density,
                            const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
                            int32_t n_maps, float *cd, void *stream /* cudaStream_t */);
+
+/* Maps of different sizes in one call (batching of uneven grids, Eq. 4 over many maps). The
+ * problem's nx, nz define an envelope. Map b has its own physical grid nz[b] x nx[b] (1 <= nx[b]
+ * <= nx, 1 <= nz[b] <= nz), with its own absorbing layer around it. Its SoS values fill the
+ * leading nz[b] x nx[b] block of its slab in sos[n_maps][nz][nx]; the rest of the slab is
+ * ignored. The gradient is written in the same layout, zero outside each map. Every element
+ * named by the transmit/receive tables must lie inside every map. All shots of all maps advance
+ * in the same launch per time step; tiles outside a map's padded grid exit at once. Workspace
+ * sizes are those of the envelope (dufwi_simulate_workspace_size / dufwi_workspace_size).
+ * The host arrays nx, nz hold n_maps entries each. */
+typedef struct {
+    const int32_t *nx;
+    const int32_t *nz;
+} dufwi_map_sizes;
+
+int dufwi_simulate_sized(const dufwi_problem *pb, const dufwi_map_sizes *sizes, const float *sos,
+                         const float *density, const dufwi_array *arr, const float *wavelet,
+                         const dufwi_shots *shots, int32_t n_maps, float *cd, void *workspace,
+                         size_t workspace_bytes, void *stream /* cudaStream_t */);
+
+int dufwi_misfit_gradient_sized(const dufwi_problem *pb, const dufwi_map_sizes *sizes, const float *sos,
+                                const float *density, const dufwi_array *arr, const float *wavelet,
+                                const dufwi_shots *shots, int32_t n_maps, const float *cd_obs,
+                                double *misfit, float *grad, float *cd_sim, void *workspace,
+                                size_t workspace_bytes, void *stream /* cudaStream_t */);
 
 /* Waits for the stream, then returns the device-side status word of the last call that used
  * this workspace (DUFWI_OK if none was raised). */

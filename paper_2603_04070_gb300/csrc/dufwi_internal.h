@@ -69,6 +69,7 @@ struct StepParams {
     int wav_per_tx;
     float inj_scale;         // forward: dt^2/dx^2
     int P, Nx, Nz;           // absorbing-layer thickness and physical grid
+    const int2 *map_dims;    // sized calls: [n_maps] (Nx, Nz) of each map; null for a uniform call
     const float2 *damp_tab;  // [P + 1][P + 1]: (a - 2, b + 1) at layer depths (dz, dx) in cells
     float c[5];              // central stencil weights, c[0] the centre weight of one axis
 };
@@ -81,7 +82,7 @@ constexpr int kPairTileZ = 32;   // core tile height of the two-step kernel (64 
 cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, int *status,
                                int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch,
                                double dt_over_dx, double d0, double dt, double c_max,
-                               cudaStream_t st);
+                               const int2 *map_dims, cudaStream_t st);
 cudaError_t launch_sample(const float *field, const int *rx_node, float *cd, long long slice,
                           int pitch, int S, int n_tx, int n_rx, int nt, int step, cudaStream_t st);
 cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const float *kap,
@@ -94,7 +95,7 @@ cudaError_t launch_cotangent_source(const float *cd_grad, const float *kap, cons
 cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps, int n_tx,
                               cudaStream_t st);
 cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *fx, int n_maps, int n_tx,
-                        int Nx, int Nz, int P, long long slice, int pitch, cudaStream_t st);
+                        int Nx, int Nz, int P, long long slice, int pitch, const int2 *map_dims, cudaStream_t st);
 cudaError_t launch_snap_absmax(const float *cur, const float *prev, unsigned *scale_bits, int S,
                                long long slice, int nxp, int nzp, int pitch, cudaStream_t st);
 cudaError_t launch_snap_store(const float *cur, const float *prev, void *snap_u, void *snap_d,

@@ -272,10 +272,34 @@ __device__ __forceinline__ float4 fma4(float4 a, float4 b, float4 c)
     return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-// Is the region [x0, x0 + w) x [z0, z0 + h) (clipped to the padded grid) free of damping?
-__device__ __forceinline__ bool region_interior(const StepParams &p, int x0, int z0, int w, int h)
+// Physical and padded size of the grid of one map (uniform calls: the problem's grid; sized
+// calls: the map's own grid, inside the envelope buffers).
+struct MapGrid {
+    int Nx, Nz, nxp, nzp;
+};
+
+__device__ __forceinline__ MapGrid map_grid(const StepParams &p, int map)
 {
-    return x0 >= p.P && min(x0 + w, p.nxp) <= p.P + p.Nx && z0 >= p.P && min(z0 + h, p.nzp) <= p.P + p.Nz;
+    MapGrid g;
+    if (p.map_dims) {
+        const int2 d = __ldg(p.map_dims + map);
+        g.Nx = d.x;
+        g.Nz = d.y;
+        g.nxp = d.x + 2 * p.P;
+        g.nzp = d.y + 2 * p.P;
+    } else {
+        g.Nx = p.Nx;
+        g.Nz = p.Nz;
+        g.nxp = p.nxp;
+        g.nzp = p.nzp;
+    }
+    return g;
+}
+
+// Is the region [x0, x0 + w) x [z0, z0 + h) (clipped to the padded grid) free of damping?
+__device__ __forceinline__ bool region_interior(const StepParams &p, const MapGrid &g, int x0, int z0, int w, int h)
+{
+    return x0 >= p.P && min(x0 + w, g.nxp) <= p.P + g.Nx && z0 >= p.P && min(z0 + h, g.nzp) <= p.P + g.Nz;
 }
 
 // Issues the TMA loads of one launch (thread 0) after the previous kernel in the stream is done.
@@ -328,6 +352,9 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     float *kp = pv + TL::kTile;
     float *hs = kp + TL::kTile;
     float *gg = hs + TL::kTile;
+    // sized calls: tiles outside this map's padded grid have nothing to do (their cells stay zero)
+    const MapGrid mg = map_grid(p, s / p.n_tx);
+    if (x0 >= mg.nxp || z0 >= mg.nzp) return;
 
     if (tid == 0) {
         prefetch_tensormap(&tm.cur_box);
@@ -360,10 +387,10 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     const int lx = (tid & 15) * 4;
     const int lz = (tid >> 4) * 4;
     const int gx = x0 + lx;
-    const bool interior = region_interior(p, x0, z0, kTileX, TZ);
+    const bool interior = region_interior(p, mg, x0, z0, kTileX, TZ);
     int xd[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
+    for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, mg.Nx);
 
     if (!wait_tile(&bar, p, tid)) return;
 
@@ -373,7 +400,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     for (int j = 0; j < 4; ++j) {
         const int lo = (lz + j) * kTileX + lx;
         nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
-                         p.damp_tab + layer_depth(z0 + lz + j, p.P, p.Nz) * (p.P + 1), xd);
+                         p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
     }
     if (inj.n > 0) {   // block-uniform: stage, inject in list order, reload
         __syncthreads();
@@ -387,15 +414,15 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
         for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
     }
 
-    const bool col_ok = gx < p.nxp;
+    const bool col_ok = gx < mg.nxp;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int gz = z0 + lz + j;
-        if (!col_ok || gz >= p.nzp) continue;
+        if (!col_ok || gz >= mg.nzp) continue;
         float4 nv = nxt[j], lv = lap[j];
-        if (gx + 4 > p.nxp) {   // lanes past the last column stay zero (row pitch padding)
-            if (gx + 1 >= p.nxp) { nv.y = 0.f; lv.y = 0.f; }
-            if (gx + 2 >= p.nxp) { nv.z = 0.f; lv.z = 0.f; }
+        if (gx + 4 > mg.nxp) {   // lanes past the last column stay zero (outside the map's grid)
+            if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
+            if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
             nv.w = 0.f; lv.w = 0.f;
         }
         const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
@@ -512,7 +539,7 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     if (tid < 180) {
         const int ex = (tid % 18) * 4, ez = (tid / 18) * 4;             // E-local block origin
         const int gx = x0 - kHalo + ex;
-        const bool interior = region_interior(p, x0 - kHalo, z0 - kHalo, kPairEX, kPairEZ);
+        const bool interior = region_interior(p, map_grid(p, 0), x0 - kHalo, z0 - kHalo, kPairEX, kPairEZ);
         int xd[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
@@ -550,7 +577,7 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     const int lx = (tid & 15) * 4, lz = ((tid >> 4) & 7) * 4;
     const int gx = x0 + lx;
     if (tid < 128) {
-        const bool interior = region_interior(p, x0, z0, kTileX, kPairZ);
+        const bool interior = region_interior(p, map_grid(p, 0), x0, z0, kTileX, kPairZ);
         int xd[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, p.Nx);
@@ -624,23 +651,26 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 }
 
 // kappa' = C^2 (dt/dx)^2 / (1 + D dt) on the padded grid; C extended by edge replication.
-__global__ void setup_kappa_kernel(const float *sos, const float *density, float *kap, int *status, int Nx,
-                                   int Nz, int P, int nxp, int nzp, int pitch, double r2, double d0, double dt,
-                                   double c_max)
+__global__ void setup_kappa_kernel(const float *sos, const float *density, float *kap, int *status, int NxE,
+                                   int NzE, int P, int nxpE, int nzpE, int pitch, double r2, double d0, double dt,
+                                   double c_max, const int2 *map_dims)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = blockIdx.y;
     const int b = blockIdx.z;
     if (x >= pitch) return;
-    float *dst = kap + (static_cast<long long>(b) * nzp + z) * pitch + x;
-    if (x >= nxp) { *dst = 0.f; return; }
+    // grid of this map (sized calls: its own, inside the envelope slab [NzE][NxE] of the map)
+    const int Nx = map_dims ? map_dims[b].x : NxE, Nz = map_dims ? map_dims[b].y : NzE;
+    const int nxp = Nx + 2 * P, nzp = Nz + 2 * P;
+    float *dst = kap + (static_cast<long long>(b) * nzpE + z) * pitch + x;
+    if (x >= nxp || z >= nzp) { *dst = 0.f; return; }
     const int xs = min(max(x - P, 0), Nx - 1), zs = min(max(z - P, 0), Nz - 1);
-    const long long src = (static_cast<long long>(b) * Nz + zs) * Nx + xs;
+    const long long src = (static_cast<long long>(b) * NzE + zs) * NxE + xs;
     const double C = sos[src];
     if (!isfinite(C)) raise_status(status, DUFWI_ERR_NONFINITE);
     else if (!(C > 0.0) || C > c_max) raise_status(status, DUFWI_ERR_CFL);
     if (density && x >= P && x < P + Nx && z >= P && z < P + Nz) {
-        if (density[src] != density[static_cast<long long>(b) * Nz * Nx]) raise_status(status, DUFWI_ERR_UNSUPPORTED);
+        if (density[src] != density[static_cast<long long>(b) * NzE * NxE]) raise_status(status, DUFWI_ERR_UNSUPPORTED);
     }
     const int dxl = x < P ? P - x : (x > P + Nx - 1 ? x - (P + Nx - 1) : 0);
     const int dzl = z < P ? P - z : (z > P + Nz - 1 ? z - (P + Nz - 1) : 0);
@@ -733,12 +763,13 @@ __global__ void misfit_sum_kernel(const double *partial, double *misfit, int n_m
 // transmits, in two short passes (every dependent FP64 chain stays below n_tx (P + 1) terms):
 //   fold_x: F[b][zp][ix] = sum_tx sum_{xp copying ix} G_s[zp][xp]
 //   fold_z: g[b][iz][ix] = (2 / C) sum_{zp copying iz} F[b][zp][ix]
-__global__ void fold_x_kernel(const float *g_shot, double *fx, int n_tx, int Nx, int P, int nzp, long long slice,
-                              int pitch)
+__global__ void fold_x_kernel(const float *g_shot, double *fx, int n_tx, int NxE, int P, int nzpE, long long slice,
+                              int pitch, const int2 *map_dims)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int zp = blockIdx.y;
     const int b = blockIdx.z;
+    const int Nx = map_dims ? map_dims[b].x : NxE;
     if (ix >= Nx) return;
     const int xlo = ix == 0 ? 0 : ix + P, xhi = ix == Nx - 1 ? Nx + 2 * P - 1 : ix + P;
     double acc = 0.0;
@@ -746,19 +777,22 @@ __global__ void fold_x_kernel(const float *g_shot, double *fx, int n_tx, int Nx,
         const float *g = g_shot + static_cast<long long>(b * n_tx + t) * slice + static_cast<long long>(zp) * pitch;
         for (int x = xlo; x <= xhi; ++x) acc += g[x];
     }
-    fx[(static_cast<long long>(b) * nzp + zp) * Nx + ix] = acc;
+    fx[(static_cast<long long>(b) * nzpE + zp) * NxE + ix] = acc;
 }
 
-__global__ void fold_z_kernel(const double *fx, const float *sos, float *grad, int Nx, int Nz, int P, int nzp)
+__global__ void fold_z_kernel(const double *fx, const float *sos, float *grad, int NxE, int NzE, int P, int nzpE,
+                              const int2 *map_dims)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y;
     const int b = blockIdx.z;
-    if (ix >= Nx) return;
+    if (ix >= NxE) return;
+    const int Nx = map_dims ? map_dims[b].x : NxE, Nz = map_dims ? map_dims[b].y : NzE;
+    const long long o = (static_cast<long long>(b) * NzE + iz) * NxE + ix;
+    if (ix >= Nx || iz >= Nz) { grad[o] = 0.f; return; }   // outside this map (sized calls)
     const int zlo = iz == 0 ? 0 : iz + P, zhi = iz == Nz - 1 ? Nz + 2 * P - 1 : iz + P;
     double acc = 0.0;
-    for (int z = zlo; z <= zhi; ++z) acc += fx[(static_cast<long long>(b) * nzp + z) * Nx + ix];
-    const long long o = (static_cast<long long>(b) * Nz + iz) * Nx + ix;
+    for (int z = zlo; z <= zhi; ++z) acc += fx[(static_cast<long long>(b) * nzpE + z) * NxE + ix];
     grad[o] = static_cast<float>(acc * (2.0 / static_cast<double>(sos[o])));
 }
 
@@ -953,11 +987,11 @@ cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepPara
 
 cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, int *status, int n_maps, int Nx,
                                int Nz, int P, int nxp, int nzp, int pitch, double dt_over_dx, double d0, double dt,
-                               double c_max, cudaStream_t st)
+                               double c_max, const int2 *map_dims, cudaStream_t st)
 {
     dim3 grid((pitch + 127) / 128, nzp, n_maps);
     setup_kappa_kernel<<<grid, 128, 0, st>>>(sos, density, kap, status, Nx, Nz, P, nxp, nzp, pitch,
-                                             dt_over_dx * dt_over_dx, d0, dt, c_max);
+                                             dt_over_dx * dt_over_dx, d0, dt, c_max, map_dims);
     return cudaGetLastError();
 }
 
@@ -996,13 +1030,14 @@ cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps,
 }
 
 cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *fx, int n_maps, int n_tx, int Nx,
-                        int Nz, int P, long long slice, int pitch, cudaStream_t st)
+                        int Nz, int P, long long slice, int pitch, const int2 *map_dims, cudaStream_t st)
 {
     const int nzp = Nz + 2 * P;
-    fold_x_kernel<<<dim3((Nx + 127) / 128, nzp, n_maps), 128, 0, st>>>(g_shot, fx, n_tx, Nx, P, nzp, slice, pitch);
+    fold_x_kernel<<<dim3((Nx + 127) / 128, nzp, n_maps), 128, 0, st>>>(g_shot, fx, n_tx, Nx, P, nzp, slice, pitch,
+                                                                       map_dims);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    fold_z_kernel<<<dim3((Nx + 127) / 128, Nz, n_maps), 128, 0, st>>>(fx, sos, grad, Nx, Nz, P, nzp);
+    fold_z_kernel<<<dim3((Nx + 127) / 128, Nz, n_maps), 128, 0, st>>>(fx, sos, grad, Nx, Nz, P, nzp, map_dims);
     return cudaGetLastError();
 }
 

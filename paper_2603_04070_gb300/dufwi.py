@@ -50,6 +50,10 @@ class _Array(ctypes.Structure):
                 ("iz", ctypes.POINTER(ctypes.c_int32))]
 
 
+class _MapSizes(ctypes.Structure):
+    _fields_ = [("nx", ctypes.POINTER(ctypes.c_int32)), ("nz", ctypes.POINTER(ctypes.c_int32))]
+
+
 class _Shots(ctypes.Structure):
     _fields_ = [("n_tx", ctypes.c_int32), ("n_rx", ctypes.c_int32),
                 ("tx_elem", ctypes.POINTER(ctypes.c_int32)),
@@ -78,6 +82,9 @@ def _load():
     lib.dufwi_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.dufwi_launch_count.restype = ctypes.c_int64
     lib.dufwi_simulate_noalloc.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp]
+    M = ctypes.POINTER(_MapSizes)
+    lib.dufwi_simulate_sized.argtypes = [P, M, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
+    lib.dufwi_misfit_gradient_sized.argtypes = [P, M, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, sz, vp]
     lib.dufwi_forward_save.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
     lib.dufwi_backward.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, sz, vp]
     lib.dufwi_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
@@ -194,10 +201,23 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _sizes_struct(sizes, n_maps):
+    """``sizes``: sequence of (nx, nz) per map -> (_MapSizes, keep-alive arrays)."""
+    arr = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32).reshape(n_maps, 2))
+    nx = np.ascontiguousarray(arr[:, 0])
+    nz = np.ascontiguousarray(arr[:, 1])
+    ip = ctypes.POINTER(ctypes.c_int32)
+    return _MapSizes(nx.ctypes.data_as(ip), nz.ctypes.data_as(ip)), (nx, nz)
+
+
 def simulate(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, *,
              density: torch.Tensor | None = None, cd: torch.Tensor | None = None,
-             workspace: torch.Tensor | None = None, stream=None, check: bool = False) -> torch.Tensor:
-    """Channel data ``[n_maps][n_tx][nt][n_rx]`` for SoS maps ``sos [n_maps][nz][nx]`` (Eqs. 2-4)."""
+             workspace: torch.Tensor | None = None, stream=None, check: bool = False,
+             sizes=None) -> torch.Tensor:
+    """Channel data ``[n_maps][n_tx][nt][n_rx]`` for SoS maps ``sos [n_maps][nz][nx]`` (Eqs. 2-4).
+
+    ``sizes``: optional per-map physical grids ``[(nx_b, nz_b)]`` inside the (nx, nz) envelope
+    (``dufwi_simulate_sized``)."""
     n_maps = sos.shape[0]
     _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
     wshape = (geom.n_tx, problem.nt) if geom.wavelet_per_tx else (problem.nt,)
@@ -211,9 +231,14 @@ def simulate(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: G
     workspace = _workspace(problem, geom, n_maps, False, workspace, sos.device)
     pb = problem.c_struct()
     arr, sh = geom.c_structs()
-    rc = _lib.dufwi_simulate(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
-                             ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd.data_ptr(),
-                             workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    args = (sos.data_ptr(), density.data_ptr() if density is not None else None, ctypes.byref(arr),
+            wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd.data_ptr(), workspace.data_ptr(),
+            workspace.numel() * workspace.element_size(), _stream(stream))
+    if sizes is None:
+        rc = _lib.dufwi_simulate(ctypes.byref(pb), *args)
+    else:
+        ms, _keep = _sizes_struct(sizes, n_maps)
+        rc = _lib.dufwi_simulate_sized(ctypes.byref(pb), ctypes.byref(ms), *args)
     _check(rc, "dufwi_simulate")
     if check:
         _check(workspace_status(workspace, stream), "dufwi_simulate (device)")
@@ -257,8 +282,10 @@ def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, 
                     cd_obs: torch.Tensor, *, density: torch.Tensor | None = None,
                     misfit: torch.Tensor | None = None, grad: torch.Tensor | None = None,
                     cd_sim: torch.Tensor | None = None, return_cd: bool = False,
-                    workspace: torch.Tensor | None = None, stream=None, check: bool = False):
-    """Misfit ``J [n_maps]`` (float64) and gradient ``dJ/dC [n_maps][nz][nx]`` (Eqs. 5-6)."""
+                    workspace: torch.Tensor | None = None, stream=None, check: bool = False, sizes=None):
+    """Misfit ``J [n_maps]`` (float64) and gradient ``dJ/dC [n_maps][nz][nx]`` (Eqs. 5-6).
+
+    ``sizes``: optional per-map physical grids inside the envelope (``dufwi_misfit_gradient_sized``)."""
     n_maps = sos.shape[0]
     _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
     wshape = (geom.n_tx, problem.nt) if geom.wavelet_per_tx else (problem.nt,)
@@ -280,11 +307,15 @@ def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, 
     workspace = _workspace(problem, geom, n_maps, True, workspace, sos.device)
     pb = problem.c_struct()
     arr, sh = geom.c_structs()
-    rc = _lib.dufwi_misfit_gradient(
-        ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
-        ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd_obs.data_ptr(),
-        misfit.data_ptr(), grad.data_ptr(), cd_sim.data_ptr() if cd_sim is not None else None,
-        workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    args = (sos.data_ptr(), density.data_ptr() if density is not None else None,
+            ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd_obs.data_ptr(),
+            misfit.data_ptr(), grad.data_ptr(), cd_sim.data_ptr() if cd_sim is not None else None,
+            workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    if sizes is None:
+        rc = _lib.dufwi_misfit_gradient(ctypes.byref(pb), *args)
+    else:
+        ms, _keep = _sizes_struct(sizes, n_maps)
+        rc = _lib.dufwi_misfit_gradient_sized(ctypes.byref(pb), ctypes.byref(ms), *args)
     _check(rc, "dufwi_misfit_gradient")
     if check:
         _check(workspace_status(workspace, stream), "dufwi_misfit_gradient (device)")

@@ -211,3 +211,28 @@ def make_workload(name: str, seed: int = 0, *, n_maps: int | None = None, nt: in
                     sos_start=sos_start, wavelet=ricker(nt_, dt, f0), elem_ix=elem_ix,
                     elem_iz=elem_iz, tx_elem=tx, rx_elem=rx, fd_order=fd_order,
                     meta={"seed": seed, "f0": f0, "kind": kind})
+
+
+def sized_batch(seed: int, sizes, nt: int, n_elem: int, n_tx: int, dx: float = 1e-4, dt: float = 1e-8,
+                f0: float = 2e6, kind: str = "disk"):
+    """Maps of different physical grids (nx_b, nz_b) embedded in the envelope (max nx, max nz).
+
+    One shared linear array, centred on the smallest map so that every element lies inside every
+    map. Returns (Workload with envelope sizes and embedded maps, list of sizes)."""
+    rng = rng_for(seed)
+    NX = max(s[0] for s in sizes)
+    NZ = max(s[1] for s in sizes)
+    B = len(sizes)
+    true = np.full((B, NZ, NX), BACKGROUND_SOS, dtype=np.float32)
+    for b, (nx, nz) in enumerate(sizes):
+        m = disk_map(rng, nx, nz, dx) if kind == "disk" else grf_rods_map(rng, nx, nz, dx, max_rods=4)
+        true[b, :nz, :nx] = m
+    start = np.full_like(true, BACKGROUND_SOS)
+    nx_min = min(s[0] for s in sizes)
+    elem_ix, elem_iz = linear_array(nx_min, n_elem)
+    tx = np.array([n_elem // 2], dtype=np.int32) if n_tx == 1 else evenly_spaced_transmits(n_elem, n_tx)
+    rx = np.tile(np.arange(n_elem, dtype=np.int32), (tx.size, 1))
+    wl = Workload(name="sized", nx=NX, nz=NZ, dx=dx, dt=dt, nt=nt, sos_true=true, sos_start=start,
+                  wavelet=ricker(nt, dt, f0), elem_ix=elem_ix, elem_iz=elem_iz, tx_elem=tx, rx_elem=rx,
+                  meta={"seed": seed, "sizes": [tuple(s) for s in sizes]})
+    return wl, [tuple(s) for s in sizes]

@@ -332,3 +332,79 @@ def test_autograd_vjp_matches_oracle_for_random_cotangent(d):
     sim = _oracle_traces(wl, wl.sos_true[0])
     J_ref, g_ref, _ = _oracle_grad(wl, wl.sos_true[0], sim - 0.5 * q[0].astype(np.float64))
     assert rel_l2(sos.grad.cpu().numpy()[0], g_ref) <= GRAD_TOL
+
+
+def test_sized_batch_matches_oracle_per_map(d):
+    """Maps of three different grids in one call (one launch per step for all shots): traces and
+    gradient of each map against the oracle run on that map's own grid."""
+    sizes = [(40, 36), (57, 49), (72, 64)]
+    wl, sizes = inputs.sized_batch(seed=21, sizes=sizes, nt=350, n_elem=12, n_tx=2)
+    geom = d.Geometry.from_workload(wl)
+    pb = _dufwi_problem(d, wl, ckpt_interval=30)
+    w = torch.from_numpy(wl.wavelet).cuda()
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    # observed data per map from the oracle on its own grid
+    obs = np.zeros((len(sizes), wl.n_tx, wl.nt, wl.n_rx), np.float32)
+    refs = []
+    for b, (nx, nz) in enumerate(sizes):
+        p = oracle.Problem(nx=nx, nz=nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml, pml_R=wl.pml_R,
+                           pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+        for k in range(wl.n_tx):
+            obs[b, k] = oracle.forward(p, wl.sos_true[b, :nz, :nx].astype(np.float64), (tix[k], tiz[k]),
+                                       wl.wavelet.astype(np.float64), rix[k], riz[k])
+        refs.append((p, oracle.misfit_gradient(p, wl.sos_start[b, :nz, :nx].astype(np.float64), tix, tiz,
+                                               wl.wavelet.astype(np.float64), rix, riz, obs[b].astype(np.float64),
+                                               return_traces=True)))
+    cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), w, geom, sizes=sizes, check=True).cpu().numpy()
+    J, g, cds = d.misfit_gradient(pb, torch.from_numpy(wl.sos_start).cuda(), w, geom, torch.from_numpy(obs).cuda(),
+                                  sizes=sizes, return_cd=True, check=True)
+    J, g, cds = J.cpu().numpy(), g.cpu().numpy(), cds.cpu().numpy()
+    for b, (nx, nz) in enumerate(sizes):
+        _, (J_ref, g_ref, cd_ref) = refs[b]
+        assert rel_l2(cd[b], obs[b]) <= TRACE_TOL
+        assert rel_l2(cds[b], cd_ref) <= TRACE_TOL
+        assert abs(J[b] - J_ref) <= 1e-4 * J_ref
+        assert rel_l2(g[b, :nz, :nx], g_ref) <= GRAD_TOL
+        assert np.all(g[b, nz:, :] == 0) and np.all(g[b, :, nx:] == 0)
+
+
+def test_sized_call_with_full_sizes_equals_uniform_call(d):
+    wl = inputs.make_workload("linear_disk", seed=22, nx=66, nz=58, nt=200, n_elem=16, n_tx=2, n_maps=2)
+    pb = _dufwi_problem(d, wl, ckpt_interval=25)
+    geom = d.Geometry.from_workload(wl)
+    w = torch.from_numpy(wl.wavelet).cuda()
+    sos = torch.from_numpy(wl.sos_true).cuda()
+    a = d.simulate(pb, sos, w, geom)
+    b = d.simulate(pb, sos, w, geom, sizes=[(wl.nx, wl.nz)] * 2)
+    assert torch.equal(a, b)
+    obs = a * 1.01
+    Ja, ga = d.misfit_gradient(pb, torch.from_numpy(wl.sos_start).cuda(), w, geom, obs)
+    Jb, gb = d.misfit_gradient(pb, torch.from_numpy(wl.sos_start).cuda(), w, geom, obs, sizes=[(wl.nx, wl.nz)] * 2)
+    assert torch.equal(Ja, Jb) and torch.equal(ga, gb)
+
+
+def test_gradient_call_captures_in_a_cuda_graph(d):
+    """After one ordinary call on a workspace, a repeat call issues only device work and can be
+    captured; replaying the graph reproduces the direct result bit for bit."""
+    wl = inputs.make_workload("linear_disk", seed=23, nx=60, nz=52, nt=180, n_elem=14, n_tx=2)
+    pb = _dufwi_problem(d, wl, ckpt_interval=20)
+    geom = d.Geometry.from_workload(wl)
+    w = torch.from_numpy(wl.wavelet).cuda()
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    obs = torch.from_numpy(_observed(wl)).cuda()
+    ws = torch.empty(d.workspace_size(pb, geom, 1), dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(sos)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)   # uploads the tables
+        s.synchronize()
+        J0, g0 = J.clone(), g.clone()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)
+    J.zero_(); g.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(J, J0) and torch.equal(g, g0)

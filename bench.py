@@ -342,10 +342,79 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_uneven_batch(args):
+    """Shots/s of the forward simulation for 32 maps of uneven grids x 16 transmits (512 shots)
+    advanced together (one launch per time step), against one shot per call on its own grid
+    (each call replayed from a CUDA graph) on a sample of the same shots."""
+    import torch
+    from paper_2603_04070_gb300 import autotune, build_lib, inputs
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    dev = torch.device("cuda", 0)
+    nt = args.nt or 6000
+    wl, sizes = inputs.uneven_batch(seed=0, nt=nt)
+    pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
+    geom = dufwi.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_true).to(dev)
+    wav = torch.from_numpy(wl.wavelet).to(dev)
+    tuned = autotune.tune(pb, sos, wav, geom, sizes=sizes)
+    ws = torch.empty(dufwi.workspace_size(pb, geom, wl.n_maps, gradient=False), dtype=torch.uint8, device=dev)
+    cd = torch.empty((wl.n_maps, wl.n_tx, nt, wl.n_rx), dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(args.steps):
+        dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
+    e[1].record()
+    torch.cuda.synchronize()
+    batched_ms = e[0].elapsed_time(e[1]) / args.steps
+    shots = wl.n_maps * wl.n_tx
+    # one shot per call, graph-captured, on a sample of shots spread over maps and transmits
+    sample = [(b, k) for b, k in zip(range(0, wl.n_maps, 4), range(0, wl.n_tx, 2))]
+    one_ms = []
+    for b, k in sample:
+        nx_b, nz_b = sizes[b]
+        pb1 = dufwi.Problem(nx=nx_b, nz=nz_b, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
+        g1 = dufwi.Geometry(wl.elem_ix, wl.elem_iz, wl.tx_elem[k:k + 1], wl.rx_elem[k:k + 1])
+        s1 = torch.from_numpy(wl.sos_true[b:b + 1, :nz_b, :nx_b].copy()).to(dev)
+        w1 = torch.empty(dufwi.workspace_size(pb1, g1, 1, gradient=False), dtype=torch.uint8, device=dev)
+        c1 = torch.empty((1, 1, nt, wl.n_rx), dtype=torch.float32, device=dev)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)
+            st.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=st):
+                dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)
+        graph.replay()
+        torch.cuda.synchronize()
+        e[0].record()
+        graph.replay()
+        e[1].record()
+        torch.cuda.synchronize()
+        one_ms.append(e[0].elapsed_time(e[1]))
+    one_shot_per_s = 1e3 / (sum(one_ms) / len(one_ms))
+    line = {"metric": "forward simulation shots/s (uneven-grid batch)", "value": shots / (batched_ms / 1e3),
+            "unit": "shots/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "32 disk maps on grids from 384x384, 512x512, 640x512 x 16 transmits = 512 "
+                                   "shots, %d steps, 128 elements; one launch per step for all shots" % nt,
+                       "grids": sizes, "tuned_options": tuned},
+            "one_shot_per_call": {"value": one_shot_per_s, "unit": "shots/s",
+                                  "sample": "%d shots, each its own call on its own grid, replayed from a CUDA "
+                                            "graph" % len(sample), "ms_per_shot": one_ms},
+            "speedup_vs_one_shot": (shots / (batched_ms / 1e3)) / one_shot_per_s}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven_batch":
+        run_uneven_batch(args)
     else:
         run_ours(args)
 

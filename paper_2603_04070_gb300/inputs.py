@@ -236,3 +236,17 @@ def sized_batch(seed: int, sizes, nt: int, n_elem: int, n_tx: int, dx: float = 1
                   wavelet=ricker(nt, dt, f0), elem_ix=elem_ix, elem_iz=elem_iz, tx_elem=tx, rx_elem=rx,
                   meta={"seed": seed, "sizes": [tuple(s) for s in sizes]})
     return wl, [tuple(s) for s in sizes]
+
+
+UNEVEN_GRIDS = ((384, 384), (512, 512), (640, 512))
+
+
+def uneven_batch(seed: int = 0, n_maps: int = 32, n_tx: int = 16, nt: int = 6000, n_elem: int = 128):
+    """Batching workload: n_maps disk maps (the linear-disk distribution), each on a grid drawn
+    from 384 x 384, 512 x 512 and 640 x 512 (nx x nz), with a 128-element array and n_tx evenly
+    spaced transmits shared by all maps."""
+    rng = rng_for(seed + 1000)
+    sizes = [UNEVEN_GRIDS[int(rng.integers(0, len(UNEVEN_GRIDS)))] for _ in range(n_maps)]
+    wl, sizes = sized_batch(seed, sizes, nt, n_elem, n_tx)
+    wl.name = "uneven_batch"
+    return wl, sizes

@@ -137,7 +137,8 @@ struct TileLayout {
     static constexpr int kTiles = MODE == kAdjoint ? 4 : 2;            // prev, kappa (+ history, sums)
     static constexpr int kFloats = kBox + kTiles * kTile;
     static constexpr uint32_t kBytes = kFloats * sizeof(float);
-    static constexpr int kThreadsPerCta = (kTileX / 4) * (TZ / 4);      // 4 (x) x 4 (z) outputs each
+    static constexpr int kPasses = TZ / 32;                            // 32-row passes per CTA
+    static constexpr int kThreadsPerCta = 128;                         // 4 (x) x 4 (z) outputs per pass
 };
 
 constexpr int kMaxInj = 64;   // point injections staged in shared memory per list
@@ -186,16 +187,18 @@ __device__ __forceinline__ void gather_injections(InjList &l, const StepParams &
 template <int MODE>
 __device__ __forceinline__ void apply_injections(const InjList &l, float *buf, const StepParams &p, const int *sorted,
                                                  int n_sorted, int s, int tx_idx, int step, int2 range, int rx0,
-                                                 int rz0, int stride)
+                                                 int rz0, int stride, int idx_lo = 0, int idx_hi = 1 << 30)
 {
     const int m = min(l.n, kMaxInj);
-    for (int e = 0; e < m; ++e) buf[l.idx[e]] += l.val[e];
+    for (int e = 0; e < m; ++e)
+        if (l.idx[e] >= idx_lo && l.idx[e] < idx_hi) buf[l.idx[e]] += l.val[e];
     if (MODE == kAdjoint) {
         for (int e = kMaxInj; e < l.n; ++e) {
             const int r = __ldg(sorted + tx_idx * n_sorted + range.x + e);
             const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
-            buf[((node >> 16) - rz0) * stride + ((node & 0xffff) - rx0)] +=
-                __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + step) * p.n_rx + r);
+            const int idx = ((node >> 16) - rz0) * stride + ((node & 0xffff) - rx0);
+            if (idx >= idx_lo && idx < idx_hi)
+                buf[idx] += __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + step) * p.n_rx + r);
         }
     }
 }
@@ -320,20 +323,18 @@ __device__ __forceinline__ bool wait_tile(uint64_t *bar, const StepParams &p, in
     return true;
 }
 
-// Minimum resident CTAs of 128 threads per SM requested from the register allocator (the 64-row
-// tile variant asks for half as many CTAs of 256 threads). Build-time knob.
+// Minimum resident CTAs per SM requested from the register allocator. Build-time knob.
 #ifndef DUFWI_STEP_MIN_CTAS_128
 #define DUFWI_STEP_MIN_CTAS_128 5
 #endif
 
-// One time step, one 64 x TZ output tile of one shot per CTA. A single mbarrier collects the TMA
-// loads of the (64 + 8) x (TZ + 8) box of U^n and of the 64 x TZ tiles of U^{n-1} and kappa'
-// (and, in the adjoint, of Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay
-// resident per SM, so the loads of some overlap the arithmetic of others.
+// One time step, one 64 x TZ output tile of one shot per CTA (128 threads, TZ / 32 passes of
+// 4 x 4 outputs per thread). A single mbarrier collects the TMA loads of the (64 + 8) x (TZ + 8)
+// box of U^n and of the 64 x TZ tiles of U^{n-1} and kappa' (and, in the adjoint, of
+// Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay resident per SM, so the
+// loads of some overlap the arithmetic of others.
 template <int R, int MODE, int TZ>
-__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta,
-                                  (DUFWI_STEP_MIN_CTAS_128 * 128 + TileLayout<MODE, TZ>::kThreadsPerCta - 1) /
-                                      TileLayout<MODE, TZ>::kThreadsPerCta)
+__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta, TZ == 32 ? DUFWI_STEP_MIN_CTAS_128 : 4)
 step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 {
     using TL = TileLayout<MODE, TZ>;
@@ -356,15 +357,12 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     const MapGrid mg = map_grid(p, s / p.n_tx);
     if (x0 >= mg.nxp || z0 >= mg.nzp) return;
 
-    if (tid == 0) {
-        prefetch_tensormap(&tm.cur_box);
-        prefetch_tensormap(&tm.out_tile);
-        mbar_init(&bar, 1);
-    }
-    __syncthreads();
-
+    // Thread 0 initialises the barrier, issues the loads and alone polls the barrier; the other
+    // threads first touch it after the CTA barrier in wait_tile, so no barrier is needed here.
     grid_dependency_wait();
     if (tid == 0) {
+        prefetch_tensormap(&tm.cur_box);
+        mbar_init(&bar, 1);
         mbar_arrive_expect_tx(&bar, TL::kBytes);
         tma_load_3d(box, &tm.cur_box, &bar, x0 - kHalo, z0 - kHalo, s);
         tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
@@ -385,7 +383,6 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
                             tid, TL::kThreadsPerCta);
 
     const int lx = (tid & 15) * 4;
-    const int lz = (tid >> 4) * 4;
     const int gx = x0 + lx;
     const bool interior = region_interior(p, mg, x0, z0, kTileX, TZ);
     int xd[4];
@@ -394,43 +391,47 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 
     if (!wait_tile(&bar, p, tid)) return;
 
-    float4 lap[4], ctr[4], nxt[4];
-    lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int lo = (lz + j) * kTileX + lx;
-        nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
-                         p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
-    }
-    if (inj.n > 0) {   // block-uniform: stage, inject in list order, reload
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
-        __syncthreads();
-        if (tid == 0)
-            apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX);
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
-    }
-
     const bool col_ok = gx < mg.nxp;
+#pragma unroll 1
+    for (int pass = 0; pass < TL::kPasses; ++pass) {
+        const int lz = (tid >> 4) * 4 + 32 * pass;
+        float4 lap[4], ctr[4], nxt[4];
+        lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int gz = z0 + lz + j;
-        if (!col_ok || gz >= mg.nzp) continue;
-        float4 nv = nxt[j], lv = lap[j];
-        if (gx + 4 > mg.nxp) {   // lanes past the last column stay zero (outside the map's grid)
-            if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
-            if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
-            nv.w = 0.f; lv.w = 0.f;
-        }
-        const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
-        st4(p.out + o, nv);
-        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
-        if (MODE == kAdjoint) {
+        for (int j = 0; j < 4; ++j) {
             const int lo = (lz + j) * kTileX + lx;
-            st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+            nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
+                             p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+        }
+        if (inj.n > 0) {   // block-uniform: stage this pass's rows, inject in list order, reload
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
+            __syncthreads();
+            if (tid == 0)
+                apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX,
+                                       32 * pass * kTileX, 32 * (pass + 1) * kTileX);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gz = z0 + lz + j;
+            if (!col_ok || gz >= mg.nzp) continue;
+            float4 nv = nxt[j], lv = lap[j];
+            if (gx + 4 > mg.nxp) {   // lanes past the last column stay zero (outside the map's grid)
+                if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
+                if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
+                nv.w = 0.f; lv.w = 0.f;
+            }
+            const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+            st4(p.out + o, nv);
+            if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
+            if (MODE == kAdjoint) {
+                const int lo = (lz + j) * kTileX + lx;
+                st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+            }
         }
     }
 

@@ -383,11 +383,13 @@ def run_uneven_batch(args):
         c1 = torch.empty((1, 1, nt, wl.n_rx), dtype=torch.float32, device=dev)
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
-            dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)
+            dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)      # uploads the tables
             st.synchronize()
+            dufwi.set_option(dufwi.OPT_REUSE_TABLES, 1)               # w1 stays reserved
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=st):
                 dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)
+        dufwi.set_option(dufwi.OPT_REUSE_TABLES, 0)
         graph.replay()
         torch.cuda.synchronize()
         e[0].record()

@@ -17,11 +17,15 @@
  *     the library copies into the workspace with stream-ordered copies. The library allocates
  *     no memory: callers query the workspace size first and pass a device buffer at least that
  *     large, aligned to 256 bytes.
- *   - The library remembers, per workspace pointer, what it last copied there. A call on the
- *     same workspace with unchanged problem and geometry skips those copies, and then issues
- *     only kernels, memsets and device-to-device copies. Such a call can be captured in a CUDA
- *     graph; run it once outside the capture first. Between calls, the workspace belongs to the
- *     library: a caller that writes into it must not rely on this cache.
+ *   - With the option DUFWI_OPT_REUSE_TABLES set, the library remembers, per workspace
+ *     pointer, what it last copied there. A call on the same workspace with unchanged problem
+ *     and geometry then skips those copies and issues only kernels, memsets and
+ *     device-to-device copies, so it can be captured in a CUDA graph. Run it once outside the
+ *     capture first. While the option is set, the workspace must stay reserved for the library
+ *     between calls: a buffer freed and re-allocated at the same address would otherwise hold
+ *     stale tables. Every index the kernels derive from the tables is bounds-checked, so
+ *     damaged tables set DUFWI_ERR_GEOMETRY in the status word rather than touching memory
+ *     outside the buffers.
  *   - Every call is asynchronous on the given stream and returns a status code. Host-side
  *     argument checks are reported by the return value. Conditions only visible on the device
  *     are recorded in a status word inside the workspace and read with dufwi_workspace_status:
@@ -156,6 +160,24 @@ int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *densi
                    int32_t n_maps, const float *cd_grad, float *grad, void *workspace,
                    size_t workspace_bytes, void *stream /* cudaStream_t */);
 
+/* Jacobian-vector product of the forward model (the linearised, "Born" simulation): for a
+ * perturbation dsos of the SoS maps, dcd[b] = (dM[b]/dC[b]) dsos[b]. Each time step advances the
+ * background field (Eq. 2, recording the channel data into cd when cd is not NULL) and then the
+ * perturbation field dU with the same update plus the source dkappa' Lap(U^n). Here
+ * dkappa' = 2 kappa' dC / C, with dC extended into the absorbing layer like C. With
+ * dufwi_backward this gives Gauss-Newton Hessian-vector products of the misfit,
+ * H v = 2 J^T (J v).
+ *   dsos   [n_maps][nz][nx] float, device
+ *   dcd    [n_maps][n_tx][nt][n_rx] float, device, output
+ *   cd     NULL or [n_maps][n_tx][nt][n_rx] float, device, output (the background data)
+ *   workspace: device, >= dufwi_jvp_workspace_size bytes. */
+int dufwi_jvp_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int32_t n_maps,
+                             size_t *bytes);
+int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+              const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *dsos,
+              float *dcd, float *cd, void *workspace, size_t workspace_bytes,
+              void *stream /* cudaStream_t */);
+
 /* Forward model for callers that cannot allocate device memory. The paper has no counterpart:
  * this serves hosts that must not call cudaMalloc while running, such as a fixed-latency
  * acquisition loop (a device allocation can synchronise the device) or an application that hands
@@ -231,9 +253,12 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     columns.
  *   DUFWI_OPT_TWO_STEP: 1 advances pairs of time steps (n, n+1 with n even) in one launch,
  *     bit-identical to one launch per step (0, the default, which measured faster on GB300).
+ *   DUFWI_OPT_REUSE_TABLES: 1 lets calls skip re-copying unchanged geometry tables into a
+ *     workspace that stays reserved between calls (see the conventions above); default 0.
  * Both functions return DUFWI_ERR_INVALID_ARG for an unknown option or value. */
 #define DUFWI_OPT_TILE_Z 1
 #define DUFWI_OPT_TWO_STEP 2
+#define DUFWI_OPT_REUSE_TABLES 3
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

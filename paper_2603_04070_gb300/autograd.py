@@ -9,6 +9,9 @@ DUFWI training of Sec. III-B, where g_k feeds N_theta_k.
 
 Gradients flow to the SoS maps only. The pulse, the density and the geometry are constants.
 Calling ``backward`` twice needs ``retain_graph=True``; the saved workspace is reused.
+Forward-mode AD (``torch.autograd.forward_ad``) uses the linearised Born simulation
+(``dufwi_jvp``). ``hvp_gauss_newton`` combines it with the adjoint into Gauss-Newton
+Hessian-vector products of the misfit.
 """
 from __future__ import annotations
 
@@ -22,10 +25,19 @@ class _Simulate(torch.autograd.Function):
     def forward(ctx, sos, wavelet, problem, geom):
         cd, ws = dufwi.forward_save(problem, sos.detach().contiguous(), wavelet.detach().contiguous(), geom)
         ctx.save_for_backward(sos, wavelet)
+        ctx.save_for_forward(sos, wavelet)
         ctx.workspace = ws
         ctx.problem = problem
         ctx.geom = geom
         return cd
+
+    @staticmethod
+    def jvp(ctx, sos_t, wavelet_t, problem_t, geom_t):
+        sos, wavelet = ctx.saved_tensors
+        if sos_t is None:
+            return None
+        return dufwi.jvp(ctx.problem, sos.detach().contiguous(), wavelet.detach().contiguous(), ctx.geom,
+                         sos_t.contiguous())
 
     @staticmethod
     def backward(ctx, cd_grad):
@@ -47,3 +59,14 @@ def misfit(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geo
     """Per-map data misfit J = sum (M - M_obs)^2 (Eq. 5 with lambda = 0), differentiable in sos."""
     r = simulate(problem, sos, wavelet, geom) - cd_obs
     return (r * r).sum(dim=(1, 2, 3), dtype=torch.float64)
+
+
+def hvp_gauss_newton(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: dufwi.Geometry,
+                     v: torch.Tensor) -> torch.Tensor:
+    """Gauss-Newton Hessian-vector product of the misfit J = sum (M - M_obs)^2: H v = 2 J^T (J v),
+    with J = dM/dC (Born forward, then the adjoint)."""
+    sos = sos.detach().contiguous()
+    wavelet = wavelet.detach().contiguous()
+    _, ws = dufwi.forward_save(problem, sos, wavelet, geom)
+    dcd = dufwi.jvp(problem, sos, wavelet, geom, v.contiguous())
+    return dufwi.backward(problem, sos, wavelet, geom, 2.0 * dcd, ws)

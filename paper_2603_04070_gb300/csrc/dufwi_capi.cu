@@ -60,13 +60,16 @@ struct Layout {
     // byte offsets into the workspace
     int tiles1, tiles2;      // tiles of the one-step kernel (tile height TZ) and of the two-step kernel
     int n_rxe;               // row length of the grown-tile receiver lists (4 n_rx)
-    size_t o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
+    size_t o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
 };
 
-// Last table contents uploaded to each workspace (see common_setup).
+// Last table contents uploaded to each workspace (see common_setup), and whether a call may
+// skip the upload when they match (DUFWI_OPT_REUSE_TABLES; off by default because a workspace
+// freed and re-allocated at the same address by a caching allocator may hold other data).
 std::mutex g_table_mutex;
 std::unordered_map<const void *, uint64_t> g_table_hash;
+int g_reuse_tables = 0;
 
 // Tile height of the one-step kernel (DUFWI_OPT_TILE_Z) and use of the two-step kernel.
 int g_tile_z = kTileZDefault;
@@ -89,8 +92,11 @@ int validate_problem(const dufwi_problem *pb)
     return DUFWI_OK;
 }
 
-int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, bool gradient, Layout *L)
+enum LayoutKind { kLayoutSimulate = 0, kLayoutGradient = 1, kLayoutJvp = 2 };
+
+int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int kind, Layout *L)
 {
+    const bool gradient = kind == kLayoutGradient;
     int rc = validate_problem(pb);
     if (rc) return rc;
     if (!sh || sh->n_tx < 1 || sh->n_rx < 0 || n_maps < 1) return DUFWI_ERR_INVALID_ARG;
@@ -114,6 +120,7 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, bool
         L->n_seg = (steps + L->K - 1) / L->K;
     }
     L->n_hist = (pb->ckpt_interval == 0) ? (steps > 0 ? steps : 1) : L->K;
+    if (kind == kLayoutJvp) L->n_hist = 1;
     L->snap_elem = pb->snapshot_dtype == DUFWI_SNAP_FP32 ? 4 : 2;
 
     const size_t field = (size_t)L->S * L->slice * sizeof(float);
@@ -151,6 +158,12 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, bool
         L->o_asrc = take(cdb);
         L->o_part = take((size_t)L->S * sizeof(double));
         L->o_fold = take((size_t)n_maps * L->nzp * L->Nx * sizeof(double));
+    }
+    if (kind == kLayoutJvp) {
+        for (int i = 0; i < 4; ++i) L->o_m[i] = take(field);          // Born field ring
+        L->o_hist = take(field);                                         // Lap(U^n) of the current step
+        L->o_dkap = take((size_t)n_maps * L->slice * sizeof(float));
+        L->o_cd = take(cdb);                                             // background traces
     }
     L->total = off;
     return DUFWI_OK;
@@ -281,8 +294,9 @@ struct Ctx {
     int tz;
     bool two_step;
     const dufwi_map_sizes *sizes = nullptr;   // sized calls: per-map grids inside the envelope
+    bool jvp = false;                         // linearised forward (Born) call
     FieldMaps fmap[4], mmap[4];
-    CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2;
+    CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1;
     int *status() const { return reinterpret_cast<int *>(ws + L.o_status); }
     template <typename T> T *at(size_t o) const { return reinterpret_cast<T *>(ws + o); }
 };
@@ -354,7 +368,7 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.ws = static_cast<char *>(workspace);
     c.st = static_cast<cudaStream_t>(stream);
     c.tz = g_tile_z;
-    c.two_step = g_two_step != 0 && !c.sizes;
+    c.two_step = g_two_step != 0 && !c.sizes && !c.jvp;
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
     std::vector<int> sorted1, sorted2, sortede;
@@ -396,12 +410,14 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
         mix(&b.off, sizeof(b.off));
         mix(b.src, b.bytes);
     }
-    bool fresh;
+    bool fresh = true;
     {
         std::lock_guard<std::mutex> lock(g_table_mutex);
-        auto it = g_table_hash.find(workspace);
-        fresh = it == g_table_hash.end() || it->second != h;
-        if (fresh) g_table_hash[workspace] = h;
+        if (g_reuse_tables) {
+            auto it = g_table_hash.find(workspace);
+            fresh = it == g_table_hash.end() || it->second != h;
+        }
+        g_table_hash[workspace] = h;
     }
     if (fresh) {
         for (const Blob &b : blobs)
@@ -427,6 +443,13 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (tensor_map(&c.kap1, kap, L, L.n_maps, 0, kTileX, c.tz) ||
         tensor_map(&c.kap2, kap, L, L.n_maps, 0, kTileX + 2 * kHalo, kPairTileZ + 2 * kHalo))
         return DUFWI_ERR_CUDA;
+    if (c.jvp) {
+        for (int i = 0; i < 4; ++i)
+            if (field_maps(&c.mmap[i], c.at<float>(L.o_m[i]), L, c.tz)) return DUFWI_ERR_CUDA;
+        if (tensor_map(&c.hist1, c.at<float>(L.o_hist), L, L.S, 1, kTileX, c.tz) ||
+            tensor_map(&c.dkap1, c.at<float>(L.o_dkap), L, L.n_maps, 0, kTileX, c.tz))
+            return DUFWI_ERR_CUDA;
+    }
     if (gradient) {
         for (int i = 0; i < 4; ++i)
             if (field_maps(&c.mmap[i], c.at<float>(L.o_m[i]), L, c.tz)) return DUFWI_ERR_CUDA;
@@ -482,6 +505,7 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
     tm.out_tile = rg.map[rg.prv].tile1;
     tm.kap_tile = c.kap1;
     if (mode == kAdjoint) { tm.hist_tile = c.hist1; tm.grad_tile = c.grad1; }
+    if (mode == kBorn) { tm.hist_tile = c.hist1; tm.grad_tile = c.dkap1; }
     p.out = rg.buf[rg.prv];
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
@@ -626,6 +650,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_two_step = value;
         return DUFWI_OK;
+    case DUFWI_OPT_REUSE_TABLES:
+        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
+        g_reuse_tables = value;
+        return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
     }
 }
@@ -636,6 +664,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     switch (option) {
     case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
+    case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
     }
 }
@@ -706,7 +735,7 @@ int dufwi_simulate_workspace_size(const dufwi_problem *pb, const dufwi_shots *sh
 {
     if (!bytes) return DUFWI_ERR_INVALID_ARG;
     Layout L;
-    int rc = make_layout(pb, shots, n_maps, false, &L);
+    int rc = make_layout(pb, shots, n_maps, kLayoutSimulate, &L);
     if (rc) return rc;
     *bytes = L.total;
     return DUFWI_OK;
@@ -716,7 +745,7 @@ int dufwi_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int3
 {
     if (!bytes) return DUFWI_ERR_INVALID_ARG;
     Layout L;
-    int rc = make_layout(pb, shots, n_maps, true, &L);
+    int rc = make_layout(pb, shots, n_maps, kLayoutGradient, &L);
     if (rc) return rc;
     *bytes = L.total;
     return DUFWI_OK;
@@ -748,7 +777,7 @@ int dufwi_simulate_sized(const dufwi_problem *pb, const dufwi_map_sizes *sizes, 
     Ctx c;
     c.pb = pb;
     c.sizes = sizes;
-    int rc = make_layout(pb, shots, n_maps, false, &c.L);
+    int rc = make_layout(pb, shots, n_maps, kLayoutSimulate, &c.L);
     if (rc) return rc;
     if (!cd && c.L.n_rx > 0) return DUFWI_ERR_INVALID_ARG;
     rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
@@ -844,7 +873,7 @@ int gradient_setup(Ctx &c, const dufwi_problem *pb, const float *sos, const floa
                    size_t workspace_bytes, void *stream)
 {
     c.pb = pb;   // c.sizes is set by the caller (null for uniform calls)
-    int rc = make_layout(pb, shots, n_maps, true, &c.L);
+    int rc = make_layout(pb, shots, n_maps, kLayoutGradient, &c.L);
     if (rc) return rc;
     return common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, true);
 }
@@ -871,7 +900,7 @@ int dufwi_misfit_gradient_sized(const dufwi_problem *pb, const dufwi_map_sizes *
     Ctx c;
     c.sizes = sizes;
     Layout chk;
-    int rc = make_layout(pb, shots, n_maps, true, &chk);
+    int rc = make_layout(pb, shots, n_maps, kLayoutGradient, &chk);
     if (rc) return rc;
     if ((!cd_obs && chk.n_rx > 0) || !misfit || !grad) return DUFWI_ERR_INVALID_ARG;
     rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
@@ -898,7 +927,7 @@ int dufwi_forward_save(const dufwi_problem *pb, const float *sos, const float *d
 {
     Ctx c;
     Layout chk;
-    int rc = make_layout(pb, shots, n_maps, true, &chk);
+    int rc = make_layout(pb, shots, n_maps, kLayoutGradient, &chk);
     if (rc) return rc;
     if (!cd && chk.n_rx > 0) return DUFWI_ERR_INVALID_ARG;
     rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
@@ -917,7 +946,7 @@ int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *densi
 {
     Ctx c;
     Layout chk;
-    int rc = make_layout(pb, shots, n_maps, true, &chk);
+    int rc = make_layout(pb, shots, n_maps, kLayoutGradient, &chk);
     if (rc) return rc;
     if ((!cd_grad && chk.n_rx > 0) || !grad) return DUFWI_ERR_INVALID_ARG;
     rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
@@ -929,6 +958,75 @@ int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *densi
                                 L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
     return gradient_reverse(c, sos, wavelet, grad);
+}
+
+int dufwi_jvp_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int32_t n_maps, size_t *bytes)
+{
+    if (!bytes) return DUFWI_ERR_INVALID_ARG;
+    Layout L;
+    int rc = make_layout(pb, shots, n_maps, kLayoutJvp, &L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return DUFWI_OK;
+}
+
+int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+              const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *dsos, float *dcd,
+              float *cd, void *workspace, size_t workspace_bytes, void *stream)
+{
+    Ctx c;
+    c.pb = pb;
+    c.jvp = true;
+    int rc = make_layout(pb, shots, n_maps, kLayoutJvp, &c.L);
+    if (rc) return rc;
+    if (!dsos || (!dcd && c.L.n_rx > 0)) return DUFWI_ERR_INVALID_ARG;
+    rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
+    if (rc) return rc;
+    const Layout &L = c.L;
+    const size_t field = (size_t)L.S * L.slice * sizeof(float);
+    long long nl = 0;
+    const int e0 = g_prof.mark(c.st);
+    CKL(launch_setup_dkappa(sos, dsos, c.at<float>(L.o_kap), c.at<float>(L.o_dkap), L.n_maps, L.Nx, L.Nz, L.P, L.nzp,
+                            L.pitch, c.st));
+    Ring fr, br;
+    for (int i = 0; i < 4; ++i) {
+        fr.buf[i] = c.at<float>(L.o_f[i]);
+        br.buf[i] = c.at<float>(L.o_m[i]);
+        CK(cudaMemsetAsync(fr.buf[i], 0, field, c.st));
+        CK(cudaMemsetAsync(br.buf[i], 0, field, c.st));
+    }
+    fr.map = c.fmap;
+    br.map = c.mmap;
+    fr.cur = br.cur = 0;
+    fr.prv = br.prv = 1;
+    float *bg_cd = cd ? cd : c.at<float>(L.o_cd);
+    StepParams pf = c.base, pb_ = c.base;
+    pf.inj_node = c.at<int>(L.o_tx);
+    pf.inj_val = wavelet;
+    pf.smp_node = c.at<int>(L.o_rx);
+    pf.cd = bg_cd;
+    pf.hist = c.at<float>(L.o_hist);
+    pb_.smp_node = c.at<int>(L.o_rx);
+    pb_.inj_node = c.at<int>(L.o_tx);
+    pb_.cd = dcd;
+    pb_.hist_slot = 0;
+    for (int n = 0; n < L.nt - 1; ++n) {
+        // background step n (records U^n, keeps Lap(U^n)), then the Born step n using it
+        pf.step = n;
+        rc = one_step(c, fr, kFwdSampleHist, pf, nl);
+        if (rc) return rc;
+        pb_.step = n;
+        rc = one_step(c, br, kBorn, pb_, nl);
+        if (rc) return rc;
+    }
+    if (L.n_rx > 0) {
+        CKL(launch_sample(fr.buf[fr.cur], c.at<int>(L.o_rx), bg_cd, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt,
+                          L.nt - 1, c.st));
+        CKL(launch_sample(br.buf[br.cur], c.at<int>(L.o_rx), dcd, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt,
+                          L.nt - 1, c.st));
+    }
+    g_prof.span(0, e0, g_prof.mark(c.st), nl);
+    return DUFWI_OK;
 }
 
 }  // extern "C"

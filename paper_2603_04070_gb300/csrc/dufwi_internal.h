@@ -28,6 +28,7 @@ enum StepMode : int {
     kFwdSampleHist = 1,  // forward step, record receivers, keep Lap(U^n) (store-all first pass)
     kFwdHist = 2,        // forward step, keep Lap(U^n) (recompute of one checkpoint segment)
     kAdjoint = 3,        // adjoint step with residual injection and zero-lag imaging
+    kBorn = 4,           // linearised (Born) step: dU^{n+1} = Eq. 2 on dU + dkappa' Lap(U^n), receivers
 };
 
 // Tensor maps of one step launch (all FP32, no swizzle, zero fill outside the tensor):
@@ -35,7 +36,8 @@ enum StepMode : int {
 //   out_tile  field updated in place: dims (nxp, nzp, S), box 64 x TZ x 1
 //   kap_tile  kappa': dims (nxp, nzp, n_maps), box 64 x TZ x 1
 //   hist_tile history ring: dims (nxp, nzp, S, n_hist), box 64 x TZ x 1 x 1 (adjoint only)
-//   grad_tile imaging sums: dims (nxp, nzp, S), box 64 x TZ x 1 (adjoint only)
+//   grad_tile imaging sums: dims (nxp, nzp, S), box 64 x TZ x 1 (adjoint); in the Born step the
+//             perturbation dkappa': dims (nxp, nzp, n_maps), box 64 x TZ x 1
 struct StepMaps {
     CUtensorMap cur_box, out_tile, kap_tile, hist_tile, grad_tile;
 };
@@ -89,6 +91,9 @@ cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const floa
                             const int *rx_node, float *asrc, double *partial, int *status,
                             int S, int n_tx, int n_rx, int nt, long long slice, int pitch,
                             cudaStream_t st);
+// dkappa' = kappa' * 2 dC / C on the padded grid (dC extended by edge replication).
+cudaError_t launch_setup_dkappa(const float *sos, const float *dsos, const float *kap, float *dkap, int n_maps, int Nx,
+                                int Nz, int P, int nzp, int pitch, cudaStream_t st);
 cudaError_t launch_cotangent_source(const float *cd_grad, const float *kap, const int *rx_node, float *asrc,
                                    int *status, int S, int n_tx, int n_rx, int nt, long long slice, int pitch,
                                    cudaStream_t st);

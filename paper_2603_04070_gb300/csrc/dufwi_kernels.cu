@@ -134,7 +134,8 @@ struct TileLayout {
     static constexpr int kBoxRows = TZ + 2 * kHalo;
     static constexpr int kBox = kBoxX * kBoxRows;                      // U^n (or mu^{m+1}) with halo
     static constexpr int kTile = kTileX * TZ;
-    static constexpr int kTiles = MODE == kAdjoint ? 4 : 2;            // prev, kappa (+ history, sums)
+    // prev, kappa (+ history and sums in the adjoint; + Lap(U^n) and dkappa' in the Born step)
+    static constexpr int kTiles = (MODE == kAdjoint || MODE == kBorn) ? 4 : 2;
     static constexpr int kFloats = kBox + kTiles * kTile;
     static constexpr uint32_t kBytes = kFloats * sizeof(float);
     static constexpr int kPasses = TZ / 32;                            // 32-row passes per CTA
@@ -162,12 +163,25 @@ __device__ __forceinline__ void gather_injections(InjList &l, const StepParams &
                                                   int rh, int stride, int tid, int nthreads)
 {
     if (MODE == kAdjoint) {
-        if (tid == 0) l.n = range.y;
-        const int m = min(range.y, kMaxInj);
+        // Every index derived from the tables is checked before use: a damaged table raises
+        // DUFWI_ERR_GEOMETRY in the status word instead of addressing outside the buffers.
+        const bool range_ok = range.x >= 0 && range.y >= 0 && range.x + range.y <= n_sorted;
+        if (tid == 0) {
+            l.n = range_ok ? range.y : 0;
+            if (!range_ok) raise_status(p.status, DUFWI_ERR_GEOMETRY);
+        }
+        const int m = range_ok ? min(range.y, kMaxInj) : 0;
         for (int e = tid; e < m; e += nthreads) {
             const int r = __ldg(sorted + tx_idx * n_sorted + range.x + e);
-            const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
-            l.idx[e] = ((node >> 16) - rz0) * stride + ((node & 0xffff) - rx0);
+            const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.inj_node + tx_idx * p.n_rx + r) : -1;
+            const int zn = node >> 16, xn = node & 0xffff;
+            if (node < 0 || zn < rz0 || zn >= rz0 + rh || xn < rx0 || xn >= rx0 + rw) {
+                l.idx[e] = -1;
+                l.val[e] = 0.0f;
+                raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                continue;
+            }
+            l.idx[e] = (zn - rz0) * stride + (xn - rx0);
             l.val[e] = __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + step) * p.n_rx + r);
         }
     } else if (tid == 0) {
@@ -187,16 +201,22 @@ __device__ __forceinline__ void gather_injections(InjList &l, const StepParams &
 template <int MODE>
 __device__ __forceinline__ void apply_injections(const InjList &l, float *buf, const StepParams &p, const int *sorted,
                                                  int n_sorted, int s, int tx_idx, int step, int2 range, int rx0,
-                                                 int rz0, int stride, int idx_lo = 0, int idx_hi = 1 << 30)
+                                                 int rz0, int rw, int rh, int stride, int idx_lo = 0,
+                                                 int idx_hi = 1 << 30)
 {
     const int m = min(l.n, kMaxInj);
     for (int e = 0; e < m; ++e)
-        if (l.idx[e] >= idx_lo && l.idx[e] < idx_hi) buf[l.idx[e]] += l.val[e];
+        if (l.idx[e] >= 0 && l.idx[e] >= idx_lo && l.idx[e] < idx_hi) buf[l.idx[e]] += l.val[e];
     if (MODE == kAdjoint) {
         for (int e = kMaxInj; e < l.n; ++e) {
             const int r = __ldg(sorted + tx_idx * n_sorted + range.x + e);
-            const int node = __ldg(p.inj_node + tx_idx * p.n_rx + r);
-            const int idx = ((node >> 16) - rz0) * stride + ((node & 0xffff) - rx0);
+            const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.inj_node + tx_idx * p.n_rx + r) : -1;
+            const int zn = node >> 16, xn = node & 0xffff;
+            if (node < 0 || zn < rz0 || zn >= rz0 + rh || xn < rx0 || xn >= rx0 + rw) {
+                raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                continue;
+            }
+            const int idx = (zn - rz0) * stride + (xn - rx0);
             if (idx >= idx_lo && idx < idx_hi)
                 buf[idx] += __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + step) * p.n_rx + r);
         }
@@ -371,6 +391,10 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
             tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
             tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
         }
+        if (MODE == kBorn) {
+            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s / p.n_tx);
+        }
     }
     grid_dependents_launch();
 
@@ -379,8 +403,12 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     int2 rx_range = make_int2(0, 0);
     if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
-    gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
-                            tid, TL::kThreadsPerCta);
+    if (MODE == kBorn) {   // the Born field has no point source of its own
+        if (tid == 0) inj.n = 0;
+    } else {
+        gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
+                                tid, TL::kThreadsPerCta);
+    }
 
     const int lx = (tid & 15) * 4;
     const int gx = x0 + lx;
@@ -402,15 +430,16 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
             const int lo = (lz + j) * kTileX + lx;
             nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
                              p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+            if (MODE == kBorn) nxt[j] = fma4(ld4s(gg + lo), ld4s(hs + lo), nxt[j]);   // + dkappa' Lap(U^n)
         }
-        if (inj.n > 0) {   // block-uniform: stage this pass's rows, inject in list order, reload
+        if (MODE != kBorn && inj.n > 0) {   // block-uniform: stage this pass's rows, inject, reload
             __syncthreads();
 #pragma unroll
             for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
             __syncthreads();
             if (tid == 0)
                 apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX,
-                                       32 * pass * kTileX, 32 * (pass + 1) * kTileX);
+                                       TZ, kTileX, 32 * pass * kTileX, 32 * (pass + 1) * kTileX);
             __syncthreads();
 #pragma unroll
             for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
@@ -436,11 +465,16 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     }
 
     // Receiver sampling of U^n from the box (each receiver lies in exactly one tile).
-    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
-        for (int e = tid; e < rx_range.y; e += TL::kThreadsPerCta) {
+    if (MODE == kFwdSample || MODE == kFwdSampleHist || MODE == kBorn) {
+        const int cnt = (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
+        for (int e = tid; e < cnt; e += TL::kThreadsPerCta) {
             const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
-            const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
+            const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.smp_node + tx_idx * p.n_rx + r) : -1;
             const int zn = node >> 16, xn = node & 0xffff;
+            if (node < 0 || zn < z0 || zn >= z0 + TZ || xn < x0 || xn >= x0 + kTileX) {
+                raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                continue;
+            }
             p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
                 box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
         }
@@ -569,7 +603,7 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     if (inj[0].n > 0) {
         if (tid == 0)
             apply_injections<MODE>(inj[0], n1, p, p.rxe_sorted, p.n_rxe, s, tx_idx, p.step, rx_ring, x0 - kHalo,
-                                   z0 - kHalo, kPairEX);
+                                   z0 - kHalo, kPairEX, kPairEZ, kPairEX);
         __syncthreads();
     }
 
@@ -602,10 +636,15 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
                     ld4s(n1 + (cz + kHalo) * kPairEX + cx + kHalo));
         }
         if (MODE == kFwdSample || MODE == kFwdSampleHist) {
-            for (int e = t; e < rx_core.y; e += kPairThreads - 128) {
+            const int cnt = (rx_core.x >= 0 && rx_core.y >= 0 && rx_core.x + rx_core.y <= p.n_rx) ? rx_core.y : 0;
+            for (int e = t; e < cnt; e += kPairThreads - 128) {
                 const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_core.x + e);
-                const int node = __ldg(p.smp_node + tx_idx * p.n_rx + r);
+                const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.smp_node + tx_idx * p.n_rx + r) : -1;
                 const int zn = node >> 16, xn = node & 0xffff;
+                if (node < 0 || zn < z0 || zn >= z0 + kPairZ || xn < x0 || xn >= x0 + kTileX) {
+                    raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                    continue;
+                }
                 float *cd = p.cd + (static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r;
                 cd[0] = box[(zn - z0 + 2 * kHalo) * kPairBoxX + (xn - x0 + 2 * kHalo)];
                 if (p.step + 1 < p.nt) cd[p.n_rx] = n1[(zn - z0 + kHalo) * kPairEX + (xn - x0 + kHalo)];
@@ -620,7 +659,8 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
         }
         __syncthreads();
         if (tid == 0)
-            apply_injections<MODE>(inj[1], pe, p, p.rx_sorted, p.n_rx, s, tx_idx, step_b, rx_core, x0, z0, kTileX);
+            apply_injections<MODE>(inj[1], pe, p, p.rx_sorted, p.n_rx, s, tx_idx, step_b, rx_core, x0, z0, kTileX,
+                                   kPairZ, kTileX);
         __syncthreads();
         if (tid < 128) {
 #pragma unroll
@@ -731,6 +771,22 @@ __global__ void residual_kernel(const float *cd_sim, const float *cd_obs, const 
     if (bad) raise_status(status, DUFWI_ERR_NONFINITE);
     const double t = block_sum(acc, red);
     if (threadIdx.x == 0) partial[s] = t;
+}
+
+// dkappa' = kappa' * 2 dC / C (kappa' = C^2 dt^2/(dx^2 (1 + D dt)) so dkappa'/dC = 2 kappa'/C),
+// with C and dC extended into the absorbing layer by edge replication.
+__global__ void setup_dkappa_kernel(const float *sos, const float *dsos, const float *kap, float *dkap, int Nx, int Nz,
+                                    int P, int nzp, int pitch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = blockIdx.y;
+    const int b = blockIdx.z;
+    if (x >= pitch) return;
+    const long long o = (static_cast<long long>(b) * nzp + z) * pitch + x;
+    const int xs = min(max(x - P, 0), Nx - 1), zs = min(max(z - P, 0), Nz - 1);
+    const long long src = (static_cast<long long>(b) * Nz + zs) * Nx + xs;
+    const double k = kap[o];   // zero on the pitch padding
+    dkap[o] = static_cast<float>(k * 2.0 * static_cast<double>(dsos[src]) / static_cast<double>(sos[src]));
 }
 
 // Adjoint source of a general cotangent v = dL/dM: kappa'_r * v (no misfit).
@@ -921,6 +977,7 @@ static cudaError_t launch_step_r(int mode, const StepMaps &tm, const StepParams 
     case kFwdSampleHist: return launch_step_rm<R, kFwdSampleHist>(tm, p, st);
     case kFwdHist: return launch_step_rm<R, kFwdHist>(tm, p, st);
     case kAdjoint: return launch_step_rm<R, kAdjoint>(tm, p, st);
+    case kBorn: return launch_step_rm<R, kBorn>(tm, p, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1010,6 +1067,14 @@ cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const floa
 {
     residual_kernel<<<S, 512, 0, st>>>(cd_sim, cd_obs, kap, rx_node, asrc, partial, status, n_tx, n_rx, nt, slice,
                                        pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_dkappa(const float *sos, const float *dsos, const float *kap, float *dkap, int n_maps, int Nx,
+                                int Nz, int P, int nzp, int pitch, cudaStream_t st)
+{
+    setup_dkappa_kernel<<<dim3((pitch + 127) / 128, nzp, n_maps), 128, 0, st>>>(sos, dsos, kap, dkap, Nx, Nz, P, nzp,
+                                                                                pitch);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE = 5, 6, 7, 8
 SNAPSHOT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 OPT_TILE_Z = 1
 OPT_TWO_STEP = 2
+OPT_REUSE_TABLES = 3
 
 
 class DufwiError(RuntimeError):
@@ -86,6 +87,8 @@ def _load():
     lib.dufwi_simulate_sized.argtypes = [P, M, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
     lib.dufwi_misfit_gradient_sized.argtypes = [P, M, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, sz, vp]
     lib.dufwi_forward_save.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
+    lib.dufwi_jvp_workspace_size.argtypes = [P, S, ctypes.c_int32, ctypes.POINTER(sz)]
+    lib.dufwi_jvp.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, sz, vp]
     lib.dufwi_backward.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, sz, vp]
     lib.dufwi_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
     lib.dufwi_get_option.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
@@ -376,6 +379,45 @@ def backward(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: G
     if check:
         _check(workspace_status(workspace, stream), "dufwi_backward (device)")
     return grad
+
+
+def jvp_workspace_size(problem: Problem, geom: Geometry, n_maps: int) -> int:
+    pb = problem.c_struct()
+    _, sh = geom.c_structs()
+    out = ctypes.c_size_t(0)
+    _check(_lib.dufwi_jvp_workspace_size(ctypes.byref(pb), ctypes.byref(sh), int(n_maps), ctypes.byref(out)),
+           "jvp_workspace_size")
+    return int(out.value)
+
+
+def jvp(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, dsos: torch.Tensor, *,
+        density: torch.Tensor | None = None, dcd: torch.Tensor | None = None, cd: torch.Tensor | None = None,
+        return_cd: bool = False, workspace: torch.Tensor | None = None, stream=None, check: bool = False):
+    """Linearised (Born) channel data dM = (dM/dC) dsos (``dufwi_jvp``); optionally also M."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, density)
+    _dev_tensor(dsos, "dsos", torch.float32, sos.shape)
+    if dcd is None:
+        dcd = torch.empty(cshape, dtype=torch.float32, device=sos.device)
+    _dev_tensor(dcd, "dcd", torch.float32, cshape)
+    if return_cd and cd is None:
+        cd = torch.empty(cshape, dtype=torch.float32, device=sos.device)
+    if cd is not None:
+        _dev_tensor(cd, "cd", torch.float32, cshape)
+    need = jvp_workspace_size(problem, geom, n_maps)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=sos.device)
+    elif workspace.numel() * workspace.element_size() < need:
+        raise DufwiError(ERR_WORKSPACE, "jvp workspace")
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_jvp(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+                        ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, dsos.data_ptr(),
+                        dcd.data_ptr(), cd.data_ptr() if cd is not None else None, workspace.data_ptr(),
+                        workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "dufwi_jvp")
+    if check:
+        _check(workspace_status(workspace, stream), "dufwi_jvp (device)")
+    return (dcd, cd) if return_cd else dcd
 
 
 def workspace_status(workspace: torch.Tensor, stream=None) -> int:

@@ -397,14 +397,88 @@ def test_gradient_call_captures_in_a_cuda_graph(d):
     J = torch.empty(1, dtype=torch.float64, device="cuda")
     g = torch.empty_like(sos)
     s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)   # uploads the tables
-        s.synchronize()
-        J0, g0 = J.clone(), g.clone()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=s):
-            d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)
-    J.zero_(); g.zero_()
-    graph.replay()
-    torch.cuda.synchronize()
-    assert torch.equal(J, J0) and torch.equal(g, g0)
+    try:
+        with torch.cuda.stream(s):
+            d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)   # uploads the tables
+            s.synchronize()
+            J0, g0 = J.clone(), g.clone()
+            d.set_option(d.OPT_REUSE_TABLES, 1)   # ws stays reserved: repeat calls may skip the copies
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)
+        J.zero_(); g.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(J, J0) and torch.equal(g, g0)
+    finally:
+        d.set_option(d.OPT_REUSE_TABLES, 0)
+        del ws
+
+
+def _born_case(seed, nt=320):
+    wl = inputs.make_workload("linear_disk", seed=seed, nx=58, nz=52, nt=nt, n_elem=14, n_tx=2)
+    rng = np.random.default_rng(seed)
+    v = (rng.standard_normal(wl.sos_start.shape) * 5.0).astype(np.float32)
+    return wl, v
+
+
+def test_born_jvp_matches_oracle_finite_differences(d):
+    """dM = (dM/dC) v against central differences of the FP64 oracle forward model."""
+    wl, v = _born_case(31)
+    C = wl.sos_true[0].astype(np.float64)
+    h = 0.05
+    ref = (_oracle_traces(wl, C + h * v[0]) - _oracle_traces(wl, C - h * v[0])) / (2 * h)
+    pb = _dufwi_problem(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    dcd, cd = d.jvp(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    torch.from_numpy(v).cuda(), return_cd=True, check=True)
+    assert rel_l2(cd.cpu().numpy()[0], _oracle_traces(wl, C)) <= TRACE_TOL
+    assert rel_l2(dcd.cpu().numpy()[0], ref) <= 1e-4
+
+
+def test_born_jvp_and_adjoint_are_transposes(d):
+    """<J w, q> = <w, J^T q> between the Born simulation and the adjoint (dot-product test)."""
+    wl, w = _born_case(32)
+    pb = _dufwi_problem(d, wl, ckpt_interval=40)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_true).cuda()
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    q = torch.randn((1, wl.n_tx, wl.nt, wl.n_rx), device="cuda") * 1e-9
+    Jw = d.jvp(pb, sos, wav, geom, torch.from_numpy(w).cuda())
+    _, ws = d.forward_save(pb, sos, wav, geom)
+    JTq = d.backward(pb, sos, wav, geom, q, ws)
+    lhs = float((Jw.double() * q.double()).sum())
+    rhs = float((torch.from_numpy(w).cuda().double() * JTq.double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+def test_gauss_newton_hvp_matches_oracle(d):
+    """H v = 2 J^T J v: oracle J v by central differences, oracle J^T through its misfit gradient
+    with M_obs = M - J v."""
+    from paper_2603_04070_gb300 import autograd
+    wl, v = _born_case(33)
+    C = wl.sos_true[0].astype(np.float64)
+    h = 0.05
+    Jv = (_oracle_traces(wl, C + h * v[0]) - _oracle_traces(wl, C - h * v[0])) / (2 * h)
+    M = _oracle_traces(wl, C)
+    _, Hv_ref, _ = _oracle_grad(wl, C, M - Jv)
+    pb = _dufwi_problem(d, wl, ckpt_interval=32)
+    geom = d.Geometry.from_workload(wl)
+    Hv = autograd.hvp_gauss_newton(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(),
+                                   geom, torch.from_numpy(v).cuda())
+    assert rel_l2(Hv.cpu().numpy()[0], Hv_ref) <= 1e-3
+
+
+def test_autograd_forward_mode_uses_born(d):
+    from paper_2603_04070_gb300 import autograd
+    import torch.autograd.forward_ad as fwAD
+    wl, v = _born_case(34, nt=200)
+    pb = _dufwi_problem(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_true).cuda()
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    tv = torch.from_numpy(v).cuda()
+    with fwAD.dual_level():
+        out = autograd.simulate(pb, fwAD.make_dual(sos, tv), wav, geom)
+        tangent = fwAD.unpack_dual(out).tangent
+    assert torch.equal(tangent, d.jvp(pb, sos, wav, geom, tv))

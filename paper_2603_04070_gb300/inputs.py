@@ -107,7 +107,7 @@ def grf_rods_map(rng, nx: int, nz: int, dx: float, max_rods: int = 4,
     tries = 0
     while len(rods) < n_rods and tries < 1000:
         tries += 1
-        r = rng.uniform(1e-3, 5e-3)
+        r = rng.uniform(1e-3, max(1e-3, min(5e-3, 0.3 * (min(nx, nz) - 1) * dx)))   # fits small test grids
         cx = rng.uniform(r, (nx - 1) * dx - r)
         cz = rng.uniform(r, (nz - 1) * dx - r)
         if any((cx - x) ** 2 + (cz - z) ** 2 < (r + q) ** 2 for x, z, q in rods):

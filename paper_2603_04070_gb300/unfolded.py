@@ -1,0 +1,119 @@
+"""Deep-unfolded FWI (DUFWI) around the GPU misfit gradient (Sec. III, Eqs. 9-10).
+
+Each iteration k computes the data-fidelity gradient g_k = dJ/dC at the current estimate C_k
+(Eq. 6) with the library's adjoint kernels. A per-iteration network N_k turns (C_k, g_k) into
+an update H_k, and C_{k+1} = C_k + H_k (Eq. 9). Training is block-wise (Sec. III-B, Eq. 10).
+Iteration k's gradients are computed once for the whole training set, N_k is fitted alone to
+the SoS-map MSE, and its outputs become the inputs of iteration k+1. No gradient flows back
+through the physics or through earlier blocks.
+
+N_k is a small convolutional net: three 3 x 3 layers with 32 channels and ReLU in between. Its
+inputs are the SoS offset by 1400 m/s and scaled (Sec. V), and the gradient normalised by its
+max |.| per map. Its output is rescaled to m/s. The convolutions run in torch (cuDNN); they are
+library dense contractions, not part of the hot path.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import torch
+import torch.nn as nn
+
+from . import dufwi
+
+SOS_OFFSET = 1400.0    # m/s, subtracted from the SoS input (Sec. V)
+SOS_SCALE = 200.0      # m/s per unit of the normalised SoS input and of the network output
+
+
+class UpdateNet(nn.Module):
+    """N_k: (C_k, g_k) -> H_k, three 3 x 3 convolutions (2 -> 32 -> 32 -> 1), ReLU in between."""
+
+    def __init__(self, channels: int = 32):
+        super().__init__()
+        self.body = nn.Sequential(
+            nn.Conv2d(2, channels, 3, padding=1), nn.ReLU(),
+            nn.Conv2d(channels, channels, 3, padding=1), nn.ReLU(),
+            nn.Conv2d(channels, 1, 3, padding=1))
+        nn.init.zeros_(self.body[-1].weight)
+        nn.init.zeros_(self.body[-1].bias)
+
+    def forward(self, sos: torch.Tensor, grad: torch.Tensor) -> torch.Tensor:
+        g = grad / grad.abs().amax(dim=(-2, -1), keepdim=True).clamp_min(1e-30)
+        x = torch.stack([(sos - SOS_OFFSET) / SOS_SCALE, g], dim=1)
+        return SOS_SCALE * self.body(x)[:, 0]
+
+
+@dataclass
+class Physics:
+    """Everything the gradient needs besides the maps: grid, pulse, array, observed data."""
+    problem: dufwi.Problem
+    wavelet: torch.Tensor
+    geom: dufwi.Geometry
+
+
+def data_gradient(phys: Physics, sos: torch.Tensor, cd_obs: torch.Tensor, chunk: int = 8):
+    """g_k = dJ/dC for a batch of maps (Eq. 6), in chunks of `chunk` maps per library call."""
+    J, g = [], []
+    for i in range(0, sos.shape[0], chunk):
+        Ji, gi = dufwi.misfit_gradient(phys.problem, sos[i:i + chunk].contiguous(), phys.wavelet, phys.geom,
+                                       cd_obs[i:i + chunk].contiguous())
+        J.append(Ji)
+        g.append(gi)
+    return torch.cat(J), torch.cat(g)
+
+
+class UnfoldedFWI(nn.Module):
+    """K unfolded iterations C_{k+1} = C_k + N_k(C_k, g_k) (Eq. 9)."""
+
+    def __init__(self, K: int = 5, channels: int = 32):
+        super().__init__()
+        self.nets = nn.ModuleList(UpdateNet(channels) for _ in range(K))
+
+    @torch.no_grad()
+    def infer(self, phys: Physics, sos0: torch.Tensor, cd_obs: torch.Tensor, timings: list | None = None):
+        """Inference from C_0 (a homogeneous map, Sec. III-A); returns all estimates C_0..C_K."""
+        out = [sos0]
+        c = sos0
+        for k, net in enumerate(self.nets):
+            if timings is not None:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            _, g = data_gradient(phys, c, cd_obs)
+            c = c + net(c, g)
+            if timings is not None:
+                torch.cuda.synchronize()
+                timings.append(time.perf_counter() - t0)
+            out.append(c)
+        return out
+
+    def train_blockwise(self, phys: Physics, sos0: torch.Tensor, cd_obs: torch.Tensor, sos_gt: torch.Tensor,
+                        epochs: int = 40, batch: int = 32, lrs=(1e-4, 1e-4, 5e-5, 1e-5, 1e-5), log=None):
+        """Block-wise training (Sec. III-B). For each k: compute g_k for the whole set once, fit
+        N_k with Adam on the SoS MSE of C_k + N_k(C_k, g_k) (Eq. 10), then advance the set to
+        C_{k+1} with N_k in inference mode. Returns the training losses per block and epoch."""
+        c = sos0
+        history = []
+        for k, net in enumerate(self.nets):
+            with torch.no_grad():
+                _, g = data_gradient(phys, c, cd_obs)
+            opt = torch.optim.Adam(net.parameters(), lr=lrs[min(k, len(lrs) - 1)])
+            losses = []
+            for _ in range(epochs):
+                perm = torch.randperm(c.shape[0], device=c.device)
+                tot = 0.0
+                for i in range(0, c.shape[0], batch):
+                    idx = perm[i:i + batch]
+                    pred = c[idx] + net(c[idx], g[idx])
+                    loss = ((pred - sos_gt[idx]) ** 2).mean()
+                    opt.zero_grad()
+                    loss.backward()
+                    opt.step()
+                    tot += float(loss.detach()) * idx.numel()
+                losses.append(tot / c.shape[0])
+            history.append(losses)
+            if log:
+                log("block %d: mse %.4g -> %.4g" % (k, losses[0], losses[-1]))
+            with torch.no_grad():
+                c = c + net(c, g)
+        return history

@@ -321,9 +321,23 @@ def run_ours(args):
         e2e = {"value": units_per_step * world * args.steps / (ems / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}
 
+    # ms per DUFWI iteration: the gradient above plus one update network N_k and the update (Eq. 9)
+    from paper_2603_04070_gb300 import unfolded
+    net = unfolded.UpdateNet().to(dev).eval()
+    with torch.no_grad():
+        for _ in range(3):
+            sos_next = sos + net(sos, grad)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            sos_next = sos + net(sos, grad)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    net_ms = e0.elapsed_time(e1) / 10
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        steps = min(1000, wl.nt)
+        steps = wl.nt
         v, dt = cpu_oracle_sample(wl, steps)
         cpu = {"value": v, "unit": UNIT, "cores": omp_cores(), "kind": "oracle",
                "sample": "FP64 oracle misfit gradient of 1 of %d transmits over the first %d of %d steps on the "
@@ -335,6 +349,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded GRF + rods SoS maps; observed data "
                 "simulated from the true map on the GPU)", "config": workload_config(wl, args),
                 "hbm_roofline_frac_40B": hbm_frac, "ms_per_gradient": ms_step,
+                "ms_per_dufwi_iteration": ms_step + net_ms, "ms_update_net": net_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
                 "clocks": clk.summary(), "profile_complete": prof["complete"]}
         print(json.dumps(line), flush=True)
@@ -411,12 +426,119 @@ def run_uneven_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dufwi_loop(args):
+    """ms per DUFWI iteration for the unfolded loop: K = 5 iterations on a batch of 8 disk maps
+    of 512 x 512 (16 transmits, 128 receivers, 6000 steps, checkpoint interval 100). Each
+    iteration is the misfit gradient of all 128 shots, the update network and the update."""
+    import torch
+    from paper_2603_04070_gb300 import build_lib, inputs
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi, unfolded
+    dev = torch.device("cuda", 0)
+    nt = args.nt or 6000
+    wl = inputs.make_workload("full_shot_set", seed=0, n_maps=8, nt=nt)
+    rng = inputs.rng_for(7)
+    wl.sos_true = np.stack([inputs.disk_map(rng, wl.nx, wl.nz, wl.dx) for _ in range(8)])
+    pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=nt, ckpt_interval=args.ckpt, c_max=wl.c_max)
+    geom = dufwi.Geometry.from_workload(wl)
+    phys = unfolded.Physics(pb, torch.from_numpy(wl.wavelet).to(dev), geom)
+    gt = torch.from_numpy(wl.sos_true).to(dev)
+    obs = dufwi.simulate(pb, gt, phys.wavelet, geom)
+    c0 = torch.from_numpy(wl.sos_start).to(dev)
+    model = unfolded.UnfoldedFWI(K=5).to(dev)
+    model.infer(phys, c0, obs)                      # warm-up
+    times = []
+    outs = model.infer(phys, c0, obs, timings=times)
+    ms = [1e3 * t for t in times]
+    line = {"metric": "ms per DUFWI iteration", "value": sum(ms) / len(ms), "unit": "ms", "n_gpus": 1,
+            "steps": len(ms), "warmup": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "unfolded DUFWI inference, K=5, batch 8 disk maps 512x512, 16 transmits x 128 "
+                                   "receivers, %d steps, checkpoint interval %d; update nets untrained" % (nt, args.ckpt)},
+            "ms_per_iteration": ms,
+            "gradient_share": "the physics gradient dominates each iteration (Sec. III-D)"}
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args):
+    """Error of each snapshot dtype against the FP64 oracle on a cropped 256 x 256 sub-problem
+    (central 64 elements, 8 transmits, 3500 steps), and on the full 1024 x 1024, 12000-step,
+    64-transmit problem the compressed gradients against the FP32-snapshot gradient."""
+    import torch
+    import oracle
+    from paper_2603_04070_gb300 import build_lib, inputs
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    dev = torch.device("cuda", 0)
+    res = {"cropped": {}, "full": {}}
+    # cropped sub-problem, compared with the oracle
+    wl = inputs.make_workload("scale", seed=0, nx=256, nz=256, nt=args.nt or 3500, n_elem=64, n_tx=8)
+    p = oracle.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml, pml_R=wl.pml_R,
+                       pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    w64 = wl.wavelet.astype(np.float64)
+    obs = np.stack([oracle.forward(p, wl.sos_true[0].astype(np.float64), (tix[k], tiz[k]), w64, rix[k], riz[k])
+                    for k in range(wl.n_tx)]).astype(np.float32)
+    t0 = time.perf_counter()
+    J_ref, g_ref, cd_ref = oracle.misfit_gradient(p, wl.sos_start[0].astype(np.float64), tix, tiz, w64, rix, riz,
+                                                  obs.astype(np.float64), ckpt=100, return_traces=True)
+    res["cropped"]["oracle_seconds"] = time.perf_counter() - t0
+    geom = dufwi.Geometry.from_workload(wl)
+    for dt_name in ("fp32", "fp16", "bf16"):
+        pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, ckpt_interval=100,
+                           snapshot_dtype=dt_name, c_max=wl.c_max)
+        J, g, cd = dufwi.misfit_gradient(pb, torch.from_numpy(wl.sos_start).to(dev), torch.from_numpy(wl.wavelet).to(dev),
+                                         geom, torch.from_numpy(obs[None]).to(dev), return_cd=True, check=True)
+        g = g.cpu().numpy()[0]
+        res["cropped"][dt_name] = {
+            "traces_rel_l2": float(np.linalg.norm(cd.cpu().numpy()[0] - cd_ref) / np.linalg.norm(cd_ref)),
+            "gradient_rel_l2": float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)),
+            "misfit_rel": float(abs(float(J[0]) - J_ref) / J_ref)}
+    res["cropped"]["residual_over_traces"] = float(np.linalg.norm(cd_ref - obs) / np.linalg.norm(cd_ref))
+    # full problem on the GPU only
+    wl = inputs.make_workload("scale", seed=0, nt=args.nt and 4 * args.nt or 12000)
+    geom = dufwi.Geometry.from_workload(wl)
+    sos_t = torch.from_numpy(wl.sos_true).to(dev)
+    wav = torch.from_numpy(wl.wavelet).to(dev)
+    pb32 = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, ckpt_interval=100, c_max=wl.c_max)
+    obs = dufwi.simulate(pb32, sos_t, wav, geom)
+    grads = {}
+    for dt_name in ("fp32", "fp16", "bf16"):
+        pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, ckpt_interval=100,
+                           snapshot_dtype=dt_name, c_max=wl.c_max)
+        ws = torch.empty(dufwi.workspace_size(pb, geom, 1), dtype=torch.uint8, device=dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        J, g = dufwi.misfit_gradient(pb, torch.from_numpy(wl.sos_start).to(dev), wav, geom, obs, workspace=ws,
+                                     check=True)
+        e[1].record()
+        torch.cuda.synchronize()
+        grads[dt_name] = g.double()
+        res["full"][dt_name] = {"ms": e[0].elapsed_time(e[1]), "workspace_GB": ws.numel() / 1e9}
+        del ws
+        torch.cuda.empty_cache()
+    for dt_name in ("fp16", "bf16"):
+        res["full"][dt_name]["gradient_rel_l2_vs_fp32_snapshots"] = float(
+            torch.linalg.norm(grads[dt_name] - grads["fp32"]) / torch.linalg.norm(grads["fp32"]))
+    cells = (wl.nx + 2 * wl.pml) * (wl.nz + 2 * wl.pml)
+    res["full"]["gcell_updates_per_s_fp32"] = 2.0 * cells * wl.nt * wl.n_tx / (res["full"]["fp32"]["ms"] / 1e3) / 1e9
+    line = {"metric": "snapshot precision study", "unit": "rel-L2", "config": {
+        "cropped": "256x256, 64 central elements, 8 transmits, %d steps, checkpoint 100" % (args.nt or 3500),
+        "full": "1024x1024, %d steps, 128 elements, 64 transmits, up to 8 rods, checkpoint 100" % wl.nt},
+        "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "uneven_batch":
         run_uneven_batch(args)
+    elif args.workload == "dufwi_loop":
+        run_dufwi_loop(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

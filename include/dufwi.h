@@ -148,6 +148,20 @@ int dufwi_forward_save(const dufwi_problem *pb, const float *sos, const float *d
                        int32_t n_maps, float *cd, void *workspace, size_t workspace_bytes,
                        void *stream /* cudaStream_t */);
 
+/* Misfit only (Eq. 5 data term), without the gradient: one forward sweep per shot, then the
+ * residual and the FP64 sum, exactly as in dufwi_misfit_gradient. It stores no snapshots and runs
+ * no adjoint, so it costs about a third of a gradient. Line searches of a classical FWI loop
+ * (Eq. 7) call it once per trial step.
+ *   cd_obs  [n_maps][n_tx][nt][n_rx] float, device
+ *   misfit  [n_maps] double, device, output: J_b = sum (M_sim - M_obs)^2
+ *   cd_sim  NULL or [n_maps][n_tx][nt][n_rx] float, device, output
+ *   workspace: device, >= dufwi_workspace_size bytes (the gradient's workspace).
+ * For the same inputs J is bit-identical to the one dufwi_misfit_gradient returns. */
+int dufwi_misfit(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                 const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_obs,
+                 double *misfit, float *cd_sim, void *workspace, size_t workspace_bytes,
+                 void *stream /* cudaStream_t */);
+
 /* Vector-Jacobian product of the forward model: grad[b] = (dM[b]/dC[b])^T cd_grad[b] for each map.
  *   cd_grad  [n_maps][n_tx][nt][n_rx] float, device: the cotangent dL/dM
  *   grad     [n_maps][nz][nx] float, device, output

@@ -921,6 +921,33 @@ int dufwi_misfit_gradient_sized(const dufwi_problem *pb, const dufwi_map_sizes *
     return gradient_reverse(c, sos, wavelet, grad);
 }
 
+int dufwi_misfit(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                 const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_obs,
+                 double *misfit, float *cd_sim, void *workspace, size_t workspace_bytes, void *stream)
+{
+    Ctx c;
+    Layout chk;
+    int rc = make_layout(pb, shots, n_maps, kLayoutGradient, &chk);
+    if (rc) return rc;
+    if ((!cd_obs && chk.n_rx > 0) || !misfit) return DUFWI_ERR_INVALID_ARG;
+    rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
+    if (rc) return rc;
+    const Layout &L = c.L;
+    Ring fr = field_ring(c, false);
+    float *cd = c.at<float>(L.o_cd);
+    rc = forward_sweep(c, fr, wavelet, cd, false, false);
+    if (rc) return rc;
+    if (cd_sim && L.n_rx > 0)
+        CK(cudaMemcpyAsync(cd_sim, cd, (size_t)L.S * L.nt * L.n_rx * sizeof(float), cudaMemcpyDeviceToDevice, c.st));
+    long long nl = 0;
+    const int e0 = g_prof.mark(c.st);
+    CKL(launch_residual(cd, cd_obs, c.at<float>(L.o_kap), c.at<int>(L.o_rx), c.at<float>(L.o_asrc),
+                        c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
+    CKL(launch_misfit_sum(c.at<double>(L.o_part), misfit, L.n_maps, L.n_tx, c.st));
+    g_prof.span(3, e0, g_prof.mark(c.st), nl);
+    return DUFWI_OK;
+}
+
 int dufwi_forward_save(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
                        const float *wavelet, const dufwi_shots *shots, int32_t n_maps, float *cd, void *workspace,
                        size_t workspace_bytes, void *stream)

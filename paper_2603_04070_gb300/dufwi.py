@@ -79,6 +79,7 @@ def _load():
     lib.dufwi_workspace_status.argtypes = [vp, vp]
     lib.dufwi_simulate.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
     lib.dufwi_misfit_gradient.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, sz, vp]
+    lib.dufwi_misfit.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, sz, vp]
     lib.dufwi_profile_enable.argtypes = [ctypes.c_int]
     lib.dufwi_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.dufwi_launch_count.restype = ctypes.c_int64
@@ -325,6 +326,32 @@ def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, 
     if return_cd:
         return misfit, grad, cd_sim
     return misfit, grad
+
+
+def misfit(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, cd_obs: torch.Tensor, *,
+           density: torch.Tensor | None = None, out: torch.Tensor | None = None,
+           cd_sim: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None,
+           check: bool = False) -> torch.Tensor:
+    """Misfit ``J [n_maps]`` (float64) alone, from one forward sweep (``dufwi_misfit``). Takes the
+    gradient's workspace; J equals the one ``misfit_gradient`` returns, bit for bit."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, density)
+    _dev_tensor(cd_obs, "cd_obs", torch.float32, cshape)
+    if out is None:
+        out = torch.empty(n_maps, dtype=torch.float64, device=sos.device)
+    _dev_tensor(out, "misfit", torch.float64, (n_maps,))
+    if cd_sim is not None:
+        _dev_tensor(cd_sim, "cd_sim", torch.float32, cshape)
+    workspace = _workspace(problem, geom, n_maps, True, workspace, sos.device)
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_misfit(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+                           ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd_obs.data_ptr(),
+                           out.data_ptr(), cd_sim.data_ptr() if cd_sim is not None else None,
+                           workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "dufwi_misfit")
+    if check:
+        _check(workspace_status(workspace, stream), "dufwi_misfit (device)")
+    return out
 
 
 def _common_inputs(problem, sos, wavelet, geom, density):

@@ -14,6 +14,12 @@ structure: a water-like background with compact inclusions (Sec. V, Sec. VII). T
 * a linear array on the top physical row, point elements every 3 cells (0.3 mm at
   dx = 0.1 mm), centred; transmits evenly spaced as floor((j + 0.5) n_elem / n_tx).
 * a 2 MHz Ricker pulse of peak 1, delayed by 1.5 / f0.
+* ``ring_phantom`` (the paper's own hardware geometry, Sec. IV and Sec. VII): a 188 x 188 grid
+  over 10 cm, a 16-element ring of 10 cm diameter, every element transmits and the opposite
+  element and its two neighbours receive (3 channels per transmit), a 350 kHz
+  derivative-of-Gaussian pulse, 1034 steps of 90.243 ns. Maps hold 1-3 rods of 1 cm diameter,
+  each bone (2700 m/s) or edema (1588 m/s), in 1500 m/s water. Observed data may carry additive
+  white Gaussian noise at a given SNR (30 dB in the paper's tests, Sec. V).
 """
 from __future__ import annotations
 
@@ -23,6 +29,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 BACKGROUND_SOS = 1540.0
+WATER_SOS = 1500.0
 
 
 def rng_for(seed: int) -> np.random.Generator:
@@ -211,6 +218,63 @@ def make_workload(name: str, seed: int = 0, *, n_maps: int | None = None, nt: in
                     sos_start=sos_start, wavelet=ricker(nt_, dt, f0), elem_ix=elem_ix,
                     elem_iz=elem_iz, tx_elem=tx, rx_elem=rx, fd_order=fd_order,
                     meta={"seed": seed, "f0": f0, "kind": kind})
+
+
+def phantom_rods_map(rng, n: int, dx: float, ring_radius_cells: float, max_rods: int = 3,
+                     diameter_m: float = 1e-2, sos_choices=(2700.0, 1588.0),
+                     background: float = WATER_SOS) -> np.ndarray:
+    """1..max_rods non-overlapping hard rods (each bone or edema SoS) in water, all inside the
+    ring with a one-diameter margin (the rod phantom of Sec. VII)."""
+    r = 0.5 * diameter_m
+    c = (n - 1) / 2.0 * dx
+    reach = ring_radius_cells * dx - 2.0 * r           # rod centres stay this far from the centre
+    X = np.arange(n) * dx
+    sos = np.full((n, n), background, dtype=np.float64)
+    n_rods = int(rng.integers(1, max_rods + 1))
+    rods: list[tuple[float, float]] = []
+    tries = 0
+    while len(rods) < n_rods and tries < 1000:
+        tries += 1
+        rho = reach * math.sqrt(rng.uniform(0.0, 1.0))
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        cx, cz = c + rho * math.cos(phi), c + rho * math.sin(phi)
+        if any((cx - x) ** 2 + (cz - z) ** 2 < (2.0 * r) ** 2 for x, z in rods):
+            continue
+        rods.append((cx, cz))
+        inside = (X[None, :] - cx) ** 2 + (X[:, None] - cz) ** 2 <= r * r
+        sos[inside] = sos_choices[int(rng.integers(0, len(sos_choices)))]
+    return sos.astype(np.float32)
+
+
+def add_awgn(rng, cd: np.ndarray, snr_db: float) -> np.ndarray:
+    """Channel data plus white Gaussian noise at the given SNR, with the signal power taken over
+    all channels and samples of each map (axis 0 indexes maps)."""
+    cd = np.asarray(cd, dtype=np.float64)
+    p = np.mean(cd.reshape(cd.shape[0], -1) ** 2, axis=1)
+    sigma = np.sqrt(p / 10.0 ** (snr_db / 10.0))
+    noise = rng.standard_normal(cd.shape) * sigma.reshape((-1,) + (1,) * (cd.ndim - 1))
+    return (cd + noise).astype(np.float32)
+
+
+def ring_phantom(seed: int = 0, n_maps: int = 1, *, n: int = 188, nt: int = 1034, n_elem: int = 16,
+                 f0: float = 350e3, dt: float = 90.243e-9, width_m: float = 0.1, fd_order: int = 8,
+                 rod_diameter_m: float = 1e-2) -> Workload:
+    """The paper's hardware geometry with rod-phantom maps (Sec. IV, Sec. VII). Element j
+    transmits; elements j + n_elem/2 - 1, j + n_elem/2, j + n_elem/2 + 1 (mod n_elem) receive.
+    The gradient is taken at homogeneous water. The absorbing-layer reference speed is 1500 m/s,
+    which reproduces the printed d0 = 1.46e6 /s at this grid."""
+    rng = rng_for(seed)
+    dx = width_m / n
+    radius = (n - 1) / 2.0
+    sos_true = np.stack([phantom_rods_map(rng, n, dx, radius, diameter_m=rod_diameter_m) for _ in range(n_maps)])
+    elem_ix, elem_iz = ring_array(n, n_elem, radius)
+    tx = np.arange(n_elem, dtype=np.int32)
+    h = n_elem // 2
+    rx = np.stack([(j + h + np.array([-1, 0, 1])) % n_elem for j in range(n_elem)]).astype(np.int32)
+    return Workload(name="ring_phantom", nx=n, nz=n, dx=dx, dt=dt, nt=nt, sos_true=sos_true,
+                    sos_start=np.full_like(sos_true, WATER_SOS), wavelet=gaussian_derivative_pulse(nt, dt, f0),
+                    elem_ix=elem_ix, elem_iz=elem_iz, tx_elem=tx, rx_elem=rx, pml_cref=WATER_SOS,
+                    fd_order=fd_order, c_max=2700.0, meta={"seed": seed, "f0": f0, "kind": "phantom_rods"})
 
 
 def sized_batch(seed: int, sizes, nt: int, n_elem: int, n_tx: int, dx: float = 1e-4, dt: float = 1e-8,

@@ -9,7 +9,10 @@ Physical conventions (paper Sec. II-A, Eqs. 2-6; readings in the C header):
 ``C`` is the SoS map ``[nz][nx]`` in m/s on the physical grid, element
 positions are physical-grid node indices ``(ix, iz)``, traces are
 ``M[t][r] = U[t]`` at the receivers, ``J = sum (M_sim - M_obs)^2`` and
-``g = dJ/dC``.
+``g = dJ/dC``. An optional density map ``rho [nz][nx]`` (kg/m^3) selects the
+variable-density operator of Eq. 1 (staggered differences with half-point
+buoyancies); without it the density is constant and the compact Laplacian of
+Eq. 2 is used.
 """
 from __future__ import annotations
 
@@ -90,6 +93,16 @@ def _get():
         _lib.orc_misfit_gradient.argtypes = [pp, dp, ctypes.c_int, ip, ip, dp, ctypes.c_int,
                                              ctypes.c_int, ip, ip, dp, ctypes.c_int,
                                              dp, dp, dp]
+        _lib.orc_stagger_coeffs.argtypes = [ctypes.c_int, dp]
+        _lib.orc_buoyancy.argtypes = [pp, dp, dp, dp]
+        _lib.orc_div_b_grad.argtypes = [pp, dp, dp, dp, dp]
+        _lib.orc_forward_rho.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_int, dp,
+                                         ctypes.c_int, ip, ip, dp]
+        _lib.orc_adjoint_probe_rho.argtypes = [pp, dp, dp, ctypes.c_int, ip, ip, dp,
+                                               ctypes.c_int, ctypes.c_int, dp]
+        _lib.orc_misfit_gradient_rho.argtypes = [pp, dp, dp, ctypes.c_int, ip, ip, dp, ctypes.c_int,
+                                                 ctypes.c_int, ip, ip, dp, ctypes.c_int,
+                                                 dp, dp, dp]
     return _lib
 
 
@@ -107,6 +120,15 @@ def _f64(a):
 
 def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _rho(p, rho):
+    """Density argument: None (constant density) or a [nz][nx] FP64 array (kept alive by the caller)."""
+    if rho is None:
+        return None, None
+    r = _f64(rho)
+    assert r.shape == (p.nz, p.nx)
+    return r, _d(r)
 
 
 def _check(rc: int, what: str):
@@ -149,7 +171,34 @@ def laplacian(p: Problem, u) -> np.ndarray:
     return out
 
 
-def forward(p: Problem, C, src, wavelet, rx_ix, rx_iz) -> np.ndarray:
+def stagger_coeffs(order: int) -> np.ndarray:
+    """Staggered first-difference weights s_1..s_{order/2}."""
+    s = np.zeros(4)
+    _check(_get().orc_stagger_coeffs(order, _d(s)), "stagger_coeffs")
+    return s[: order // 2].copy()
+
+
+def buoyancy(p: Problem, rho_pad) -> tuple[np.ndarray, np.ndarray]:
+    """Half-point buoyancies (bx at (x+1/2, z), bz at (x, z+1/2)) of a padded density map."""
+    s = p.c_struct()
+    r = _f64(rho_pad)
+    assert r.shape == (p.nzp, p.nxp)
+    bx, bz = np.zeros_like(r), np.zeros_like(r)
+    _check(_get().orc_buoyancy(ctypes.byref(s), _d(r), _d(bx), _d(bz)), "buoyancy")
+    return bx, bz
+
+
+def div_b_grad(p: Problem, bx, bz, u) -> np.ndarray:
+    """Staggered (1/dx^2)[D-_x(bx D+_x u) + D-_z(bz D+_z u)] on the padded grid."""
+    s = p.c_struct()
+    bx, bz, u = _f64(bx), _f64(bz), _f64(u)
+    assert u.shape == bx.shape == bz.shape == (p.nzp, p.nxp)
+    out = np.zeros_like(u)
+    _check(_get().orc_div_b_grad(ctypes.byref(s), _d(bx), _d(bz), _d(u), _d(out)), "div_b_grad")
+    return out
+
+
+def forward(p: Problem, C, src, wavelet, rx_ix, rx_iz, rho=None) -> np.ndarray:
     """Traces ``[nt][n_rx]`` of one transmit from node ``src = (ix, iz)``."""
     s = p.c_struct()
     C = _f64(C)
@@ -157,30 +206,33 @@ def forward(p: Problem, C, src, wavelet, rx_ix, rx_iz) -> np.ndarray:
     rx_ix, rx_iz = _i32(rx_ix), _i32(rx_iz)
     assert C.shape == (p.nz, p.nx) and w.shape == (p.nt,) and rx_ix.shape == rx_iz.shape
     out = np.zeros((p.nt, rx_ix.size))
-    _check(_get().orc_forward(ctypes.byref(s), _d(C), int(src[0]), int(src[1]), _d(w),
-                              rx_ix.size, _i(rx_ix), _i(rx_iz), _d(out)), "forward")
+    r, rp = _rho(p, rho)
+    _check(_get().orc_forward_rho(ctypes.byref(s), _d(C), rp, int(src[0]), int(src[1]), _d(w),
+                                  rx_ix.size, _i(rx_ix), _i(rx_iz), _d(out)), "forward")
     return out
 
 
-def adjoint_probe(p: Problem, C, rx_ix, rx_iz, q, probe) -> np.ndarray:
+def adjoint_probe(p: Problem, C, rx_ix, rx_iz, q, probe, rho=None) -> np.ndarray:
     """Adjoint field ``lam[t]`` at node ``probe`` for receiver series ``q[nt][n_rx]``."""
     s = p.c_struct()
     C, q = _f64(C), _f64(q)
     rx_ix, rx_iz = _i32(rx_ix), _i32(rx_iz)
     assert q.shape == (p.nt, rx_ix.size)
     out = np.zeros(p.nt)
-    _check(_get().orc_adjoint_probe(ctypes.byref(s), _d(C), rx_ix.size, _i(rx_ix), _i(rx_iz),
-                                    _d(q), int(probe[0]), int(probe[1]), _d(out)), "adjoint_probe")
+    r, rp = _rho(p, rho)
+    _check(_get().orc_adjoint_probe_rho(ctypes.byref(s), _d(C), rp, rx_ix.size, _i(rx_ix), _i(rx_iz),
+                                        _d(q), int(probe[0]), int(probe[1]), _d(out)), "adjoint_probe")
     return out
 
 
 def misfit_gradient(p: Problem, C, tx_ix, tx_iz, wavelet, rx_ix, rx_iz, M_obs, ckpt: int = 0,
-                    return_traces: bool = False):
+                    return_traces: bool = False, rho=None):
     """Misfit ``J`` and gradient ``g = dJ/dC`` (``[nz][nx]``) of one map.
 
     ``tx_ix, tx_iz``: ``[n_tx]``; ``wavelet``: ``[nt]`` or ``[n_tx][nt]``;
     ``rx_ix, rx_iz``: ``[n_tx][n_rx]``; ``M_obs``: ``[n_tx][nt][n_rx]``;
-    ``ckpt``: snapshot interval of the forward fields (0 = keep all).
+    ``ckpt``: snapshot interval of the forward fields (0 = keep all);
+    ``rho``: optional density map ``[nz][nx]`` (variable-density operator).
     """
     s = p.c_struct()
     C = _f64(C)
@@ -194,9 +246,10 @@ def misfit_gradient(p: Problem, C, tx_ix, tx_iz, wavelet, rx_ix, rx_iz, M_obs, c
     J = np.zeros(1)
     g = np.zeros((p.nz, p.nx))
     M_sim = np.zeros((n_tx, p.nt, n_rx))
-    _check(_get().orc_misfit_gradient(ctypes.byref(s), _d(C), n_tx, _i(tx_ix), _i(tx_iz),
-                                      _d(w), n_wav, n_rx, _i(rx_ix), _i(rx_iz), _d(M_obs),
-                                      int(ckpt), _d(J), _d(g), _d(M_sim)), "misfit_gradient")
+    r, rp = _rho(p, rho)
+    _check(_get().orc_misfit_gradient_rho(ctypes.byref(s), _d(C), rp, n_tx, _i(tx_ix), _i(tx_iz),
+                                          _d(w), n_wav, n_rx, _i(rx_ix), _i(rx_iz), _d(M_obs),
+                                          int(ckpt), _d(J), _d(g), _d(M_sim)), "misfit_gradient")
     if return_traces:
         return float(J[0]), g, M_sim
     return float(J[0]), g

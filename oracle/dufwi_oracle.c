@@ -34,6 +34,16 @@
  *   - Source: a point source w(t) at one node, S[t] = dt^2 w((t-1) dt)/dx^2,
  *     i.e. the step that produces U[t+1] adds dt^2 w[t]/dx^2 at the node.
  *   - Receivers record M[t][r] = U[t](x_r) for t = 0..nt-1, U[0] = U[-1] = 0.
+ *   - Variable density (Eq. 1 with rho(x,z)): the density term
+ *     rho div((1/rho) grad u) is discretised on a staggered grid,
+ *     D-_x(b D+_x u) + D-_z(b D+_z u), divided by dx^2. D+ and D- are the
+ *     textbook staggered first differences of the same order as the
+ *     Laplacian; the buoyancy b = 1/rho at a half point is the inverse of the
+ *     mean density of its two nodes; b = 0 at half points outside the padded
+ *     grid. rho multiplies at the node: kappa = rho C^2 dt^2/(1 + D dt). The
+ *     density is extended into the absorbing layer by edge replication. With
+ *     no density array the compact Laplacian above is used (constant rho,
+ *     which then drops out).
  *   - Misfit J = sum over transmits, samples and receivers of
  *     (M_sim - M_obs)^2 (Eq. 5 data term, lambda = 0); g = dJ/dC (Eq. 6), the
  *     exact gradient of the discrete J, obtained with the discrete adjoint.
@@ -138,8 +148,8 @@ int orc_pad(const orc_problem *p, const double *C, double *Cpad)
 
 /* The three element-wise coefficient maps of Eq. 2:
  *   a = (2 - D^2 dt^2)/(1 + D dt), b = (D dt - 1)/(1 + D dt),
- *   kappa = C^2 dt^2/(1 + D dt). */
-static void coefficient_maps(const orc_problem *p, const double *Cpad, const double *D,
+ *   kappa = rho C^2 dt^2/(1 + D dt)  (rho = 1 without a density map). */
+static void coefficient_maps(const orc_problem *p, const double *Cpad, const double *rho_pad, const double *D,
                              double *a, double *b, double *kappa)
 {
     size_t n = (size_t)padded_nx(p) * padded_nz(p);
@@ -148,7 +158,7 @@ static void coefficient_maps(const orc_problem *p, const double *Cpad, const dou
         double den = 1.0 + D[i] * dt;
         a[i] = (2.0 - D[i] * D[i] * dt * dt) / den;
         b[i] = (D[i] * dt - 1.0) / den;
-        kappa[i] = Cpad[i] * Cpad[i] * dt * dt / den;
+        kappa[i] = (rho_pad ? rho_pad[i] : 1.0) * Cpad[i] * Cpad[i] * dt * dt / den;
     }
 }
 
@@ -174,14 +184,111 @@ int orc_laplacian(const orc_problem *p, const double *u, double *out)
     return ORC_OK;
 }
 
+/* Staggered first-difference weights of order 2, 4, 6 or 8: s[k-1]
+ * multiplies u(x + (k - 1/2) dx) - u(x - (k - 1/2) dx), k = 1..order/2
+ * (the Taylor weights of the centred derivative on a half-shifted grid). */
+int orc_stagger_coeffs(int order, double *s)
+{
+    switch (order) {
+    case 2:
+        s[0] = 1.0;
+        return ORC_OK;
+    case 4:
+        s[0] = 9.0 / 8.0; s[1] = -1.0 / 24.0;
+        return ORC_OK;
+    case 6:
+        s[0] = 75.0 / 64.0; s[1] = -25.0 / 384.0; s[2] = 3.0 / 640.0;
+        return ORC_OK;
+    case 8:
+        s[0] = 1225.0 / 1024.0; s[1] = -245.0 / 3072.0; s[2] = 49.0 / 5120.0;
+        s[3] = -5.0 / 7168.0;
+        return ORC_OK;
+    default:
+        return ORC_EINVAL;
+    }
+}
+
+/* Buoyancy at the half points of the padded grid:
+ *   bx[z][x] = b at (x + 1/2, z) = 2 / (rho[z][x] + rho[z][x+1]),  x < nxp - 1
+ *   bz[z][x] = b at (x, z + 1/2) = 2 / (rho[z][x] + rho[z+1][x]),  z < nzp - 1
+ * and 0 at the half point past the last node of each row or column. */
+int orc_buoyancy(const orc_problem *p, const double *rho, double *bx, double *bz)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p);
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            size_t i = (size_t)z * nxp + x;
+            bx[i] = x < nxp - 1 ? 2.0 / (rho[i] + rho[i + 1]) : 0.0;
+            bz[i] = z < nzp - 1 ? 2.0 / (rho[i] + rho[i + nxp]) : 0.0;
+        }
+    return ORC_OK;
+}
+
+/* u at (z, x) with zero outside the padded grid. */
+static double u_at(const double *u, int nxp, int nzp, int z, int x)
+{
+    return (x >= 0 && x < nxp && z >= 0 && z < nzp) ? u[(size_t)z * nxp + x] : 0.0;
+}
+
+/* Flux b D+u at the x half point (j + 1/2, z), zero where b is outside. */
+static double flux_x(const double *bx, const double *u, int nxp, int nzp, const double *s, int h, int z, int j)
+{
+    if (j < 0 || j >= nxp) return 0.0;
+    double d = 0.0;
+    for (int k = 1; k <= h; ++k) d += s[k - 1] * (u_at(u, nxp, nzp, z, j + k) - u_at(u, nxp, nzp, z, j - k + 1));
+    return bx[(size_t)z * nxp + j] * d;
+}
+
+static double flux_z(const double *bz, const double *u, int nxp, int nzp, const double *s, int h, int j, int x)
+{
+    if (j < 0 || j >= nzp) return 0.0;
+    double d = 0.0;
+    for (int k = 1; k <= h; ++k) d += s[k - 1] * (u_at(u, nxp, nzp, j + k, x) - u_at(u, nxp, nzp, j - k + 1, x));
+    return bz[(size_t)j * nxp + x] * d;
+}
+
+/* out = (1/dx^2) [D-_x (bx D+_x u) + D-_z (bz D+_z u)] on the padded grid:
+ * D- of a flux f at node x is sum_k s_k (f(x + k - 1/2) - f(x - k + 1/2)). */
+int orc_div_b_grad(const orc_problem *p, const double *bx, const double *bz, const double *u, double *out)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p);
+    int h = p->fd_order / 2;
+    double s[4];
+    if (orc_stagger_coeffs(p->fd_order, s) != ORC_OK) return ORC_EINVAL;
+    double inv_dx2 = 1.0 / (p->dx * p->dx);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            double acc = 0.0;
+            for (int k = 1; k <= h; ++k) {
+                acc += s[k - 1] * (flux_x(bx, u, nxp, nzp, s, h, z, x + k - 1) - flux_x(bx, u, nxp, nzp, s, h, z, x - k));
+                acc += s[k - 1] * (flux_z(bz, u, nxp, nzp, s, h, z + k - 1, x) - flux_z(bz, u, nxp, nzp, s, h, z - k, x));
+            }
+            out[(size_t)z * nxp + x] = acc * inv_dx2;
+        }
+    return ORC_OK;
+}
+
+/* The spatial operator of one simulation: the compact Laplacian (constant
+ * density), or the staggered density operator when bx, bz are given. */
+typedef struct {
+    const double *bx, *bz;
+} orc_op;
+
+static void apply_op(const orc_problem *p, const orc_op *op, const double *u, double *out)
+{
+    if (op && op->bx) orc_div_b_grad(p, op->bx, op->bz, u, out);
+    else orc_laplacian(p, u, out);
+}
+
 /* One application of Eq. 2 without the source:
  *   next = a*cur + b*prev + kappa*lap(cur). lapc receives lap(cur). */
-static void eq2_step(const orc_problem *p, const double *a, const double *b,
+static void eq2_step(const orc_problem *p, const orc_op *op, const double *a, const double *b,
                      const double *kappa, const double *cur, const double *prev,
                      double *next, double *lapc)
 {
     size_t n = (size_t)padded_nx(p) * padded_nz(p);
-    orc_laplacian(p, cur, lapc);
+    apply_op(p, op, cur, lapc);
     for (size_t i = 0; i < n; ++i)
         next[i] = a[i] * cur[i] + b[i] * prev[i] + kappa[i] * lapc[i];
 }
@@ -201,39 +308,81 @@ static int valid_problem(const orc_problem *p)
     return orc_fd_coeffs(p->fd_order, c) == ORC_OK;
 }
 
+/* Density of one map on the padded grid and its half-point buoyancies
+ * (rho == NULL: constant density, compact Laplacian). */
+typedef struct {
+    double *rho_pad, *bx, *bz;
+    orc_op op;
+} orc_medium;
+
+static void medium_free(orc_medium *m)
+{
+    free(m->rho_pad); free(m->bx); free(m->bz);
+    memset(m, 0, sizeof(*m));
+}
+
+static int medium_init(const orc_problem *p, const double *rho, orc_medium *m)
+{
+    memset(m, 0, sizeof(*m));
+    if (!rho) return ORC_OK;
+    for (size_t i = 0; i < (size_t)p->nx * p->nz; ++i)
+        if (!(rho[i] > 0.0) || !isfinite(rho[i])) return ORC_EINVAL;
+    size_t n = (size_t)padded_nx(p) * padded_nz(p);
+    m->rho_pad = malloc(n * sizeof(double));
+    m->bx = malloc(n * sizeof(double));
+    m->bz = malloc(n * sizeof(double));
+    if (!m->rho_pad || !m->bx || !m->bz) { medium_free(m); return ORC_ENOMEM; }
+    orc_pad(p, rho, m->rho_pad);
+    orc_buoyancy(p, m->rho_pad, m->bx, m->bz);
+    m->op.bx = m->bx;
+    m->op.bz = m->bz;
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Forward model of one transmit, Eqs. 2-3: a point source at (sx, sz)
  * driven by w[0..nt-1], traces M[t][r] = U[t] at the receivers. */
-int orc_forward(const orc_problem *p, const double *C,
-                int sx, int sz, const double *w,
-                int n_rx, const int *rx_ix, const int *rx_iz,
-                double *traces /* [nt][n_rx] */)
+int orc_forward_rho(const orc_problem *p, const double *C, const double *rho,
+                    int sx, int sz, const double *w,
+                    int n_rx, const int *rx_ix, const int *rx_iz,
+                    double *traces /* [nt][n_rx] */)
 {
     if (!valid_problem(p)) return ORC_EINVAL;
+    orc_medium med;
+    int mrc = medium_init(p, rho, &med);
+    if (mrc) return mrc;
     size_t n = (size_t)padded_nx(p) * padded_nz(p), src;
     if (node_index(p, sx, sz, &src)) return ORC_EINVAL;
     size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
     double *buf = calloc(n * 9, sizeof(double));
-    if (!rx || !buf) { free(rx); free(buf); return ORC_ENOMEM; }
+    if (!rx || !buf) { free(rx); free(buf); medium_free(&med); return ORC_ENOMEM; }
     for (int r = 0; r < n_rx; ++r)
-        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { free(rx); free(buf); return ORC_EINVAL; }
+        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { free(rx); free(buf); medium_free(&med); return ORC_EINVAL; }
     double *D = buf, *Cpad = buf + n, *a = buf + 2 * n, *b = buf + 3 * n, *kap = buf + 4 * n;
     double *prev = buf + 5 * n, *cur = buf + 6 * n, *next = buf + 7 * n, *lap = buf + 8 * n;
     orc_damping(p, D);
     orc_pad(p, C, Cpad);
-    coefficient_maps(p, Cpad, D, a, b, kap);
+    coefficient_maps(p, Cpad, med.rho_pad, D, a, b, kap);
     double src_scale = p->dt * p->dt / (p->dx * p->dx);
 
     for (int t = 0; t < p->nt; ++t) {
         /* cur holds U[t] */
         for (int r = 0; r < n_rx; ++r) traces[(size_t)t * n_rx + r] = cur[rx[r]];
         if (t == p->nt - 1) break;
-        eq2_step(p, a, b, kap, cur, prev, next, lap);
+        eq2_step(p, &med.op, a, b, kap, cur, prev, next, lap);
         next[src] += src_scale * w[t];
         double *tmp = prev; prev = cur; cur = next; next = tmp;
     }
-    free(rx); free(buf);
+    free(rx); free(buf); medium_free(&med);
     return ORC_OK;
+}
+
+int orc_forward(const orc_problem *p, const double *C,
+                int sx, int sz, const double *w,
+                int n_rx, const int *rx_ix, const int *rx_iz,
+                double *traces /* [nt][n_rx] */)
+{
+    return orc_forward_rho(p, C, NULL, sx, sz, w, n_rx, rx_ix, rx_iz, traces);
 }
 
 /* ------------------------------------------------------------------ */
@@ -242,14 +391,17 @@ int orc_forward(const orc_problem *p, const double *C,
  * fields lam[t] (t = nt-1 .. 1) obey
  *   lam[t] = R^T q[t] + a*lam[t+1] + Lap(kappa*lam[t+1]) + b*lam[t+2],
  *   lam[nt] = lam[nt+1] = 0,
- * because the Laplacian with zero exterior is a symmetric matrix. */
-static void adjoint_step(const orc_problem *p, const double *a, const double *b,
+ * because the Laplacian with zero exterior is a symmetric matrix. The
+ * staggered density operator is symmetric too: it is -G^T B G with G the
+ * D+ differences (zero exterior) and B the diagonal of half-point buoyancies,
+ * since D- = -G^T. */
+static void adjoint_step(const orc_problem *p, const orc_op *op, const double *a, const double *b,
                          const double *kappa, const double *lam1, const double *lam2,
                          double *lam0, double *work, double *lapw)
 {
     size_t n = (size_t)padded_nx(p) * padded_nz(p);
     for (size_t i = 0; i < n; ++i) work[i] = kappa[i] * lam1[i];
-    orc_laplacian(p, work, lapw);
+    apply_op(p, op, work, lapw);
     for (size_t i = 0; i < n; ++i)
         lam0[i] = a[i] * lam1[i] + lapw[i] + b[i] * lam2[i];
 }
@@ -257,32 +409,42 @@ static void adjoint_step(const orc_problem *p, const double *a, const double *b,
 /* Adjoint fields driven by receiver series q[nt][n_rx]; returns lam[t] at
  * one probe node for t = 0..nt-1 (lam[0] included for completeness).
  * For a source w at the probe node, <F w, q> = sum_t w[t] dt^2/dx^2 lam[t+1]. */
-int orc_adjoint_probe(const orc_problem *p, const double *C,
-                      int n_rx, const int *rx_ix, const int *rx_iz, const double *q,
-                      int px, int pz, double *lam_probe /* [nt] */)
+int orc_adjoint_probe_rho(const orc_problem *p, const double *C, const double *rho,
+                          int n_rx, const int *rx_ix, const int *rx_iz, const double *q,
+                          int px, int pz, double *lam_probe /* [nt] */)
 {
     if (!valid_problem(p)) return ORC_EINVAL;
+    orc_medium med;
+    int mrc = medium_init(p, rho, &med);
+    if (mrc) return mrc;
     size_t n = (size_t)padded_nx(p) * padded_nz(p), probe;
     if (node_index(p, px, pz, &probe)) return ORC_EINVAL;
     size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
     double *buf = calloc(n * 10, sizeof(double));
-    if (!rx || !buf) { free(rx); free(buf); return ORC_ENOMEM; }
+    if (!rx || !buf) { free(rx); free(buf); medium_free(&med); return ORC_ENOMEM; }
     for (int r = 0; r < n_rx; ++r)
-        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { free(rx); free(buf); return ORC_EINVAL; }
+        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { free(rx); free(buf); medium_free(&med); return ORC_EINVAL; }
     double *D = buf, *Cpad = buf + n, *a = buf + 2 * n, *b = buf + 3 * n, *kap = buf + 4 * n;
     double *l2 = buf + 5 * n, *l1 = buf + 6 * n, *l0 = buf + 7 * n, *work = buf + 8 * n, *lapw = buf + 9 * n;
     orc_damping(p, D);
     orc_pad(p, C, Cpad);
-    coefficient_maps(p, Cpad, D, a, b, kap);
+    coefficient_maps(p, Cpad, med.rho_pad, D, a, b, kap);
     /* l1 = lam[t+1], l2 = lam[t+2] */
     for (int t = p->nt - 1; t >= 0; --t) {
-        adjoint_step(p, a, b, kap, l1, l2, l0, work, lapw);
+        adjoint_step(p, &med.op, a, b, kap, l1, l2, l0, work, lapw);
         for (int r = 0; r < n_rx; ++r) l0[rx[r]] += q[(size_t)t * n_rx + r];
         lam_probe[t] = l0[probe];
         double *tmp = l2; l2 = l1; l1 = l0; l0 = tmp;
     }
-    free(rx); free(buf);
+    free(rx); free(buf); medium_free(&med);
     return ORC_OK;
+}
+
+int orc_adjoint_probe(const orc_problem *p, const double *C,
+                      int n_rx, const int *rx_ix, const int *rx_iz, const double *q,
+                      int px, int pz, double *lam_probe /* [nt] */)
+{
+    return orc_adjoint_probe_rho(p, C, NULL, n_rx, rx_ix, rx_iz, q, px, pz, lam_probe);
 }
 
 /* ------------------------------------------------------------------ */
@@ -301,14 +463,17 @@ int orc_adjoint_probe(const orc_problem *p, const double *C,
  * wavelet: [n_wav][nt] with n_wav = 1 (shared) or n_tx (one per transmit).
  * rx_ix, rx_iz: [n_tx][n_rx]. M_obs: [n_tx][nt][n_rx]. M_sim (optional
  * output): [n_tx][nt][n_rx]. g: [nz][nx]. */
-int orc_misfit_gradient(const orc_problem *p, const double *C,
-                        int n_tx, const int *tx_ix, const int *tx_iz,
-                        const double *wavelet, int n_wav,
-                        int n_rx, const int *rx_ix, const int *rx_iz,
-                        const double *M_obs, int ckpt,
-                        double *J, double *g, double *M_sim)
+int orc_misfit_gradient_rho(const orc_problem *p, const double *C, const double *rho,
+                            int n_tx, const int *tx_ix, const int *tx_iz,
+                            const double *wavelet, int n_wav,
+                            int n_rx, const int *rx_ix, const int *rx_iz,
+                            const double *M_obs, int ckpt,
+                            double *J, double *g, double *M_sim)
 {
     if (!valid_problem(p) || n_tx < 1 || n_rx < 0 || (n_wav != 1 && n_wav != n_tx)) return ORC_EINVAL;
+    orc_medium med;
+    int mrc = medium_init(p, rho, &med);
+    if (mrc) return mrc;
     int nxp = padded_nx(p), nzp = padded_nz(p), nt = p->nt;
     size_t n = (size_t)nxp * nzp;
     if (ckpt < 1 || ckpt > nt) ckpt = nt;
@@ -324,6 +489,7 @@ int orc_misfit_gradient(const orc_problem *p, const double *C,
     size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
     if (!base || !snap || !seg || !gpad || !trace || !q || !rx) {
         free(base); free(snap); free(seg); free(gpad); free(trace); free(q); free(rx);
+        medium_free(&med);
         return ORC_ENOMEM;
     }
     double *D = base, *Cpad = base + n, *a = base + 2 * n, *b = base + 3 * n, *kap = base + 4 * n;
@@ -331,7 +497,7 @@ int orc_misfit_gradient(const orc_problem *p, const double *C,
     double *l2 = base + 9 * n, *l1 = base + 10 * n, *l0 = base + 11 * n, *work = base + 12 * n;
     orc_damping(p, D);
     orc_pad(p, C, Cpad);
-    coefficient_maps(p, Cpad, D, a, b, kap);
+    coefficient_maps(p, Cpad, med.rho_pad, D, a, b, kap);
     double src_scale = p->dt * p->dt / (p->dx * p->dx);
     double Jsum = 0.0;
     int status = ORC_OK;
@@ -354,7 +520,7 @@ int orc_misfit_gradient(const orc_problem *p, const double *C,
             }
             for (int r = 0; r < n_rx; ++r) trace[(size_t)t * n_rx + r] = cur[rx[r]];
             if (t == nt - 1) break;
-            eq2_step(p, a, b, kap, cur, prev, next, lap);
+            eq2_step(p, &med.op, a, b, kap, cur, prev, next, lap);
             next[src] += src_scale * w[t];
             double *tmp = prev; prev = cur; cur = next; next = tmp;
         }
@@ -380,14 +546,14 @@ int orc_misfit_gradient(const orc_problem *p, const double *C,
                 double *u_t = seg + (size_t)(t - t0) * n;
                 double *u_prev = (t == t0) ? prev : seg + (size_t)(t - t0 - 1) * n;
                 double *u_next = seg + (size_t)(t - t0 + 1) * n;
-                eq2_step(p, a, b, kap, u_t, u_prev, u_next, lap);
+                eq2_step(p, &med.op, a, b, kap, u_t, u_prev, u_next, lap);
                 u_next[src] += src_scale * w[t];
             }
             /* adjoint indices t = t_hi .. t0+1 pair with U[t-1] in this segment */
             for (int t = t_hi; t >= t0 + 1; --t) {
-                adjoint_step(p, a, b, kap, l1, l2, l0, work, lap);
+                adjoint_step(p, &med.op, a, b, kap, l1, l2, l0, work, lap);
                 for (int r = 0; r < n_rx; ++r) l0[rx[r]] += q[(size_t)t * n_rx + r];
-                orc_laplacian(p, seg + (size_t)(t - 1 - t0) * n, lap);
+                apply_op(p, &med.op, seg + (size_t)(t - 1 - t0) * n, lap);
                 for (size_t i = 0; i < n; ++i) gpad[i] += l0[i] * lap[i];
                 double *tmp = l2; l2 = l1; l1 = l0; l0 = tmp;
             }
@@ -395,9 +561,9 @@ int orc_misfit_gradient(const orc_problem *p, const double *C,
         }
     }
     if (status == ORC_OK) {
-        /* chain rule through kappa = C^2 dt^2/(1 + D dt), then fold the padding */
+        /* chain rule through kappa = rho C^2 dt^2/(1 + D dt), then fold the padding */
         for (size_t i = 0; i < n; ++i)
-            gpad[i] *= 2.0 * Cpad[i] * p->dt * p->dt / (1.0 + D[i] * p->dt);
+            gpad[i] *= 2.0 * (med.rho_pad ? med.rho_pad[i] : 1.0) * Cpad[i] * p->dt * p->dt / (1.0 + D[i] * p->dt);
         memset(g, 0, sizeof(double) * (size_t)p->nx * p->nz);
         for (int z = 0; z < nzp; ++z)
             for (int x = 0; x < nxp; ++x) {
@@ -407,5 +573,17 @@ int orc_misfit_gradient(const orc_problem *p, const double *C,
         *J = Jsum;
     }
     free(base); free(snap); free(seg); free(gpad); free(trace); free(q); free(rx);
+    medium_free(&med);
     return status;
+}
+
+int orc_misfit_gradient(const orc_problem *p, const double *C,
+                        int n_tx, const int *tx_ix, const int *tx_iz,
+                        const double *wavelet, int n_wav,
+                        int n_rx, const int *rx_ix, const int *rx_iz,
+                        const double *M_obs, int ckpt,
+                        double *J, double *g, double *M_sim)
+{
+    return orc_misfit_gradient_rho(p, C, NULL, n_tx, tx_ix, tx_iz, wavelet, n_wav, n_rx, rx_ix, rx_iz, M_obs,
+                                   ckpt, J, g, M_sim);
 }

@@ -117,19 +117,38 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_traffic(kind: str):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+STEP_KERNEL_MARK = ("// <one-step kernel source>\n", "// </one-step kernel source>\n")
+
+
+def step_kernel_source_sha256() -> str:
+    """SHA-256 of the one-step kernel's source: the marked regions of dufwi_kernels.cu (its
+    device helpers, the kernel and its launchers), concatenated in file order."""
     src = os.path.join(ROOT, "paper_2603_04070_gb300", "csrc", "dufwi_kernels.cu")
+    with open(src) as f:
+        text = f.read()
+    b, e = STEP_KERNEL_MARK
+    parts, pos = [], 0
+    while True:
+        i = text.find(b, pos)
+        if i < 0:
+            break
+        j = text.index(e, i)
+        parts.append(text[i + len(b):j])
+        pos = j + len(e)
+    return hashlib.sha256("".join(parts).encode()).hexdigest()
+
+
+def kernel_traffic(kind: str, key: str = "per_launch_dram_bytes_full_size"):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the current one-step kernel source (else None). key selects the cold-cache figure
+    (ncu's default) or the warm-L2 one (per_launch_dram_bytes_warm_l2)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        if rec.get("kernel_source_sha256") != sha:
+        if rec.get("step_kernel_source_sha256") != step_kernel_source_sha256():
             return None
-        return rec.get("per_launch_dram_bytes_full_size", {}).get(kind)
+        return rec.get(key, {}).get(kind)
     except Exception:
         return None
 
@@ -278,7 +297,9 @@ def run_ours(args):
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "step_kernel (%s sweep)" % dom, "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": kernel_traffic(dom), "algorithmic_bytes_per_launch": bytes_per_launch,
+                "traffic": kernel_traffic(dom),
+                "traffic_warm_l2": kernel_traffic(dom, "per_launch_dram_bytes_warm_l2"),
+                "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": 1e3 * avg_launch_ms,
                 "sweep_ms_per_step": {k: prof[k]["ms"] / args.steps for k in kinds + ["other"]},
                 "launches_per_step": {k: prof[k]["launches"] / args.steps for k in kinds + ["other"]}}

@@ -40,6 +40,36 @@ bool stencil_weights(int order, float c[5])
     }
 }
 
+// Staggered first-difference weights of the variable-density operator (textbook values).
+bool stagger_weights(int order, float sw[4])
+{
+    for (int i = 0; i < 4; ++i) sw[i] = 0.f;
+    switch (order) {
+    case 2: sw[0] = 1.0f; return true;
+    case 4: sw[0] = (float)(9.0 / 8.0); sw[1] = (float)(-1.0 / 24.0); return true;
+    case 6: sw[0] = (float)(75.0 / 64.0); sw[1] = (float)(-25.0 / 384.0); sw[2] = (float)(3.0 / 640.0); return true;
+    case 8:
+        sw[0] = (float)(1225.0 / 1024.0); sw[1] = (float)(-245.0 / 3072.0); sw[2] = (float)(49.0 / 5120.0);
+        sw[3] = (float)(-5.0 / 7168.0);
+        return true;
+    default: return false;
+    }
+}
+
+// Leapfrog limit of the staggered operator in 2-D: its 1-D symbol peaks at the Nyquist
+// wavenumber with magnitude 4 (sum_k s_k (-1)^(k+1))^2.
+double stagger_stability_limit(int order)
+{
+    static const double w[4][4] = {{1.0, 0, 0, 0},
+                                   {9.0 / 8.0, -1.0 / 24.0, 0, 0},
+                                   {75.0 / 64.0, -25.0 / 384.0, 3.0 / 640.0, 0},
+                                   {1225.0 / 1024.0, -245.0 / 3072.0, 49.0 / 5120.0, -5.0 / 7168.0}};
+    if (order != 2 && order != 4 && order != 6 && order != 8) return -1.0;
+    double a = 0.0;
+    for (int k = 1; k <= order / 2; ++k) a += w[order / 2 - 1][k - 1] * ((k & 1) ? 1.0 : -1.0);
+    return 2.0 / sqrt(2.0 * 4.0 * a * a);
+}
+
 double stability_limit(int order)
 {
     static const double w[4][5] = {{-2.0, 1.0, 0, 0, 0},
@@ -60,7 +90,7 @@ struct Layout {
     // byte offsets into the workspace
     int tiles1, tiles2;      // tiles of the one-step kernel (tile height TZ) and of the two-step kernel
     int n_rxe;               // row length of the grown-tile receiver lists (4 n_rx)
-    size_t o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
+    size_t o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
 };
 
@@ -144,6 +174,8 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     L->o_sortede = take(sizeof(int) * (size_t)L->n_tx * L->n_rxe);
     L->o_damp = take(sizeof(float2) * (size_t)(L->P + 1) * (L->P + 1));
     L->o_kap = take((size_t)n_maps * L->slice * sizeof(float));
+    L->o_bx = take((size_t)n_maps * L->slice * sizeof(float));     // buoyancies (density maps only)
+    L->o_bz = take((size_t)n_maps * L->slice * sizeof(float));
     for (int i = 0; i < 4; ++i) L->o_f[i] = take(field);
     if (gradient) {
         const bool store_all = pb->ckpt_interval == 0 || pb->ckpt_interval >= steps;
@@ -280,10 +312,13 @@ constexpr size_t kProfEvents = 1 << 14;
 
 // Tensor maps of one field buffer: read with halo by the one-step kernel (box1, 72 x (TZ + 8)),
 // updated in place by it (tile1, 64 x TZ), read with halo by the two-step kernel (box2, 80 x 48)
-// and read on the grown tile by it (ring2, 72 x 40).
+// and read on the grown tile by it (ring2, 72 x 40). The variable-density kernel reads the same
+// 80 x 48 box (halo 8) around its 64 x 32 tiles.
 struct FieldMaps {
     CUtensorMap box1, tile1, box2, ring2;
 };
+static_assert(kTileX + 4 * kHalo == kVBoxX && kPairTileZ + 4 * kHalo == kVBoxZ,
+              "the two-step box doubles as the variable-density box");
 
 struct Ctx {
     Layout L;
@@ -295,8 +330,9 @@ struct Ctx {
     bool two_step;
     const dufwi_map_sizes *sizes = nullptr;   // sized calls: per-map grids inside the envelope
     bool jvp = false;                         // linearised forward (Born) call
+    bool vd = false;                          // density map given: staggered variable-density operator
     FieldMaps fmap[4], mmap[4];
-    CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1;
+    CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1, bx1, bz1;
     int *status() const { return reinterpret_cast<int *>(ws + L.o_status); }
     template <typename T> T *at(size_t o) const { return reinterpret_cast<T *>(ws + o); }
 };
@@ -367,8 +403,11 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (rc) return rc;
     c.ws = static_cast<char *>(workspace);
     c.st = static_cast<cudaStream_t>(stream);
-    c.tz = g_tile_z;
-    c.two_step = g_two_step != 0 && !c.sizes && !c.jvp;
+    c.vd = density != nullptr;
+    if (c.vd && c.jvp) return DUFWI_ERR_UNSUPPORTED;   // no Born step for the density operator
+    if (c.vd && c.pb->c_max * c.pb->dt / c.pb->dx > stagger_stability_limit(c.pb->fd_order)) return DUFWI_ERR_CFL;
+    c.tz = c.vd ? kVTileZ : g_tile_z;
+    c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd;
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
     std::vector<int> sorted1, sorted2, sortede;
@@ -431,8 +470,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
 
     long long nl = 0;
     const int e0 = g_prof.mark(c.st);
-    CKL(launch_setup_kappa(sos, density, c.at<float>(L.o_kap), c.status(), L.n_maps, L.Nx, L.Nz, L.P, L.nxp, L.nzp,
-                           L.pitch, pb->dt / pb->dx, d0, pb->dt, pb->c_max,
+    CKL(launch_setup_kappa(sos, density, c.at<float>(L.o_kap), c.at<float>(L.o_bx), c.at<float>(L.o_bz), c.status(),
+                           L.n_maps, L.Nx, L.Nz, L.P, L.nxp, L.nzp, L.pitch, pb->dt / pb->dx, d0, pb->dt, pb->c_max,
                            c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
 
@@ -442,6 +481,9 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
         if (field_maps(&c.fmap[i], c.at<float>(L.o_f[i]), L, c.tz)) return DUFWI_ERR_CUDA;
     if (tensor_map(&c.kap1, kap, L, L.n_maps, 0, kTileX, c.tz) ||
         tensor_map(&c.kap2, kap, L, L.n_maps, 0, kTileX + 2 * kHalo, kPairTileZ + 2 * kHalo))
+        return DUFWI_ERR_CUDA;
+    if (c.vd && (tensor_map(&c.bx1, c.at<float>(L.o_bx), L, L.n_maps, 0, kVFxX, kVTileZ) ||
+                 tensor_map(&c.bz1, c.at<float>(L.o_bz), L, L.n_maps, 0, kTileX, kVFzZ)))
         return DUFWI_ERR_CUDA;
     if (c.jvp) {
         for (int i = 0; i < 4; ++i)
@@ -473,6 +515,7 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     p.damp_tab = c.at<float2>(L.o_damp);
     p.map_dims = c.sizes ? c.at<int2>(L.o_mapdims) : nullptr;
     stencil_weights(pb->fd_order, p.c);
+    stagger_weights(pb->fd_order, p.sw);
     p.tile_z = c.tz;
     p.rxe_tab = c.at<int2>(L.o_tabe);
     p.rxe_sorted = c.at<int>(L.o_sortede);
@@ -509,7 +552,14 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
     p.out = rg.buf[rg.prv];
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
-    CKL(launch_step(c.L.radius, mode, tm, p, c.st));
+    if (c.vd) {   // the tile height is 32 here, so tile1, kap1, hist1 and grad1 fit the kernel
+        tm.cur_box = rg.map[rg.cur].box2;
+        tm.bx_tile = c.bx1;
+        tm.bz_tile = c.bz1;
+        CKL(launch_step_vd(c.L.radius, mode, tm, p, c.st));
+    } else {
+        CKL(launch_step(c.L.radius, mode, tm, p, c.st));
+    }
     std::swap(rg.cur, rg.prv);
     return DUFWI_OK;
 }

@@ -8,6 +8,9 @@
 //   kappa  [n_maps][nzp][pitch] float: kappa' = C^2 dt^2 / (dx^2 (1 + D dt)), the Eq. 2
 //          coefficient with the 1/dx^2 of the Laplacian folded in. It is computed once per call
 //          in FP64 and rounded once.
+//   bx, bz [n_maps][nzp][pitch] float: buoyancy 1/rho at the half points (x + 1/2, z) and
+//          (x, z + 1/2), 2 / (rho + rho_neighbour) in FP64 rounded once; 0 past the last node of
+//          a row (bx) or column (bz). Used only with a density map (variable-density operator).
 //   node   packed (zp << 16) | xp padded-grid node of an element.
 #pragma once
 
@@ -21,6 +24,15 @@ constexpr int kTileX = 64;                    // output tile width (x, contiguou
 constexpr int kHalo = 4;                      // halo loaded on every side (max stencil radius)
 constexpr int kBoxX = kTileX + 2 * kHalo;     // TMA box: 72 floats = 288 bytes per row
 constexpr int kTileZDefault = 32;             // output tile height (z): 32 or 64
+
+// Variable-density step (staggered operator of Eq. 1): 64 x 32 output tiles, a halo of 8 for the
+// U^n box (two staggered differences of radius up to 4) and of 4 for the half-point buoyancies.
+constexpr int kVHalo = 2 * kHalo;             // 8
+constexpr int kVTileZ = 32;
+constexpr int kVBoxX = kTileX + 2 * kVHalo;   // 80 floats = 320 bytes per row
+constexpr int kVBoxZ = kVTileZ + 2 * kVHalo;  // 48
+constexpr int kVFxX = kTileX + 2 * kHalo;     // 72 x-half-points per row: x0 - 4 + i + 1/2
+constexpr int kVFzZ = kVTileZ + 2 * kHalo;    // 40 z-half-point rows: z0 - 4 + j + 1/2
 
 // Step kernel variants.
 enum StepMode : int {
@@ -38,8 +50,10 @@ enum StepMode : int {
 //   hist_tile history ring: dims (nxp, nzp, S, n_hist), box 64 x TZ x 1 x 1 (adjoint only)
 //   grad_tile imaging sums: dims (nxp, nzp, S), box 64 x TZ x 1 (adjoint); in the Born step the
 //             perturbation dkappa': dims (nxp, nzp, n_maps), box 64 x TZ x 1
+//   bx_tile, bz_tile  variable-density step only: buoyancies, dims (nxp, nzp, n_maps), boxes
+//             72 x 32 x 1 (from x0 - 4) and 64 x 40 x 1 (from z0 - 4); cur_box is then 80 x 48
 struct StepMaps {
-    CUtensorMap cur_box, out_tile, kap_tile, hist_tile, grad_tile;
+    CUtensorMap cur_box, out_tile, kap_tile, hist_tile, grad_tile, bx_tile, bz_tile;
 };
 
 struct StepParams {
@@ -74,6 +88,7 @@ struct StepParams {
     const int2 *map_dims;    // sized calls: [n_maps] (Nx, Nz) of each map; null for a uniform call
     const float2 *damp_tab;  // [P + 1][P + 1]: (a - 2, b + 1) at layer depths (dz, dx) in cells
     float c[5];              // central stencil weights, c[0] the centre weight of one axis
+    float sw[4];             // staggered first-difference weights s_1..s_R (variable density)
 };
 
 // Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.
@@ -81,8 +96,12 @@ cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepPara
 // Two time steps per launch (core tiles 64 x 32; see step2_kernel).
 cudaError_t launch_step2(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 constexpr int kPairTileZ = 32;   // core tile height of the two-step kernel (64 x 32 tiles)
-cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, int *status,
-                               int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch,
+// Variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint; 64 x 32 tiles).
+cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
+// kappa' on the padded grid; with a density map kappa' = rho C^2 dt^2/(dx^2 (1 + D dt)), and the
+// buoyancies bx, bz are written too (both may be null without a density map).
+cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, float *bx, float *bz,
+                               int *status, int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch,
                                double dt_over_dx, double d0, double dt, double c_max,
                                const int2 *map_dims, cudaStream_t st);
 cudaError_t launch_sample(const float *field, const int *rx_node, float *cd, long long slice,

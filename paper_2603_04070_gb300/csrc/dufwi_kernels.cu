@@ -30,6 +30,7 @@
 namespace dufwi {
 
 namespace {
+// <one-step kernel source>
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -481,6 +482,218 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     }
 }
 
+// </one-step kernel source>
+
+// ---- variable density (Eq. 1 with rho(x, z)) ---------------------------------------------------
+// The density term rho div(b grad u), b = 1/rho, on a staggered grid. Fluxes at half points,
+//   f_x(j + 1/2) = b_x(j) sum_k s_k (u(j + k) - u(j - k + 1)),
+// and their divergence at the nodes, L u(x) = sum_k s_k (f_x(x + k - 1/2) - f_x(x - k + 1/2)) + the
+// same along z; kappa' carries rho and 1/dx^2. With u = 0 and b = 0 outside the padded grid
+// (the TMA zero fill, and b = 0 stored past the last node), L = -G^T B G is symmetric, so the
+// adjoint in mu = kappa' lambda form is again the forward update, and the imaging term is
+// mu^m L U^{m-1} as for the compact Laplacian.
+//
+// One CTA: a 64 x 32 output tile of one shot, 128 threads. TMA brings the 80 x 48 box of U^n and
+// the 72 x 32 and 64 x 40 tiles of half-point buoyancies (plus U^{n-1}, kappa' and, in the
+// adjoint, the history and the imaging sums) onto one mbarrier. Phase 1 turns the buoyancy tiles
+// into fluxes in place (four half points per work item, 128-bit shared-memory accesses);
+// phase 2 forms 4 x 4 divergences per thread and runs the common Eq. 2 epilogue.
+template <int MODE>
+struct VdLayout {
+    static constexpr int kBox = kVBoxX * kVBoxZ;
+    static constexpr int kFx = kVFxX * kVTileZ;
+    static constexpr int kFz = kTileX * kVFzZ;
+    static constexpr int kTile = kTileX * kVTileZ;
+    static constexpr int kTiles = MODE == kAdjoint ? 4 : 2;
+    static constexpr int kFloats = kBox + kFx + kFz + kTiles * kTile;
+    static constexpr uint32_t kBytes = kFloats * sizeof(float);
+};
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(128, 3) vd_step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
+{
+    using VL = VdLayout<MODE>;
+    constexpr int TZ = kVTileZ;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ InjList inj;
+
+    const int tid = threadIdx.x;
+    const int s = blockIdx.z;
+    const int x0 = blockIdx.x * kTileX;
+    const int z0 = blockIdx.y * TZ;
+    const int tx_idx = s % p.n_tx;
+    const int map = s / p.n_tx;
+    const long long shot_off = static_cast<long long>(s) * p.slice;
+    float *box = smem;
+    float *fx = box + VL::kBox;
+    float *fz = fx + VL::kFx;
+    float *pv = fz + VL::kFz;
+    float *kp = pv + VL::kTile;
+    float *hs = kp + VL::kTile;
+    float *gg = hs + VL::kTile;
+    const MapGrid mg = map_grid(p, map);
+    if (x0 >= mg.nxp || z0 >= mg.nzp) return;
+
+    grid_dependency_wait();
+    if (tid == 0) {
+        prefetch_tensormap(&tm.cur_box);
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, VL::kBytes);
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - kVHalo, z0 - kVHalo, s);
+        tma_load_3d(fx, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
+        tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
+        tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+        tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+        if (MODE == kAdjoint) {
+            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        }
+    }
+    grid_dependents_launch();
+
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    int2 rx_range = make_int2(0, 0);
+    if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
+    gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
+                            tid, 128);
+
+    const int lx = (tid & 15) * 4;
+    const int lz = (tid >> 4) * 4;
+    const int gx = x0 + lx;
+    const bool interior = region_interior(p, mg, x0, z0, kTileX, TZ);
+    int xd[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, mg.Nx);
+
+    if (!wait_tile(&bar, p, tid)) return;
+
+    // phase 1a: x fluxes at half points x0 - 4 + i + 1/2 (i = 0..71), rows z0 .. z0 + 31. The
+    // half point i needs box columns i + 4 + k and i + 5 - k (box column 0 is x0 - 8).
+    for (int e = tid; e < (kVFxX / 4) * TZ; e += 128) {
+        const int zz = e / (kVFxX / 4), i = (e % (kVFxX / 4)) * 4;
+        const float *row = box + (zz + kVHalo) * kVBoxX + i;
+        const float4 a = ld4s(row), b = ld4s(row + 4), c = ld4s(row + 8);
+        const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+        float d[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], w[q + 4 + k] - w[q + 5 - k], acc);
+            d[q] = acc;
+        }
+        float *f = fx + zz * kVFxX + i;
+        const float4 bb = ld4s(f);
+        st4s(f, make_float4(bb.x * d[0], bb.y * d[1], bb.z * d[2], bb.w * d[3]));
+    }
+    // phase 1b: z fluxes at half points z0 - 4 + j + 1/2 (j = 0..39), columns x0 .. x0 + 63; the
+    // half point j needs box rows j + 4 + k and j + 5 - k.
+    for (int e = tid; e < (kTileX / 4) * kVFzZ; e += 128) {
+        const int j = e / (kTileX / 4), xx = (e % (kTileX / 4)) * 4;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+            const float4 up = ld4s(box + (j + 4 + k) * kVBoxX + xx + kVHalo);
+            const float4 dn = ld4s(box + (j + 5 - k) * kVBoxX + xx + kVHalo);
+            const float sk = p.sw[k - 1];
+            acc.x = fmaf(sk, up.x - dn.x, acc.x);
+            acc.y = fmaf(sk, up.y - dn.y, acc.y);
+            acc.z = fmaf(sk, up.z - dn.z, acc.z);
+            acc.w = fmaf(sk, up.w - dn.w, acc.w);
+        }
+        float *f = fz + j * kTileX + xx;
+        const float4 bb = ld4s(f);
+        st4s(f, make_float4(bb.x * acc.x, bb.y * acc.y, bb.z * acc.z, bb.w * acc.w));
+    }
+    __syncthreads();
+
+    // phase 2: divergence at the 4 x 4 block (lx, lz): x fluxes lx .. lx + 10 of each row,
+    // z flux rows lz .. lz + 10 (node x uses half points x + k - 1/2 and x - k + 1/2).
+    float4 lap[4], ctr[4], nxt[4];
+    float4 zr[11];
+#pragma unroll
+    for (int r = 0; r < 11; ++r) zr[r] = ld4s(fz + (lz + r) * kTileX + lx);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float *fr = fx + (lz + j) * kVFxX + lx;
+        const float4 a = ld4s(fr), b = ld4s(fr + 4), c = ld4s(fr + 8);
+        const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+        float lxv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], w[q + k + 3] - w[q - k + 4], acc);
+            lxv[q] = acc;
+        }
+        float4 lzv = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+            const float4 up = zr[j + k + 3], dn = zr[j - k + 4];
+            const float sk = p.sw[k - 1];
+            lzv.x = fmaf(sk, up.x - dn.x, lzv.x);
+            lzv.y = fmaf(sk, up.y - dn.y, lzv.y);
+            lzv.z = fmaf(sk, up.z - dn.z, lzv.z);
+            lzv.w = fmaf(sk, up.w - dn.w, lzv.w);
+        }
+        lap[j] = make_float4(lxv[0] + lzv.x, lxv[1] + lzv.y, lxv[2] + lzv.z, lxv[3] + lzv.w);
+        ctr[j] = ld4s(box + (lz + j + kVHalo) * kVBoxX + lx + kVHalo);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int lo = (lz + j) * kTileX + lx;
+        nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
+                         p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+    }
+    if (inj.n > 0) {   // block-uniform: stage the rows, inject in list order, reload
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
+        __syncthreads();
+        if (tid == 0)
+            apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ,
+                                   kTileX);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+    }
+    const bool col_ok = gx < mg.nxp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gz = z0 + lz + j;
+        if (!col_ok || gz >= mg.nzp) continue;
+        float4 nv = nxt[j], lv = lap[j];
+        if (gx + 4 > mg.nxp) {
+            if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
+            if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
+            nv.w = 0.f; lv.w = 0.f;
+        }
+        const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+        st4(p.out + o, nv);
+        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
+        if (MODE == kAdjoint) {
+            const int lo = (lz + j) * kTileX + lx;
+            st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+        }
+    }
+
+    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+        const int cnt = (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
+        for (int e = tid; e < cnt; e += 128) {
+            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
+            const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.smp_node + tx_idx * p.n_rx + r) : -1;
+            const int zn = node >> 16, xn = node & 0xffff;
+            if (node < 0 || zn < z0 || zn >= z0 + TZ || xn < x0 || xn >= x0 + kTileX) {
+                raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                continue;
+            }
+            p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
+                box[(zn - z0 + kVHalo) * kVBoxX + (xn - x0 + kVHalo)];
+        }
+    }
+}
+
 // ---- two time steps per launch ----------------------------------------------------------------
 // Core tile 64 x 32 per CTA, 192 threads. Phase A computes U^{n+1} on the core plus a 4-cell
 // ring (72 x 40, 180 blocks of 4 x 4) from an 80 x 48 TMA box of U^n and the 72 x 40 boxes of
@@ -692,9 +905,15 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 }
 
 // kappa' = C^2 (dt/dx)^2 / (1 + D dt) on the padded grid; C extended by edge replication.
-__global__ void setup_kappa_kernel(const float *sos, const float *density, float *kap, int *status, int NxE,
-                                   int NzE, int P, int nxpE, int nzpE, int pitch, double r2, double d0, double dt,
-                                   double c_max, const int2 *map_dims)
+// kappa' (and, with a density map, the half-point buoyancies) of one padded cell. Density and
+// SoS are edge-replicated into the absorbing layer. With a density map the status word records
+// non-finite or non-positive densities, and a local effective speed above c_max. That speed is
+// C sqrt(g), with g the Gershgorin row sum of the symmetrised second-order density operator
+// along each axis relative to its value in a uniform medium; g <= 1.21 at any density step, and
+// the check guards the time step rather than proving stability.
+__global__ void setup_kappa_kernel(const float *sos, const float *density, float *kap, float *bxo, float *bzo,
+                                   int *status, int NxE, int NzE, int P, int nxpE, int nzpE, int pitch, double r2,
+                                   double d0, double dt, double c_max, const int2 *map_dims)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = blockIdx.y;
@@ -703,21 +922,43 @@ __global__ void setup_kappa_kernel(const float *sos, const float *density, float
     // grid of this map (sized calls: its own, inside the envelope slab [NzE][NxE] of the map)
     const int Nx = map_dims ? map_dims[b].x : NxE, Nz = map_dims ? map_dims[b].y : NzE;
     const int nxp = Nx + 2 * P, nzp = Nz + 2 * P;
-    float *dst = kap + (static_cast<long long>(b) * nzpE + z) * pitch + x;
-    if (x >= nxp || z >= nzp) { *dst = 0.f; return; }
-    const int xs = min(max(x - P, 0), Nx - 1), zs = min(max(z - P, 0), Nz - 1);
-    const long long src = (static_cast<long long>(b) * NzE + zs) * NxE + xs;
-    const double C = sos[src];
-    if (!isfinite(C)) raise_status(status, DUFWI_ERR_NONFINITE);
-    else if (!(C > 0.0) || C > c_max) raise_status(status, DUFWI_ERR_CFL);
-    if (density && x >= P && x < P + Nx && z >= P && z < P + Nz) {
-        if (density[src] != density[static_cast<long long>(b) * NzE * NxE]) raise_status(status, DUFWI_ERR_UNSUPPORTED);
+    const long long o = (static_cast<long long>(b) * nzpE + z) * pitch + x;
+    if (x >= nxp || z >= nzp) {
+        kap[o] = 0.f;
+        if (density) { bxo[o] = 0.f; bzo[o] = 0.f; }
+        return;
     }
+    auto src_of = [&](int xx, int zz) {
+        const int xs = min(max(xx - P, 0), Nx - 1), zs = min(max(zz - P, 0), Nz - 1);
+        return (static_cast<long long>(b) * NzE + zs) * NxE + xs;
+    };
+    const long long src = src_of(x, z);
+    const double C = sos[src];
+    double ceff = C, rho = 1.0;
+    if (density) {
+        rho = density[src];
+        const bool interior_cell = x >= P && x < P + Nx && z >= P && z < P + Nz;
+        if (interior_cell && !isfinite(rho)) raise_status(status, DUFWI_ERR_NONFINITE);
+        else if (interior_cell && !(rho > 0.0)) raise_status(status, DUFWI_ERR_INVALID_ARG);
+        const double rx = x + 1 < nxp ? static_cast<double>(density[src_of(x + 1, z)]) : rho;
+        const double rz = z + 1 < nzp ? static_cast<double>(density[src_of(x, z + 1)]) : rho;
+        const double rxm = x > 0 ? static_cast<double>(density[src_of(x - 1, z)]) : rho;
+        const double rzm = z > 0 ? static_cast<double>(density[src_of(x, z - 1)]) : rho;
+        bxo[o] = x + 1 < nxp ? static_cast<float>(2.0 / (rho + rx)) : 0.f;
+        bzo[o] = z + 1 < nzp ? static_cast<float>(2.0 / (rho + rz)) : 0.f;
+        auto row_sum = [rho](double rp, double rm) {
+            const double bp = 2.0 / (rho + rp), bm = 2.0 / (rho + rm);
+            return 0.25 * (rho * (bp + bm) + sqrt(rho * rp) * bp + sqrt(rho * rm) * bm);
+        };
+        ceff = C * sqrt(fmax(row_sum(rx, rxm), row_sum(rz, rzm)));
+    }
+    if (!isfinite(C)) raise_status(status, DUFWI_ERR_NONFINITE);
+    else if (!(C > 0.0) || C > c_max || (density && ceff > c_max)) raise_status(status, DUFWI_ERR_CFL);
     const int dxl = x < P ? P - x : (x > P + Nx - 1 ? x - (P + Nx - 1) : 0);
     const int dzl = z < P ? P - z : (z > P + Nz - 1 ? z - (P + Nz - 1) : 0);
     const double xx = static_cast<double>(dxl) / P, zz = static_cast<double>(dzl) / P;
     const double D = d0 * xx * xx + d0 * zz * zz;
-    *dst = static_cast<float>(C * C * r2 / (1.0 + D * dt));
+    kap[o] = static_cast<float>(rho * C * C * r2 / (1.0 + D * dt));
 }
 
 __global__ void sample_kernel(const float *field, const int *rx_node, float *cd, long long slice, int pitch,
@@ -932,6 +1173,7 @@ __global__ void snap_load_kernel(float *cur, float *prev, const T *su, const T *
 
 // ---- launchers ------------------------------------------------------------------------------
 
+// <one-step kernel source>
 template <int R, int MODE, int TZ>
 static cudaError_t launch_step_rmt(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
@@ -981,6 +1223,8 @@ static cudaError_t launch_step_r(int mode, const StepMaps &tm, const StepParams 
     default: return cudaErrorInvalidValue;
     }
 }
+
+// </one-step kernel source>
 
 template <int R, int MODE>
 static cudaError_t launch_step2_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
@@ -1032,6 +1276,58 @@ cudaError_t launch_step2(int radius, int mode, const StepMaps &tm, const StepPar
     }
 }
 
+template <int R, int MODE>
+static cudaError_t launch_step_vd_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    using VL = VdLayout<MODE>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(vd_step_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             VL::kBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(vd_step_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_maps * p.n_tx);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = VL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, vd_step_kernel<R, MODE>, tm, p);
+}
+
+template <int R>
+static cudaError_t launch_step_vd_r(int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    switch (mode) {
+    case kFwdSample: return launch_step_vd_rm<R, kFwdSample>(tm, p, st);
+    case kFwdSampleHist: return launch_step_vd_rm<R, kFwdSampleHist>(tm, p, st);
+    case kFwdHist: return launch_step_vd_rm<R, kFwdHist>(tm, p, st);
+    case kAdjoint: return launch_step_vd_rm<R, kAdjoint>(tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    if (p.tile_z != kVTileZ) return cudaErrorInvalidValue;
+    switch (radius) {
+    case 1: return launch_step_vd_r<1>(mode, tm, p, st);
+    case 2: return launch_step_vd_r<2>(mode, tm, p, st);
+    case 3: return launch_step_vd_r<3>(mode, tm, p, st);
+    case 4: return launch_step_vd_r<4>(mode, tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// <one-step kernel source>
 cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
     switch (radius) {
@@ -1043,12 +1339,15 @@ cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepPara
     }
 }
 
-cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, int *status, int n_maps, int Nx,
-                               int Nz, int P, int nxp, int nzp, int pitch, double dt_over_dx, double d0, double dt,
-                               double c_max, const int2 *map_dims, cudaStream_t st)
+// </one-step kernel source>
+
+cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, float *bx, float *bz, int *status,
+                               int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch, double dt_over_dx,
+                               double d0, double dt, double c_max, const int2 *map_dims, cudaStream_t st)
 {
+    if (density && (!bx || !bz)) return cudaErrorInvalidValue;
     dim3 grid((pitch + 127) / 128, nzp, n_maps);
-    setup_kappa_kernel<<<grid, 128, 0, st>>>(sos, density, kap, status, Nx, Nz, P, nxp, nzp, pitch,
+    setup_kappa_kernel<<<grid, 128, 0, st>>>(sos, density, kap, bx, bz, status, Nx, Nz, P, nxp, nzp, pitch,
                                              dt_over_dx * dt_over_dx, d0, dt, c_max, map_dims);
     return cudaGetLastError();
 }

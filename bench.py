@@ -37,6 +37,7 @@ UNIT = "Gcell-updates/s"
 # mu^{m+2}, kappa, Lap(U^{m-1}) and writes mu^m (the imaging sum ideally stays on chip).
 ALGO_BYTES = {"forward": 16, "recompute": 20, "adjoint": 20}
 GRADIENT_BYTES_PER_CELL = 40          # forward 16 + history 4 + 4 + adjoint 16
+VD_EXTRA_BYTES = 8                    # variable density: two half-point buoyancies read per step
 
 
 def parse():
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--n-tx", type=int, default=None, help="override the number of transmits")
     ap.add_argument("--tile-z", type=int, default=None, help="step-kernel tile height (32 or 64)")
     ap.add_argument("--two-step", type=int, default=None, help="1: two time steps per launch, 0: one")
+    ap.add_argument("--density", action="store_true",
+                    help="variable density (Eq. 1): a density map per shot set, staggered operator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -212,7 +215,9 @@ def workload_config(wl, args):
             "maps_per_gpu": wl.n_maps, "n_tx": wl.n_tx, "n_rx": wl.n_rx, "fd_order": wl.fd_order,
             "ckpt_interval": args.ckpt, "snapshot_dtype": args.snapshot,
             "l2": "flushed between timed steps (256 MiB write outside the events)",
-            "tile": [64, args.tile_z_used], "two_step": args.two_step_used}
+            "tile": [64, args.tile_z_used], "two_step": args.two_step_used,
+            "density": ("variable: water-like background + smooth field + 1-3 rods of 1050-1900 kg/m^3, "
+                        "staggered operator" if getattr(args, "density", False) else "constant (compact Laplacian)")}
 
 
 def run_ours(args):
@@ -239,7 +244,13 @@ def run_ours(args):
     sos_true = torch.from_numpy(wl.sos_true).to(dev)
     sos = torch.from_numpy(wl.sos_start).to(dev)
     wav = torch.from_numpy(wl.wavelet).to(dev)
-    obs = dufwi.simulate(pb, sos_true, wav, geom, check=True)
+    rho = None
+    if args.density:
+        rng = inputs.rng_for(900 + rank)
+        pb.c_max = 2000.0      # headroom for the local effective speed at density steps
+        rho = torch.from_numpy(np.stack([inputs.density_map(rng, wl.nx, wl.nz, wl.dx)
+                                         for _ in range(wl.n_maps)])).to(dev)
+    obs = dufwi.simulate(pb, sos_true, wav, geom, density=rho, check=True)
     ws = torch.empty(dufwi.workspace_size(pb, geom, wl.n_maps), dtype=torch.uint8, device=dev)
     misfit = torch.empty(wl.n_maps, dtype=torch.float64, device=dev)
     grad = torch.empty_like(sos)
@@ -247,7 +258,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        dufwi.misfit_gradient(pb, sos, wav, geom, obs, misfit=misfit, grad=grad, workspace=ws)
+        dufwi.misfit_gradient(pb, sos, wav, geom, obs, density=rho, misfit=misfit, grad=grad, workspace=ws)
 
     args.tile_z_used = dufwi.get_option(dufwi.OPT_TILE_Z)
     args.two_step_used = dufwi.get_option(dufwi.OPT_TWO_STEP)
@@ -287,18 +298,19 @@ def run_ours(args):
     units_per_step = 2.0 * cells * wl.nt * S                       # fwd + adj cell updates
     value = units_per_step * world * args.steps / (ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    hbm_frac = GRADIENT_BYTES_PER_CELL * cells * wl.nt * S / (peak * 1e9) / (ms_step / 1e3)
+    extra = VD_EXTRA_BYTES if args.density else 0
+    hbm_frac = (GRADIENT_BYTES_PER_CELL + 2 * extra) * cells * wl.nt * S / (peak * 1e9) / (ms_step / 1e3)
 
     # dominant kernel: the sweep kind with the largest share of device time
     kinds = ["forward", "recompute", "adjoint"]
     dom = max(kinds, key=lambda k: prof[k]["ms"])
     avg_launch_ms = prof[dom]["ms"] / max(prof[dom]["launches"], 1)
-    bytes_per_launch = ALGO_BYTES[dom] * cells * S
+    bytes_per_launch = (ALGO_BYTES[dom] + extra) * cells * S
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "step_kernel (%s sweep)" % dom, "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": kernel_traffic(dom),
-                "traffic_warm_l2": kernel_traffic(dom, "per_launch_dram_bytes_warm_l2"),
+                "traffic": None if args.density else kernel_traffic(dom),
+                "traffic_warm_l2": None if args.density else kernel_traffic(dom, "per_launch_dram_bytes_warm_l2"),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": 1e3 * avg_launch_ms,
                 "sweep_ms_per_step": {k: prof[k]["ms"] / args.steps for k in kinds + ["other"]},
@@ -313,12 +325,17 @@ def run_ours(args):
         h_grad = torch.empty(grad.shape, dtype=torch.float32).pin_memory()
         h_mis = torch.empty(misfit.shape, dtype=torch.float64).pin_memory()
         d_sos, d_obs, d_wav = torch.empty_like(sos), torch.empty_like(obs), torch.empty_like(wav)
+        h_rho = rho.cpu().pin_memory() if rho is not None else None
+        d_rho = torch.empty_like(rho) if rho is not None else None
 
         def e2e_step():
             d_sos.copy_(h_sos, non_blocking=True)
             d_obs.copy_(h_obs, non_blocking=True)
             d_wav.copy_(h_wav, non_blocking=True)
-            dufwi.misfit_gradient(pb, d_sos, d_wav, geom, d_obs, misfit=misfit, grad=grad, workspace=ws)
+            if d_rho is not None:
+                d_rho.copy_(h_rho, non_blocking=True)
+            dufwi.misfit_gradient(pb, d_sos, d_wav, geom, d_obs, density=d_rho, misfit=misfit, grad=grad,
+                                  workspace=ws)
             h_grad.copy_(grad, non_blocking=True)
             h_mis.copy_(misfit, non_blocking=True)
 
@@ -337,7 +354,7 @@ def run_ours(args):
             t = torch.tensor([ems], dtype=torch.float64, device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ems = float(t.item())
-        h2d = h_sos.numel() * 4 + h_obs.numel() * 4 + h_wav.numel() * 4
+        h2d = h_sos.numel() * 4 + h_obs.numel() * 4 + h_wav.numel() * 4 + (h_rho.numel() * 4 if h_rho is not None else 0)
         d2h = h_grad.numel() * 4 + h_mis.numel() * 8
         e2e = {"value": units_per_step * world * args.steps / (ems / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}

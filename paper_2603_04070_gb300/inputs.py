@@ -246,6 +246,24 @@ def phantom_rods_map(rng, n: int, dx: float, ring_radius_cells: float, max_rods:
     return sos.astype(np.float32)
 
 
+def density_map(rng, nx: int, nz: int, dx: float, max_rods: int = 3, background: float = 1000.0,
+                amp: float = 50.0, corr_m: float = 2e-3) -> np.ndarray:
+    """Density (kg/m^3) for the variable-density operator: water-like background plus a smooth
+    Gaussian random field (max |.| = amp), plus 1..max_rods hard rods of density U[1050, 1900]
+    (soft tissue to bone), radius U[1, 3] mm clamped to small grids."""
+    f = _gaussian_field(rng, nx, nz, corr_m / math.sqrt(2.0) / dx)
+    f *= amp / max(np.max(np.abs(f)), 1e-30)
+    rho = background + f
+    X = np.arange(nx) * dx
+    Z = np.arange(nz) * dx
+    for _ in range(int(rng.integers(1, max_rods + 1))):
+        r = rng.uniform(1e-3, max(1e-3, min(3e-3, 0.3 * (min(nx, nz) - 1) * dx)))
+        cx = rng.uniform(r, (nx - 1) * dx - r)
+        cz = rng.uniform(r, (nz - 1) * dx - r)
+        rho[(X[None, :] - cx) ** 2 + (Z[:, None] - cz) ** 2 <= r * r] = rng.uniform(1050.0, 1900.0)
+    return rho.astype(np.float32)
+
+
 def add_awgn(rng, cd: np.ndarray, snr_db: float) -> np.ndarray:
     """Channel data plus white Gaussian noise at the given SNR, with the signal power taken over
     all channels and samples of each map (axis 0 indexes maps)."""

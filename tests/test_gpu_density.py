@@ -1,0 +1,169 @@
+"""Variable-density path (Eq. 1 with rho(x, z); staggered operator) on the GPU against the oracle.
+
+Same tolerances as the constant-density path: traces rel-L2 <= 1e-5, gradient rel-L2 <= 1e-4,
+misfit relative error <= 1e-4. The maps carry density steps of up to 1.9x (soft tissue to
+bone) and speed contrasts, with residuals of a few percent of the traces."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_04070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-5
+GRAD_TOL = 1e-4
+C_MAX = 2000.0
+
+
+@pytest.fixture(scope="module")
+def d():
+    from paper_2603_04070_gb300 import build_lib
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    return dufwi
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case(seed, nx, nz, nt, n_elem, n_tx, n_maps=1, order=8):
+    wl = inputs.make_workload("linear_disk", seed=seed, nx=nx, nz=nz, nt=nt, n_elem=n_elem, n_tx=n_tx,
+                              n_maps=n_maps, fd_order=order)
+    rng = inputs.rng_for(seed + 500)
+    rho = np.stack([inputs.density_map(rng, nx, nz, wl.dx) for _ in range(n_maps)])
+    return wl, rho
+
+
+def _op(wl):
+    return oracle.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml, pml_R=wl.pml_R,
+                          pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+
+
+def _pb(d, wl, **kw):
+    return d.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
+                     pml_cref=wl.pml_cref, fd_order=wl.fd_order, c_max=C_MAX, **kw)
+
+
+def _oracle_traces(wl, C, rho):
+    p = _op(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return np.stack([oracle.forward(p, np.asarray(C, np.float64), (tix[k], tiz[k]), wl.wavelet.astype(np.float64),
+                                    rix[k], riz[k], rho=rho) for k in range(wl.n_tx)])
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_density_simulate_matches_oracle_ragged_grid(d, order):
+    wl, rho = _case(order, 97, 71, 500, 24, 3, order=order)
+    geom = d.Geometry.from_workload(wl)
+    cd = d.simulate(_pb(d, wl), torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    density=torch.from_numpy(rho).cuda(), check=True).cpu().numpy()
+    ref = _oracle_traces(wl, wl.sos_true[0], rho[0])
+    assert rel_l2(cd[0], ref) <= TRACE_TOL
+    # the density matters: the constant-density path gives visibly different traces
+    cd0 = d.simulate(_pb(d, wl), torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                     check=True).cpu().numpy()
+    assert rel_l2(cd0[0], ref) > 1e-3
+
+
+@pytest.mark.parametrize("ckpt", [0, 50])
+def test_density_gradient_matches_oracle(d, ckpt):
+    wl, rho = _case(11, 72, 60, 600, 20, 2, n_maps=2)
+    obs = np.stack([_oracle_traces(wl, wl.sos_true[b], rho[b]) for b in range(2)]).astype(np.float32)
+    geom = d.Geometry.from_workload(wl)
+    pb = _pb(d, wl, ckpt_interval=ckpt)
+    J, g, cd = d.misfit_gradient(pb, torch.from_numpy(wl.sos_start).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                                 torch.from_numpy(obs).cuda(), density=torch.from_numpy(rho).cuda(), return_cd=True,
+                                 check=True)
+    J2 = d.misfit(pb, torch.from_numpy(wl.sos_start).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                  torch.from_numpy(obs).cuda(), density=torch.from_numpy(rho).cuda(), check=True)
+    torch.cuda.synchronize()
+    assert torch.equal(J, J2)
+    p = _op(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    for b in range(2):
+        Jr, gr, Mr = oracle.misfit_gradient(p, wl.sos_start[b].astype(np.float64), tix, tiz,
+                                            wl.wavelet.astype(np.float64), rix, riz, obs[b].astype(np.float64),
+                                            return_traces=True, rho=rho[b])
+        assert rel_l2(cd[b].cpu().numpy(), Mr) <= TRACE_TOL
+        assert abs(float(J[b]) - Jr) <= 1e-4 * Jr
+        assert rel_l2(g[b].cpu().numpy(), gr) <= GRAD_TOL
+
+
+def test_density_checkpointed_gradient_bit_identical(d):
+    wl, rho = _case(12, 64, 64, 400, 16, 2)
+    obs = _oracle_traces(wl, wl.sos_true[0], rho[0])[None].astype(np.float32)
+    geom = d.Geometry.from_workload(wl)
+    out = []
+    for ckpt in (0, 37):
+        J, g = d.misfit_gradient(_pb(d, wl, ckpt_interval=ckpt), torch.from_numpy(wl.sos_start).cuda(),
+                                 torch.from_numpy(wl.wavelet).cuda(), geom, torch.from_numpy(obs).cuda(),
+                                 density=torch.from_numpy(rho).cuda(), check=True)
+        out.append((J.cpu(), g.cpu()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def test_density_sized_batch_matches_oracle(d):
+    """Maps of different grids in one call, each with its own density."""
+    sizes = [(80, 64), (64, 72), (96, 80)]
+    wl, sizes = inputs.sized_batch(3, sizes, nt=400, n_elem=16, n_tx=2)
+    rng = inputs.rng_for(77)
+    rho = np.full(wl.sos_true.shape, 1000.0, dtype=np.float32)
+    for b, (nx, nz) in enumerate(sizes):
+        rho[b, :nz, :nx] = inputs.density_map(rng, nx, nz, wl.dx)
+    geom = d.Geometry.from_workload(wl)
+    cd = d.simulate(_pb(d, wl), torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    density=torch.from_numpy(rho).cuda(), sizes=sizes, check=True).cpu().numpy()
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    for b, (nx, nz) in enumerate(sizes):
+        p = oracle.Problem(nx=nx, nz=nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml, pml_R=wl.pml_R,
+                           pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+        ref = np.stack([oracle.forward(p, wl.sos_true[b, :nz, :nx].astype(np.float64), (tix[k], tiz[k]),
+                                       wl.wavelet.astype(np.float64), rix[k], riz[k], rho=rho[b, :nz, :nx])
+                        for k in range(wl.n_tx)])
+        assert rel_l2(cd[b], ref) <= TRACE_TOL, b
+
+
+def test_density_status_word_and_unsupported_calls(d):
+    wl, rho = _case(13, 40, 40, 60, 8, 1)
+    geom = d.Geometry.from_workload(wl)
+    pb = _pb(d, wl)
+    sos = torch.from_numpy(wl.sos_true).cuda()
+    w = torch.from_numpy(wl.wavelet).cuda()
+    ws = torch.empty(d.workspace_size(pb, geom, 1, gradient=False), dtype=torch.uint8, device="cuda")
+    r = torch.from_numpy(rho).cuda()
+    d.simulate(pb, sos, w, geom, workspace=ws, density=r)
+    assert d.workspace_status(ws) == d.OK
+    bad = r.clone()
+    bad[0, 4, 6] = -1.0
+    d.simulate(pb, sos, w, geom, workspace=ws, density=bad)
+    assert d.workspace_status(ws) == d.ERR_INVALID_ARG
+    bad[0, 4, 6] = float("nan")
+    d.simulate(pb, sos, w, geom, workspace=ws, density=bad)
+    assert d.workspace_status(ws) == d.ERR_NONFINITE
+    # a density step raises the local effective speed: 1950 m/s is fine in a uniform density but
+    # not next to a density ratio of 0.172, where the guard factor peaks at sqrt(1.1036)
+    fast = torch.full_like(sos, 1950.0)
+    d.simulate(pb, fast, w, geom, workspace=ws, density=torch.full_like(r, 1000.0))
+    assert d.workspace_status(ws) == d.OK
+    step = torch.full_like(r, 1000.0)
+    step[0, 20:, :] = 172.0
+    d.simulate(pb, fast, w, geom, workspace=ws, density=step)
+    assert d.workspace_status(ws) == d.ERR_CFL
+    with pytest.raises(d.DufwiError) as e:
+        d.jvp(pb, sos, w, geom, torch.zeros_like(sos), density=r)
+    assert e.value.status == d.ERR_UNSUPPORTED
+    # host CFL check against the staggered operator's (slightly lower) limit
+    lim = d.cfl_limit(8)
+    tight = d.Problem(nx=40, nz=40, dx=1e-4, dt=0.995 * lim * 1e-4 / C_MAX, nt=60, fd_order=8, c_max=C_MAX)
+    d.simulate(tight, sos, w[:60], geom)                 # constant density: within the compact limit
+    with pytest.raises(d.DufwiError) as e:
+        d.simulate(tight, sos, w[:60], geom, density=r)
+    assert e.value.status == d.ERR_CFL

@@ -2,7 +2,10 @@
 
 Same tolerances as the constant-density path: traces rel-L2 <= 1e-5, gradient rel-L2 <= 1e-4,
 misfit relative error <= 1e-4. The maps carry density steps of up to 1.9x (soft tissue to
-bone) and speed contrasts, with residuals of a few percent of the traces."""
+bone). The true SoS maps are the smooth-field-plus-rods kind, so that the residual stays a few
+percent of the traces: the density reflections are common to the observed and the simulated
+data, and a residual of under 1% would put the FP32 gradient error above 1e-4 by the error
+model err ~ 1e-5 |M| / |r| (see the weak-scatterer test of the constant-density path)."""
 import numpy as np
 import pytest
 import torch
@@ -36,6 +39,8 @@ def _case(seed, nx, nz, nt, n_elem, n_tx, n_maps=1, order=8):
                               n_maps=n_maps, fd_order=order)
     rng = inputs.rng_for(seed + 500)
     rho = np.stack([inputs.density_map(rng, nx, nz, wl.dx) for _ in range(n_maps)])
+    r2 = inputs.rng_for(seed + 900)
+    wl.sos_true = np.stack([inputs.grf_rods_map(r2, nx, nz, wl.dx) for _ in range(n_maps)])
     return wl, rho
 
 
@@ -91,6 +96,7 @@ def test_density_gradient_matches_oracle(d, ckpt):
         Jr, gr, Mr = oracle.misfit_gradient(p, wl.sos_start[b].astype(np.float64), tix, tiz,
                                             wl.wavelet.astype(np.float64), rix, riz, obs[b].astype(np.float64),
                                             return_traces=True, rho=rho[b])
+        assert np.linalg.norm(Mr - obs[b]) >= 0.03 * np.linalg.norm(Mr)     # residual of a few percent
         assert rel_l2(cd[b].cpu().numpy(), Mr) <= TRACE_TOL
         assert abs(float(J[b]) - Jr) <= 1e-4 * Jr
         assert rel_l2(g[b].cpu().numpy(), gr) <= GRAD_TOL

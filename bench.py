@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--n-tx", type=int, default=None, help="override the number of transmits")
     ap.add_argument("--tile-z", type=int, default=None, help="step-kernel tile height (32 or 64)")
     ap.add_argument("--two-step", type=int, default=None, help="1: two time steps per launch, 0: one")
+    ap.add_argument("--persistent", type=int, default=None,
+                    help="1: one cooperative launch per sweep segment, 0: one launch per step")
     ap.add_argument("--density", action="store_true",
                     help="variable density (Eq. 1): a density map per shot set, staggered operator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -215,7 +217,8 @@ def workload_config(wl, args):
             "maps_per_gpu": wl.n_maps, "n_tx": wl.n_tx, "n_rx": wl.n_rx, "fd_order": wl.fd_order,
             "ckpt_interval": args.ckpt, "snapshot_dtype": args.snapshot,
             "l2": "flushed between timed steps (256 MiB write outside the events)",
-            "tile": [64, args.tile_z_used], "two_step": args.two_step_used,
+            "tile": [64, 32 if getattr(args, "persistent_used", 0) else args.tile_z_used],
+            "two_step": args.two_step_used, "persistent": getattr(args, "persistent_used", 0),
             "density": ("variable: water-like background + smooth field + 1-3 rods of 1050-1900 kg/m^3, "
                         "staggered operator" if getattr(args, "density", False) else "constant (compact Laplacian)")}
 
@@ -236,6 +239,8 @@ def run_ours(args):
         dufwi.set_option(dufwi.OPT_TILE_Z, args.tile_z)
     if args.two_step is not None:
         dufwi.set_option(dufwi.OPT_TWO_STEP, args.two_step)
+    if args.persistent is not None:
+        dufwi.set_option(dufwi.OPT_PERSISTENT, args.persistent)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
@@ -262,6 +267,7 @@ def run_ours(args):
 
     args.tile_z_used = dufwi.get_option(dufwi.OPT_TILE_Z)
     args.two_step_used = dufwi.get_option(dufwi.OPT_TWO_STEP)
+    args.persistent_used = dufwi.get_option(dufwi.OPT_PERSISTENT)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

@@ -269,10 +269,16 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     bit-identical to one launch per step (0, the default, which measured faster on GB300).
  *   DUFWI_OPT_REUSE_TABLES: 1 lets calls skip re-copying unchanged geometry tables into a
  *     workspace that stays reserved between calls (see the conventions above); default 0.
+ *   DUFWI_OPT_PERSISTENT: 1 runs each sweep segment (the forward sweep between snapshots, a
+ *     recompute segment, an adjoint segment) as one cooperative launch whose CTAs stay resident
+ *     and pass 64 x 32 tiles from step to step through per-tile counters in the workspace,
+ *     instead of one launch per time step; bit-identical results. Not used with the two-step
+ *     kernel, the Born step or a density map; 0 (the default) launches once per step.
  * Both functions return DUFWI_ERR_INVALID_ARG for an unknown option or value. */
 #define DUFWI_OPT_TILE_Z 1
 #define DUFWI_OPT_TWO_STEP 2
 #define DUFWI_OPT_REUSE_TABLES 3
+#define DUFWI_OPT_PERSISTENT 4
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

@@ -89,8 +89,9 @@ struct Layout {
     size_t snap_elem;
     // byte offsets into the workspace
     int tiles1, tiles2;      // tiles of the one-step kernel (tile height TZ) and of the two-step kernel
+    int tiles_x, tiles_z32;  // 64 x 32 tiles of one shot (persistent sweeps)
     int n_rxe;               // row length of the grown-tile receiver lists (4 n_rx)
-    size_t o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
+    size_t o_flags, o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
 };
 
@@ -104,6 +105,7 @@ int g_reuse_tables = 0;
 // Tile height of the one-step kernel (DUFWI_OPT_TILE_Z) and use of the two-step kernel.
 int g_tile_z = kTileZDefault;
 int g_two_step = 0;
+int g_persistent = 0;   // DUFWI_OPT_PERSISTENT: one cooperative launch per sweep segment
 
 int validate_problem(const dufwi_problem *pb)
 {
@@ -159,10 +161,14 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
     const size_t nrx1 = L->n_rx > 0 ? L->n_rx : 1;
     const int tiles_x = (L->nxp + kTileX - 1) / kTileX;
-    L->tiles1 = tiles_x * ((L->nzp + g_tile_z - 1) / g_tile_z);
+    // receiver tables are sized for the smallest tile height (32 rows), whatever the call uses
+    L->tiles1 = tiles_x * ((L->nzp + 31) / 32);
     L->tiles2 = tiles_x * ((L->nzp + kPairTileZ - 1) / kPairTileZ);
     L->n_rxe = 4 * (int)nrx1;
+    L->tiles_x = tiles_x;
+    L->tiles_z32 = (L->nzp + 31) / 32;
     L->o_status = take(sizeof(int));
+    L->o_flags = take(sizeof(int) * ((size_t)L->S * L->tiles_x * L->tiles_z32 + 1));   // tile counters + abort
     L->o_mapdims = take(sizeof(int2) * (size_t)n_maps);
     L->o_tx = take(sizeof(int) * L->n_tx);
     L->o_rx = take(sizeof(int) * (size_t)L->n_tx * nrx1);
@@ -331,6 +337,7 @@ struct Ctx {
     const dufwi_map_sizes *sizes = nullptr;   // sized calls: per-map grids inside the envelope
     bool jvp = false;                         // linearised forward (Born) call
     bool vd = false;                          // density map given: staggered variable-density operator
+    bool persistent = false;                  // one cooperative launch per sweep segment
     FieldMaps fmap[4], mmap[4];
     CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1, bx1, bz1;
     int *status() const { return reinterpret_cast<int *>(ws + L.o_status); }
@@ -406,8 +413,9 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.vd = density != nullptr;
     if (c.vd && c.jvp) return DUFWI_ERR_UNSUPPORTED;   // no Born step for the density operator
     if (c.vd && c.pb->c_max * c.pb->dt / c.pb->dx > stagger_stability_limit(c.pb->fd_order)) return DUFWI_ERR_CFL;
-    c.tz = c.vd ? kVTileZ : g_tile_z;
     c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd;
+    c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd;
+    c.tz = (c.vd || c.persistent) ? 32 : g_tile_z;
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
     std::vector<int> sorted1, sorted2, sortede;
@@ -585,6 +593,43 @@ int two_steps(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
     return DUFWI_OK;
 }
 
+// Steps of one sweep in one persistent launch: forward n = n0 .. n0 + n - 1 (mode != kAdjoint) or
+// adjoint m = n0 .. n0 - n + 1. The ring's two buffers alternate inside the launch.
+int sweep(Ctx &c, Ring &rg, int mode, StepParams p, int n0, int n, float *hist0, int hist_slot0, long long &nl)
+{
+    if (n <= 0) return DUFWI_OK;
+    const Layout &L = c.L;
+    SweepMaps tm;
+    memset(&tm, 0, sizeof(tm));
+    tm.box[0] = rg.map[rg.cur].box1;
+    tm.tile[0] = rg.map[rg.prv].tile1;
+    tm.box[1] = rg.map[rg.prv].box1;
+    tm.tile[1] = rg.map[rg.cur].tile1;
+    tm.kap = c.kap1;
+    if (mode == kAdjoint) { tm.hist = c.hist1; tm.grad = c.grad1; }
+    SweepParams sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.n_steps = n;
+    sp.step0 = n0;
+    sp.tiles_x = L.tiles_x;
+    sp.tiles_z = L.tiles_z32;
+    sp.tiles = L.S * L.tiles_x * L.tiles_z32;
+    sp.flags = c.at<int>(L.o_flags);
+    sp.abort = sp.flags + sp.tiles;
+    sp.out[0] = rg.buf[rg.prv];
+    sp.out[1] = rg.buf[rg.cur];
+    sp.hist0 = hist0;
+    sp.hist_stride = (long long)L.S * L.slice;
+    sp.hist_slot0 = hist_slot0;
+    p.rx_tab = c.at<int2>(L.o_tab1);
+    p.rx_sorted = c.at<int>(L.o_sorted1);
+    CK(cudaMemsetAsync(sp.flags, 0, sizeof(int) * ((size_t)sp.tiles + 1), c.st));
+    int grid = 0;
+    CKL(launch_sweep(L.radius, mode, tm, p, sp, &grid, c.st));
+    if (n & 1) std::swap(rg.cur, rg.prv);
+    return DUFWI_OK;
+}
+
 // Forward steps n = n0 .. n1-1 (producing U^{n1}). Steps pair up from even n when the two-step
 // kernel is enabled, so every schedule covering a step uses the same grouping. hist: base of the
 // history slots of this range (slot n - h0), or null.
@@ -597,6 +642,8 @@ int forward_range(Ctx &c, Ring &rg, int n0, int n1, int mode, const float *wavel
     p.inj_val = wavelet;
     p.smp_node = c.at<int>(c.L.o_rx);
     p.cd = cd;
+    if (c.persistent)
+        return sweep(c, rg, mode, p, n0, n1 - n0, hist ? hist + (size_t)(n0 - h0) * hstride : nullptr, 0, nl);
     for (int n = n0; n < n1;) {
         p.step = n;
         p.hist = hist ? hist + (size_t)(n - h0) * hstride : nullptr;
@@ -621,6 +668,7 @@ int adjoint_range(Ctx &c, Ring &rg, int m1, int m0, const float *asrc, float *g_
     p.inj_node = c.at<int>(c.L.o_rx);
     p.inj_val = asrc;
     p.grad = g_shot;
+    if (c.persistent) return sweep(c, rg, kAdjoint, p, m1, m1 - m0 + 1, nullptr, m1 - 1 - h0, nl);
     for (int m = m1; m >= m0;) {
         p.step = m;
         p.hist_slot = m - 1 - h0;
@@ -704,6 +752,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_reuse_tables = value;
         return DUFWI_OK;
+    case DUFWI_OPT_PERSISTENT:
+        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
+        g_persistent = value;
+        return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
     }
 }
@@ -713,6 +765,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     if (!value) return DUFWI_ERR_INVALID_ARG;
     switch (option) {
     case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
+    case DUFWI_OPT_PERSISTENT: *value = g_persistent; return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;

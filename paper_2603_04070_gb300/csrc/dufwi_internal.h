@@ -91,11 +91,40 @@ struct StepParams {
     float sw[4];             // staggered first-difference weights s_1..s_R (variable density)
 };
 
+// Persistent sweep: n_steps consecutive steps of one sweep in a single cooperative launch. Work
+// items are (local step i, tile k) in the order g = i * tiles + k; CTA b takes g = b, b + G, ...
+// Before item (i, k) a CTA waits until tile k and its four neighbours in the same shot have
+// completed i local steps (per-tile counters in flags, published with release semantics after
+// the tile's stores); the smallest unfinished item therefore never waits, so all-resident CTAs
+// cannot deadlock. The two field buffers alternate: local step i reads the current field through
+// box[i & 1] and the previous one through tile[i & 1], and writes the new field in place of the
+// previous one at out[i & 1].
+struct SweepMaps {
+    CUtensorMap box[2], tile[2], kap, hist, grad;
+};
+
+struct SweepParams {
+    int n_steps;             // steps in this launch
+    int step0;               // first step: forward n = step0 + i, adjoint m = step0 - i
+    int tiles_x, tiles_z;    // tiles of one shot (64 x 32)
+    int tiles;               // tiles of all shots
+    int *flags;              // [tiles] local steps completed (zeroed before the launch)
+    int *abort;              // set by a CTA whose wait ran out; every waiter then returns
+    float *out[2];           // field written by local step i: out[i & 1]
+    float *hist0;            // forward history: slot of step0 (stride hist_stride floats per step)
+    long long hist_stride;
+    int hist_slot0;          // adjoint: history slot of m - 1 for m = step0
+};
+
 // Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.
 cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 // Two time steps per launch (core tiles 64 x 32; see step2_kernel).
 cudaError_t launch_step2(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 constexpr int kPairTileZ = 32;   // core tile height of the two-step kernel (64 x 32 tiles)
+// Persistent sweep (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint; 64 x 32 tiles). grid_ctas
+// receives the grid used (all CTAs co-resident, cooperative launch).
+cudaError_t launch_sweep(int radius, int mode, const SweepMaps &tm, const StepParams &p, const SweepParams &sp,
+                         int *grid_ctas, cudaStream_t st);
 // Variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint; 64 x 32 tiles).
 cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 // kappa' on the padded grid; with a density map kappa' = rho C^2 dt^2/(dx^2 (1 + D dt)), and the

@@ -694,6 +694,213 @@ __global__ void __launch_bounds__(128, 3) vd_step_kernel(const __grid_constant__
     }
 }
 
+// ---- persistent sweep ---------------------------------------------------------------------------
+// Several time steps of one sweep in one cooperative launch (see SweepParams). Each work item is
+// the one-step update of one 64 x 32 tile; the arithmetic is that of step_kernel<R, MODE, 32>, so
+// the results are bit-identical. Ordering between CTAs: the producer's threads store the tile,
+// the CTA barrier orders those stores before thread 0's release of the tile counter; a consumer's
+// thread 0 acquires the counters of the tile and its four neighbours, then a proxy fence orders
+// that acquire before its TMA (async proxy) reads. Counter waits are bounded like the mbarrier
+// waits: a CTA whose wait runs out raises DUFWI_ERR_TIMEOUT, sets the abort word and returns, and
+// every other waiter returns when it sees the abort word.
+__device__ __forceinline__ int ld_acquire(const int *ptr)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *ptr, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Thread 0: waits until the counters of tile k and its in-shot neighbours reach target; false on
+// abort or timeout (the abort word is then set).
+__device__ bool wait_neighbours(const SweepParams &sp, int k, int target, int *status)
+{
+    const int per_shot = sp.tiles_x * sp.tiles_z;
+    const int t = k % per_shot, tx = t % sp.tiles_x, tz = t / sp.tiles_x;
+    unsigned long long t0 = 0;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        const bool use = d == 0 || (d == 1 && tx > 0) || (d == 2 && tx + 1 < sp.tiles_x) || (d == 3 && tz > 0) ||
+                         (d == 4 && tz + 1 < sp.tiles_z);
+        const int dk = d == 0 ? k : (d == 1 ? k - 1 : (d == 2 ? k + 1 : (d == 3 ? k - sp.tiles_x : k + sp.tiles_x)));
+        if (!use) continue;
+        while (ld_acquire(sp.flags + dk) < target) {
+            if (ld_acquire(sp.abort) != 0) return false;
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitLimitNs) {
+                raise_status(status, DUFWI_ERR_TIMEOUT);
+                st_release(sp.abort, 1);
+                return false;
+            }
+            __nanosleep(32);
+        }
+    }
+    return true;
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(128, DUFWI_STEP_MIN_CTAS_128)
+sweep_kernel(const __grid_constant__ SweepMaps tm, const StepParams p, const SweepParams sp)
+{
+    using TL = TileLayout<MODE, 32>;
+    constexpr int TZ = 32;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ InjList inj;
+    __shared__ int go;
+
+    const int tid = threadIdx.x;
+    float *box = smem;
+    float *pv = box + TL::kBox;
+    float *kp = pv + TL::kTile;
+    float *hs = kp + TL::kTile;
+    float *gg = hs + TL::kTile;
+    const int per_shot = sp.tiles_x * sp.tiles_z;
+    const int n_items = sp.n_steps * sp.tiles;   // < 2^31 (checked on the host)
+    if (tid == 0) {
+        prefetch_tensormap(&tm.box[0]);
+        prefetch_tensormap(&tm.box[1]);
+        mbar_init(&bar, 1);
+    }
+    __syncthreads();
+    const int lx = (tid & 15) * 4;
+    const int lz = (tid >> 4) * 4;
+    uint32_t parity = 0;
+#pragma unroll 1
+    for (int g = blockIdx.x; g < n_items; g += gridDim.x) {
+        const int i = g / sp.tiles;
+        const int k = g - i * sp.tiles;
+        const int s = k / per_shot;
+        const int t = k % per_shot;
+        const int x0 = (t % sp.tiles_x) * kTileX;
+        const int z0 = (t / sp.tiles_x) * TZ;
+        const int tx_idx = s % p.n_tx;
+        const int map = s / p.n_tx;
+        const int step = MODE == kAdjoint ? sp.step0 - i : sp.step0 + i;
+        const MapGrid mg = map_grid(p, map);
+        const bool active = x0 < mg.nxp && z0 < mg.nzp;   // sized calls: tiles outside the map stay zero
+        float *out = (i & 1) ? sp.out[1] : sp.out[0];
+
+        if (tid == 0) {
+            const int ok = wait_neighbours(sp, k, i, p.status) ? 1 : 0;
+            if (ok && active) {
+                fence_proxy_async_global();    // acquired stores of other CTAs, before the TMA reads
+                fence_proxy_async_shared();    // this CTA's earlier shared-memory use, before the TMA writes
+                mbar_arrive_expect_tx(&bar, TL::kBytes);
+                tma_load_3d(box, &tm.box[i & 1], &bar, x0 - kHalo, z0 - kHalo, s);
+                tma_load_3d(pv, &tm.tile[i & 1], &bar, x0, z0, s);
+                tma_load_3d(kp, &tm.kap, &bar, x0, z0, map);
+                if (MODE == kAdjoint) {
+                    tma_load_4d(hs, &tm.hist, &bar, x0, z0, s, sp.hist_slot0 - i);
+                    tma_load_3d(gg, &tm.grad, &bar, x0, z0, s);
+                }
+            }
+            go = ok;
+        }
+        __syncthreads();
+        if (!go) return;
+        if (active) {
+            int2 rx_range = make_int2(0, 0);
+            if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * per_shot + t);
+            gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, step, rx_range, x0, z0, kTileX, TZ,
+                                    kTileX, tid, 128);
+            const int gx = x0 + lx;
+            const bool interior = region_interior(p, mg, x0, z0, kTileX, TZ);
+            int xd[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xd[q] = layer_depth(gx + q, p.P, mg.Nx);
+
+            // bounded wait on this item's phase (thread 0 polls, the CTA barrier publishes the result)
+            int fail = 0;
+            if (tid == 0) fail = !mbar_wait_bounded(&bar, parity);
+            if (__syncthreads_or(fail)) {
+                if (tid == 0) {
+                    raise_status(p.status, DUFWI_ERR_TIMEOUT);
+                    st_release(sp.abort, 1);
+                    mbar_wait_bounded(&bar, parity);
+                }
+                return;
+            }
+            if (!mbar_try_wait_sleep(&bar, parity) && !mbar_wait_bounded(&bar, parity))
+                raise_status(p.status, DUFWI_ERR_TIMEOUT);
+            parity ^= 1u;
+
+            float4 lap[4], ctr[4], nxt[4];
+            lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int lo = (lz + j) * kTileX + lx;
+                nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
+                                 p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+            }
+            if (inj.n > 0) {
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
+                __syncthreads();
+                if (tid == 0)
+                    apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, step, rx_range, x0, z0, kTileX,
+                                           TZ, kTileX);
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+            }
+            const bool col_ok = gx < mg.nxp;
+            const long long shot_off = static_cast<long long>(s) * p.slice;
+            float *hist = (MODE == kFwdSampleHist || MODE == kFwdHist) ? sp.hist0 + sp.hist_stride * i : nullptr;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gz = z0 + lz + j;
+                if (!col_ok || gz >= mg.nzp) continue;
+                float4 nv = nxt[j], lv = lap[j];
+                if (gx + 4 > mg.nxp) {
+                    if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
+                    if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
+                    nv.w = 0.f; lv.w = 0.f;
+                }
+                const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+                st4(out + o, nv);
+                if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(hist + o, lv);
+                if (MODE == kAdjoint) {
+                    const int lo = (lz + j) * kTileX + lx;
+                    st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+                }
+            }
+            if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+                const int cnt =
+                    (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
+                for (int e = tid; e < cnt; e += 128) {
+                    const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
+                    const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.smp_node + tx_idx * p.n_rx + r) : -1;
+                    const int zn = node >> 16, xn = node & 0xffff;
+                    if (node < 0 || zn < z0 || zn >= z0 + TZ || xn < x0 || xn >= x0 + kTileX) {
+                        raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                        continue;
+                    }
+                    p.cd[(static_cast<long long>(s) * p.nt + step) * p.n_rx + r] =
+                        box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
+                }
+            }
+        }
+        // publish: every thread's stores and shared-memory reads are done before the release
+        __syncthreads();
+        if (tid == 0) {
+            fence_proxy_async_global();
+            __threadfence();
+            st_release(sp.flags + k, i + 1);
+        }
+    }
+}
+
 // ---- two time steps per launch ----------------------------------------------------------------
 // Core tile 64 x 32 per CTA, 192 threads. Phase A computes U^{n+1} on the core plus a 4-cell
 // ring (72 x 40, 180 blocks of 4 x 4) from an 80 x 48 TMA box of U^n and the 72 x 40 boxes of
@@ -1272,6 +1479,72 @@ cudaError_t launch_step2(int radius, int mode, const StepMaps &tm, const StepPar
     case 2: return launch_step2_r<2>(mode, tm, p, st);
     case 3: return launch_step2_r<3>(mode, tm, p, st);
     case 4: return launch_step2_r<4>(mode, tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R, int MODE>
+static cudaError_t launch_sweep_rm(const SweepMaps &tm, const StepParams &p, const SweepParams &sp, int *grid_ctas,
+                                   cudaStream_t st)
+{
+    using TL = TileLayout<MODE, 32>;
+    static int max_ctas = 0;   // co-resident CTAs of this variant on the device of the first call
+    if (max_ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TL::kBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(sweep_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, MODE>, 128, TL::kBytes)) !=
+            cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        max_ctas = per_sm * sms;
+    }
+    const long long items = static_cast<long long>(sp.n_steps) * sp.tiles;
+    if (items >= (1ll << 31)) return cudaErrorInvalidValue;
+    const int grid = static_cast<int>(std::min<long long>(items, max_ctas));
+    if (grid_ctas) *grid_ctas = grid;
+    if (grid < 1) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = TL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<R, MODE>, tm, p, sp);
+}
+
+template <int R>
+static cudaError_t launch_sweep_r(int mode, const SweepMaps &tm, const StepParams &p, const SweepParams &sp,
+                                  int *grid_ctas, cudaStream_t st)
+{
+    switch (mode) {
+    case kFwdSample: return launch_sweep_rm<R, kFwdSample>(tm, p, sp, grid_ctas, st);
+    case kFwdSampleHist: return launch_sweep_rm<R, kFwdSampleHist>(tm, p, sp, grid_ctas, st);
+    case kFwdHist: return launch_sweep_rm<R, kFwdHist>(tm, p, sp, grid_ctas, st);
+    case kAdjoint: return launch_sweep_rm<R, kAdjoint>(tm, p, sp, grid_ctas, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sweep(int radius, int mode, const SweepMaps &tm, const StepParams &p, const SweepParams &sp,
+                         int *grid_ctas, cudaStream_t st)
+{
+    if (p.tile_z != 32) return cudaErrorInvalidValue;
+    switch (radius) {
+    case 1: return launch_sweep_r<1>(mode, tm, p, sp, grid_ctas, st);
+    case 2: return launch_sweep_r<2>(mode, tm, p, sp, grid_ctas, st);
+    case 3: return launch_sweep_r<3>(mode, tm, p, sp, grid_ctas, st);
+    case 4: return launch_sweep_r<4>(mode, tm, p, sp, grid_ctas, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -28,6 +28,7 @@ SNAPSHOT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 OPT_TILE_Z = 1
 OPT_TWO_STEP = 2
 OPT_REUSE_TABLES = 3
+OPT_PERSISTENT = 4
 
 
 class DufwiError(RuntimeError):

@@ -299,6 +299,52 @@ def test_two_step_kernel_is_bit_identical_to_one_step(d, ckpt):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("ckpt,order,nx,nz,n_tx,n_maps", [(0, 8, 90, 77, 3, 2), (40, 8, 150, 61, 2, 1),
+                                                          (25, 4, 33, 20, 1, 1)])
+def test_persistent_sweeps_are_bit_identical(d, ckpt, order, nx, nz, n_tx, n_maps):
+    """One cooperative launch per sweep segment (tiles handed from step to step through per-tile
+    counters) gives exactly the results of one launch per step: same tile arithmetic, same
+    injection order. Cases: store-all, checkpointed with an odd segment count, and a grid of
+    fewer tiles than resident CTAs."""
+    wl = inputs.make_workload("linear_disk", seed=13, nx=nx, nz=nz, nt=257, n_elem=min(20, nx // 4), n_tx=n_tx,
+                              n_maps=n_maps, fd_order=order)
+    M_obs = _observed(wl)
+    out = []
+    for persistent in (0, 1):
+        d.set_option(d.OPT_PERSISTENT, persistent)
+        try:
+            pb = _dufwi_problem(d, wl, ckpt_interval=ckpt)
+            geom = d.Geometry.from_workload(wl)
+            cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                            check=True).cpu().numpy()
+            J, g, cds = _gpu_grad(d, wl, M_obs, ckpt_interval=ckpt)
+            out.append((cd, J, g, cds))
+        finally:
+            d.set_option(d.OPT_PERSISTENT, 0)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_persistent_sweeps_sized_batch_bit_identical(d):
+    sizes = [(96, 70), (64, 96), (80, 80)]
+    wl, sizes = inputs.sized_batch(8, sizes, nt=200, n_elem=16, n_tx=2)
+    M = []
+    for persistent in (0, 1):
+        d.set_option(d.OPT_PERSISTENT, persistent)
+        try:
+            pb = _dufwi_problem(d, wl, ckpt_interval=30)
+            geom = d.Geometry.from_workload(wl)
+            sos = torch.from_numpy(wl.sos_true).cuda()
+            cd = d.simulate(pb, sos, torch.from_numpy(wl.wavelet).cuda(), geom, sizes=sizes, check=True)
+            J, g = d.misfit_gradient(pb, torch.from_numpy(wl.sos_start).cuda(), torch.from_numpy(wl.wavelet).cuda(),
+                                     geom, cd, sizes=sizes, check=True)
+            M.append((cd.cpu().numpy(), J.cpu().numpy(), g.cpu().numpy()))
+        finally:
+            d.set_option(d.OPT_PERSISTENT, 0)
+    for a, b in zip(M[0], M[1]):
+        assert np.array_equal(a, b)
+
+
 def test_autograd_matches_misfit_gradient_bit_for_bit(d):
     """loss = sum (M - M_obs)^2 through the autograd wrapper gives the misfit gradient exactly:
     the cotangent 2 (M - M_obs) enters the same adjoint kernels."""

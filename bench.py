@@ -517,6 +517,8 @@ def run_ring_phantom(args):
     from paper_2603_04070_gb300 import build_lib, inputs
     build_lib.build()
     from paper_2603_04070_gb300 import dufwi, fwi, unfolded
+    if args.persistent is not None:
+        dufwi.set_option(dufwi.OPT_PERSISTENT, args.persistent)
     dev = torch.device("cuda", 0)
     wl = inputs.ring_phantom(seed=0, n_maps=1)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cref=wl.pml_cref, ckpt_interval=0,

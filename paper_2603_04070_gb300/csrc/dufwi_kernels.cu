@@ -720,30 +720,42 @@ __device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence
 
 // Thread 0: waits until the counters of tile k and its in-shot neighbours reach target; false on
 // abort or timeout (the abort word is then set).
+__device__ __forceinline__ int ld_relaxed(const int *ptr)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
+    return v;
+}
+
+// Thread 0: waits until the counters of tile k and its in-shot neighbours reach target; false on
+// abort or timeout (the abort word is then set). The up to five counters are read together with
+// relaxed loads (one round trip to L2 per poll); the fence after the last poll makes the reads
+// an acquire pattern with the producers' releases.
 __device__ bool wait_neighbours(const SweepParams &sp, int k, int target, int *status)
 {
     const int per_shot = sp.tiles_x * sp.tiles_z;
     const int t = k % per_shot, tx = t % sp.tiles_x, tz = t / sp.tiles_x;
+    const int kl = tx > 0 ? k - 1 : k;
+    const int kr = tx + 1 < sp.tiles_x ? k + 1 : k;
+    const int ku = tz > 0 ? k - sp.tiles_x : k;
+    const int kd = tz + 1 < sp.tiles_z ? k + sp.tiles_x : k;
     unsigned long long t0 = 0;
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-        const bool use = d == 0 || (d == 1 && tx > 0) || (d == 2 && tx + 1 < sp.tiles_x) || (d == 3 && tz > 0) ||
-                         (d == 4 && tz + 1 < sp.tiles_z);
-        const int dk = d == 0 ? k : (d == 1 ? k - 1 : (d == 2 ? k + 1 : (d == 3 ? k - sp.tiles_x : k + sp.tiles_x)));
-        if (!use) continue;
-        while (ld_acquire(sp.flags + dk) < target) {
-            if (ld_acquire(sp.abort) != 0) return false;
-            const unsigned long long now = global_ns();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > kWaitLimitNs) {
-                raise_status(status, DUFWI_ERR_TIMEOUT);
-                st_release(sp.abort, 1);
-                return false;
-            }
-            __nanosleep(32);
+    while (true) {
+        const int a = ld_relaxed(sp.flags + k), b = ld_relaxed(sp.flags + kl), c = ld_relaxed(sp.flags + kr);
+        const int e = ld_relaxed(sp.flags + ku), f = ld_relaxed(sp.flags + kd);
+        if (min(min(a, b), min(min(c, e), f)) >= target) break;
+        if (ld_relaxed(sp.abort) != 0) return false;
+        const unsigned long long now = global_ns();
+        if (t0 == 0) {
+            t0 = now;
+        } else if (now - t0 > kWaitLimitNs) {
+            raise_status(status, DUFWI_ERR_TIMEOUT);
+            st_release(sp.abort, 1);
+            return false;
         }
+        __nanosleep(32);
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     return true;
 }
 
@@ -895,8 +907,7 @@ sweep_kernel(const __grid_constant__ SweepMaps tm, const StepParams p, const Swe
         __syncthreads();
         if (tid == 0) {
             fence_proxy_async_global();
-            __threadfence();
-            st_release(sp.flags + k, i + 1);
+            st_release(sp.flags + k, i + 1);   // release: cumulative over the CTA's stores ordered by the barrier
         }
     }
 }

@@ -1,10 +1,11 @@
-"""Autotuner for the step-kernel launch options (tile height, one or two steps per launch).
+"""Autotuner for the step-kernel launch options (tile height, one or two steps per launch, one
+launch per step or one persistent launch per sweep segment).
 
 For a given problem shape the tuner times a short forward simulation with each candidate
 option set, on the caller's device, and keeps the fastest. Results are cached per (GPU name,
 grid, shots, stencil order): in memory, and optionally in a JSON file. The options change
 speed only: every candidate produces bit-identical results, which the tests check for the
-one/two-step pair.
+one/two-step pair and the per-step/persistent pair.
 """
 from __future__ import annotations
 
@@ -17,9 +18,10 @@ import torch
 from . import dufwi
 
 CANDIDATES = (
-    {"tile_z": 32, "two_step": 0},
-    {"tile_z": 64, "two_step": 0},
-    {"tile_z": 32, "two_step": 1},
+    {"tile_z": 32, "two_step": 0, "persistent": 0},
+    {"tile_z": 64, "two_step": 0, "persistent": 0},
+    {"tile_z": 32, "two_step": 1, "persistent": 0},
+    {"tile_z": 32, "two_step": 0, "persistent": 1},
 )
 
 _lock = threading.Lock()
@@ -35,6 +37,7 @@ def _key(problem: dufwi.Problem, geom: dufwi.Geometry, n_maps: int) -> str:
 def apply(options: dict):
     dufwi.set_option(dufwi.OPT_TILE_Z, int(options["tile_z"]))
     dufwi.set_option(dufwi.OPT_TWO_STEP, int(options["two_step"]))
+    dufwi.set_option(dufwi.OPT_PERSISTENT, int(options.get("persistent", 0)))
 
 
 def tune(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: dufwi.Geometry, *,

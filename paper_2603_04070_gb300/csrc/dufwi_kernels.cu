@@ -740,20 +740,21 @@ __device__ bool wait_neighbours(const SweepParams &sp, int k, int target, int *s
     const int ku = tz > 0 ? k - sp.tiles_x : k;
     const int kd = tz + 1 < sp.tiles_z ? k + sp.tiles_x : k;
     unsigned long long t0 = 0;
-    while (true) {
+    for (unsigned polls = 0;; ++polls) {
         const int a = ld_relaxed(sp.flags + k), b = ld_relaxed(sp.flags + kl), c = ld_relaxed(sp.flags + kr);
         const int e = ld_relaxed(sp.flags + ku), f = ld_relaxed(sp.flags + kd);
         if (min(min(a, b), min(min(c, e), f)) >= target) break;
-        if (ld_relaxed(sp.abort) != 0) return false;
-        const unsigned long long now = global_ns();
-        if (t0 == 0) {
-            t0 = now;
-        } else if (now - t0 > kWaitLimitNs) {
-            raise_status(status, DUFWI_ERR_TIMEOUT);
-            st_release(sp.abort, 1);
-            return false;
+        if ((polls & 31) == 31) {   // abort word and time limit every 32 polls
+            if (ld_relaxed(sp.abort) != 0) return false;
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitLimitNs) {
+                raise_status(status, DUFWI_ERR_TIMEOUT);
+                st_release(sp.abort, 1);
+                return false;
+            }
         }
-        __nanosleep(32);
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     return true;
@@ -905,10 +906,9 @@ sweep_kernel(const __grid_constant__ SweepMaps tm, const StepParams p, const Swe
         }
         // publish: every thread's stores and shared-memory reads are done before the release
         __syncthreads();
-        if (tid == 0) {
-            fence_proxy_async_global();
-            st_release(sp.flags + k, i + 1);   // release: cumulative over the CTA's stores ordered by the barrier
-        }
+        // release by a thread of warp 1 (cumulative over the CTA's stores ordered by the barrier), so
+        // that thread 0 can go on to the next item's counter wait and loads meanwhile
+        if (tid == 32) st_release(sp.flags + k, i + 1);
     }
 }
 
@@ -1518,7 +1518,10 @@ static cudaError_t launch_sweep_rm(const SweepMaps &tm, const StepParams &p, con
     }
     const long long items = static_cast<long long>(sp.n_steps) * sp.tiles;
     if (items >= (1ll << 31)) return cudaErrorInvalidValue;
-    const int grid = static_cast<int>(std::min<long long>(items, max_ctas));
+    // Items of one round (grid consecutive items) must not depend on each other, or the round
+    // serialises: dependencies lie tiles - tiles_x items back at the least.
+    const int no_chain = std::max(1, sp.tiles - sp.tiles_x);
+    const int grid = static_cast<int>(std::min<long long>(std::min<long long>(items, max_ctas), no_chain));
     if (grid_ctas) *grid_ctas = grid;
     if (grid < 1) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};

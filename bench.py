@@ -59,6 +59,8 @@ def parse():
                     help="variable density (Eq. 1): a density map per shot set, staggered operator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-store-all", action="store_true",
+                    help="skip the store-all (no checkpoint) comparison measured beside the headline")
     return ap.parse_args()
 
 
@@ -379,6 +381,37 @@ def run_ours(args):
         torch.cuda.synchronize()
     net_ms = e0.elapsed_time(e1) / 10
 
+    # the same gradient with the whole history kept in HBM (no checkpoints, no recompute), when the
+    # run is checkpointed and the history fits comfortably: context beside the configured method
+    store_all = None
+    if args.ckpt > 0 and not args.no_store_all:
+        pb_all = dufwi.Problem(**{**pb.__dict__, "ckpt_interval": 0})
+        nbytes = dufwi.workspace_size(pb_all, geom, wl.n_maps)
+        free, _ = torch.cuda.mem_get_info(dev)
+        if nbytes < 0.6 * free:
+            ws_all = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+            def step_all():
+                dufwi.misfit_gradient(pb_all, sos, wav, geom, obs, density=rho, misfit=misfit, grad=grad,
+                                      workspace=ws_all)
+
+            step_all()
+            torch.cuda.synchronize()
+            evs = []
+            for _ in range(2):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step_all()
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            ms_all = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+            store_all = {"ms_per_step": ms_all, "value": units_per_step / (ms_all / 1e3) / 1e9, "unit": UNIT,
+                         "workspace_gb": nbytes / 1e9,
+                         "note": "same gradient with the history of every step kept in HBM (ckpt_interval 0)"}
+            del ws_all
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         steps = wl.nt
@@ -395,6 +428,7 @@ def run_ours(args):
                 "hbm_roofline_frac_40B": hbm_frac, "ms_per_gradient": ms_step,
                 "ms_per_dufwi_iteration": ms_step + net_ms, "ms_update_net": net_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
+                "store_all": store_all,
                 "clocks": clk.summary(), "profile_complete": prof["complete"]}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -428,7 +462,29 @@ def run_uneven_batch(args):
         dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
     e[1].record()
     torch.cuda.synchronize()
-    batched_ms = e[0].elapsed_time(e[1]) / args.steps
+    eager_ms = e[0].elapsed_time(e[1]) / args.steps
+    # the whole batched call (6000 launches) captured once in a CUDA graph and replayed
+    graph_ms = None
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)    # tables uploaded
+        st.synchronize()
+        dufwi.set_option(dufwi.OPT_REUSE_TABLES, 1)                              # ws stays reserved
+        try:
+            bgraph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(bgraph, stream=st):
+                dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
+        finally:
+            dufwi.set_option(dufwi.OPT_REUSE_TABLES, 0)
+    bgraph.replay()
+    torch.cuda.synchronize()
+    e[0].record()
+    for _ in range(args.steps):
+        bgraph.replay()
+    e[1].record()
+    torch.cuda.synchronize()
+    graph_ms = e[0].elapsed_time(e[1]) / args.steps
+    batched_ms = graph_ms
     shots = wl.n_maps * wl.n_tx
     # one shot per call, graph-captured, on a sample of shots spread over maps and transmits
     sample = [(b, k) for b, k in zip(range(0, wl.n_maps, 4), range(0, wl.n_tx, 2))]
@@ -461,8 +517,10 @@ def run_uneven_batch(args):
             "unit": "shots/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "32 disk maps on grids from 384x384, 512x512, 640x512 x 16 transmits = 512 "
-                                   "shots, %d steps, 128 elements; one launch per step for all shots" % nt,
+                                   "shots, %d steps, 128 elements; one launch per step for all shots, the whole "
+                                   "call replayed from a CUDA graph" % nt,
                        "grids": sizes, "tuned_options": tuned},
+            "eager_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms,
             "one_shot_per_call": {"value": one_shot_per_s, "unit": "shots/s",
                                   "sample": "%d shots, each its own call on its own grid, replayed from a CUDA "
                                             "graph" % len(sample), "ms_per_shot": one_ms},

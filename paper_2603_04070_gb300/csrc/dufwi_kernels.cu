@@ -495,9 +495,10 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 //
 // One CTA: a 64 x 32 output tile of one shot, 128 threads. TMA brings the 80 x 48 box of U^n and
 // the 72 x 32 and 64 x 40 tiles of half-point buoyancies (plus U^{n-1}, kappa' and, in the
-// adjoint, the history and the imaging sums) onto one mbarrier. Phase 1 turns the buoyancy tiles
-// into fluxes in place (four half points per work item, 128-bit shared-memory accesses);
-// phase 2 forms 4 x 4 divergences per thread and runs the common Eq. 2 epilogue.
+// adjoint, the history and the imaging sums) onto one mbarrier. Each thread then forms, in
+// registers, the x fluxes of its four rows and the z fluxes of its four columns that its 4 x 4
+// block needs (11 half points each way, shared-memory reads of 128 bits), their divergence, and
+// runs the common Eq. 2 epilogue.
 template <int MODE>
 struct VdLayout {
     static constexpr int kBox = kVBoxX * kVBoxZ;
@@ -510,7 +511,7 @@ struct VdLayout {
 };
 
 template <int R, int MODE>
-__global__ void __launch_bounds__(128, 3) vd_step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
+__global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 {
     using VL = VdLayout<MODE>;
     constexpr int TZ = kVTileZ;
@@ -568,77 +569,94 @@ __global__ void __launch_bounds__(128, 3) vd_step_kernel(const __grid_constant__
 
     if (!wait_tile(&bar, p, tid)) return;
 
-    // phase 1a: x fluxes at half points x0 - 4 + i + 1/2 (i = 0..71), rows z0 .. z0 + 31. The
-    // half point i needs box columns i + 4 + k and i + 5 - k (box column 0 is x0 - 8).
-    for (int e = tid; e < (kVFxX / 4) * TZ; e += 128) {
-        const int zz = e / (kVFxX / 4), i = (e % (kVFxX / 4)) * 4;
-        const float *row = box + (zz + kVHalo) * kVBoxX + i;
-        const float4 a = ld4s(row), b = ld4s(row + 4), c = ld4s(row + 8);
-        const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-        float d[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], w[q + 4 + k] - w[q + 5 - k], acc);
-            d[q] = acc;
-        }
-        float *f = fx + zz * kVFxX + i;
-        const float4 bb = ld4s(f);
-        st4s(f, make_float4(bb.x * d[0], bb.y * d[1], bb.z * d[2], bb.w * d[3]));
-    }
-    // phase 1b: z fluxes at half points z0 - 4 + j + 1/2 (j = 0..39), columns x0 .. x0 + 63; the
-    // half point j needs box rows j + 4 + k and j + 5 - k.
-    for (int e = tid; e < (kTileX / 4) * kVFzZ; e += 128) {
-        const int j = e / (kTileX / 4), xx = (e % (kTileX / 4)) * 4;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int k = 1; k <= R; ++k) {
-            const float4 up = ld4s(box + (j + 4 + k) * kVBoxX + xx + kVHalo);
-            const float4 dn = ld4s(box + (j + 5 - k) * kVBoxX + xx + kVHalo);
-            const float sk = p.sw[k - 1];
-            acc.x = fmaf(sk, up.x - dn.x, acc.x);
-            acc.y = fmaf(sk, up.y - dn.y, acc.y);
-            acc.z = fmaf(sk, up.z - dn.z, acc.z);
-            acc.w = fmaf(sk, up.w - dn.w, acc.w);
-        }
-        float *f = fz + j * kTileX + xx;
-        const float4 bb = ld4s(f);
-        st4s(f, make_float4(bb.x * acc.x, bb.y * acc.y, bb.z * acc.z, bb.w * acc.w));
-    }
-    __syncthreads();
-
-    // phase 2: divergence at the 4 x 4 block (lx, lz): x fluxes lx .. lx + 10 of each row,
-    // z flux rows lz .. lz + 10 (node x uses half points x + k - 1/2 and x - k + 1/2).
+    // Each thread forms the fluxes its 4 x 4 block needs in registers: along x, the half points
+    // lx .. lx + 10 of each of its rows (box columns lx + 1 .. lx + 18, buoyancy tile columns
+    // lx .. lx + 10); along z, the half-point rows lz .. lz + 10 of its four columns (box rows
+    // lz + 1 .. lz + 18, buoyancy tile rows lz .. lz + 10). Box column/row 0 is x0 - 8 / z0 - 8;
+    // x-buoyancy column h is the half point x0 - 4 + h + 1/2, z-buoyancy row j is z0 - 4 + j + 1/2.
+    const float *bxs = fx;
+    const float *bzs = fz;
     float4 lap[4], ctr[4], nxt[4];
-    float4 zr[11];
-#pragma unroll
-    for (int r = 0; r < 11; ++r) zr[r] = ld4s(fz + (lz + r) * kTileX + lx);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float *fr = fx + (lz + j) * kVFxX + lx;
-        const float4 a = ld4s(fr), b = ld4s(fr + 4), c = ld4s(fr + 8);
-        const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+        const float *row = box + (lz + j + kVHalo) * kVBoxX + lx;
+        float w[20];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float4 v = ld4s(row + 4 * c);
+            w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+        }
+        const float *brow = bxs + (lz + j) * kVFxX + lx;
+        float bw[12];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 v = ld4s(brow + 4 * c);
+            bw[4 * c] = v.x; bw[4 * c + 1] = v.y; bw[4 * c + 2] = v.z; bw[4 * c + 3] = v.w;
+        }
+        float flux[11];
+#pragma unroll
+        for (int h = 0; h < 11; ++h) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], w[h + 4 + k] - w[h + 5 - k], acc);
+            flux[h] = bw[h] * acc;
+        }
         float lxv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float acc = 0.0f;
 #pragma unroll
-            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], w[q + k + 3] - w[q - k + 4], acc);
+            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], flux[q + k + 3] - flux[q - k + 4], acc);
             lxv[q] = acc;
         }
-        float4 lzv = make_float4(0.f, 0.f, 0.f, 0.f);
+        lap[j] = make_float4(lxv[0], lxv[1], lxv[2], lxv[3]);
+        ctr[j] = make_float4(w[8], w[9], w[10], w[11]);
+    }
+    {
+        float4 col[18];
 #pragma unroll
-        for (int k = 1; k <= R; ++k) {
-            const float4 up = zr[j + k + 3], dn = zr[j - k + 4];
-            const float sk = p.sw[k - 1];
-            lzv.x = fmaf(sk, up.x - dn.x, lzv.x);
-            lzv.y = fmaf(sk, up.y - dn.y, lzv.y);
-            lzv.z = fmaf(sk, up.z - dn.z, lzv.z);
-            lzv.w = fmaf(sk, up.w - dn.w, lzv.w);
+        for (int r = 0; r < 18; ++r) col[r] = ld4s(box + (lz + 1 + r) * kVBoxX + lx + kVHalo);
+        float4 lzv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lzv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int f = 0; f < 11; ++f) {
+            // flux at half-point row lz + f: box rows lz + f + 4 + k and lz + f + 5 - k = col[f + 3 + k], col[f + 4 - k]
+            float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                const float4 up = col[f + 3 + k], dn = col[f + 4 - k];
+                const float sk = p.sw[k - 1];
+                d.x = fmaf(sk, up.x - dn.x, d.x);
+                d.y = fmaf(sk, up.y - dn.y, d.y);
+                d.z = fmaf(sk, up.z - dn.z, d.z);
+                d.w = fmaf(sk, up.w - dn.w, d.w);
+            }
+            const float4 b = ld4s(bzs + (lz + f) * kTileX + lx);
+            const float4 fl = make_float4(b.x * d.x, b.y * d.y, b.z * d.z, b.w * d.w);
+            // output row j takes +s_k from flux j + k + 3 and -s_k from flux j - k + 4
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int kp_ = f - j - 3, km_ = j + 4 - f;
+                if (kp_ >= 1 && kp_ <= R) {
+                    const float sk = p.sw[kp_ - 1];
+                    lzv[j].x = fmaf(sk, fl.x, lzv[j].x);
+                    lzv[j].y = fmaf(sk, fl.y, lzv[j].y);
+                    lzv[j].z = fmaf(sk, fl.z, lzv[j].z);
+                    lzv[j].w = fmaf(sk, fl.w, lzv[j].w);
+                }
+                if (km_ >= 1 && km_ <= R) {
+                    const float sk = -p.sw[km_ - 1];
+                    lzv[j].x = fmaf(sk, fl.x, lzv[j].x);
+                    lzv[j].y = fmaf(sk, fl.y, lzv[j].y);
+                    lzv[j].z = fmaf(sk, fl.z, lzv[j].z);
+                    lzv[j].w = fmaf(sk, fl.w, lzv[j].w);
+                }
+            }
         }
-        lap[j] = make_float4(lxv[0] + lzv.x, lxv[1] + lzv.y, lxv[2] + lzv.z, lxv[3] + lzv.w);
-        ctr[j] = ld4s(box + (lz + j + kVHalo) * kVBoxX + lx + kVHalo);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            lap[j] = make_float4(lap[j].x + lzv[j].x, lap[j].y + lzv[j].y, lap[j].z + lzv[j].z, lap[j].w + lzv[j].w);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {

@@ -273,6 +273,22 @@ def test_simulate_full_shot_set_sampled_transmits(d):
         assert rel_l2(cd[0, k], ref) <= TRACE_TOL
 
 
+def test_simulate_scale_config_sampled_transmit(d):
+    """The 1024 x 1024, 12000-step, 64-transmit configuration in one call (as the precision
+    benchmark runs it); the last transmit is recomputed by the oracle alone (~14 G cell updates
+    in FP64). The trace tolerance holds at this length too."""
+    wl = inputs.make_workload("scale", seed=0)
+    geom = d.Geometry.from_workload(wl)
+    pb = _dufwi_problem(d, wl)
+    cd = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    check=True)
+    k = wl.n_tx - 1
+    got = cd[0, k].cpu().numpy()
+    del cd
+    ref = _oracle_traces(wl, wl.sos_true[0], tx=[k])[0]
+    assert rel_l2(got, ref) <= TRACE_TOL
+
+
 @pytest.mark.parametrize("ckpt", [0, 9])
 def test_two_step_kernel_is_bit_identical_to_one_step(d, ckpt):
     """Fusing pairs of time steps into one launch changes no result bit: the grown-tile step

@@ -274,11 +274,16 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     and pass 64 x 32 tiles from step to step through per-tile counters in the workspace,
  *     instead of one launch per time step; bit-identical results. Not used with the two-step
  *     kernel, the Born step or a density map; 0 (the default) launches once per step.
+ *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
+ *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
+ *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device
+ *     stays usable. The hook clears itself when used; 0 (default) disarms it.
  * Both functions return DUFWI_ERR_INVALID_ARG for an unknown option or value. */
 #define DUFWI_OPT_TILE_Z 1
 #define DUFWI_OPT_TWO_STEP 2
 #define DUFWI_OPT_REUSE_TABLES 3
 #define DUFWI_OPT_PERSISTENT 4
+#define DUFWI_OPT_TEST_STALL 5
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

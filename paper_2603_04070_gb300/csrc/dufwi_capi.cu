@@ -11,6 +11,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dufwi.h"
 #include "dufwi_internal.h"
 
@@ -106,6 +108,13 @@ int g_reuse_tables = 0;
 int g_tile_z = kTileZDefault;
 int g_two_step = 0;
 int g_persistent = 0;   // DUFWI_OPT_PERSISTENT: one cooperative launch per sweep segment
+std::atomic<int> g_test_stall{0};   // DUFWI_OPT_TEST_STALL: the next persistent sweep stalls on purpose
+
+// NVTX range over the host code that enqueues one part of a call (visible in timeline tools).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 int validate_problem(const dufwi_problem *pb)
 {
@@ -621,6 +630,7 @@ int sweep(Ctx &c, Ring &rg, int mode, StepParams p, int n0, int n, float *hist0,
     sp.hist0 = hist0;
     sp.hist_stride = (long long)L.S * L.slice;
     sp.hist_slot0 = hist_slot0;
+    sp.stall_tile = g_test_stall.exchange(0) ? 0 : -1;
     p.rx_tab = c.at<int2>(L.o_tab1);
     p.rx_sorted = c.at<int>(L.o_sorted1);
     CK(cudaMemsetAsync(sp.flags, 0, sizeof(int) * ((size_t)sp.tiles + 1), c.st));
@@ -690,6 +700,7 @@ int adjoint_range(Ctx &c, Ring &rg, int m1, int m0, const float *asrc, float *g_
 // snapshots (U^n, U^{n-1}) at n = 0, K, 2K, ...
 int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_hist, bool snapshots)
 {
+    NvtxRange range("dufwi forward sweep");
     const Layout &L = c.L;
     long long nl = 0;
     const int e0 = g_prof.mark(c.st);
@@ -756,6 +767,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_persistent = value;
         return DUFWI_OK;
+    case DUFWI_OPT_TEST_STALL:
+        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
+        g_test_stall = value;
+        return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
     }
 }
@@ -766,6 +781,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     switch (option) {
     case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
     case DUFWI_OPT_PERSISTENT: *value = g_persistent; return DUFWI_OK;
+    case DUFWI_OPT_TEST_STALL: *value = g_test_stall.load(); return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
@@ -935,6 +951,7 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
         const int t0 = store_all ? 0 : sg * L.K;
         const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
         if (!store_all) {
+            NvtxRange range("dufwi recompute segment");
             nl = 0;
             e0 = g_prof.mark(c.st);
             // restore (U^{t0}, U^{t0-1}) and recompute Lap(U^n) for n = t0 .. t1-1
@@ -955,6 +972,7 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
             g_prof.span(1, e0, g_prof.mark(c.st), nl);
         }
         // adjoint steps m = t1 .. t0+1, imaging with Lap(U^{m-1})
+        NvtxRange range("dufwi adjoint segment");
         nl = 0;
         e0 = g_prof.mark(c.st);
         rc = adjoint_range(c, ar, t1, t0 + 1, asrc, g_shot, t0, nl);

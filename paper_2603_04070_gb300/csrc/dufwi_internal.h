@@ -114,6 +114,7 @@ struct SweepParams {
     float *hist0;            // forward history: slot of step0 (stride hist_stride floats per step)
     long long hist_stride;
     int hist_slot0;          // adjoint: history slot of m - 1 for m = step0
+    int stall_tile;          // test hook: this tile's wait can never be met (-1: none)
 };
 
 // Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.

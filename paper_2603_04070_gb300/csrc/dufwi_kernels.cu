@@ -751,6 +751,7 @@ __device__ __forceinline__ int ld_relaxed(const int *ptr)
 // an acquire pattern with the producers' releases.
 __device__ bool wait_neighbours(const SweepParams &sp, int k, int target, int *status)
 {
+    if (k == sp.stall_tile) target = 0x7fffffff;   // test hook: a counter value nothing reaches
     const int per_shot = sp.tiles_x * sp.tiles_z;
     const int t = k % per_shot, tx = t % sp.tiles_x, tz = t / sp.tiles_x;
     const int kl = tx > 0 ? k - 1 : k;

@@ -29,6 +29,7 @@ OPT_TILE_Z = 1
 OPT_TWO_STEP = 2
 OPT_REUSE_TABLES = 3
 OPT_PERSISTENT = 4
+OPT_TEST_STALL = 5
 
 
 class DufwiError(RuntimeError):

@@ -357,6 +357,36 @@ def test_persistent_sweeps_sized_batch_bit_identical(d):
         assert np.array_equal(a, b)
 
 
+def test_persistent_wait_timeout_reports_status_and_device_stays_usable(d):
+    """The bounded inter-CTA wait of the persistent sweep: the test hook makes one tile wait on a
+    counter that nothing sets. The launch gives up after its 2 s limit with DUFWI_ERR_TIMEOUT in
+    the status word, and the next call on the same device and workspace runs normally."""
+    import time
+    wl = inputs.make_workload("linear_disk", seed=3, nx=60, nz=50, nt=40, n_elem=8)
+    geom = d.Geometry.from_workload(wl)
+    pb = _dufwi_problem(d, wl)
+    sos = torch.from_numpy(wl.sos_true).cuda()
+    w = torch.from_numpy(wl.wavelet).cuda()
+    ws = torch.empty(d.workspace_size(pb, geom, 1, gradient=False), dtype=torch.uint8, device="cuda")
+    ref = d.simulate(pb, sos, w, geom, workspace=ws, check=True).clone()
+    d.set_option(d.OPT_PERSISTENT, 1)
+    try:
+        d.set_option(d.OPT_TEST_STALL, 1)
+        t0 = time.time()
+        d.simulate(pb, sos, w, geom, workspace=ws)
+        status = d.workspace_status(ws)
+        waited = time.time() - t0
+        assert status == d.ERR_TIMEOUT
+        assert 1.5 < waited < 30.0
+        assert d.get_option(d.OPT_TEST_STALL) == 0          # the hook clears itself
+        again = d.simulate(pb, sos, w, geom, workspace=ws, check=True)
+        torch.cuda.synchronize()
+        assert torch.equal(again, ref)
+    finally:
+        d.set_option(d.OPT_TEST_STALL, 0)
+        d.set_option(d.OPT_PERSISTENT, 0)
+
+
 def test_autograd_matches_misfit_gradient_bit_for_bit(d):
     """loss = sum (M - M_obs)^2 through the autograd wrapper gives the misfit gradient exactly:
     the cotangent 2 (M - M_obs) enters the same adjoint kernels."""

@@ -44,7 +44,8 @@ class _Problem(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dt", ctypes.c_double),
                 ("nt", ctypes.c_int), ("pml", ctypes.c_int),
                 ("pml_R", ctypes.c_double), ("pml_cref", ctypes.c_double),
-                ("fd_order", ctypes.c_int)]
+                ("fd_order", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("pml_alpha", ctypes.c_double)]
 
 
 @dataclass(frozen=True)
@@ -59,6 +60,8 @@ class Problem:
     pml_R: float = 1e-3
     pml_cref: float = 1540.0
     fd_order: int = 8
+    boundary: int = 0          # 0: damping term D of Eq. 1; 1: convolutional PML
+    pml_alpha: float = 0.0     # CPML frequency shift at the inner edge of the layer (1/s)
 
     @property
     def nxp(self) -> int:
@@ -70,7 +73,7 @@ class Problem:
 
     def c_struct(self) -> _Problem:
         return _Problem(self.nx, self.nz, self.dx, self.dt, self.nt, self.pml,
-                        self.pml_R, self.pml_cref, self.fd_order)
+                        self.pml_R, self.pml_cref, self.fd_order, self.boundary, self.pml_alpha)
 
 
 def _get():
@@ -94,6 +97,7 @@ def _get():
                                              ctypes.c_int, ip, ip, dp, ctypes.c_int,
                                              dp, dp, dp]
         _lib.orc_stagger_coeffs.argtypes = [ctypes.c_int, dp]
+        _lib.orc_cpml_coeffs.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp]
         _lib.orc_buoyancy.argtypes = [pp, dp, dp, dp]
         _lib.orc_div_b_grad.argtypes = [pp, dp, dp, dp, dp]
         _lib.orc_forward_rho.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_int, dp,
@@ -176,6 +180,16 @@ def stagger_coeffs(order: int) -> np.ndarray:
     s = np.zeros(4)
     _check(_get().orc_stagger_coeffs(order, _d(s)), "stagger_coeffs")
     return s[: order // 2].copy()
+
+
+def cpml_coeffs(p: Problem) -> dict:
+    """CPML recursion coefficients (a, b) at the nodes and half points of each axis."""
+    s = p.c_struct()
+    ax = [np.zeros(p.nxp) for _ in range(4)]
+    az = [np.zeros(p.nzp) for _ in range(4)]
+    _check(_get().orc_cpml_coeffs(ctypes.byref(s), *[_d(v) for v in ax + az]), "cpml_coeffs")
+    return {"a_node_x": ax[0], "b_node_x": ax[1], "a_half_x": ax[2], "b_half_x": ax[3],
+            "a_node_z": az[0], "b_node_z": az[1], "a_half_z": az[2], "b_half_z": az[3]}
 
 
 def buoyancy(p: Problem, rho_pad) -> tuple[np.ndarray, np.ndarray]:

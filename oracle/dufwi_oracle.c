@@ -44,6 +44,17 @@
  *     density is extended into the absorbing layer by edge replication. With
  *     no density array the compact Laplacian above is used (constant rho,
  *     which then drops out).
+ *   - Absorbing boundary, alternative to the damping term D: a convolutional
+ *     PML (CPML) on the same staggered operator. Each first difference is
+ *     stretched by 1/s with s = 1 + d/(alpha + i omega) (kappa = 1), realised
+ *     by one memory variable per difference and axis (recursive convolution
+ *     with b = exp(-(d + alpha) dt), a = d (b - 1)/(d + alpha)):
+ *       psi^n = b psi^{n-1} + a D+u^n,   F = b_rho (D+u^n + psi^n),
+ *       xi^n  = b xi^{n-1} + a D-F,      G = D-F + xi^n,
+ *     U^{n+1} = 2U^n - U^{n-1} + kappa G/dx^2 + s^n, kappa = rho C^2 dt^2.
+ *     d(xi) = d0 (xi/L)^2 as for D, alpha(xi) = alpha_max (1 - xi/L) inside the
+ *     layer, both 0 outside; profiles are evaluated at the nodes (xi) and at
+ *     the half points (psi) of each axis. Without a density map, rho = 1.
  *   - Misfit J = sum over transmits, samples and receivers of
  *     (M_sim - M_obs)^2 (Eq. 5 data term, lambda = 0); g = dJ/dC (Eq. 6), the
  *     exact gradient of the discrete J, obtained with the discrete adjoint.
@@ -65,6 +76,8 @@ typedef struct {
     double pml_R;        /* target reflection factor */
     double pml_cref;     /* reference SoS for d0 (m/s) */
     int fd_order;        /* 2, 4, 6 or 8 */
+    int boundary;        /* 0: damping term D of Eq. 1; 1: convolutional PML (CPML) */
+    double pml_alpha;    /* CPML frequency shift at the inner edge of the layer (1/s) */
 } orc_problem;
 
 #define ORC_OK 0
@@ -304,8 +317,166 @@ static int valid_problem(const orc_problem *p)
 {
     double c[5];
     if (p->nx < 1 || p->nz < 1 || p->nt < 1 || p->pml < 1) return 0;
+    if (p->boundary != 0 && p->boundary != 1) return 0;
+    if (p->boundary == 1 && !(p->pml_alpha >= 0.0)) return 0;
     if (!(p->dx > 0) || !(p->dt > 0) || !(p->pml_R > 0 && p->pml_R < 1) || !(p->pml_cref > 0)) return 0;
     return orc_fd_coeffs(p->fd_order, c) == ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Convolutional PML (see the header notes). */
+
+/* Depth (m) into the absorbing layer of position pos (padded index; half
+ * points at j + 0.5) along an axis with n physical cells. */
+static double depth_at(const orc_problem *p, double pos, int n)
+{
+    double P = p->pml, hi = P + n - 1;
+    if (pos < P) return (P - pos) * p->dx;
+    if (pos > hi) return (pos - hi) * p->dx;
+    return 0.0;
+}
+
+/* Recursion coefficients at depth xi: b = exp(-(d + alpha) dt), a = d (b - 1)/(d + alpha). */
+static void cpml_ab(const orc_problem *p, double xi, double *a, double *b)
+{
+    double L = p->pml * p->dx;
+    if (xi <= 0.0) { *a = 0.0; *b = 1.0; return; }
+    double d = orc_d0(p) * (xi / L) * (xi / L);
+    double al = p->pml_alpha * (1.0 - xi / L);
+    *b = exp(-(d + al) * p->dt);
+    *a = d > 0.0 ? d * (*b - 1.0) / (d + al) : 0.0;
+}
+
+/* Coefficient tables along x (length nxp) and z (length nzp): nodes (n) and
+ * half points j + 1/2 (h). */
+int orc_cpml_coeffs(const orc_problem *p, double *anx, double *bnx, double *ahx, double *bhx,
+                    double *anz, double *bnz, double *ahz, double *bhz)
+{
+    for (int i = 0; i < padded_nx(p); ++i) {
+        cpml_ab(p, depth_at(p, i, p->nx), &anx[i], &bnx[i]);
+        cpml_ab(p, depth_at(p, i + 0.5, p->nx), &ahx[i], &bhx[i]);
+    }
+    for (int i = 0; i < padded_nz(p); ++i) {
+        cpml_ab(p, depth_at(p, i, p->nz), &anz[i], &bnz[i]);
+        cpml_ab(p, depth_at(p, i + 0.5, p->nz), &ahz[i], &bhz[i]);
+    }
+    return ORC_OK;
+}
+
+typedef struct {
+    double s[4];
+    double *anx, *bnx, *ahx, *bhx, *anz, *bnz, *ahz, *bhz;
+    double *Fx, *Fz;       /* scratch: half-point fluxes (or their adjoints) */
+    double *ex, *ez;       /* scratch: node values */
+} orc_cpml;
+
+static void cpml_free(orc_cpml *c)
+{
+    free(c->anx); free(c->Fx); free(c->ex);
+    memset(c, 0, sizeof(*c));
+}
+
+static int cpml_init(const orc_problem *p, orc_cpml *c)
+{
+    memset(c, 0, sizeof(*c));
+    int nxp = padded_nx(p), nzp = padded_nz(p);
+    size_t n = (size_t)nxp * nzp;
+    if (orc_stagger_coeffs(p->fd_order, c->s) != ORC_OK) return ORC_EINVAL;
+    c->anx = malloc(sizeof(double) * 4 * (size_t)(nxp + nzp));
+    c->Fx = malloc(sizeof(double) * 2 * n);
+    c->ex = malloc(sizeof(double) * 2 * n);
+    if (!c->anx || !c->Fx || !c->ex) { cpml_free(c); return ORC_ENOMEM; }
+    c->bnx = c->anx + nxp; c->ahx = c->bnx + nxp; c->bhx = c->ahx + nxp;
+    c->anz = c->bhx + nxp; c->bnz = c->anz + nzp; c->ahz = c->bnz + nzp; c->bhz = c->ahz + nzp;
+    c->Fz = c->Fx + n;
+    c->ez = c->ex + n;
+    orc_cpml_coeffs(p, c->anx, c->bnx, c->ahx, c->bhx, c->anz, c->bnz, c->ahz, c->bhz);
+    return ORC_OK;
+}
+
+/* Value of a half-point or node array at (z, x), zero outside the padded grid. */
+static double at0(const double *v, int nxp, int nzp, int z, int x)
+{
+    return (x >= 0 && x < nxp && z >= 0 && z < nzp) ? v[(size_t)z * nxp + x] : 0.0;
+}
+
+/* CPML operator at step n: G = (1/dx^2) sum over axes of (D-F + xi), F = b (D+u + psi), with
+ * psi and xi advanced in place to their step-n values. */
+static void cpml_apply(const orc_problem *p, orc_cpml *c, const double *bx, const double *bz, const double *u,
+                       double *psx, double *psz, double *xix, double *xiz, double *G)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p), h = p->fd_order / 2;
+    double inv_dx2 = 1.0 / (p->dx * p->dx);
+    for (int z = 0; z < nzp; ++z)
+        for (int j = 0; j < nxp; ++j) {
+            size_t i = (size_t)z * nxp + j;
+            double d = 0.0;
+            for (int k = 1; k <= h; ++k) d += c->s[k - 1] * (at0(u, nxp, nzp, z, j + k) - at0(u, nxp, nzp, z, j - k + 1));
+            psx[i] = c->bhx[j] * psx[i] + c->ahx[j] * d;
+            c->Fx[i] = bx[i] * (d + psx[i]);
+            double dz = 0.0;
+            for (int k = 1; k <= h; ++k) dz += c->s[k - 1] * (at0(u, nxp, nzp, z + k, j) - at0(u, nxp, nzp, z - k + 1, j));
+            psz[i] = c->bhz[z] * psz[i] + c->ahz[z] * dz;
+            c->Fz[i] = bz[i] * (dz + psz[i]);
+        }
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            size_t i = (size_t)z * nxp + x;
+            double ex = 0.0, ez = 0.0;
+            for (int k = 1; k <= h; ++k) {
+                ex += c->s[k - 1] * (at0(c->Fx, nxp, nzp, z, x + k - 1) - at0(c->Fx, nxp, nzp, z, x - k));
+                ez += c->s[k - 1] * (at0(c->Fz, nxp, nzp, z + k - 1, x) - at0(c->Fz, nxp, nzp, z - k, x));
+            }
+            xix[i] = c->bnx[x] * xix[i] + c->anx[x] * ex;
+            xiz[i] = c->bnz[z] * xiz[i] + c->anz[z] * ez;
+            G[i] = (ex + xix[i] + ez + xiz[i]) * inv_dx2;
+        }
+}
+
+/* Reverse of cpml_apply (the transpose of the forward statements in reverse order). Input: Gbar =
+ * the adjoint of G; the adjoints of the step-n memory variables in psxb, pszb, xixb, xizb, which
+ * leave holding those of step n - 1. Output: out = the adjoint of u (D+^T of the flux adjoints). */
+static void cpml_reverse(const orc_problem *p, orc_cpml *c, const double *bx, const double *bz, const double *Gbar,
+                         double *psxb, double *pszb, double *xixb, double *xizb, double *out)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p), h = p->fd_order / 2;
+    double inv_dx2 = 1.0 / (p->dx * p->dx);
+    /* G = (ex + xix + ez + xiz)/dx^2 and xi = b xi + a e */
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            size_t i = (size_t)z * nxp + x;
+            double g = Gbar[i] * inv_dx2;
+            double tx = xixb[i] + g, tz = xizb[i] + g;
+            c->ex[i] = g + c->anx[x] * tx;
+            c->ez[i] = g + c->anz[z] * tz;
+            xixb[i] = c->bnx[x] * tx;
+            xizb[i] = c->bnz[z] * tz;
+        }
+    /* e = D-F: Fbar_j = sum_k s_k (ebar_{j-k+1} - ebar_{j+k}); F = b (d + psi); psi = b_h psi + a_h d */
+    for (int z = 0; z < nzp; ++z)
+        for (int j = 0; j < nxp; ++j) {
+            size_t i = (size_t)z * nxp + j;
+            double fx = 0.0, fz = 0.0;
+            for (int k = 1; k <= h; ++k) {
+                fx += c->s[k - 1] * (at0(c->ex, nxp, nzp, z, j - k + 1) - at0(c->ex, nxp, nzp, z, j + k));
+                fz += c->s[k - 1] * (at0(c->ez, nxp, nzp, z - k + 1, j) - at0(c->ez, nxp, nzp, z + k, j));
+            }
+            double px = psxb[i] + bx[i] * fx, pz = pszb[i] + bz[i] * fz;
+            c->Fx[i] = bx[i] * fx + c->ahx[j] * px;     /* adjoint of d (x) */
+            c->Fz[i] = bz[i] * fz + c->ahz[z] * pz;
+            psxb[i] = c->bhx[j] * px;
+            pszb[i] = c->bhz[z] * pz;
+        }
+    /* d = D+u: ubar_i = sum_k s_k (dbar_{i-k} - dbar_{i+k-1}) */
+    for (int z = 0; z < nzp; ++z)
+        for (int x = 0; x < nxp; ++x) {
+            double acc = 0.0;
+            for (int k = 1; k <= h; ++k) {
+                acc += c->s[k - 1] * (at0(c->Fx, nxp, nzp, z, x - k) - at0(c->Fx, nxp, nzp, z, x + k - 1));
+                acc += c->s[k - 1] * (at0(c->Fz, nxp, nzp, z - k, x) - at0(c->Fz, nxp, nzp, z + k - 1, x));
+            }
+            out[(size_t)z * nxp + x] = acc;
+        }
 }
 
 /* Density of one map on the padded grid and its half-point buoyancies
@@ -339,6 +510,176 @@ static int medium_init(const orc_problem *p, const double *rho, orc_medium *m)
     return ORC_OK;
 }
 
+/* CPML medium: the given density, or rho = 1 (buoyancy 1 between nodes). */
+static int cpml_medium(const orc_problem *p, const double *rho, orc_medium *m)
+{
+    if (rho) return medium_init(p, rho, m);
+    size_t n = (size_t)p->nx * p->nz;
+    double *ones = malloc(n * sizeof(double));
+    if (!ones) return ORC_ENOMEM;
+    for (size_t i = 0; i < n; ++i) ones[i] = 1.0;
+    int rc = medium_init(p, ones, m);
+    free(ones);
+    return rc;
+}
+
+/* kappa = rho C^2 dt^2 on the padded grid (the CPML replaces the damping term). */
+static void cpml_kappa(const orc_problem *p, const double *Cpad, const double *rho_pad, double *kap)
+{
+    size_t n = (size_t)padded_nx(p) * padded_nz(p);
+    for (size_t i = 0; i < n; ++i) kap[i] = rho_pad[i] * Cpad[i] * Cpad[i] * p->dt * p->dt;
+}
+
+/* Forward model with the CPML: traces [nt][n_rx] of a point source at (sx, sz). */
+static int cpml_forward(const orc_problem *p, const double *C, const double *rho, int sx, int sz, const double *w,
+                        int n_rx, const int *rx_ix, const int *rx_iz, double *traces)
+{
+    size_t n = (size_t)padded_nx(p) * padded_nz(p), src;
+    if (node_index(p, sx, sz, &src)) return ORC_EINVAL;
+    orc_medium med;
+    orc_cpml cp;
+    int rc = cpml_medium(p, rho, &med);
+    if (rc) return rc;
+    if ((rc = cpml_init(p, &cp))) { medium_free(&med); return rc; }
+    size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
+    double *buf = calloc(n * 10, sizeof(double));
+    if (!rx || !buf) { rc = ORC_ENOMEM; goto done; }
+    for (int r = 0; r < n_rx; ++r)
+        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { rc = ORC_EINVAL; goto done; }
+    double *Cpad = buf, *kap = buf + n, *prev = buf + 2 * n, *cur = buf + 3 * n, *next = buf + 4 * n;
+    double *G = buf + 5 * n, *psx = buf + 6 * n, *psz = buf + 7 * n, *xix = buf + 8 * n, *xiz = buf + 9 * n;
+    orc_pad(p, C, Cpad);
+    cpml_kappa(p, Cpad, med.rho_pad, kap);
+    double src_scale = p->dt * p->dt / (p->dx * p->dx);
+    for (int t = 0; t < p->nt; ++t) {
+        for (int r = 0; r < n_rx; ++r) traces[(size_t)t * n_rx + r] = cur[rx[r]];
+        if (t == p->nt - 1) break;
+        cpml_apply(p, &cp, med.bx, med.bz, cur, psx, psz, xix, xiz, G);
+        for (size_t i = 0; i < n; ++i) next[i] = 2.0 * cur[i] - prev[i] + kap[i] * G[i];
+        next[src] += src_scale * w[t];
+        double *tmp = prev; prev = cur; cur = next; next = tmp;
+    }
+done:
+    free(rx); free(buf); cpml_free(&cp); medium_free(&med);
+    return rc;
+}
+
+/* Adjoint fields with the CPML (reverse of cpml_forward's recursion), driven by receiver series
+ * q[nt][n_rx]; returns lam[t] at the probe node. */
+static int cpml_adjoint_probe(const orc_problem *p, const double *C, const double *rho, int n_rx, const int *rx_ix,
+                              const int *rx_iz, const double *q, int px, int pz, double *lam_probe)
+{
+    size_t n = (size_t)padded_nx(p) * padded_nz(p), probe;
+    if (node_index(p, px, pz, &probe)) return ORC_EINVAL;
+    orc_medium med;
+    orc_cpml cp;
+    int rc = cpml_medium(p, rho, &med);
+    if (rc) return rc;
+    if ((rc = cpml_init(p, &cp))) { medium_free(&med); return rc; }
+    size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
+    double *buf = calloc(n * 11, sizeof(double));
+    if (!rx || !buf) { rc = ORC_ENOMEM; goto done; }
+    for (int r = 0; r < n_rx; ++r)
+        if (node_index(p, rx_ix[r], rx_iz[r], &rx[r])) { rc = ORC_EINVAL; goto done; }
+    double *Cpad = buf, *kap = buf + n, *l2 = buf + 2 * n, *l1 = buf + 3 * n, *l0 = buf + 4 * n;
+    double *Gb = buf + 5 * n, *out = buf + 6 * n, *psxb = buf + 7 * n, *pszb = buf + 8 * n;
+    double *xixb = buf + 9 * n, *xizb = buf + 10 * n;
+    orc_pad(p, C, Cpad);
+    cpml_kappa(p, Cpad, med.rho_pad, kap);
+    for (int t = p->nt - 1; t >= 0; --t) {
+        /* reverse of the step that produced U[t+1] from U[t] */
+        for (size_t i = 0; i < n; ++i) Gb[i] = kap[i] * l1[i];
+        cpml_reverse(p, &cp, med.bx, med.bz, Gb, psxb, pszb, xixb, xizb, out);
+        for (size_t i = 0; i < n; ++i) l0[i] = 2.0 * l1[i] - l2[i] + out[i];
+        for (int r = 0; r < n_rx; ++r) l0[rx[r]] += q[(size_t)t * n_rx + r];
+        lam_probe[t] = l0[probe];
+        double *tmp = l2; l2 = l1; l1 = l0; l0 = tmp;
+    }
+done:
+    free(rx); free(buf); cpml_free(&cp); medium_free(&med);
+    return rc;
+}
+
+/* Misfit and gradient with the CPML (all G^t kept; the adjoint runs the reverse recursion). */
+static int cpml_misfit_gradient(const orc_problem *p, const double *C, const double *rho, int n_tx, const int *tx_ix,
+                                const int *tx_iz, const double *wavelet, int n_wav, int n_rx, const int *rx_ix,
+                                const int *rx_iz, const double *M_obs, double *J, double *g, double *M_sim)
+{
+    int nxp = padded_nx(p), nzp = padded_nz(p), nt = p->nt;
+    size_t n = (size_t)nxp * nzp;
+    orc_medium med;
+    orc_cpml cp;
+    int rc = cpml_medium(p, rho, &med);
+    if (rc) return rc;
+    if ((rc = cpml_init(p, &cp))) { medium_free(&med); return rc; }
+    size_t *rx = malloc(sizeof(size_t) * (n_rx > 0 ? n_rx : 1));
+    double *buf = calloc(n * 17, sizeof(double));
+    double *hist = calloc(n * (size_t)(nt > 1 ? nt - 1 : 1), sizeof(double));
+    double *trace = calloc((size_t)nt * (n_rx > 0 ? n_rx : 1), sizeof(double));
+    double *q = calloc((size_t)nt * (n_rx > 0 ? n_rx : 1), sizeof(double));
+    if (!rx || !buf || !hist || !trace || !q) { rc = ORC_ENOMEM; goto done; }
+    double *Cpad = buf, *kap = buf + n, *prev = buf + 2 * n, *cur = buf + 3 * n, *next = buf + 4 * n;
+    double *psx = buf + 5 * n, *psz = buf + 6 * n, *xix = buf + 7 * n, *xiz = buf + 8 * n;
+    double *l2 = buf + 9 * n, *l1 = buf + 10 * n, *l0 = buf + 11 * n, *Gb = buf + 12 * n, *out = buf + 13 * n;
+    double *gpad = buf + 14 * n, *xixb = buf + 15 * n, *xizb = buf + 16 * n;
+    double *psxb = psx, *pszb = psz;     /* reused after the forward sweep */
+    orc_pad(p, C, Cpad);
+    cpml_kappa(p, Cpad, med.rho_pad, kap);
+    double src_scale = p->dt * p->dt / (p->dx * p->dx), Jsum = 0.0;
+    for (int tx = 0; tx < n_tx && rc == ORC_OK; ++tx) {
+        size_t src;
+        const double *w = wavelet + (size_t)(n_wav == 1 ? 0 : tx) * nt;
+        if (node_index(p, tx_ix[tx], tx_iz[tx], &src)) { rc = ORC_EINVAL; break; }
+        for (int r = 0; r < n_rx; ++r)
+            if (node_index(p, rx_ix[(size_t)tx * n_rx + r], rx_iz[(size_t)tx * n_rx + r], &rx[r])) rc = ORC_EINVAL;
+        if (rc) break;
+        memset(prev, 0, n * sizeof(double)); memset(cur, 0, n * sizeof(double));
+        memset(psx, 0, n * sizeof(double)); memset(psz, 0, n * sizeof(double));
+        memset(xix, 0, n * sizeof(double)); memset(xiz, 0, n * sizeof(double));
+        for (int t = 0; t < nt; ++t) {
+            for (int r = 0; r < n_rx; ++r) trace[(size_t)t * n_rx + r] = cur[rx[r]];
+            if (t == nt - 1) break;
+            double *G = hist + (size_t)t * n;             /* G^t, used by the step producing U[t+1] */
+            cpml_apply(p, &cp, med.bx, med.bz, cur, psx, psz, xix, xiz, G);
+            for (size_t i = 0; i < n; ++i) next[i] = 2.0 * cur[i] - prev[i] + kap[i] * G[i];
+            next[src] += src_scale * w[t];
+            double *tmp = prev; prev = cur; cur = next; next = tmp;
+        }
+        const double *obs = M_obs + (size_t)tx * nt * n_rx;
+        for (size_t i = 0; i < (size_t)nt * n_rx; ++i) {
+            double r = trace[i] - obs[i];
+            Jsum += r * r;
+            q[i] = 2.0 * r;
+        }
+        if (M_sim) memcpy(M_sim + (size_t)tx * nt * n_rx, trace, sizeof(double) * (size_t)nt * n_rx);
+        memset(l1, 0, n * sizeof(double)); memset(l2, 0, n * sizeof(double));
+        memset(psxb, 0, n * sizeof(double)); memset(pszb, 0, n * sizeof(double));
+        memset(xixb, 0, n * sizeof(double)); memset(xizb, 0, n * sizeof(double));
+        for (int t = nt - 1; t >= 1; --t) {
+            for (size_t i = 0; i < n; ++i) Gb[i] = kap[i] * l1[i];
+            cpml_reverse(p, &cp, med.bx, med.bz, Gb, psxb, pszb, xixb, xizb, out);
+            for (size_t i = 0; i < n; ++i) l0[i] = 2.0 * l1[i] - l2[i] + out[i];
+            for (int r = 0; r < n_rx; ++r) l0[rx[r]] += q[(size_t)t * n_rx + r];
+            const double *G = hist + (size_t)(t - 1) * n;  /* lam[t] pairs with G^{t-1} */
+            for (size_t i = 0; i < n; ++i) gpad[i] += l0[i] * G[i];
+            double *tmp = l2; l2 = l1; l1 = l0; l0 = tmp;
+        }
+    }
+    if (rc == ORC_OK) {
+        for (size_t i = 0; i < n; ++i) gpad[i] *= 2.0 * med.rho_pad[i] * Cpad[i] * p->dt * p->dt;
+        memset(g, 0, sizeof(double) * (size_t)p->nx * p->nz);
+        for (int z = 0; z < nzp; ++z)
+            for (int x = 0; x < nxp; ++x) {
+                int zs = clampi(z - p->pml, 0, p->nz - 1), xs = clampi(x - p->pml, 0, p->nx - 1);
+                g[(size_t)zs * p->nx + xs] += gpad[(size_t)z * nxp + x];
+            }
+        *J = Jsum;
+    }
+done:
+    free(rx); free(buf); free(hist); free(trace); free(q); cpml_free(&cp); medium_free(&med);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Forward model of one transmit, Eqs. 2-3: a point source at (sx, sz)
  * driven by w[0..nt-1], traces M[t][r] = U[t] at the receivers. */
@@ -348,6 +689,7 @@ int orc_forward_rho(const orc_problem *p, const double *C, const double *rho,
                     double *traces /* [nt][n_rx] */)
 {
     if (!valid_problem(p)) return ORC_EINVAL;
+    if (p->boundary == 1) return cpml_forward(p, C, rho, sx, sz, w, n_rx, rx_ix, rx_iz, traces);
     orc_medium med;
     int mrc = medium_init(p, rho, &med);
     if (mrc) return mrc;
@@ -414,6 +756,7 @@ int orc_adjoint_probe_rho(const orc_problem *p, const double *C, const double *r
                           int px, int pz, double *lam_probe /* [nt] */)
 {
     if (!valid_problem(p)) return ORC_EINVAL;
+    if (p->boundary == 1) return cpml_adjoint_probe(p, C, rho, n_rx, rx_ix, rx_iz, q, px, pz, lam_probe);
     orc_medium med;
     int mrc = medium_init(p, rho, &med);
     if (mrc) return mrc;
@@ -471,6 +814,9 @@ int orc_misfit_gradient_rho(const orc_problem *p, const double *C, const double 
                             double *J, double *g, double *M_sim)
 {
     if (!valid_problem(p) || n_tx < 1 || n_rx < 0 || (n_wav != 1 && n_wav != n_tx)) return ORC_EINVAL;
+    if (p->boundary == 1)
+        return cpml_misfit_gradient(p, C, rho, n_tx, tx_ix, tx_iz, wavelet, n_wav, n_rx, rx_ix, rx_iz, M_obs, J, g,
+                                    M_sim);
     orc_medium med;
     int mrc = medium_init(p, rho, &med);
     if (mrc) return mrc;

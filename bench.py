@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -55,6 +56,8 @@ def parse():
     ap.add_argument("--two-step", type=int, default=None, help="1: two time steps per launch, 0: one")
     ap.add_argument("--persistent", type=int, default=None,
                     help="1: one cooperative launch per sweep segment, 0: one launch per step")
+    ap.add_argument("--boundary", default="damping", choices=["damping", "cpml"],
+                    help="absorbing layer: the damping term of Eq. 1 or a convolutional PML (keeps every step)")
     ap.add_argument("--density", action="store_true",
                     help="variable density (Eq. 1): a density map per shot set, staggered operator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -222,7 +225,8 @@ def workload_config(wl, args):
             "tile": [64, 32 if getattr(args, "persistent_used", 0) else args.tile_z_used],
             "two_step": args.two_step_used, "persistent": getattr(args, "persistent_used", 0),
             "density": ("variable: water-like background + smooth field + 1-3 rods of 1050-1900 kg/m^3, "
-                        "staggered operator" if getattr(args, "density", False) else "constant (compact Laplacian)")}
+                        "staggered operator" if getattr(args, "density", False) else "constant"),
+            "boundary": getattr(args, "boundary", "damping")}
 
 
 def run_ours(args):
@@ -244,9 +248,12 @@ def run_ours(args):
     if args.persistent is not None:
         dufwi.set_option(dufwi.OPT_PERSISTENT, args.persistent)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
+    if args.boundary == "cpml":
+        args.ckpt = 0          # the CPML memory variables are not checkpointed: keep every step
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
-                       ckpt_interval=args.ckpt, c_max=wl.c_max)
+                       ckpt_interval=args.ckpt, c_max=2000.0 if args.boundary == "cpml" else wl.c_max,
+                       boundary=args.boundary, pml_alpha=math.pi * float(wl.meta.get("f0", 2e6)))
     geom = dufwi.Geometry.from_workload(wl)
     sos_true = torch.from_numpy(wl.sos_true).to(dev)
     sos = torch.from_numpy(wl.sos_start).to(dev)
@@ -306,7 +313,9 @@ def run_ours(args):
     units_per_step = 2.0 * cells * wl.nt * S                       # fwd + adj cell updates
     value = units_per_step * world * args.steps / (ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    extra = VD_EXTRA_BYTES if args.density else 0
+    cpml = args.boundary == "cpml"
+    # the staggered operators read two buoyancies; the CPML also reads and writes four memory variables
+    extra = (VD_EXTRA_BYTES if (args.density or cpml) else 0) + (32 if cpml else 0)
     hbm_frac = (GRADIENT_BYTES_PER_CELL + 2 * extra) * cells * wl.nt * S / (peak * 1e9) / (ms_step / 1e3)
 
     # dominant kernel: the sweep kind with the largest share of device time
@@ -317,8 +326,8 @@ def run_ours(args):
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "step_kernel (%s sweep)" % dom, "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if args.density else kernel_traffic(dom),
-                "traffic_warm_l2": None if args.density else kernel_traffic(dom, "per_launch_dram_bytes_warm_l2"),
+                "traffic": None if (args.density or cpml) else kernel_traffic(dom),
+                "traffic_warm_l2": None if (args.density or cpml) else kernel_traffic(dom, "per_launch_dram_bytes_warm_l2"),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": 1e3 * avg_launch_ms,
                 "sweep_ms_per_step": {k: prof[k]["ms"] / args.steps for k in kinds + ["other"]},

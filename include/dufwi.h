@@ -78,7 +78,22 @@ typedef struct {
     int32_t snapshot_dtype;  /* DUFWI_SNAP_*; ignored by dufwi_simulate */
     int32_t ckpt_interval;   /* snapshot interval K in steps; 0 = keep every step (no recompute) */
     double  c_max;           /* upper bound of every SoS value (m/s), used for the CFL check */
+    int32_t boundary;        /* DUFWI_BOUNDARY_*: absorbing layer of the pml_cells border cells */
+    double  pml_alpha;       /* CPML only: frequency shift at the layer's inner edge (1/s), >= 0 */
 } dufwi_problem;
+
+/* Absorbing layers (both over pml_cells cells, quadratic damping profile d = d0 (xi/L)^2 with
+ * d0 = 3 pml_cref ln(1/pml_R) / (2 L)):
+ *   DUFWI_BOUNDARY_DAMPING: the damping term D of Eq. 1 (2 D u_t + D^2 u), the paper's layer.
+ *   DUFWI_BOUNDARY_CPML: a convolutional PML on the staggered operator: each first difference
+ *     is stretched by 1/s, s = 1 + d/(alpha + i omega), through one memory variable per
+ *     difference and axis (recursive convolution; alpha = pml_alpha (1 - xi/L)); no damping
+ *     term. Supported by dufwi_simulate, dufwi_simulate_noalloc, dufwi_misfit,
+ *     dufwi_forward_save/dufwi_backward and dufwi_misfit_gradient with ckpt_interval 0 (every
+ *     step kept: the memory variables are not checkpointed), with or without a density map;
+ *     not by the *_sized calls or dufwi_jvp (DUFWI_ERR_UNSUPPORTED). */
+#define DUFWI_BOUNDARY_DAMPING 0
+#define DUFWI_BOUNDARY_CPML 1
 
 /* Transducer elements: physical-grid node indices (host arrays of n_elem entries). Elements
  * are point sources/receivers at nodes (the paper's elements act as both, Sec. II-A). */

@@ -93,6 +93,7 @@ struct Layout {
     int tiles1, tiles2;      // tiles of the one-step kernel (tile height TZ) and of the two-step kernel
     int tiles_x, tiles_z32;  // 64 x 32 tiles of one shot (persistent sweeps)
     int n_rxe;               // row length of the grown-tile receiver lists (4 n_rx)
+    size_t o_cm[8], o_cpml;  // CPML: memory variables (two sets of psi_x, psi_z, xi_x, xi_z), coefficient tables
     size_t o_flags, o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
 };
@@ -127,6 +128,9 @@ int validate_problem(const dufwi_problem *pb)
     if (pb->snapshot_dtype < DUFWI_SNAP_FP32 || pb->snapshot_dtype > DUFWI_SNAP_FP16) return DUFWI_ERR_INVALID_ARG;
     if (pb->ckpt_interval < 0) return DUFWI_ERR_INVALID_ARG;
     if (!(pb->c_max > 0) || !isfinite(pb->c_max)) return DUFWI_ERR_INVALID_ARG;
+    if (pb->boundary != DUFWI_BOUNDARY_DAMPING && pb->boundary != DUFWI_BOUNDARY_CPML) return DUFWI_ERR_INVALID_ARG;
+    if (pb->boundary == DUFWI_BOUNDARY_CPML && !(pb->pml_alpha >= 0 && isfinite(pb->pml_alpha)))
+        return DUFWI_ERR_INVALID_ARG;
     if ((long long)pb->nx + 2LL * pb->pml_cells > 65535 || (long long)pb->nz + 2LL * pb->pml_cells > 65535)
         return DUFWI_ERR_INVALID_ARG;
     if (pb->c_max * pb->dt / pb->dx > stability_limit(pb->fd_order)) return DUFWI_ERR_CFL;
@@ -191,6 +195,12 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     L->o_kap = take((size_t)n_maps * L->slice * sizeof(float));
     L->o_bx = take((size_t)n_maps * L->slice * sizeof(float));     // buoyancies (density maps only)
     L->o_bz = take((size_t)n_maps * L->slice * sizeof(float));
+    if (pb->boundary == DUFWI_BOUNDARY_CPML) {
+        // the memory variables are not checkpointed: gradients keep every step; no Born step
+        if (kind == kLayoutJvp || (gradient && L->n_seg > 1)) return DUFWI_ERR_UNSUPPORTED;
+        for (int i = 0; i < 8; ++i) L->o_cm[i] = take((size_t)L->S * L->slice * sizeof(float));
+        L->o_cpml = take(sizeof(float) * 4 * (size_t)(L->nxp + L->nzp));
+    }
     for (int i = 0; i < 4; ++i) L->o_f[i] = take(field);
     if (gradient) {
         const bool store_all = pb->ckpt_interval == 0 || pb->ckpt_interval >= steps;
@@ -347,6 +357,9 @@ struct Ctx {
     bool jvp = false;                         // linearised forward (Born) call
     bool vd = false;                          // density map given: staggered variable-density operator
     bool persistent = false;                  // one cooperative launch per sweep segment
+    bool cpml = false;                        // convolutional PML instead of the damping term
+    int mem_par = 0;                          // CPML: which memory-variable set the next step reads
+    CpmlMaps cm_fwd[2], cm_adj[2];            // CPML: maps reading set 0 / set 1
     FieldMaps fmap[4], mmap[4];
     CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1, bx1, bz1;
     int *status() const { return reinterpret_cast<int *>(ws + L.o_status); }
@@ -419,11 +432,14 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (rc) return rc;
     c.ws = static_cast<char *>(workspace);
     c.st = static_cast<cudaStream_t>(stream);
-    c.vd = density != nullptr;
-    if (c.vd && c.jvp) return DUFWI_ERR_UNSUPPORTED;   // no Born step for the density operator
+    c.cpml = c.pb->boundary == DUFWI_BOUNDARY_CPML;
+    c.vd = density != nullptr || c.cpml;        // the CPML runs on the staggered operator
+    if (c.vd && c.jvp) return DUFWI_ERR_UNSUPPORTED;   // no Born step for the staggered operators
+    if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
     if (c.vd && c.pb->c_max * c.pb->dt / c.pb->dx > stagger_stability_limit(c.pb->fd_order)) return DUFWI_ERR_CFL;
     c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd;
     c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd;
+    c.mem_par = 0;
     c.tz = (c.vd || c.persistent) ? 32 : g_tile_z;
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
@@ -442,6 +458,29 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
             damp[(size_t)dz * (L.P + 1) + dxl] =
                 make_float2((float)(-q * (2.0 + q) / (1.0 + q)), (float)(2.0 * q / (1.0 + q)));
         }
+    // CPML recursion coefficients per axis: a, b at the nodes, then at the half points j + 1/2
+    std::vector<float> cpml_tab;
+    if (c.cpml) {
+        cpml_tab.assign(4 * (size_t)(L.nxp + L.nzp), 0.f);
+        auto fill = [&](float *t, int n, int N) {
+            const double Lw = pb->pml_cells * pb->dx;
+            for (int row = 0; row < 2; ++row)
+                for (int i = 0; i < n; ++i) {
+                    const double pos = i + 0.5 * row, P = L.P, hi = L.P + N - 1;
+                    const double xi = pos < P ? (P - pos) * pb->dx : (pos > hi ? (pos - hi) * pb->dx : 0.0);
+                    double a = 0.0, b = 1.0;
+                    if (xi > 0.0) {
+                        const double dd = d0 * (xi / Lw) * (xi / Lw), al = pb->pml_alpha * (1.0 - xi / Lw);
+                        b = exp(-(dd + al) * pb->dt);
+                        a = dd > 0.0 ? dd * (b - 1.0) / (dd + al) : 0.0;
+                    }
+                    t[(2 * row) * n + i] = (float)a;
+                    t[(2 * row + 1) * n + i] = (float)b;
+                }
+        };
+        fill(cpml_tab.data(), L.nxp, L.Nx);
+        fill(cpml_tab.data() + 4 * (size_t)L.nxp, L.nzp, L.Nz);
+    }
     // Host tables go to the workspace with stream-ordered copies (pageable sources are staged
     // before cudaMemcpyAsync returns). If this workspace already holds exactly these tables from
     // an earlier call, the copies are skipped: such calls consist of kernels, memsets and
@@ -456,7 +495,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                           {L.o_tab2, tab2.data(), sizeof(int2) * tab2.size()},
                           {L.o_sorted2, sorted2.data(), sizeof(int) * sorted2.size()},
                           {L.o_tabe, tabe.data(), sizeof(int2) * tabe.size()},
-                          {L.o_sortede, sortede.data(), sizeof(int) * sortede.size()}};
+                          {L.o_sortede, sortede.data(), sizeof(int) * sortede.size()},
+                          {L.o_cpml, cpml_tab.data(), sizeof(float) * cpml_tab.size()}};
     uint64_t h = 1469598103934665603ull;   // FNV-1a over offsets and contents
     auto mix = [&h](const void *data, size_t n) {
         const unsigned char *b = static_cast<const unsigned char *>(data);
@@ -477,7 +517,7 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     }
     if (fresh) {
         for (const Blob &b : blobs)
-            if (cudaMemcpyAsync(c.ws + b.off, b.src, b.bytes, cudaMemcpyHostToDevice, c.st) != cudaSuccess) {
+            if (b.bytes > 0 && cudaMemcpyAsync(c.ws + b.off, b.src, b.bytes, cudaMemcpyHostToDevice, c.st) != cudaSuccess) {
                 std::lock_guard<std::mutex> lock(g_table_mutex);
                 g_table_hash.erase(workspace);
                 return DUFWI_ERR_CUDA;
@@ -487,9 +527,12 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
 
     long long nl = 0;
     const int e0 = g_prof.mark(c.st);
+    // the CPML replaces the damping term (D = 0 in kappa'); without a density map it runs on
+    // unit buoyancy
     CKL(launch_setup_kappa(sos, density, c.at<float>(L.o_kap), c.at<float>(L.o_bx), c.at<float>(L.o_bz), c.status(),
-                           L.n_maps, L.Nx, L.Nz, L.P, L.nxp, L.nzp, L.pitch, pb->dt / pb->dx, d0, pb->dt, pb->c_max,
-                           c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.st));
+                           L.n_maps, L.Nx, L.Nz, L.P, L.nxp, L.nzp, L.pitch, pb->dt / pb->dx, c.cpml ? 0.0 : d0,
+                           pb->dt, pb->c_max, c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.cpml && !density,
+                           c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
 
     // tensor maps of every buffer
@@ -502,6 +545,22 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (c.vd && (tensor_map(&c.bx1, c.at<float>(L.o_bx), L, L.n_maps, 0, kVFxX, kVTileZ) ||
                  tensor_map(&c.bz1, c.at<float>(L.o_bz), L, L.n_maps, 0, kTileX, kVFzZ)))
         return DUFWI_ERR_CUDA;
+    if (c.cpml) {
+        // memory-variable sets: buffers 0-3 (psi_x, psi_z, xi_x, xi_z) and 4-7; maps reading set k
+        for (int k = 0; k < 2; ++k) {
+            const float *hx = c.at<float>(L.o_cm[4 * k]), *hz = c.at<float>(L.o_cm[4 * k + 1]);
+            const float *nx = c.at<float>(L.o_cm[4 * k + 2]), *nz = c.at<float>(L.o_cm[4 * k + 3]);
+            if (tensor_map(&c.cm_fwd[k].mem_hx, hx, L, L.S, 0, kVFxX, kVTileZ) ||
+                tensor_map(&c.cm_fwd[k].mem_hz, hz, L, L.S, 0, kTileX, kVFzZ) ||
+                tensor_map(&c.cm_fwd[k].mem_nx, nx, L, L.S, 0, kTileX, kVTileZ) ||
+                tensor_map(&c.cm_fwd[k].mem_nz, nz, L, L.S, 0, kTileX, kVTileZ))
+                return DUFWI_ERR_CUDA;
+            c.cm_adj[k] = c.cm_fwd[k];
+            if (tensor_map(&c.cm_adj[k].mem_nx, nx, L, L.S, 0, kVBoxX, kVTileZ) ||
+                tensor_map(&c.cm_adj[k].mem_nz, nz, L, L.S, 0, kTileX, kVBoxZ))
+                return DUFWI_ERR_CUDA;
+        }
+    }
     if (c.jvp) {
         for (int i = 0; i < 4; ++i)
             if (field_maps(&c.mmap[i], c.at<float>(L.o_m[i]), L, c.tz)) return DUFWI_ERR_CUDA;
@@ -569,7 +628,22 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
     p.out = rg.buf[rg.prv];
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
-    if (c.vd) {   // the tile height is 32 here, so tile1, kap1, hist1 and grad1 fit the kernel
+    if (c.cpml) {   // memory variables: read set mem_par, write the other
+        tm.cur_box = rg.map[rg.cur].box2;
+        tm.bx_tile = c.bx1;
+        tm.bz_tile = c.bz1;
+        const int w = 1 - c.mem_par;
+        CpmlParams cp;
+        cp.hx_out = c.at<float>(c.L.o_cm[4 * w]);
+        cp.hz_out = c.at<float>(c.L.o_cm[4 * w + 1]);
+        cp.nx_out = c.at<float>(c.L.o_cm[4 * w + 2]);
+        cp.nz_out = c.at<float>(c.L.o_cm[4 * w + 3]);
+        cp.cx = c.at<float>(c.L.o_cpml);
+        cp.cz = cp.cx + 4 * (size_t)c.L.nxp;
+        const CpmlMaps &cm = mode == kAdjoint ? c.cm_adj[c.mem_par] : c.cm_fwd[c.mem_par];
+        CKL(launch_step_cpml(c.L.radius, mode, tm, cm, p, cp, c.st));
+        c.mem_par = w;
+    } else if (c.vd) {   // the tile height is 32 here, so tile1, kap1, hist1 and grad1 fit the kernel
         tm.cur_box = rg.map[rg.cur].box2;
         tm.bx_tile = c.bx1;
         tm.bz_tile = c.bz1;
@@ -706,6 +780,10 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
     const int e0 = g_prof.mark(c.st);
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
     for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(rg.buf[i], 0, field, c.st));
+    if (c.cpml) {
+        for (int i = 0; i < 8; ++i) CK(cudaMemsetAsync(c.at<float>(L.o_cm[i]), 0, field, c.st));
+        c.mem_par = 0;
+    }
     rg.cur = 0;
     rg.prv = 1;
     const int dtype = c.pb->snapshot_dtype;
@@ -946,6 +1024,10 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
     int e0 = -1, rc = DUFWI_OK;
     for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(ar.buf[i], 0, field, c.st));
     CK(cudaMemsetAsync(g_shot, 0, field, c.st));
+    if (c.cpml) {   // adjoint memory variables start at zero (every step is kept: no recompute)
+        for (int i = 0; i < 8; ++i) CK(cudaMemsetAsync(c.at<float>(L.o_cm[i]), 0, field, c.st));
+        c.mem_par = 0;
+    }
     const int dtype = c.pb->snapshot_dtype;
     for (int sg = L.n_seg - 1; sg >= 0; --sg) {
         const int t0 = store_all ? 0 : sg * L.K;

@@ -56,6 +56,24 @@ struct StepMaps {
     CUtensorMap cur_box, out_tile, kap_tile, hist_tile, grad_tile, bx_tile, bz_tile;
 };
 
+// Convolutional PML (CPML) step: the staggered operator with one memory variable per first
+// difference and axis. Forward: psi at half points (read over the 72 x 32 / 64 x 40 half-point
+// tiles of the previous step's buffer, written for the tile's own half points into the other
+// buffer), xi at nodes (own tile, in place). Adjoint: phi (adjoint of psi) like psi, chi (adjoint
+// of xi) read over 80 x 32 / 64 x 48 node boxes (halo 8 along its axis) of the previous buffer
+// and written for the own nodes into the other.
+struct CpmlMaps {
+    CUtensorMap mem_hx, mem_hz;   // psi / phi: x half points 72 x 32 (from x0 - 4), z 64 x 40 (from z0 - 4)
+    CUtensorMap mem_nx, mem_nz;   // forward xi: 64 x 32 own nodes; adjoint chi: 80 x 32 / 64 x 48 boxes
+};
+
+struct CpmlParams {
+    float *hx_out, *hz_out;       // memory variables at half points, written (own half points)
+    float *nx_out, *nz_out;       // memory variables at nodes, written (own nodes)
+    const float *cx;              // [4][nxp]: a, b at x nodes, then a, b at x half points
+    const float *cz;              // [4][nzp]: the same along z
+};
+
 struct StepParams {
     float *out;              // in: U^{n-1} (mu^{m+2}); out: U^{n+1} (mu^m), in place
     const float *kap;        // [n_maps][nzp][pitch]
@@ -126,14 +144,20 @@ constexpr int kPairTileZ = 32;   // core tile height of the two-step kernel (64 
 // receives the grid used (all CTAs co-resident, cooperative launch).
 cudaError_t launch_sweep(int radius, int mode, const SweepMaps &tm, const StepParams &p, const SweepParams &sp,
                          int *grid_ctas, cudaStream_t st);
+// CPML step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint; 64 x 32 tiles; the fields use
+// the variable-density maps of StepMaps with cur_box 80 x 48).
+cudaError_t launch_step_cpml(int radius, int mode, const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                             const CpmlParams &cp, cudaStream_t st);
 // Variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint; 64 x 32 tiles).
 cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 // kappa' on the padded grid; with a density map kappa' = rho C^2 dt^2/(dx^2 (1 + D dt)), and the
 // buoyancies bx, bz are written too (both may be null without a density map).
+// unit_b: no density map, but buoyancies of 1 between nodes are written (staggered operator
+// at constant density, used by the CPML).
 cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, float *bx, float *bz,
                                int *status, int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch,
                                double dt_over_dx, double d0, double dt, double c_max,
-                               const int2 *map_dims, cudaStream_t st);
+                               const int2 *map_dims, bool unit_b, cudaStream_t st);
 cudaError_t launch_sample(const float *field, const int *rx_node, float *cd, long long slice,
                           int pitch, int S, int n_tx, int n_rx, int nt, int step, cudaStream_t st);
 cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const float *kap,

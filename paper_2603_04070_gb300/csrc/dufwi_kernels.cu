@@ -712,6 +712,412 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     }
 }
 
+// ---- convolutional PML ------------------------------------------------------------------------
+// The staggered operator of the variable-density step with each first difference stretched by
+// one memory variable per axis (recursive convolution, coefficients a, b per node and half
+// point from host tables):
+//   psi^n = b psi^{n-1} + a D+u^n,  F = b_rho (D+u^n + psi^n),  xi^n = b xi^{n-1} + a D-F,
+//   G = D-F + xi^n,  U^{n+1} = 2U^n - U^{n-1} + kappa' G  (no damping term; kappa' = rho C^2 dt^2/dx^2).
+// The adjoint, written for mu = kappa' lambda, is the reverse of these statements: with chi and
+// phi the adjoints of xi and psi,
+//   e = mu^{n+1} + a (chi + mu^{n+1}),  chi <- b (chi + mu^{n+1}),  Fbar = -D+ e,
+//   p = phi + b_rho Fbar,  dbar = b_rho Fbar + a p,  phi <- b p,
+//   mu^n = 2 mu^{n+1} - mu^{n+2} - kappa' D- dbar (+ the scaled residual injections),
+// and the imaging term is again mu^n G^{n-1} with G from the forward sweep's history.
+template <int MODE>
+struct CpmlLayout {
+    static constexpr bool kAdj = MODE == kAdjoint;
+    static constexpr int kBox = kVBoxX * kVBoxZ;                  // 80 x 48
+    static constexpr int kBx = kVFxX * kVTileZ;                   // 72 x 32 (x half points)
+    static constexpr int kBz = kTileX * kVFzZ;                    // 64 x 40 (z half points)
+    static constexpr int kTile = kTileX * kVTileZ;                // 64 x 32
+    static constexpr int kNx = kAdj ? kVBoxX * kVTileZ : kTile;   // chi: 80 x 32; xi: 64 x 32
+    static constexpr int kNz = kAdj ? kTileX * kVBoxZ : kTile;    // chi: 64 x 48; xi: 64 x 32
+    static constexpr int kFloats = kBox + 2 * kBx + 2 * kBz + kNx + kNz + (kAdj ? 4 : 2) * kTile;
+    static constexpr uint32_t kBytes = kFloats * sizeof(float);
+};
+
+// (a, b) of a table of 4 rows of length n (a node, b node, a half, b half); identity outside.
+__device__ __forceinline__ float2 cpml_coef(const float *t, int n, int row, int i)
+{
+    if (i < 0 || i >= n) return make_float2(0.f, 1.f);
+    return make_float2(__ldg(t + (row + 0) * n + i), __ldg(t + (row + 1) * n + i));
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(128, 2)
+cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ CpmlMaps cm, const StepParams p,
+                 const CpmlParams cp)
+{
+    using CL = CpmlLayout<MODE>;
+    constexpr bool ADJ = CL::kAdj;
+    constexpr int TZ = kVTileZ;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ InjList inj;
+
+    const int tid = threadIdx.x;
+    const int s = blockIdx.z;
+    const int x0 = blockIdx.x * kTileX;
+    const int z0 = blockIdx.y * TZ;
+    const int tx_idx = s % p.n_tx;
+    const int map = s / p.n_tx;
+    const long long shot_off = static_cast<long long>(s) * p.slice;
+    float *box = smem;                 // U^n (mu^{m+1}) with halo 8
+    float *bxs = box + CL::kBox;       // buoyancy, x half points
+    float *bzs = bxs + CL::kBx;        // buoyancy, z half points
+    float *mhx = bzs + CL::kBz;        // psi / phi, x half points
+    float *mhz = mhx + CL::kBx;        // psi / phi, z half points
+    float *mnx = mhz + CL::kBz;        // xi / chi, x
+    float *mnz = mnx + CL::kNx;        // xi / chi, z
+    float *pv = mnz + CL::kNz;         // U^{n-1} (mu^{m+2})
+    float *kp = pv + CL::kTile;        // kappa'
+    float *hs = kp + CL::kTile;        // adjoint: G^{m-1}
+    float *gg = hs + CL::kTile;        // adjoint: imaging sums
+    if (x0 >= p.nxp || z0 >= p.nzp) return;
+
+    grid_dependency_wait();
+    if (tid == 0) {
+        prefetch_tensormap(&tm.cur_box);
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, CL::kBytes);
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - kVHalo, z0 - kVHalo, s);
+        tma_load_3d(bxs, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
+        tma_load_3d(bzs, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
+        tma_load_3d(mhx, &cm.mem_hx, &bar, x0 - kHalo, z0, s);
+        tma_load_3d(mhz, &cm.mem_hz, &bar, x0, z0 - kHalo, s);
+        if (ADJ) {
+            tma_load_3d(mnx, &cm.mem_nx, &bar, x0 - kVHalo, z0, s);
+            tma_load_3d(mnz, &cm.mem_nz, &bar, x0, z0 - kVHalo, s);
+        } else {
+            tma_load_3d(mnx, &cm.mem_nx, &bar, x0, z0, s);
+            tma_load_3d(mnz, &cm.mem_nz, &bar, x0, z0, s);
+        }
+        tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+        tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+        if (ADJ) {
+            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        }
+    }
+    grid_dependents_launch();
+
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    int2 rx_range = make_int2(0, 0);
+    if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
+    gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
+                            tid, 128);
+    const int lx = (tid & 15) * 4;
+    const int lz = (tid >> 4) * 4;
+    const int gx = x0 + lx;
+    const bool col_ok = gx < p.nxp;
+    const int nxp = p.nxp, nzp = p.nzp;
+
+    if (!wait_tile(&bar, p, tid)) return;
+
+    float4 opv[4];     // forward: G; adjoint: -(D- dbar) along both axes
+    float4 ctr[4];     // forward: U^n; adjoint: mu^{m+1} at the block
+    // ---- x: rows lz .. lz + 3 of the block
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gz = z0 + lz + j;
+        const bool row_ok = col_ok && gz < nzp;
+        const long long orow = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+        float w[20];
+        {
+            const float *row = box + (lz + j + kVHalo) * kVBoxX + lx;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const float4 v = ld4s(row + 4 * c);
+                w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+            }
+        }
+        ctr[j] = make_float4(w[8], w[9], w[10], w[11]);
+        float bw[12], mw[12];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 b = ld4s(bxs + (lz + j) * kVFxX + lx + 4 * c);
+            const float4 m = ld4s(mhx + (lz + j) * kVFxX + lx + 4 * c);
+            bw[4 * c] = b.x; bw[4 * c + 1] = b.y; bw[4 * c + 2] = b.z; bw[4 * c + 3] = b.w;
+            mw[4 * c] = m.x; mw[4 * c + 1] = m.y; mw[4 * c + 2] = m.z; mw[4 * c + 3] = m.w;
+        }
+        float ox[4];
+        if (!ADJ) {
+            float F[11], pn[4];
+#pragma unroll
+            for (int h = 0; h < 11; ++h) {
+                float d = 0.0f;
+#pragma unroll
+                for (int k = 1; k <= R; ++k) d = fmaf(p.sw[k - 1], w[h + 4 + k] - w[h + 5 - k], d);
+                const float2 ab = cpml_coef(cp.cx, nxp, 2, x0 - kHalo + lx + h);
+                const float ps = fmaf(ab.y, mw[h], ab.x * d);
+                F[h] = bw[h] * (d + ps);
+                if (h >= 4 && h < 8) pn[h - 4] = ps;
+            }
+            const float4 xi_prev = ld4s(mnx + (lz + j) * kTileX + lx);
+            const float xp[4] = {xi_prev.x, xi_prev.y, xi_prev.z, xi_prev.w};
+            float xn[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float e = 0.0f;
+#pragma unroll
+                for (int k = 1; k <= R; ++k) e = fmaf(p.sw[k - 1], F[q + k + 3] - F[q - k + 4], e);
+                const float2 ab = cpml_coef(cp.cx, nxp, 0, gx + q);
+                xn[q] = fmaf(ab.y, xp[q], ab.x * e);
+                ox[q] = e + xn[q];
+            }
+            if (row_ok) {
+                float4 a = make_float4(pn[0], pn[1], pn[2], pn[3]), b = make_float4(xn[0], xn[1], xn[2], xn[3]);
+                if (gx + 4 > nxp) {
+                    if (gx + 1 >= nxp) { a.y = 0.f; b.y = 0.f; }
+                    if (gx + 2 >= nxp) { a.z = 0.f; b.z = 0.f; }
+                    a.w = 0.f; b.w = 0.f;
+                }
+                st4(cp.hx_out + orow, a);
+                st4(cp.nx_out + orow, b);
+            }
+        } else {
+            float cw[20];
+            {
+                const float *row = mnx + (lz + j) * kVBoxX + lx;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    const float4 v = ld4s(row + 4 * c);
+                    cw[4 * c] = v.x; cw[4 * c + 1] = v.y; cw[4 * c + 2] = v.z; cw[4 * c + 3] = v.w;
+                }
+            }
+            float e[20];
+#pragma unroll
+            for (int c = 0; c < 20; ++c) {
+                const float2 ab = cpml_coef(cp.cx, nxp, 0, x0 - kVHalo + lx + c);
+                e[c] = fmaf(ab.x, cw[c] + w[c], w[c]);
+            }
+            float db[11], pn[4];
+#pragma unroll
+            for (int h = 0; h < 11; ++h) {
+                float fb = 0.0f;
+#pragma unroll
+                for (int k = 1; k <= R; ++k) fb = fmaf(p.sw[k - 1], e[h + 5 - k] - e[h + 4 + k], fb);
+                const float2 ab = cpml_coef(cp.cx, nxp, 2, x0 - kHalo + lx + h);
+                const float bf = bw[h] * fb;
+                const float pp = mw[h] + bf;
+                db[h] = fmaf(ab.x, pp, bf);
+                if (h >= 4 && h < 8) pn[h - 4] = ab.y * pp;
+            }
+            float cn[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], db[q + 4 - k] - db[q + 3 + k], acc);
+                ox[q] = acc;
+                const float2 ab = cpml_coef(cp.cx, nxp, 0, gx + q);
+                cn[q] = ab.y * (cw[8 + q] + w[8 + q]);
+            }
+            if (row_ok) {
+                float4 a = make_float4(pn[0], pn[1], pn[2], pn[3]), b = make_float4(cn[0], cn[1], cn[2], cn[3]);
+                if (gx + 4 > nxp) {
+                    if (gx + 1 >= nxp) { a.y = 0.f; b.y = 0.f; }
+                    if (gx + 2 >= nxp) { a.z = 0.f; b.z = 0.f; }
+                    a.w = 0.f; b.w = 0.f;
+                }
+                st4(cp.hx_out + orow, a);
+                st4(cp.nx_out + orow, b);
+            }
+        }
+        opv[j] = make_float4(ox[0], ox[1], ox[2], ox[3]);
+    }
+    // ---- z: columns lx .. lx + 3 of the block
+    {
+        float4 col[18];
+#pragma unroll
+        for (int r = 0; r < 18; ++r) col[r] = ld4s(box + (lz + 1 + r) * kVBoxX + lx + kVHalo);
+        float4 oz[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) oz[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!ADJ) {
+#pragma unroll
+            for (int f = 0; f < 11; ++f) {
+                float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                    const float4 up = col[f + 3 + k], dn = col[f + 4 - k];
+                    const float sk = p.sw[k - 1];
+                    d.x = fmaf(sk, up.x - dn.x, d.x);
+                    d.y = fmaf(sk, up.y - dn.y, d.y);
+                    d.z = fmaf(sk, up.z - dn.z, d.z);
+                    d.w = fmaf(sk, up.w - dn.w, d.w);
+                }
+                const float2 ab = cpml_coef(cp.cz, nzp, 2, z0 - kHalo + lz + f);
+                const float4 m = ld4s(mhz + (lz + f) * kTileX + lx);
+                const float4 ps = make_float4(fmaf(ab.y, m.x, ab.x * d.x), fmaf(ab.y, m.y, ab.x * d.y),
+                                              fmaf(ab.y, m.z, ab.x * d.z), fmaf(ab.y, m.w, ab.x * d.w));
+                const float4 b = ld4s(bzs + (lz + f) * kTileX + lx);
+                const float4 fl = make_float4(b.x * (d.x + ps.x), b.y * (d.y + ps.y), b.z * (d.z + ps.z),
+                                              b.w * (d.w + ps.w));
+                if (f >= 4 && f < 8) {
+                    const int gz = z0 + lz + f - 4;
+                    if (col_ok && gz < nzp) {
+                        float4 v = ps;
+                        if (gx + 4 > nxp) {
+                            if (gx + 1 >= nxp) v.y = 0.f;
+                            if (gx + 2 >= nxp) v.z = 0.f;
+                            v.w = 0.f;
+                        }
+                        st4(cp.hz_out + shot_off + static_cast<long long>(gz) * p.pitch + gx, v);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int kp_ = f - j - 3, km_ = j + 4 - f;
+                    if (kp_ >= 1 && kp_ <= R) oz[j] = fma4(make_float4(p.sw[kp_ - 1], p.sw[kp_ - 1], p.sw[kp_ - 1],
+                                                                       p.sw[kp_ - 1]), fl, oz[j]);
+                    if (km_ >= 1 && km_ <= R) oz[j] = fma4(make_float4(-p.sw[km_ - 1], -p.sw[km_ - 1],
+                                                                       -p.sw[km_ - 1], -p.sw[km_ - 1]), fl, oz[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gz = z0 + lz + j;
+                const float2 ab = cpml_coef(cp.cz, nzp, 0, gz);
+                const float4 xp = ld4s(mnz + (lz + j) * kTileX + lx);
+                float4 xn = make_float4(fmaf(ab.y, xp.x, ab.x * oz[j].x), fmaf(ab.y, xp.y, ab.x * oz[j].y),
+                                        fmaf(ab.y, xp.z, ab.x * oz[j].z), fmaf(ab.y, xp.w, ab.x * oz[j].w));
+                opv[j] = make_float4(opv[j].x + (oz[j].x + xn.x), opv[j].y + (oz[j].y + xn.y),
+                                     opv[j].z + (oz[j].z + xn.z), opv[j].w + (oz[j].w + xn.w));
+                if (col_ok && gz < nzp) {
+                    if (gx + 4 > nxp) {
+                        if (gx + 1 >= nxp) xn.y = 0.f;
+                        if (gx + 2 >= nxp) xn.z = 0.f;
+                        xn.w = 0.f;
+                    }
+                    st4(cp.nz_out + shot_off + static_cast<long long>(gz) * p.pitch + gx, xn);
+                }
+            }
+        } else {
+            // e at node rows lz + 1 .. lz + 18 of the box, chi from its 64 x 48 box (same rows)
+            float4 e[18];
+#pragma unroll
+            for (int r = 0; r < 18; ++r) {
+                const float4 c = ld4s(mnz + (lz + 1 + r) * kTileX + lx);
+                const float a = cpml_coef(cp.cz, nzp, 0, z0 - kVHalo + lz + 1 + r).x;
+                e[r] = make_float4(fmaf(a, c.x + col[r].x, col[r].x), fmaf(a, c.y + col[r].y, col[r].y),
+                                   fmaf(a, c.z + col[r].z, col[r].z), fmaf(a, c.w + col[r].w, col[r].w));
+            }
+#pragma unroll
+            for (int f = 0; f < 11; ++f) {
+                float4 fb = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                    const float4 a = e[f + 4 - k], b = e[f + 3 + k];
+                    const float sk = p.sw[k - 1];
+                    fb.x = fmaf(sk, a.x - b.x, fb.x);
+                    fb.y = fmaf(sk, a.y - b.y, fb.y);
+                    fb.z = fmaf(sk, a.z - b.z, fb.z);
+                    fb.w = fmaf(sk, a.w - b.w, fb.w);
+                }
+                const float2 ab = cpml_coef(cp.cz, nzp, 2, z0 - kHalo + lz + f);
+                const float4 b = ld4s(bzs + (lz + f) * kTileX + lx);
+                const float4 m = ld4s(mhz + (lz + f) * kTileX + lx);
+                const float4 bf = make_float4(b.x * fb.x, b.y * fb.y, b.z * fb.z, b.w * fb.w);
+                const float4 pp = make_float4(m.x + bf.x, m.y + bf.y, m.z + bf.z, m.w + bf.w);
+                const float4 db = make_float4(fmaf(ab.x, pp.x, bf.x), fmaf(ab.x, pp.y, bf.y), fmaf(ab.x, pp.z, bf.z),
+                                              fmaf(ab.x, pp.w, bf.w));
+                if (f >= 4 && f < 8) {
+                    const int gz = z0 + lz + f - 4;
+                    if (col_ok && gz < nzp) {
+                        float4 v = make_float4(ab.y * pp.x, ab.y * pp.y, ab.y * pp.z, ab.y * pp.w);
+                        if (gx + 4 > nxp) {
+                            if (gx + 1 >= nxp) v.y = 0.f;
+                            if (gx + 2 >= nxp) v.z = 0.f;
+                            v.w = 0.f;
+                        }
+                        st4(cp.hz_out + shot_off + static_cast<long long>(gz) * p.pitch + gx, v);
+                    }
+                }
+                // out_j = sum_k s_k (dbar_{j+4-k} - dbar_{j+3+k})
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int kp_ = j + 4 - f, km_ = f - j - 3;
+                    if (kp_ >= 1 && kp_ <= R) oz[j] = fma4(make_float4(p.sw[kp_ - 1], p.sw[kp_ - 1], p.sw[kp_ - 1],
+                                                                       p.sw[kp_ - 1]), db, oz[j]);
+                    if (km_ >= 1 && km_ <= R) oz[j] = fma4(make_float4(-p.sw[km_ - 1], -p.sw[km_ - 1],
+                                                                       -p.sw[km_ - 1], -p.sw[km_ - 1]), db, oz[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gz = z0 + lz + j;
+                const float b = cpml_coef(cp.cz, nzp, 0, gz).y;
+                const float4 c = ld4s(mnz + (lz + 8 + j) * kTileX + lx);
+                const float4 m = col[7 + j];
+                float4 cn = make_float4(b * (c.x + m.x), b * (c.y + m.y), b * (c.z + m.z), b * (c.w + m.w));
+                opv[j] = make_float4(opv[j].x + oz[j].x, opv[j].y + oz[j].y, opv[j].z + oz[j].z, opv[j].w + oz[j].w);
+                if (col_ok && gz < nzp) {
+                    if (gx + 4 > nxp) {
+                        if (gx + 1 >= nxp) cn.y = 0.f;
+                        if (gx + 2 >= nxp) cn.z = 0.f;
+                        cn.w = 0.f;
+                    }
+                    st4(cp.nz_out + shot_off + static_cast<long long>(gz) * p.pitch + gx, cn);
+                }
+            }
+        }
+    }
+    // ---- update: U^{n+1} = 2U^n - U^{n-1} + kappa' G  (adjoint: mu^m = 2mu^{m+1} - mu^{m+2} + kappa' out)
+    float4 nxt[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int lo = (lz + j) * kTileX + lx;
+        const float4 pp = ld4s(pv + lo), kk = ld4s(kp + lo), u = ctr[j];
+        nxt[j] = fma4(kk, opv[j], make_float4(2.f * u.x - pp.x, 2.f * u.y - pp.y, 2.f * u.z - pp.z, 2.f * u.w - pp.w));
+    }
+    if (inj.n > 0) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
+        __syncthreads();
+        if (tid == 0)
+            apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ,
+                                   kTileX);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gz = z0 + lz + j;
+        if (!col_ok || gz >= nzp) continue;
+        float4 nv = nxt[j], lv = opv[j];
+        if (gx + 4 > nxp) {
+            if (gx + 1 >= nxp) { nv.y = 0.f; lv.y = 0.f; }
+            if (gx + 2 >= nxp) { nv.z = 0.f; lv.z = 0.f; }
+            nv.w = 0.f; lv.w = 0.f;
+        }
+        const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+        st4(p.out + o, nv);
+        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
+        if (MODE == kAdjoint) {
+            const int lo = (lz + j) * kTileX + lx;
+            st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+        }
+    }
+    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+        const int cnt = (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
+        for (int e = tid; e < cnt; e += 128) {
+            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
+            const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.smp_node + tx_idx * p.n_rx + r) : -1;
+            const int zn = node >> 16, xn = node & 0xffff;
+            if (node < 0 || zn < z0 || zn >= z0 + TZ || xn < x0 || xn >= x0 + kTileX) {
+                raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                continue;
+            }
+            p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
+                box[(zn - z0 + kVHalo) * kVBoxX + (xn - x0 + kVHalo)];
+        }
+    }
+}
+
 // ---- persistent sweep ---------------------------------------------------------------------------
 // Several time steps of one sweep in one cooperative launch (see SweepParams). Each work item is
 // the one-step update of one 64 x 32 tile; the arithmetic is that of step_kernel<R, MODE, 32>, so
@@ -1150,7 +1556,7 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 // the check guards the time step rather than proving stability.
 __global__ void setup_kappa_kernel(const float *sos, const float *density, float *kap, float *bxo, float *bzo,
                                    int *status, int NxE, int NzE, int P, int nxpE, int nzpE, int pitch, double r2,
-                                   double d0, double dt, double c_max, const int2 *map_dims)
+                                   double d0, double dt, double c_max, const int2 *map_dims, bool unit_b)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = blockIdx.y;
@@ -1162,8 +1568,12 @@ __global__ void setup_kappa_kernel(const float *sos, const float *density, float
     const long long o = (static_cast<long long>(b) * nzpE + z) * pitch + x;
     if (x >= nxp || z >= nzp) {
         kap[o] = 0.f;
-        if (density) { bxo[o] = 0.f; bzo[o] = 0.f; }
+        if (density || unit_b) { bxo[o] = 0.f; bzo[o] = 0.f; }
         return;
+    }
+    if (unit_b) {
+        bxo[o] = x + 1 < nxp ? 1.f : 0.f;
+        bzo[o] = z + 1 < nzp ? 1.f : 0.f;
     }
     auto src_of = [&](int xx, int zz) {
         const int xs = min(max(xx - P, 0), Nx - 1), zs = min(max(zz - P, 0), Nz - 1);
@@ -1583,6 +1993,60 @@ cudaError_t launch_sweep(int radius, int mode, const SweepMaps &tm, const StepPa
 }
 
 template <int R, int MODE>
+static cudaError_t launch_step_cpml_rm(const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                                       const CpmlParams &cp, cudaStream_t st)
+{
+    using CL = CpmlLayout<MODE>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(cpml_step_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             CL::kBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(cpml_step_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_maps * p.n_tx);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = CL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cpml_step_kernel<R, MODE>, tm, cm, p, cp);
+}
+
+template <int R>
+static cudaError_t launch_step_cpml_r(int mode, const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                                      const CpmlParams &cp, cudaStream_t st)
+{
+    switch (mode) {
+    case kFwdSample: return launch_step_cpml_rm<R, kFwdSample>(tm, cm, p, cp, st);
+    case kFwdSampleHist: return launch_step_cpml_rm<R, kFwdSampleHist>(tm, cm, p, cp, st);
+    case kFwdHist: return launch_step_cpml_rm<R, kFwdHist>(tm, cm, p, cp, st);
+    case kAdjoint: return launch_step_cpml_rm<R, kAdjoint>(tm, cm, p, cp, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step_cpml(int radius, int mode, const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                             const CpmlParams &cp, cudaStream_t st)
+{
+    if (p.tile_z != kVTileZ || p.map_dims) return cudaErrorInvalidValue;
+    switch (radius) {
+    case 1: return launch_step_cpml_r<1>(mode, tm, cm, p, cp, st);
+    case 2: return launch_step_cpml_r<2>(mode, tm, cm, p, cp, st);
+    case 3: return launch_step_cpml_r<3>(mode, tm, cm, p, cp, st);
+    case 4: return launch_step_cpml_r<4>(mode, tm, cm, p, cp, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R, int MODE>
 static cudaError_t launch_step_vd_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
     using VL = VdLayout<MODE>;
@@ -1649,12 +2113,13 @@ cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepPara
 
 cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, float *bx, float *bz, int *status,
                                int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch, double dt_over_dx,
-                               double d0, double dt, double c_max, const int2 *map_dims, cudaStream_t st)
+                               double d0, double dt, double c_max, const int2 *map_dims, bool unit_b,
+                               cudaStream_t st)
 {
-    if (density && (!bx || !bz)) return cudaErrorInvalidValue;
+    if ((density || unit_b) && (!bx || !bz)) return cudaErrorInvalidValue;
     dim3 grid((pitch + 127) / 128, nzp, n_maps);
     setup_kappa_kernel<<<grid, 128, 0, st>>>(sos, density, kap, bx, bz, status, Nx, Nz, P, nxp, nzp, pitch,
-                                             dt_over_dx * dt_over_dx, d0, dt, c_max, map_dims);
+                                             dt_over_dx * dt_over_dx, d0, dt, c_max, map_dims, unit_b);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,149 @@
+"""Convolutional PML (the alternative absorbing layer) on the GPU against the oracle.
+
+Same tolerances as the other paths: traces rel-L2 <= 1e-5, gradient rel-L2 <= 1e-4, misfit
+relative error <= 1e-4. Gradients keep every step (the memory variables are not checkpointed)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_04070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-5
+GRAD_TOL = 1e-4
+C_MAX = 2000.0
+
+
+@pytest.fixture(scope="module")
+def d():
+    from paper_2603_04070_gb300 import build_lib
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    return dufwi
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case(seed, nx, nz, nt, n_elem, n_tx, n_maps=1, order=8, density=False):
+    wl = inputs.make_workload("linear_disk", seed=seed, nx=nx, nz=nz, nt=nt, n_elem=n_elem, n_tx=n_tx,
+                              n_maps=n_maps, fd_order=order)
+    r2 = inputs.rng_for(seed + 900)
+    wl.sos_true = np.stack([inputs.grf_rods_map(r2, nx, nz, wl.dx) for _ in range(n_maps)])
+    rho = None
+    if density:
+        rng = inputs.rng_for(seed + 500)
+        rho = np.stack([inputs.density_map(rng, nx, nz, wl.dx) for _ in range(n_maps)])
+    return wl, rho
+
+
+ALPHA = math.pi * 2e6
+
+
+def _op(wl):
+    return oracle.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml, pml_R=wl.pml_R,
+                          pml_cref=wl.pml_cref, fd_order=wl.fd_order, boundary=1, pml_alpha=ALPHA)
+
+
+def _pb(d, wl, **kw):
+    return d.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
+                     pml_cref=wl.pml_cref, fd_order=wl.fd_order, c_max=C_MAX, boundary="cpml", pml_alpha=ALPHA, **kw)
+
+
+def _oracle_traces(wl, C, rho):
+    p = _op(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return np.stack([oracle.forward(p, np.asarray(C, np.float64), (tix[k], tiz[k]), wl.wavelet.astype(np.float64),
+                                    rix[k], riz[k], rho=rho) for k in range(wl.n_tx)])
+
+
+def _t(a):
+    return None if a is None else torch.from_numpy(a).cuda()
+
+
+@pytest.mark.parametrize("order,density", [(8, False), (8, True), (4, False), (2, True)])
+def test_cpml_simulate_matches_oracle(d, order, density):
+    wl, rho = _case(order + 3 * density, 97, 71, 500, 24, 3, order=order, density=density)
+    geom = d.Geometry.from_workload(wl)
+    cd = d.simulate(_pb(d, wl), _t(wl.sos_true), _t(wl.wavelet), geom, density=_t(rho), check=True).cpu().numpy()
+    ref = _oracle_traces(wl, wl.sos_true[0], None if rho is None else rho[0])
+    assert rel_l2(cd[0], ref) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("density", [False, True])
+def test_cpml_gradient_matches_oracle(d, density):
+    wl, rho = _case(21, 72, 60, 600, 20, 2, n_maps=2, density=density)
+    obs = np.stack([_oracle_traces(wl, wl.sos_true[b], None if rho is None else rho[b])
+                    for b in range(2)]).astype(np.float32)
+    geom = d.Geometry.from_workload(wl)
+    pb = _pb(d, wl)
+    J, g, cd = d.misfit_gradient(pb, _t(wl.sos_start), _t(wl.wavelet), geom, _t(obs), density=_t(rho),
+                                 return_cd=True, check=True)
+    J2 = d.misfit(pb, _t(wl.sos_start), _t(wl.wavelet), geom, _t(obs), density=_t(rho), check=True)
+    torch.cuda.synchronize()
+    assert torch.equal(J, J2)
+    p = _op(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    for b in range(2):
+        Jr, gr, Mr = oracle.misfit_gradient(p, wl.sos_start[b].astype(np.float64), tix, tiz,
+                                            wl.wavelet.astype(np.float64), rix, riz, obs[b].astype(np.float64),
+                                            return_traces=True, rho=None if rho is None else rho[b])
+        assert np.linalg.norm(Mr - obs[b]) >= 0.03 * np.linalg.norm(Mr)
+        assert rel_l2(cd[b].cpu().numpy(), Mr) <= TRACE_TOL
+        assert abs(float(J[b]) - Jr) <= 1e-4 * Jr
+        assert rel_l2(g[b].cpu().numpy(), gr) <= GRAD_TOL
+
+
+def test_cpml_backward_equals_misfit_gradient(d):
+    """dufwi_backward with the cotangent 2 (M - M_obs) gives the gradient of the misfit call."""
+    wl, _ = _case(22, 64, 56, 300, 16, 2)
+    geom = d.Geometry.from_workload(wl)
+    pb = _pb(d, wl)
+    obs = d.simulate(pb, _t(wl.sos_true), _t(wl.wavelet), geom)
+    J, g = d.misfit_gradient(pb, _t(wl.sos_start), _t(wl.wavelet), geom, obs, check=True)
+    cd, ws = d.forward_save(pb, _t(wl.sos_start), _t(wl.wavelet), geom)
+    g2 = d.backward(pb, _t(wl.sos_start), _t(wl.wavelet), geom, (2.0 * (cd - obs)).contiguous(), ws)
+    torch.cuda.synchronize()
+    assert torch.equal(g, g2)
+
+
+def test_cpml_absorbs_better_than_the_damping_layer(d):
+    """Border return against a domain three times as large, both layers 20 cells thick."""
+    c, dx, dt, f0, nt = 1540.0, 1e-4, 1e-8, 2e6, 700
+    w = _t(inputs.ricker(nt, dt, f0))
+    refl = {}
+    for boundary in ("damping", "cpml"):
+        tr = []
+        for n, src, rec in ((60, 30, 52), (180, 90, 112)):
+            pb = d.Problem(nx=n, nz=n, dx=dx, dt=dt, nt=nt, pml_cells=20, pml_cref=c, c_max=C_MAX, boundary=boundary,
+                           pml_alpha=math.pi * f0)
+            geom = d.Geometry(np.array([src, rec], np.int32), np.array([src, src], np.int32), np.array([0], np.int32),
+                              np.array([[1]], np.int32))
+            cd = d.simulate(pb, torch.full((1, n, n), c, device="cuda"), w, geom, check=True)
+            tr.append(cd[0, 0, :, 0].cpu().numpy().astype(np.float64))
+        refl[boundary] = np.max(np.abs(tr[0] - tr[1])) / np.max(np.abs(tr[1]))
+    assert refl["cpml"] < 2e-3 and refl["cpml"] < 0.1 * refl["damping"], refl
+
+
+def test_cpml_unsupported_combinations(d):
+    wl, _ = _case(23, 40, 40, 60, 8, 1)
+    geom = d.Geometry.from_workload(wl)
+    sos, w = _t(wl.sos_true), _t(wl.wavelet)
+    with pytest.raises(d.DufwiError) as e:                      # checkpointed gradient
+        d.misfit_gradient(_pb(d, wl, ckpt_interval=10), sos, w, geom, torch.zeros((1, 1, 60, 8), device="cuda"))
+    assert e.value.status == d.ERR_UNSUPPORTED
+    with pytest.raises(d.DufwiError) as e:                      # Born step
+        d.jvp(_pb(d, wl), sos, w, geom, torch.zeros_like(sos))
+    assert e.value.status == d.ERR_UNSUPPORTED
+    with pytest.raises(d.DufwiError) as e:                      # maps of different sizes
+        d.simulate(_pb(d, wl), sos, w, geom, sizes=[(40, 40)])
+    assert e.value.status == d.ERR_UNSUPPORTED

@@ -539,8 +539,11 @@ def run_uneven_batch(args):
 
 def run_dufwi_loop(args):
     """ms per DUFWI iteration for the unfolded loop: K = 5 iterations on a batch of 8 disk maps
-    of 512 x 512 (16 transmits, 128 receivers, 6000 steps, checkpoint interval 100). Each
-    iteration is the misfit gradient of all 128 shots, the update network and the update."""
+    of 512 x 512 (16 transmits, 128 receivers, 6000 steps). Each iteration is the misfit
+    gradient of all 128 shots, the update network and the update. Three forms of the gradient:
+    the batched, checkpointed form with FP32 snapshots (the headline of this mode), the same with
+    FP16 snapshots (mixed precision), and the plain FP32 single-shot form (one call per map and
+    transmit, every step kept, the per-shot gradients summed), timed over one iteration."""
     import torch
     from paper_2603_04070_gb300 import build_lib, inputs
     build_lib.build()
@@ -559,13 +562,52 @@ def run_dufwi_loop(args):
     model = unfolded.UnfoldedFWI(K=5).to(dev)
     model.infer(phys, c0, obs)                      # warm-up
     times = []
-    outs = model.infer(phys, c0, obs, timings=times)
+    model.infer(phys, c0, obs, timings=times)
     ms = [1e3 * t for t in times]
-    line = {"metric": "ms per DUFWI iteration", "value": sum(ms) / len(ms), "unit": "ms", "n_gpus": 1,
+    # mixed precision: FP16 snapshots
+    phys16 = unfolded.Physics(dufwi.Problem(**{**pb.__dict__, "snapshot_dtype": "fp16"}), phys.wavelet, geom)
+    model.infer(phys16, c0, obs)
+    times16 = []
+    model.infer(phys16, c0, obs, timings=times16)
+    ms16 = [1e3 * t for t in times16]
+    # plain FP32 single-shot form: one gradient call per (map, transmit), every step kept
+    pb1 = dufwi.Problem(**{**pb.__dict__, "ckpt_interval": 0})
+    ws1 = None
+    net = model.nets[0]
+
+    def single_shot_iteration(c):
+        nonlocal ws1
+        g = torch.zeros_like(c)
+        for b in range(wl.n_maps):
+            for k in range(wl.n_tx):
+                g1 = dufwi.Geometry(wl.elem_ix, wl.elem_iz, wl.tx_elem[k:k + 1], wl.rx_elem[k:k + 1])
+                if ws1 is None:
+                    ws1 = torch.empty(dufwi.workspace_size(pb1, g1, 1), dtype=torch.uint8, device=dev)
+                _, gk = dufwi.misfit_gradient(pb1, c[b:b + 1], phys.wavelet, g1, obs[b:b + 1, k:k + 1].contiguous(),
+                                              workspace=ws1)
+                g[b] += gk[0]
+        with torch.no_grad():
+            return c + net(c, g)
+
+    single_shot_iteration(c0)                       # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single_shot_iteration(c0)
+    torch.cuda.synchronize()
+    ms_single = 1e3 * (time.perf_counter() - t0)
+    value = sum(ms) / len(ms)
+    line = {"metric": "ms per DUFWI iteration", "value": value, "unit": "ms", "n_gpus": 1,
             "steps": len(ms), "warmup": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "unfolded DUFWI inference, K=5, batch 8 disk maps 512x512, 16 transmits x 128 "
-                                   "receivers, %d steps, checkpoint interval %d; update nets untrained" % (nt, args.ckpt)},
+                                   "receivers, %d steps, checkpoint interval %d, FP32 snapshots; update nets "
+                                   "untrained" % (nt, args.ckpt)},
             "ms_per_iteration": ms,
+            "fp16_snapshots_ms_per_iteration": sum(ms16) / len(ms16),
+            "plain_fp32_single_shot_ms_per_iteration": ms_single,
+            "plain_fp32_single_shot_form": "one misfit_gradient call per map and transmit (128 calls), every "
+                                           "step kept, gradients summed; one iteration timed",
+            "speedup_batched_vs_single_shot": ms_single / value,
+            "speedup_batched_fp16_vs_single_shot": ms_single / (sum(ms16) / len(ms16)),
             "gradient_share": "the physics gradient dominates each iteration (Sec. III-D)"}
     print(json.dumps(line), flush=True)
 

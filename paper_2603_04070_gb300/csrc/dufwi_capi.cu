@@ -641,7 +641,13 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
         cp.cx = c.at<float>(c.L.o_cpml);
         cp.cz = cp.cx + 4 * (size_t)c.L.nxp;
         const CpmlMaps &cm = mode == kAdjoint ? c.cm_adj[c.mem_par] : c.cm_fwd[c.mem_par];
-        CKL(launch_step_cpml(c.L.radius, mode, tm, cm, p, cp, c.st));
+        // tiles away from the layer take the staggered kernel (their memory variables stay zero),
+        // the others the CPML kernel; both read step n and write disjoint tiles of step n + 1
+        StepParams pi = p, pl = p;
+        pi.tile_class = 1;
+        pl.tile_class = 2;
+        CKL(launch_step_vd(c.L.radius, mode, tm, pi, c.st));
+        CKL(launch_step_cpml(c.L.radius, mode, tm, cm, pl, cp, c.st));
         c.mem_par = w;
     } else if (c.vd) {   // the tile height is 32 here, so tile1, kap1, hist1 and grad1 fit the kernel
         tm.cur_box = rg.map[rg.cur].box2;

@@ -499,6 +499,14 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 // registers, the x fluxes of its four rows and the z fluxes of its four columns that its 4 x 4
 // block needs (11 half points each way, shared-memory reads of 128 bits), their divergence, and
 // runs the common Eq. 2 epilogue.
+// CPML split: does the 64 x 32 tile at (x0, z0), grown by 8 cells, lie inside the physical grid
+// (where every CPML coefficient is the identity, so that the memory variables stay zero)?
+__device__ __forceinline__ bool cpml_free_tile(const StepParams &p, int x0, int z0)
+{
+    return x0 - 2 * kHalo >= p.P && x0 + kTileX + 2 * kHalo <= p.P + p.Nx - 1 && z0 - 2 * kHalo >= p.P &&
+           z0 + kVTileZ + 2 * kHalo <= p.P + p.Nz - 1;
+}
+
 template <int MODE>
 struct VdLayout {
     static constexpr int kBox = kVBoxX * kVBoxZ;
@@ -535,6 +543,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     float *gg = hs + VL::kTile;
     const MapGrid mg = map_grid(p, map);
     if (x0 >= mg.nxp || z0 >= mg.nzp) return;
+    if (p.tile_class == 1 && !cpml_free_tile(p, x0, z0)) return;   // CPML split: layer tiles run elsewhere
 
     grid_dependency_wait();
     if (tid == 0) {
@@ -775,6 +784,7 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
     float *hs = kp + CL::kTile;        // adjoint: G^{m-1}
     float *gg = hs + CL::kTile;        // adjoint: imaging sums
     if (x0 >= p.nxp || z0 >= p.nzp) return;
+    if (p.tile_class == 2 && cpml_free_tile(p, x0, z0)) return;    // CPML split: interior tiles run elsewhere
 
     grid_dependency_wait();
     if (tid == 0) {

@@ -737,6 +737,7 @@ int forward_range(Ctx &c, Ring &rg, int n0, int n1, int mode, const float *wavel
     for (int n = n0; n < n1;) {
         p.step = n;
         p.hist = hist ? hist + (size_t)(n - h0) * hstride : nullptr;
+        p.early = (!c.two_step && n >= n0 + 2) ? 1 : 0;   // the two launches before were steps n-2, n-1
         if (c.two_step && n % 2 == 0 && n + 2 <= n1) {
             p.hist2 = hist ? hist + (size_t)(n + 1 - h0) * hstride : nullptr;
             int rc = two_steps(c, rg, mode, p, nl);
@@ -762,6 +763,7 @@ int adjoint_range(Ctx &c, Ring &rg, int m1, int m0, const float *asrc, float *g_
     for (int m = m1; m >= m0;) {
         p.step = m;
         p.hist_slot = m - 1 - h0;
+        p.early = (!c.two_step && m <= m1 - 2) ? 1 : 0;   // the two launches before were steps m+2, m+1
         if (c.two_step && m % 2 == 0 && m - 1 >= m0) {
             p.hist_slot2 = m - 2 - h0;
             int rc = two_steps(c, rg, kAdjoint, p, nl);

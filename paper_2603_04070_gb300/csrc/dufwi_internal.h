@@ -107,6 +107,9 @@ struct StepParams {
     const float2 *damp_tab;  // [P + 1][P + 1]: (a - 2, b + 1) at layer depths (dz, dx) in cells
     float c[5];              // central stencil weights, c[0] the centre weight of one axis
     float sw[4];             // staggered first-difference weights s_1..s_R (variable density)
+    int early;               // one-step kernel: U^{n-1}, kappa' (and the history) may be loaded before
+                             // the wait for the previous launch: neither of the last two launches
+                             // wrote them (set by the host from the third step of a range on)
     int tile_class;          // CPML split: 0 every tile; 1 only tiles whose region grown by 8 cells
                              // lies inside the physical grid (no memory variables); 2 only the others
 };

@@ -380,18 +380,29 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 
     // Thread 0 initialises the barrier, issues the loads and alone polls the barrier; the other
     // threads first touch it after the CTA barrier in wait_tile, so no barrier is needed here.
-    grid_dependency_wait();
+    // With p.early the operands that no launch of the last two wrote (U^{n-1}, kappa', and in the
+    // adjoint the history) are requested before the wait for the previous launch, overlapping
+    // its tail; the host sets it only where that holds.
+    const bool early = MODE != kBorn && p.early;
     if (tid == 0) {
         prefetch_tensormap(&tm.cur_box);
         mbar_init(&bar, 1);
         mbar_arrive_expect_tx(&bar, TL::kBytes);
-        tma_load_3d(box, &tm.cur_box, &bar, x0 - kHalo, z0 - kHalo, s);
-        tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
-        tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, s / p.n_tx);
-        if (MODE == kAdjoint) {
-            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
-            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        if (early) {
+            tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+            tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, s / p.n_tx);
+            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
+    }
+    grid_dependency_wait();
+    if (tid == 0) {
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - kHalo, z0 - kHalo, s);
+        if (!early) {
+            tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+            tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, s / p.n_tx);
+            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+        }
+        if (MODE == kAdjoint) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
         if (MODE == kBorn) {
             tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
             tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s / p.n_tx);

@@ -121,3 +121,33 @@ def test_geometry_errors_are_reported_before_any_device_work():
                                  fake, ctypes.c_void_p(1 << 20), need - 1, None) == d.ERR_WORKSPACE
     assert d._lib.dufwi_simulate(ctypes.byref(c), fake, None, ctypes.byref(arr), fake, ctypes.byref(sh), 1,
                                  fake, ctypes.c_void_p((1 << 20) + 4), need, None) == d.ERR_WORKSPACE
+
+
+def test_boundary_and_option_validation():
+    """Absorbing-layer selection and launch options are checked on the host."""
+    d = _lib_module()
+    g = _geom(d)
+    damp = d.workspace_size(_problem(d), g, 1)
+    cpml = d.workspace_size(_problem(d, boundary="cpml", pml_alpha=6e6), g, 1)
+    assert cpml > damp                                   # memory variables and coefficient tables
+    with pytest.raises(d.DufwiError) as e:               # memory variables are not checkpointed
+        d.workspace_size(_problem(d, nt=2000, boundary="cpml", ckpt_interval=50), g, 1)
+    assert e.value.status == d.ERR_UNSUPPORTED
+    with pytest.raises(d.DufwiError) as e:               # no Born step on the staggered operators
+        d.jvp_workspace_size(_problem(d, boundary="cpml"), g, 1)
+    assert e.value.status == d.ERR_UNSUPPORTED
+    with pytest.raises(d.DufwiError) as e:
+        d.workspace_size(_problem(d, boundary="cpml", pml_alpha=-1.0), g, 1)
+    assert e.value.status == d.ERR_INVALID_ARG
+    bad = _problem(d).c_struct()
+    bad.boundary = 7
+    sh = g.c_structs()[1]
+    out = ctypes.c_size_t(0)
+    assert d._lib.dufwi_workspace_size(ctypes.byref(bad), ctypes.byref(sh), 1, ctypes.byref(out)) == d.ERR_INVALID_ARG
+    for opt, good, badv in ((d.OPT_PERSISTENT, 1, 2), (d.OPT_TEST_STALL, 0, 3), (d.OPT_TILE_Z, 64, 48)):
+        before = d.get_option(opt)
+        with pytest.raises(d.DufwiError):
+            d.set_option(opt, badv)
+        d.set_option(opt, good)
+        assert d.get_option(opt) == good
+        d.set_option(opt, before)

@@ -556,20 +556,31 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     if (x0 >= mg.nxp || z0 >= mg.nzp) return;
     if (p.tile_class == 1 && !cpml_free_tile(p, x0, z0)) return;   // CPML split: layer tiles run elsewhere
 
-    grid_dependency_wait();
+    // operands that neither of the last two launches wrote may be requested before the wait
+    // (p.early, as in the one-step kernel)
     if (tid == 0) {
         prefetch_tensormap(&tm.cur_box);
         mbar_init(&bar, 1);
         mbar_arrive_expect_tx(&bar, VL::kBytes);
-        tma_load_3d(box, &tm.cur_box, &bar, x0 - kVHalo, z0 - kVHalo, s);
-        tma_load_3d(fx, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
-        tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
-        tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
-        tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
-        if (MODE == kAdjoint) {
-            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
-            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        if (p.early) {
+            tma_load_3d(fx, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
+            tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
+            tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+            tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
+    }
+    grid_dependency_wait();
+    if (tid == 0) {
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - kVHalo, z0 - kVHalo, s);
+        if (!p.early) {
+            tma_load_3d(fx, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
+            tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
+            tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+            tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+        }
+        if (MODE == kAdjoint) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
     }
     grid_dependents_launch();
 
@@ -797,14 +808,27 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
     if (x0 >= p.nxp || z0 >= p.nzp) return;
     if (p.tile_class == 2 && cpml_free_tile(p, x0, z0)) return;    // CPML split: interior tiles run elsewhere
 
-    grid_dependency_wait();
+    // early (as in the one-step kernel): buoyancies, U^{n-1}, kappa' and the history before the
+    // wait; the memory variables come from the previous step and are requested after it
     if (tid == 0) {
         prefetch_tensormap(&tm.cur_box);
         mbar_init(&bar, 1);
         mbar_arrive_expect_tx(&bar, CL::kBytes);
+        if (p.early) {
+            tma_load_3d(bxs, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
+            tma_load_3d(bzs, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
+            tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+            tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+            if (ADJ) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+        }
+    }
+    grid_dependency_wait();
+    if (tid == 0) {
         tma_load_3d(box, &tm.cur_box, &bar, x0 - kVHalo, z0 - kVHalo, s);
-        tma_load_3d(bxs, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
-        tma_load_3d(bzs, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
+        if (!p.early) {
+            tma_load_3d(bxs, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
+            tma_load_3d(bzs, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
+        }
         tma_load_3d(mhx, &cm.mem_hx, &bar, x0 - kHalo, z0, s);
         tma_load_3d(mhz, &cm.mem_hz, &bar, x0, z0 - kHalo, s);
         if (ADJ) {
@@ -814,12 +838,12 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
             tma_load_3d(mnx, &cm.mem_nx, &bar, x0, z0, s);
             tma_load_3d(mnz, &cm.mem_nz, &bar, x0, z0, s);
         }
-        tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
-        tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
-        if (ADJ) {
-            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
-            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        if (!p.early) {
+            tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+            tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+            if (ADJ) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
+        if (ADJ) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
     }
     grid_dependents_launch();
 

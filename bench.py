@@ -186,8 +186,10 @@ def omp_cores():
 
 
 def run_reference(args):
-    args.tile_z_used = None
-    args.two_step_used = None
+    # the same config object as the default GPU line (launch options at their defaults)
+    args.tile_z_used = 32
+    args.two_step_used = 0
+    args.persistent_used = 0
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -500,14 +502,17 @@ def run_uneven_batch(args):
     graph_ms = e[0].elapsed_time(e[1]) / args.steps
     batched_ms = graph_ms
     shots = wl.n_maps * wl.n_tx
-    # one shot per call, graph-captured, on a sample of shots spread over maps and transmits
+    # one shot per call, graph-captured, on a sample of shots spread over maps and transmits; each
+    # shot with the launch options the autotuner picks for its own (single-shot) shape
     sample = [(b, k) for b, k in zip(range(0, wl.n_maps, 4), range(0, wl.n_tx, 2))]
     one_ms = []
+    one_tuned = []
     for b, k in sample:
         nx_b, nz_b = sizes[b]
         pb1 = dufwi.Problem(nx=nx_b, nz=nz_b, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
         g1 = dufwi.Geometry(wl.elem_ix, wl.elem_iz, wl.tx_elem[k:k + 1], wl.rx_elem[k:k + 1])
         s1 = torch.from_numpy(wl.sos_true[b:b + 1, :nz_b, :nx_b].copy()).to(dev)
+        one_tuned.append(autotune.tune(pb1, s1, wav, g1))
         w1 = torch.empty(dufwi.workspace_size(pb1, g1, 1, gradient=False), dtype=torch.uint8, device=dev)
         c1 = torch.empty((1, 1, nt, wl.n_rx), dtype=torch.float32, device=dev)
         st = torch.cuda.Stream()
@@ -537,7 +542,10 @@ def run_uneven_batch(args):
             "eager_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms,
             "one_shot_per_call": {"value": one_shot_per_s, "unit": "shots/s",
                                   "sample": "%d shots, each its own call on its own grid, replayed from a CUDA "
-                                            "graph" % len(sample), "ms_per_shot": one_ms},
+                                            "graph, launch options autotuned per shape" % len(sample),
+                                  "ms_per_shot": one_ms,
+                                  "tuned_options": [{k: v for k, v in t.items() if k != "candidates_ms_per_step"}
+                                                    for t in one_tuned]},
             "speedup_vs_one_shot": (shots / (batched_ms / 1e3)) / one_shot_per_s}
     print(json.dumps(line), flush=True)
 
@@ -614,6 +622,66 @@ def run_dufwi_loop(args):
             "speedup_batched_vs_single_shot": ms_single / value,
             "speedup_batched_fp16_vs_single_shot": ms_single / (sum(ms16) / len(ms16)),
             "gradient_share": "the physics gradient dominates each iteration (Sec. III-D)"}
+    print(json.dumps(line), flush=True)
+
+
+def run_hvp(args):
+    """Born (linearised) forward and Gauss-Newton Hessian-vector product H v = 2 J^T (J v) on the
+    full shot set (512 x 512, 16 transmits, 6000 steps, checkpoint interval 100): device time of
+    the JVP (background and Born step per time step), of the VJP of a cotangent (recompute and
+    adjoint sweeps from the saved snapshots), and of a whole HVP (forward with snapshots, JVP,
+    VJP), each over the same workspaces, after warm-up."""
+    import torch
+    from paper_2603_04070_gb300 import build_lib, inputs
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    dev = torch.device("cuda", 0)
+    wl = inputs.make_workload("full_shot_set", seed=0, nt=args.nt)
+    pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, ckpt_interval=args.ckpt, c_max=wl.c_max)
+    geom = dufwi.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).to(dev)
+    wav = torch.from_numpy(wl.wavelet).to(dev)
+    v = torch.from_numpy(wl.sos_true - wl.sos_start).to(dev).contiguous()
+    ws_j = torch.empty(dufwi.jvp_workspace_size(pb, geom, 1), dtype=torch.uint8, device=dev)
+    ws_g = torch.empty(dufwi.workspace_size(pb, geom, 1), dtype=torch.uint8, device=dev)
+    dcd = torch.empty((1, wl.n_tx, wl.nt, wl.n_rx), dtype=torch.float32, device=dev)
+    cd = torch.empty_like(dcd)
+    g = torch.empty_like(sos)
+
+    def jvp():
+        dufwi.jvp(pb, sos, wav, geom, v, dcd=dcd, workspace=ws_j)
+
+    def fwd():
+        dufwi.forward_save(pb, sos, wav, geom, workspace=ws_g, cd=cd)
+
+    def vjp():
+        dufwi.backward(pb, sos, wav, geom, dcd, ws_g, grad=g)
+
+    def timed(fn, reps=3):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        for _ in range(reps):
+            fn()
+        e[1].record()
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]) / reps
+
+    ms_jvp = timed(jvp)
+    ms_fwd = timed(fwd)
+    ms_vjp = timed(vjp)
+    ms_hvp = timed(lambda: (fwd(), jvp(), vjp()))
+    cells = (wl.nx + 2 * wl.pml) * (wl.nz + 2 * wl.pml) * wl.n_tx * wl.nt
+    line = {"metric": "ms per Gauss-Newton Hessian-vector product", "value": ms_hvp, "unit": "ms", "n_gpus": 1,
+            "steps": 3, "warmup": max(args.warmup, 1), "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "full_shot_set: 512x512 (+20), 16 transmits x 128 receivers, "
+                                                        "%d steps, checkpoint interval %d" % (wl.nt, args.ckpt)},
+            "ms_jvp": ms_jvp, "ms_forward_save": ms_fwd, "ms_vjp": ms_vjp,
+            "jvp_gcell_updates_per_s": 2.0 * cells / (ms_jvp / 1e3) / 1e9,
+            "note": "JVP: background + Born step per time step (2 cell updates per cell and step); VJP: recompute "
+                    "+ adjoint sweeps from the snapshots of forward_save"}
     print(json.dumps(line), flush=True)
 
 
@@ -772,6 +840,8 @@ def main():
         run_precision(args)
     elif args.workload == "ring_phantom":
         run_ring_phantom(args)
+    elif args.workload == "hvp":
+        run_hvp(args)
     else:
         run_ours(args)
 

@@ -236,6 +236,20 @@ def test_compressed_snapshots(d, dtype, tol):
     assert err <= tol
 
 
+def test_fp16_snapshots_meet_the_fp32_bounds_at_scale(d):
+    """The compressed path at a paper-scale size: the cropped 256 x 256 sub-problem of the 1024 x
+    1024 configuration (central 64 elements, 8 transmits, 3500 steps, checkpoints every 100 steps)
+    with FP16 snapshots stays within the FP32 bounds against the oracle (traces 1e-5, gradient
+    1e-4). BF16 snapshots are measured at about 2e-4 here and are not held to this bound."""
+    wl = inputs.make_workload("scale", seed=0, nx=256, nz=256, nt=3500, n_elem=64, n_tx=8)
+    M_obs = _observed(wl)
+    J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0], ckpt=100)
+    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=100, snapshot_dtype="fp16")
+    assert rel_l2(cd[0], cd_ref) <= TRACE_TOL
+    assert abs(float(J[0]) - J_ref) <= 1e-4 * J_ref
+    assert rel_l2(g[0], g_ref) <= GRAD_TOL
+
+
 def test_zero_residual_gives_zero_gradient(d):
     """Observed data equal to the GPU's own simulation at the start map: J = 0 and g = 0."""
     wl = inputs.make_workload("linear_disk", seed=9, nx=50, nz=50, nt=200, n_elem=12, n_tx=2)

@@ -5,6 +5,7 @@ statically. The library loads without a GPU, so the C ABI can be inspected on an
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import subprocess
 import sys
@@ -38,9 +39,18 @@ def _stale() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
-    nvcc = _nvcc()
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
+    # several processes (one per GPU) may call this at once: one builds, the others wait and reuse
+    with open(os.path.join(objdir, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return LIB
+        return _build(objdir, verbose)
+
+
+def _build(objdir: str, verbose: bool) -> str:
+    nvcc = _nvcc()
 
     def compile_one(src):
         obj = os.path.join(objdir, src.replace(".cu", ".o"))

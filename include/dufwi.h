@@ -293,17 +293,12 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device
  *     stays usable. The hook clears itself when used; 0 (default) disarms it.
- *   DUFWI_OPT_OVERLAP: 1 (default) runs the recompute of checkpoint segment s-1 on a second,
- *     library-owned stream of the device beside the adjoint of segment s (two history banks,
- *     ordered by events; the call still completes in the caller's stream order); 0 runs them
- *     one after the other. Bit-identical results.
  * Both functions return DUFWI_ERR_INVALID_ARG for an unknown option or value. */
 #define DUFWI_OPT_TILE_Z 1
 #define DUFWI_OPT_TWO_STEP 2
 #define DUFWI_OPT_REUSE_TABLES 3
 #define DUFWI_OPT_PERSISTENT 4
 #define DUFWI_OPT_TEST_STALL 5
-#define DUFWI_OPT_OVERLAP 6
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

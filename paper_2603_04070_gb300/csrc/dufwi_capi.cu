@@ -87,7 +87,6 @@ double stability_limit(int order)
 
 struct Layout {
     int Nx, Nz, P, nxp, nzp, pitch, radius, S, n_tx, n_rx, n_maps, nt, K, n_seg, n_hist;
-    int n_hist_alloc;        // history slots: two banks of K when checkpointed (recompute and adjoint overlap)
     long long slice;
     size_t snap_elem;
     // byte offsets into the workspace
@@ -111,30 +110,6 @@ int g_tile_z = kTileZDefault;
 int g_two_step = 0;
 int g_persistent = 0;   // DUFWI_OPT_PERSISTENT: one cooperative launch per sweep segment
 std::atomic<int> g_test_stall{0};   // DUFWI_OPT_TEST_STALL: the next persistent sweep stalls on purpose
-int g_overlap = 1;      // DUFWI_OPT_OVERLAP: recompute of segment s-1 beside the adjoint of segment s
-
-// Second stream and ordering events of the overlapped reverse sweep, per host thread and device
-// (created on the first checkpointed gradient, kept; no creation or destruction inside later
-// calls, which may be captured into CUDA graphs).
-struct OverlapRes {
-    cudaStream_t st = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr, rec[2] = {nullptr, nullptr}, adj[2] = {nullptr, nullptr};
-};
-
-OverlapRes *overlap_resources()
-{
-    thread_local std::unordered_map<int, OverlapRes> res;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    auto it = res.find(dev);
-    if (it != res.end()) return &it->second;
-    OverlapRes r;
-    bool ok = cudaStreamCreateWithFlags(&r.st, cudaStreamNonBlocking) == cudaSuccess;
-    for (cudaEvent_t *e : {&r.fork, &r.join, &r.rec[0], &r.rec[1], &r.adj[0], &r.adj[1]})
-        ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) return nullptr;
-    return &(res[dev] = r);
-}
 
 // NVTX range over the host code that enqueues one part of a call (visible in timeline tools).
 struct NvtxRange {
@@ -231,8 +206,7 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         const bool store_all = pb->ckpt_interval == 0 || pb->ckpt_interval >= steps;
         for (int i = 0; i < 4; ++i) L->o_m[i] = take(field);
         L->o_grad = take(field);
-        L->n_hist_alloc = store_all ? L->n_hist : 2 * L->n_hist;
-        L->o_hist = take(field * (size_t)L->n_hist_alloc);
+        L->o_hist = take(field * (size_t)L->n_hist);
         if (!store_all) {
             L->o_snap = take((size_t)L->n_seg * 2 * L->S * L->slice * L->snap_elem);
             L->o_scale = take((size_t)L->n_seg * 2 * L->S * sizeof(unsigned));
@@ -598,8 +572,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
         for (int i = 0; i < 4; ++i)
             if (field_maps(&c.mmap[i], c.at<float>(L.o_m[i]), L, c.tz)) return DUFWI_ERR_CUDA;
         const float *hist = c.at<float>(L.o_hist), *g = c.at<float>(L.o_grad);
-        if (tensor_map(&c.hist1, hist, L, L.S, L.n_hist_alloc, kTileX, c.tz) ||
-            tensor_map(&c.hist2, hist, L, L.S, L.n_hist_alloc, kTileX, kPairTileZ) ||
+        if (tensor_map(&c.hist1, hist, L, L.S, L.n_hist, kTileX, c.tz) ||
+            tensor_map(&c.hist2, hist, L, L.S, L.n_hist, kTileX, kPairTileZ) ||
             tensor_map(&c.grad1, g, L, L.S, 0, kTileX, c.tz) || tensor_map(&c.grad2, g, L, L.S, 0, kTileX, kPairTileZ))
             return DUFWI_ERR_CUDA;
     }
@@ -883,10 +857,6 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_test_stall = value;
         return DUFWI_OK;
-    case DUFWI_OPT_OVERLAP:
-        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
-        g_overlap = value;
-        return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
     }
 }
@@ -898,7 +868,6 @@ int dufwi_get_option(int32_t option, int32_t *value)
     case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
     case DUFWI_OPT_PERSISTENT: *value = g_persistent; return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL: *value = g_test_stall.load(); return DUFWI_OK;
-    case DUFWI_OPT_OVERLAP: *value = g_overlap; return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;
     default: return DUFWI_ERR_INVALID_ARG;
@@ -1068,32 +1037,11 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
         c.mem_par = 0;
     }
     const int dtype = c.pb->snapshot_dtype;
-    const size_t hstride = (size_t)L.S * L.slice;
-    // Overlap: the recompute of segment s - 1 runs on a second stream beside the adjoint of
-    // segment s. History bank s % 2 holds segment s; events order each adjoint after its
-    // recompute, and each recompute after the adjoint that last read its bank.
-    const bool overlap = !store_all && g_overlap != 0 && L.n_seg > 1;
-    cudaStream_t main_st = c.st, st2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr};
-    if (overlap) {
-        OverlapRes *r = overlap_resources();
-        if (!r) return DUFWI_ERR_CUDA;
-        st2 = r->st;
-        ev_fork = r->fork; ev_join = r->join;
-        ev_rec[0] = r->rec[0]; ev_rec[1] = r->rec[1]; ev_adj[0] = r->adj[0]; ev_adj[1] = r->adj[1];
-        if (cudaEventRecord(ev_fork, main_st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_fork, 0) != cudaSuccess)
-            return DUFWI_ERR_CUDA;
-    }
     for (int sg = L.n_seg - 1; sg >= 0; --sg) {
         const int t0 = store_all ? 0 : sg * L.K;
         const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
-        const int bank = store_all ? 0 : (sg & 1) * L.K;   // first history slot of this segment
         if (!store_all) {
             NvtxRange range("dufwi recompute segment");
-            if (overlap) {
-                c.st = st2;
-                if (sg + 2 <= L.n_seg - 1 && cudaStreamWaitEvent(st2, ev_adj[sg & 1], 0) != cudaSuccess) rc = DUFWI_ERR_CUDA;
-            }
             nl = 0;
             e0 = g_prof.mark(c.st);
             // restore (U^{t0}, U^{t0-1}) and recompute Lap(U^n) for n = t0 .. t1-1
@@ -1101,56 +1049,26 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
             fr.cur = 0;
             fr.prv = 1;
-            if (rc == DUFWI_OK) {
-                if (dtype == DUFWI_SNAP_FP32) {
-                    if (cudaMemcpyAsync(fr.buf[0], snap, field, cudaMemcpyDeviceToDevice, c.st) != cudaSuccess ||
-                        cudaMemcpyAsync(fr.buf[1], snap_d, field, cudaMemcpyDeviceToDevice, c.st) != cudaSuccess)
-                        rc = DUFWI_ERR_CUDA;
-                } else {
-                    const unsigned *sc = c.at<unsigned>(L.o_scale) + (size_t)sg * 2 * L.S;
-                    if (launch_snap_load(fr.buf[0], fr.buf[1], snap, snap_d, sc, dtype, L.S, L.slice, L.nxp, L.nzp,
-                                         L.pitch, c.st) != cudaSuccess)
-                        rc = DUFWI_ERR_CUDA;
-                    else {
-                        ++nl;
-                        g_launches.fetch_add(1, std::memory_order_relaxed);
-                    }
-                }
+            if (dtype == DUFWI_SNAP_FP32) {
+                CK(cudaMemcpyAsync(fr.buf[0], snap, field, cudaMemcpyDeviceToDevice, c.st));
+                CK(cudaMemcpyAsync(fr.buf[1], snap_d, field, cudaMemcpyDeviceToDevice, c.st));
+            } else {
+                const unsigned *sc = c.at<unsigned>(L.o_scale) + (size_t)sg * 2 * L.S;
+                CKL(launch_snap_load(fr.buf[0], fr.buf[1], snap, snap_d, sc, dtype, L.S, L.slice, L.nxp, L.nzp,
+                                     L.pitch, c.st));
             }
-            if (rc == DUFWI_OK) rc = forward_range(c, fr, t0, t1, kFwdHist, wavelet, nullptr, hist + bank * hstride, t0, nl);
-            if (rc == DUFWI_OK) g_prof.span(1, e0, g_prof.mark(c.st), nl);
-            if (overlap) {
-                if (rc == DUFWI_OK && (cudaEventRecord(ev_rec[sg & 1], st2) != cudaSuccess ||
-                                       cudaStreamWaitEvent(main_st, ev_rec[sg & 1], 0) != cudaSuccess))
-                    rc = DUFWI_ERR_CUDA;
-                c.st = main_st;
-            }
-            if (rc) {
-                if (overlap) {   // rejoin the second stream before returning
-                    cudaEventRecord(ev_join, st2);
-                    cudaStreamWaitEvent(main_st, ev_join, 0);
-                }
-                return rc;
-            }
+            rc = forward_range(c, fr, t0, t1, kFwdHist, wavelet, nullptr, hist, t0, nl);
+            if (rc) return rc;
+            g_prof.span(1, e0, g_prof.mark(c.st), nl);
         }
-        // adjoint steps m = t1 .. t0+1, imaging with Lap(U^{m-1}) (history slot bank + m-1-t0)
+        // adjoint steps m = t1 .. t0+1, imaging with Lap(U^{m-1})
         NvtxRange range("dufwi adjoint segment");
         nl = 0;
         e0 = g_prof.mark(c.st);
-        rc = adjoint_range(c, ar, t1, t0 + 1, asrc, g_shot, t0 - bank, nl);
-        if (rc == DUFWI_OK && overlap && cudaEventRecord(ev_adj[sg & 1], main_st) != cudaSuccess) rc = DUFWI_ERR_CUDA;
-        if (rc) {
-            if (overlap) {
-                cudaEventRecord(ev_join, st2);
-                cudaStreamWaitEvent(main_st, ev_join, 0);
-            }
-            return rc;
-        }
+        rc = adjoint_range(c, ar, t1, t0 + 1, asrc, g_shot, t0, nl);
+        if (rc) return rc;
         g_prof.span(2, e0, g_prof.mark(c.st), nl);
     }
-    if (overlap &&
-        (cudaEventRecord(ev_join, st2) != cudaSuccess || cudaStreamWaitEvent(main_st, ev_join, 0) != cudaSuccess))
-        return DUFWI_ERR_CUDA;
     // (2/C) scaling, fold of the absorbing layer, FP64 reduction over transmits
     nl = 0;
     e0 = g_prof.mark(c.st);

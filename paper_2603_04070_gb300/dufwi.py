@@ -31,7 +31,6 @@ OPT_TWO_STEP = 2
 OPT_REUSE_TABLES = 3
 OPT_PERSISTENT = 4
 OPT_TEST_STALL = 5
-OPT_OVERLAP = 6
 
 
 class DufwiError(RuntimeError):

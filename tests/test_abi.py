@@ -144,9 +144,7 @@ def test_boundary_and_option_validation():
     sh = g.c_structs()[1]
     out = ctypes.c_size_t(0)
     assert d._lib.dufwi_workspace_size(ctypes.byref(bad), ctypes.byref(sh), 1, ctypes.byref(out)) == d.ERR_INVALID_ARG
-    assert d.get_option(d.OPT_OVERLAP) == 1                 # default: recompute beside the adjoint
-    for opt, good, badv in ((d.OPT_PERSISTENT, 1, 2), (d.OPT_TEST_STALL, 0, 3), (d.OPT_TILE_Z, 64, 48),
-                            (d.OPT_OVERLAP, 0, 2)):
+    for opt, good, badv in ((d.OPT_PERSISTENT, 1, 2), (d.OPT_TEST_STALL, 0, 3), (d.OPT_TILE_Z, 64, 48)):
         before = d.get_option(opt)
         with pytest.raises(d.DufwiError):
             d.set_option(opt, badv)

@@ -351,23 +351,6 @@ def test_persistent_sweeps_are_bit_identical(d, ckpt, order, nx, nz, n_tx, n_map
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("ckpt,dtype", [(30, "fp32"), (25, "fp16"), (64, "bf16")])
-def test_overlapped_reverse_sweep_is_bit_identical(d, ckpt, dtype):
-    """Recompute of segment s-1 on the library's second stream beside the adjoint of segment s
-    (two history banks) gives exactly the sequential result, for even and odd segment counts."""
-    wl = inputs.make_workload("linear_disk", seed=14, nx=88, nz=70, nt=257, n_elem=20, n_tx=3, n_maps=2)
-    M_obs = _observed(wl)
-    out = []
-    for overlap in (0, 1):
-        d.set_option(d.OPT_OVERLAP, overlap)
-        try:
-            out.append(_gpu_grad(d, wl, M_obs, ckpt_interval=ckpt, snapshot_dtype=dtype))
-        finally:
-            d.set_option(d.OPT_OVERLAP, 1)
-    for a, b in zip(out[0], out[1]):
-        assert np.array_equal(a, b)
-
-
 def test_persistent_sweeps_sized_batch_bit_identical(d):
     sizes = [(96, 70), (64, 96), (80, 80)]
     wl, sizes = inputs.sized_batch(8, sizes, nt=200, n_elem=16, n_tx=2)

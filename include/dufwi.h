@@ -288,7 +288,10 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     recompute segment, an adjoint segment) as one cooperative launch whose CTAs stay resident
  *     and pass 64 x 32 tiles from step to step through per-tile counters in the workspace,
  *     instead of one launch per time step; bit-identical results. Not used with the two-step
- *     kernel, the Born step or a density map; 0 (the default) launches once per step.
+ *     kernel, the Born step or a density map; 0 (the default) launches once per step. The
+ *     counters rely on all CTAs of the launch being resident: do not run other kernels on the
+ *     device at the same time (another stream, another process). If residency is lost the
+ *     bounded waits end the launch with DUFWI_ERR_TIMEOUT in the status word.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device

@@ -68,8 +68,7 @@ class _Shots(ctypes.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libdufwi.so is not built (run __graft_entry__.build() or "
-                          "python -m paper_2603_04070_gb300.build_lib)")
+        raise ImportError("libdufwi.so is not built (run python -m paper_2603_04070_gb300.build_lib)")
     lib = ctypes.CDLL(LIB_PATH)
     P, A, S = ctypes.POINTER(_Problem), ctypes.POINTER(_Array), ctypes.POINTER(_Shots)
     vp, sz = ctypes.c_void_p, ctypes.c_size_t

@@ -115,3 +115,31 @@ def test_classical_fwi_on_gpu(d):
         assert torch.all(J[1:] < J[:-1]), (loop.__name__, J)
         assert torch.isfinite(res.sos).all()
         assert res.sos.min() >= 1300.0 and res.sos.max() <= 3000.0
+
+
+def test_autotune_gradient_probe_bit_identical(d):
+    """The gradient-mode tuner times every launch-option candidate on a short misfit gradient and
+    keeps one of them; the options change speed only, so the full gradient under the chosen set
+    equals the gradient under the default set bit for bit. A second call hits the cache."""
+    from paper_2603_04070_gb300 import autotune
+    wl = inputs.ring_phantom(seed=5, n_maps=1)
+    pb, geom = _setup(d, wl, ckpt_interval=0)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    obs = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), wav, geom)
+    try:
+        autotune.apply(autotune.CANDIDATES[0])
+        J0, g0 = d.misfit_gradient(pb, sos, wav, geom, obs)
+        best = autotune.tune(pb, sos, wav, geom, gradient=True, cd_obs=obs, steps=120, repeats=1)
+        picked = {k: best[k] for k in ("tile_z", "two_step", "persistent")}
+        assert picked in [dict(c) for c in autotune.CANDIDATES]
+        assert len(best["candidates_ms_per_step"]) == len(autotune.CANDIDATES)
+        assert all(t > 0 for t in best["candidates_ms_per_step"])
+        J1, g1 = d.misfit_gradient(pb, sos, wav, geom, obs)
+        torch.cuda.synchronize()
+        assert torch.equal(J0, J1)
+        assert torch.equal(g0, g1)
+        again = autotune.tune(pb, sos, wav, geom, gradient=True, cd_obs=obs)
+        assert again == best
+    finally:
+        autotune.apply(autotune.CANDIDATES[0])

@@ -630,7 +630,9 @@ def run_hvp(args):
     full shot set (512 x 512, 16 transmits, 6000 steps, checkpoint interval 100): device time of
     the JVP (background and Born step per time step), of the VJP of a cotangent (recompute and
     adjoint sweeps from the saved snapshots), and of a whole HVP (forward with snapshots, JVP,
-    VJP), each over the same workspaces, after warm-up."""
+    VJP), each over the same workspaces, after warm-up. Also the exact Hessian-vector product of
+    the misfit: the second-order call (background, Born, adjoint and differentiated-adjoint sweeps,
+    returning J v and d/dC[J^T w] . v for the residual cotangent w) plus the VJP of 2 J v."""
     import torch
     from paper_2603_04070_gb300 import build_lib, inputs
     build_lib.build()
@@ -647,6 +649,19 @@ def run_hvp(args):
     dcd = torch.empty((1, wl.n_tx, wl.nt, wl.n_rx), dtype=torch.float32, device=dev)
     cd = torch.empty_like(dcd)
     g = torch.empty_like(sos)
+    ws_s = torch.empty(dufwi.second_order_workspace_size(pb, geom, 1), dtype=torch.uint8, device=dev)
+    obs = dufwi.simulate(pb, torch.from_numpy(wl.sos_true).to(dev), wav, geom)
+    w_res = 2.0 * (dufwi.simulate(pb, sos, wav, geom) - obs)       # residual cotangent at the start map
+    so = torch.empty_like(sos)
+    dcd_s = torch.empty_like(dcd)
+
+    def second():
+        dufwi.second_order(pb, sos, wav, geom, w_res, v, so=so, dcd=dcd_s, workspace=ws_s)
+
+    def exact_hvp():       # H v = so + 2 J^T (J v); the VJP reuses the forward_save workspace
+        second()
+        fwd()
+        dufwi.backward(pb, sos, wav, geom, 2.0 * dcd_s, ws_g, grad=g)
 
     def jvp():
         dufwi.jvp(pb, sos, wav, geom, v, dcd=dcd, workspace=ws_j)
@@ -673,15 +688,21 @@ def run_hvp(args):
     ms_fwd = timed(fwd)
     ms_vjp = timed(vjp)
     ms_hvp = timed(lambda: (fwd(), jvp(), vjp()))
+    ms_second = timed(second, reps=2)
+    ms_exact = timed(exact_hvp, reps=2)
     cells = (wl.nx + 2 * wl.pml) * (wl.nz + 2 * wl.pml) * wl.n_tx * wl.nt
     line = {"metric": "ms per Gauss-Newton Hessian-vector product", "value": ms_hvp, "unit": "ms", "n_gpus": 1,
             "steps": 3, "warmup": max(args.warmup, 1), "higher_is_better": False, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "full_shot_set: 512x512 (+20), 16 transmits x 128 receivers, "
                                                         "%d steps, checkpoint interval %d" % (wl.nt, args.ckpt)},
             "ms_jvp": ms_jvp, "ms_forward_save": ms_fwd, "ms_vjp": ms_vjp,
+            "ms_second_order": ms_second, "ms_exact_hvp": ms_exact,
+            "second_order_workspace_gb": ws_s.numel() / 1e9,
             "jvp_gcell_updates_per_s": 2.0 * cells / (ms_jvp / 1e3) / 1e9,
             "note": "JVP: background + Born step per time step (2 cell updates per cell and step); VJP: recompute "
-                    "+ adjoint sweeps from the snapshots of forward_save"}
+                    "+ adjoint sweeps from the snapshots of forward_save; second order: background + Born "
+                    "forward with snapshots of both, per segment their recompute, then adjoint + "
+                    "differentiated adjoint; exact HVP = second order + forward_save + VJP of 2 J v"}
     print(json.dumps(line), flush=True)
 
 

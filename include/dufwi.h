@@ -207,6 +207,37 @@ int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, c
               float *dcd, float *cd, void *workspace, size_t workspace_bytes,
               void *stream /* cudaStream_t */);
 
+/* Second-order product of the forward model: the derivative of the vector-Jacobian product
+ * G = (dM/dC)^T cd_grad along an SoS direction dsos, with cd_grad held fixed,
+ *   so[b] = d/dC[(dM[b]/dC[b])^T cd_grad[b]] . dsos[b]
+ * (the Hessian of the scalar <M, cd_grad> applied to dsos). With cd_grad = 2 (M - M_obs) the
+ * exact Hessian-vector product of the misfit (Eqs. 5-6) is H v = so + 2 J^T (J v), J = dM/dC;
+ * the call returns J v as well (dcd). It differentiates the discrete adjoint once more: with
+ * dkappa' = 2 kappa' dsos / C (dsos extended into the absorbing layer like C),
+ *   dU^{n+1} = Eq. 2 on dU + dkappa' Lap(U^n)                       (the Born field of dufwi_jvp)
+ *   mu^m     = Eq. 2 on mu + kappa' cd_grad^m at the receivers      (the adjoint of dufwi_backward)
+ *   dmu^m    = Eq. 2 on dmu + dkappa' Lap(mu^{m+1}) + dkappa' cd_grad^m at the receivers
+ *   so = (2/C) fold[sum_m dmu^m Lap(U^{m-1}) + mu^m Lap(dU^{m-1})] - (2 dsos / C^2) fold[sum_m mu^m Lap(U^{m-1})]
+ * The forward pass keeps Lap(U^n) and Lap(dU^n) for every step (ckpt_interval 0) or, with
+ * checkpoints, FP32 snapshots of U and dU every ckpt_interval steps (snapshot_dtype is not used
+ * here) and recomputes each segment's two histories during the reverse pass.
+ *   cd_grad [n_maps][n_tx][nt][n_rx] float, device (NULL only when n_rx == 0)
+ *   dsos    [n_maps][nz][nx] float, device
+ *   dcd     NULL or [n_maps][n_tx][nt][n_rx] float, device, output: J dsos
+ *   so      [n_maps][nz][nx] float, device, output
+ *   grad    NULL or [n_maps][nz][nx] float, device, output: (dM/dC)^T cd_grad
+ *   workspace: device, >= dufwi_second_order_workspace_size bytes.
+ * Constant density and the damping layer only: a density map or DUFWI_BOUNDARY_CPML gives
+ * DUFWI_ERR_UNSUPPORTED. The launch options (tile height, two-step, persistent) do not apply:
+ * every step uses 64 x 32 tiles, one launch per step. */
+int dufwi_second_order_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots,
+                                      int32_t n_maps, size_t *bytes);
+int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *density,
+                       const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                       int32_t n_maps, const float *cd_grad, const float *dsos, float *dcd, float *so,
+                       float *grad, void *workspace, size_t workspace_bytes,
+                       void *stream /* cudaStream_t */);
+
 /* Forward model for callers that cannot allocate device memory. The paper has no counterpart:
  * this serves hosts that must not call cudaMalloc while running, such as a fixed-latency
  * acquisition loop (a device allocation can synchronise the device) or an application that hands

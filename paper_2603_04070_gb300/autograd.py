@@ -12,6 +12,13 @@ Calling ``backward`` twice needs ``retain_graph=True``; the saved workspace is r
 Forward-mode AD (``torch.autograd.forward_ad``) uses the linearised Born simulation
 (``dufwi_jvp``). ``hvp_gauss_newton`` combines it with the adjoint into Gauss-Newton
 Hessian-vector products of the misfit.
+
+Double backward: with ``create_graph=True`` the vector-Jacobian product is itself a node,
+G(C, w) = (dM/dC)^T w, whose backward is ``dufwi_second_order``. For a cotangent v of G it
+returns the Born data (dM/dC) v for w and the second-order term d/dC[(dM/dC)^T w] . v for C, so
+``torch.autograd.grad`` of a gradient gives exact Hessian-vector products of any loss built on
+the channel data (``hvp`` does this for the misfit). Third derivatives are not provided: a
+second backward with ``create_graph=True`` raises.
 """
 from __future__ import annotations
 
@@ -44,9 +51,37 @@ class _Simulate(torch.autograd.Function):
         sos, wavelet = ctx.saved_tensors
         grad = None
         if ctx.needs_input_grad[0]:
-            grad = dufwi.backward(ctx.problem, sos.detach().contiguous(), wavelet.detach().contiguous(), ctx.geom,
-                                  cd_grad.contiguous(), ctx.workspace)
+            if torch.is_grad_enabled():   # create_graph: the product must be differentiable in (C, w)
+                grad = _VJP.apply(sos, cd_grad, wavelet, ctx.problem, ctx.geom, ctx.workspace)
+            else:
+                grad = dufwi.backward(ctx.problem, sos.detach().contiguous(), wavelet.detach().contiguous(),
+                                      ctx.geom, cd_grad.contiguous(), ctx.workspace)
         return grad, None, None, None
+
+
+class _VJP(torch.autograd.Function):
+    """G = (dM/dC)^T w as a function of C and w (the differentiable form of the backward pass)."""
+
+    @staticmethod
+    def forward(ctx, sos, cd_grad, wavelet, problem, geom, workspace):
+        sos_d = sos.detach().contiguous()
+        w_d = cd_grad.detach().contiguous()
+        grad = dufwi.backward(problem, sos_d, wavelet.detach().contiguous(), geom, w_d, workspace)
+        ctx.save_for_backward(sos, cd_grad, wavelet)
+        ctx.problem = problem
+        ctx.geom = geom
+        return grad
+
+    @staticmethod
+    def backward(ctx, v):
+        if torch.is_grad_enabled():
+            raise RuntimeError("dufwi autograd: third derivatives are not provided (the second backward must not "
+                               "use create_graph=True)")
+        sos, cd_grad, wavelet = ctx.saved_tensors
+        so, dcd = dufwi.second_order(ctx.problem, sos.detach().contiguous(), wavelet.detach().contiguous(), ctx.geom,
+                                     cd_grad.detach().contiguous(), v.contiguous())
+        return (so if ctx.needs_input_grad[0] else None), (dcd if ctx.needs_input_grad[1] else None), \
+            None, None, None, None
 
 
 def simulate(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: dufwi.Geometry) -> torch.Tensor:
@@ -70,3 +105,15 @@ def hvp_gauss_newton(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.T
     _, ws = dufwi.forward_save(problem, sos, wavelet, geom)
     dcd = dufwi.jvp(problem, sos, wavelet, geom, v.contiguous())
     return dufwi.backward(problem, sos, wavelet, geom, 2.0 * dcd, ws)
+
+
+def hvp(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: dufwi.Geometry, cd_obs: torch.Tensor,
+        v: torch.Tensor) -> torch.Tensor:
+    """Exact Hessian-vector product of the misfit J = sum (M - M_obs)^2 per map, by double
+    backward through the autograd wrapper: H v = 2 J^T (J v) + d/dC[J^T 2 (M - M_obs)] . v."""
+    c = sos.detach().clone().requires_grad_(True)
+    with torch.enable_grad():
+        J = misfit(problem, c, wavelet, geom, cd_obs).sum()
+        (g,) = torch.autograd.grad(J, c, create_graph=True)
+        (Hv,) = torch.autograd.grad(g, c, grad_outputs=v)
+    return Hv

@@ -96,6 +96,9 @@ struct Layout {
     size_t o_cm[8], o_cpml;  // CPML: memory variables (two sets of psi_x, psi_z, xi_x, xi_z), coefficient tables
     size_t o_flags, o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
+    // second-order calls: adjoint and differentiated-adjoint rings, second and third histories,
+    // two more imaging sums, the second adjoint source
+    size_t o_mu[4], o_dmu[4], o_hist2, o_hist3, o_acc1, o_acc2, o_asrc2;
 };
 
 // Last table contents uploaded to each workspace (see common_setup), and whether a call may
@@ -137,7 +140,7 @@ int validate_problem(const dufwi_problem *pb)
     return DUFWI_OK;
 }
 
-enum LayoutKind { kLayoutSimulate = 0, kLayoutGradient = 1, kLayoutJvp = 2 };
+enum LayoutKind { kLayoutSimulate = 0, kLayoutGradient = 1, kLayoutJvp = 2, kLayoutSecond = 3 };
 
 int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int kind, Layout *L)
 {
@@ -197,7 +200,7 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     L->o_bz = take((size_t)n_maps * L->slice * sizeof(float));
     if (pb->boundary == DUFWI_BOUNDARY_CPML) {
         // the memory variables are not checkpointed: gradients keep every step; no Born step
-        if (kind == kLayoutJvp || (gradient && L->n_seg > 1)) return DUFWI_ERR_UNSUPPORTED;
+        if (kind == kLayoutJvp || kind == kLayoutSecond || (gradient && L->n_seg > 1)) return DUFWI_ERR_UNSUPPORTED;
         for (int i = 0; i < 8; ++i) L->o_cm[i] = take((size_t)L->S * L->slice * sizeof(float));
         L->o_cpml = take(sizeof(float) * 4 * (size_t)(L->nxp + L->nzp));
     }
@@ -221,6 +224,26 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         L->o_hist = take(field);                                         // Lap(U^n) of the current step
         L->o_dkap = take((size_t)n_maps * L->slice * sizeof(float));
         L->o_cd = take(cdb);                                             // background traces
+    }
+    if (kind == kLayoutSecond) {
+        const bool store_all = pb->ckpt_interval == 0 || pb->ckpt_interval >= steps;
+        for (int i = 0; i < 4; ++i) {
+            L->o_m[i] = take(field);                                     // Born field dU
+            L->o_mu[i] = take(field);                                    // adjoint mu
+            L->o_dmu[i] = take(field);                                   // its derivative along v
+        }
+        L->o_hist = take(field * (size_t)L->n_hist);                     // Lap(U^n)
+        L->o_hist2 = take(field * (size_t)L->n_hist);                    // Lap(dU^n)
+        L->o_hist3 = take(field);                                        // Lap(mu^{m+1}) of the current step
+        L->o_grad = take(field);                                         // sum mu^m Lap(U^{m-1})
+        L->o_acc1 = take(field);                                         // sum dmu^m Lap(U^{m-1})
+        L->o_acc2 = take(field);                                         // sum mu^m Lap(dU^{m-1})
+        if (!store_all) L->o_snap = take((size_t)L->n_seg * 4 * field);  // FP32 U^t0, U^t0-1, dU^t0, dU^t0-1
+        L->o_dkap = take((size_t)n_maps * L->slice * sizeof(float));
+        L->o_cd = take(cdb);                                             // Born traces when not requested
+        L->o_asrc = take(cdb);                                           // kappa'_r w
+        L->o_asrc2 = take(cdb);                                          // dkappa'_r w
+        L->o_fold = take((size_t)n_maps * L->nzp * L->Nx * sizeof(double));
     }
     L->total = off;
     return DUFWI_OK;
@@ -358,10 +381,13 @@ struct Ctx {
     bool vd = false;                          // density map given: staggered variable-density operator
     bool persistent = false;                  // one cooperative launch per sweep segment
     bool cpml = false;                        // convolutional PML instead of the damping term
+    bool so = false;                          // second-order call (dufwi_second_order)
     int mem_par = 0;                          // CPML: which memory-variable set the next step reads
     CpmlMaps cm_fwd[2], cm_adj[2];            // CPML: maps reading set 0 / set 1
     FieldMaps fmap[4], mmap[4];
     CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1, bx1, bz1;
+    FieldMaps mumap[4], dmumap[4];            // second-order calls: mu and dmu rings
+    CUtensorMap so_h2, so_h3, so_acc1, so_acc2;
     int *status() const { return reinterpret_cast<int *>(ws + L.o_status); }
     template <typename T> T *at(size_t o) const { return reinterpret_cast<T *>(ws + o); }
 };
@@ -434,13 +460,13 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.st = static_cast<cudaStream_t>(stream);
     c.cpml = c.pb->boundary == DUFWI_BOUNDARY_CPML;
     c.vd = density != nullptr || c.cpml;        // the CPML runs on the staggered operator
-    if (c.vd && c.jvp) return DUFWI_ERR_UNSUPPORTED;   // no Born step for the staggered operators
+    if (c.vd && (c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;   // no Born step for the staggered operators
     if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
     if (c.vd && c.pb->c_max * c.pb->dt / c.pb->dx > stagger_stability_limit(c.pb->fd_order)) return DUFWI_ERR_CFL;
-    c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd;
-    c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd;
+    c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd && !c.so;
+    c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd && !c.so;
     c.mem_par = 0;
-    c.tz = (c.vd || c.persistent) ? 32 : g_tile_z;
+    c.tz = (c.vd || c.persistent || c.so) ? 32 : g_tile_z;
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
     std::vector<int> sorted1, sorted2, sortede;
@@ -566,6 +592,21 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
             if (field_maps(&c.mmap[i], c.at<float>(L.o_m[i]), L, c.tz)) return DUFWI_ERR_CUDA;
         if (tensor_map(&c.hist1, c.at<float>(L.o_hist), L, L.S, 1, kTileX, c.tz) ||
             tensor_map(&c.dkap1, c.at<float>(L.o_dkap), L, L.n_maps, 0, kTileX, c.tz))
+            return DUFWI_ERR_CUDA;
+    }
+    if (c.so) {   // 64 x 32 tiles throughout (c.tz is 32)
+        for (int i = 0; i < 4; ++i)
+            if (field_maps(&c.mmap[i], c.at<float>(L.o_m[i]), L, c.tz) ||
+                field_maps(&c.mumap[i], c.at<float>(L.o_mu[i]), L, c.tz) ||
+                field_maps(&c.dmumap[i], c.at<float>(L.o_dmu[i]), L, c.tz))
+                return DUFWI_ERR_CUDA;
+        if (tensor_map(&c.hist1, c.at<float>(L.o_hist), L, L.S, L.n_hist, kTileX, c.tz) ||
+            tensor_map(&c.so_h2, c.at<float>(L.o_hist2), L, L.S, L.n_hist, kTileX, c.tz) ||
+            tensor_map(&c.so_h3, c.at<float>(L.o_hist3), L, L.S, 0, kTileX, c.tz) ||
+            tensor_map(&c.dkap1, c.at<float>(L.o_dkap), L, L.n_maps, 0, kTileX, c.tz) ||
+            tensor_map(&c.grad1, c.at<float>(L.o_grad), L, L.S, 0, kTileX, c.tz) ||
+            tensor_map(&c.so_acc1, c.at<float>(L.o_acc1), L, L.S, 0, kTileX, c.tz) ||
+            tensor_map(&c.so_acc2, c.at<float>(L.o_acc2), L, L.S, 0, kTileX, c.tz))
             return DUFWI_ERR_CUDA;
     }
     if (gradient) {
@@ -1264,6 +1305,222 @@ int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, c
                           L.nt - 1, c.st));
     }
     g_prof.span(0, e0, g_prof.mark(c.st), nl);
+    return DUFWI_OK;
+}
+
+}  // extern "C"
+
+namespace dufwi {
+namespace {
+
+// One step of a second-order sweep on ring r (updated in place, like one_step).
+int so_step(Ctx &c, Ring &r, int kind, StepParams p, const SoParams &q, long long &nl)
+{
+    SoMaps tm;
+    memset(&tm, 0, sizeof(tm));
+    tm.cur_box = r.map[r.cur].box1;
+    tm.out_tile = r.map[r.prv].tile1;
+    tm.kap_tile = c.kap1;
+    tm.h1 = c.hist1;
+    tm.h2 = c.so_h2;
+    tm.src = c.so_h3;
+    tm.dk = c.dkap1;
+    if (kind == kSoAdj) {          // sums of mu^m Lap(U^{m-1}) and mu^m Lap(dU^{m-1})
+        tm.g1 = c.grad1;
+        tm.g2 = c.so_acc2;
+    }
+    if (kind == kSoBornAdj) tm.g1 = c.so_acc1;   // sum of dmu^m Lap(U^{m-1})
+    p.out = r.buf[r.prv];
+    p.rx_tab = c.at<int2>(c.L.o_tab1);
+    p.rx_sorted = c.at<int>(c.L.o_sorted1);
+    CKL(launch_so_step(c.L.radius, kind, tm, p, q, c.st));
+    std::swap(r.cur, r.prv);
+    return DUFWI_OK;
+}
+
+// Background and Born steps n = n0 .. n1-1, interleaved: the background step keeps Lap(U^n) in
+// slot n - h0 of the first history, then the Born step adds dkappa' times it and keeps Lap(dU^n)
+// in the same slot of the second. dcd: Born traces (dU^n at the receivers), or null.
+int so_forward_range(Ctx &c, Ring &fr, Ring &br, int n0, int n1, int h0, const float *wavelet, float *dcd,
+                     long long &nl)
+{
+    const Layout &L = c.L;
+    const size_t hstride = (size_t)L.S * L.slice;
+    float *h1 = c.at<float>(L.o_hist), *h2 = c.at<float>(L.o_hist2);
+    StepParams pf = c.base;
+    pf.inj_node = c.at<int>(L.o_tx);
+    pf.inj_val = wavelet;
+    StepParams pb = c.base;
+    pb.smp_node = c.at<int>(L.o_rx);
+    pb.cd = dcd;
+    for (int n = n0; n < n1; ++n) {
+        pf.step = n;
+        pf.hist = h1 + (size_t)(n - h0) * hstride;
+        int rc = one_step(c, fr, kFwdHist, pf, nl);
+        if (rc) return rc;
+        pb.step = n;
+        SoParams q;
+        memset(&q, 0, sizeof(q));
+        q.lap_out = h2 + (size_t)(n - h0) * hstride;
+        q.h1_slot = n - h0;
+        rc = so_step(c, br, kSoBorn, pb, q, nl);
+        if (rc) return rc;
+    }
+    return DUFWI_OK;
+}
+
+Ring ring_of(Ctx &c, const size_t *offsets, const FieldMaps *maps)
+{
+    Ring r;
+    for (int i = 0; i < 4; ++i) r.buf[i] = c.at<float>(offsets[i]);
+    r.map = maps;
+    r.cur = 0;
+    r.prv = 1;
+    return r;
+}
+
+}  // namespace
+}  // namespace dufwi
+
+extern "C" {
+
+int dufwi_second_order_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int32_t n_maps,
+                                      size_t *bytes)
+{
+    if (!bytes) return DUFWI_ERR_INVALID_ARG;
+    Layout L;
+    int rc = make_layout(pb, shots, n_maps, kLayoutSecond, &L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return DUFWI_OK;
+}
+
+int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                       const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_grad,
+                       const float *dsos, float *dcd, float *so, float *grad, void *workspace,
+                       size_t workspace_bytes, void *stream)
+{
+    Ctx c;
+    c.pb = pb;
+    c.so = true;
+    int rc = make_layout(pb, shots, n_maps, kLayoutSecond, &c.L);
+    if (rc) return rc;
+    if (!dsos || !so || (!cd_grad && c.L.n_rx > 0)) return DUFWI_ERR_INVALID_ARG;
+    rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
+    if (rc) return rc;
+    NvtxRange range("dufwi second order");
+    const Layout &L = c.L;
+    const size_t field = (size_t)L.S * L.slice * sizeof(float);
+    const bool store_all = L.n_seg == 1;
+    long long nl = 0;
+    int e0 = g_prof.mark(c.st);
+    const float *kap = c.at<float>(L.o_kap);
+    float *dkap = c.at<float>(L.o_dkap);
+    float *asrc = c.at<float>(L.o_asrc), *asrc2 = c.at<float>(L.o_asrc2);
+    CKL(launch_setup_dkappa(sos, dsos, kap, dkap, L.n_maps, L.Nx, L.Nz, L.P, L.nzp, L.pitch, c.st));
+    if (L.n_rx > 0) {   // kappa'_r w drives mu, dkappa'_r w enters dmu
+        CKL(launch_cotangent_source(cd_grad, kap, c.at<int>(L.o_rx), asrc, c.status(), L.S, L.n_tx, L.n_rx, L.nt,
+                                    L.slice, L.pitch, c.st));
+        CKL(launch_cotangent_source(cd_grad, dkap, c.at<int>(L.o_rx), asrc2, c.status(), L.S, L.n_tx, L.n_rx, L.nt,
+                                    L.slice, L.pitch, c.st));
+    }
+    Ring fr = ring_of(c, L.o_f, c.fmap), br = ring_of(c, L.o_m, c.mmap);
+    Ring ar = ring_of(c, L.o_mu, c.mumap), dr = ring_of(c, L.o_dmu, c.dmumap);
+    for (int i = 0; i < 4; ++i) {
+        CK(cudaMemsetAsync(fr.buf[i], 0, field, c.st));
+        CK(cudaMemsetAsync(br.buf[i], 0, field, c.st));
+        CK(cudaMemsetAsync(ar.buf[i], 0, field, c.st));
+        CK(cudaMemsetAsync(dr.buf[i], 0, field, c.st));
+    }
+    float *accG = c.at<float>(L.o_grad), *accA = c.at<float>(L.o_acc1), *accB = c.at<float>(L.o_acc2);
+    CK(cudaMemsetAsync(accG, 0, field, c.st));
+    CK(cudaMemsetAsync(accA, 0, field, c.st));
+    CK(cudaMemsetAsync(accB, 0, field, c.st));
+    CK(cudaMemsetAsync(c.at<float>(L.o_hist3), 0, field, c.st));
+    g_prof.span(3, e0, g_prof.mark(c.st), nl);
+
+    // forward: background and Born fields together, FP32 snapshots of both at segment starts
+    nl = 0;
+    e0 = g_prof.mark(c.st);
+    float *dcd_out = L.n_rx > 0 ? (dcd ? dcd : c.at<float>(L.o_cd)) : nullptr;
+    for (int sg = 0; sg < L.n_seg; ++sg) {
+        const int t0 = store_all ? 0 : sg * L.K;
+        const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
+        if (!store_all) {
+            char *snap = c.at<char>(L.o_snap) + (size_t)sg * 4 * field;
+            CK(cudaMemcpyAsync(snap, fr.buf[fr.cur], field, cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(snap + field, fr.buf[fr.prv], field, cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(snap + 2 * field, br.buf[br.cur], field, cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(snap + 3 * field, br.buf[br.prv], field, cudaMemcpyDeviceToDevice, c.st));
+        }
+        rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, dcd_out, nl);
+        if (rc) return rc;
+    }
+    if (dcd_out)
+        CKL(launch_sample(br.buf[br.cur], c.at<int>(L.o_rx), dcd_out, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt,
+                          L.nt - 1, c.st));
+    g_prof.span(0, e0, g_prof.mark(c.st), nl);
+
+    // reverse: per segment, the two histories (recomputed from the snapshots when checkpointed),
+    // then mu and dmu from step t1 down to t0 + 1, interleaved (dmu's step m reads Lap(mu^{m+1})
+    // that mu's step m has just written)
+    float *h3 = c.at<float>(L.o_hist3);
+    for (int sg = L.n_seg - 1; sg >= 0; --sg) {
+        const int t0 = store_all ? 0 : sg * L.K;
+        const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
+        if (!store_all) {
+            nl = 0;
+            e0 = g_prof.mark(c.st);
+            const char *snap = c.at<char>(L.o_snap) + (size_t)sg * 4 * field;
+            fr.cur = br.cur = 0;
+            fr.prv = br.prv = 1;
+            CK(cudaMemcpyAsync(fr.buf[0], snap, field, cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(fr.buf[1], snap + field, field, cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(br.buf[0], snap + 2 * field, field, cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(br.buf[1], snap + 3 * field, field, cudaMemcpyDeviceToDevice, c.st));
+            rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, nullptr, nl);
+            if (rc) return rc;
+            g_prof.span(1, e0, g_prof.mark(c.st), nl);
+        }
+        nl = 0;
+        e0 = g_prof.mark(c.st);
+        StepParams pa = c.base;
+        pa.inj_node = c.at<int>(L.o_rx);
+        pa.inj_val = asrc;
+        StepParams pd = pa;
+        pd.inj_val = asrc2;
+        for (int m = t1; m >= t0 + 1; --m) {
+            pa.step = pd.step = m;
+            SoParams qa, qd;
+            memset(&qa, 0, sizeof(qa));
+            memset(&qd, 0, sizeof(qd));
+            qa.lap_out = h3;
+            qa.sum1 = accG;
+            qa.sum2 = accB;
+            qa.h1_slot = qa.h2_slot = m - 1 - t0;
+            rc = so_step(c, ar, kSoAdj, pa, qa, nl);
+            if (rc) return rc;
+            qd.sum1 = accA;
+            qd.h1_slot = m - 1 - t0;
+            rc = so_step(c, dr, kSoBornAdj, pd, qd, nl);
+            if (rc) return rc;
+        }
+        g_prof.span(2, e0, g_prof.mark(c.st), nl);
+    }
+
+    // so = (2/C) fold[A + B - (v/C) G]; grad = (2/C) fold[G]
+    nl = 0;
+    e0 = g_prof.mark(c.st);
+    CKL(launch_so_combine(accA, accB, accG, sos, dsos, L.S, L.n_tx, L.Nx, L.Nz, L.P, L.nzp, L.pitch, L.slice, c.st));
+    CKL(launch_fold(accA, sos, so, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
+                    nullptr, c.st));
+    ++nl;
+    if (grad) {
+        CKL(launch_fold(accG, sos, grad, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
+                        nullptr, c.st));
+        ++nl;
+    }
+    g_prof.span(3, e0, g_prof.mark(c.st), nl);
     return DUFWI_OK;
 }
 

@@ -43,6 +43,13 @@ enum StepMode : int {
     kBorn = 4,           // linearised (Born) step: dU^{n+1} = Eq. 2 on dU + dkappa' Lap(U^n), receivers
 };
 
+// Second-order sweep kinds (so_step_kernel).
+enum SoKind : int {
+    kSoBorn = 0,         // Born step that also keeps Lap(dU^n); receivers sampled when cd is set
+    kSoAdj = 1,          // adjoint step, two imaging sums (with Lap(U^{m-1}) and Lap(dU^{m-1})), keeps Lap(mu^{m+1})
+    kSoBornAdj = 2,      // derivative of the adjoint step along v: source dkappa' Lap(mu^{m+1}), imaging with Lap(U^{m-1})
+};
+
 // Tensor maps of one step launch (all FP32, no swizzle, zero fill outside the tensor):
 //   cur_box   field being read with halo: dims (nxp, nzp, S), box 72 x (TZ + 8) x 1
 //   out_tile  field updated in place: dims (nxp, nzp, S), box 64 x TZ x 1
@@ -114,6 +121,24 @@ struct StepParams {
                              // lies inside the physical grid (no memory variables); 2 only the others
 };
 
+// Second-order products (the derivative of the vector-Jacobian product along an SoS direction):
+// tensor maps and extra arguments of so_step_kernel (64 x 32 tiles).
+struct SoMaps {
+    CUtensorMap cur_box, out_tile, kap_tile;   // the advanced field (box with halo, previous tile), kappa'
+    CUtensorMap h1, h2;                        // histories [slot][S]: Lap(U^n), Lap(dU^n)
+    CUtensorMap src;                           // Lap(mu^{m+1}) of the current adjoint step [S]
+    CUtensorMap dk;                            // dkappa' [n_maps]
+    CUtensorMap g1, g2;                        // running imaging sums [S]
+};
+
+struct SoParams {
+    float *lap_out;          // Born: Lap(dU^n) (second-history slot); adjoint: Lap(mu^{m+1})
+    float *sum1;             // adjoint: sum of mu^m Lap(U^{m-1}); Born-adjoint: sum of dmu^m Lap(U^{m-1})
+    float *sum2;             // adjoint: sum of mu^m Lap(dU^{m-1})
+    int h1_slot;             // slot of Lap(U^n) (Born) or Lap(U^{m-1}) (adjoint kinds) in h1
+    int h2_slot;             // adjoint: slot of Lap(dU^{m-1}) in h2
+};
+
 // Persistent sweep: n_steps consecutive steps of one sweep in a single cooperative launch. Work
 // items are (local step i, tile k) in the order g = i * tiles + k; CTA b takes g = b, b + G, ...
 // Before item (i, k) a CTA waits until tile k and its four neighbours in the same shot have
@@ -155,6 +180,13 @@ cudaError_t launch_step_cpml(int radius, int mode, const StepMaps &tm, const Cpm
                              const CpmlParams &cp, cudaStream_t st);
 // Variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint; 64 x 32 tiles).
 cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
+// One step of the second-order sweeps (kinds kSoBorn, kSoAdj, kSoBornAdj; 64 x 32 tiles).
+cudaError_t launch_so_step(int radius, int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,
+                           cudaStream_t st);
+// Second-order term before the fold: a += b - (v / C) g on the padded grid of every shot, with v
+// and C edge-replicated into the absorbing layer.
+cudaError_t launch_so_combine(float *a, const float *b, const float *g, const float *sos, const float *dsos, int S,
+                              int n_tx, int Nx, int Nz, int P, int nzp, int pitch, long long slice, cudaStream_t st);
 // kappa' on the padded grid; with a density map kappa' = rho C^2 dt^2/(dx^2 (1 + D dt)), and the
 // buoyancies bx, bz are written too (both may be null without a density map).
 // unit_b: no density map, but buoyancies of 1 between nodes are written (staggered operator

@@ -495,6 +495,174 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 
 // </one-step kernel source>
 
+// ---- second-order products ---------------------------------------------------------------------
+// For a cotangent w on the channel data and an SoS direction v, the derivative along v of
+// G = (dM/dC)^T w (Eq. 6 for w = 2 (M - M_obs)) follows from differentiating the discrete adjoint
+// once more. With dkappa' = 2 kappa' v / C:
+//   dU^{n+1} = Eq. 2 on dU + dkappa' Lap(U^n)                         (Born field)
+//   mu^m     = Eq. 2 on mu + kappa' w^m at the receivers              (adjoint, mu = kappa' lambda)
+//   dmu^m    = Eq. 2 on dmu + dkappa' Lap(mu^{m+1}) + dkappa' w^m     (derivative of mu along v)
+//   dG = (2/C) sum_m [dmu^m Lap(U^{m-1}) + mu^m Lap(dU^{m-1})] - (2 v / C^2) sum_m mu^m Lap(U^{m-1})
+// so_step_kernel advances one of the three fields by one step with the extra terms of its kind
+// (SoKind). It is the one-step kernel's tile scheme (64 x 32 tiles, 128 threads, 4 x 4 outputs
+// per thread, one mbarrier for all TMA loads) with more operand tiles and no early loads.
+template <int KIND>
+struct SoLayout {
+    static constexpr int kBox = kBoxX * (32 + 2 * kHalo);
+    static constexpr int kTile = kTileX * 32;
+    // prev, kappa' + (Born: Lap(U^n), dkappa'; adjoint: two histories, two sums;
+    // Born-adjoint: history, Lap(mu^{m+1}), dkappa', sum)
+    static constexpr int kTiles = KIND == kSoBorn ? 4 : 6;
+    static constexpr uint32_t kBytes = (kBox + kTiles * kTile) * sizeof(float);
+};
+
+template <int R, int KIND>
+__global__ void __launch_bounds__(128, 3)
+so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoParams q)
+{
+    using SL = SoLayout<KIND>;
+    constexpr int TZ = 32;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ InjList inj;
+
+    const int tid = threadIdx.x;
+    const int s = blockIdx.z;
+    const int map = s / p.n_tx;
+    const int x0 = blockIdx.x * kTileX;
+    const int z0 = blockIdx.y * TZ;
+    const int tx_idx = s % p.n_tx;
+    const long long shot_off = static_cast<long long>(s) * p.slice;
+    float *box = smem;
+    float *pv = box + SL::kBox;
+    float *kp = pv + SL::kTile;
+    float *t0 = kp + SL::kTile;
+    float *t1 = t0 + SL::kTile;
+    float *t2 = t1 + SL::kTile;
+    float *t3 = t2 + SL::kTile;
+    const MapGrid mg = map_grid(p, map);
+
+    if (tid == 0) {
+        prefetch_tensormap(&tm.cur_box);
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, SL::kBytes);
+    }
+    grid_dependency_wait();
+    if (tid == 0) {
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - kHalo, z0 - kHalo, s);
+        tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+        tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+        tma_load_4d(t0, &tm.h1, &bar, x0, z0, s, q.h1_slot);
+        if (KIND == kSoBorn) {
+            tma_load_3d(t1, &tm.dk, &bar, x0, z0, map);
+        } else if (KIND == kSoAdj) {
+            tma_load_4d(t1, &tm.h2, &bar, x0, z0, s, q.h2_slot);
+            tma_load_3d(t2, &tm.g1, &bar, x0, z0, s);
+            tma_load_3d(t3, &tm.g2, &bar, x0, z0, s);
+        } else {
+            tma_load_3d(t1, &tm.src, &bar, x0, z0, s);
+            tma_load_3d(t2, &tm.dk, &bar, x0, z0, map);
+            tma_load_3d(t3, &tm.g1, &bar, x0, z0, s);
+        }
+    }
+    grid_dependents_launch();
+
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    const int2 rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
+    if (KIND == kSoBorn) {   // the Born field has no point source of its own
+        if (tid == 0) inj.n = 0;
+    } else {                 // kappa' w (adjoint) or dkappa' w (Born-adjoint) at the receivers
+        gather_injections<kAdjoint>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ,
+                                    kTileX, tid, 128);
+    }
+
+    const int lx = (tid & 15) * 4;
+    const int gx = x0 + lx;
+    const int lz = (tid >> 4) * 4;
+    const bool interior = region_interior(p, mg, x0, z0, kTileX, TZ);
+    int xd[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xd[i] = layer_depth(gx + i, p.P, mg.Nx);
+
+    if (!wait_tile(&bar, p, tid)) return;
+
+    float4 lap[4], ctr[4], nxt[4];
+    lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int lo = (lz + j) * kTileX + lx;
+        nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
+                         p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+        if (KIND == kSoBorn) nxt[j] = fma4(ld4s(t1 + lo), ld4s(t0 + lo), nxt[j]);      // + dkappa' Lap(U^n)
+        if (KIND == kSoBornAdj) nxt[j] = fma4(ld4s(t2 + lo), ld4s(t1 + lo), nxt[j]);   // + dkappa' Lap(mu^{m+1})
+    }
+    if (KIND != kSoBorn && inj.n > 0) {   // block-uniform: stage the rows, inject, reload
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
+        __syncthreads();
+        if (tid == 0)
+            apply_injections<kAdjoint>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX,
+                                       TZ, kTileX);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+    }
+    const bool col_ok = gx < mg.nxp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gz = z0 + lz + j;
+        if (!col_ok || gz >= mg.nzp) continue;
+        float4 nv = nxt[j], lv = lap[j];
+        if (gx + 4 > mg.nxp) {   // lanes past the last column stay zero
+            if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
+            if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
+            nv.w = 0.f; lv.w = 0.f;
+        }
+        const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+        const int lo = (lz + j) * kTileX + lx;
+        st4(p.out + o, nv);
+        if (KIND == kSoBorn || KIND == kSoAdj) st4(q.lap_out + o, lv);
+        if (KIND == kSoAdj) {
+            st4(q.sum1 + o, fma4(nv, ld4s(t0 + lo), ld4s(t2 + lo)));
+            st4(q.sum2 + o, fma4(nv, ld4s(t1 + lo), ld4s(t3 + lo)));
+        }
+        if (KIND == kSoBornAdj) st4(q.sum1 + o, fma4(nv, ld4s(t0 + lo), ld4s(t3 + lo)));
+    }
+
+    // Born traces: dU^n at the receivers, from the box (each receiver lies in exactly one tile)
+    if (KIND == kSoBorn && p.cd) {
+        const int cnt = (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
+        for (int e = tid; e < cnt; e += 128) {
+            const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
+            const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.smp_node + tx_idx * p.n_rx + r) : -1;
+            const int zn = node >> 16, xn = node & 0xffff;
+            if (node < 0 || zn < z0 || zn >= z0 + TZ || xn < x0 || xn >= x0 + kTileX) {
+                raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                continue;
+            }
+            p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
+                box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
+        }
+    }
+}
+
+// a += b - (v / C) g per padded cell of every shot (v, C edge-replicated), before the fold.
+__global__ void so_combine_kernel(float *a, const float *b, const float *g, const float *sos, const float *dsos,
+                                  int n_tx, int Nx, int Nz, int P, int pitch, long long slice)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = blockIdx.y;
+    const int s = blockIdx.z;
+    if (x >= pitch) return;
+    const int map = s / n_tx;
+    const int xs = min(max(x - P, 0), Nx - 1), zs = min(max(z - P, 0), Nz - 1);
+    const long long src = (static_cast<long long>(map) * Nz + zs) * Nx + xs;
+    const float r = dsos[src] / sos[src];
+    const long long o = static_cast<long long>(s) * slice + static_cast<long long>(z) * pitch + x;
+    a[o] = (a[o] + b[o]) - r * g[o];
+}
+
 // ---- variable density (Eq. 1 with rho(x, z)) ---------------------------------------------------
 // The density term rho div(b grad u), b = 1/rho, on a staggered grid. Fluxes at half points,
 //   f_x(j + 1/2) = b_x(j) sum_k s_k (u(j + k) - u(j - k + 1)),
@@ -2140,6 +2308,66 @@ cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepP
     case 4: return launch_step_vd_r<4>(mode, tm, p, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+template <int R, int KIND>
+static cudaError_t launch_so_step_rk(const SoMaps &tm, const StepParams &p, const SoParams &q, cudaStream_t st)
+{
+    using SL = SoLayout<KIND>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(so_step_kernel<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SL::kBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(so_step_kernel<R, KIND>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + 31) / 32, p.n_maps * p.n_tx);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = SL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, so_step_kernel<R, KIND>, tm, p, q);
+}
+
+template <int R>
+static cudaError_t launch_so_step_r(int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,
+                                    cudaStream_t st)
+{
+    switch (kind) {
+    case kSoBorn: return launch_so_step_rk<R, kSoBorn>(tm, p, q, st);
+    case kSoAdj: return launch_so_step_rk<R, kSoAdj>(tm, p, q, st);
+    case kSoBornAdj: return launch_so_step_rk<R, kSoBornAdj>(tm, p, q, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_so_step(int radius, int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,
+                           cudaStream_t st)
+{
+    if (p.tile_z != 32 || p.map_dims) return cudaErrorInvalidValue;
+    switch (radius) {
+    case 1: return launch_so_step_r<1>(kind, tm, p, q, st);
+    case 2: return launch_so_step_r<2>(kind, tm, p, q, st);
+    case 3: return launch_so_step_r<3>(kind, tm, p, q, st);
+    case 4: return launch_so_step_r<4>(kind, tm, p, q, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_so_combine(float *a, const float *b, const float *g, const float *sos, const float *dsos, int S,
+                              int n_tx, int Nx, int Nz, int P, int nzp, int pitch, long long slice, cudaStream_t st)
+{
+    so_combine_kernel<<<dim3((pitch + 127) / 128, nzp, S), 128, 0, st>>>(a, b, g, sos, dsos, n_tx, Nx, Nz, P, pitch,
+                                                                          slice);
+    return cudaGetLastError();
 }
 
 // <one-step kernel source>

@@ -94,6 +94,8 @@ def _load():
     lib.dufwi_jvp_workspace_size.argtypes = [P, S, ctypes.c_int32, ctypes.POINTER(sz)]
     lib.dufwi_jvp.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, sz, vp]
     lib.dufwi_backward.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, sz, vp]
+    lib.dufwi_second_order_workspace_size.argtypes = [P, S, ctypes.c_int32, ctypes.POINTER(sz)]
+    lib.dufwi_second_order.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.dufwi_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
     lib.dufwi_get_option.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     return lib
@@ -450,6 +452,55 @@ def jvp(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geomet
     if check:
         _check(workspace_status(workspace, stream), "dufwi_jvp (device)")
     return (dcd, cd) if return_cd else dcd
+
+
+def second_order_workspace_size(problem: Problem, geom: Geometry, n_maps: int) -> int:
+    pb = problem.c_struct()
+    _, sh = geom.c_structs()
+    out = ctypes.c_size_t(0)
+    _check(_lib.dufwi_second_order_workspace_size(ctypes.byref(pb), ctypes.byref(sh), int(n_maps),
+                                                  ctypes.byref(out)), "second_order_workspace_size")
+    return int(out.value)
+
+
+def second_order(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, cd_grad: torch.Tensor,
+                 dsos: torch.Tensor, *, so: torch.Tensor | None = None, dcd: torch.Tensor | None = None,
+                 grad: torch.Tensor | None = None, return_grad: bool = False, workspace: torch.Tensor | None = None,
+                 stream=None, check: bool = False):
+    """Second-order product ``so = d/dC[(dM/dC)^T cd_grad] . dsos`` and the Born data
+    ``dcd = (dM/dC) dsos`` (``dufwi_second_order``); with ``return_grad`` also
+    ``grad = (dM/dC)^T cd_grad``. Returns ``(so, dcd)`` or ``(so, dcd, grad)``.
+
+    With ``cd_grad = 2 (M - M_obs)`` the exact Hessian-vector product of the misfit is
+    ``so + 2 (dM/dC)^T dcd``."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, None)
+    _dev_tensor(cd_grad, "cd_grad", torch.float32, cshape)
+    _dev_tensor(dsos, "dsos", torch.float32, sos.shape)
+    if so is None:
+        so = torch.empty_like(sos)
+    _dev_tensor(so, "so", torch.float32, sos.shape)
+    if dcd is None:
+        dcd = torch.empty(cshape, dtype=torch.float32, device=sos.device)
+    _dev_tensor(dcd, "dcd", torch.float32, cshape)
+    if return_grad and grad is None:
+        grad = torch.empty_like(sos)
+    if grad is not None:
+        _dev_tensor(grad, "grad", torch.float32, sos.shape)
+    need = second_order_workspace_size(problem, geom, n_maps)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=sos.device)
+    elif workspace.numel() * workspace.element_size() < need:
+        raise DufwiError(ERR_WORKSPACE, "second_order workspace")
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_second_order(ctypes.byref(pb), sos.data_ptr(), None, ctypes.byref(arr), wavelet.data_ptr(),
+                                 ctypes.byref(sh), n_maps, cd_grad.data_ptr(), dsos.data_ptr(), dcd.data_ptr(),
+                                 so.data_ptr(), grad.data_ptr() if grad is not None else None, workspace.data_ptr(),
+                                 workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "dufwi_second_order")
+    if check:
+        _check(workspace_status(workspace, stream), "dufwi_second_order (device)")
+    return (so, dcd, grad) if return_grad else (so, dcd)
 
 
 def workspace_status(workspace: torch.Tensor, stream=None) -> int:

@@ -151,3 +151,25 @@ def test_boundary_and_option_validation():
         d.set_option(opt, good)
         assert d.get_option(opt) == good
         d.set_option(opt, before)
+
+
+def test_second_order_workspace_sizing_and_validation():
+    """The second-order call keeps two histories: every step with ckpt_interval 0, one segment
+    of each plus four FP32 snapshots per segment otherwise; the staggered operators have no
+    Born step."""
+    d = _lib_module()
+    g = _geom(d)
+    pb_all = _problem(d, nt=200)
+    pb_ck = _problem(d, nt=200, ckpt_interval=20)
+    n_all = d.second_order_workspace_size(pb_all, g, 1)
+    n_ck = d.second_order_workspace_size(pb_ck, g, 1)
+    field = 4 * 2 * (48 + 40) * ((64 + 40 + 7) // 8 * 8)          # S x nzp x pitch floats
+    assert n_all >= 2 * 199 * field                                  # Lap(U^n), Lap(dU^n) for every step
+    assert 2 * 20 * field + 10 * 4 * field <= n_ck < n_all
+    assert d.second_order_workspace_size(pb_all, g, 3) > n_all
+    with pytest.raises(d.DufwiError) as e:
+        d.second_order_workspace_size(_problem(d, boundary="cpml"), g, 1)
+    assert e.value.status == d.ERR_UNSUPPORTED
+    with pytest.raises(d.DufwiError) as e:
+        d.second_order_workspace_size(_problem(d, nt=0), g, 1)
+    assert e.value.status == d.ERR_INVALID_ARG

@@ -1,0 +1,192 @@
+"""Second-order products on the GPU (``dufwi_second_order`` and the autograd double backward)
+against central differences of the FP64 oracle's first-order products, which the oracle pins
+pin in turn (finite-difference gradients, adjoint dot-product test)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_04070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-4
+SO_TOL = 1e-3     # FP32 second-order sums against an FP64 central difference (h = 0.05 m/s)
+
+
+@pytest.fixture(scope="module")
+def d():
+    from paper_2603_04070_gb300 import build_lib
+    build_lib.build()
+    from paper_2603_04070_gb300 import dufwi
+    return dufwi
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _oracle_problem(wl):
+    return oracle.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml, pml_R=wl.pml_R,
+                          pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+
+
+def _traces(wl, C):
+    p = _oracle_problem(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return np.stack([oracle.forward(p, np.asarray(C, np.float64), (tix[k], tiz[k]), wl.wavelet.astype(np.float64),
+                                    rix[k], riz[k]) for k in range(wl.n_tx)])
+
+
+def _grad(wl, C, M_obs):
+    p = _oracle_problem(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return oracle.misfit_gradient(p, np.asarray(C, np.float64), tix, tiz, wl.wavelet.astype(np.float64), rix, riz,
+                                  np.asarray(M_obs, np.float64))[1]
+
+
+def _vjp(wl, C, w):
+    """(dM/dC)^T w of one map: the oracle misfit gradient with M_obs = M(C) - w/2."""
+    return _grad(wl, C, _traces(wl, C) - 0.5 * w)
+
+
+def _case(seed, nx=56, nz=50, nt=300, n_tx=2, order=8):
+    wl = inputs.make_workload("full_shot_set", seed=seed, nx=nx, nz=nz, nt=nt, n_elem=14, n_tx=n_tx,
+                              fd_order=order)
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(wl.sos_start.shape) * 5.0
+    return wl, v
+
+
+def _problem(d, wl, **kw):
+    return d.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
+                     pml_cref=wl.pml_cref, fd_order=wl.fd_order, c_max=wl.c_max, **kw)
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("ckpt,order", [(0, 8), (37, 8), (0, 4)])
+def test_second_order_matches_oracle_differences(d, ckpt, order):
+    """so = d/dC[(dM/dC)^T w] . v for the residual cotangent w = 2 (M(C) - M_obs), against the
+    central difference of the oracle's (dM/dC)^T w along v with w held fixed; the returned
+    first-order products against the oracle too."""
+    wl, v = _case(40 + order, order=order)
+    C = wl.sos_start[0].astype(np.float64)
+    M_obs = _traces(wl, wl.sos_true[0])
+    w = 2.0 * (_traces(wl, C) - M_obs)
+    h = 0.05
+    ref = (_vjp(wl, C + h * v[0], w) - _vjp(wl, C - h * v[0], w)) / (2 * h)
+    pb = _problem(d, wl, ckpt_interval=ckpt)
+    geom = d.Geometry.from_workload(wl)
+    so, dcd, g = d.second_order(pb, _cuda(wl.sos_start), _cuda(wl.wavelet), geom, _cuda(w[None]), _cuda(v),
+                                return_grad=True, check=True)
+    torch.cuda.synchronize()
+    assert rel_l2(so.cpu().numpy()[0], ref) <= SO_TOL
+    assert rel_l2(g.cpu().numpy()[0], _vjp(wl, C, w)) <= GRAD_TOL
+    jv_ref = (_traces(wl, C + h * v[0]) - _traces(wl, C - h * v[0])) / (2 * h)
+    assert rel_l2(dcd.cpu().numpy()[0], jv_ref) <= 1e-4
+
+
+def test_second_order_first_order_outputs_agree_with_jvp_and_backward(d):
+    """The Born data and the vector-Jacobian product returned by the second-order call are the
+    ones of dufwi_jvp and dufwi_backward (same tile arithmetic, to FP32 rounding), on two maps."""
+    wl = inputs.make_workload("linear_disk", seed=9, nx=70, nz=54, nt=240, n_elem=16, n_tx=2, n_maps=2)
+    rng = np.random.default_rng(9)
+    v = _cuda(rng.standard_normal(wl.sos_true.shape) * 4.0)
+    w = _cuda(rng.standard_normal((2, wl.n_tx, wl.nt, wl.n_rx)) * 1e-9)
+    pb = _problem(d, wl, ckpt_interval=50)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav = _cuda(wl.sos_true), _cuda(wl.wavelet)
+    so, dcd, g = d.second_order(pb, sos, wav, geom, w, v, return_grad=True, check=True)
+    jv = d.jvp(pb, sos, wav, geom, v)
+    _, ws = d.forward_save(pb, sos, wav, geom)
+    g1 = d.backward(pb, sos, wav, geom, w, ws)
+    torch.cuda.synchronize()
+    assert rel_l2(dcd.cpu().numpy(), jv.cpu().numpy()) <= 1e-6
+    assert rel_l2(g.cpu().numpy(), g1.cpu().numpy()) <= 1e-6
+    assert float(so.abs().max()) > 0
+
+
+def test_second_order_checkpointed_is_bit_identical_to_store_all(d):
+    """Recomputing each segment's two histories from FP32 snapshots reproduces them exactly."""
+    wl, v = _case(50, nt=260)
+    rng = np.random.default_rng(50)
+    w = _cuda(rng.standard_normal((1, wl.n_tx, wl.nt, wl.n_rx)) * 1e-9)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav, vv = _cuda(wl.sos_start), _cuda(wl.wavelet), _cuda(v)
+    out = []
+    for ckpt in (0, 25, 100):
+        so, dcd, g = d.second_order(_problem(d, wl, ckpt_interval=ckpt), sos, wav, geom, w, vv, return_grad=True,
+                                    check=True)
+        torch.cuda.synchronize()
+        out.append((so.cpu(), dcd.cpu(), g.cpu()))
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert torch.equal(a, b)
+
+
+def test_exact_hvp_by_double_backward_matches_oracle(d):
+    """H v of the misfit at a nonzero residual (start map against data of the true map), through
+    torch.autograd.grad twice, against the central difference of the oracle gradient with M_obs
+    held fixed. The Gauss-Newton product alone misses the residual term by far more than the
+    tolerance."""
+    from paper_2603_04070_gb300 import autograd
+    wl, v = _case(60)
+    C = wl.sos_start[0].astype(np.float64)
+    M_obs = _traces(wl, wl.sos_true[0])
+    h = 0.05
+    ref = (_grad(wl, C + h * v[0], M_obs) - _grad(wl, C - h * v[0], M_obs)) / (2 * h)
+    pb = _problem(d, wl, ckpt_interval=40)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav, obs, vv = _cuda(wl.sos_start), _cuda(wl.wavelet), _cuda(M_obs[None]), _cuda(v)
+    Hv = autograd.hvp(pb, sos, wav, geom, obs, vv)
+    gn = autograd.hvp_gauss_newton(pb, sos, wav, geom, vv)
+    torch.cuda.synchronize()
+    assert rel_l2(Hv.cpu().numpy()[0], ref) <= SO_TOL
+    assert rel_l2(gn.cpu().numpy()[0], ref) > 10 * SO_TOL
+
+
+def test_exact_hvp_is_symmetric(d):
+    """<u, H v> = <v, H u> for the exact Hessian (two maps, each its own product)."""
+    from paper_2603_04070_gb300 import autograd
+    wl = inputs.make_workload("linear_disk", seed=61, nx=60, nz=52, nt=280, n_elem=14, n_tx=2, n_maps=2)
+    rng = np.random.default_rng(61)
+    u = _cuda(rng.standard_normal(wl.sos_true.shape) * 5.0)
+    v = _cuda(rng.standard_normal(wl.sos_true.shape) * 5.0)
+    pb = _problem(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav = _cuda(wl.sos_start), _cuda(wl.wavelet)
+    obs = d.simulate(pb, _cuda(wl.sos_true), wav, geom)
+    Hv = autograd.hvp(pb, sos, wav, geom, obs, v).double()
+    Hu = autograd.hvp(pb, sos, wav, geom, obs, u).double()
+    a = (u.double() * Hv).flatten(1).sum(1)
+    b = (v.double() * Hu).flatten(1).sum(1)
+    assert torch.all((a - b).abs() <= 1e-4 * torch.maximum(a.abs(), b.abs()))
+
+
+def test_second_order_rejects_density_and_third_derivatives(d):
+    from paper_2603_04070_gb300 import autograd
+    wl, v = _case(62, nt=120)
+    pb = _problem(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav = _cuda(wl.sos_start), _cuda(wl.wavelet)
+    w = torch.zeros((1, wl.n_tx, wl.nt, wl.n_rx), device="cuda")
+    import ctypes
+    arr, sh = geom.c_structs()
+    so = torch.empty_like(sos)
+    ws = torch.empty(d.second_order_workspace_size(pb, geom, 1), dtype=torch.uint8, device="cuda")
+    rc = d._lib.dufwi_second_order(ctypes.byref(pb.c_struct()), sos.data_ptr(), sos.data_ptr(), ctypes.byref(arr),
+                                   wav.data_ptr(), ctypes.byref(sh), 1, w.data_ptr(), _cuda(v).data_ptr(), None,
+                                   so.data_ptr(), None, ws.data_ptr(), ws.numel(), None)
+    assert rc == d.ERR_UNSUPPORTED                      # a density map: no Born step on the staggered operator
+    c = sos.clone().requires_grad_(True)
+    J = autograd.misfit(pb, c, wav, geom, d.simulate(pb, _cuda(wl.sos_true), wav, geom)).sum()
+    (g,) = torch.autograd.grad(J, c, create_graph=True)
+    with pytest.raises(RuntimeError, match="third derivatives"):
+        torch.autograd.grad(g, c, grad_outputs=_cuda(v), create_graph=True)

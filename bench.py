@@ -663,6 +663,13 @@ def run_hvp(args):
         fwd()
         dufwi.backward(pb, sos, wav, geom, 2.0 * dcd_s, ws_g, grad=g)
 
+    hv = torch.empty_like(sos)
+    mis = torch.empty(1, dtype=torch.float64, device=dev)
+    g2 = torch.empty_like(sos)
+
+    def fused_hvp():       # dufwi_hvp: H v, the misfit and its gradient from one set of sweeps
+        dufwi.hvp(pb, sos, wav, geom, obs, v, hv=hv, misfit=mis, grad=g2, workspace=ws_s)
+
     def jvp():
         dufwi.jvp(pb, sos, wav, geom, v, dcd=dcd, workspace=ws_j)
 
@@ -690,19 +697,21 @@ def run_hvp(args):
     ms_hvp = timed(lambda: (fwd(), jvp(), vjp()))
     ms_second = timed(second, reps=2)
     ms_exact = timed(exact_hvp, reps=2)
+    ms_fused = timed(fused_hvp, reps=2)
     cells = (wl.nx + 2 * wl.pml) * (wl.nz + 2 * wl.pml) * wl.n_tx * wl.nt
     line = {"metric": "ms per Gauss-Newton Hessian-vector product", "value": ms_hvp, "unit": "ms", "n_gpus": 1,
             "steps": 3, "warmup": max(args.warmup, 1), "higher_is_better": False, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "full_shot_set: 512x512 (+20), 16 transmits x 128 receivers, "
                                                         "%d steps, checkpoint interval %d" % (wl.nt, args.ckpt)},
             "ms_jvp": ms_jvp, "ms_forward_save": ms_fwd, "ms_vjp": ms_vjp,
-            "ms_second_order": ms_second, "ms_exact_hvp": ms_exact,
+            "ms_second_order": ms_second, "ms_exact_hvp": ms_exact, "ms_fused_hvp_with_gradient": ms_fused,
             "second_order_workspace_gb": ws_s.numel() / 1e9,
             "jvp_gcell_updates_per_s": 2.0 * cells / (ms_jvp / 1e3) / 1e9,
             "note": "JVP: background + Born step per time step (2 cell updates per cell and step); VJP: recompute "
                     "+ adjoint sweeps from the snapshots of forward_save; second order: background + Born "
                     "forward with snapshots of both, per segment their recompute, then adjoint + "
-                    "differentiated adjoint; exact HVP = second order + forward_save + VJP of 2 J v"}
+                    "differentiated adjoint; exact HVP = second order + forward_save + VJP of 2 J v; fused: dufwi_hvp "
+                    "(the adjoint of 2 J v carried by the differentiated adjoint; misfit and gradient included)"}
     print(json.dumps(line), flush=True)
 
 

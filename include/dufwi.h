@@ -238,6 +238,24 @@ int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *d
                        float *grad, void *workspace, size_t workspace_bytes,
                        void *stream /* cudaStream_t */);
 
+/* Exact Hessian-vector product of the misfit J = sum (M - M_obs)^2 (Eqs. 5-6) in one call:
+ *   hv[b] = H[b] dsos[b] = 2 J^T (J dsos) + d/dC[J^T w] . dsos,  w = 2 (M - M_obs), J = dM/dC,
+ * with the misfit and its gradient beside it. It runs the sweeps of dufwi_second_order with
+ * w known after the forward pass (the background traces are recorded). The adjoint of 2 J dsos
+ * satisfies the same recursion as dmu, so it is carried by dmu through its receiver source
+ * (dkappa'_r w + kappa'_r 2 (J dsos)) and shares dmu's imaging sum: no extra sweep.
+ *   cd_obs [n_maps][n_tx][nt][n_rx] float, device (NULL only when n_rx == 0)
+ *   dsos   [n_maps][nz][nx] float, device
+ *   hv     [n_maps][nz][nx] float, device, output
+ *   misfit NULL or [n_maps] double, device, output (as dufwi_misfit_gradient)
+ *   grad   NULL or [n_maps][nz][nx] float, device, output (the misfit gradient)
+ *   workspace: device, >= dufwi_second_order_workspace_size bytes.
+ * Same support as dufwi_second_order. */
+int dufwi_hvp(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+              const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_obs,
+              const float *dsos, float *hv, double *misfit, float *grad, void *workspace,
+              size_t workspace_bytes, void *stream /* cudaStream_t */);
+
 /* Forward model for callers that cannot allocate device memory. The paper has no counterpart:
  * this serves hosts that must not call cudaMalloc while running, such as a fixed-latency
  * acquisition loop (a device allocation can synchronise the device) or an application that hands

@@ -98,7 +98,7 @@ struct Layout {
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
     // second-order calls: adjoint and differentiated-adjoint rings, second and third histories,
     // two more imaging sums, the second adjoint source
-    size_t o_mu[4], o_dmu[4], o_hist2, o_hist3, o_acc1, o_acc2, o_asrc2;
+    size_t o_mu[4], o_dmu[4], o_hist2, o_hist3, o_acc1, o_acc2, o_asrc2, o_cd2;
 };
 
 // Last table contents uploaded to each workspace (see common_setup), and whether a call may
@@ -242,7 +242,9 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         L->o_dkap = take((size_t)n_maps * L->slice * sizeof(float));
         L->o_cd = take(cdb);                                             // Born traces when not requested
         L->o_asrc = take(cdb);                                           // kappa'_r w
-        L->o_asrc2 = take(cdb);                                          // dkappa'_r w
+        L->o_asrc2 = take(cdb);                                          // dkappa'_r w (+ kappa'_r 2 J v)
+        L->o_cd2 = take(cdb);                                            // background traces (HVP form)
+        L->o_part = take((size_t)L->S * sizeof(double));
         L->o_fold = take((size_t)n_maps * L->nzp * L->Nx * sizeof(double));
     }
     L->total = off;
@@ -1340,9 +1342,10 @@ int so_step(Ctx &c, Ring &r, int kind, StepParams p, const SoParams &q, long lon
 
 // Background and Born steps n = n0 .. n1-1, interleaved: the background step keeps Lap(U^n) in
 // slot n - h0 of the first history, then the Born step adds dkappa' times it and keeps Lap(dU^n)
-// in the same slot of the second. dcd: Born traces (dU^n at the receivers), or null.
-int so_forward_range(Ctx &c, Ring &fr, Ring &br, int n0, int n1, int h0, const float *wavelet, float *dcd,
-                     long long &nl)
+// in the same slot of the second. cd / dcd: background / Born traces (U^n, dU^n at the
+// receivers), or null.
+int so_forward_range(Ctx &c, Ring &fr, Ring &br, int n0, int n1, int h0, const float *wavelet, float *cd,
+                     float *dcd, long long &nl)
 {
     const Layout &L = c.L;
     const size_t hstride = (size_t)L.S * L.slice;
@@ -1350,13 +1353,16 @@ int so_forward_range(Ctx &c, Ring &fr, Ring &br, int n0, int n1, int h0, const f
     StepParams pf = c.base;
     pf.inj_node = c.at<int>(L.o_tx);
     pf.inj_val = wavelet;
+    pf.smp_node = c.at<int>(L.o_rx);
+    pf.cd = cd;
+    const int fmode = cd ? kFwdSampleHist : kFwdHist;
     StepParams pb = c.base;
     pb.smp_node = c.at<int>(L.o_rx);
     pb.cd = dcd;
     for (int n = n0; n < n1; ++n) {
         pf.step = n;
         pf.hist = h1 + (size_t)(n - h0) * hstride;
-        int rc = one_step(c, fr, kFwdHist, pf, nl);
+        int rc = one_step(c, fr, fmode, pf, nl);
         if (rc) return rc;
         pb.step = n;
         SoParams q;
@@ -1382,47 +1388,34 @@ Ring ring_of(Ctx &c, const size_t *offsets, const FieldMaps *maps)
 }  // namespace
 }  // namespace dufwi
 
-extern "C" {
+namespace dufwi {
+namespace {
 
-int dufwi_second_order_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int32_t n_maps,
-                                      size_t *bytes)
+// Shared body of dufwi_second_order (cd_obs null: the cotangent cd_grad is given) and dufwi_hvp
+// (cd_obs given: the cotangent is w = 2 (M - M_obs), known after the forward pass, and the
+// adjoint of 2 J v joins dmu through its receiver source). Outputs: so (the second-order term,
+// or H v for dufwi_hvp), dcd (J v, or null), grad ((dM/dC)^T w, or null), misfit (or null).
+int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float *dsos, const float *cd_grad,
+                     const float *cd_obs, double *misfit, float *dcd, float *so, float *grad)
 {
-    if (!bytes) return DUFWI_ERR_INVALID_ARG;
-    Layout L;
-    int rc = make_layout(pb, shots, n_maps, kLayoutSecond, &L);
-    if (rc) return rc;
-    *bytes = L.total;
-    return DUFWI_OK;
-}
-
-int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
-                       const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_grad,
-                       const float *dsos, float *dcd, float *so, float *grad, void *workspace,
-                       size_t workspace_bytes, void *stream)
-{
-    Ctx c;
-    c.pb = pb;
-    c.so = true;
-    int rc = make_layout(pb, shots, n_maps, kLayoutSecond, &c.L);
-    if (rc) return rc;
-    if (!dsos || !so || (!cd_grad && c.L.n_rx > 0)) return DUFWI_ERR_INVALID_ARG;
-    rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
-    if (rc) return rc;
-    NvtxRange range("dufwi second order");
+    NvtxRange range(cd_obs ? "dufwi hvp" : "dufwi second order");
     const Layout &L = c.L;
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
     const bool store_all = L.n_seg == 1;
+    const bool hvp = cd_obs != nullptr;
     long long nl = 0;
+    int rc = DUFWI_OK;
     int e0 = g_prof.mark(c.st);
     const float *kap = c.at<float>(L.o_kap);
+    const int *rx = c.at<int>(L.o_rx);
     float *dkap = c.at<float>(L.o_dkap);
     float *asrc = c.at<float>(L.o_asrc), *asrc2 = c.at<float>(L.o_asrc2);
     CKL(launch_setup_dkappa(sos, dsos, kap, dkap, L.n_maps, L.Nx, L.Nz, L.P, L.nzp, L.pitch, c.st));
-    if (L.n_rx > 0) {   // kappa'_r w drives mu, dkappa'_r w enters dmu
-        CKL(launch_cotangent_source(cd_grad, kap, c.at<int>(L.o_rx), asrc, c.status(), L.S, L.n_tx, L.n_rx, L.nt,
-                                    L.slice, L.pitch, c.st));
-        CKL(launch_cotangent_source(cd_grad, dkap, c.at<int>(L.o_rx), asrc2, c.status(), L.S, L.n_tx, L.n_rx, L.nt,
-                                    L.slice, L.pitch, c.st));
+    if (!hvp && L.n_rx > 0) {   // kappa'_r w drives mu, dkappa'_r w enters dmu
+        CKL(launch_cotangent_source(cd_grad, kap, rx, asrc, c.status(), L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch,
+                                    c.st));
+        CKL(launch_cotangent_source(cd_grad, dkap, rx, asrc2, c.status(), L.S, L.n_tx, L.n_rx, L.nt, L.slice,
+                                    L.pitch, c.st));
     }
     Ring fr = ring_of(c, L.o_f, c.fmap), br = ring_of(c, L.o_m, c.mmap);
     Ring ar = ring_of(c, L.o_mu, c.mumap), dr = ring_of(c, L.o_dmu, c.dmumap);
@@ -1443,6 +1436,7 @@ int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *d
     nl = 0;
     e0 = g_prof.mark(c.st);
     float *dcd_out = L.n_rx > 0 ? (dcd ? dcd : c.at<float>(L.o_cd)) : nullptr;
+    float *cd_bg = (hvp && L.n_rx > 0) ? c.at<float>(L.o_cd2) : nullptr;
     for (int sg = 0; sg < L.n_seg; ++sg) {
         const int t0 = store_all ? 0 : sg * L.K;
         const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
@@ -1453,13 +1447,28 @@ int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *d
             CK(cudaMemcpyAsync(snap + 2 * field, br.buf[br.cur], field, cudaMemcpyDeviceToDevice, c.st));
             CK(cudaMemcpyAsync(snap + 3 * field, br.buf[br.prv], field, cudaMemcpyDeviceToDevice, c.st));
         }
-        rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, dcd_out, nl);
+        rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, cd_bg, dcd_out, nl);
         if (rc) return rc;
     }
     if (dcd_out)
-        CKL(launch_sample(br.buf[br.cur], c.at<int>(L.o_rx), dcd_out, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt,
-                          L.nt - 1, c.st));
+        CKL(launch_sample(br.buf[br.cur], rx, dcd_out, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt, L.nt - 1, c.st));
+    if (cd_bg)
+        CKL(launch_sample(fr.buf[fr.cur], rx, cd_bg, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt, L.nt - 1, c.st));
     g_prof.span(0, e0, g_prof.mark(c.st), nl);
+    if (hvp) {   // residual, misfit, the adjoint source and dmu's source with kappa'_r 2 J v added
+        nl = 0;
+        e0 = g_prof.mark(c.st);
+        if (L.n_rx > 0) {
+            CKL(launch_residual(cd_bg, cd_obs, kap, rx, asrc, c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx,
+                                L.nt, L.slice, L.pitch, c.st));
+            CKL(launch_hvp_source(cd_bg, cd_obs, dcd_out, kap, dkap, rx, asrc2, L.S, L.n_tx, L.n_rx, L.nt, L.slice,
+                                  L.pitch, c.st));
+        } else {
+            CK(cudaMemsetAsync(c.at<double>(L.o_part), 0, sizeof(double) * L.S, c.st));
+        }
+        if (misfit) CKL(launch_misfit_sum(c.at<double>(L.o_part), misfit, L.n_maps, L.n_tx, c.st));
+        g_prof.span(3, e0, g_prof.mark(c.st), nl);
+    }
 
     // reverse: per segment, the two histories (recomputed from the snapshots when checkpointed),
     // then mu and dmu from step t1 down to t0 + 1, interleaved (dmu's step m reads Lap(mu^{m+1})
@@ -1478,14 +1487,14 @@ int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *d
             CK(cudaMemcpyAsync(fr.buf[1], snap + field, field, cudaMemcpyDeviceToDevice, c.st));
             CK(cudaMemcpyAsync(br.buf[0], snap + 2 * field, field, cudaMemcpyDeviceToDevice, c.st));
             CK(cudaMemcpyAsync(br.buf[1], snap + 3 * field, field, cudaMemcpyDeviceToDevice, c.st));
-            rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, nullptr, nl);
+            rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, nullptr, nullptr, nl);
             if (rc) return rc;
             g_prof.span(1, e0, g_prof.mark(c.st), nl);
         }
         nl = 0;
         e0 = g_prof.mark(c.st);
         StepParams pa = c.base;
-        pa.inj_node = c.at<int>(L.o_rx);
+        pa.inj_node = rx;
         pa.inj_val = asrc;
         StepParams pd = pa;
         pd.inj_val = asrc2;
@@ -1522,6 +1531,54 @@ int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *d
     }
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
     return DUFWI_OK;
+}
+
+}  // namespace
+}  // namespace dufwi
+
+extern "C" {
+
+int dufwi_second_order_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int32_t n_maps,
+                                      size_t *bytes)
+{
+    if (!bytes) return DUFWI_ERR_INVALID_ARG;
+    Layout L;
+    int rc = make_layout(pb, shots, n_maps, kLayoutSecond, &L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return DUFWI_OK;
+}
+
+int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+                       const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_grad,
+                       const float *dsos, float *dcd, float *so, float *grad, void *workspace,
+                       size_t workspace_bytes, void *stream)
+{
+    Ctx c;
+    c.pb = pb;
+    c.so = true;
+    int rc = make_layout(pb, shots, n_maps, kLayoutSecond, &c.L);
+    if (rc) return rc;
+    if (!dsos || !so || (!cd_grad && c.L.n_rx > 0)) return DUFWI_ERR_INVALID_ARG;
+    rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
+    if (rc) return rc;
+    return second_order_run(c, sos, wavelet, dsos, cd_grad, nullptr, nullptr, dcd, so, grad);
+}
+
+int dufwi_hvp(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
+              const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_obs, const float *dsos,
+              float *hv, double *misfit, float *grad, void *workspace, size_t workspace_bytes, void *stream)
+{
+    Ctx c;
+    c.pb = pb;
+    c.so = true;
+    int rc = make_layout(pb, shots, n_maps, kLayoutSecond, &c.L);
+    if (rc) return rc;
+    if (!dsos || !hv || (!cd_obs && c.L.n_rx > 0)) return DUFWI_ERR_INVALID_ARG;
+    rc = common_setup(c, sos, density, arr, wavelet, shots, workspace, workspace_bytes, stream, false);
+    if (rc) return rc;
+    static const float kNoObs = 0.f;   // n_rx == 0: no residual; a non-null marker selects the HVP form
+    return second_order_run(c, sos, wavelet, dsos, nullptr, cd_obs ? cd_obs : &kNoObs, misfit, nullptr, hv, grad);
 }
 
 }  // extern "C"

@@ -187,6 +187,10 @@ cudaError_t launch_so_step(int radius, int kind, const SoMaps &tm, const StepPar
 // and C edge-replicated into the absorbing layer.
 cudaError_t launch_so_combine(float *a, const float *b, const float *g, const float *sos, const float *dsos, int S,
                               int n_tx, int Nx, int Nz, int P, int nzp, int pitch, long long slice, cudaStream_t st);
+// Exact misfit HVP: dmu's receiver source dkappa'_r 2 (M - M_obs) + kappa'_r 2 (J v).
+cudaError_t launch_hvp_source(const float *cd_sim, const float *cd_obs, const float *dcd, const float *kap,
+                              const float *dkap, const int *rx_node, float *asrc2, int S, int n_tx, int n_rx, int nt,
+                              long long slice, int pitch, cudaStream_t st);
 // kappa' on the padded grid; with a density map kappa' = rho C^2 dt^2/(dx^2 (1 + D dt)), and the
 // buoyancies bx, bz are written too (both may be null without a density map).
 // unit_b: no density map, but buoyancies of 1 between nodes are written (staggered operator

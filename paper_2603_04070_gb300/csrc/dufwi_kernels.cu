@@ -647,6 +647,27 @@ so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoPa
     }
 }
 
+// Receiver source of the differentiated adjoint for the exact Hessian-vector product of the
+// misfit: dkappa'_r w + kappa'_r 2 (J v) with w = 2 (M - M_obs). The adjoint of 2 J v obeys the
+// same recursion as dmu, so it rides on dmu's source and the two share one imaging sum.
+__global__ void hvp_source_kernel(const float *cd_sim, const float *cd_obs, const float *dcd, const float *kap,
+                                  const float *dkap, const int *rx_node, float *asrc2, int n_tx, int n_rx, int nt,
+                                  long long slice, int pitch)
+{
+    const int s = blockIdx.y;
+    const int tx_idx = s % n_tx, map = s / n_tx;
+    const long long base = static_cast<long long>(s) * nt * n_rx;
+    const long long n = static_cast<long long>(nt) * n_rx;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(i % n_rx);
+        const int node = rx_node[tx_idx * n_rx + r];
+        const long long o = map * slice + static_cast<long long>(node >> 16) * pitch + (node & 0xffff);
+        const float w = 2.0f * (cd_sim[base + i] - cd_obs[base + i]);
+        asrc2[base + i] = dkap[o] * w + kap[o] * (2.0f * dcd[base + i]);
+    }
+}
+
 // a += b - (v / C) g per padded cell of every shot (v, C edge-replicated), before the fold.
 __global__ void so_combine_kernel(float *a, const float *b, const float *g, const float *sos, const float *dsos,
                                   int n_tx, int Nx, int Nz, int P, int pitch, long long slice)
@@ -2360,6 +2381,18 @@ cudaError_t launch_so_step(int radius, int kind, const SoMaps &tm, const StepPar
     case 4: return launch_so_step_r<4>(kind, tm, p, q, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_hvp_source(const float *cd_sim, const float *cd_obs, const float *dcd, const float *kap,
+                              const float *dkap, const int *rx_node, float *asrc2, int S, int n_tx, int n_rx, int nt,
+                              long long slice, int pitch, cudaStream_t st)
+{
+    if (n_rx == 0) return cudaSuccess;
+    const long long n = static_cast<long long>(nt) * n_rx;
+    dim3 grid(static_cast<unsigned>(std::min<long long>((n + 255) / 256, 64)), S);
+    hvp_source_kernel<<<grid, 256, 0, st>>>(cd_sim, cd_obs, dcd, kap, dkap, rx_node, asrc2, n_tx, n_rx, nt, slice,
+                                            pitch);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_so_combine(float *a, const float *b, const float *g, const float *sos, const float *dsos, int S,

@@ -96,6 +96,7 @@ def _load():
     lib.dufwi_backward.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, sz, vp]
     lib.dufwi_second_order_workspace_size.argtypes = [P, S, ctypes.c_int32, ctypes.POINTER(sz)]
     lib.dufwi_second_order.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.dufwi_hvp.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.dufwi_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
     lib.dufwi_get_option.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     return lib
@@ -501,6 +502,46 @@ def second_order(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geo
     if check:
         _check(workspace_status(workspace, stream), "dufwi_second_order (device)")
     return (so, dcd, grad) if return_grad else (so, dcd)
+
+
+def hvp(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, cd_obs: torch.Tensor,
+        dsos: torch.Tensor, *, hv: torch.Tensor | None = None, misfit: torch.Tensor | None = None,
+        grad: torch.Tensor | None = None, return_all: bool = False, workspace: torch.Tensor | None = None,
+        stream=None, check: bool = False):
+    """Exact Hessian-vector product ``H dsos`` of the misfit J = sum (M - M_obs)^2 per map
+    (``dufwi_hvp``), one call. With ``return_all`` returns ``(hv, misfit [n_maps] float64,
+    grad)``: the misfit and its gradient come from the same sweeps."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, None)
+    _dev_tensor(cd_obs, "cd_obs", torch.float32, cshape)
+    _dev_tensor(dsos, "dsos", torch.float32, sos.shape)
+    if hv is None:
+        hv = torch.empty_like(sos)
+    _dev_tensor(hv, "hv", torch.float32, sos.shape)
+    if return_all:
+        if misfit is None:
+            misfit = torch.empty(n_maps, dtype=torch.float64, device=sos.device)
+        if grad is None:
+            grad = torch.empty_like(sos)
+    if misfit is not None:
+        _dev_tensor(misfit, "misfit", torch.float64, (n_maps,))
+    if grad is not None:
+        _dev_tensor(grad, "grad", torch.float32, sos.shape)
+    need = second_order_workspace_size(problem, geom, n_maps)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=sos.device)
+    elif workspace.numel() * workspace.element_size() < need:
+        raise DufwiError(ERR_WORKSPACE, "hvp workspace")
+    pb = problem.c_struct()
+    arr, sh = geom.c_structs()
+    rc = _lib.dufwi_hvp(ctypes.byref(pb), sos.data_ptr(), None, ctypes.byref(arr), wavelet.data_ptr(),
+                        ctypes.byref(sh), n_maps, cd_obs.data_ptr(), dsos.data_ptr(), hv.data_ptr(),
+                        misfit.data_ptr() if misfit is not None else None,
+                        grad.data_ptr() if grad is not None else None, workspace.data_ptr(),
+                        workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "dufwi_hvp")
+    if check:
+        _check(workspace_status(workspace, stream), "dufwi_hvp (device)")
+    return (hv, misfit, grad) if return_all else hv
 
 
 def workspace_status(workspace: torch.Tensor, stream=None) -> int:

@@ -190,3 +190,27 @@ def test_second_order_rejects_density_and_third_derivatives(d):
     (g,) = torch.autograd.grad(J, c, create_graph=True)
     with pytest.raises(RuntimeError, match="third derivatives"):
         torch.autograd.grad(g, c, grad_outputs=_cuda(v), create_graph=True)
+
+
+@pytest.mark.parametrize("ckpt", [0, 40])
+def test_fused_hvp_matches_double_backward_and_oracle(d, ckpt):
+    """dufwi_hvp (the adjoint of 2 J v carried by dmu's receiver source) against the double
+    backward of the autograd wrapper (separate sweeps) and the oracle's central differences; its
+    misfit and gradient against dufwi_misfit_gradient."""
+    from paper_2603_04070_gb300 import autograd
+    wl, v = _case(63)
+    C = wl.sos_start[0].astype(np.float64)
+    M_obs = _traces(wl, wl.sos_true[0])
+    h = 0.05
+    ref = (_grad(wl, C + h * v[0], M_obs) - _grad(wl, C - h * v[0], M_obs)) / (2 * h)
+    pb = _problem(d, wl, ckpt_interval=ckpt)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav, obs, vv = _cuda(wl.sos_start), _cuda(wl.wavelet), _cuda(M_obs[None]), _cuda(v)
+    hv, J, g = d.hvp(pb, sos, wav, geom, obs, vv, return_all=True, check=True)
+    Hv2 = autograd.hvp(pb, sos, wav, geom, obs, vv)
+    J1, g1 = d.misfit_gradient(pb, sos, wav, geom, obs)
+    torch.cuda.synchronize()
+    assert rel_l2(hv.cpu().numpy()[0], ref) <= SO_TOL
+    assert rel_l2(hv.cpu().numpy(), Hv2.cpu().numpy()) <= 1e-5
+    assert torch.equal(J, J1)
+    assert rel_l2(g.cpu().numpy(), g1.cpu().numpy()) <= 1e-6

@@ -11,6 +11,11 @@ gamma_k < 0 for a descent step. Two ways to choose the step are provided:
   Optimization, Algorithm 7.4), with H_0 = (s^T y / y^T y) I. A unit step is tried first, then
   halved under the same Armijo test. The first iteration, with no pairs yet, is a steepest-descent
   step of ``alpha`` m/s. Pairs with s^T y <= 0 are skipped.
+* ``newton_cg``: truncated Newton. The direction approximately solves H_k d = -g_k by conjugate
+  gradients with exact Hessian-vector products (``dufwi_hvp``), stopped when the residual falls
+  below ``cg_tol`` |g_k| or at the first direction of non-positive curvature (Nocedal and
+  Wright, Algorithm 7.1; with no CG step taken the direction is -g_k, scaled to ``alpha`` m/s).
+  A unit step is tried first, then halved under the Armijo test.
 
 Each map of a batch is an independent problem: its own step sizes and curvature pairs. Maps are
 evaluated together in one library call per trial step. A line search needs misfits only, so
@@ -42,6 +47,7 @@ class FWIResult:
     evaluations: int = 0                                # misfit-only calls
     gradients: int = 0                                  # gradient calls
     seconds: list = field(default_factory=list)         # wall time per iteration (device synchronised)
+    cg_steps: list = field(default_factory=list)        # newton_cg: CG steps per map and iteration
 
 
 def cuda_evaluator(problem, wavelet, geom, cd_obs, *, workspace=None):
@@ -111,6 +117,85 @@ def steepest_descent(evaluate: Callable, sos0: torch.Tensor, iters: int, *, alph
         c, J_acc, step = _line_search(evaluate, c, J, g, d, a / gmax, c_lo, c_hi, max_halvings, res)
         res.steps.append((step * gmax).cpu())           # accepted alpha in m/s
         a = torch.where(step > 0, 2.0 * step * gmax, 0.25 * a)
+        J, g = evaluate(c, True)
+        res.gradients += 1
+        if sync and c.is_cuda:
+            torch.cuda.synchronize()
+        res.seconds.append(time.perf_counter() - t0)
+    res.misfits.append(J.detach().cpu().clone())
+    res.sos = c
+    return res
+
+
+def cuda_hessvec(problem, wavelet, geom, cd_obs, *, workspace=None):
+    """(sos, v) -> H v [B, nz, nx], the exact Hessian-vector product of the misfit (``dufwi_hvp``)."""
+    from . import dufwi
+    n_maps = cd_obs.shape[0]
+    if workspace is None:
+        nbytes = dufwi.second_order_workspace_size(problem, geom, n_maps)
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=cd_obs.device)
+
+    def hessvec(sos, v):
+        return dufwi.hvp(problem, sos, wavelet, geom, cd_obs, v.contiguous(), workspace=workspace)
+    return hessvec
+
+
+def cg_newton_direction(g: torch.Tensor, hessvec, sos: torch.Tensor, cg_iters: int, cg_tol: float):
+    """Per map, an approximate solution d of H d = -g by conjugate gradients (all maps advance
+    together: one Hessian-vector call per CG iteration, on directions scaled to unit max-norm).
+    Returns (d, cg steps taken per map). A map stops at |r| <= cg_tol |g| or at the first
+    direction p with p^T H p <= 0."""
+    B = g.shape[0]
+    gd = g.to(torch.float64)
+    d = torch.zeros_like(gd)
+    r = -gd.clone()                                   # residual of H d = -g at d = 0
+    p = r.clone()
+    rr = _dot(r, r)
+    stop = rr.sqrt() <= cg_tol * _dot(gd, gd).sqrt()
+    steps = torch.zeros(B, dtype=torch.int64, device=g.device)
+    for _ in range(cg_iters):
+        if bool(stop.all()):
+            break
+        # H p = |p|_inf H (p / |p|_inf): the product is linear, and a unit-scale direction keeps
+        # the FP32 sweeps far from underflow (p has the scale of the gradient, ~1e-17 here)
+        pm = p.abs().flatten(1).amax(1).clamp_min(1e-300)
+        Hp = hessvec(sos, (p / _per_map(pm, p)).to(sos.dtype)).to(torch.float64) * _per_map(pm, p)
+        pHp = _dot(p, Hp)
+        neg = ~stop & (pHp <= 0)
+        stop |= neg
+        act = ~stop
+        a = torch.where(act, rr / torch.where(pHp > 0, pHp, torch.ones_like(pHp)), torch.zeros_like(rr))
+        d = d + _per_map(a, d) * p
+        r = r - _per_map(a, r) * Hp
+        rr_new = _dot(r, r)
+        steps = steps + act.to(torch.int64)
+        stop |= act & (rr_new.sqrt() <= cg_tol * _dot(gd, gd).sqrt())
+        beta = torch.where(act, rr_new / torch.where(rr > 0, rr, torch.ones_like(rr)), torch.zeros_like(rr))
+        p = torch.where(_per_map(act, p).bool(), r + _per_map(beta, p) * p, p)
+        rr = torch.where(act, rr_new, rr)
+    return d, steps
+
+
+def newton_cg(evaluate: Callable, hessvec: Callable, sos0: torch.Tensor, iters: int, *, cg_iters: int = 10,
+              cg_tol: float = 0.1, alpha: float = 20.0, c_lo: float = 1300.0, c_hi: float = 3000.0,
+              max_halvings: int = 6, sync: bool = True) -> FWIResult:
+    """Eq. 7 with gamma_k g_k replaced by the truncated-Newton step t_k d_k, H_k d_k ~ -g_k."""
+    c = sos0.clone()
+    res = FWIResult(sos=c)
+    J, g = evaluate(c, True)
+    res.gradients += 1
+    for _ in range(iters):
+        t0 = time.perf_counter()
+        res.misfits.append(J.detach().cpu().clone())
+        d, steps = cg_newton_direction(g, hessvec, c, cg_iters, cg_tol)
+        res.cg_steps.append(steps.cpu())
+        scale = torch.ones(c.shape[0], dtype=torch.float64, device=c.device)
+        for b in range(c.shape[0]):
+            if int(steps[b]) == 0:             # no CG step: steepest descent of alpha m/s
+                d[b] = -g[b].to(torch.float64)
+                scale[b] = alpha / float(g[b].abs().max().clamp_min(1e-30))
+        c, _, step = _line_search(evaluate, c, J, g, d.to(c.dtype), scale, c_lo, c_hi, max_halvings, res)
+        res.steps.append(step.cpu())
         J, g = evaluate(c, True)
         res.gradients += 1
         if sync and c.is_cuda:

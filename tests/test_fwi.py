@@ -63,6 +63,47 @@ def _quadratic(n_maps=2, n=64, seed=0):
     return evaluate, cstar
 
 
+def _quadratic_hessvec(n_maps=2, n=64):
+    w = torch.from_numpy(np.logspace(0, 2, n).reshape(1, 8, n // 8).repeat(n_maps, 0))
+    return lambda c, v: (2.0 * w * v.to(torch.float64)).to(v.dtype)
+
+
+def test_cg_direction_solves_newton_system_exactly():
+    """CG on H = diag(2w) (64 distinct eigenvalues, condition number 100): with enough steps
+    d = -H^-1 g to rounding, and the residual test, not the step cap, ends it (finite-precision
+    CG needs somewhat more than the 64 steps of exact arithmetic)."""
+    rng = np.random.default_rng(3)
+    g = torch.from_numpy(rng.standard_normal((2, 8, 8)))
+    hv = _quadratic_hessvec()
+    d, steps = fwi.cg_newton_direction(g, hv, torch.zeros_like(g), 200, 1e-12)
+    w = torch.from_numpy(np.logspace(0, 2, 64).reshape(8, 8))
+    assert torch.allclose(d, -g / (2.0 * w), rtol=1e-8, atol=1e-12)
+    assert torch.all(steps < 200)
+
+
+def test_newton_cg_converges_in_one_step_on_quadratic():
+    evaluate, cstar = _quadratic()
+    c0 = torch.full(cstar.shape, 1500.0, dtype=torch.float64)
+    res = fwi.newton_cg(evaluate, _quadratic_hessvec(), c0, 2, cg_iters=100, cg_tol=1e-12, sync=False)
+    J = torch.stack(res.misfits)
+    assert torch.all(J[1] <= 1e-16 * J[0])
+    assert torch.allclose(res.sos, cstar, atol=1e-6)
+    assert torch.all(res.steps[0] == 1.0)                      # the unit Newton step is accepted
+
+
+def test_truncated_newton_is_monotone_and_handles_negative_curvature():
+    evaluate, cstar = _quadratic(seed=4)
+    c0 = torch.full(cstar.shape, 1500.0, dtype=torch.float64)
+    res = fwi.newton_cg(evaluate, _quadratic_hessvec(), c0, 8, cg_iters=3, cg_tol=1e-3, sync=False)
+    J = torch.stack(res.misfits)
+    assert torch.all(J[1:] <= J[:-1]) and J[-1].max() <= 1e-3 * J[0].min()
+    # a Hessian that reports negative curvature: no CG step, steepest descent of alpha m/s instead
+    bad = fwi.newton_cg(evaluate, lambda c, v: -v, c0, 3, cg_iters=5, sync=False)
+    assert all(int(s.max()) == 0 for s in bad.cg_steps)
+    Jb = torch.stack(bad.misfits)
+    assert torch.all(Jb[1:] < Jb[:-1])
+
+
 def test_lbfgs_converges_on_quadratic():
     evaluate, cstar = _quadratic()
     c0 = torch.full(cstar.shape, 1500.0, dtype=torch.float64)

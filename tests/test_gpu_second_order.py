@@ -214,3 +214,24 @@ def test_fused_hvp_matches_double_backward_and_oracle(d, ckpt):
     assert rel_l2(hv.cpu().numpy(), Hv2.cpu().numpy()) <= 1e-5
     assert torch.equal(J, J1)
     assert rel_l2(g.cpu().numpy(), g1.cpu().numpy()) <= 1e-6
+
+
+def test_newton_cg_fwi_with_exact_hvp(d):
+    """Truncated Newton (CG on dufwi_hvp products) lowers the misfit monotonically, by more than an
+    order of magnitude in its first iteration on this case (the FP64 oracle with differenced
+    Hessian products gives 20x), and further than L-BFGS after the same number of iterations."""
+    from paper_2603_04070_gb300 import fwi
+    wl, _ = _case(64)
+    pb = _problem(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    wav = _cuda(wl.wavelet)
+    obs = d.simulate(pb, _cuda(wl.sos_true), wav, geom)
+    ev = fwi.cuda_evaluator(pb, wav, geom, obs)
+    hv = fwi.cuda_hessvec(pb, wav, geom, obs)
+    c0 = _cuda(wl.sos_start)
+    res = fwi.newton_cg(ev, hv, c0, 3, cg_iters=4)
+    J = torch.stack(res.misfits)[:, 0]
+    assert torch.all(J[1:] < J[:-1])
+    assert float(J[1]) < 0.1 * float(J[0])
+    lb = fwi.lbfgs(ev, c0, 3)
+    assert float(J[-1]) < float(torch.stack(lb.misfits)[-1, 0])

@@ -1,7 +1,7 @@
 """Classical FWI around the GPU misfit and gradient (Sec. II-B, Eqs. 5-7).
 
 Eq. 7 updates the SoS map along the data-fidelity gradient, C_{k+1} = C_k + gamma_k g_k, with
-gamma_k < 0 for a descent step. Two ways to choose the step are provided:
+gamma_k < 0 for a descent step. Three ways to choose the step are provided:
 
 * ``steepest_descent``: the direction is -g_k. The trial step is scaled so that its largest
   change is ``alpha`` m/s, and ``alpha`` is halved until the misfit falls by the Armijo margin

@@ -235,3 +235,33 @@ def test_newton_cg_fwi_with_exact_hvp(d):
     assert float(J[1]) < 0.1 * float(J[0])
     lb = fwi.lbfgs(ev, c0, 3)
     assert float(J[-1]) < float(torch.stack(lb.misfits)[-1, 0])
+
+
+def test_exact_hvp_full_shot_set_properties(d):
+    """Full shot set (512 x 512 + 20, 16 transmits x 128 receivers, 6000 steps, checkpoint
+    interval 100), where the oracle would take minutes per product: properties that hold at any
+    size. The Hessian is symmetric; dufwi_hvp agrees with the composed form (dufwi_second_order
+    plus the VJP of 2 J v); its misfit equals dufwi_misfit_gradient's and its gradient agrees."""
+    wl = inputs.make_workload("full_shot_set", seed=0)
+    pb = _problem(d, wl, ckpt_interval=100)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav = _cuda(wl.sos_start), _cuda(wl.wavelet)
+    obs = d.simulate(pb, _cuda(wl.sos_true), wav, geom)
+    rng = np.random.default_rng(0)
+    v = _cuda(rng.standard_normal(wl.sos_start.shape) * 5.0)
+    u = _cuda(rng.standard_normal(wl.sos_start.shape) * 5.0)
+    ws = torch.empty(d.second_order_workspace_size(pb, geom, 1), dtype=torch.uint8, device="cuda")
+    Hv, J, g = d.hvp(pb, sos, wav, geom, obs, v, return_all=True, workspace=ws, check=True)
+    Hv, J, g = Hv.clone(), J.clone(), g.clone()
+    Hu = d.hvp(pb, sos, wav, geom, obs, u, workspace=ws, check=True).clone()
+    a, b = float((u.double() * Hv.double()).sum()), float((v.double() * Hu.double()).sum())
+    assert abs(a - b) <= 1e-4 * max(abs(a), abs(b))
+    J1, g1 = d.misfit_gradient(pb, sos, wav, geom, obs)
+    cd = d.simulate(pb, sos, wav, geom)
+    so, dcd = d.second_order(pb, sos, wav, geom, 2.0 * (cd - obs), v, workspace=ws, check=True)
+    _, wsg = d.forward_save(pb, sos, wav, geom)
+    gn = d.backward(pb, sos, wav, geom, 2.0 * dcd, wsg)
+    torch.cuda.synchronize()
+    assert torch.equal(J, J1)
+    assert rel_l2(g.cpu().numpy(), g1.cpu().numpy()) <= 1e-6
+    assert rel_l2(Hv.cpu().numpy(), (so + gn).cpu().numpy()) <= 1e-5

@@ -48,6 +48,27 @@ def _oracle_compute(problem, sos, wavelet, geom, cd_obs):
     return torch.tensor(Js, dtype=torch.float64), torch.from_numpy(np.stack(gs)).float()
 
 
+def _oracle_compute64(problem, sos, wavelet, geom, cd_obs):
+    import oracle
+    wl = problem
+    p = oracle.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml=wl.pml_cells, pml_R=wl.pml_R,
+                       pml_cref=wl.pml_cref, fd_order=wl.fd_order)
+    return torch.from_numpy(np.stack([
+        oracle.misfit_gradient(p, sos[b].double().numpy(), geom.elem_ix[geom.tx_elem], geom.elem_iz[geom.tx_elem],
+                               wavelet.double().numpy(), geom.elem_ix[geom.rx_elem], geom.elem_iz[geom.rx_elem],
+                               cd_obs[b].double().numpy())[1] for b in range(sos.shape[0])]))
+
+
+def _oracle_hvp(problem, sos, wavelet, geom, cd_obs, v):
+    """(H v, J, g) of this rank's transmits: central differences (FP64) of the oracle gradient
+    along v."""
+    h = 0.05
+    J, g = _oracle_compute(problem, sos, wavelet, geom, cd_obs)
+    gp = _oracle_compute64(problem, sos.double() + h * v.double(), wavelet, geom, cd_obs)
+    gm = _oracle_compute64(problem, sos.double() - h * v.double(), wavelet, geom, cd_obs)
+    return (gp - gm) / (2 * h), J, g
+
+
 def _case():
     from paper_2603_04070_gb300 import dufwi
     wl = inputs.make_workload("linear_disk", seed=31, nx=24, nz=20, nt=120, n_elem=6, n_tx=3, n_maps=2)
@@ -67,8 +88,10 @@ def _worker(rank, world, port, out_path):
     try:
         pb, geom, sos, w, obs = _case()
         J, g = parallel.sharded_misfit_gradient(pb, sos, w, geom, obs, compute=_oracle_compute)
+        v = torch.from_numpy(np.random.default_rng(5).standard_normal(tuple(sos.shape))) * 5.0
+        hv, J2, g2 = parallel.sharded_hvp(pb, sos, w, geom, obs, v, compute=_oracle_hvp)
         if rank == 0:
-            torch.save({"J": J, "g": g}, out_path)
+            torch.save({"J": J, "g": g, "hv": hv, "J2": J2, "g2": g2, "v": v}, out_path)
     finally:
         dist.destroy_process_group()
 
@@ -89,3 +112,8 @@ def test_transmit_sharded_gradient_on_two_gloo_ranks(tmp_path):
     J_ref, g_ref = _oracle_compute(pb, sos, w, geom, obs)
     assert torch.allclose(res["J"], J_ref, rtol=1e-12, atol=0)
     assert torch.allclose(res["g"], g_ref, rtol=1e-5, atol=1e-6 * float(g_ref.abs().max()))
+    # the HVP split: the per-rank products (and misfits, gradients) sum to the whole-set ones
+    hv_ref, _, _ = _oracle_hvp(pb, sos, w, geom, obs, res["v"])
+    assert torch.allclose(res["J2"], J_ref, rtol=1e-12, atol=0)
+    assert torch.allclose(res["g2"], g_ref, rtol=1e-5, atol=1e-6 * float(g_ref.abs().max()))
+    assert float((res["hv"].double() - hv_ref).norm() / hv_ref.norm()) <= 1e-6

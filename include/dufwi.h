@@ -31,7 +31,7 @@
  *     are recorded in a status word inside the workspace and read with dufwi_workspace_status:
  *       * an SoS value that is not finite, or not in (0, c_max];
  *       * non-finite observed data;
- *       * a non-constant density;
+ *       * a density value that is not finite or not positive;
  *       * a bounded device wait that ran out.
  *     No C++ exception crosses this boundary.
  */
@@ -50,7 +50,7 @@ extern "C" {
 #define DUFWI_ERR_INVALID_ARG    1  /* a size, pointer or option is out of range */
 #define DUFWI_ERR_CFL            2  /* c_max dt/dx above the stencil's stability limit, or SoS > c_max */
 #define DUFWI_ERR_GEOMETRY       3  /* an element lies outside the physical grid */
-#define DUFWI_ERR_UNSUPPORTED    4  /* variable density (Eq. 1 with non-constant rho) */
+#define DUFWI_ERR_UNSUPPORTED    4  /* a combination the library does not provide (see each call) */
 #define DUFWI_ERR_WORKSPACE      5  /* workspace too small or misaligned */
 #define DUFWI_ERR_CUDA           6  /* a CUDA runtime call failed */
 #define DUFWI_ERR_TIMEOUT        7  /* a bounded device wait gave up */
@@ -91,7 +91,8 @@ typedef struct {
  *     term. Supported by dufwi_simulate, dufwi_simulate_noalloc, dufwi_misfit,
  *     dufwi_forward_save/dufwi_backward and dufwi_misfit_gradient with ckpt_interval 0 (every
  *     step kept: the memory variables are not checkpointed), with or without a density map;
- *     not by the *_sized calls or dufwi_jvp (DUFWI_ERR_UNSUPPORTED). */
+ *     not by the *_sized calls, dufwi_jvp, dufwi_second_order or dufwi_hvp
+ *     (DUFWI_ERR_UNSUPPORTED). */
 #define DUFWI_BOUNDARY_DAMPING 0
 #define DUFWI_BOUNDARY_CPML 1
 
@@ -125,9 +126,10 @@ int dufwi_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int3
 
 /* Forward model, Eqs. 2-4: the channel data of every shot.
  *   sos      [n_maps][nz][nx] float, device, m/s
- *   density  NULL (constant density, as in the paper) or [n_maps][nz][nx] float, device. The
- *            result does not depend on a constant density. A non-constant one sets
- *            DUFWI_ERR_UNSUPPORTED in the workspace status word.
+ *   density  NULL (constant density, as in the paper) or [n_maps][nz][nx] float, device,
+ *            kg/m^3: Eq. 1's rho div(rho^-1 grad u) on a staggered grid (half-point
+ *            buoyancies). The result does not depend on a constant density. A value that is
+ *            not finite or not positive is recorded in the workspace status word.
  *   wavelet  [nt] or [n_tx][nt] float, device. The source adds dt^2 w[t]/dx^2 at the transmit
  *            node in the step that produces U[t+1].
  *   cd       [n_maps][n_tx][nt][n_rx] float, device, output (may be NULL when n_rx = 0)
@@ -195,7 +197,8 @@ int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *densi
  * perturbation field dU with the same update plus the source dkappa' Lap(U^n). Here
  * dkappa' = 2 kappa' dC / C, with dC extended into the absorbing layer like C. With
  * dufwi_backward this gives Gauss-Newton Hessian-vector products of the misfit,
- * H v = 2 J^T (J v).
+ * H v = 2 J^T (J v). With a density map both fields use the variable-density operator and
+ * Lap is that operator; DUFWI_BOUNDARY_CPML gives DUFWI_ERR_UNSUPPORTED.
  *   dsos   [n_maps][nz][nx] float, device
  *   dcd    [n_maps][n_tx][nt][n_rx] float, device, output
  *   cd     NULL or [n_maps][n_tx][nt][n_rx] float, device, output (the background data)

@@ -462,7 +462,10 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.st = static_cast<cudaStream_t>(stream);
     c.cpml = c.pb->boundary == DUFWI_BOUNDARY_CPML;
     c.vd = density != nullptr || c.cpml;        // the CPML runs on the staggered operator
-    if (c.vd && (c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;   // no Born step for the staggered operators
+    // the Born step runs on the variable-density operator, not with the CPML's memory variables;
+    // the second-order kernels use the compact Laplacian (constant density) only
+    if (c.cpml && (c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
+    if (c.so && density) return DUFWI_ERR_UNSUPPORTED;
     if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
     if (c.vd && c.pb->c_max * c.pb->dt / c.pb->dx > stagger_stability_limit(c.pb->fd_order)) return DUFWI_ERR_CFL;
     c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd && !c.so;
@@ -970,7 +973,7 @@ const char *dufwi_status_string(int status)
     case DUFWI_ERR_INVALID_ARG: return "invalid argument";
     case DUFWI_ERR_CFL: return "CFL condition violated (or SoS above c_max)";
     case DUFWI_ERR_GEOMETRY: return "element outside the physical grid";
-    case DUFWI_ERR_UNSUPPORTED: return "unsupported (non-constant density)";
+    case DUFWI_ERR_UNSUPPORTED: return "unsupported combination";
     case DUFWI_ERR_WORKSPACE: return "workspace too small or misaligned";
     case DUFWI_ERR_CUDA: return "CUDA error";
     case DUFWI_ERR_TIMEOUT: return "device wait timed out";

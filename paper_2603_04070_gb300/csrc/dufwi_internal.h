@@ -178,7 +178,7 @@ cudaError_t launch_sweep(int radius, int mode, const SweepMaps &tm, const StepPa
 // the variable-density maps of StepMaps with cur_box 80 x 48).
 cudaError_t launch_step_cpml(int radius, int mode, const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
                              const CpmlParams &cp, cudaStream_t st);
-// Variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint; 64 x 32 tiles).
+// Variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint, kBorn; 64 x 32 tiles).
 cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 // One step of the second-order sweeps (kinds kSoBorn, kSoAdj, kSoBornAdj; 64 x 32 tiles).
 cudaError_t launch_so_step(int radius, int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,

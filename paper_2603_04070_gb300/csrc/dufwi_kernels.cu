@@ -713,7 +713,8 @@ struct VdLayout {
     static constexpr int kFx = kVFxX * kVTileZ;
     static constexpr int kFz = kTileX * kVFzZ;
     static constexpr int kTile = kTileX * kVTileZ;
-    static constexpr int kTiles = MODE == kAdjoint ? 4 : 2;
+    // prev, kappa' (+ history and sums in the adjoint; + Lap(U^n) and dkappa' in the Born step)
+    static constexpr int kTiles = (MODE == kAdjoint || MODE == kBorn) ? 4 : 2;
     static constexpr int kFloats = kBox + kFx + kFz + kTiles * kTile;
     static constexpr uint32_t kBytes = kFloats * sizeof(float);
 };
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
         prefetch_tensormap(&tm.cur_box);
         mbar_init(&bar, 1);
         mbar_arrive_expect_tx(&bar, VL::kBytes);
-        if (p.early) {
+        if (MODE != kBorn && p.early) {
             tma_load_3d(fx, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
             tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
@@ -762,7 +763,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     grid_dependency_wait();
     if (tid == 0) {
         tma_load_3d(box, &tm.cur_box, &bar, x0 - kVHalo, z0 - kVHalo, s);
-        if (!p.early) {
+        if (MODE == kBorn || !p.early) {
             tma_load_3d(fx, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
             tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
@@ -770,14 +771,22 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
             if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
         if (MODE == kAdjoint) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        if (MODE == kBorn) {   // Lap(U^n) of the background step, dkappa'
+            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, map);
+        }
     }
     grid_dependents_launch();
 
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     int2 rx_range = make_int2(0, 0);
     if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
-    gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
-                            tid, 128);
+    if (MODE == kBorn) {   // the Born field has no point source of its own
+        if (tid == 0) inj.n = 0;
+    } else {
+        gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
+                                tid, 128);
+    }
 
     const int lx = (tid & 15) * 4;
     const int lz = (tid >> 4) * 4;
@@ -883,8 +892,9 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
         const int lo = (lz + j) * kTileX + lx;
         nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
                          p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+        if (MODE == kBorn) nxt[j] = fma4(ld4s(gg + lo), ld4s(hs + lo), nxt[j]);   // + dkappa' L(U^n)
     }
-    if (inj.n > 0) {   // block-uniform: stage the rows, inject in list order, reload
+    if (MODE != kBorn && inj.n > 0) {   // block-uniform: stage the rows, inject in list order, reload
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
@@ -916,7 +926,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
         }
     }
 
-    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+    if (MODE == kFwdSample || MODE == kFwdSampleHist || MODE == kBorn) {
         const int cnt = (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
         for (int e = tid; e < cnt; e += 128) {
             const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
@@ -2315,6 +2325,7 @@ static cudaError_t launch_step_vd_r(int mode, const StepMaps &tm, const StepPara
     case kFwdSampleHist: return launch_step_vd_rm<R, kFwdSampleHist>(tm, p, st);
     case kFwdHist: return launch_step_vd_rm<R, kFwdHist>(tm, p, st);
     case kAdjoint: return launch_step_vd_rm<R, kAdjoint>(tm, p, st);
+    case kBorn: return launch_step_vd_rm<R, kBorn>(tm, p, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -163,9 +163,6 @@ def test_density_status_word_and_unsupported_calls(d):
     step[0, 20:, :] = 172.0
     d.simulate(pb, fast, w, geom, workspace=ws, density=step)
     assert d.workspace_status(ws) == d.ERR_CFL
-    with pytest.raises(d.DufwiError) as e:
-        d.jvp(pb, sos, w, geom, torch.zeros_like(sos), density=r)
-    assert e.value.status == d.ERR_UNSUPPORTED
     # host CFL check against the staggered operator's (slightly lower) limit
     lim = d.cfl_limit(8)
     tight = d.Problem(nx=40, nz=40, dx=1e-4, dt=0.995 * lim * 1e-4 / C_MAX, nt=60, fd_order=8, c_max=C_MAX)
@@ -173,3 +170,44 @@ def test_density_status_word_and_unsupported_calls(d):
     with pytest.raises(d.DufwiError) as e:
         d.simulate(tight, sos, w[:60], geom, density=r)
     assert e.value.status == d.ERR_CFL
+
+
+def _born_case(seed):
+    wl, rho = _case(seed, 58, 52, 320, 14, 2)
+    rng = np.random.default_rng(seed)
+    v = (rng.standard_normal(wl.sos_true.shape) * 5.0).astype(np.float32)
+    return wl, rho, v
+
+
+def test_density_born_jvp_matches_oracle_finite_differences(d):
+    """dM = (dM/dC) v on the variable-density operator (the Born source dkappa' L(U^n) with L the
+    staggered operator) against central differences of the FP64 oracle's forward model with the
+    same density map."""
+    wl, rho, v = _born_case(71)
+    C = wl.sos_true[0].astype(np.float64)
+    h = 0.05
+    ref = (_oracle_traces(wl, C + h * v[0], rho[0]) - _oracle_traces(wl, C - h * v[0], rho[0])) / (2 * h)
+    pb = _pb(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    r = torch.from_numpy(rho).cuda()
+    dcd, cd = d.jvp(pb, torch.from_numpy(wl.sos_true).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                    torch.from_numpy(v).cuda(), density=r, return_cd=True, check=True)
+    assert rel_l2(cd.cpu().numpy()[0], _oracle_traces(wl, C, rho[0])) <= TRACE_TOL
+    assert rel_l2(dcd.cpu().numpy()[0], ref) <= 1e-4
+
+
+def test_density_born_jvp_and_adjoint_are_transposes(d):
+    """<J v, q> = <v, J^T q> between the variable-density Born simulation and adjoint."""
+    wl, rho, v = _born_case(72)
+    pb = _pb(d, wl, ckpt_interval=40)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_true).cuda()
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    r = torch.from_numpy(rho).cuda()
+    q = torch.randn((1, wl.n_tx, wl.nt, wl.n_rx), device="cuda") * 1e-9
+    Jv = d.jvp(pb, sos, wav, geom, torch.from_numpy(v).cuda(), density=r, check=True)
+    _, ws = d.forward_save(pb, sos, wav, geom, density=r)
+    JTq = d.backward(pb, sos, wav, geom, q, ws, density=r, check=True)
+    lhs = float((Jv.double() * q.double()).sum())
+    rhs = float((torch.from_numpy(v).cuda().double() * JTq.double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)

@@ -7,6 +7,12 @@ Iteration k's gradients are computed once for the whole training set, N_k is fit
 the SoS-map MSE, and its outputs become the inputs of iteration k+1. No gradient flows back
 through the physics or through earlier blocks.
 
+End-to-end training (``train_end_to_end``), which the paper avoids, backpropagates the loss
+through every iteration, the physics included. Then dL/dC_k picks up the term H_k gbar_k, where
+gbar_k = dL/dg_k and H_k is the Hessian of the misfit at C_k. ``data_gradient_differentiable``
+supplies it: g_k = dJ/dC is an autograd node whose backward is the exact Hessian-vector product
+of ``dufwi_hvp`` (the Hessian is symmetric, so the VJP of g is H gbar).
+
 N_k is a small convolutional net: three 3 x 3 layers with 32 channels and ReLU in between. Its
 inputs are the SoS offset by 1400 m/s and scaled (Sec. V), and the gradient normalised by its
 max |.| per map. Its output is rescaled to m/s. The convolutions run in torch (cuDNN); they are
@@ -63,6 +69,39 @@ def data_gradient(phys: Physics, sos: torch.Tensor, cd_obs: torch.Tensor, chunk:
     return torch.cat(J), torch.cat(g)
 
 
+class _DataGradient(torch.autograd.Function):
+    """g = dJ/dC (Eq. 6) as a function of C; backward: H gbar by dufwi_hvp."""
+
+    @staticmethod
+    def forward(ctx, sos, cd_obs, phys, chunk):
+        _, g = data_gradient(phys, sos.detach(), cd_obs.detach(), chunk)
+        ctx.save_for_backward(sos, cd_obs)
+        ctx.phys = phys
+        ctx.chunk = chunk
+        return g
+
+    @staticmethod
+    def backward(ctx, gbar):
+        if not ctx.needs_input_grad[0]:
+            return None, None, None, None
+        sos, cd_obs = ctx.saved_tensors
+        phys = ctx.phys
+        # H gbar = s H (gbar / s), s = max |gbar| per map: a unit-scale direction keeps the FP32
+        # sweeps in range whatever the scale of the cotangent
+        s = gbar.abs().amax(dim=(-2, -1), keepdim=True).clamp_min(1e-30)
+        v = (gbar / s).contiguous()
+        out = []
+        for i in range(0, sos.shape[0], ctx.chunk):
+            out.append(dufwi.hvp(phys.problem, sos[i:i + ctx.chunk].detach().contiguous(), phys.wavelet, phys.geom,
+                                 cd_obs[i:i + ctx.chunk].detach().contiguous(), v[i:i + ctx.chunk]))
+        return torch.cat(out) * s, None, None, None
+
+
+def data_gradient_differentiable(phys: Physics, sos: torch.Tensor, cd_obs: torch.Tensor, chunk: int = 8):
+    """g_k = dJ/dC as an autograd node: backpropagating through it applies the exact Hessian."""
+    return _DataGradient.apply(sos, cd_obs, phys, chunk)
+
+
 class UnfoldedFWI(nn.Module):
     """K unfolded iterations C_{k+1} = C_k + N_k(C_k, g_k) (Eq. 9)."""
 
@@ -117,3 +156,30 @@ class UnfoldedFWI(nn.Module):
             with torch.no_grad():
                 c = c + net(c, g)
         return history
+
+    def train_end_to_end(self, phys: Physics, sos0: torch.Tensor, cd_obs: torch.Tensor, sos_gt: torch.Tensor,
+                         epochs: int = 20, batch: int = 8, lr: float = 1e-4, log=None):
+        """End-to-end training: every N_k at once, on the SoS MSE of C_K (Eq. 10 at the last
+        iteration), with gradients through the K data gradients (exact Hessian-vector products)
+        as well as through the nets. Returns the training loss per epoch."""
+        opt = torch.optim.Adam(self.parameters(), lr=lr)
+        losses = []
+        for _ in range(epochs):
+            perm = torch.randperm(sos0.shape[0], device=sos0.device)
+            tot = 0.0
+            for i in range(0, sos0.shape[0], batch):
+                idx = perm[i:i + batch]
+                c = sos0[idx]
+                obs = cd_obs[idx]
+                for net in self.nets:
+                    g = data_gradient_differentiable(phys, c, obs)
+                    c = c + net(c, g)
+                loss = ((c - sos_gt[idx]) ** 2).mean()
+                opt.zero_grad()
+                loss.backward()
+                opt.step()
+                tot += float(loss.detach()) * idx.numel()
+            losses.append(tot / sos0.shape[0])
+            if log:
+                log("end-to-end epoch %d: mse %.4g" % (len(losses), losses[-1]))
+        return losses

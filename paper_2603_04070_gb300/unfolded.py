@@ -45,9 +45,10 @@ class UpdateNet(nn.Module):
         nn.init.zeros_(self.body[-1].bias)
 
     def forward(self, sos: torch.Tensor, grad: torch.Tensor) -> torch.Tensor:
+        """H_k in the dtype of sos; the net itself runs in the dtype of its parameters."""
         g = grad / grad.abs().amax(dim=(-2, -1), keepdim=True).clamp_min(1e-30)
-        x = torch.stack([(sos - SOS_OFFSET) / SOS_SCALE, g], dim=1)
-        return SOS_SCALE * self.body(x)[:, 0]
+        x = torch.stack([(sos - SOS_OFFSET) / SOS_SCALE, g], dim=1).to(self.body[0].weight.dtype)
+        return (SOS_SCALE * self.body(x)[:, 0]).to(sos.dtype)
 
 
 @dataclass

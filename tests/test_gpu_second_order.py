@@ -294,9 +294,10 @@ def test_unfolded_end_to_end_gradient_matches_loss_differences(d):
     nets and both data gradients (exact Hessian-vector products): its projection on its own
     direction d equals the central difference of the loss along d, computed by running the loop
     forward (physics included) at theta +- h d, closer than the truncated gradient that treats
-    the data gradients as constants (the Hessian term is a few percent here). Convolutions run
-    in FP32 (TF32 off): TF32 rounding would put non-smooth noise of ~1e-3 on the loss. Training
-    then lowers the loss."""
+    the data gradients as constants (the Hessian term is a few percent here). The nets run in
+    FP64 with deterministic cuDNN algorithms: TF32 or FP32 rounding, and run-to-run differences
+    in the nets' training, would put noise of up to ~1e-3 on the loss. Training then lowers the
+    loss."""
     from paper_2603_04070_gb300 import unfolded
     torch.manual_seed(0)
     wl = inputs.make_workload("linear_disk", seed=81, nx=48, nz=48, nt=260, n_elem=14, n_tx=3, n_maps=4)
@@ -306,11 +307,14 @@ def test_unfolded_end_to_end_gradient_matches_loss_differences(d):
     gt = _cuda(wl.sos_true)
     obs = d.simulate(pb, gt, phys.wavelet, geom)
     c0 = _cuda(wl.sos_start)
-    tf32 = (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32)
+    flags = (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32,
+             torch.backends.cudnn.deterministic, torch.backends.cudnn.benchmark)
     torch.backends.cudnn.allow_tf32 = False
     torch.backends.cuda.matmul.allow_tf32 = False
+    torch.backends.cudnn.deterministic = True
+    torch.backends.cudnn.benchmark = False
     try:
-        model = unfolded.UnfoldedFWI(K=2).cuda()
+        model = unfolded.UnfoldedFWI(K=2).cuda().double()
         model.train_blockwise(phys, c0, obs, gt, epochs=20, batch=4, lrs=(3e-3, 1e-3))
         params = list(model.parameters())
 
@@ -351,4 +355,5 @@ def test_unfolded_end_to_end_gradient_matches_loss_differences(d):
         assert all(np.isfinite(losses))
         assert losses[-1] < losses[0]
     finally:
-        torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32 = tf32
+        (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32,
+         torch.backends.cudnn.deterministic, torch.backends.cudnn.benchmark) = flags

@@ -173,3 +173,36 @@ def test_second_order_workspace_sizing_and_validation():
     with pytest.raises(d.DufwiError) as e:
         d.second_order_workspace_size(_problem(d, nt=0), g, 1)
     assert e.value.status == d.ERR_INVALID_ARG
+
+
+def test_second_order_entry_points_reject_bad_arguments_before_device_work():
+    """dufwi_second_order / dufwi_hvp: a missing output or input, or a CPML problem, is reported
+    by the return value before anything touches the device (dummy host pointers suffice)."""
+    d = _lib_module()
+    g = _geom(d)
+    arr, sh = g.c_structs()
+    pb = _problem(d).c_struct()
+    buf = (ctypes.c_float * 16)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    lib = d._lib
+    # so (output) missing
+    assert lib.dufwi_second_order(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, p,
+                                  None, None, None, p, 1 << 30, None) == d.ERR_INVALID_ARG
+    # dsos missing
+    assert lib.dufwi_second_order(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, None,
+                                  None, p, None, p, 1 << 30, None) == d.ERR_INVALID_ARG
+    # cd_grad missing with receivers
+    assert lib.dufwi_second_order(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, None, p,
+                                  None, p, None, p, 1 << 30, None) == d.ERR_INVALID_ARG
+    # hv missing; cd_obs missing
+    assert lib.dufwi_hvp(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, p, None, None,
+                         None, p, 1 << 30, None) == d.ERR_INVALID_ARG
+    assert lib.dufwi_hvp(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, None, p, p, None,
+                         None, p, 1 << 30, None) == d.ERR_INVALID_ARG
+    # the CPML has no Born step: unsupported, from the layout check
+    cp = _problem(d, boundary="cpml").c_struct()
+    assert lib.dufwi_hvp(ctypes.byref(cp), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, p, p, None,
+                         None, p, 1 << 30, None) == d.ERR_UNSUPPORTED
+    # a workspace below the layout's size is rejected before the tables are copied
+    assert lib.dufwi_hvp(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, p, p, None,
+                         None, p, 64, None) == d.ERR_WORKSPACE

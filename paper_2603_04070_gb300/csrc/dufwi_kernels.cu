@@ -85,6 +85,47 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, ui
         : "memory");
 }
 
+// L2 eviction hints for the history stream (written once by the forward or recompute sweep, read
+// once by the adjoint): evict-first, so that it does not push out of L2 the fields, kappa' and
+// the imaging sums that every step re-reads. Build-time knob DUFWI_L2_HINTS (1 default, 0 off);
+// the hints change timing only.
+#ifndef DUFWI_L2_HINTS
+#define DUFWI_L2_HINTS 1
+#endif
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void tma_load_4d_stream(void *dst, const CUtensorMap *tm, uint64_t *bar, int x, int y,
+                                                   int z, int w)
+{
+#if DUFWI_L2_HINTS
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar)),
+        "l"(l2_evict_first_policy())
+        : "memory");
+#else
+    tma_load_4d(dst, tm, bar, x, y, z, w);
+#endif
+}
+
+__device__ __forceinline__ void st4_stream(float *p, float4 v)
+{
+#if DUFWI_L2_HINTS
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(l2_evict_first_policy())
+                 : "memory");
+#else
+    st4(p, v);
+#endif
+}
+
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *tm)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
@@ -391,7 +432,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
         if (early) {
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
             tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, s / p.n_tx);
-            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            if (MODE == kAdjoint) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
     }
     grid_dependency_wait();
@@ -400,7 +441,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
         if (!early) {
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
             tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, s / p.n_tx);
-            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            if (MODE == kAdjoint) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
         if (MODE == kAdjoint) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
         if (MODE == kBorn) {
@@ -468,7 +509,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
             }
             const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
             st4(p.out + o, nv);
-            if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
+            if (MODE == kFwdSampleHist || MODE == kFwdHist) st4_stream(p.hist + o, lv);
             if (MODE == kAdjoint) {
                 const int lo = (lz + j) * kTileX + lx;
                 st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));

@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
             tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
             tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
-            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            if (MODE == kAdjoint) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
     }
     grid_dependency_wait();
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
             tma_load_3d(fz, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
             tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
-            if (MODE == kAdjoint) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            if (MODE == kAdjoint) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
         if (MODE == kAdjoint) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
         if (MODE == kBorn) {   // Lap(U^n) of the background step, dkappa'
@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
         }
         const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
         st4(p.out + o, nv);
-        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
+        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4_stream(p.hist + o, lv);
         if (MODE == kAdjoint) {
             const int lo = (lz + j) * kTileX + lx;
             st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
@@ -1059,7 +1059,7 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
             tma_load_3d(bzs, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
             tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
-            if (ADJ) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            if (ADJ) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
     }
     grid_dependency_wait();
@@ -1081,7 +1081,7 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
         if (!p.early) {
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
             tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
-            if (ADJ) tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            if (ADJ) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
         }
         if (ADJ) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
     }
@@ -1381,7 +1381,7 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
         }
         const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
         st4(p.out + o, nv);
-        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4(p.hist + o, lv);
+        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4_stream(p.hist + o, lv);
         if (MODE == kAdjoint) {
             const int lo = (lz + j) * kTileX + lx;
             st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));

@@ -1412,13 +1412,6 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
 // that acquire before its TMA (async proxy) reads. Counter waits are bounded like the mbarrier
 // waits: a CTA whose wait runs out raises DUFWI_ERR_TIMEOUT, sets the abort word and returns, and
 // every other waiter returns when it sees the abort word.
-__device__ __forceinline__ int ld_acquire(const int *ptr)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void st_release(int *ptr, int v)
 {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
@@ -1427,8 +1420,6 @@ __device__ __forceinline__ void st_release(int *ptr, int v)
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Thread 0: waits until the counters of tile k and its in-shot neighbours reach target; false on
-// abort or timeout (the abort word is then set).
 __device__ __forceinline__ int ld_relaxed(const int *ptr)
 {
     int v;

@@ -198,10 +198,22 @@ def _dev_tensor(t: torch.Tensor, name: str, dtype, shape=None) -> torch.Tensor:
     return t
 
 
+def _alloc_workspace(need: int, device) -> torch.Tensor:
+    """The workspace buffer; an allocation failure becomes a DufwiError naming the size (the
+    library itself never allocates device memory)."""
+    try:
+        return torch.empty(need, dtype=torch.uint8, device=device)
+    except (torch.cuda.OutOfMemoryError, RuntimeError) as e:
+        if "out of memory" not in str(e).lower():
+            raise
+        raise DufwiError(ERR_WORKSPACE, "could not allocate a workspace of %d bytes (%.2f GB) on %s: %s"
+                         % (need, need / 1e9, device, str(e).splitlines()[0])) from e
+
+
 def _workspace(problem, geom, n_maps, gradient, workspace, device):
     need = workspace_size(problem, geom, n_maps, gradient)
     if workspace is None:
-        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+        workspace = _alloc_workspace(need, device)
     elif workspace.numel() * workspace.element_size() < need:
         raise DufwiError(ERR_WORKSPACE, "workspace of %d bytes < %d" %
                          (workspace.numel() * workspace.element_size(), need))
@@ -440,7 +452,7 @@ def jvp(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geomet
         _dev_tensor(cd, "cd", torch.float32, cshape)
     need = jvp_workspace_size(problem, geom, n_maps)
     if workspace is None:
-        workspace = torch.empty(need, dtype=torch.uint8, device=sos.device)
+        workspace = _alloc_workspace(need, sos.device)
     elif workspace.numel() * workspace.element_size() < need:
         raise DufwiError(ERR_WORKSPACE, "jvp workspace")
     pb = problem.c_struct()
@@ -489,7 +501,7 @@ def second_order(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geo
         _dev_tensor(grad, "grad", torch.float32, sos.shape)
     need = second_order_workspace_size(problem, geom, n_maps)
     if workspace is None:
-        workspace = torch.empty(need, dtype=torch.uint8, device=sos.device)
+        workspace = _alloc_workspace(need, sos.device)
     elif workspace.numel() * workspace.element_size() < need:
         raise DufwiError(ERR_WORKSPACE, "second_order workspace")
     pb = problem.c_struct()
@@ -528,7 +540,7 @@ def hvp(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geomet
         _dev_tensor(grad, "grad", torch.float32, sos.shape)
     need = second_order_workspace_size(problem, geom, n_maps)
     if workspace is None:
-        workspace = torch.empty(need, dtype=torch.uint8, device=sos.device)
+        workspace = _alloc_workspace(need, sos.device)
     elif workspace.numel() * workspace.element_size() < need:
         raise DufwiError(ERR_WORKSPACE, "hvp workspace")
     pb = problem.c_struct()

@@ -206,3 +206,32 @@ def test_second_order_entry_points_reject_bad_arguments_before_device_work():
     # a workspace below the layout's size is rejected before the tables are copied
     assert lib.dufwi_hvp(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, p, p, None,
                          None, p, 64, None) == d.ERR_WORKSPACE
+
+
+def test_workspace_allocation_failure_is_reported_as_a_library_error(monkeypatch):
+    """The library allocates nothing; the binding allocates the workspace. A fault-injecting
+    allocator that runs out of memory makes the binding raise DufwiError(ERR_WORKSPACE) with the
+    size it needed; other allocator errors pass through unchanged."""
+    import torch
+    d = _lib_module()
+    g = _geom(d)
+    pb = _problem(d)
+    need = d.workspace_size(pb, g, 1)
+    real_empty = torch.empty
+
+    def oom(*a, **k):
+        if k.get("dtype") is torch.uint8:
+            raise torch.cuda.OutOfMemoryError("CUDA out of memory. Tried to allocate 1.00 GiB")
+        return real_empty(*a, **k)
+
+    monkeypatch.setattr(d.torch, "empty", oom)
+    with pytest.raises(d.DufwiError) as e:
+        d._workspace(pb, g, 1, True, None, "cpu")
+    assert e.value.status == d.ERR_WORKSPACE and str(need) in str(e.value)
+
+    def broken(*a, **k):
+        raise RuntimeError("device-side failure of another kind")
+
+    monkeypatch.setattr(d.torch, "empty", broken)
+    with pytest.raises(RuntimeError, match="another kind"):
+        d._workspace(pb, g, 1, True, None, "cpu")

@@ -1,0 +1,38 @@
+"""The benchmark's output contract, checked on the CPU: the reference arm (the FP64 oracle on a
+bounded sample) prints exactly one JSON line with every field the contract asks for, and its
+config is the one the GPU line builds for the same workload with the default launch options."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_complete_json_line(monkeypatch):
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # the GPU line's config for the same workload, default launch options
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2603_04070_gb300 import inputs
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()
+    args.tile_z_used, args.two_step_used, args.persistent_used = 32, 0, 0
+    wl = inputs.make_workload(args.workload, seed=0, nt=args.nt, n_tx=args.n_tx)
+    assert d["config"] == json.loads(json.dumps(bench.workload_config(wl, args)))
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT

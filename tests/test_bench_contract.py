@@ -36,3 +36,21 @@ def test_reference_arm_prints_one_complete_json_line(monkeypatch):
     wl = inputs.make_workload(args.workload, seed=0, nt=args.nt, n_tx=args.n_tx)
     assert d["config"] == json.loads(json.dumps(bench.workload_config(wl, args)))
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+
+
+def test_reference_arm_under_torchrun_prints_once(tmp_path):
+    """Launched as the multi-GPU bench is (torchrun, two ranks), the reference arm runs on rank 0
+    alone: one JSON line with n_gpus = 2, and every rank exits 0."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "0"]
+    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2

@@ -8,6 +8,8 @@ Compressed checkpoint snapshots (BF16 or FP16) leave the traces and the misfit u
 since both come from the uncompressed first sweep. Their gradient errors are measured and
 bounded separately.
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -236,18 +238,29 @@ def test_compressed_snapshots(d, dtype, tol):
     assert err <= tol
 
 
-def test_fp16_snapshots_meet_the_fp32_bounds_at_scale(d):
-    """The compressed path at a paper-scale size: the cropped 256 x 256 sub-problem of the 1024 x
-    1024 configuration (central 64 elements, 8 transmits, 3500 steps, checkpoints every 100 steps)
-    with FP16 snapshots stays within the FP32 bounds against the oracle (traces 1e-5, gradient
-    1e-4). BF16 snapshots are measured at about 2e-4 here and are not held to this bound."""
+@functools.lru_cache(maxsize=1)
+def _cropped_scale_case():
+    """The cropped 256 x 256 sub-problem of the 1024 x 1024 configuration (central 64 elements,
+    8 transmits, 3500 steps) with its oracle observed data and oracle gradient (checkpoints every
+    100 steps), computed once for the snapshot-precision cases."""
     wl = inputs.make_workload("scale", seed=0, nx=256, nz=256, nt=3500, n_elem=64, n_tx=8)
     M_obs = _observed(wl)
-    J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0], ckpt=100)
-    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=100, snapshot_dtype="fp16")
-    assert rel_l2(cd[0], cd_ref) <= TRACE_TOL
-    assert abs(float(J[0]) - J_ref) <= 1e-4 * J_ref
-    assert rel_l2(g[0], g_ref) <= GRAD_TOL
+    return wl, M_obs, _oracle_grad(wl, wl.sos_start[0], M_obs[0], ckpt=100)
+
+
+@pytest.mark.parametrize("dtype,grad_tol", [("fp32", GRAD_TOL), ("fp16", GRAD_TOL), ("bf16", 1e-3)])
+def test_snapshot_precision_at_scale_vs_oracle(d, dtype, grad_tol):
+    """The snapshot-precision study against the oracle at a paper-scale size (the cropped case
+    above, checkpoints every 100 steps). FP32 and FP16 snapshots stay within the FP32 bounds
+    (traces 1e-5, gradient 1e-4); BF16 snapshots, measured at about 2e-4, are held to 1e-3. The
+    errors are printed (pytest -s) for the precision summary."""
+    wl, M_obs, (J_ref, g_ref, cd_ref) = _cropped_scale_case()
+    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=100, snapshot_dtype=dtype)
+    errs = (rel_l2(cd[0], cd_ref), abs(float(J[0]) - J_ref) / J_ref, rel_l2(g[0], g_ref))
+    print("snapshots %s at 256x256x8x3500 vs oracle: traces %.3e misfit %.3e gradient %.3e" % ((dtype,) + errs))
+    assert errs[0] <= TRACE_TOL
+    assert errs[1] <= 1e-4
+    assert errs[2] <= grad_tol
 
 
 def test_zero_residual_gives_zero_gradient(d):

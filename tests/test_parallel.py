@@ -117,3 +117,59 @@ def test_transmit_sharded_gradient_on_two_gloo_ranks(tmp_path):
     assert torch.allclose(res["J2"], J_ref, rtol=1e-12, atol=0)
     assert torch.allclose(res["g2"], g_ref, rtol=1e-5, atol=1e-6 * float(g_ref.abs().max()))
     assert float((res["hv"].double() - hv_ref).norm() / hv_ref.norm()) <= 1e-6
+
+
+def _failing_worker(rank, world, port, out_dir):
+    """Rank 1's computation fails before the collective (an exception on the host); rank 0 must
+    see an error from the all-reduce within the process group's timeout instead of waiting."""
+    import datetime
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    pb, geom, sos, w, obs = _case()
+
+    def compute(problem, s, wav, g, o):
+        if rank == 1:
+            raise RuntimeError("injected failure on rank 1")
+        return _oracle_compute(problem, s, wav, g, o)
+
+    t0 = time.time()
+    try:
+        parallel.sharded_misfit_gradient(pb, sos, w, geom, obs, compute=compute)
+        outcome = "completed"
+    except Exception as e:   # rank 0: the collective fails; rank 1: the injected error
+        outcome = "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")
+    with open(os.path.join(out_dir, "rank%d.txt" % rank), "w") as f:
+        f.write("%s\n%.1f\n" % (outcome, time.time() - t0))
+    if rank == 1:
+        os._exit(3)                 # the failed rank leaves without tearing the group down
+    try:
+        dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+def test_a_failed_rank_is_reported_not_waited_for(tmp_path):
+    """Failure detection on the host (no GPU involved): a rank that raises before the FP64
+    all-reduce of the transmit-sharded gradient leaves; the other rank's collective ends with an
+    error within the 10 s process-group timeout instead of waiting on it."""
+    from paper_2603_04070_gb300 import build_lib
+    build_lib.build()
+    sp = mp.get_context("spawn")
+    port = _free_port()
+    procs = [sp.Process(target=_failing_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p_ in procs:
+        p_.start()
+    for p_ in procs:
+        p_.join(timeout=120)
+    alive = [p_ for p_ in procs if p_.is_alive()]
+    for p_ in alive:                 # only if the bound above was exceeded: end this test's own processes
+        p_.kill()
+    assert not alive
+    assert procs[1].exitcode == 3
+    r0 = (tmp_path / "rank0.txt").read_text().split("\n")
+    r1 = (tmp_path / "rank1.txt").read_text().split("\n")
+    assert r1[0].startswith("RuntimeError: injected failure")
+    assert not r0[0].startswith("completed")
+    assert float(r0[1]) < 30.0

@@ -235,3 +235,44 @@ def test_workspace_allocation_failure_is_reported_as_a_library_error(monkeypatch
     monkeypatch.setattr(d.torch, "empty", broken)
     with pytest.raises(RuntimeError, match="another kind"):
         d._workspace(pb, g, 1, True, None, "cpu")
+
+
+def _header_text():
+    with open(os.path.join(ROOT, "include", "dufwi.h")) as f:
+        return re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, snapshot types, boundaries, options and the no-alloc scratch size: the
+    binding's values are the header's."""
+    d = _lib_module()
+    defs = {m.group(1): m.group(2).strip() for m in re.finditer(r"^#define\s+DUFWI_(\w+)\s+(.+)$", _header_text(),
+                                                                 flags=re.M)}
+    for name, val in defs.items():
+        if name == "H":
+            continue
+        v = eval(val.replace("u", ""), {})                                   # e.g. (64u << 20)
+        if name.startswith("SNAP_"):
+            assert d.SNAPSHOT_DTYPES[name[5:].lower()] == v, name
+        elif name.startswith("BOUNDARY_"):
+            assert d.BOUNDARIES[name[9:].lower()] == v, name
+        else:
+            assert getattr(d, name) == v, name
+
+
+def test_binding_argument_counts_match_the_header_prototypes():
+    """Every declared function the binding gives argtypes to takes as many arguments as its
+    prototype has parameters (a mismatch would pass garbage through ctypes silently)."""
+    d = _lib_module()
+    text = _header_text()
+    protos = {}
+    for m in re.finditer(r"\b(dufwi_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = m.group(2).strip()
+        protos[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    checked = 0
+    for name, n in protos.items():
+        fn = getattr(d._lib, name)
+        if getattr(fn, "argtypes", None) is not None:
+            assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+            checked += 1
+    assert checked >= 20

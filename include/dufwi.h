@@ -80,7 +80,27 @@ typedef struct {
     double  c_max;           /* upper bound of every SoS value (m/s), used for the CFL check */
     int32_t boundary;        /* DUFWI_BOUNDARY_*: absorbing layer of the pml_cells border cells */
     double  pml_alpha;       /* CPML only: frequency shift at the layer's inner edge (1/s), >= 0 */
+    int32_t forward_precision; /* DUFWI_FORWARD_*: arithmetic of the forward (and recompute) steps */
 } dufwi_problem;
+
+/* Arithmetic of the forward steps (the simulation of Eqs. 2-3, and the recompute of checkpoint
+ * segments). The adjoint and the imaging condition run in FP32 in both modes.
+ *   DUFWI_FORWARD_FP32: FP32 stencil and update; traces within ~1e-6 (rel-L2) of the FP64
+ *     recursion. The gradient (Eq. 6) is linear in the residual r = M_sim - M_obs, so its error
+ *     grows like |M| / |r|: 1e-3 to 1e-2 when a weak scatterer leaves r at 0.1-1 % of M.
+ *   DUFWI_FORWARD_COMPENSATED: the field is carried as hi + lo FP32 planes and every rounding of
+ *     the step is recovered with error-free transformations (TwoSum, TwoProd by FMA); the stencil
+ *     weights are scaled to integers and kappa' and the damping coefficients are FP64 values held
+ *     as hi + lo. Traces match the FP64 recursion to ~1e-13, and the residual is formed from
+ *     (hi, lo) before rounding, so the gradient meets 1e-4 at any residual level. The traces
+ *     returned are the hi planes (the FP32 rounding of the result). Costs: about 7x the FP32
+ *     step's arithmetic, two more field planes and 8 B/cell more traffic per forward step, and
+ *     FP32 snapshots of four planes instead of two. Constant density and the damping layer only:
+ *     with a density map, the CPML, dufwi_jvp, dufwi_second_order or dufwi_hvp it returns
+ *     DUFWI_ERR_UNSUPPORTED. The launch options (tile height, two steps, persistent sweeps) do not
+ *     apply: the compensated step runs one launch per step on 64 x 32 tiles. */
+#define DUFWI_FORWARD_FP32 0
+#define DUFWI_FORWARD_COMPENSATED 1
 
 /* Absorbing layers (both over pml_cells cells, quadratic damping profile d = d0 (xi/L)^2 with
  * d0 = 3 pml_cref ln(1/pml_R) / (2 L)):

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libdufwi.so")
-SOURCES = ["dufwi_kernels.cu", "dufwi_capi.cu", "dufwi_noalloc.cu"]
+SOURCES = ["dufwi_kernels.cu", "dufwi_comp.cu", "dufwi_capi.cu", "dufwi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 # Extra nvcc flags for build-time knobs (e.g. -DDUFWI_STEP_MIN_CTAS_128=8), space separated.

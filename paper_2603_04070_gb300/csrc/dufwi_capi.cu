@@ -99,6 +99,11 @@ struct Layout {
     // second-order calls: adjoint and differentiated-adjoint rings, second and third histories,
     // two more imaging sums, the second adjoint source
     size_t o_mu[4], o_dmu[4], o_hist2, o_hist3, o_acc1, o_acc2, o_asrc2, o_cd2;
+    // compensated forward steps: low planes of the forward ring, kappa' / s_R as hi + lo, the
+    // double-float damping table, low parts of the traces; snapshot planes per segment
+    bool comp;
+    int snap_planes;
+    size_t o_fl[2], o_kqh, o_kql, o_dampc, o_cdl;
 };
 
 // Last table contents uploaded to each workspace (see common_setup), and whether a call may
@@ -136,6 +141,8 @@ int validate_problem(const dufwi_problem *pb)
         return DUFWI_ERR_INVALID_ARG;
     if ((long long)pb->nx + 2LL * pb->pml_cells > 65535 || (long long)pb->nz + 2LL * pb->pml_cells > 65535)
         return DUFWI_ERR_INVALID_ARG;
+    if (pb->forward_precision != DUFWI_FORWARD_FP32 && pb->forward_precision != DUFWI_FORWARD_COMPENSATED)
+        return DUFWI_ERR_INVALID_ARG;
     if (pb->c_max * pb->dt / pb->dx > stability_limit(pb->fd_order)) return DUFWI_ERR_CFL;
     return DUFWI_OK;
 }
@@ -170,6 +177,11 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     L->n_hist = (pb->ckpt_interval == 0) ? (steps > 0 ? steps : 1) : L->K;
     if (kind == kLayoutJvp) L->n_hist = 1;
     L->snap_elem = pb->snapshot_dtype == DUFWI_SNAP_FP32 ? 4 : 2;
+    L->comp = pb->forward_precision == DUFWI_FORWARD_COMPENSATED;
+    if (L->comp && (pb->boundary != DUFWI_BOUNDARY_DAMPING || kind == kLayoutJvp || kind == kLayoutSecond))
+        return DUFWI_ERR_UNSUPPORTED;
+    // FP32 snapshots of the compensated field keep both planes of U^t and U^{t-1}
+    L->snap_planes = (L->comp && pb->snapshot_dtype == DUFWI_SNAP_FP32) ? 4 : 2;
 
     const size_t field = (size_t)L->S * L->slice * sizeof(float);
     const size_t cdb = (size_t)L->S * L->nt * (L->n_rx > 0 ? L->n_rx : 1) * sizeof(float);
@@ -205,13 +217,20 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         L->o_cpml = take(sizeof(float) * 4 * (size_t)(L->nxp + L->nzp));
     }
     for (int i = 0; i < 4; ++i) L->o_f[i] = take(field);
+    if (L->comp) {
+        for (int i = 0; i < 2; ++i) L->o_fl[i] = take(field);
+        L->o_kqh = take((size_t)n_maps * L->slice * sizeof(float));
+        L->o_kql = take((size_t)n_maps * L->slice * sizeof(float));
+        L->o_dampc = take(sizeof(float4) * (size_t)(L->P + 1) * (L->P + 1));
+        if (gradient) L->o_cdl = take(cdb);
+    }
     if (gradient) {
         const bool store_all = pb->ckpt_interval == 0 || pb->ckpt_interval >= steps;
         for (int i = 0; i < 4; ++i) L->o_m[i] = take(field);
         L->o_grad = take(field);
         L->o_hist = take(field * (size_t)L->n_hist);
         if (!store_all) {
-            L->o_snap = take((size_t)L->n_seg * 2 * L->S * L->slice * L->snap_elem);
+            L->o_snap = take((size_t)L->n_seg * L->snap_planes * L->S * L->slice * L->snap_elem);
             L->o_scale = take((size_t)L->n_seg * 2 * L->S * sizeof(unsigned));
         }
         L->o_cd = take(cdb);
@@ -384,6 +403,11 @@ struct Ctx {
     bool persistent = false;                  // one cooperative launch per sweep segment
     bool cpml = false;                        // convolutional PML instead of the damping term
     bool so = false;                          // second-order call (dufwi_second_order)
+    bool comp = false;                        // compensated forward steps (hi + lo planes)
+    float *cd_lo = nullptr;                   // compensated: low parts of the traces of the current sweep
+    CompParams cq;                            // compensated: constant arguments of the step
+    FieldMaps lomap[2];                       // compensated: maps of the low planes of the forward ring
+    CUtensorMap kqh1, kql1;                   // compensated: kappa' / s_R, hi and lo
     int mem_par = 0;                          // CPML: which memory-variable set the next step reads
     CpmlMaps cm_fwd[2], cm_adj[2];            // CPML: maps reading set 0 / set 1
     FieldMaps fmap[4], mmap[4];
@@ -467,11 +491,13 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (c.cpml && (c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
     if (c.so && density) return DUFWI_ERR_UNSUPPORTED;
     if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
+    c.comp = L.comp;
+    if (c.comp && (density || c.cpml || c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
     if (c.vd && c.pb->c_max * c.pb->dt / c.pb->dx > stagger_stability_limit(c.pb->fd_order)) return DUFWI_ERR_CFL;
-    c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd && !c.so;
-    c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd && !c.so;
+    c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd && !c.so && !c.comp;
+    c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd && !c.so && !c.comp;
     c.mem_par = 0;
-    c.tz = (c.vd || c.persistent || c.so) ? 32 : g_tile_z;
+    c.tz = (c.vd || c.persistent || c.so || c.comp) ? 32 : g_tile_z;
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
     std::vector<int> sorted1, sorted2, sortede;
@@ -489,6 +515,24 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
             damp[(size_t)dz * (L.P + 1) + dxl] =
                 make_float2((float)(-q * (2.0 + q) / (1.0 + q)), (float)(2.0 * q / (1.0 + q)));
         }
+    // compensated steps: the same terms as FP64 values split into hi + lo
+    std::vector<float4> dampc;
+    if (c.comp) {
+        dampc.resize((size_t)(L.P + 1) * (L.P + 1));
+        auto split = [](double v, float &hi, float &lo) {
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+        };
+        for (int dz = 0; dz <= L.P; ++dz)
+            for (int dxl = 0; dxl <= L.P; ++dxl) {
+                const double xz = (double)dz / L.P, xx = (double)dxl / L.P;
+                const double q = (d0 * xx * xx + d0 * xz * xz) * pb->dt;
+                float4 v;
+                split(-q * (2.0 + q) / (1.0 + q), v.x, v.y);
+                split(2.0 * q / (1.0 + q), v.z, v.w);
+                dampc[(size_t)dz * (L.P + 1) + dxl] = v;
+            }
+    }
     // CPML recursion coefficients per axis: a, b at the nodes, then at the half points j + 1/2
     std::vector<float> cpml_tab;
     if (c.cpml) {
@@ -527,7 +571,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                           {L.o_sorted2, sorted2.data(), sizeof(int) * sorted2.size()},
                           {L.o_tabe, tabe.data(), sizeof(int2) * tabe.size()},
                           {L.o_sortede, sortede.data(), sizeof(int) * sortede.size()},
-                          {L.o_cpml, cpml_tab.data(), sizeof(float) * cpml_tab.size()}};
+                          {L.o_cpml, cpml_tab.data(), sizeof(float) * cpml_tab.size()},
+                          {L.o_dampc, dampc.data(), sizeof(float4) * dampc.size()}};
     uint64_t h = 1469598103934665603ull;   // FNV-1a over offsets and contents
     auto mix = [&h](const void *data, size_t n) {
         const unsigned char *b = static_cast<const unsigned char *>(data);
@@ -564,6 +609,10 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                            L.n_maps, L.Nx, L.Nz, L.P, L.nxp, L.nzp, L.pitch, pb->dt / pb->dx, c.cpml ? 0.0 : d0,
                            pb->dt, pb->c_max, c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.cpml && !density,
                            c.st));
+    if (c.comp)
+        CKL(launch_setup_kq(sos, c.at<float>(L.o_kqh), c.at<float>(L.o_kql), L.n_maps, L.Nx, L.Nz, L.P, L.nzp,
+                            L.pitch, pb->dt / pb->dx, comp_weight_scale(pb->fd_order), d0, pb->dt,
+                            c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
 
     // tensor maps of every buffer
@@ -573,6 +622,19 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (tensor_map(&c.kap1, kap, L, L.n_maps, 0, kTileX, c.tz) ||
         tensor_map(&c.kap2, kap, L, L.n_maps, 0, kTileX + 2 * kHalo, kPairTileZ + 2 * kHalo))
         return DUFWI_ERR_CUDA;
+    if (c.comp) {
+        for (int i = 0; i < 2; ++i)
+            if (field_maps(&c.lomap[i], c.at<float>(L.o_fl[i]), L, c.tz)) return DUFWI_ERR_CUDA;
+        if (tensor_map(&c.kqh1, c.at<float>(L.o_kqh), L, L.n_maps, 0, kTileX, c.tz) ||
+            tensor_map(&c.kql1, c.at<float>(L.o_kql), L, L.n_maps, 0, kTileX, c.tz))
+            return DUFWI_ERR_CUDA;
+        const double s64 = pb->dt * pb->dt / (pb->dx * pb->dx);
+        c.cq.out_lo = nullptr;
+        c.cq.cd_lo = nullptr;
+        c.cq.damp = c.at<float4>(L.o_dampc);
+        c.cq.src_lo = (float)(s64 - (double)(float)s64);
+        c.cq.hist_scale = (float)(1.0 / comp_weight_scale(pb->fd_order));
+    }
     if (c.vd && (tensor_map(&c.bx1, c.at<float>(L.o_bx), L, L.n_maps, 0, kVFxX, kVTileZ) ||
                  tensor_map(&c.bz1, c.at<float>(L.o_bz), L, L.n_maps, 0, kTileX, kVFzZ)))
         return DUFWI_ERR_CUDA;
@@ -650,6 +712,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
 struct Ring {
     float *buf[4];
     const FieldMaps *map;
+    float *lo[4] = {nullptr, nullptr, nullptr, nullptr};   // compensated forward ring: low planes (0, 1)
+    const FieldMaps *lmap = nullptr;
     int cur, prv;
     void spares(int &a, int &b) const
     {
@@ -674,6 +738,22 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
     p.out = rg.buf[rg.prv];
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
+    if (rg.lo[0] && mode != kAdjoint) {   // compensated forward step on (hi, lo) planes
+        CompMaps cm;
+        memset(&cm, 0, sizeof(cm));
+        cm.hi_box = rg.map[rg.cur].box1;
+        cm.lo_box = rg.lmap[rg.cur].box1;
+        cm.hi_tile = rg.map[rg.prv].tile1;
+        cm.lo_tile = rg.lmap[rg.prv].tile1;
+        cm.kq_hi = c.kqh1;
+        cm.kq_lo = c.kql1;
+        CompParams q = c.cq;
+        q.out_lo = rg.lo[rg.prv];
+        q.cd_lo = c.cd_lo;
+        CKL(launch_comp_step(c.L.radius, mode, cm, p, q, c.st));
+        std::swap(rg.cur, rg.prv);
+        return DUFWI_OK;
+    }
     if (c.cpml) {   // memory variables: read set mem_par, write the other
         tm.cur_box = rg.map[rg.cur].box2;
         tm.bx_tile = c.bx1;
@@ -834,6 +914,8 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
     const int e0 = g_prof.mark(c.st);
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
     for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(rg.buf[i], 0, field, c.st));
+    for (int i = 0; i < 2; ++i)
+        if (rg.lo[i]) CK(cudaMemsetAsync(rg.lo[i], 0, field, c.st));
     if (c.cpml) {
         for (int i = 0; i < 8; ++i) CK(cudaMemsetAsync(c.at<float>(L.o_cm[i]), 0, field, c.st));
         c.mem_par = 0;
@@ -847,12 +929,16 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
     for (int n = 0; n < L.nt - 1; n += seg) {
         if (snapshots) {
             const int sg = n / L.K;
-            char *snap = c.at<char>(L.o_snap) + (size_t)sg * 2 * L.S * L.slice * L.snap_elem;
+            char *snap = c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
             float *cur = rg.buf[rg.cur], *prv = rg.buf[rg.prv];
             if (dtype == DUFWI_SNAP_FP32) {
                 CK(cudaMemcpyAsync(snap, cur, field, cudaMemcpyDeviceToDevice, c.st));
                 CK(cudaMemcpyAsync(snap_d, prv, field, cudaMemcpyDeviceToDevice, c.st));
+                if (L.snap_planes == 4) {   // low planes of the compensated field
+                    CK(cudaMemcpyAsync(snap + 2 * field, rg.lo[rg.cur], field, cudaMemcpyDeviceToDevice, c.st));
+                    CK(cudaMemcpyAsync(snap + 3 * field, rg.lo[rg.prv], field, cudaMemcpyDeviceToDevice, c.st));
+                }
             } else {
                 unsigned *sc = c.at<unsigned>(L.o_scale) + (size_t)sg * 2 * L.S;
                 CK(cudaMemsetAsync(sc, 0, 2 * L.S * sizeof(unsigned), c.st));
@@ -864,9 +950,13 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
         int rc = forward_range(c, rg, n, n1, mode, wavelet, cd, hist, 0, nl);
         if (rc) return rc;
     }
-    if (L.n_rx > 0)
+    if (L.n_rx > 0) {
         CKL(launch_sample(rg.buf[rg.cur], c.at<int>(L.o_rx), cd, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt,
                           L.nt - 1, c.st));
+        if (rg.lo[0] && c.cd_lo)
+            CKL(launch_sample(rg.lo[rg.cur], c.at<int>(L.o_rx), c.cd_lo, L.slice, L.pitch, L.S, L.n_tx, L.n_rx,
+                              L.nt, L.nt - 1, c.st));
+    }
     g_prof.span(0, e0, g_prof.mark(c.st), nl);
     return DUFWI_OK;
 }
@@ -1036,6 +1126,10 @@ int dufwi_simulate_sized(const dufwi_problem *pb, const dufwi_map_sizes *sizes, 
     Ring rg;
     for (int i = 0; i < 4; ++i) rg.buf[i] = c.at<float>(c.L.o_f[i]);
     rg.map = c.fmap;
+    if (c.comp) {
+        for (int i = 0; i < 2; ++i) rg.lo[i] = c.at<float>(c.L.o_fl[i]);
+        rg.lmap = c.lomap;
+    }
     return forward_sweep(c, rg, wavelet, cd, false, false);
 }
 
@@ -1049,6 +1143,10 @@ Ring field_ring(Ctx &c, bool adjoint)
     Ring r;
     for (int i = 0; i < 4; ++i) r.buf[i] = c.at<float>(adjoint ? c.L.o_m[i] : c.L.o_f[i]);
     r.map = adjoint ? c.mmap : c.fmap;
+    if (c.comp && !adjoint) {   // the adjoint runs in FP32 in both modes
+        for (int i = 0; i < 2; ++i) r.lo[i] = c.at<float>(c.L.o_fl[i]);
+        r.lmap = c.lomap;
+    }
     r.cur = 0;
     r.prv = 1;
     return r;
@@ -1060,6 +1158,7 @@ int gradient_forward(Ctx &c, const float *wavelet)
 {
     Ring fr = field_ring(c, false);
     const bool store_all = (c.L.n_seg == 1);
+    c.cd_lo = c.comp ? c.at<float>(c.L.o_cdl) : nullptr;
     return forward_sweep(c, fr, wavelet, c.at<float>(c.L.o_cd), store_all, !store_all);
 }
 
@@ -1091,17 +1190,24 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
             nl = 0;
             e0 = g_prof.mark(c.st);
             // restore (U^{t0}, U^{t0-1}) and recompute Lap(U^n) for n = t0 .. t1-1
-            char *snap = c.at<char>(L.o_snap) + (size_t)sg * 2 * L.S * L.slice * L.snap_elem;
+            char *snap = c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
             fr.cur = 0;
             fr.prv = 1;
             if (dtype == DUFWI_SNAP_FP32) {
                 CK(cudaMemcpyAsync(fr.buf[0], snap, field, cudaMemcpyDeviceToDevice, c.st));
                 CK(cudaMemcpyAsync(fr.buf[1], snap_d, field, cudaMemcpyDeviceToDevice, c.st));
+                if (L.snap_planes == 4) {
+                    CK(cudaMemcpyAsync(fr.lo[0], snap + 2 * field, field, cudaMemcpyDeviceToDevice, c.st));
+                    CK(cudaMemcpyAsync(fr.lo[1], snap + 3 * field, field, cudaMemcpyDeviceToDevice, c.st));
+                }
             } else {
                 const unsigned *sc = c.at<unsigned>(L.o_scale) + (size_t)sg * 2 * L.S;
                 CKL(launch_snap_load(fr.buf[0], fr.buf[1], snap, snap_d, sc, dtype, L.S, L.slice, L.nxp, L.nzp,
                                      L.pitch, c.st));
+                // compensated steps restart from the rounded snapshot: low planes zero
+                for (int i = 0; i < 2; ++i)
+                    if (fr.lo[i]) CK(cudaMemsetAsync(fr.lo[i], 0, field, c.st));
             }
             rc = forward_range(c, fr, t0, t1, kFwdHist, wavelet, nullptr, hist, t0, nl);
             if (rc) return rc;
@@ -1171,7 +1277,8 @@ int dufwi_misfit_gradient_sized(const dufwi_problem *pb, const dufwi_map_sizes *
     // residual, misfit and adjoint source
     long long nl = 0;
     const int e0 = g_prof.mark(c.st);
-    CKL(launch_residual(cd, cd_obs, c.at<float>(L.o_kap), c.at<int>(L.o_rx), c.at<float>(L.o_asrc),
+    CKL(launch_residual(cd, c.comp ? c.at<float>(L.o_cdl) : nullptr, cd_obs, c.at<float>(L.o_kap),
+                        c.at<int>(L.o_rx), c.at<float>(L.o_asrc),
                         c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
     CKL(launch_misfit_sum(c.at<double>(L.o_part), misfit, L.n_maps, L.n_tx, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
@@ -1192,13 +1299,15 @@ int dufwi_misfit(const dufwi_problem *pb, const float *sos, const float *density
     const Layout &L = c.L;
     Ring fr = field_ring(c, false);
     float *cd = c.at<float>(L.o_cd);
+    c.cd_lo = c.comp ? c.at<float>(L.o_cdl) : nullptr;
     rc = forward_sweep(c, fr, wavelet, cd, false, false);
     if (rc) return rc;
     if (cd_sim && L.n_rx > 0)
         CK(cudaMemcpyAsync(cd_sim, cd, (size_t)L.S * L.nt * L.n_rx * sizeof(float), cudaMemcpyDeviceToDevice, c.st));
     long long nl = 0;
     const int e0 = g_prof.mark(c.st);
-    CKL(launch_residual(cd, cd_obs, c.at<float>(L.o_kap), c.at<int>(L.o_rx), c.at<float>(L.o_asrc),
+    CKL(launch_residual(cd, c.comp ? c.at<float>(L.o_cdl) : nullptr, cd_obs, c.at<float>(L.o_kap),
+                        c.at<int>(L.o_rx), c.at<float>(L.o_asrc),
                         c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
     CKL(launch_misfit_sum(c.at<double>(L.o_part), misfit, L.n_maps, L.n_tx, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
@@ -1462,7 +1571,7 @@ int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float
         nl = 0;
         e0 = g_prof.mark(c.st);
         if (L.n_rx > 0) {
-            CKL(launch_residual(cd_bg, cd_obs, kap, rx, asrc, c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx,
+            CKL(launch_residual(cd_bg, nullptr, cd_obs, kap, rx, asrc, c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx,
                                 L.nt, L.slice, L.pitch, c.st));
             CKL(launch_hvp_source(cd_bg, cd_obs, dcd_out, kap, dkap, rx, asrc2, L.S, L.n_tx, L.n_rx, L.nt, L.slice,
                                   L.pitch, c.st));

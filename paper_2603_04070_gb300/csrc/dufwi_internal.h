@@ -121,6 +121,22 @@ struct StepParams {
                              // lies inside the physical grid (no memory variables); 2 only the others
 };
 
+// Compensated forward step (comp_step_kernel, 64 x 32 tiles): the field as hi + lo planes of FP32.
+//   hi_box, lo_box    U^n planes read with halo: dims (nxp, nzp, S), box 72 x 40 x 1
+//   hi_tile, lo_tile  U^{n-1} planes, updated in place to U^{n+1}: box 64 x 32 x 1
+//   kq_hi, kq_lo      kappa' / s_R as hi + lo: dims (nxp, nzp, n_maps), box 64 x 32 x 1
+struct CompMaps {
+    CUtensorMap hi_box, lo_box, hi_tile, lo_tile, kq_hi, kq_lo;
+};
+
+struct CompParams {
+    float *out_lo;           // low plane of U^{n-1} in, of U^{n+1} out (StepParams::out is the high plane)
+    float *cd_lo;            // low parts of the channel data [S][nt][n_rx], or null
+    const float4 *damp;      // [P + 1][P + 1]: (a - 2) hi, lo, (b + 1) hi, lo at layer depths (dz, dx)
+    float src_lo;            // low part of dt^2/dx^2 (StepParams::inj_scale is the high part)
+    float hist_scale;        // 1 / s_R: the history holds Lap(U^n) with the textbook weights
+};
+
 // Second-order products (the derivative of the vector-Jacobian product along an SoS direction):
 // tensor maps and extra arguments of so_step_kernel (64 x 32 tiles).
 struct SoMaps {
@@ -191,6 +207,15 @@ cudaError_t launch_so_combine(float *a, const float *b, const float *g, const fl
 cudaError_t launch_hvp_source(const float *cd_sim, const float *cd_obs, const float *dcd, const float *kap,
                               const float *dkap, const int *rx_node, float *asrc2, int S, int n_tx, int n_rx, int nt,
                               long long slice, int pitch, cudaStream_t st);
+// Compensated forward step (modes kFwdSample, kFwdSampleHist, kFwdHist; p.tile_z must be 32).
+cudaError_t launch_comp_step(int radius, int mode, const CompMaps &tm, const StepParams &p, const CompParams &q,
+                             cudaStream_t st);
+// s_R: the factor that makes the central weights of order `order` integers (0 for other orders).
+double comp_weight_scale(int order);
+// kq = kappa' / s_R on the padded grid (FP64, split into hi + lo), for the compensated step.
+cudaError_t launch_setup_kq(const float *sos, float *kq_hi, float *kq_lo, int n_maps, int Nx, int Nz, int P, int nzp,
+                            int pitch, double dt_over_dx, double weight_scale, double d0, double dt,
+                            const int2 *map_dims, cudaStream_t st);
 // kappa' on the padded grid; with a density map kappa' = rho C^2 dt^2/(dx^2 (1 + D dt)), and the
 // buoyancies bx, bz are written too (both may be null without a density map).
 // unit_b: no density map, but buoyancies of 1 between nodes are written (staggered operator
@@ -201,7 +226,8 @@ cudaError_t launch_setup_kappa(const float *sos, const float *density, float *ka
                                const int2 *map_dims, bool unit_b, cudaStream_t st);
 cudaError_t launch_sample(const float *field, const int *rx_node, float *cd, long long slice,
                           int pitch, int S, int n_tx, int n_rx, int nt, int step, cudaStream_t st);
-cudaError_t launch_residual(const float *cd_sim, const float *cd_obs, const float *kap,
+// cd_lo: low parts of the simulated traces (compensated forward steps), or null.
+cudaError_t launch_residual(const float *cd_sim, const float *cd_lo, const float *cd_obs, const float *kap,
                             const int *rx_node, float *asrc, double *partial, int *status,
                             int S, int n_tx, int n_rx, int nt, long long slice, int pitch,
                             cudaStream_t st);

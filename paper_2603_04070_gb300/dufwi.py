@@ -26,6 +26,7 @@ OK, ERR_INVALID_ARG, ERR_CFL, ERR_GEOMETRY, ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE = 5, 6, 7, 8
 SNAPSHOT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 BOUNDARIES = {"damping": 0, "cpml": 1}
+FORWARD_PRECISIONS = {"fp32": 0, "compensated": 1}
 OPT_TILE_Z = 1
 OPT_TWO_STEP = 2
 OPT_REUSE_TABLES = 3
@@ -46,7 +47,8 @@ class _Problem(ctypes.Structure):
                 ("pml_R", ctypes.c_double), ("pml_cref", ctypes.c_double),
                 ("fd_order", ctypes.c_int32), ("snapshot_dtype", ctypes.c_int32),
                 ("ckpt_interval", ctypes.c_int32), ("c_max", ctypes.c_double),
-                ("boundary", ctypes.c_int32), ("pml_alpha", ctypes.c_double)]
+                ("boundary", ctypes.c_int32), ("pml_alpha", ctypes.c_double),
+                ("forward_precision", ctypes.c_int32)]
 
 
 class _Array(ctypes.Structure):
@@ -134,11 +136,13 @@ class Problem:
     c_max: float = 1700.0
     boundary: str = "damping"          # "damping" (the term D of Eq. 1) or "cpml"
     pml_alpha: float = 0.0             # CPML frequency shift at the layer's inner edge (1/s)
+    forward_precision: str = "fp32"    # "fp32" or "compensated" (hi + lo FP32 planes, error-free steps)
 
     def c_struct(self) -> _Problem:
         return _Problem(self.nx, self.nz, self.dx, self.dt, self.nt, self.pml_cells, self.pml_R,
                         self.pml_cref, self.fd_order, SNAPSHOT_DTYPES[self.snapshot_dtype],
-                        self.ckpt_interval, self.c_max, BOUNDARIES[self.boundary], self.pml_alpha)
+                        self.ckpt_interval, self.c_max, BOUNDARIES[self.boundary], self.pml_alpha,
+                        FORWARD_PRECISIONS[self.forward_precision])
 
 
 class Geometry:

@@ -256,6 +256,8 @@ def test_binding_constants_match_the_header():
             assert d.SNAPSHOT_DTYPES[name[5:].lower()] == v, name
         elif name.startswith("BOUNDARY_"):
             assert d.BOUNDARIES[name[9:].lower()] == v, name
+        elif name.startswith("FORWARD_"):
+            assert d.FORWARD_PRECISIONS[name[8:].lower()] == v, name
         else:
             assert getattr(d, name) == v, name
 
@@ -276,3 +278,62 @@ def test_binding_argument_counts_match_the_header_prototypes():
             assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
             checked += 1
     assert checked >= 20
+
+
+def test_problem_struct_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of dufwi_problem has the C struct's size and field offsets (a C program
+    compiled against include/dufwi.h prints them), so no field is passed at the wrong place."""
+    import subprocess
+    d = _lib_module()
+    fields = [f[0] for f in d._Problem._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join('printf("%%s %%zu\\n", "%s", offsetof(dufwi_problem, %s));' % (f, f) for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dufwi.h"\nint main(void){%s'
+                   'printf("sizeof %%zu\\n", sizeof(dufwi_problem));return 0;}\n' % body)
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().split("\n") if line)
+    assert int(out.pop("sizeof")) == ctypes.sizeof(d._Problem)
+    for f in fields:
+        assert int(out[f]) == getattr(d._Problem, f).offset, f
+
+
+def test_compensated_forward_validation_and_sizing():
+    """The compensated forward mode adds two low planes, kappa' / s_R as hi + lo and the low
+    parts of the traces, and four-plane FP32 snapshots; it is refused on the host for the CPML,
+    the Born and second-order calls, a density map, and unknown precision values."""
+    d = _lib_module()
+    g = _geom(d)
+    field = 2 * (48 + 40) * ((64 + 40 + 7) // 8 * 8) * 4          # S x nzp x pitch floats, bytes
+    for grad in (False, True):
+        plain = d.workspace_size(_problem(d), g, 1, gradient=grad)
+        comp = d.workspace_size(_problem(d, forward_precision="compensated"), g, 1, gradient=grad)
+        assert comp >= plain + 2 * field + field                     # low planes + kq (two half-size maps)
+    # FP32 snapshots: four planes per segment instead of two
+    ck = dict(nt=2001, ckpt_interval=100)
+    gap_fp32 = (d.workspace_size(_problem(d, forward_precision="compensated", **ck), g, 1)
+                - d.workspace_size(_problem(d, **ck), g, 1))
+    gap_fp16 = (d.workspace_size(_problem(d, forward_precision="compensated", snapshot_dtype="fp16", **ck), g, 1)
+                - d.workspace_size(_problem(d, snapshot_dtype="fp16", **ck), g, 1))
+    assert gap_fp32 - gap_fp16 >= 20 * 2 * field
+    for kw in (dict(boundary="cpml"),):
+        with pytest.raises(d.DufwiError) as e:
+            d.workspace_size(_problem(d, forward_precision="compensated", **kw), g, 1)
+        assert e.value.status == d.ERR_UNSUPPORTED
+    for fn in (d.jvp_workspace_size, d.second_order_workspace_size):
+        with pytest.raises(d.DufwiError) as e:
+            fn(_problem(d, forward_precision="compensated"), g, 1)
+        assert e.value.status == d.ERR_UNSUPPORTED
+    bad = _problem(d).c_struct()
+    bad.forward_precision = 2
+    sh = g.c_structs()[1]
+    out = ctypes.c_size_t(0)
+    assert d._lib.dufwi_workspace_size(ctypes.byref(bad), ctypes.byref(sh), 1, ctypes.byref(out)) == d.ERR_INVALID_ARG
+    # a density map with the compensated steps: refused before any device work (dummy pointers)
+    pb = _problem(d, forward_precision="compensated")
+    arr, sh = g.c_structs()
+    c = pb.c_struct()
+    need = d.workspace_size(pb, g, 1, gradient=False)
+    fake = ctypes.c_void_p(1 << 20)
+    assert d._lib.dufwi_simulate(ctypes.byref(c), fake, fake, ctypes.byref(arr), fake, ctypes.byref(sh), 1,
+                                 fake, ctypes.c_void_p(1 << 20), need, None) == d.ERR_UNSUPPORTED

@@ -116,20 +116,6 @@ def test_gradient_linear_disk_full_size(d, seed):
     assert errs[2] <= GRAD_TOL
 
 
-def test_gradient_weak_scatterer_small_grid(d):
-    """A weak scatterer (residual below 1 % of the traces) on a 64 x 64 grid with checkpoints
-    every 50 steps: the plain 1e-4 gradient bound."""
-    wl = inputs.make_workload("linear_disk", seed=65, nx=64, nz=64, nt=400, n_elem=16, n_tx=2)
-    M_obs = _observed(wl)
-    J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0])
-    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=50)
-    ratio = np.linalg.norm(cd_ref - M_obs[0]) / np.linalg.norm(cd_ref)
-    assert ratio < 1e-2
-    assert rel_l2(cd[0], cd_ref) <= TRACE_TOL
-    assert abs(float(J[0]) - J_ref) <= MISFIT_TOL * J_ref
-    assert rel_l2(g[0], g_ref) <= GRAD_TOL
-
-
 @pytest.mark.parametrize("ckpt", [1, 37])
 def test_compensated_checkpointed_gradient_is_bit_identical_to_store_all(d, ckpt):
     """FP32 snapshots keep both planes of U^t and U^{t-1}, and the recompute runs the same

@@ -650,15 +650,16 @@ def test_unfolded_loop_block_training_reduces_sos_error(d):
     assert mse2 < mse0
 
 
-def test_gradient_error_model_for_weak_scatterers(d):
-    """A weak scatterer leaves a residual of ~0.5% of the traces. The FP32 gradient error then
-    follows the error model err <~ 1e-5 |M| / |r| (the ~1e-6 FP32 trace error, relative to the
-    residual), so it lands above 1e-4 but stays inside that model."""
+def test_gradient_weak_scatterer_meets_the_bound(d):
+    """A weak scatterer leaves a residual below 1 % of the traces. The gradient is linear in the
+    residual, so the FP32 forward's ~1e-6 trace error would reach it amplified by |M| / |r|; the
+    compensated forward steps (hi + lo planes) keep it within the plain 1e-4 bound."""
     wl = inputs.make_workload("linear_disk", seed=65, nx=64, nz=64, nt=400, n_elem=16, n_tx=2)
     M_obs = _observed(wl)
     J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0])
-    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=50)
+    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=50, forward_precision="compensated")
     ratio = np.linalg.norm(cd_ref - M_obs[0]) / np.linalg.norm(cd_ref)
     assert ratio < 1e-2
     assert rel_l2(cd[0], cd_ref) <= TRACE_TOL
-    assert rel_l2(g[0], g_ref) <= 1e-5 / ratio
+    assert abs(J[0] - J_ref) <= 1e-6 * J_ref
+    assert rel_l2(g[0], g_ref) <= GRAD_TOL

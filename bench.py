@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--two-step", type=int, default=None, help="1: two time steps per launch, 0: one")
     ap.add_argument("--persistent", type=int, default=None,
                     help="1: one cooperative launch per sweep segment, 0: one launch per step")
+    ap.add_argument("--multi-tile", type=int, default=None,
+                    help="1: multi-tile one-step kernel (co-resident CTAs, two-stage TMA loads), 0: one tile per CTA")
+    ap.add_argument("--forward-precision", default="fp32", choices=["fp32", "compensated"],
+                    help="forward steps in FP32, or compensated (hi + lo planes, error-free arithmetic)")
     ap.add_argument("--boundary", default="damping", choices=["damping", "cpml"],
                     help="absorbing layer: the damping term of Eq. 1 or a convolutional PML (keeps every step)")
     ap.add_argument("--density", action="store_true",
@@ -226,6 +230,8 @@ def workload_config(wl, args):
             "l2": "flushed between timed steps (256 MiB write outside the events)",
             "tile": [64, 32 if getattr(args, "persistent_used", 0) else args.tile_z_used],
             "two_step": args.two_step_used, "persistent": getattr(args, "persistent_used", 0),
+            "multi_tile": getattr(args, "multi_tile_used", 0),
+            "forward_precision": getattr(args, "forward_precision", "fp32"),
             "density": ("variable: water-like background + smooth field + 1-3 rods of 1050-1900 kg/m^3, "
                         "staggered operator" if getattr(args, "density", False) else "constant"),
             "boundary": getattr(args, "boundary", "damping")}
@@ -249,13 +255,16 @@ def run_ours(args):
         dufwi.set_option(dufwi.OPT_TWO_STEP, args.two_step)
     if args.persistent is not None:
         dufwi.set_option(dufwi.OPT_PERSISTENT, args.persistent)
+    if args.multi_tile is not None:
+        dufwi.set_option(dufwi.OPT_MULTI_TILE, args.multi_tile)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
     if args.boundary == "cpml":
         args.ckpt = 0          # the CPML memory variables are not checkpointed: keep every step
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
                        ckpt_interval=args.ckpt, c_max=2000.0 if args.boundary == "cpml" else wl.c_max,
-                       boundary=args.boundary, pml_alpha=math.pi * float(wl.meta.get("f0", 2e6)))
+                       boundary=args.boundary, pml_alpha=math.pi * float(wl.meta.get("f0", 2e6)),
+                       forward_precision=args.forward_precision)
     geom = dufwi.Geometry.from_workload(wl)
     sos_true = torch.from_numpy(wl.sos_true).to(dev)
     sos = torch.from_numpy(wl.sos_start).to(dev)
@@ -279,6 +288,7 @@ def run_ours(args):
     args.tile_z_used = dufwi.get_option(dufwi.OPT_TILE_Z)
     args.two_step_used = dufwi.get_option(dufwi.OPT_TWO_STEP)
     args.persistent_used = dufwi.get_option(dufwi.OPT_PERSISTENT)
+    args.multi_tile_used = dufwi.get_option(dufwi.OPT_MULTI_TILE)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

@@ -364,6 +364,11 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     counters rely on all CTAs of the launch being resident: do not run other kernels on the
  *     device at the same time (another stream, another process). If residency is lost the
  *     bounded waits end the launch with DUFWI_ERR_TIMEOUT in the status word.
+ *   DUFWI_OPT_MULTI_TILE: 1 runs the one-step kernel in its multi-tile form: a grid of as many
+ *     CTAs as the device holds at once, each walking 64 x 32 tiles of all shots with two
+ *     shared-memory stages, so the loads of the next tile overlap the arithmetic of the current
+ *     one; bit-identical to the one-tile-per-CTA form. Not used with the two-step or persistent
+ *     kernels, a density map, the CPML or the compensated forward steps.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device
@@ -374,6 +379,7 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
 #define DUFWI_OPT_REUSE_TABLES 3
 #define DUFWI_OPT_PERSISTENT 4
 #define DUFWI_OPT_TEST_STALL 5
+#define DUFWI_OPT_MULTI_TILE 6
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

@@ -117,6 +117,7 @@ int g_reuse_tables = 0;
 int g_tile_z = kTileZDefault;
 int g_two_step = 0;
 int g_persistent = 0;   // DUFWI_OPT_PERSISTENT: one cooperative launch per sweep segment
+int g_multi_tile = 0;   // DUFWI_OPT_MULTI_TILE: the multi-tile one-step kernel (64 x 32 tiles)
 std::atomic<int> g_test_stall{0};   // DUFWI_OPT_TEST_STALL: the next persistent sweep stalls on purpose
 
 // NVTX range over the host code that enqueues one part of a call (visible in timeline tools).
@@ -404,6 +405,7 @@ struct Ctx {
     bool cpml = false;                        // convolutional PML instead of the damping term
     bool so = false;                          // second-order call (dufwi_second_order)
     bool comp = false;                        // compensated forward steps (hi + lo planes)
+    bool multi_tile = false;                  // multi-tile one-step kernel (two-stage TMA pipeline)
     float *cd_lo = nullptr;                   // compensated: low parts of the traces of the current sweep
     CompParams cq;                            // compensated: constant arguments of the step
     FieldMaps lomap[2];                       // compensated: maps of the low planes of the forward ring
@@ -497,7 +499,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd && !c.so && !c.comp;
     c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd && !c.so && !c.comp;
     c.mem_par = 0;
-    c.tz = (c.vd || c.persistent || c.so || c.comp) ? 32 : g_tile_z;
+    c.multi_tile = g_multi_tile != 0 && !c.two_step && !c.persistent && !c.vd && !c.so && !c.comp;
+    c.tz = (c.vd || c.persistent || c.so || c.comp || c.multi_tile) ? 32 : g_tile_z;
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
     std::vector<int> sorted1, sorted2, sortede;
@@ -780,6 +783,8 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
         tm.bx_tile = c.bx1;
         tm.bz_tile = c.bz1;
         CKL(launch_step_vd(c.L.radius, mode, tm, p, c.st));
+    } else if (c.multi_tile) {
+        CKL(launch_step_mt(c.L.radius, mode, tm, p, c.st));
     } else {
         CKL(launch_step(c.L.radius, mode, tm, p, c.st));
     }
@@ -989,6 +994,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_persistent = value;
         return DUFWI_OK;
+    case DUFWI_OPT_MULTI_TILE:
+        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
+        g_multi_tile = value;
+        return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL:
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_test_stall = value;
@@ -1003,6 +1012,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     switch (option) {
     case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
     case DUFWI_OPT_PERSISTENT: *value = g_persistent; return DUFWI_OK;
+    case DUFWI_OPT_MULTI_TILE: *value = g_multi_tile; return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL: *value = g_test_stall.load(); return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;

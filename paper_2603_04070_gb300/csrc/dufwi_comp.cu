@@ -30,8 +30,6 @@
 // textbook weights, for the imaging condition) is written rounded to FP32.
 #include "dufwi_internal.h"
 
-#include <atomic>
-
 #include "../../include/dufwi.h"
 #include "dufwi_device.cuh"
 
@@ -329,27 +327,11 @@ __global__ void setup_kq_kernel(const float *sos, float *kq_hi, float *kq_lo, in
     kq_lo[o] = static_cast<float>(v - static_cast<double>(hi));
 }
 
-// Per-device configuration of a kernel's shared-memory attributes (done once per device).
-template <typename K>
-cudaError_t configure_once(K kernel, std::atomic<uint64_t> &done)
-{
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const uint64_t bit = 1ull << (dev & 63);
-    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCompBytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
-    return e;
-}
-
 template <int R, int MODE>
 cudaError_t launch_comp_rm(const CompMaps &tm, const StepParams &p, const CompParams &q, cudaStream_t st)
 {
-    static std::atomic<uint64_t> done{0};
-    cudaError_t e = configure_once(comp_step_kernel<R, MODE>, done);
+    static DeviceCache dc;
+    cudaError_t e = configure_kernel(comp_step_kernel<R, MODE>, kCompBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kCompTileZ - 1) / kCompTileZ, p.n_maps * p.n_tx);

@@ -37,6 +37,10 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, ui
         : "memory");
 }
 
+// Orders this thread's earlier accesses (generic proxy) before later TMA (async proxy) accesses.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void raise_status(int *status, int code)
 {
     if (status) atomicMax(status, code);

@@ -18,7 +18,58 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace dufwi {
+
+// Kernel attributes (dynamic shared memory, carveout) and resident-CTA counts belong to a device:
+// launchers keep them per device index, so a process may drive several GPUs and several host
+// threads may launch at once (a repeated attribute call is harmless; the cached values are the
+// same whichever thread stores them).
+constexpr int kMaxDevices = 64;
+
+struct DeviceCache {
+    std::atomic<uint64_t> configured{0};        // bit d: attributes set on device d
+    std::atomic<int> resident[kMaxDevices] = {};  // co-resident CTAs on device d (0: not computed)
+};
+
+template <typename K>
+inline cudaError_t configure_kernel(K kernel, uint32_t smem_bytes, DeviceCache &dc, int *device = nullptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (device) *device = dev;
+    const uint64_t bit = 1ull << dev;
+    if (dc.configured.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) dc.configured.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+// CTAs of `kernel` (threads per CTA, dynamic shared memory) that fit on the current device at once.
+template <typename K>
+inline cudaError_t resident_ctas(K kernel, int threads, uint32_t smem_bytes, DeviceCache &dc, int *out)
+{
+    int dev = 0;
+    cudaError_t e = configure_kernel(kernel, smem_bytes, dc, &dev);
+    if (e != cudaSuccess) return e;
+    int n = dc.resident[dev].load(std::memory_order_acquire);
+    if (n == 0) {
+        int sms = 0, per_sm = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem_bytes)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        n = per_sm * sms;
+        dc.resident[dev].store(n, std::memory_order_release);
+    }
+    *out = n;
+    return cudaSuccess;
+}
 
 constexpr int kTileX = 64;                    // output tile width (x, contiguous)
 constexpr int kHalo = 4;                      // halo loaded on every side (max stencil radius)
@@ -183,6 +234,9 @@ struct SweepParams {
 
 // Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.
 cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
+// Multi-tile form of the one-step kernel (64 x 32 tiles, a grid of co-resident CTAs walking all
+// tiles with two-stage TMA loads); same modes and results as launch_step with tile height 32.
+cudaError_t launch_step_mt(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 // Two time steps per launch (core tiles 64 x 32; see step2_kernel).
 cudaError_t launch_step2(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 constexpr int kPairTileZ = 32;   // core tile height of the two-step kernel (64 x 32 tiles)

@@ -359,6 +359,188 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     }
 }
 
+// Multi-tile form of the one-step kernel. A grid of G CTAs (as many as fit on the device at
+// once) walks the 64 x 32 tiles of all shots: CTA b takes tiles t = b, b + G, b + 2G, ... (t runs
+// over shots, then tile rows, then tile columns). Two shared-memory stages, each with its own
+// mbarrier, hold the operands of two tiles: the TMA loads of tile i + 1 are issued before tile i
+// is computed, so their latency overlaps the arithmetic instead of being exposed once per CTA as
+// in the one-tile-per-CTA form, and the tiles are spread evenly over the CTAs (no partial last
+// wave). The arithmetic, injections, sampling and stores per tile are those of step_kernel with
+// TZ = 32, so the results are bit-identical.
+template <int R, int MODE>
+__global__ void __launch_bounds__(128, (MODE == kAdjoint || MODE == kBorn) ? 2 : 4)
+step_mt_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
+{
+    using TL = TileLayout<MODE, 32>;
+    constexpr int TZ = 32;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ alignas(8) uint64_t bar[2];
+    __shared__ InjList inj;
+
+    const int tid = threadIdx.x;
+    const int tiles_x = (p.nxp + kTileX - 1) / kTileX;
+    const int per_shot = tiles_x * ((p.nzp + TZ - 1) / TZ);
+    const int total = p.n_maps * p.n_tx * per_shot;
+    const int G = gridDim.x;
+    const bool early = MODE != kBorn && p.early;
+
+    // tile t -> shot, origin and row-major tile index within the shot; false for tiles outside the
+    // shot's own grid (sized calls), which have nothing to do
+    auto locate = [&](int t, int &s, int &x0, int &z0, int &tile) {
+        s = t / per_shot;
+        tile = t - s * per_shot;
+        x0 = (tile % tiles_x) * kTileX;
+        z0 = (tile / tiles_x) * TZ;
+        const MapGrid g = map_grid(p, s / p.n_tx);
+        return x0 < g.nxp && z0 < g.nzp;
+    };
+    auto stage_base = [&](int k) { return smem + k * TL::kFloats; };
+    // thread 0: the loads of tile t into stage k (part 1: operands no launch of the last two wrote;
+    // part 2: the box of U^n and, in the adjoint, the imaging sums)
+    auto issue = [&](int t, int k, bool part1, bool part2) {
+        int s, x0, z0, tile;
+        locate(t, s, x0, z0, tile);
+        float *box = stage_base(k), *pv = box + TL::kBox, *kp = pv + TL::kTile, *hs = kp + TL::kTile;
+        float *gg = hs + TL::kTile;
+        if (part1) {
+            tma_load_3d(pv, &tm.out_tile, &bar[k], x0, z0, s);
+            tma_load_3d(kp, &tm.kap_tile, &bar[k], x0, z0, s / p.n_tx);
+            if (MODE == kAdjoint) tma_load_4d_stream(hs, &tm.hist_tile, &bar[k], x0, z0, s, p.hist_slot);
+            if (MODE == kBorn) {
+                tma_load_4d(hs, &tm.hist_tile, &bar[k], x0, z0, s, p.hist_slot);
+                tma_load_3d(gg, &tm.grad_tile, &bar[k], x0, z0, s / p.n_tx);
+            }
+        }
+        if (part2) {
+            tma_load_3d(box, &tm.cur_box, &bar[k], x0 - kHalo, z0 - kHalo, s);
+            if (MODE == kAdjoint) tma_load_3d(gg, &tm.grad_tile, &bar[k], x0, z0, s);
+        }
+    };
+
+    if (tid == 0) {
+        prefetch_tensormap(&tm.cur_box);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();   // barriers initialised before any thread polls them
+    int s0, x00, z00, tile0;
+    const bool first_valid = blockIdx.x < total && locate(blockIdx.x, s0, x00, z00, tile0);
+    if (tid == 0 && first_valid) {
+        mbar_arrive_expect_tx(&bar[0], TL::kBytes);
+        if (early) issue(blockIdx.x, 0, true, false);
+    }
+    grid_dependency_wait();
+    if (tid == 0 && first_valid) issue(blockIdx.x, 0, !early, true);
+    grid_dependents_launch();
+
+    uint32_t parity = 0;   // bit k: phase parity of the next completion of stage k
+    const int lx = (tid & 15) * 4;
+    const int lz = (tid >> 4) * 4;
+    int i = 0;
+    for (int t = blockIdx.x; t < total; t += G, ++i) {
+        const int k = i & 1;
+        // the loads of the next tile go to the other stage, which the previous iteration released
+        const int tn = t + G;
+        int sn, xn, zn, tilen;
+        const bool next_valid = tn < total && locate(tn, sn, xn, zn, tilen);
+        if (tid == 0 && next_valid) {
+            fence_proxy_async_shared();
+            mbar_arrive_expect_tx(&bar[k ^ 1], TL::kBytes);
+            issue(tn, k ^ 1, true, true);
+        }
+        int s, x0, z0, tile;
+        if (!locate(t, s, x0, z0, tile)) {
+            __syncthreads();
+            continue;
+        }
+        const int tx_idx = s % p.n_tx;
+        const long long shot_off = static_cast<long long>(s) * p.slice;
+        const MapGrid mg = map_grid(p, s / p.n_tx);
+        float *box = stage_base(k), *pv = box + TL::kBox, *kp = pv + TL::kTile, *hs = kp + TL::kTile;
+        float *gg = hs + TL::kTile;
+
+        int2 rx_range = make_int2(0, 0);
+        if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * per_shot + tile);
+        if (MODE == kBorn) {
+            if (tid == 0) inj.n = 0;
+        } else {
+            gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ,
+                                    kTileX, tid, TL::kThreadsPerCta);
+        }
+        const int gx = x0 + lx;
+        const bool interior = region_interior(p, mg, x0, z0, kTileX, TZ);
+        int xd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xd[q] = layer_depth(gx + q, p.P, mg.Nx);
+
+        const uint32_t pk = (parity >> k) & 1u;
+        const int fail = !mbar_wait_bounded(&bar[k], pk);
+        if (__syncthreads_or(fail)) {   // also publishes the injection list
+            if (tid == 0) raise_status(p.status, DUFWI_ERR_TIMEOUT);
+            mbar_wait_bounded(&bar[k], pk);                                        // copies still in flight
+            if (next_valid) mbar_wait_bounded(&bar[k ^ 1], (parity >> (k ^ 1)) & 1u);
+            return;
+        }
+        parity ^= 1u << k;
+
+        const bool col_ok = gx < mg.nxp;
+        float4 lap[4], ctr[4], nxt[4];
+        lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int lo = (lz + j) * kTileX + lx;
+            nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
+                             p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+            if (MODE == kBorn) nxt[j] = fma4(ld4s(gg + lo), ld4s(hs + lo), nxt[j]);
+        }
+        if (MODE != kBorn && inj.n > 0) {   // block-uniform: stage the rows, inject, reload
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
+            __syncthreads();
+            if (tid == 0)
+                apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX,
+                                       TZ, kTileX, 0, TZ * kTileX);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gz = z0 + lz + j;
+            if (!col_ok || gz >= mg.nzp) continue;
+            float4 nv = nxt[j], lv = lap[j];
+            if (gx + 4 > mg.nxp) {
+                if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
+                if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
+                nv.w = 0.f; lv.w = 0.f;
+            }
+            const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+            st4(p.out + o, nv);
+            if (MODE == kFwdSampleHist || MODE == kFwdHist) st4_stream(p.hist + o, lv);
+            if (MODE == kAdjoint) {
+                const int lo = (lz + j) * kTileX + lx;
+                st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+            }
+        }
+        if (MODE == kFwdSample || MODE == kFwdSampleHist || MODE == kBorn) {
+            const int cnt = (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
+            for (int e = tid; e < cnt; e += TL::kThreadsPerCta) {
+                const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
+                const int node = (r >= 0 && r < p.n_rx) ? __ldg(p.smp_node + tx_idx * p.n_rx + r) : -1;
+                const int zn2 = node >> 16, xn2 = node & 0xffff;
+                if (node < 0 || zn2 < z0 || zn2 >= z0 + TZ || xn2 < x0 || xn2 >= x0 + kTileX) {
+                    raise_status(p.status, DUFWI_ERR_GEOMETRY);
+                    continue;
+                }
+                p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
+                    box[(zn2 - z0 + kHalo) * kBoxX + (xn2 - x0 + kHalo)];
+            }
+        }
+        __syncthreads();   // stage k and the injection list are free for reuse
+    }
+}
+
 // </one-step kernel source>
 
 // ---- second-order products ---------------------------------------------------------------------
@@ -1242,8 +1424,6 @@ __device__ __forceinline__ void st_release(int *ptr, int v)
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ int ld_relaxed(const int *ptr)
 {
@@ -1929,16 +2109,9 @@ template <int R, int MODE, int TZ>
 static cudaError_t launch_step_rmt(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
     using TL = TileLayout<MODE, TZ>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<R, MODE, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             TL::kBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(step_kernel<R, MODE, TZ>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceCache dc;   // shared-memory attributes, set once per device
+    cudaError_t e = configure_kernel(step_kernel<R, MODE, TZ>, TL::kBytes, dc);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + TZ - 1) / TZ, p.n_maps * p.n_tx);
     cfg.blockDim = dim3(TL::kThreadsPerCta);
@@ -1975,22 +2148,53 @@ static cudaError_t launch_step_r(int mode, const StepMaps &tm, const StepParams 
     }
 }
 
+template <int R, int MODE>
+static cudaError_t launch_step_mt_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    using TL = TileLayout<MODE, 32>;
+    constexpr uint32_t kBytes = 2 * TL::kBytes;   // two stages
+    static DeviceCache dc;
+    int resident = 0;
+    cudaError_t e = resident_ctas(step_mt_kernel<R, MODE>, TL::kThreadsPerCta, kBytes, dc, &resident);
+    if (e != cudaSuccess) return e;
+    const long long tiles = static_cast<long long>((p.nxp + kTileX - 1) / kTileX) * ((p.nzp + 31) / 32) *
+                            p.n_maps * p.n_tx;
+    if (tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(std::min<long long>(tiles, resident)));
+    cfg.blockDim = dim3(TL::kThreadsPerCta);
+    cfg.dynamicSmemBytes = kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step_mt_kernel<R, MODE>, tm, p);
+}
+
+template <int R>
+static cudaError_t launch_step_mt_r(int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    switch (mode) {
+    case kFwdSample: return launch_step_mt_rm<R, kFwdSample>(tm, p, st);
+    case kFwdSampleHist: return launch_step_mt_rm<R, kFwdSampleHist>(tm, p, st);
+    case kFwdHist: return launch_step_mt_rm<R, kFwdHist>(tm, p, st);
+    case kAdjoint: return launch_step_mt_rm<R, kAdjoint>(tm, p, st);
+    case kBorn: return launch_step_mt_rm<R, kBorn>(tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // </one-step kernel source>
 
 template <int R, int MODE>
 static cudaError_t launch_step2_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
     using PL = PairLayout<MODE>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step2_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             PL::kBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(step2_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceCache dc;   // shared-memory attributes, set once per device
+    cudaError_t e = configure_kernel(step2_kernel<R, MODE>, PL::kBytes, dc);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kPairZ - 1) / kPairZ, p.n_maps * p.n_tx);
     cfg.blockDim = dim3(kPairThreads);
@@ -2032,23 +2236,10 @@ static cudaError_t launch_sweep_rm(const SweepMaps &tm, const StepParams &p, con
                                    cudaStream_t st)
 {
     using TL = TileLayout<MODE, 32>;
-    static int max_ctas = 0;   // co-resident CTAs of this variant on the device of the first call
-    if (max_ctas == 0) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             TL::kBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(sweep_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, MODE>, 128, TL::kBytes)) !=
-            cudaSuccess)
-            return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        max_ctas = per_sm * sms;
-    }
+    static DeviceCache dc;   // attributes and co-resident CTAs of this variant, per device
+    int max_ctas = 0;
+    cudaError_t e = resident_ctas(sweep_kernel<R, MODE>, 128, TL::kBytes, dc, &max_ctas);
+    if (e != cudaSuccess) return e;
     const long long items = static_cast<long long>(sp.n_steps) * sp.tiles;
     if (items >= (1ll << 31)) return cudaErrorInvalidValue;
     // Items of one round (grid consecutive items) must not depend on each other, or the round
@@ -2101,16 +2292,9 @@ static cudaError_t launch_step_cpml_rm(const StepMaps &tm, const CpmlMaps &cm, c
                                        const CpmlParams &cp, cudaStream_t st)
 {
     using CL = CpmlLayout<MODE>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(cpml_step_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             CL::kBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(cpml_step_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceCache dc;   // shared-memory attributes, set once per device
+    cudaError_t e = configure_kernel(cpml_step_kernel<R, MODE>, CL::kBytes, dc);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_maps * p.n_tx);
     cfg.blockDim = dim3(128);
@@ -2154,16 +2338,9 @@ template <int R, int MODE>
 static cudaError_t launch_step_vd_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
     using VL = VdLayout<MODE>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(vd_step_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             VL::kBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(vd_step_kernel<R, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceCache dc;   // shared-memory attributes, set once per device
+    cudaError_t e = configure_kernel(vd_step_kernel<R, MODE>, VL::kBytes, dc);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_maps * p.n_tx);
     cfg.blockDim = dim3(128);
@@ -2206,16 +2383,9 @@ template <int R, int KIND>
 static cudaError_t launch_so_step_rk(const SoMaps &tm, const StepParams &p, const SoParams &q, cudaStream_t st)
 {
     using SL = SoLayout<KIND>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(so_step_kernel<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SL::kBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(so_step_kernel<R, KIND>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static DeviceCache dc;   // shared-memory attributes, set once per device
+    cudaError_t e = configure_kernel(so_step_kernel<R, KIND>, SL::kBytes, dc);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + 31) / 32, p.n_maps * p.n_tx);
     cfg.blockDim = dim3(128);
@@ -2282,6 +2452,18 @@ cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepPara
     case 2: return launch_step_r<2>(mode, tm, p, st);
     case 3: return launch_step_r<3>(mode, tm, p, st);
     case 4: return launch_step_r<4>(mode, tm, p, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step_mt(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st)
+{
+    if (p.tile_z != 32) return cudaErrorInvalidValue;
+    switch (radius) {
+    case 1: return launch_step_mt_r<1>(mode, tm, p, st);
+    case 2: return launch_step_mt_r<2>(mode, tm, p, st);
+    case 3: return launch_step_mt_r<3>(mode, tm, p, st);
+    case 4: return launch_step_mt_r<4>(mode, tm, p, st);
     default: return cudaErrorInvalidValue;
     }
 }

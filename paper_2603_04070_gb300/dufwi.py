@@ -32,6 +32,7 @@ OPT_TWO_STEP = 2
 OPT_REUSE_TABLES = 3
 OPT_PERSISTENT = 4
 OPT_TEST_STALL = 5
+OPT_MULTI_TILE = 6
 
 
 class DufwiError(RuntimeError):

@@ -338,6 +338,58 @@ def test_two_step_kernel_is_bit_identical_to_one_step(d, ckpt):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("ckpt,order,nx,nz,n_tx,n_maps", [(0, 8, 90, 77, 3, 2), (9, 8, 150, 61, 2, 1),
+                                                          (25, 4, 33, 20, 1, 1), (7, 6, 300, 260, 4, 2)])
+def test_multi_tile_kernel_is_bit_identical_to_one_step(d, ckpt, order, nx, nz, n_tx, n_maps):
+    """The multi-tile form (co-resident CTAs walking the tiles with two-stage TMA loads) runs the
+    per-tile arithmetic of the one-tile-per-CTA form with 32-row tiles: traces, misfit and
+    gradient are identical bit for bit, for grids smaller and larger than one wave of CTAs, and
+    for the Born step."""
+    wl = inputs.make_workload("linear_disk", seed=13 + order, nx=nx, nz=nz, nt=180, n_elem=min(20, nx // 4),
+                              n_tx=n_tx, n_maps=n_maps)
+    wl.fd_order = order
+    M_obs = _observed(wl)
+    geom = d.Geometry.from_workload(wl)
+    out = []
+    for mt in (0, 1):
+        d.set_option(d.OPT_MULTI_TILE, mt)
+        try:
+            pb = _dufwi_problem(d, wl, ckpt_interval=ckpt)
+            sos = torch.from_numpy(wl.sos_true).cuda()
+            w = torch.from_numpy(wl.wavelet).cuda()
+            cd = d.simulate(pb, sos, w, geom, check=True).cpu().numpy()
+            J, g, cds = _gpu_grad(d, wl, M_obs, ckpt_interval=ckpt)
+            dsos = torch.from_numpy(np.random.default_rng(order).standard_normal(wl.sos_true.shape)
+                                    .astype(np.float32)).cuda()
+            jv = d.jvp(pb, sos, w, geom, dsos).cpu().numpy()
+            out.append((cd, J, g, cds, jv))
+        finally:
+            d.set_option(d.OPT_MULTI_TILE, 0)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_multi_tile_kernel_sized_batch_is_bit_identical(d):
+    """Uneven grids in one call: tiles outside a map's grid are skipped inside the tile walk."""
+    wl, sizes = inputs.sized_batch(seed=4, sizes=[(96, 80), (64, 48), (130, 70)], nt=160, n_elem=16, n_tx=2)
+    geom = d.Geometry.from_workload(wl)
+    out = []
+    for mt in (0, 1):
+        d.set_option(d.OPT_MULTI_TILE, mt)
+        try:
+            pb = _dufwi_problem(d, wl, ckpt_interval=30)
+            sos = torch.from_numpy(wl.sos_true).cuda()
+            w = torch.from_numpy(wl.wavelet).cuda()
+            cd = d.simulate(pb, sos, w, geom, check=True, sizes=sizes)
+            J, g = d.misfit_gradient(pb, torch.from_numpy(wl.sos_start).cuda(), w, geom, cd * 1.01, check=True,
+                                     sizes=sizes)
+            out.append((cd.cpu().numpy(), J.cpu().numpy(), g.cpu().numpy()))
+        finally:
+            d.set_option(d.OPT_MULTI_TILE, 0)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("ckpt,order,nx,nz,n_tx,n_maps", [(0, 8, 90, 77, 3, 2), (40, 8, 150, 61, 2, 1),
                                                           (25, 4, 33, 20, 1, 1)])
 def test_persistent_sweeps_are_bit_identical(d, ckpt, order, nx, nz, n_tx, n_maps):

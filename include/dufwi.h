@@ -175,6 +175,18 @@ int dufwi_misfit_gradient(const dufwi_problem *pb, const float *sos, const float
                           float *cd_sim, void *workspace, size_t workspace_bytes,
                           void *stream /* cudaStream_t */);
 
+/* dufwi_misfit_gradient with the gradient written in FP64: grad is [n_maps][nz][nx] double. The
+ * per-shot imaging sums are FP32 as always; the sum over transmits, the fold of the absorbing layer
+ * and the 2/C scaling are FP64 in both calls, and this one skips the final rounding to FP32. A
+ * caller that splits the transmits of a map across devices sums these partial gradients in FP64
+ * (Eqs. 5-6 are sums over transmits) and rounds once at the end. Same support as
+ * dufwi_misfit_gradient. */
+int dufwi_misfit_gradient_fp64(const dufwi_problem *pb, const float *sos, const float *density,
+                               const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                               int32_t n_maps, const float *cd_obs, double *misfit, double *grad,
+                               float *cd_sim, void *workspace, size_t workspace_bytes,
+                               void *stream /* cudaStream_t */);
+
 /* Forward model that keeps what the adjoint needs: the same channel data as dufwi_simulate, plus
  * the snapshots (every ckpt_interval steps) or the whole history, stored in `workspace`. The
  * workspace must hold dufwi_workspace_size bytes. Pair it with dufwi_backward, which turns any
@@ -289,15 +301,28 @@ int dufwi_hvp(const dufwi_problem *pb, const float *sos, const float *density, c
  *   - Size limit: problems whose dufwi_simulate_workspace_size exceeds the array are rejected with
  *     DUFWI_ERR_WORKSPACE before any device work.
  *   - First call on a device: it looks up the array's device address with that device current,
- *     then caches it. Make this first call before any stream capture.
+ *     then caches it. With lazy module loading (the CUDA default since 12.2) that lookup is also
+ *     what loads the library's device code holding the array, so the first call on each device
+ *     does reserve the array's memory and may synchronise. Make one warm-up call per device at
+ *     start-up, before the phase that must not allocate and before any stream capture.
  *   - Sharing: all calls share the array, which keeps the last call's contents. Every buffer that
  *     must start at zero is cleared by the call itself. Calls that overlap on the GPU (other
  *     streams or host threads without ordering between them) race on the array.
+ *   - Device-side conditions (an SoS value that is not finite or above c_max, an invalid density,
+ *     a bounded wait that ran out) land in the status word at the start of the array, as they do
+ *     in a caller's workspace; dufwi_noalloc_status reads it.
  * The call allocates no device memory: no cudaMalloc, no cudaFree, no allocating library call. */
 #define DUFWI_NOALLOC_SCRATCH_BYTES (64u << 20)
 int dufwi_simulate_noalloc(const dufwi_problem *pb, const float *sos, const float *density,
                            const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
                            int32_t n_maps, float *cd, void *stream /* cudaStream_t */);
+
+/* Device status of the last dufwi_simulate_noalloc call on the current device (the counterpart of
+ * dufwi_workspace_status for the static array; the paper has none). It copies the status word
+ * into host memory on `stream` and synchronises that stream, so call it after the simulation,
+ * on the same stream. Returns the DUFWI_* code recorded by the kernels (DUFWI_OK if none), or
+ * DUFWI_ERR_CUDA if the copy fails. It allocates nothing. */
+int dufwi_noalloc_status(void *stream /* cudaStream_t */);
 
 /* Maps of different sizes in one call (batching of uneven grids, Eq. 4 over many maps). The
  * problem's nx, nz define an envelope. Map b has its own physical grid nz[b] x nx[b] (1 <= nx[b]

@@ -1174,7 +1174,7 @@ int gradient_forward(Ctx &c, const float *wavelet)
 
 // Second half: reverse sweep driven by the scaled adjoint source already in the workspace
 // (kappa'_r times dJ/dM), recomputing each checkpoint segment, then the fold into grad.
-int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad)
+int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad, double *grad64 = nullptr)
 {
     const Layout &L = c.L;
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
@@ -1234,12 +1234,17 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
     // (2/C) scaling, fold of the absorbing layer, FP64 reduction over transmits
     nl = 0;
     e0 = g_prof.mark(c.st);
-    CKL(launch_fold(g_shot, sos, grad, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
+    CKL(launch_fold(g_shot, sos, grad, grad64, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
                     c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.st));
     ++nl;
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
     return DUFWI_OK;
 }
+
+int misfit_gradient_impl(const dufwi_problem *pb, const dufwi_map_sizes *sizes, const float *sos,
+                         const float *density, const dufwi_array *arr, const float *wavelet,
+                         const dufwi_shots *shots, int32_t n_maps, const float *cd_obs, double *misfit, float *grad,
+                         double *grad64, float *cd_sim, void *workspace, size_t workspace_bytes, void *stream);
 
 int gradient_setup(Ctx &c, const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
                    const float *wavelet, const dufwi_shots *shots, int32_t n_maps, void *workspace,
@@ -1270,12 +1275,38 @@ int dufwi_misfit_gradient_sized(const dufwi_problem *pb, const dufwi_map_sizes *
                                 const dufwi_shots *shots, int32_t n_maps, const float *cd_obs, double *misfit,
                                 float *grad, float *cd_sim, void *workspace, size_t workspace_bytes, void *stream)
 {
+    if (!grad) return DUFWI_ERR_INVALID_ARG;
+    return misfit_gradient_impl(pb, sizes, sos, density, arr, wavelet, shots, n_maps, cd_obs, misfit, grad, nullptr,
+                                cd_sim, workspace, workspace_bytes, stream);
+}
+
+int dufwi_misfit_gradient_fp64(const dufwi_problem *pb, const float *sos, const float *density,
+                               const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots,
+                               int32_t n_maps, const float *cd_obs, double *misfit, double *grad, float *cd_sim,
+                               void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!grad) return DUFWI_ERR_INVALID_ARG;
+    return misfit_gradient_impl(pb, nullptr, sos, density, arr, wavelet, shots, n_maps, cd_obs, misfit, nullptr, grad,
+                                cd_sim, workspace, workspace_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace dufwi {
+namespace {
+
+// Body of the gradient entry points: grad (FP32) or grad64 (FP64) receives the gradient.
+int misfit_gradient_impl(const dufwi_problem *pb, const dufwi_map_sizes *sizes, const float *sos,
+                         const float *density, const dufwi_array *arr, const float *wavelet,
+                         const dufwi_shots *shots, int32_t n_maps, const float *cd_obs, double *misfit, float *grad,
+                         double *grad64, float *cd_sim, void *workspace, size_t workspace_bytes, void *stream)
+{
     Ctx c;
     c.sizes = sizes;
     Layout chk;
     int rc = make_layout(pb, shots, n_maps, kLayoutGradient, &chk);
     if (rc) return rc;
-    if ((!cd_obs && chk.n_rx > 0) || !misfit || !grad) return DUFWI_ERR_INVALID_ARG;
+    if ((!cd_obs && chk.n_rx > 0) || !misfit || (!grad && !grad64)) return DUFWI_ERR_INVALID_ARG;
     rc = gradient_setup(c, pb, sos, density, arr, wavelet, shots, n_maps, workspace, workspace_bytes, stream);
     if (rc) return rc;
     const Layout &L = c.L;
@@ -1292,8 +1323,13 @@ int dufwi_misfit_gradient_sized(const dufwi_problem *pb, const dufwi_map_sizes *
                         c.at<double>(L.o_part), c.status(), L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
     CKL(launch_misfit_sum(c.at<double>(L.o_part), misfit, L.n_maps, L.n_tx, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
-    return gradient_reverse(c, sos, wavelet, grad);
+    return gradient_reverse(c, sos, wavelet, grad, grad64);
 }
+
+}  // namespace
+}  // namespace dufwi
+
+extern "C" {
 
 int dufwi_misfit(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
                  const float *wavelet, const dufwi_shots *shots, int32_t n_maps, const float *cd_obs,
@@ -1643,11 +1679,11 @@ int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float
     nl = 0;
     e0 = g_prof.mark(c.st);
     CKL(launch_so_combine(accA, accB, accG, sos, dsos, L.S, L.n_tx, L.Nx, L.Nz, L.P, L.nzp, L.pitch, L.slice, c.st));
-    CKL(launch_fold(accA, sos, so, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
+    CKL(launch_fold(accA, sos, so, nullptr, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
                     nullptr, c.st));
     ++nl;
     if (grad) {
-        CKL(launch_fold(accG, sos, grad, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
+        CKL(launch_fold(accG, sos, grad, nullptr, c.at<double>(L.o_fold), L.n_maps, L.n_tx, L.Nx, L.Nz, L.P, L.slice, L.pitch,
                         nullptr, c.st));
         ++nl;
     }

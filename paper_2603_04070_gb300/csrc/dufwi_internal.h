@@ -293,8 +293,10 @@ cudaError_t launch_cotangent_source(const float *cd_grad, const float *kap, cons
                                    cudaStream_t st);
 cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps, int n_tx,
                               cudaStream_t st);
-cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *fx, int n_maps, int n_tx,
-                        int Nx, int Nz, int P, long long slice, int pitch, const int2 *map_dims, cudaStream_t st);
+// grad64 (when not null) receives the gradient in FP64 instead of grad (FP32).
+cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *grad64, double *fx, int n_maps,
+                        int n_tx, int Nx, int Nz, int P, long long slice, int pitch, const int2 *map_dims,
+                        cudaStream_t st);
 cudaError_t launch_snap_absmax(const float *cur, const float *prev, unsigned *scale_bits, int S,
                                long long slice, int nxp, int nzp, int pitch, cudaStream_t st);
 cudaError_t launch_snap_store(const float *cur, const float *prev, void *snap_u, void *snap_d,

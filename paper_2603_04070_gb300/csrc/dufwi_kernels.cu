@@ -2009,7 +2009,8 @@ __global__ void fold_x_kernel(const float *g_shot, double *fx, int n_tx, int NxE
     fx[(static_cast<long long>(b) * nzpE + zp) * NxE + ix] = acc;
 }
 
-__global__ void fold_z_kernel(const double *fx, const float *sos, float *grad, int NxE, int NzE, int P, int nzpE,
+template <typename T>
+__global__ void fold_z_kernel(const double *fx, const float *sos, T *grad, int NxE, int NzE, int P, int nzpE,
                               const int2 *map_dims)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2018,11 +2019,11 @@ __global__ void fold_z_kernel(const double *fx, const float *sos, float *grad, i
     if (ix >= NxE) return;
     const int Nx = map_dims ? map_dims[b].x : NxE, Nz = map_dims ? map_dims[b].y : NzE;
     const long long o = (static_cast<long long>(b) * NzE + iz) * NxE + ix;
-    if (ix >= Nx || iz >= Nz) { grad[o] = 0.f; return; }   // outside this map (sized calls)
+    if (ix >= Nx || iz >= Nz) { grad[o] = T(0); return; }   // outside this map (sized calls)
     const int zlo = iz == 0 ? 0 : iz + P, zhi = iz == Nz - 1 ? Nz + 2 * P - 1 : iz + P;
     double acc = 0.0;
     for (int z = zlo; z <= zhi; ++z) acc += fx[(static_cast<long long>(b) * nzpE + z) * NxE + ix];
-    grad[o] = static_cast<float>(acc * (2.0 / static_cast<double>(sos[o])));
+    grad[o] = static_cast<T>(acc * (2.0 / static_cast<double>(sos[o])));
 }
 
 // ---- checkpoint snapshots -------------------------------------------------------------------
@@ -2524,15 +2525,21 @@ cudaError_t launch_misfit_sum(const double *partial, double *misfit, int n_maps,
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *fx, int n_maps, int n_tx, int Nx,
-                        int Nz, int P, long long slice, int pitch, const int2 *map_dims, cudaStream_t st)
+cudaError_t launch_fold(const float *g_shot, const float *sos, float *grad, double *grad64, double *fx, int n_maps,
+                        int n_tx, int Nx, int Nz, int P, long long slice, int pitch, const int2 *map_dims,
+                        cudaStream_t st)
 {
     const int nzp = Nz + 2 * P;
     fold_x_kernel<<<dim3((Nx + 127) / 128, nzp, n_maps), 128, 0, st>>>(g_shot, fx, n_tx, Nx, P, nzp, slice, pitch,
                                                                        map_dims);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    fold_z_kernel<<<dim3((Nx + 127) / 128, Nz, n_maps), 128, 0, st>>>(fx, sos, grad, Nx, Nz, P, nzp, map_dims);
+    if (grad64)
+        fold_z_kernel<double><<<dim3((Nx + 127) / 128, Nz, n_maps), 128, 0, st>>>(fx, sos, grad64, Nx, Nz, P, nzp,
+                                                                                   map_dims);
+    else
+        fold_z_kernel<float><<<dim3((Nx + 127) / 128, Nz, n_maps), 128, 0, st>>>(fx, sos, grad, Nx, Nz, P, nzp,
+                                                                                 map_dims);
     return cudaGetLastError();
 }
 

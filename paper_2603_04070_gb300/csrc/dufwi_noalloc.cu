@@ -61,3 +61,17 @@ extern "C" int dufwi_simulate_noalloc(const dufwi_problem *pb, const float *sos,
     return dufwi_simulate(pb, sos, density, arr, wavelet, shots, n_maps, cd, scratch,
                           (size_t)DUFWI_NOALLOC_SCRATCH_BYTES, stream);
 }
+
+// The status word is the first int of the scratch array (the layout puts it at offset 0 of every
+// workspace). Reading it allocates nothing: a pageable host int and a stream synchronisation.
+extern "C" int dufwi_noalloc_status(void *stream)
+{
+    void *scratch = nullptr;
+    int rc = scratch_address(&scratch);
+    if (rc) return rc;
+    int h = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&h, scratch, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DUFWI_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return DUFWI_ERR_CUDA;
+    return h;
+}

@@ -86,10 +86,12 @@ def _load():
     lib.dufwi_simulate.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
     lib.dufwi_misfit_gradient.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, sz, vp]
     lib.dufwi_misfit.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, sz, vp]
+    lib.dufwi_misfit_gradient_fp64.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, sz, vp]
     lib.dufwi_profile_enable.argtypes = [ctypes.c_int]
     lib.dufwi_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.dufwi_launch_count.restype = ctypes.c_int64
     lib.dufwi_simulate_noalloc.argtypes = [P, vp, vp, A, vp, S, ctypes.c_int32, vp, vp]
+    lib.dufwi_noalloc_status.argtypes = [vp]
     M = ctypes.POINTER(_MapSizes)
     lib.dufwi_simulate_sized.argtypes = [P, M, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, sz, vp]
     lib.dufwi_misfit_gradient_sized.argtypes = [P, M, vp, vp, A, vp, S, ctypes.c_int32, vp, vp, vp, vp, vp, sz, vp]
@@ -279,14 +281,15 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 def simulate_noalloc(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, *,
                      density: torch.Tensor | None = None, cd: torch.Tensor | None = None,
-                     stream=None) -> torch.Tensor:
+                     stream=None, check: bool = False) -> torch.Tensor:
     """Channel data as ``simulate``, through ``dufwi_simulate_noalloc``.
 
     That entry point is for callers that must not allocate device memory while running, e.g. a
     fixed-latency acquisition loop or an application that owns all device memory through its
     own pool. It takes its scratch space from a static 64 MiB array inside the library, instead
     of a workspace. All calls share that array, so calls that overlap on the GPU race. Only the
-    output ``cd`` is allocated here, and only when the caller does not pass one.
+    output ``cd`` is allocated here, and only when the caller does not pass one. ``check``
+    reads the device status word (``dufwi_noalloc_status``) and raises on a device-side error.
     """
     n_maps = sos.shape[0]
     _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
@@ -304,7 +307,14 @@ def simulate_noalloc(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor,
                                      density.data_ptr() if density is not None else None, ctypes.byref(arr),
                                      wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd.data_ptr(), _stream(stream))
     _check(rc, "dufwi_simulate_noalloc")
+    if check:
+        _check(noalloc_status(stream), "dufwi_simulate_noalloc (device)")
     return cd
+
+
+def noalloc_status(stream=None) -> int:
+    """Status word of the last ``simulate_noalloc`` on the current device (synchronises ``stream``)."""
+    return int(_lib.dufwi_noalloc_status(_stream(stream)))
 
 
 def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry,
@@ -314,7 +324,9 @@ def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, 
                     workspace: torch.Tensor | None = None, stream=None, check: bool = False, sizes=None):
     """Misfit ``J [n_maps]`` (float64) and gradient ``dJ/dC [n_maps][nz][nx]`` (Eqs. 5-6).
 
-    ``sizes``: optional per-map physical grids inside the envelope (``dufwi_misfit_gradient_sized``)."""
+    ``sizes``: optional per-map physical grids inside the envelope (``dufwi_misfit_gradient_sized``).
+    A float64 ``grad`` selects ``dufwi_misfit_gradient_fp64`` (the FP64 cross-transmit sum and fold
+    without the final rounding to FP32; uniform calls only)."""
     n_maps = sos.shape[0]
     _dev_tensor(sos, "sos", torch.float32, (n_maps, problem.nz, problem.nx))
     wshape = (geom.n_tx, problem.nt) if geom.wavelet_per_tx else (problem.nt,)
@@ -328,7 +340,10 @@ def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, 
     if grad is None:
         grad = torch.empty_like(sos)
     _dev_tensor(misfit, "misfit", torch.float64, (n_maps,))
-    _dev_tensor(grad, "grad", torch.float32, sos.shape)
+    grad64 = isinstance(grad, torch.Tensor) and grad.dtype == torch.float64
+    if grad64 and sizes is not None:
+        raise ValueError("a float64 gradient is available for uniform calls only")
+    _dev_tensor(grad, "grad", torch.float64 if grad64 else torch.float32, sos.shape)
     if return_cd and cd_sim is None:
         cd_sim = torch.empty(cshape, dtype=torch.float32, device=sos.device)
     if cd_sim is not None:
@@ -340,7 +355,9 @@ def misfit_gradient(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, 
             ctypes.byref(arr), wavelet.data_ptr(), ctypes.byref(sh), n_maps, cd_obs.data_ptr(),
             misfit.data_ptr(), grad.data_ptr(), cd_sim.data_ptr() if cd_sim is not None else None,
             workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream(stream))
-    if sizes is None:
+    if grad64:
+        rc = _lib.dufwi_misfit_gradient_fp64(ctypes.byref(pb), *args)
+    elif sizes is None:
         rc = _lib.dufwi_misfit_gradient(ctypes.byref(pb), *args)
     else:
         ms, _keep = _sizes_struct(sizes, n_maps)

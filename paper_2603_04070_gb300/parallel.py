@@ -44,7 +44,9 @@ def shard_transmits(n_tx: int, world: int, rank: int) -> range:
 
 def gradient_allreduce(misfit: torch.Tensor, grad: torch.Tensor, group=None):
     """Sum per-rank partial misfits [B] and gradients [B, nz, nx] over ranks in FP64 (the one
-    collective of transmit sharding). Returns (misfit FP64, gradient FP32) on the inputs' device."""
+    collective of transmit sharding). Partial gradients may come in FP64 (the library's FP64
+    output) or FP32; the sum is FP64 and is rounded to FP32 once, at the end. Returns (misfit FP64,
+    gradient FP32) on the inputs' device."""
     if not dist.is_available() or not dist.is_initialized():
         return misfit.to(torch.float64), grad.to(torch.float32)
     m = misfit.to(torch.float64).contiguous()
@@ -55,8 +57,11 @@ def gradient_allreduce(misfit: torch.Tensor, grad: torch.Tensor, group=None):
 
 
 def _cuda_compute(problem, sos, wavelet, geom, cd_obs):
+    """The rank's partial misfit and gradient, the gradient left in FP64 (dufwi_misfit_gradient_fp64),
+    so that the sum over ranks is FP64 from the library's cross-transmit sum to the final rounding."""
     from . import dufwi
-    return dufwi.misfit_gradient(problem, sos, wavelet, geom, cd_obs)
+    grad = torch.empty(sos.shape, dtype=torch.float64, device=sos.device)
+    return dufwi.misfit_gradient(problem, sos, wavelet, geom, cd_obs, grad=grad)
 
 
 def _transmit_shard(geom, wavelet, cd_obs, group):

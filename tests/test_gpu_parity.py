@@ -223,6 +223,27 @@ def test_gradient_batched_maps(d):
         assert rel_l2(g[b], g_ref) <= GRAD_TOL
 
 
+def test_fp64_gradient_output(d):
+    """dufwi_misfit_gradient_fp64 skips only the final rounding: its gradient rounded to FP32 is the
+    FP32 call's gradient bit for bit, its misfit is the same, and it matches the oracle."""
+    wl = inputs.make_workload("linear_disk", seed=10, nx=70, nz=58, nt=400, n_elem=18, n_tx=3, n_maps=2)
+    M_obs = _observed(wl)
+    pb = _dufwi_problem(d, wl, ckpt_interval=40)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    w = torch.from_numpy(wl.wavelet).cuda()
+    obs = torch.from_numpy(M_obs).cuda()
+    J32, g32 = d.misfit_gradient(pb, sos, w, geom, obs, check=True)
+    g64 = torch.empty(sos.shape, dtype=torch.float64, device="cuda")
+    J64, g64 = d.misfit_gradient(pb, sos, w, geom, obs, grad=g64, check=True)
+    assert g64.dtype == torch.float64
+    assert torch.equal(J32, J64)
+    assert torch.equal(g64.float(), g32)
+    for b in range(wl.n_maps):
+        _, g_ref, _ = _oracle_grad(wl, wl.sos_start[b], M_obs[b])
+        assert rel_l2(g64[b].cpu().numpy(), g_ref) <= GRAD_TOL
+
+
 @pytest.mark.parametrize("dtype,tol", [("fp16", 6e-3), ("bf16", 6e-2)])
 def test_compressed_snapshots(d, dtype, tol):
     """BF16/FP16 snapshots with per-snapshot power-of-two max-abs scaling: traces and misfit are

@@ -59,6 +59,13 @@ def _oracle_compute64(problem, sos, wavelet, geom, cd_obs):
                                cd_obs[b].double().numpy())[1] for b in range(sos.shape[0])]))
 
 
+def _oracle_compute_fp64(problem, sos, wavelet, geom, cd_obs):
+    """(J, g) of this rank's transmits with g left in FP64, as the library's FP64 gradient output
+    (dufwi_misfit_gradient_fp64) hands it to the sharded sum."""
+    J, _ = _oracle_compute(problem, sos, wavelet, geom, cd_obs)
+    return J, _oracle_compute64(problem, sos, wavelet, geom, cd_obs)
+
+
 def _oracle_hvp(problem, sos, wavelet, geom, cd_obs, v):
     """(H v, J, g) of this rank's transmits: central differences (FP64) of the oracle gradient
     along v."""
@@ -88,10 +95,11 @@ def _worker(rank, world, port, out_path):
     try:
         pb, geom, sos, w, obs = _case()
         J, g = parallel.sharded_misfit_gradient(pb, sos, w, geom, obs, compute=_oracle_compute)
+        J64, g64 = parallel.sharded_misfit_gradient(pb, sos, w, geom, obs, compute=_oracle_compute_fp64)
         v = torch.from_numpy(np.random.default_rng(5).standard_normal(tuple(sos.shape))) * 5.0
         hv, J2, g2 = parallel.sharded_hvp(pb, sos, w, geom, obs, v, compute=_oracle_hvp)
         if rank == 0:
-            torch.save({"J": J, "g": g, "hv": hv, "J2": J2, "g2": g2, "v": v}, out_path)
+            torch.save({"J": J, "g": g, "g64": g64, "hv": hv, "J2": J2, "g2": g2, "v": v}, out_path)
     finally:
         dist.destroy_process_group()
 
@@ -112,6 +120,12 @@ def test_transmit_sharded_gradient_on_two_gloo_ranks(tmp_path):
     J_ref, g_ref = _oracle_compute(pb, sos, w, geom, obs)
     assert torch.allclose(res["J"], J_ref, rtol=1e-12, atol=0)
     assert torch.allclose(res["g"], g_ref, rtol=1e-5, atol=1e-6 * float(g_ref.abs().max()))
+    # FP64 partials: the sum is FP64 to the end and rounded once, so it is the whole-set FP64
+    # gradient rounded to FP32, up to one unit in the last place from the FP64 summation order
+    g64_ref = _oracle_compute64(pb, sos, w, geom, obs)
+    assert res["g64"].dtype == torch.float32
+    ulp = torch.abs(torch.nextafter(g64_ref.float(), torch.tensor(float("inf"))) - g64_ref.float())
+    assert bool((res["g64"] - g64_ref.float()).abs().le(ulp).all())
     # the HVP split: the per-rank products (and misfits, gradients) sum to the whole-set ones
     hv_ref, _, _ = _oracle_hvp(pb, sos, w, geom, obs, res["v"])
     assert torch.allclose(res["J2"], J_ref, rtol=1e-12, atol=0)

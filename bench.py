@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-store-all", action="store_true",
                     help="skip the store-all (no checkpoint) comparison measured beside the headline")
+    ap.add_argument("--no-scale", action="store_true",
+                    help="skip the 1024x1024, 64-transmit, 12000-step gradient measured beside the headline")
     return ap.parse_args()
 
 
@@ -135,13 +137,16 @@ STEP_KERNEL_MARK = ("// <one-step kernel source>\n", "// </one-step kernel sourc
 
 
 def step_kernel_source_sha256() -> str:
-    """SHA-256 of the one-step kernel's source: the marked regions of dufwi_kernels.cu (its
-    device helpers, the kernel and its launchers), concatenated in file order."""
-    src = os.path.join(ROOT, "paper_2603_04070_gb300", "csrc", "dufwi_kernels.cu")
-    with open(src) as f:
+    """SHA-256 of the one-step kernel's source: the shared device primitives (dufwi_device.cuh)
+    and the marked regions of dufwi_kernels.cu (its helpers, the kernels and their launchers),
+    concatenated in file order."""
+    csrc = os.path.join(ROOT, "paper_2603_04070_gb300", "csrc")
+    with open(os.path.join(csrc, "dufwi_device.cuh")) as f:
+        header = f.read()
+    with open(os.path.join(csrc, "dufwi_kernels.cu")) as f:
         text = f.read()
     b, e = STEP_KERNEL_MARK
-    parts, pos = [], 0
+    parts, pos = [header], 0
     while True:
         i = text.find(b, pos)
         if i < 0:
@@ -165,6 +170,81 @@ def kernel_traffic(kind: str, key: str = "per_launch_dram_bytes_full_size"):
         return rec.get(key, {}).get(kind)
     except Exception:
         return None
+
+
+def scale_traffic():
+    """Per-launch DRAM bytes of the step kernel on the 1024 x 1024 workload (profiles/
+    ncu_traffic_scale.json), if taken on the current one-step kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic_scale.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("step_kernel_source_sha256") != step_kernel_source_sha256():
+            return None
+        return rec.get("per_launch_dram_bytes_full_size")
+    except Exception:
+        return None
+
+
+def measure_scale(dufwi, inputs, dev, flush, stream, peak):
+    """The 1024 x 1024, 64-transmit, 12000-step gradient with FP16 snapshots every 100 steps: its
+    live set (fields, kappa' and imaging sums of 64 shots, ~1.5 GB) is far above the 129 MB L2, so
+    this is the measurement where HBM bandwidth, not L2, is the bound. One untimed short call warms
+    the kernels; one full gradient is timed with CUDA events."""
+    import torch
+    wl = inputs.make_workload("scale", seed=0)
+    pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
+                       pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype="fp16", ckpt_interval=100,
+                       c_max=wl.c_max)
+    geom = dufwi.Geometry.from_workload(wl)
+    sos_true = torch.from_numpy(wl.sos_true).to(dev)
+    sos = torch.from_numpy(wl.sos_start).to(dev)
+    wav = torch.from_numpy(wl.wavelet).to(dev)
+    obs = dufwi.simulate(pb, sos_true, wav, geom, check=True)
+    nbytes = dufwi.workspace_size(pb, geom, 1)
+    free, _ = torch.cuda.mem_get_info(dev)
+    if nbytes > 0.8 * free:
+        return {"skipped": "workspace of %.1f GB does not fit the free %.1f GB" % (nbytes / 1e9, free / 1e9)}
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    misfit = torch.empty(1, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(sos)
+    pb_short = dufwi.Problem(**{**pb.__dict__, "nt": 300})
+    dufwi.misfit_gradient(pb_short, sos, wav[:300].contiguous(), geom, obs[:, :, :300].contiguous(), misfit=misfit,
+                          grad=grad, workspace=ws)
+    torch.cuda.synchronize()
+    dufwi.profile_enable(True)
+    dufwi.profile_read(reset=True)
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    dufwi.misfit_gradient(pb, sos, wav, geom, obs, misfit=misfit, grad=grad, workspace=ws)
+    b.record(stream)
+    torch.cuda.synchronize()
+    prof = dufwi.profile_read(reset=True)
+    dufwi.profile_enable(False)
+    status = dufwi.workspace_status(ws)
+    ms = a.elapsed_time(b)
+    cells = wl.padded_cells
+    S = wl.n_tx
+    kinds = ["forward", "recompute", "adjoint"]
+    dom = max(kinds, key=lambda k: prof[k]["ms"])
+    avg_ms = prof[dom]["ms"] / max(prof[dom]["launches"], 1)
+    bytes_per_launch = ALGO_BYTES[dom] * cells * S
+    traffic = scale_traffic()
+    rec = {"workload": "scale: %dx%d grid (+%d absorbing cells per side), %d steps, %d elements, %d transmits, "
+                       "%d receivers, checkpointed adjoint (every 100 steps, FP16 snapshots)"
+                       % (wl.nx, wl.nz, wl.pml, wl.nt, wl.elem_ix.size, wl.n_tx, wl.n_rx),
+           "ms_per_gradient": ms, "value": 2.0 * cells * wl.nt * S / (ms / 1e3) / 1e9, "unit": UNIT,
+           "hbm_roofline_frac_40B": GRADIENT_BYTES_PER_CELL * cells * wl.nt * S / (peak * 1e9) / (ms / 1e3),
+           "workspace_gb": nbytes / 1e9, "status": dufwi.status_string(status),
+           "sweep_ms": {k: prof[k]["ms"] for k in kinds + ["other"]},
+           "dominant": {"kernel": "step_kernel (%s sweep)" % dom, "avg_launch_us": 1e3 * avg_ms,
+                        "algorithmic_bytes_per_launch": bytes_per_launch,
+                        "achieved_gbs": bytes_per_launch / (avg_ms / 1e3) / 1e9,
+                        "frac": bytes_per_launch / (avg_ms / 1e3) / 1e9 / peak,
+                        "dram_bytes_per_launch": traffic.get(dom) if traffic else None}}
+    del ws
+    return rec
 
 
 def cpu_oracle_sample(wl, n_steps: int):
@@ -438,6 +518,11 @@ def run_ours(args):
                          "note": "same gradient with the history of every step kept in HBM (ckpt_interval 0)"}
             del ws_all
 
+    scale = None
+    if not args.no_scale and args.workload == "full_shot_set" and not (args.density or cpml) \
+            and args.forward_precision == "fp32":
+        scale = measure_scale(dufwi, inputs, dev, flush, stream, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         steps = wl.nt
@@ -454,7 +539,7 @@ def run_ours(args):
                 "hbm_roofline_frac_40B": hbm_frac, "ms_per_gradient": ms_step,
                 "ms_per_dufwi_iteration": ms_step + net_ms, "ms_update_net": net_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-                "store_all": store_all,
+                "store_all": store_all, "scale": scale,
                 "clocks": clk.summary(), "profile_complete": prof["complete"]}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -308,6 +308,45 @@ def test_gradient_full_shot_set_grid_single_transmit(d):
     assert rel_l2(g[0], g_ref) <= GRAD_TOL
 
 
+def test_gradient_full_shot_set_all_transmits(d):
+    """The headline launch exactly: 512 x 512, 6000 steps, all 16 transmits and 128 receivers in one
+    call, checkpoint interval 100, FP32 snapshots; the FP64 cross-transmit reduction (Eqs. 4-6)
+    against the oracle's gradient over the same 16 transmits (about 4 min of host time)."""
+    wl = inputs.make_workload("full_shot_set", seed=0)
+    assert (wl.n_tx, wl.n_rx, wl.nt) == (16, 128, 6000)
+    M_obs = _observed(wl)
+    J_ref, g_ref, cd_ref = _oracle_grad(wl, wl.sos_start[0], M_obs[0], ckpt=100)
+    J, g, cd = _gpu_grad(d, wl, M_obs, ckpt_interval=100)
+    errs = (rel_l2(cd[0], cd_ref), abs(float(J[0]) - J_ref) / J_ref, rel_l2(g[0], g_ref))
+    print("full shot set, 16 transmits: traces %.2e misfit %.2e gradient %.2e" % errs)
+    assert errs[0] <= TRACE_TOL
+    assert errs[1] <= 1e-4
+    assert errs[2] <= GRAD_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp32", "compensated"])
+def test_gradient_cell_by_cell_on_a_tiny_grid(d, precision):
+    """Every cell of a 14 x 12 gradient against the oracle, not only the field norm: the edge cells
+    carry the fold of the 20-cell absorbing layer (and the corners that of two strips), so an error
+    confined to the layer or the fold would show there. Bound: max |g - g_ref| <= 1e-4 max |g_ref|,
+    over the interior, the edge rows and columns, and the corners separately."""
+    wl = inputs.make_workload("linear_disk", seed=21, nx=14, nz=12, nt=260, n_elem=4, n_tx=2)
+    wl.sos_start = (wl.sos_start + np.random.default_rng(2).uniform(-20, 20, wl.sos_start.shape)).astype(np.float32)
+    M_obs = _observed(wl)
+    _, g_ref, _ = _oracle_grad(wl, wl.sos_start[0], M_obs[0])
+    _, g, _ = _gpu_grad(d, wl, M_obs, ckpt_interval=31, forward_precision=precision)
+    err = np.abs(g[0].astype(np.float64) - g_ref)
+    scale = np.abs(g_ref).max()
+    edge = np.zeros(g_ref.shape, bool)
+    edge[0, :] = edge[-1, :] = edge[:, 0] = edge[:, -1] = True
+    corners = np.zeros(g_ref.shape, bool)
+    corners[0, 0] = corners[0, -1] = corners[-1, 0] = corners[-1, -1] = True
+    for name, mask in (("interior", ~edge), ("edges", edge & ~corners), ("corners", corners)):
+        worst = err[mask].max() / scale
+        print("%s %s: max cell error / max |g| = %.2e" % (precision, name, worst))
+        assert worst <= 1e-4, name
+
+
 def test_simulate_full_shot_set_sampled_transmits(d):
     """All 16 transmits of the 512 x 512, 6000-step workload in one call (the benchmark's launch
     configuration); two sampled transmits are recomputed by the oracle."""

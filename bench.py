@@ -68,6 +68,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-store-all", action="store_true",
                     help="skip the store-all (no checkpoint) comparison measured beside the headline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch options instead of tuning them on a short gradient probe")
+    ap.add_argument("--hybrid-gb", type=float, default=40.0,
+                    help="workspace budget (GB) of the hybrid-history gradient measured beside the headline "
+                         "(0: skip)")
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the 1024x1024, 64-transmit, 12000-step gradient measured beside the headline")
     return ap.parse_args()
@@ -365,6 +370,18 @@ def run_ours(args):
     def step():
         dufwi.misfit_gradient(pb, sos, wav, geom, obs, density=rho, misfit=misfit, grad=grad, workspace=ws)
 
+    # launch options: tuned on a short gradient probe unless forced on the command line
+    tuned = None
+    forced = any(v is not None for v in (args.tile_z, args.two_step, args.persistent, args.multi_tile))
+    if not forced and not args.no_autotune and not (args.density or args.boundary == "cpml") \
+            and args.forward_precision == "fp32":
+        from paper_2603_04070_gb300 import autotune
+        tuned = autotune.tune(pb, sos, wav, geom, gradient=True, cd_obs=obs, steps=300, repeats=2)
+        tuned = {"chosen": {k: tuned[k] for k in autotune.KNOBS},
+                 "candidates": [{**c, "ms_per_step": t} for c, t in zip(tuned["candidates"],
+                                                                          tuned["candidates_ms_per_step"])],
+                 "probe": "misfit gradient, 300 steps, checkpoints every 75 steps, 2 repeats per candidate"}
+
     args.tile_z_used = dufwi.get_option(dufwi.OPT_TILE_Z)
     args.two_step_used = dufwi.get_option(dufwi.OPT_TWO_STEP)
     args.persistent_used = dufwi.get_option(dufwi.OPT_PERSISTENT)
@@ -518,6 +535,48 @@ def run_ours(args):
                          "note": "same gradient with the history of every step kept in HBM (ckpt_interval 0)"}
             del ws_all
 
+    # hybrid history: as many of the last checkpoint segments keep their history as fit the budget
+    hybrid = None
+    if args.hybrid_gb > 0 and args.ckpt > 0 and not cpml:
+        from paper_2603_04070_gb300 import autotune
+        budget = int(args.hybrid_gb * 1e9)
+        k = autotune.kept_segments_for_budget(pb, geom, wl.n_maps, budget)
+        if k > 0:
+            pb_h = dufwi.Problem(**{**pb.__dict__, "kept_segments": k})
+            nbytes = dufwi.workspace_size(pb_h, geom, wl.n_maps)
+            free, _ = torch.cuda.mem_get_info(dev)
+            if nbytes < 0.8 * free:
+                ws_h = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+                def step_h():
+                    dufwi.misfit_gradient(pb_h, sos, wav, geom, obs, density=rho, misfit=misfit, grad=grad,
+                                          workspace=ws_h)
+
+                step_h()
+                torch.cuda.synchronize()
+                dufwi.profile_enable(True)
+                dufwi.profile_read(reset=True)
+                evs = []
+                for _ in range(max(2, min(args.steps, 3))):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    step_h()
+                    b.record(stream)
+                    evs.append((a, b))
+                torch.cuda.synchronize()
+                prof_h = dufwi.profile_read(reset=True)
+                dufwi.profile_enable(False)
+                ms_h = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+                n_seg = (wl.nt - 1 + args.ckpt - 1) // args.ckpt
+                hybrid = {"ms_per_step": ms_h, "value": units_per_step / (ms_h / 1e3) / 1e9, "unit": UNIT,
+                          "budget_gb": args.hybrid_gb, "workspace_gb": nbytes / 1e9, "kept_segments": k,
+                          "segments": n_seg,
+                          "sweep_ms_per_step": {kk: prof_h[kk]["ms"] / len(evs) for kk in kinds + ["other"]},
+                          "note": "checkpointed every %d steps; the last %d of %d segments keep their history "
+                                  "from the forward sweep, the others are recomputed" % (args.ckpt, k, n_seg)}
+                del ws_h
+
     scale = None
     if not args.no_scale and args.workload == "full_shot_set" and not (args.density or cpml) \
             and args.forward_precision == "fp32":
@@ -539,7 +598,7 @@ def run_ours(args):
                 "hbm_roofline_frac_40B": hbm_frac, "ms_per_gradient": ms_step,
                 "ms_per_dufwi_iteration": ms_step + net_ms, "ms_update_net": net_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-                "store_all": store_all, "scale": scale,
+                "store_all": store_all, "hybrid": hybrid, "scale": scale, "autotune": tuned,
                 "clocks": clk.summary(), "profile_complete": prof["complete"]}
         print(json.dumps(line), flush=True)
     if world > 1:

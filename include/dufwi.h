@@ -81,7 +81,20 @@ typedef struct {
     int32_t boundary;        /* DUFWI_BOUNDARY_*: absorbing layer of the pml_cells border cells */
     double  pml_alpha;       /* CPML only: frequency shift at the layer's inner edge (1/s), >= 0 */
     int32_t forward_precision; /* DUFWI_FORWARD_*: arithmetic of the forward (and recompute) steps */
+    int32_t kept_segments;   /* gradient calls with checkpoints: how many of the last checkpoint
+                              * segments keep their history from the forward sweep (0 = recompute
+                              * every segment; >= the segment count = keep all, no snapshots) */
 } dufwi_problem;
+
+/* Hybrid history (kept_segments = k > 0 with ckpt_interval K > 0): the forward sweep writes the
+ * history Lap(U^n) of the last k segments of K steps as it goes and takes snapshots only at the
+ * starts of the earlier ones. The reverse sweep runs the adjoint straight through the kept
+ * segments, then recomputes each earlier segment from its snapshot into the slots the kept
+ * segments have freed. The history ring holds max(k, 1) segments, so the workspace grows by
+ * (k - 1) K fields of S x (nz + 2P) x pitch floats, less the snapshots of the kept segments, and
+ * each kept segment saves one recompute of K steps. The results are bit-identical to keeping
+ * every step (the recompute reproduces the forward sweep exactly with FP32 snapshots).
+ * dufwi_misfit, dufwi_jvp and the second-order calls ignore it. */
 
 /* Arithmetic of the forward steps (the simulation of Eqs. 2-3, and the recompute of checkpoint
  * segments). The adjoint and the imaging condition run in FP32 in both modes.
@@ -394,6 +407,10 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     shared-memory stages, so the loads of the next tile overlap the arithmetic of the current
  *     one; bit-identical to the one-tile-per-CTA form. Not used with the two-step or persistent
  *     kernels, a density map, the CPML or the compensated forward steps.
+ *   DUFWI_OPT_EARLY_LOADS: 1 (default) lets a one-step launch request the operands that neither
+ *     of the two previous launches wrote (U^{n-1}, kappa', the adjoint's history tile) before it
+ *     waits for the previous launch (programmatic dependent launch); 0 requests everything after
+ *     the wait. Same results either way.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device
@@ -405,6 +422,7 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
 #define DUFWI_OPT_PERSISTENT 4
 #define DUFWI_OPT_TEST_STALL 5
 #define DUFWI_OPT_MULTI_TILE 6
+#define DUFWI_OPT_EARLY_LOADS 7
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

@@ -1,12 +1,18 @@
-"""Autotuner for the step-kernel launch options (tile height, one or two steps per launch, one
-launch per step or one persistent launch per sweep segment).
+"""Autotuner for the step-kernel launch options and for the history split of gradients.
 
-For a given problem shape the tuner times a short forward simulation (or, for callers whose
-work is gradients, a short misfit gradient) with each candidate option set, on the caller's
-device, and keeps the fastest. Results are cached per (GPU name,
-grid, shots, stencil order): in memory, and optionally in a JSON file. The options change
-speed only: every candidate produces bit-identical results, which the tests check for the
-one/two-step pair and the per-step/persistent pair.
+Launch options: the tile height of the one-step kernel (64 x 32 or 64 x 64), its multi-tile form
+(co-resident CTAs walking the tiles with two-stage TMA loads), early requests of the operands the
+previous two launches did not write (on or off), two steps per launch, and one persistent launch
+per sweep segment. For a given problem shape the tuner times a short forward simulation (or, for
+callers whose work is gradients, a short misfit gradient) with each candidate, on the caller's
+device, and keeps the fastest. Results are cached per (GPU name, grid, shots, stencil order): in
+memory, and optionally in a JSON file. The options change speed only: every candidate produces
+bit-identical results (tests check each pair against the default).
+
+History split: ``kept_segments_for_budget`` picks how many checkpoint segments keep their
+history from the forward sweep (each one saves the recompute of a segment) so that the gradient's
+workspace stays within a memory budget; more kept segments never cost time, so the largest count
+that fits is the fastest.
 """
 from __future__ import annotations
 
@@ -18,12 +24,18 @@ import torch
 
 from . import dufwi
 
+_BASE = {"tile_z": 32, "two_step": 0, "persistent": 0, "multi_tile": 0, "early": 1}
 CANDIDATES = (
-    {"tile_z": 32, "two_step": 0, "persistent": 0},
-    {"tile_z": 64, "two_step": 0, "persistent": 0},
-    {"tile_z": 32, "two_step": 1, "persistent": 0},
-    {"tile_z": 32, "two_step": 0, "persistent": 1},
+    dict(_BASE),
+    {**_BASE, "early": 0},
+    {**_BASE, "tile_z": 64},
+    {**_BASE, "tile_z": 64, "early": 0},
+    {**_BASE, "multi_tile": 1},
+    {**_BASE, "multi_tile": 1, "early": 0},
+    {**_BASE, "two_step": 1},
+    {**_BASE, "persistent": 1},
 )
+KNOBS = tuple(_BASE)
 
 _lock = threading.Lock()
 _cache: dict[str, dict] = {}
@@ -36,9 +48,36 @@ def _key(problem: dufwi.Problem, geom: dufwi.Geometry, n_maps: int) -> str:
 
 
 def apply(options: dict):
-    dufwi.set_option(dufwi.OPT_TILE_Z, int(options["tile_z"]))
-    dufwi.set_option(dufwi.OPT_TWO_STEP, int(options["two_step"]))
+    dufwi.set_option(dufwi.OPT_TILE_Z, int(options.get("tile_z", 32)))
+    dufwi.set_option(dufwi.OPT_TWO_STEP, int(options.get("two_step", 0)))
     dufwi.set_option(dufwi.OPT_PERSISTENT, int(options.get("persistent", 0)))
+    dufwi.set_option(dufwi.OPT_MULTI_TILE, int(options.get("multi_tile", 0)))
+    dufwi.set_option(dufwi.OPT_EARLY_LOADS, int(options.get("early", 1)))
+
+
+def kept_segments_for_budget(problem: dufwi.Problem, geom: dufwi.Geometry, n_maps: int, budget_bytes: int) -> int:
+    """Largest kept_segments whose gradient workspace fits budget_bytes (0 if none beyond the plain
+    checkpointed layout fits; the plain layout's own size is not checked here)."""
+    steps = problem.nt - 1
+    K = problem.ckpt_interval
+    if K <= 0 or K >= steps:
+        return 0
+    n_seg = (steps + K - 1) // K
+
+    def size(k):
+        return dufwi.workspace_size(dufwi.Problem(**{**problem.__dict__, "kept_segments": k}), geom, n_maps)
+
+    lo, hi = 0, n_seg
+    if size(1) > budget_bytes:
+        return 0
+    lo = 1
+    while lo < hi:                      # the size grows with k: largest k with size(k) <= budget
+        mid = (lo + hi + 1) // 2
+        if size(mid) <= budget_bytes:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
 
 
 def tune(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: dufwi.Geometry, *,
@@ -94,6 +133,7 @@ def tune(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom:
     best = dict(CANDIDATES[min(range(len(CANDIDATES)), key=lambda i: timings[i])])
     best["ms_per_step"] = min(timings) / nt
     best["candidates_ms_per_step"] = [t / nt for t in timings]
+    best["candidates"] = [dict(c) for c in CANDIDATES]
     apply(best)
     with _lock:
         _cache[key] = best

@@ -87,6 +87,8 @@ double stability_limit(int order)
 
 struct Layout {
     int Nx, Nz, P, nxp, nzp, pitch, radius, S, n_tx, n_rx, n_maps, nt, K, n_seg, n_hist;
+    int n_keep;              // gradient calls: last checkpoint segments whose history the forward sweep keeps
+    int first_kept;          // n_seg - n_keep: segments before it are recomputed from snapshots
     long long slice;
     size_t snap_elem;
     // byte offsets into the workspace
@@ -118,6 +120,7 @@ int g_tile_z = kTileZDefault;
 int g_two_step = 0;
 int g_persistent = 0;   // DUFWI_OPT_PERSISTENT: one cooperative launch per sweep segment
 int g_multi_tile = 0;   // DUFWI_OPT_MULTI_TILE: the multi-tile one-step kernel (64 x 32 tiles)
+int g_early = 1;        // DUFWI_OPT_EARLY_LOADS: operands not written by the last two launches requested early
 std::atomic<int> g_test_stall{0};   // DUFWI_OPT_TEST_STALL: the next persistent sweep stalls on purpose
 
 // NVTX range over the host code that enqueues one part of a call (visible in timeline tools).
@@ -135,7 +138,7 @@ int validate_problem(const dufwi_problem *pb)
         return DUFWI_ERR_INVALID_ARG;
     if (!stencil_weights(pb->fd_order, c)) return DUFWI_ERR_INVALID_ARG;
     if (pb->snapshot_dtype < DUFWI_SNAP_FP32 || pb->snapshot_dtype > DUFWI_SNAP_FP16) return DUFWI_ERR_INVALID_ARG;
-    if (pb->ckpt_interval < 0) return DUFWI_ERR_INVALID_ARG;
+    if (pb->ckpt_interval < 0 || pb->kept_segments < 0) return DUFWI_ERR_INVALID_ARG;
     if (!(pb->c_max > 0) || !isfinite(pb->c_max)) return DUFWI_ERR_INVALID_ARG;
     if (pb->boundary != DUFWI_BOUNDARY_DAMPING && pb->boundary != DUFWI_BOUNDARY_CPML) return DUFWI_ERR_INVALID_ARG;
     if (pb->boundary == DUFWI_BOUNDARY_CPML && !(pb->pml_alpha >= 0 && isfinite(pb->pml_alpha)))
@@ -176,6 +179,12 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         L->n_seg = (steps + L->K - 1) / L->K;
     }
     L->n_hist = (pb->ckpt_interval == 0) ? (steps > 0 ? steps : 1) : L->K;
+    // hybrid history (gradient calls): the last n_keep segments keep the history written by the
+    // forward sweep; the recompute of earlier segments reuses their slots once the adjoint has
+    // consumed them, so the ring holds max(n_keep, 1) segments
+    L->n_keep = (gradient && L->n_seg > 1) ? std::min(pb->kept_segments, L->n_seg) : 0;
+    L->first_kept = L->n_seg - L->n_keep;
+    if (L->n_keep > 0) L->n_hist = L->n_keep * L->K;
     if (kind == kLayoutJvp) L->n_hist = 1;
     L->snap_elem = pb->snapshot_dtype == DUFWI_SNAP_FP32 ? 4 : 2;
     L->comp = pb->forward_precision == DUFWI_FORWARD_COMPENSATED;
@@ -230,9 +239,9 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         for (int i = 0; i < 4; ++i) L->o_m[i] = take(field);
         L->o_grad = take(field);
         L->o_hist = take(field * (size_t)L->n_hist);
-        if (!store_all) {
-            L->o_snap = take((size_t)L->n_seg * L->snap_planes * L->S * L->slice * L->snap_elem);
-            L->o_scale = take((size_t)L->n_seg * 2 * L->S * sizeof(unsigned));
+        if (!store_all && L->first_kept > 0) {   // snapshots of the recomputed segments only
+            L->o_snap = take((size_t)L->first_kept * L->snap_planes * L->S * L->slice * L->snap_elem);
+            L->o_scale = take((size_t)L->first_kept * 2 * L->S * sizeof(unsigned));
         }
         L->o_cd = take(cdb);
         L->o_asrc = take(cdb);
@@ -868,7 +877,7 @@ int forward_range(Ctx &c, Ring &rg, int n0, int n1, int mode, const float *wavel
     for (int n = n0; n < n1;) {
         p.step = n;
         p.hist = hist ? hist + (size_t)(n - h0) * hstride : nullptr;
-        p.early = (!c.two_step && n >= n0 + 2) ? 1 : 0;   // the two launches before were steps n-2, n-1
+        p.early = (g_early && !c.two_step && n >= n0 + 2) ? 1 : 0;   // the two launches before: steps n-2, n-1
         if (c.two_step && n % 2 == 0 && n + 2 <= n1) {
             p.hist2 = hist ? hist + (size_t)(n + 1 - h0) * hstride : nullptr;
             int rc = two_steps(c, rg, mode, p, nl);
@@ -894,7 +903,7 @@ int adjoint_range(Ctx &c, Ring &rg, int m1, int m0, const float *asrc, float *g_
     for (int m = m1; m >= m0;) {
         p.step = m;
         p.hist_slot = m - 1 - h0;
-        p.early = (!c.two_step && m <= m1 - 2) ? 1 : 0;   // the two launches before were steps m+2, m+1
+        p.early = (g_early && !c.two_step && m <= m1 - 2) ? 1 : 0;   // the two launches before: m+2, m+1
         if (c.two_step && m % 2 == 0 && m - 1 >= m0) {
             p.hist_slot2 = m - 2 - h0;
             int rc = two_steps(c, rg, kAdjoint, p, nl);
@@ -931,9 +940,12 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
     const int mode = store_hist ? kFwdSampleHist : kFwdSample;
     float *hist = store_hist ? c.at<float>(L.o_hist) : nullptr;
     const int seg = snapshots ? L.K : (L.nt > 1 ? L.nt - 1 : 1);
+    const size_t hstride = (size_t)L.S * L.slice;
     for (int n = 0; n < L.nt - 1; n += seg) {
-        if (snapshots) {
-            const int sg = n / L.K;
+        const int sg = n / L.K;
+        // hybrid history: a kept segment writes its history into its own slots instead of a snapshot
+        const bool kept = snapshots && sg >= L.first_kept;
+        if (snapshots && !kept) {
             char *snap = c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
             float *cur = rg.buf[rg.cur], *prv = rg.buf[rg.prv];
@@ -952,7 +964,9 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
             }
         }
         const int n1 = std::min(n + seg, L.nt - 1);
-        int rc = forward_range(c, rg, n, n1, mode, wavelet, cd, hist, 0, nl);
+        int rc = kept ? forward_range(c, rg, n, n1, kFwdSampleHist, wavelet, cd,
+                                      c.at<float>(L.o_hist) + (size_t)(sg - L.first_kept) * L.K * hstride, n, nl)
+                      : forward_range(c, rg, n, n1, mode, wavelet, cd, hist, 0, nl);
         if (rc) return rc;
     }
     if (L.n_rx > 0) {
@@ -998,6 +1012,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_multi_tile = value;
         return DUFWI_OK;
+    case DUFWI_OPT_EARLY_LOADS:
+        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
+        g_early = value;
+        return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL:
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_test_stall = value;
@@ -1013,6 +1031,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     case DUFWI_OPT_TILE_Z: *value = g_tile_z; return DUFWI_OK;
     case DUFWI_OPT_PERSISTENT: *value = g_persistent; return DUFWI_OK;
     case DUFWI_OPT_MULTI_TILE: *value = g_multi_tile; return DUFWI_OK;
+    case DUFWI_OPT_EARLY_LOADS: *value = g_early; return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL: *value = g_test_stall.load(); return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;
@@ -1195,7 +1214,9 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
     for (int sg = L.n_seg - 1; sg >= 0; --sg) {
         const int t0 = store_all ? 0 : sg * L.K;
         const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
-        if (!store_all) {
+        // slot of Lap(U^t) is t - h0: a kept segment's own slots, else the ring's first segment
+        const int h0 = sg >= L.first_kept ? t0 - (sg - L.first_kept) * L.K : t0;
+        if (!store_all && sg < L.first_kept) {
             NvtxRange range("dufwi recompute segment");
             nl = 0;
             e0 = g_prof.mark(c.st);
@@ -1227,7 +1248,7 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
         NvtxRange range("dufwi adjoint segment");
         nl = 0;
         e0 = g_prof.mark(c.st);
-        rc = adjoint_range(c, ar, t1, t0 + 1, asrc, g_shot, t0, nl);
+        rc = adjoint_range(c, ar, t1, t0 + 1, asrc, g_shot, h0, nl);
         if (rc) return rc;
         g_prof.span(2, e0, g_prof.mark(c.st), nl);
     }

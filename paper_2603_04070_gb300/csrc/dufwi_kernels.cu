@@ -170,41 +170,6 @@ __device__ __forceinline__ void lap_block(const float *src, int cx, int cz, cons
     }
 }
 
-// One row of lap_block: the same arithmetic for the four cells of row cz, with the z-neighbours
-// taken from a register window win[i] = row cz - R + i (win[R] is the row itself), so a thread
-// walking its rows keeps only 2R + 1 float4 of the column live.
-template <int R, int SX>
-__device__ __forceinline__ void lap_row(const float *src, int cx, int cz, const float *c, const float4 (&win)[2 * R + 1],
-                                        float4 &lap, float4 &ctr)
-{
-    const float2 m4 = make_float2(-4.0f, -4.0f);
-    const float4 lft = ld4s(src + cz * SX + cx - 4);
-    const float4 rgt = ld4s(src + cz * SX + cx + 4);
-    const float4 cc = win[R];
-    ctr = cc;
-    const float w[12] = {lft.x, lft.y, lft.z, lft.w, cc.x, cc.y, cc.z, cc.w, rgt.x, rgt.y, rgt.z, rgt.w};
-    float2 l[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float2 u = make_float2(w[4 + 2 * h], w[5 + 2 * h]);
-        const float2 nu4 = __fmul2_rn(m4, u);
-        float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int kk = 1; kk <= R; ++kk) {
-            const float2 xs = (kk & 1)
-                ? make_float2(w[4 + 2 * h - kk] + w[4 + 2 * h + kk], w[5 + 2 * h - kk] + w[5 + 2 * h + kk])
-                : __fadd2_rn(make_float2(w[4 + 2 * h - kk], w[5 + 2 * h - kk]),
-                             make_float2(w[4 + 2 * h + kk], w[5 + 2 * h + kk]));
-            const float4 &cm = win[R - kk], &cp = win[R + kk];
-            const float2 zs = h == 0 ? __fadd2_rn(make_float2(cm.x, cm.y), make_float2(cp.x, cp.y))
-                                     : __fadd2_rn(make_float2(cm.z, cm.w), make_float2(cp.z, cp.w));
-            acc = __ffma2_rn(make_float2(c[kk], c[kk]), __fadd2_rn(__fadd2_rn(xs, zs), nu4), acc);
-        }
-        l[h] = acc;
-    }
-    lap = make_float4(l[0].x, l[0].y, l[1].x, l[1].y);
-}
-
 // Eq. 2 for four cells of a row: 2u - p + (a - 2) u + (b + 1) p + kappa' lap. The small damping
 // terms (a - 2, b + 1) come from a table over the layer depths (FP64 on the host, rounded once);
 // trow is the table row of this z, xd the x depths of the four lanes.
@@ -245,14 +210,9 @@ __device__ __forceinline__ bool wait_tile(uint64_t *bar, const StepParams &p, in
     return true;
 }
 
-// Minimum resident CTAs per SM requested from the register allocator, for 64 x 32 tiles: the
-// adjoint and Born steps (43.5 KB of shared memory per CTA, so at most 5 per SM) and the forward
-// modes (27.5 KB, up to 8 per SM). Build-time knobs.
+// Minimum resident CTAs per SM requested from the register allocator. Build-time knob.
 #ifndef DUFWI_STEP_MIN_CTAS_128
 #define DUFWI_STEP_MIN_CTAS_128 5
-#endif
-#ifndef DUFWI_STEP_MIN_CTAS_FWD
-#define DUFWI_STEP_MIN_CTAS_FWD 5
 #endif
 
 // One time step, one 64 x TZ output tile of one shot per CTA (128 threads, TZ / 32 passes of
@@ -261,10 +221,7 @@ __device__ __forceinline__ bool wait_tile(uint64_t *bar, const StepParams &p, in
 // Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay resident per SM, so the
 // loads of some overlap the arithmetic of others.
 template <int R, int MODE, int TZ>
-__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta,
-                                  TZ == 32 ? ((MODE == kAdjoint || MODE == kBorn) ? DUFWI_STEP_MIN_CTAS_128
-                                                                                 : DUFWI_STEP_MIN_CTAS_FWD)
-                                           : 4)
+__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta, TZ == 32 ? DUFWI_STEP_MIN_CTAS_128 : 4)
 step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 {
     using TL = TileLayout<MODE, TZ>;
@@ -341,60 +298,46 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     if (!wait_tile(&bar, p, tid)) return;
 
     const bool col_ok = gx < mg.nxp;
-    // Rows are finished one at a time (Laplacian, update, stores), so only a sliding window of the
-    // column and one row of results stay in registers. A tile with point injections (block-uniform)
-    // stages its updated rows in the U^{n-1} tile instead, applies the list in order, and stores
-    // them in a second loop.
-    const bool staged = MODE != kBorn && inj.n > 0;
 #pragma unroll 1
     for (int pass = 0; pass < TL::kPasses; ++pass) {
         const int lz = (tid >> 4) * 4 + 32 * pass;
-        if (staged) __syncthreads();
-        float4 win[2 * R + 1];
-#pragma unroll
-        for (int i = 1; i <= 2 * R; ++i) win[i] = ld4s(box + (kHalo + lz - R - 1 + i) * kBoxX + kHalo + lx);
+        float4 lap[4], ctr[4], nxt[4];
+        lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-#pragma unroll
-            for (int i = 0; i < 2 * R; ++i) win[i] = win[i + 1];
-            win[2 * R] = ld4s(box + (kHalo + lz + j + R) * kBoxX + kHalo + lx);
-            float4 lap, ctr;
-            lap_row<R, kBoxX>(box, kHalo + lx, kHalo + lz + j, p.c, win, lap, ctr);
             const int lo = (lz + j) * kTileX + lx;
-            float4 nv = eq2_row(ctr, ld4s(pv + lo), ld4s(kp + lo), lap, interior,
-                                p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
-            if (MODE == kBorn) nv = fma4(ld4s(gg + lo), ld4s(hs + lo), nv);   // + dkappa' Lap(U^n)
-            const int gz = z0 + lz + j;
-            const bool row_ok = col_ok && gz < mg.nzp;
-            if (gx + 4 > mg.nxp) {   // lanes past the last column stay zero (outside the map's grid)
-                if (gx + 1 >= mg.nxp) { nv.y = 0.f; lap.y = 0.f; }
-                if (gx + 2 >= mg.nxp) { nv.z = 0.f; lap.z = 0.f; }
-                nv.w = 0.f; lap.w = 0.f;
-            }
-            const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
-            if ((MODE == kFwdSampleHist || MODE == kFwdHist) && row_ok) st4_stream(p.hist + o, lap);
-            if (staged) {
-                st4s(pv + lo, nv);
-            } else if (row_ok) {
-                st4(p.out + o, nv);
-                if (MODE == kAdjoint) st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
-            }
+            nxt[j] = eq2_row(ctr[j], ld4s(pv + lo), ld4s(kp + lo), lap[j], interior,
+                             p.damp_tab + layer_depth(z0 + lz + j, p.P, mg.Nz) * (p.P + 1), xd);
+            if (MODE == kBorn) nxt[j] = fma4(ld4s(gg + lo), ld4s(hs + lo), nxt[j]);   // + dkappa' Lap(U^n)
         }
-        if (staged) {
+        if (MODE != kBorn && inj.n > 0) {   // block-uniform: stage this pass's rows, inject, reload
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) st4s(pv + (lz + j) * kTileX + lx, nxt[j]);
             __syncthreads();
             if (tid == 0)
                 apply_injections<MODE>(inj, pv, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX,
                                        TZ, kTileX, 32 * pass * kTileX, 32 * (pass + 1) * kTileX);
             __syncthreads();
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int gz = z0 + lz + j;
-                if (!col_ok || gz >= mg.nzp) continue;
+            for (int j = 0; j < 4; ++j) nxt[j] = ld4s(pv + (lz + j) * kTileX + lx);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gz = z0 + lz + j;
+            if (!col_ok || gz >= mg.nzp) continue;
+            float4 nv = nxt[j], lv = lap[j];
+            if (gx + 4 > mg.nxp) {   // lanes past the last column stay zero (outside the map's grid)
+                if (gx + 1 >= mg.nxp) { nv.y = 0.f; lv.y = 0.f; }
+                if (gx + 2 >= mg.nxp) { nv.z = 0.f; lv.z = 0.f; }
+                nv.w = 0.f; lv.w = 0.f;
+            }
+            const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+            st4(p.out + o, nv);
+            if (MODE == kFwdSampleHist || MODE == kFwdHist) st4_stream(p.hist + o, lv);
+            if (MODE == kAdjoint) {
                 const int lo = (lz + j) * kTileX + lx;
-                const float4 nv = ld4s(pv + lo);
-                const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
-                st4(p.out + o, nv);
-                if (MODE == kAdjoint) st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+                st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
             }
         }
     }

@@ -33,6 +33,7 @@ OPT_REUSE_TABLES = 3
 OPT_PERSISTENT = 4
 OPT_TEST_STALL = 5
 OPT_MULTI_TILE = 6
+OPT_EARLY_LOADS = 7
 
 
 class DufwiError(RuntimeError):
@@ -49,7 +50,7 @@ class _Problem(ctypes.Structure):
                 ("fd_order", ctypes.c_int32), ("snapshot_dtype", ctypes.c_int32),
                 ("ckpt_interval", ctypes.c_int32), ("c_max", ctypes.c_double),
                 ("boundary", ctypes.c_int32), ("pml_alpha", ctypes.c_double),
-                ("forward_precision", ctypes.c_int32)]
+                ("forward_precision", ctypes.c_int32), ("kept_segments", ctypes.c_int32)]
 
 
 class _Array(ctypes.Structure):
@@ -140,12 +141,13 @@ class Problem:
     boundary: str = "damping"          # "damping" (the term D of Eq. 1) or "cpml"
     pml_alpha: float = 0.0             # CPML frequency shift at the layer's inner edge (1/s)
     forward_precision: str = "fp32"    # "fp32" or "compensated" (hi + lo FP32 planes, error-free steps)
+    kept_segments: int = 0             # last checkpoint segments whose history the forward sweep keeps
 
     def c_struct(self) -> _Problem:
         return _Problem(self.nx, self.nz, self.dx, self.dt, self.nt, self.pml_cells, self.pml_R,
                         self.pml_cref, self.fd_order, SNAPSHOT_DTYPES[self.snapshot_dtype],
                         self.ckpt_interval, self.c_max, BOUNDARIES[self.boundary], self.pml_alpha,
-                        FORWARD_PRECISIONS[self.forward_precision])
+                        FORWARD_PRECISIONS[self.forward_precision], self.kept_segments)
 
 
 class Geometry:

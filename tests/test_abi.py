@@ -337,3 +337,41 @@ def test_compensated_forward_validation_and_sizing():
     fake = ctypes.c_void_p(1 << 20)
     assert d._lib.dufwi_simulate(ctypes.byref(c), fake, fake, ctypes.byref(arr), fake, ctypes.byref(sh), 1,
                                  fake, ctypes.c_void_p(1 << 20), need, None) == d.ERR_UNSUPPORTED
+
+
+def test_hybrid_history_workspace_sizing():
+    """kept_segments = k keeps k segments of history (k K fields) and drops their snapshots; k at or
+    above the segment count keeps every step and takes no snapshots; negative k is refused."""
+    d = _lib_module()
+    g = _geom(d)
+    field = 2 * (48 + 40) * ((64 + 40 + 7) // 8 * 8) * 4
+    K, nt = 50, 1001                                     # 20 segments
+    base = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K), g, 1)
+    k1 = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=1), g, 1)
+    k5 = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=5), g, 1)
+    kall = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=20), g, 1)
+    kmore = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=500), g, 1)
+    store_all = d.workspace_size(_problem(d, nt=nt, ckpt_interval=0), g, 1)
+    assert abs(k1 - (base - 2 * field)) <= 4096             # one segment's snapshot fewer
+    assert abs(k5 - k1 - 4 * K * field + 4 * 2 * field) <= 4096
+    assert kall == kmore
+    assert abs(kall - store_all) <= K * field + 4096          # 20 K slots against nt - 1 = 1000 steps
+    assert d.workspace_size(_problem(d, nt=nt, ckpt_interval=0, kept_segments=3), g, 1) == store_all
+    with pytest.raises(d.DufwiError) as e:
+        d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=-1), g, 1)
+    assert e.value.status == d.ERR_INVALID_ARG
+
+
+def test_kept_segments_for_budget_is_the_largest_fit():
+    from paper_2603_04070_gb300 import autotune
+    d = _lib_module()
+    g = _geom(d)
+    pb = _problem(d, nt=1001, ckpt_interval=50)
+    sizes = [d.workspace_size(_problem(d, nt=1001, ckpt_interval=50, kept_segments=k), g, 1) for k in range(21)]
+    assert all(a <= b for a, b in zip(sizes[1:], sizes[2:]))
+    for k in (1, 7, 20):
+        assert autotune.kept_segments_for_budget(pb, g, 1, sizes[k]) == k
+        if k > 1:
+            assert autotune.kept_segments_for_budget(pb, g, 1, sizes[k] - 1) == k - 1
+    assert autotune.kept_segments_for_budget(pb, g, 1, sizes[1] - 1) == 0
+    assert autotune.kept_segments_for_budget(_problem(d, nt=1001, ckpt_interval=0), g, 1, 1 << 40) == 0

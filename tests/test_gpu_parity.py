@@ -212,6 +212,32 @@ def test_checkpointed_gradient_is_bit_identical_to_store_all(d, ckpt):
     assert np.array_equal(J0, J1) and np.array_equal(g0, g1)
 
 
+@pytest.mark.parametrize("kept,precision", [(1, "fp32"), (3, "fp32"), (8, "fp32"), (99, "fp32"), (2, "compensated")])
+def test_hybrid_history_is_bit_identical_to_store_all(d, kept, precision):
+    """The last `kept` checkpoint segments keep their history from the forward sweep; the earlier
+    ones are recomputed into the slots the kept ones freed. Every split gives the store-all
+    gradient bit for bit (8 segments of 37 steps here; 99 keeps them all)."""
+    wl = inputs.make_workload("linear_disk", seed=6, nx=64, nz=64, nt=290, n_elem=16, n_tx=2, n_maps=2)
+    M_obs = _observed(wl)
+    J0, g0, c0 = _gpu_grad(d, wl, M_obs, forward_precision=precision)
+    J1, g1, c1 = _gpu_grad(d, wl, M_obs, ckpt_interval=37, kept_segments=kept, forward_precision=precision)
+    assert np.array_equal(J0, J1) and np.array_equal(g0, g1) and np.array_equal(c0, c1)
+
+
+def test_hybrid_history_with_compressed_snapshots(d):
+    """With FP16 snapshots only the recomputed segments carry the snapshot error: keeping every
+    segment gives the store-all gradient exactly, keeping some lands between the two."""
+    wl = inputs.make_workload("linear_disk", seed=8, nx=80, nz=80, nt=801, n_elem=24, n_tx=2)
+    M_obs = _observed(wl)
+    _, g_all, _ = _gpu_grad(d, wl, M_obs)
+    errs = []
+    for kept in (0, 8, 16):
+        _, g, _ = _gpu_grad(d, wl, M_obs, ckpt_interval=50, snapshot_dtype="fp16", kept_segments=kept)
+        errs.append(rel_l2(g[0], g_all[0]))
+    assert errs[2] == 0.0
+    assert 0.0 < errs[1] <= errs[0]
+
+
 def test_gradient_batched_maps(d):
     wl = inputs.make_workload("linear_disk", seed=7, nx=70, nz=58, nt=500, n_elem=22, n_tx=3, n_maps=2)
     wl.sos_start = (wl.sos_start + np.random.default_rng(1).uniform(-5, 5, wl.sos_start.shape)).astype(np.float32)

@@ -131,8 +131,14 @@ def test_autotune_gradient_probe_bit_identical(d):
         autotune.apply(autotune.CANDIDATES[0])
         J0, g0 = d.misfit_gradient(pb, sos, wav, geom, obs)
         best = autotune.tune(pb, sos, wav, geom, gradient=True, cd_obs=obs, steps=120, repeats=1)
-        picked = {k: best[k] for k in ("tile_z", "two_step", "persistent")}
+        picked = {k: best[k] for k in autotune.KNOBS}
         assert picked in [dict(c) for c in autotune.CANDIDATES]
+        # every candidate gives the default gradient bit for bit
+        for cand in autotune.CANDIDATES:
+            autotune.apply(cand)
+            Jc, gc = d.misfit_gradient(pb, sos, wav, geom, obs)
+            assert torch.equal(J0, Jc) and torch.equal(g0, gc), cand
+        autotune.apply(picked)
         assert len(best["candidates_ms_per_step"]) == len(autotune.CANDIDATES)
         assert all(t > 0 for t in best["candidates_ms_per_step"])
         J1, g1 = d.misfit_gradient(pb, sos, wav, geom, obs)

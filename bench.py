@@ -343,8 +343,6 @@ def run_ours(args):
     if args.multi_tile is not None:
         dufwi.set_option(dufwi.OPT_MULTI_TILE, args.multi_tile)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
-    if args.boundary == "cpml":
-        args.ckpt = 0          # the CPML memory variables are not checkpointed: keep every step
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
                        ckpt_interval=args.ckpt, c_max=2000.0 if args.boundary == "cpml" else wl.c_max,

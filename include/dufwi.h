@@ -122,9 +122,10 @@ typedef struct {
  *     is stretched by 1/s, s = 1 + d/(alpha + i omega), through one memory variable per
  *     difference and axis (recursive convolution; alpha = pml_alpha (1 - xi/L)); no damping
  *     term. Supported by dufwi_simulate, dufwi_simulate_noalloc, dufwi_misfit,
- *     dufwi_forward_save/dufwi_backward and dufwi_misfit_gradient with ckpt_interval 0 (every
- *     step kept: the memory variables are not checkpointed), with or without a density map;
- *     not by the *_sized calls, dufwi_jvp, dufwi_second_order or dufwi_hvp
+ *     dufwi_forward_save/dufwi_backward and dufwi_misfit_gradient, with or without a density map
+ *     and with any ckpt_interval: a checkpoint stores the four memory fields read at its step in
+ *     FP32 beside (U^t, U^{t-1}), and the adjoint keeps its own memory variables apart from the
+ *     forward's; not by the *_sized calls, dufwi_jvp, dufwi_second_order or dufwi_hvp
  *     (DUFWI_ERR_UNSUPPORTED). */
 #define DUFWI_BOUNDARY_DAMPING 0
 #define DUFWI_BOUNDARY_CPML 1

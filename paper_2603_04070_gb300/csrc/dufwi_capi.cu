@@ -96,6 +96,8 @@ struct Layout {
     int tiles_x, tiles_z32;  // 64 x 32 tiles of one shot (persistent sweeps)
     int n_rxe;               // row length of the grown-tile receiver lists (4 n_rx)
     size_t o_cm[8], o_cpml;  // CPML: memory variables (two sets of psi_x, psi_z, xi_x, xi_z), coefficient tables
+    size_t o_cma[8];         // CPML gradients: the adjoint's memory variables (two sets), apart from the forward's
+    size_t o_snapm;          // CPML gradients: FP32 snapshots of the forward memory set read at each segment start
     size_t o_flags, o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
     // second-order calls: adjoint and differentiated-adjoint rings, second and third histories,
@@ -221,10 +223,15 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     L->o_bx = take((size_t)n_maps * L->slice * sizeof(float));     // buoyancies (density maps only)
     L->o_bz = take((size_t)n_maps * L->slice * sizeof(float));
     if (pb->boundary == DUFWI_BOUNDARY_CPML) {
-        // the memory variables are not checkpointed: gradients keep every step; no Born step
-        if (kind == kLayoutJvp || kind == kLayoutSecond || (gradient && L->n_seg > 1)) return DUFWI_ERR_UNSUPPORTED;
+        if (kind == kLayoutJvp || kind == kLayoutSecond) return DUFWI_ERR_UNSUPPORTED;   // no Born step
         for (int i = 0; i < 8; ++i) L->o_cm[i] = take((size_t)L->S * L->slice * sizeof(float));
         L->o_cpml = take(sizeof(float) * 4 * (size_t)(L->nxp + L->nzp));
+        if (gradient) {
+            for (int i = 0; i < 8; ++i) L->o_cma[i] = take((size_t)L->S * L->slice * sizeof(float));
+            // a recomputed segment restarts from (U^t, U^{t-1}) and the four memory fields read at step t
+            if (L->n_seg > 1 && L->first_kept > 0)
+                L->o_snapm = take((size_t)L->first_kept * 4 * L->S * L->slice * sizeof(float));
+        }
     }
     for (int i = 0; i < 4; ++i) L->o_f[i] = take(field);
     if (L->comp) {
@@ -419,7 +426,8 @@ struct Ctx {
     CompParams cq;                            // compensated: constant arguments of the step
     FieldMaps lomap[2];                       // compensated: maps of the low planes of the forward ring
     CUtensorMap kqh1, kql1;                   // compensated: kappa' / s_R, hi and lo
-    int mem_par = 0;                          // CPML: which memory-variable set the next step reads
+    int mem_par = 0;                          // CPML: which memory-variable set the next forward step reads
+    int amem_par = 0;                         // CPML: the same for the adjoint's own sets (gradient calls)
     CpmlMaps cm_fwd[2], cm_adj[2];            // CPML: maps reading set 0 / set 1
     FieldMaps fmap[4], mmap[4];
     CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1, bx1, bz1;
@@ -660,9 +668,15 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                 tensor_map(&c.cm_fwd[k].mem_nx, nx, L, L.S, 0, kTileX, kVTileZ) ||
                 tensor_map(&c.cm_fwd[k].mem_nz, nz, L, L.S, 0, kTileX, kVTileZ))
                 return DUFWI_ERR_CUDA;
-            c.cm_adj[k] = c.cm_fwd[k];
-            if (tensor_map(&c.cm_adj[k].mem_nx, nx, L, L.S, 0, kVBoxX, kVTileZ) ||
-                tensor_map(&c.cm_adj[k].mem_nz, nz, L, L.S, 0, kTileX, kVBoxZ))
+            // the adjoint has sets of its own in gradient calls (a recompute between adjoint segments
+            // must not overwrite them); chi is read over node boxes with a halo along its axis
+            const size_t *ao = gradient ? L.o_cma : L.o_cm;
+            const float *ahx = c.at<float>(ao[4 * k]), *ahz = c.at<float>(ao[4 * k + 1]);
+            const float *anx = c.at<float>(ao[4 * k + 2]), *anz = c.at<float>(ao[4 * k + 3]);
+            if (tensor_map(&c.cm_adj[k].mem_hx, ahx, L, L.S, 0, kVFxX, kVTileZ) ||
+                tensor_map(&c.cm_adj[k].mem_hz, ahz, L, L.S, 0, kTileX, kVFzZ) ||
+                tensor_map(&c.cm_adj[k].mem_nx, anx, L, L.S, 0, kVBoxX, kVTileZ) ||
+                tensor_map(&c.cm_adj[k].mem_nz, anz, L, L.S, 0, kTileX, kVBoxZ))
                 return DUFWI_ERR_CUDA;
         }
     }
@@ -770,15 +784,18 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
         tm.cur_box = rg.map[rg.cur].box2;
         tm.bx_tile = c.bx1;
         tm.bz_tile = c.bz1;
-        const int w = 1 - c.mem_par;
+        const bool adj = mode == kAdjoint;
+        int &par = adj ? c.amem_par : c.mem_par;
+        const size_t *o = (adj && c.L.o_cma[0]) ? c.L.o_cma : c.L.o_cm;
+        const int w = 1 - par;
         CpmlParams cp;
-        cp.hx_out = c.at<float>(c.L.o_cm[4 * w]);
-        cp.hz_out = c.at<float>(c.L.o_cm[4 * w + 1]);
-        cp.nx_out = c.at<float>(c.L.o_cm[4 * w + 2]);
-        cp.nz_out = c.at<float>(c.L.o_cm[4 * w + 3]);
+        cp.hx_out = c.at<float>(o[4 * w]);
+        cp.hz_out = c.at<float>(o[4 * w + 1]);
+        cp.nx_out = c.at<float>(o[4 * w + 2]);
+        cp.nz_out = c.at<float>(o[4 * w + 3]);
         cp.cx = c.at<float>(c.L.o_cpml);
         cp.cz = cp.cx + 4 * (size_t)c.L.nxp;
-        const CpmlMaps &cm = mode == kAdjoint ? c.cm_adj[c.mem_par] : c.cm_fwd[c.mem_par];
+        const CpmlMaps &cm = adj ? c.cm_adj[par] : c.cm_fwd[par];
         // tiles away from the layer take the staggered kernel (their memory variables stay zero),
         // the others the CPML kernel; both read step n and write disjoint tiles of step n + 1
         StepParams pi = p, pl = p;
@@ -786,7 +803,7 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
         pl.tile_class = 2;
         CKL(launch_step_vd(c.L.radius, mode, tm, pi, c.st));
         CKL(launch_step_cpml(c.L.radius, mode, tm, cm, pl, cp, c.st));
-        c.mem_par = w;
+        par = w;
     } else if (c.vd) {   // the tile height is 32 here, so tile1, kap1, hist1 and grad1 fit the kernel
         tm.cur_box = rg.map[rg.cur].box2;
         tm.bx_tile = c.bx1;
@@ -949,6 +966,12 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
             char *snap = c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
             float *cur = rg.buf[rg.cur], *prv = rg.buf[rg.prv];
+            if (c.cpml && L.o_snapm) {   // the CPML memory set the next step reads (set mem_par)
+                char *sm = c.at<char>(L.o_snapm) + (size_t)sg * 4 * field;
+                for (int i = 0; i < 4; ++i)
+                    CK(cudaMemcpyAsync(sm + i * field, c.at<float>(L.o_cm[4 * c.mem_par + i]), field,
+                                       cudaMemcpyDeviceToDevice, c.st));
+            }
             if (dtype == DUFWI_SNAP_FP32) {
                 CK(cudaMemcpyAsync(snap, cur, field, cudaMemcpyDeviceToDevice, c.st));
                 CK(cudaMemcpyAsync(snap_d, prv, field, cudaMemcpyDeviceToDevice, c.st));
@@ -1206,9 +1229,9 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
     int e0 = -1, rc = DUFWI_OK;
     for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(ar.buf[i], 0, field, c.st));
     CK(cudaMemsetAsync(g_shot, 0, field, c.st));
-    if (c.cpml) {   // adjoint memory variables start at zero (every step is kept: no recompute)
-        for (int i = 0; i < 8; ++i) CK(cudaMemsetAsync(c.at<float>(L.o_cm[i]), 0, field, c.st));
-        c.mem_par = 0;
+    if (c.cpml) {   // the adjoint's memory variables start at zero, in sets of their own
+        for (int i = 0; i < 8; ++i) CK(cudaMemsetAsync(c.at<float>(L.o_cma[i]), 0, field, c.st));
+        c.amem_par = 0;
     }
     const int dtype = c.pb->snapshot_dtype;
     for (int sg = L.n_seg - 1; sg >= 0; --sg) {
@@ -1221,6 +1244,13 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
             nl = 0;
             e0 = g_prof.mark(c.st);
             // restore (U^{t0}, U^{t0-1}) and recompute Lap(U^n) for n = t0 .. t1-1
+            if (c.cpml) {   // and the forward memory set step t0 reads: set t0 & 1
+                c.mem_par = t0 & 1;
+                const char *sm = c.at<char>(L.o_snapm) + (size_t)sg * 4 * field;
+                for (int i = 0; i < 4; ++i)
+                    CK(cudaMemcpyAsync(c.at<float>(L.o_cm[4 * c.mem_par + i]), sm + i * field, field,
+                                       cudaMemcpyDeviceToDevice, c.st));
+            }
             char *snap = c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
             char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
             fr.cur = 0;

@@ -1,7 +1,8 @@
 """Convolutional PML (the alternative absorbing layer) on the GPU against the oracle.
 
 Same tolerances as the other paths: traces rel-L2 <= 1e-5, gradient rel-L2 <= 1e-4, misfit
-relative error <= 1e-4. Gradients keep every step (the memory variables are not checkpointed)."""
+relative error <= 1e-4. Checkpointed gradients snapshot the forward memory variables with the
+fields at each segment start and keep the adjoint's memory variables apart."""
 import math
 
 import numpy as np
@@ -134,13 +135,45 @@ def test_cpml_absorbs_better_than_the_damping_layer(d):
     assert refl["cpml"] < 2e-3 and refl["cpml"] < 0.1 * refl["damping"], refl
 
 
+@pytest.mark.parametrize("ckpt,kept,density", [(1, 0, False), (7, 0, True), (64, 0, False), (25, 3, True)])
+def test_cpml_checkpointed_gradient_is_bit_identical_to_store_all(d, ckpt, kept, density):
+    """Snapshots of (U^t, U^{t-1}) and of the four forward memory fields read at step t restore
+    the exact forward state, and the adjoint's memory variables live in sets of their own, so the
+    checkpointed gradient (with or without kept segments) equals the store-all one bit for bit."""
+    wl, rho = _case(24, 64, 56, 300, 16, 2, n_maps=2, density=density)
+    geom = d.Geometry.from_workload(wl)
+    sos, w = _t(wl.sos_start), _t(wl.wavelet)
+    obs = d.simulate(_pb(d, wl), _t(wl.sos_true), w, geom, density=_t(rho))
+    J0, g0 = d.misfit_gradient(_pb(d, wl), sos, w, geom, obs, density=_t(rho), check=True)
+    J1, g1 = d.misfit_gradient(_pb(d, wl, ckpt_interval=ckpt, kept_segments=kept), sos, w, geom, obs,
+                               density=_t(rho), check=True)
+    assert torch.equal(J0, J1) and torch.equal(g0, g1)
+    cd, ws = d.forward_save(_pb(d, wl, ckpt_interval=ckpt), sos, w, geom, density=_t(rho))
+    g2 = d.backward(_pb(d, wl, ckpt_interval=ckpt), sos, w, geom, (2.0 * (cd - obs)).contiguous(), ws,
+                    density=_t(rho))
+    assert torch.equal(g0, g2)
+
+
+def test_cpml_checkpointed_gradient_matches_oracle(d):
+    """Checkpoints every 50 steps on the CPML, against the oracle's gradient."""
+    wl, _ = _case(25, 80, 70, 700, 20, 2)
+    obs = _oracle_traces(wl, wl.sos_true[0], None)[None].astype(np.float32)
+    geom = d.Geometry.from_workload(wl)
+    J, g = d.misfit_gradient(_pb(d, wl, ckpt_interval=50), _t(wl.sos_start), _t(wl.wavelet), geom, _t(obs),
+                             check=True)
+    p = _op(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    Jr, gr = oracle.misfit_gradient(p, wl.sos_start[0].astype(np.float64), tix, tiz, wl.wavelet.astype(np.float64),
+                                    rix, riz, obs[0].astype(np.float64), ckpt=50)[:2]
+    assert abs(float(J[0]) - Jr) <= 1e-4 * Jr
+    assert rel_l2(g[0].cpu().numpy(), gr) <= GRAD_TOL
+
+
 def test_cpml_unsupported_combinations(d):
     wl, _ = _case(23, 40, 40, 60, 8, 1)
     geom = d.Geometry.from_workload(wl)
     sos, w = _t(wl.sos_true), _t(wl.wavelet)
-    with pytest.raises(d.DufwiError) as e:                      # checkpointed gradient
-        d.misfit_gradient(_pb(d, wl, ckpt_interval=10), sos, w, geom, torch.zeros((1, 1, 60, 8), device="cuda"))
-    assert e.value.status == d.ERR_UNSUPPORTED
     with pytest.raises(d.DufwiError) as e:                      # Born step
         d.jvp(_pb(d, wl), sos, w, geom, torch.zeros_like(sos))
     assert e.value.status == d.ERR_UNSUPPORTED

@@ -755,6 +755,8 @@ __device__ __forceinline__ bool cpml_free_tile(const StepParams &p, int x0, int 
            z0 + kVTileZ + 2 * kHalo <= p.P + p.Nz - 1;
 }
 
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 template <int MODE>
 struct VdLayout {
     static constexpr int kBox = kVBoxX * kVBoxZ;
@@ -854,6 +856,10 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     const float *bxs = fx;
     const float *bzs = fz;
     float4 lap[4], ctr[4], nxt[4];
+    // The arithmetic runs on packed FP32 pairs (f32x2: the same IEEE operations per lane, in the
+    // same order as the scalar form). Along x the pairs are two neighbouring half points (fluxes)
+    // or two neighbouring cells (divergence), built once per row from shifted copies so that
+    // every packed operand is an aligned register pair; along z they are two columns of a float4.
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const float *row = box + (lz + j + kVHalo) * kVBoxX + lx;
@@ -870,70 +876,76 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
             const float4 v = ld4s(brow + 4 * c);
             bw[4 * c] = v.x; bw[4 * c + 1] = v.y; bw[4 * c + 2] = v.z; bw[4 * c + 3] = v.w;
         }
-        float flux[11];
+        // flux h (h = 0..10) = bw[h] sum_k s_k (w[h + 4 + k] - w[h + 5 - k]); pairs (h, h + 1), h even
+        float flux[12];
 #pragma unroll
-        for (int h = 0; h < 11; ++h) {
-            float acc = 0.0f;
+        for (int h = 0; h < 12; h += 2) {
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], w[h + 4 + k] - w[h + 5 - k], acc);
-            flux[h] = bw[h] * acc;
+            for (int k = 1; k <= R; ++k) {
+                const float2 hi = make_float2(w[h + 4 + k], h + 5 + k < 20 ? w[h + 5 + k] : 0.0f);
+                const float2 lo = make_float2(w[h + 5 - k], w[h + 6 - k]);
+                acc = __ffma2_rn(make_float2(p.sw[k - 1], p.sw[k - 1]), __fadd2_rn(hi, neg2(lo)), acc);
+            }
+            const float2 f = __fmul2_rn(make_float2(bw[h], bw[h + 1]), acc);
+            flux[h] = f.x;
+            flux[h + 1] = f.y;
         }
-        float lxv[4];
+        // divergence at cells q = 0..3: sum_k s_k (flux[q + k + 3] - flux[q - k + 4]); pairs (q, q + 1)
+        float2 lxv[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float acc = 0.0f;
+        for (int q = 0; q < 4; q += 2) {
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int k = 1; k <= R; ++k) acc = fmaf(p.sw[k - 1], flux[q + k + 3] - flux[q - k + 4], acc);
-            lxv[q] = acc;
+            for (int k = 1; k <= R; ++k)
+                acc = __ffma2_rn(make_float2(p.sw[k - 1], p.sw[k - 1]),
+                                 __fadd2_rn(make_float2(flux[q + k + 3], flux[q + k + 4]),
+                                            neg2(make_float2(flux[q - k + 4], flux[q - k + 5]))),
+                                 acc);
+            lxv[q / 2] = acc;
         }
-        lap[j] = make_float4(lxv[0], lxv[1], lxv[2], lxv[3]);
+        lap[j] = make_float4(lxv[0].x, lxv[0].y, lxv[1].x, lxv[1].y);
         ctr[j] = make_float4(w[8], w[9], w[10], w[11]);
     }
     {
         float4 col[18];
 #pragma unroll
         for (int r = 0; r < 18; ++r) col[r] = ld4s(box + (lz + 1 + r) * kVBoxX + lx + kVHalo);
-        float4 lzv[4];
+        float2 lzv[4][2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) lzv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < 4; ++j) lzv[j][0] = lzv[j][1] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int f = 0; f < 11; ++f) {
             // flux at half-point row lz + f: box rows lz + f + 4 + k and lz + f + 5 - k = col[f + 3 + k], col[f + 4 - k]
-            float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 d[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
             for (int k = 1; k <= R; ++k) {
                 const float4 up = col[f + 3 + k], dn = col[f + 4 - k];
-                const float sk = p.sw[k - 1];
-                d.x = fmaf(sk, up.x - dn.x, d.x);
-                d.y = fmaf(sk, up.y - dn.y, d.y);
-                d.z = fmaf(sk, up.z - dn.z, d.z);
-                d.w = fmaf(sk, up.w - dn.w, d.w);
+                const float2 sk = make_float2(p.sw[k - 1], p.sw[k - 1]);
+                d[0] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.x, up.y), neg2(make_float2(dn.x, dn.y))), d[0]);
+                d[1] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.z, up.w), neg2(make_float2(dn.z, dn.w))), d[1]);
             }
             const float4 b = ld4s(bzs + (lz + f) * kTileX + lx);
-            const float4 fl = make_float4(b.x * d.x, b.y * d.y, b.z * d.z, b.w * d.w);
+            const float2 fl[2] = {__fmul2_rn(make_float2(b.x, b.y), d[0]), __fmul2_rn(make_float2(b.z, b.w), d[1])};
             // output row j takes +s_k from flux j + k + 3 and -s_k from flux j - k + 4
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int kp_ = f - j - 3, km_ = j + 4 - f;
-                if (kp_ >= 1 && kp_ <= R) {
-                    const float sk = p.sw[kp_ - 1];
-                    lzv[j].x = fmaf(sk, fl.x, lzv[j].x);
-                    lzv[j].y = fmaf(sk, fl.y, lzv[j].y);
-                    lzv[j].z = fmaf(sk, fl.z, lzv[j].z);
-                    lzv[j].w = fmaf(sk, fl.w, lzv[j].w);
-                }
-                if (km_ >= 1 && km_ <= R) {
-                    const float sk = -p.sw[km_ - 1];
-                    lzv[j].x = fmaf(sk, fl.x, lzv[j].x);
-                    lzv[j].y = fmaf(sk, fl.y, lzv[j].y);
-                    lzv[j].z = fmaf(sk, fl.z, lzv[j].z);
-                    lzv[j].w = fmaf(sk, fl.w, lzv[j].w);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (kp_ >= 1 && kp_ <= R)
+                        lzv[j][h] = __ffma2_rn(make_float2(p.sw[kp_ - 1], p.sw[kp_ - 1]), fl[h], lzv[j][h]);
+                    if (km_ >= 1 && km_ <= R)
+                        lzv[j][h] = __ffma2_rn(make_float2(-p.sw[km_ - 1], -p.sw[km_ - 1]), fl[h], lzv[j][h]);
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            lap[j] = make_float4(lap[j].x + lzv[j].x, lap[j].y + lzv[j].y, lap[j].z + lzv[j].z, lap[j].w + lzv[j].w);
+        for (int j = 0; j < 4; ++j) {
+            const float2 a01 = __fadd2_rn(make_float2(lap[j].x, lap[j].y), lzv[j][0]);
+            const float2 a23 = __fadd2_rn(make_float2(lap[j].z, lap[j].w), lzv[j][1]);
+            lap[j] = make_float4(a01.x, a01.y, a23.x, a23.y);
+        }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {

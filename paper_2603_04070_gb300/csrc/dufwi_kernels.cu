@@ -848,84 +848,50 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
 
     if (!wait_tile(&bar, p, tid)) return;
 
-    // Fluxes b D+u are formed once per tile, in place of the buoyancies they scale: x-fluxes at
-    // the 72 x 32 half points of the x-buoyancy tile (column h is the half point x0 - 4 + h + 1/2,
-    // row r is z0 + r) and z-fluxes at the 64 x 40 half points of the z-buoyancy tile (row j is
-    // z0 - 4 + j + 1/2). Box column/row 0 is x0 - 8 / z0 - 8. Each half point is computed by one
-    // thread, from the box only, so the in-place writes race with nothing before the barrier.
-    // Arithmetic runs on packed FP32 pairs (the same IEEE operations per lane as the scalar form).
-    float *bxs = fx;
-    float *bzs = fz;
-    {
-        // x: thread (row tid / 4, quarter tid % 4) takes 5, 4, 5, 4 groups of four columns
-        const int xr = tid >> 2, part = tid & 3;
-        const int g0 = part == 0 ? 0 : (part == 1 ? 5 : (part == 2 ? 9 : 14));
-        const int ng = (part & 1) ? 4 : 5;
-        const float *brow = box + (xr + kVHalo) * kVBoxX;
-        float4 win[7];
-#pragma unroll
-        for (int i = 0; i < 7; ++i) win[i] = (i < ng + 2) ? ld4s(brow + 4 * (g0 + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            if (i >= ng) break;
-            const float w[12] = {win[i].x, win[i].y, win[i].z, win[i].w, win[i + 1].x, win[i + 1].y,
-                                 win[i + 1].z, win[i + 1].w, win[i + 2].x, win[i + 2].y, win[i + 2].z, win[i + 2].w};
-            // flux at column c = 4 (g0 + i) + q: sum_k s_k (w[q + 4 + k] - w[q + 5 - k]); pairs (q, q + 1)
-            float2 acc[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float2 a2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-                for (int k = 1; k <= R; ++k)
-                    a2 = __ffma2_rn(make_float2(p.sw[k - 1], p.sw[k - 1]),
-                                    __fadd2_rn(make_float2(w[2 * h + 4 + k], w[2 * h + 5 + k]),
-                                               neg2(make_float2(w[2 * h + 5 - k], w[2 * h + 6 - k]))),
-                                    a2);
-                acc[h] = a2;
-            }
-            float *bp = bxs + xr * kVFxX + 4 * (g0 + i);
-            const float4 bv = ld4s(bp);
-            const float2 f0 = __fmul2_rn(make_float2(bv.x, bv.y), acc[0]);
-            const float2 f1 = __fmul2_rn(make_float2(bv.z, bv.w), acc[1]);
-            st4s(bp, make_float4(f0.x, f0.y, f1.x, f1.y));
-        }
-        // z: thread (column group tid % 16, run tid / 16) takes the half-point rows 5 run .. 5 run + 4
-        const int zc = (tid & 15) * 4, zr0 = (tid >> 4) * 5;
-        float4 col[12];
-#pragma unroll
-        for (int r = 0; r < 12; ++r) col[r] = ld4s(box + (zr0 + 1 + r) * kVBoxX + zc + kVHalo);
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            // half-point row j = zr0 + m: box rows j + 4 + k and j + 5 - k = col[m + 3 + k], col[m + 4 - k]
-            float2 d[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-            for (int k = 1; k <= R; ++k) {
-                const float4 up = col[m + 3 + k], dn = col[m + 4 - k];
-                const float2 sk = make_float2(p.sw[k - 1], p.sw[k - 1]);
-                d[0] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.x, up.y), neg2(make_float2(dn.x, dn.y))), d[0]);
-                d[1] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.z, up.w), neg2(make_float2(dn.z, dn.w))), d[1]);
-            }
-            float *bp = bzs + (zr0 + m) * kTileX + zc;
-            const float4 bv = ld4s(bp);
-            const float2 f0 = __fmul2_rn(make_float2(bv.x, bv.y), d[0]);
-            const float2 f1 = __fmul2_rn(make_float2(bv.z, bv.w), d[1]);
-            st4s(bp, make_float4(f0.x, f0.y, f1.x, f1.y));
-        }
-    }
-    __syncthreads();   // every flux of the tile is in shared memory
-
+    // Each thread forms the fluxes its 4 x 4 block needs in registers: along x, the half points
+    // lx .. lx + 10 of each of its rows (box columns lx + 1 .. lx + 18, buoyancy tile columns
+    // lx .. lx + 10); along z, the half-point rows lz .. lz + 10 of its four columns (box rows
+    // lz + 1 .. lz + 18, buoyancy tile rows lz .. lz + 10). Box column/row 0 is x0 - 8 / z0 - 8;
+    // x-buoyancy column h is the half point x0 - 4 + h + 1/2, z-buoyancy row j is z0 - 4 + j + 1/2.
+    const float *bxs = fx;
+    const float *bzs = fz;
     float4 lap[4], ctr[4], nxt[4];
+    // The arithmetic runs on packed FP32 pairs (f32x2: the same IEEE operations per lane, in the
+    // same order as the scalar form). Along x the pairs are two neighbouring half points (fluxes)
+    // or two neighbouring cells (divergence), built once per row from shifted copies so that
+    // every packed operand is an aligned register pair; along z they are two columns of a float4.
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        // divergence along x at cells q = 0..3: sum_k s_k (flux[q + k + 3] - flux[q - k + 4]), flux[h] at
-        // x-flux column lx + h; pairs (q, q + 1)
-        const float *frow = bxs + (lz + j) * kVFxX + lx;
-        float flux[12];
+        const float *row = box + (lz + j + kVHalo) * kVBoxX + lx;
+        float w[20];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float4 v = ld4s(row + 4 * c);
+            w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+        }
+        const float *brow = bxs + (lz + j) * kVFxX + lx;
+        float bw[12];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float4 v = ld4s(frow + 4 * c);
-            flux[4 * c] = v.x; flux[4 * c + 1] = v.y; flux[4 * c + 2] = v.z; flux[4 * c + 3] = v.w;
+            const float4 v = ld4s(brow + 4 * c);
+            bw[4 * c] = v.x; bw[4 * c + 1] = v.y; bw[4 * c + 2] = v.z; bw[4 * c + 3] = v.w;
         }
+        // flux h (h = 0..10) = bw[h] sum_k s_k (w[h + 4 + k] - w[h + 5 - k]); pairs (h, h + 1), h even
+        float flux[12];
+#pragma unroll
+        for (int h = 0; h < 12; h += 2) {
+            float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                const float2 hi = make_float2(w[h + 4 + k], h + 5 + k < 20 ? w[h + 5 + k] : 0.0f);
+                const float2 lo = make_float2(w[h + 5 - k], w[h + 6 - k]);
+                acc = __ffma2_rn(make_float2(p.sw[k - 1], p.sw[k - 1]), __fadd2_rn(hi, neg2(lo)), acc);
+            }
+            const float2 f = __fmul2_rn(make_float2(bw[h], bw[h + 1]), acc);
+            flux[h] = f.x;
+            flux[h + 1] = f.y;
+        }
+        // divergence at cells q = 0..3: sum_k s_k (flux[q + k + 3] - flux[q - k + 4]); pairs (q, q + 1)
         float2 lxv[2];
 #pragma unroll
         for (int q = 0; q < 4; q += 2) {
@@ -939,18 +905,29 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
             lxv[q / 2] = acc;
         }
         lap[j] = make_float4(lxv[0].x, lxv[0].y, lxv[1].x, lxv[1].y);
-        ctr[j] = ld4s(box + (lz + j + kVHalo) * kVBoxX + lx + kVHalo);
+        ctr[j] = make_float4(w[8], w[9], w[10], w[11]);
     }
     {
-        // divergence along z: output row j takes +s_k from flux row j + k + 3 and -s_k from j - k + 4
-        // (z-flux rows lz .. lz + 10), accumulated in increasing flux row
+        float4 col[18];
+#pragma unroll
+        for (int r = 0; r < 18; ++r) col[r] = ld4s(box + (lz + 1 + r) * kVBoxX + lx + kVHalo);
         float2 lzv[4][2];
 #pragma unroll
         for (int j = 0; j < 4; ++j) lzv[j][0] = lzv[j][1] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int f = 0; f < 11; ++f) {
-            const float4 fv = ld4s(bzs + (lz + f) * kTileX + lx);
-            const float2 fl[2] = {make_float2(fv.x, fv.y), make_float2(fv.z, fv.w)};
+            // flux at half-point row lz + f: box rows lz + f + 4 + k and lz + f + 5 - k = col[f + 3 + k], col[f + 4 - k]
+            float2 d[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                const float4 up = col[f + 3 + k], dn = col[f + 4 - k];
+                const float2 sk = make_float2(p.sw[k - 1], p.sw[k - 1]);
+                d[0] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.x, up.y), neg2(make_float2(dn.x, dn.y))), d[0]);
+                d[1] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.z, up.w), neg2(make_float2(dn.z, dn.w))), d[1]);
+            }
+            const float4 b = ld4s(bzs + (lz + f) * kTileX + lx);
+            const float2 fl[2] = {__fmul2_rn(make_float2(b.x, b.y), d[0]), __fmul2_rn(make_float2(b.z, b.w), d[1])};
+            // output row j takes +s_k from flux j + k + 3 and -s_k from flux j - k + 4
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int kp_ = f - j - 3, km_ = j + 4 - f;

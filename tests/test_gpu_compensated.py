@@ -201,3 +201,88 @@ def test_fp32_mode_error_grows_with_weak_residuals_and_compensated_does_not(d):
     print("seed 1 gradient rel-L2: fp32 %.2e, compensated %.2e" % (e32, ec))
     assert e32 > GRAD_TOL
     assert ec <= GRAD_TOL
+
+
+def test_compensated_edge_cases(d):
+    """Elements on the grid corners, a transmitter that also receives (listed twice), a receive
+    subset that changes per transmit, per-transmit pulses, and the shortest time axes."""
+    nx, nz = 40, 33
+    elem_ix = np.array([0, nx - 1, 0, nx - 1, 17], np.int32)
+    elem_iz = np.array([0, 0, nz - 1, nz - 1, 16], np.int32)
+    tx = np.array([4, 0], np.int32)
+    rx = np.array([[4, 4, 0, 1], [2, 3, 0, 4]], np.int32)
+    rng = np.random.default_rng(1)
+    C = (1540.0 + 30.0 * rng.standard_normal((1, nz, nx))).astype(np.float32)
+    for nt in (1, 2, 3, 150):
+        w = np.stack([inputs.ricker(nt, 1e-8, 2e6), 0.5 * inputs.ricker(nt, 1e-8, 1.5e6)]).astype(np.float32)
+        pb = d.Problem(nx=nx, nz=nz, dx=1e-4, dt=1e-8, nt=nt, c_max=1800.0, forward_precision="compensated")
+        geom = d.Geometry(elem_ix, elem_iz, tx, rx, wavelet_per_tx=True)
+        cd = d.simulate(pb, torch.from_numpy(C).cuda(), torch.from_numpy(w).cuda(), geom, check=True).cpu().numpy()
+        p = oracle.Problem(nx=nx, nz=nz, dx=1e-4, dt=1e-8, nt=nt, pml=20, pml_cref=1540.0, fd_order=8)
+        for k in range(2):
+            ref = oracle.forward(p, C[0].astype(np.float64), (elem_ix[tx[k]], elem_iz[tx[k]]), w[k].astype(np.float64),
+                                 elem_ix[rx[k]], elem_iz[rx[k]])
+            if nt <= 2:
+                # U[0] = 0 and U[1] is the scaled first pulse sample at the transmitter, rounded once
+                assert np.array_equal(cd[0, k], ref.astype(np.float32))
+            else:
+                assert rel_l2(cd[0, k], ref) <= TRACE_TOL
+        assert np.array_equal(cd[0, 0, :, 0], cd[0, 0, :, 1])
+
+
+def test_compensated_no_receivers_and_zero_residual(d):
+    """No receivers: empty channel data, J = 0 and g = 0. Observed data equal to the compensated
+    simulation's own (FP32-rounded) traces: J and g come only from the dropped low parts, so J
+    is tiny against the misfit of a real scatterer."""
+    pb = d.Problem(nx=30, nz=30, dx=1e-4, dt=1e-8, nt=50, forward_precision="compensated", ckpt_interval=7)
+    geom = d.Geometry(np.array([5, 9], np.int32), np.array([0, 0], np.int32), np.array([0]), np.zeros((1, 0), np.int32))
+    w = torch.from_numpy(inputs.ricker(50, 1e-8, 2e6)).cuda()
+    sos = torch.full((1, 30, 30), 1540.0, device="cuda")
+    assert d.simulate(pb, sos, w, geom, check=True).shape == (1, 1, 50, 0)
+    J, g = d.misfit_gradient(pb, sos, w, geom, torch.zeros((1, 1, 50, 0), device="cuda"), check=True)
+    assert float(J[0]) == 0.0 and torch.count_nonzero(g).item() == 0
+    wl = inputs.make_workload("linear_disk", seed=9, nx=50, nz=50, nt=200, n_elem=12, n_tx=2)
+    geom = d.Geometry.from_workload(wl)
+    pb = _problem(d, wl, ckpt_interval=20)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    w = torch.from_numpy(wl.wavelet).cuda()
+    obs_self = d.simulate(pb, sos, w, geom)
+    J_self, _ = d.misfit_gradient(pb, sos, w, geom, obs_self, check=True)
+    obs_true = d.simulate(pb, torch.from_numpy(wl.sos_true).cuda(), w, geom)
+    J_true, _ = d.misfit_gradient(pb, sos, w, geom, obs_true, check=True)
+    # the low parts are below half an FP32 unit of the traces: J_self / |M|^2 ~ 1e-15, against a
+    # residual of about 1% for the disk (J_true / |M|^2 ~ 1e-4)
+    assert 0.0 < float(J_self[0]) <= 1e-9 * float(J_true[0])
+
+
+def test_compensated_graph_capture_replays_bit_identically(d):
+    """With DUFWI_OPT_REUSE_TABLES a repeat call issues only kernels, memsets and device copies;
+    the compensated gradient captured in a CUDA graph and replayed equals the eager one."""
+    wl = inputs.make_workload("linear_disk", seed=2, nx=48, nz=44, nt=120, n_elem=12, n_tx=2)
+    M_obs = _observed(wl)
+    pb = _problem(d, wl, ckpt_interval=25)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    w = torch.from_numpy(wl.wavelet).cuda()
+    obs = torch.from_numpy(M_obs).cuda()
+    ws = torch.empty(d.workspace_size(pb, geom, 1), dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(sos)
+    s = torch.cuda.Stream()
+    try:
+        with torch.cuda.stream(s):
+            d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)   # uploads the tables
+            s.synchronize()
+            J0, g0 = J.clone(), g.clone()
+            d.set_option(d.OPT_REUSE_TABLES, 1)   # ws stays reserved: repeat calls may skip the copies
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)
+        J.zero_()
+        g.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(J, J0) and torch.equal(g, g0)
+    finally:
+        d.set_option(d.OPT_REUSE_TABLES, 0)
+        del ws

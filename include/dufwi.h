@@ -113,10 +113,12 @@ typedef struct {
  *     (hi, lo) before rounding, so the gradient meets 1e-4 at any residual level. The traces
  *     returned are the hi planes (the FP32 rounding of the result). Costs: about 7x the FP32
  *     step's arithmetic, two more field planes and 8 B/cell more traffic per forward step, and
- *     FP32 snapshots of four planes instead of two. Constant density and the damping layer only:
- *     with a density map, the CPML, dufwi_jvp, dufwi_second_order or dufwi_hvp it returns
- *     DUFWI_ERR_UNSUPPORTED. The launch options (tile height, two steps, persistent sweeps) do not
- *     apply: the compensated step runs one launch per step on 64 x 32 tiles. */
+ *     FP32 snapshots of four planes instead of two. With a density map the staggered operator of
+ *     Eq. 1 is compensated the same way (integer staggered weights, buoyancies and kappa' as
+ *     hi + lo; about 10x the FP32 variable-density step's arithmetic). With the CPML, dufwi_jvp,
+ *     dufwi_second_order or dufwi_hvp it returns DUFWI_ERR_UNSUPPORTED. The launch options (tile
+ *     height, two steps, persistent sweeps, multi-tile) do not apply: the compensated step runs
+ *     one launch per step on 64 x 32 tiles. */
 #define DUFWI_FORWARD_FP32 0
 #define DUFWI_FORWARD_COMPENSATED 1
 

@@ -108,6 +108,7 @@ struct Layout {
     bool comp;
     int snap_planes;
     size_t o_fl[2], o_kqh, o_kql, o_dampc, o_cdl;
+    size_t o_bxl, o_bzl;     // compensated steps with a density map: low parts of the buoyancies
 };
 
 // Last table contents uploaded to each workspace (see common_setup), and whether a call may
@@ -239,6 +240,8 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         L->o_kqh = take((size_t)n_maps * L->slice * sizeof(float));
         L->o_kql = take((size_t)n_maps * L->slice * sizeof(float));
         L->o_dampc = take(sizeof(float4) * (size_t)(L->P + 1) * (L->P + 1));
+        L->o_bxl = take((size_t)n_maps * L->slice * sizeof(float));
+        L->o_bzl = take((size_t)n_maps * L->slice * sizeof(float));
         if (gradient) L->o_cdl = take(cdb);
     }
     if (gradient) {
@@ -425,7 +428,8 @@ struct Ctx {
     float *cd_lo = nullptr;                   // compensated: low parts of the traces of the current sweep
     CompParams cq;                            // compensated: constant arguments of the step
     FieldMaps lomap[2];                       // compensated: maps of the low planes of the forward ring
-    CUtensorMap kqh1, kql1;                   // compensated: kappa' / s_R, hi and lo
+    CUtensorMap kqh1, kql1;                   // compensated: kappa' / s_R (or / S^2 with density), hi and lo
+    CUtensorMap bxl1, bzl1;                   // compensated with density: low parts of the buoyancies
     int mem_par = 0;                          // CPML: which memory-variable set the next forward step reads
     int amem_par = 0;                         // CPML: the same for the adjoint's own sets (gradient calls)
     CpmlMaps cm_fwd[2], cm_adj[2];            // CPML: maps reading set 0 / set 1
@@ -511,7 +515,7 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     if (c.so && density) return DUFWI_ERR_UNSUPPORTED;
     if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
     c.comp = L.comp;
-    if (c.comp && (density || c.cpml || c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
+    if (c.comp && (c.cpml || c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
     if (c.vd && c.pb->c_max * c.pb->dt / c.pb->dx > stagger_stability_limit(c.pb->fd_order)) return DUFWI_ERR_CFL;
     c.two_step = g_two_step != 0 && !c.sizes && !c.jvp && !c.vd && !c.so && !c.comp;
     c.persistent = g_persistent != 0 && !c.two_step && !c.jvp && !c.vd && !c.so && !c.comp;
@@ -629,7 +633,12 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                            L.n_maps, L.Nx, L.Nz, L.P, L.nxp, L.nzp, L.pitch, pb->dt / pb->dx, c.cpml ? 0.0 : d0,
                            pb->dt, pb->c_max, c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.cpml && !density,
                            c.st));
-    if (c.comp)
+    if (c.comp && density)
+        CKL(launch_setup_comp_vd(sos, density, c.at<float>(L.o_kqh), c.at<float>(L.o_kql), c.at<float>(L.o_bxl),
+                                 c.at<float>(L.o_bzl), L.n_maps, L.Nx, L.Nz, L.P, L.nzp, L.pitch, pb->dt / pb->dx,
+                                 comp_stagger_scale(pb->fd_order), d0, pb->dt,
+                                 c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.st));
+    else if (c.comp)
         CKL(launch_setup_kq(sos, c.at<float>(L.o_kqh), c.at<float>(L.o_kql), L.n_maps, L.Nx, L.Nz, L.P, L.nzp,
                             L.pitch, pb->dt / pb->dx, comp_weight_scale(pb->fd_order), d0, pb->dt,
                             c.sizes ? c.at<int2>(L.o_mapdims) : nullptr, c.st));
@@ -653,10 +662,16 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
         c.cq.cd_lo = nullptr;
         c.cq.damp = c.at<float4>(L.o_dampc);
         c.cq.src_lo = (float)(s64 - (double)(float)s64);
-        c.cq.hist_scale = (float)(1.0 / comp_weight_scale(pb->fd_order));
+        // the history holds the operator with the textbook weights: S(U) / s_R, or G / S^2 with density
+        const double sc = c.vd ? comp_stagger_scale(pb->fd_order) * comp_stagger_scale(pb->fd_order)
+                               : comp_weight_scale(pb->fd_order);
+        c.cq.hist_scale = (float)(1.0 / sc);
     }
     if (c.vd && (tensor_map(&c.bx1, c.at<float>(L.o_bx), L, L.n_maps, 0, kVFxX, kVTileZ) ||
                  tensor_map(&c.bz1, c.at<float>(L.o_bz), L, L.n_maps, 0, kTileX, kVFzZ)))
+        return DUFWI_ERR_CUDA;
+    if (c.comp && c.vd && (tensor_map(&c.bxl1, c.at<float>(L.o_bxl), L, L.n_maps, 0, kVFxX, kVTileZ) ||
+                           tensor_map(&c.bzl1, c.at<float>(L.o_bzl), L, L.n_maps, 0, kTileX, kVFzZ)))
         return DUFWI_ERR_CUDA;
     if (c.cpml) {
         // memory-variable sets: buffers 0-3 (psi_x, psi_z, xi_x, xi_z) and 4-7; maps reading set k
@@ -764,6 +779,26 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
     p.out = rg.buf[rg.prv];
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
+    if (rg.lo[0] && mode != kAdjoint && c.vd) {   // compensated variable-density forward step
+        CompVdMaps cm;
+        memset(&cm, 0, sizeof(cm));
+        cm.hi_box = rg.map[rg.cur].box2;
+        cm.lo_box = rg.lmap[rg.cur].box2;
+        cm.hi_tile = rg.map[rg.prv].tile1;
+        cm.lo_tile = rg.lmap[rg.prv].tile1;
+        cm.kq_hi = c.kqh1;
+        cm.kq_lo = c.kql1;
+        cm.bx_hi = c.bx1;
+        cm.bx_lo = c.bxl1;
+        cm.bz_hi = c.bz1;
+        cm.bz_lo = c.bzl1;
+        CompParams q = c.cq;
+        q.out_lo = rg.lo[rg.prv];
+        q.cd_lo = c.cd_lo;
+        CKL(launch_comp_vd_step(c.L.radius, mode, cm, p, q, c.st));
+        std::swap(rg.cur, rg.prv);
+        return DUFWI_OK;
+    }
     if (rg.lo[0] && mode != kAdjoint) {   // compensated forward step on (hi, lo) planes
         CompMaps cm;
         memset(&cm, 0, sizeof(cm));

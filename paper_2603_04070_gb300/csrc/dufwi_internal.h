@@ -180,6 +180,13 @@ struct CompMaps {
     CUtensorMap hi_box, lo_box, hi_tile, lo_tile, kq_hi, kq_lo;
 };
 
+// Compensated variable-density step (comp_vd_step_kernel, 64 x 32 tiles): the U^n planes read
+// with halo 8 (boxes 80 x 48), U^{n-1} and kq tiles (64 x 32), the buoyancies as hi and lo planes
+// (x: 72 x 32 from x0 - 4; z: 64 x 40 from z0 - 4; dims (nxp, nzp, n_maps)).
+struct CompVdMaps {
+    CUtensorMap hi_box, lo_box, hi_tile, lo_tile, kq_hi, kq_lo, bx_hi, bx_lo, bz_hi, bz_lo;
+};
+
 struct CompParams {
     float *out_lo;           // low plane of U^{n-1} in, of U^{n+1} out (StepParams::out is the high plane)
     float *cd_lo;            // low parts of the channel data [S][nt][n_rx], or null
@@ -266,6 +273,15 @@ cudaError_t launch_comp_step(int radius, int mode, const CompMaps &tm, const Ste
                              cudaStream_t st);
 // s_R: the factor that makes the central weights of order `order` integers (0 for other orders).
 double comp_weight_scale(int order);
+// S: the factor that makes the staggered weights of order `order` integers (0 for other orders).
+double comp_stagger_scale(int order);
+// Compensated variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist; p.tile_z 32).
+cudaError_t launch_comp_vd_step(int radius, int mode, const CompVdMaps &tm, const StepParams &p, const CompParams &q,
+                                cudaStream_t st);
+// kq = rho kappa'-form / S^2 (hi + lo) and the low parts of the buoyancies, from SoS and density.
+cudaError_t launch_setup_comp_vd(const float *sos, const float *density, float *kq_hi, float *kq_lo, float *bx_lo,
+                                 float *bz_lo, int n_maps, int Nx, int Nz, int P, int nzp, int pitch, double dt_over_dx,
+                                 double stagger_scale, double d0, double dt, const int2 *map_dims, cudaStream_t st);
 // kq = kappa' / s_R on the padded grid (FP64, split into hi + lo), for the compensated step.
 cudaError_t launch_setup_kq(const float *sos, float *kq_hi, float *kq_lo, int n_maps, int Nx, int Nz, int P, int nzp,
                             int pitch, double dt_over_dx, double weight_scale, double d0, double dt,

@@ -303,7 +303,7 @@ def test_problem_struct_layout_matches_the_header(tmp_path):
 def test_compensated_forward_validation_and_sizing():
     """The compensated forward mode adds two low planes, kappa' / s_R as hi + lo and the low
     parts of the traces, and four-plane FP32 snapshots; it is refused on the host for the CPML,
-    the Born and second-order calls, a density map, and unknown precision values."""
+    the Born and second-order calls, and unknown precision values."""
     d = _lib_module()
     g = _geom(d)
     field = 2 * (48 + 40) * ((64 + 40 + 7) // 8 * 8) * 4          # S x nzp x pitch floats, bytes
@@ -331,14 +331,6 @@ def test_compensated_forward_validation_and_sizing():
     sh = g.c_structs()[1]
     out = ctypes.c_size_t(0)
     assert d._lib.dufwi_workspace_size(ctypes.byref(bad), ctypes.byref(sh), 1, ctypes.byref(out)) == d.ERR_INVALID_ARG
-    # a density map with the compensated steps: refused before any device work (dummy pointers)
-    pb = _problem(d, forward_precision="compensated")
-    arr, sh = g.c_structs()
-    c = pb.c_struct()
-    need = d.workspace_size(pb, g, 1, gradient=False)
-    fake = ctypes.c_void_p(1 << 20)
-    assert d._lib.dufwi_simulate(ctypes.byref(c), fake, fake, ctypes.byref(arr), fake, ctypes.byref(sh), 1,
-                                 fake, ctypes.c_void_p(1 << 20), need, None) == d.ERR_UNSUPPORTED
 
 
 def test_hybrid_history_workspace_sizing():

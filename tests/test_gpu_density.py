@@ -2,10 +2,11 @@
 
 Same tolerances as the constant-density path: traces rel-L2 <= 1e-5, gradient rel-L2 <= 1e-4,
 misfit relative error <= 1e-4. The maps carry density steps of up to 1.9x (soft tissue to
-bone). The true SoS maps are the smooth-field-plus-rods kind, so that the residual stays a few
-percent of the traces: the density reflections are common to the observed and the simulated
-data, and a residual of under 1% would put the FP32 gradient error above 1e-4 by the error
-model err ~ 1e-5 |M| / |r| (see the weak-scatterer test of the constant-density path)."""
+bone). Two kinds of true SoS maps: the smooth-field-plus-rods kind, whose residual is a few
+percent of the traces (FP32 forward steps), and the 128 x 128 linear-disk kind, whose weak disk
+leaves a residual of 0.1-2% with the density reflections common to the observed and the simulated
+data; those use the compensated forward steps (hi + lo planes), since the FP32 trace error would
+reach the gradient amplified by |M| / |r|."""
 import numpy as np
 import pytest
 import torch
@@ -211,3 +212,64 @@ def test_density_born_jvp_and_adjoint_are_transposes(d):
     lhs = float((Jv.double() * q.double()).sum())
     rhs = float((torch.from_numpy(v).cuda().double() * JTq.double()).sum())
     assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+# ------------------------------------------------------------------- compensated forward steps
+COMP_TRACE_TOL = 1e-6
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_density_compensated_traces_match_oracle(d, order):
+    """The compensated staggered operator (integer staggered weights, buoyancies and kappa' as
+    hi + lo) against the oracle on a ragged grid, every order."""
+    wl, rho = _case(order + 40, 97, 71, 500, 24, 3, order=order)
+    geom = d.Geometry.from_workload(wl)
+    cd = d.simulate(_pb(d, wl, forward_precision="compensated"), torch.from_numpy(wl.sos_true).cuda(),
+                    torch.from_numpy(wl.wavelet).cuda(), geom, density=torch.from_numpy(rho).cuda(),
+                    check=True).cpu().numpy()
+    err = rel_l2(cd[0], _oracle_traces(wl, wl.sos_true[0], rho[0]))
+    print("order %d compensated density traces rel-L2 %.2e" % (order, err))
+    assert err <= COMP_TRACE_TOL
+
+
+@pytest.mark.parametrize("seed", [0, 1, 3, 8])
+def test_density_gradient_weak_disk_full_size(d, seed):
+    """The 128 x 128 linear-disk configuration (2000 steps, centre transmit, 32 receivers, one weak
+    disk) with a density map (smooth field and rods of 1050-1900 kg/m^3) common to the true and
+    the start medium: the gradient at 1540 m/s against the oracle within the plain 1e-4 bound,
+    with the compensated forward steps; every step kept for even seeds, checkpoints every 100
+    otherwise."""
+    wl = inputs.make_workload("linear_disk", seed=seed)
+    rho = inputs.density_map(inputs.rng_for(seed + 700), wl.nx, wl.nz, wl.dx)[None]
+    ckpt = 0 if seed % 2 == 0 else 100
+    obs = np.stack([_oracle_traces(wl, wl.sos_true[0], rho[0])]).astype(np.float32)
+    p = _op(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    J_ref, g_ref, M_ref = oracle.misfit_gradient(p, wl.sos_start[0].astype(np.float64), tix, tiz,
+                                                 wl.wavelet.astype(np.float64), rix, riz, obs[0].astype(np.float64),
+                                                 ckpt=ckpt, return_traces=True, rho=rho[0])
+    geom = d.Geometry.from_workload(wl)
+    J, g, cd = d.misfit_gradient(_pb(d, wl, forward_precision="compensated", ckpt_interval=ckpt),
+                                 torch.from_numpy(wl.sos_start).cuda(), torch.from_numpy(wl.wavelet).cuda(), geom,
+                                 torch.from_numpy(obs).cuda(), density=torch.from_numpy(rho).cuda(), return_cd=True,
+                                 check=True)
+    ratio = np.linalg.norm(M_ref - obs[0]) / np.linalg.norm(M_ref)
+    errs = (rel_l2(cd[0].cpu().numpy(), M_ref), abs(float(J[0]) - J_ref) / J_ref, rel_l2(g[0].cpu().numpy(), g_ref))
+    print("density seed %d |r|/|M| %.2e: traces %.2e misfit %.2e gradient %.2e" % ((seed, ratio) + errs))
+    assert ratio < 0.05
+    assert errs[0] <= COMP_TRACE_TOL
+    assert errs[1] <= 1e-6
+    assert errs[2] <= GRAD_TOL
+
+
+def test_density_compensated_checkpointed_is_bit_identical_to_store_all(d):
+    wl, rho = _case(47, 64, 56, 300, 16, 2, n_maps=2)
+    geom = d.Geometry.from_workload(wl)
+    sos, w, r = torch.from_numpy(wl.sos_start).cuda(), torch.from_numpy(wl.wavelet).cuda(), torch.from_numpy(rho).cuda()
+    obs = d.simulate(_pb(d, wl), torch.from_numpy(wl.sos_true).cuda(), w, geom, density=r)
+    J0, g0 = d.misfit_gradient(_pb(d, wl, forward_precision="compensated"), sos, w, geom, obs, density=r, check=True)
+    for ckpt, kept in ((23, 0), (23, 4)):
+        J1, g1 = d.misfit_gradient(_pb(d, wl, forward_precision="compensated", ckpt_interval=ckpt,
+                                       kept_segments=kept), sos, w, geom, obs, density=r, check=True)
+        assert torch.equal(J0, J1) and torch.equal(g0, g1)

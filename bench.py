@@ -245,6 +245,8 @@ def measure_scale(dufwi, inputs, dev, flush, stream, peak):
            "sweep_ms": {k: prof[k]["ms"] for k in kinds + ["other"]},
            "dominant": {"kernel": "step_kernel (%s sweep)" % dom, "avg_launch_us": 1e3 * avg_ms,
                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                "unique_bytes_per_launch": unique_per_launch,
+                "frac_unique_bytes": unique_per_launch / (avg_launch_ms / 1e3) / 1e9 / peak,
                         "achieved_gbs": bytes_per_launch / (avg_ms / 1e3) / 1e9,
                         "frac": bytes_per_launch / (avg_ms / 1e3) / 1e9 / peak,
                         "dram_bytes_per_launch": traffic.get(dom) if traffic else None}}
@@ -434,6 +436,9 @@ def run_ours(args):
     avg_launch_ms = prof[dom]["ms"] * launches_per_unit / max(prof[dom]["launches"], 1)
     bytes_per_launch = (ALGO_BYTES[dom] + extra) * cells * S
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+    # unique bytes: kappa' (and the buoyancies) belong to a map and are read once for its transmits
+    per_map = 4 + (VD_EXTRA_BYTES if (args.density or cpml) else 0)
+    unique_per_launch = (ALGO_BYTES[dom] + extra - per_map) * cells * S + per_map * cells * wl.n_maps
     kname = ("vd_step_kernel + cpml_step_kernel, one step" if cpml else
              "vd_step_kernel" if args.density else "step_kernel")
     roofline = {"bound": "hbm", "kernel": "%s (%s sweep)" % (kname, dom), "achieved": achieved, "peak": peak,
@@ -441,6 +446,8 @@ def run_ours(args):
                 "traffic": None if (args.density or cpml) else kernel_traffic(dom),
                 "traffic_warm_l2": None if (args.density or cpml) else kernel_traffic(dom, "per_launch_dram_bytes_warm_l2"),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
+                "unique_bytes_per_launch": unique_per_launch,
+                "frac_unique_bytes": unique_per_launch / (avg_launch_ms / 1e3) / 1e9 / peak,
                 "avg_launch_us": 1e3 * avg_launch_ms,
                 "sweep_ms_per_step": {k: prof[k]["ms"] / args.steps for k in kinds + ["other"]},
                 "launches_per_step": {k: prof[k]["launches"] / args.steps for k in kinds + ["other"]}}

@@ -245,8 +245,6 @@ def measure_scale(dufwi, inputs, dev, flush, stream, peak):
            "sweep_ms": {k: prof[k]["ms"] for k in kinds + ["other"]},
            "dominant": {"kernel": "step_kernel (%s sweep)" % dom, "avg_launch_us": 1e3 * avg_ms,
                         "algorithmic_bytes_per_launch": bytes_per_launch,
-                "unique_bytes_per_launch": unique_per_launch,
-                "frac_unique_bytes": unique_per_launch / (avg_launch_ms / 1e3) / 1e9 / peak,
                         "achieved_gbs": bytes_per_launch / (avg_ms / 1e3) / 1e9,
                         "frac": bytes_per_launch / (avg_ms / 1e3) / 1e9 / peak,
                         "dram_bytes_per_launch": traffic.get(dom) if traffic else None}}

@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--hybrid-gb", type=float, default=40.0,
                     help="workspace budget (GB) of the hybrid-history gradient measured beside the headline "
                          "(0: skip)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 128x128 gradient and the 512-shot uneven batch measured beside the headline")
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the 1024x1024, 64-transmit, 12000-step gradient measured beside the headline")
     return ap.parse_args()
@@ -585,6 +587,15 @@ def run_ours(args):
             and args.forward_precision == "fp32":
         scale = measure_scale(dufwi, inputs, dev, flush, stream, peak)
 
+    # the other configurations of the method beside the headline: the 128 x 128 gradient (FP32 and
+    # compensated) and the 512-shot uneven-grid batch (its options are tuned, then restored)
+    linear_disk = batching = None
+    if args.workload == "full_shot_set" and not (args.density or cpml) and args.forward_precision == "fp32" \
+            and not args.no_configs:
+        from paper_2603_04070_gb300 import autotune
+        linear_disk = measure_linear_disk(dufwi, inputs, dev, flush, stream)
+        batching = measure_uneven_batch(dufwi, inputs, autotune, dev, 6000, 2, 1)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         steps = wl.nt
@@ -601,110 +612,164 @@ def run_ours(args):
                 "hbm_roofline_frac_40B": hbm_frac, "ms_per_gradient": ms_step,
                 "ms_per_dufwi_iteration": ms_step + net_ms, "ms_update_net": net_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-                "store_all": store_all, "hybrid": hybrid, "scale": scale, "autotune": tuned,
+                "store_all": store_all, "hybrid": hybrid, "scale": scale, "linear_disk": linear_disk,
+                "uneven_batch": batching, "autotune": tuned,
                 "clocks": clk.summary(), "profile_complete": prof["complete"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_uneven_batch(args):
+def measure_uneven_batch(dufwi, inputs, autotune, dev, nt, steps, warmup):
     """Shots/s of the forward simulation for 32 maps of uneven grids x 16 transmits (512 shots)
-    advanced together (one launch per time step), against one shot per call on its own grid
-    (each call replayed from a CUDA graph) on a sample of the same shots."""
+    advanced together (one launch per time step, the whole call replayed from a CUDA graph),
+    against one shot per call on its own grid (each call replayed from a CUDA graph) on a sample
+    of the same shots. The launch options it tunes are restored afterwards."""
+    import torch
+    saved = {k: dufwi.get_option(o) for k, o in (("tile_z", dufwi.OPT_TILE_Z), ("two_step", dufwi.OPT_TWO_STEP),
+                                                 ("persistent", dufwi.OPT_PERSISTENT),
+                                                 ("multi_tile", dufwi.OPT_MULTI_TILE),
+                                                 ("early", dufwi.OPT_EARLY_LOADS))}
+    wl, sizes = inputs.uneven_batch(seed=0, nt=nt)
+    pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
+    geom = dufwi.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_true).to(dev)
+    wav = torch.from_numpy(wl.wavelet).to(dev)
+    try:
+        tuned = autotune.tune(pb, sos, wav, geom, sizes=sizes)
+        ws = torch.empty(dufwi.workspace_size(pb, geom, wl.n_maps, gradient=False), dtype=torch.uint8, device=dev)
+        cd = torch.empty((wl.n_maps, wl.n_tx, nt, wl.n_rx), dtype=torch.float32, device=dev)
+        for _ in range(max(warmup, 1)):
+            dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        for _ in range(steps):
+            dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
+        e[1].record()
+        torch.cuda.synchronize()
+        eager_ms = e[0].elapsed_time(e[1]) / steps
+        # the whole batched call (one launch per step) captured once in a CUDA graph and replayed
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)    # tables uploaded
+            st.synchronize()
+            dufwi.set_option(dufwi.OPT_REUSE_TABLES, 1)                              # ws stays reserved
+            try:
+                bgraph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(bgraph, stream=st):
+                    dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
+            finally:
+                dufwi.set_option(dufwi.OPT_REUSE_TABLES, 0)
+        bgraph.replay()
+        torch.cuda.synchronize()
+        e[0].record()
+        for _ in range(steps):
+            bgraph.replay()
+        e[1].record()
+        torch.cuda.synchronize()
+        graph_ms = e[0].elapsed_time(e[1]) / steps
+        del bgraph, ws, cd
+        shots = wl.n_maps * wl.n_tx
+        # one shot per call, graph-captured, on a sample of shots spread over maps and transmits;
+        # each shot with the launch options the autotuner picks for its own (single-shot) shape
+        sample = [(b, k) for b, k in zip(range(0, wl.n_maps, 4), range(0, wl.n_tx, 2))]
+        one_ms, one_tuned = [], []
+        for b, k in sample:
+            nx_b, nz_b = sizes[b]
+            pb1 = dufwi.Problem(nx=nx_b, nz=nz_b, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
+            g1 = dufwi.Geometry(wl.elem_ix, wl.elem_iz, wl.tx_elem[k:k + 1], wl.rx_elem[k:k + 1])
+            s1 = torch.from_numpy(wl.sos_true[b:b + 1, :nz_b, :nx_b].copy()).to(dev)
+            one_tuned.append(autotune.tune(pb1, s1, wav, g1))
+            w1 = torch.empty(dufwi.workspace_size(pb1, g1, 1, gradient=False), dtype=torch.uint8, device=dev)
+            c1 = torch.empty((1, 1, nt, wl.n_rx), dtype=torch.float32, device=dev)
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)      # uploads the tables
+                st.synchronize()
+                dufwi.set_option(dufwi.OPT_REUSE_TABLES, 1)               # w1 stays reserved
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=st):
+                    dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)
+            dufwi.set_option(dufwi.OPT_REUSE_TABLES, 0)
+            graph.replay()
+            torch.cuda.synchronize()
+            e[0].record()
+            graph.replay()
+            e[1].record()
+            torch.cuda.synchronize()
+            one_ms.append(e[0].elapsed_time(e[1]))
+    finally:
+        autotune.apply(saved)
+    one_shot_per_s = 1e3 / (sum(one_ms) / len(one_ms))
+    return {"value": shots / (graph_ms / 1e3), "unit": "shots/s", "ms_per_call": graph_ms,
+            "workload": "32 disk maps on grids from 384x384, 512x512, 640x512 x 16 transmits = 512 shots, %d "
+                        "steps, 128 elements; one launch per step for all shots, the whole call replayed from a "
+                        "CUDA graph" % nt,
+            "grids": sizes, "tuned_options": {k: v for k, v in tuned.items() if k in autotune.KNOBS},
+            "eager_ms_per_call": eager_ms,
+            "one_shot_per_call": {"value": one_shot_per_s, "unit": "shots/s",
+                                  "sample": "%d shots, each its own call on its own grid, replayed from a CUDA "
+                                            "graph, launch options autotuned per shape" % len(sample),
+                                  "ms_per_shot": one_ms,
+                                  "tuned_options": [{k: v for k, v in t.items() if k in autotune.KNOBS}
+                                                    for t in one_tuned]},
+            "speedup_vs_one_shot": (shots / (graph_ms / 1e3)) / one_shot_per_s}
+
+
+def run_uneven_batch(args):
+    """The uneven-grid batch on its own line (see measure_uneven_batch)."""
     import torch
     from paper_2603_04070_gb300 import autotune, build_lib, inputs
     build_lib.build()
     from paper_2603_04070_gb300 import dufwi
     dev = torch.device("cuda", 0)
     nt = args.nt or 6000
-    wl, sizes = inputs.uneven_batch(seed=0, nt=nt)
-    pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
-    geom = dufwi.Geometry.from_workload(wl)
-    sos = torch.from_numpy(wl.sos_true).to(dev)
-    wav = torch.from_numpy(wl.wavelet).to(dev)
-    tuned = autotune.tune(pb, sos, wav, geom, sizes=sizes)
-    ws = torch.empty(dufwi.workspace_size(pb, geom, wl.n_maps, gradient=False), dtype=torch.uint8, device=dev)
-    cd = torch.empty((wl.n_maps, wl.n_tx, nt, wl.n_rx), dtype=torch.float32, device=dev)
-    for _ in range(max(args.warmup, 1)):
-        dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
-    torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    e[0].record()
-    for _ in range(args.steps):
-        dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
-    e[1].record()
-    torch.cuda.synchronize()
-    eager_ms = e[0].elapsed_time(e[1]) / args.steps
-    # the whole batched call (6000 launches) captured once in a CUDA graph and replayed
-    graph_ms = None
-    st = torch.cuda.Stream()
-    with torch.cuda.stream(st):
-        dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)    # tables uploaded
-        st.synchronize()
-        dufwi.set_option(dufwi.OPT_REUSE_TABLES, 1)                              # ws stays reserved
-        try:
-            bgraph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(bgraph, stream=st):
-                dufwi.simulate(pb, sos, wav, geom, cd=cd, workspace=ws, sizes=sizes)
-        finally:
-            dufwi.set_option(dufwi.OPT_REUSE_TABLES, 0)
-    bgraph.replay()
-    torch.cuda.synchronize()
-    e[0].record()
-    for _ in range(args.steps):
-        bgraph.replay()
-    e[1].record()
-    torch.cuda.synchronize()
-    graph_ms = e[0].elapsed_time(e[1]) / args.steps
-    batched_ms = graph_ms
-    shots = wl.n_maps * wl.n_tx
-    # one shot per call, graph-captured, on a sample of shots spread over maps and transmits; each
-    # shot with the launch options the autotuner picks for its own (single-shot) shape
-    sample = [(b, k) for b, k in zip(range(0, wl.n_maps, 4), range(0, wl.n_tx, 2))]
-    one_ms = []
-    one_tuned = []
-    for b, k in sample:
-        nx_b, nz_b = sizes[b]
-        pb1 = dufwi.Problem(nx=nx_b, nz=nz_b, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
-        g1 = dufwi.Geometry(wl.elem_ix, wl.elem_iz, wl.tx_elem[k:k + 1], wl.rx_elem[k:k + 1])
-        s1 = torch.from_numpy(wl.sos_true[b:b + 1, :nz_b, :nx_b].copy()).to(dev)
-        one_tuned.append(autotune.tune(pb1, s1, wav, g1))
-        w1 = torch.empty(dufwi.workspace_size(pb1, g1, 1, gradient=False), dtype=torch.uint8, device=dev)
-        c1 = torch.empty((1, 1, nt, wl.n_rx), dtype=torch.float32, device=dev)
-        st = torch.cuda.Stream()
-        with torch.cuda.stream(st):
-            dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)      # uploads the tables
-            st.synchronize()
-            dufwi.set_option(dufwi.OPT_REUSE_TABLES, 1)               # w1 stays reserved
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph, stream=st):
-                dufwi.simulate(pb1, s1, wav, g1, cd=c1, workspace=w1)
-        dufwi.set_option(dufwi.OPT_REUSE_TABLES, 0)
-        graph.replay()
-        torch.cuda.synchronize()
-        e[0].record()
-        graph.replay()
-        e[1].record()
-        torch.cuda.synchronize()
-        one_ms.append(e[0].elapsed_time(e[1]))
-    one_shot_per_s = 1e3 / (sum(one_ms) / len(one_ms))
-    line = {"metric": "forward simulation shots/s (uneven-grid batch)", "value": shots / (batched_ms / 1e3),
-            "unit": "shots/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms,
+    rec = measure_uneven_batch(dufwi, inputs, autotune, dev, nt, args.steps, args.warmup)
+    line = {"metric": "forward simulation shots/s (uneven-grid batch)", "value": rec["value"], "unit": "shots/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_call"],
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "32 disk maps on grids from 384x384, 512x512, 640x512 x 16 transmits = 512 "
-                                   "shots, %d steps, 128 elements; one launch per step for all shots, the whole "
-                                   "call replayed from a CUDA graph" % nt,
-                       "grids": sizes, "tuned_options": tuned},
-            "eager_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms,
-            "one_shot_per_call": {"value": one_shot_per_s, "unit": "shots/s",
-                                  "sample": "%d shots, each its own call on its own grid, replayed from a CUDA "
-                                            "graph, launch options autotuned per shape" % len(sample),
-                                  "ms_per_shot": one_ms,
-                                  "tuned_options": [{k: v for k, v in t.items() if k != "candidates_ms_per_step"}
-                                                    for t in one_tuned]},
-            "speedup_vs_one_shot": (shots / (batched_ms / 1e3)) / one_shot_per_s}
+            "config": {"workload": rec["workload"], "grids": rec["grids"], "tuned_options": rec["tuned_options"]},
+            "eager_ms_per_step": rec["eager_ms_per_call"], "graph_ms_per_step": rec["ms_per_call"],
+            "one_shot_per_call": rec["one_shot_per_call"], "speedup_vs_one_shot": rec["speedup_vs_one_shot"]}
     print(json.dumps(line), flush=True)
+
+
+def measure_linear_disk(dufwi, inputs, dev, flush, stream):
+    """The 128 x 128 linear-disk gradient (2000 steps, one transmit, 32 receivers, every step kept):
+    ms per gradient with FP32 and with compensated forward steps (the parity-grade form at weak
+    residuals). One shot of 168 x 168 padded cells per launch is far below a wave of the GPU, so the
+    time is launch latency."""
+    import torch
+    wl = inputs.make_workload("linear_disk", seed=1)
+    geom = dufwi.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).to(dev)
+    wav = torch.from_numpy(wl.wavelet).to(dev)
+    rec = {"workload": "linear_disk: 128x128 grid (+20 absorbing cells per side), 2000 steps, 32 elements, "
+                       "centre transmit, 32 receivers, every step kept"}
+    for prec in ("fp32", "compensated"):
+        pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
+                           pml_cref=wl.pml_cref, fd_order=wl.fd_order, c_max=wl.c_max, forward_precision=prec)
+        obs = dufwi.simulate(pb, torch.from_numpy(wl.sos_true).to(dev), wav, geom)
+        ws = torch.empty(dufwi.workspace_size(pb, geom, 1), dtype=torch.uint8, device=dev)
+        J = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty_like(sos)
+        for _ in range(3):
+            dufwi.misfit_gradient(pb, sos, wav, geom, obs, misfit=J, grad=g, workspace=ws)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(5):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dufwi.misfit_gradient(pb, sos, wav, geom, obs, misfit=J, grad=g, workspace=ws)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+        rec[prec] = {"ms_per_gradient": ms,
+                     "value": 2.0 * wl.padded_cells * wl.nt / (ms / 1e3) / 1e9, "unit": UNIT}
+    return rec
 
 
 def run_dufwi_loop(args):

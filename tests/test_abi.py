@@ -369,3 +369,24 @@ def test_kept_segments_for_budget_is_the_largest_fit():
             assert autotune.kept_segments_for_budget(pb, g, 1, sizes[k] - 1) == k - 1
     assert autotune.kept_segments_for_budget(pb, g, 1, sizes[1] - 1) == 0
     assert autotune.kept_segments_for_budget(_problem(d, nt=1001, ckpt_interval=0), g, 1, 1 << 40) == 0
+
+
+def test_autotune_candidates_are_valid_option_sets():
+    """Every launch form the tuner times is a set of valid option values (host-side round trip),
+    and applying a set changes only the five launch options."""
+    from paper_2603_04070_gb300 import autotune
+    d = _lib_module()
+    opts = {"tile_z": d.OPT_TILE_Z, "two_step": d.OPT_TWO_STEP, "persistent": d.OPT_PERSISTENT,
+            "multi_tile": d.OPT_MULTI_TILE, "early": d.OPT_EARLY_LOADS}
+    assert set(autotune.KNOBS) == set(opts)
+    before = {k: d.get_option(o) for k, o in opts.items()}
+    reuse = d.get_option(d.OPT_REUSE_TABLES)
+    try:
+        for cand in autotune.CANDIDATES:
+            autotune.apply(cand)
+            assert {k: d.get_option(o) for k, o in opts.items()} == cand
+            assert d.get_option(d.OPT_REUSE_TABLES) == reuse
+        assert len({tuple(sorted(c.items())) for c in autotune.CANDIDATES}) == len(autotune.CANDIDATES)
+    finally:
+        autotune.apply(before)
+    assert {k: d.get_option(o) for k, o in opts.items()} == before

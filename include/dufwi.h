@@ -87,8 +87,9 @@ typedef struct {
     double  pml_alpha;       /* CPML only: frequency shift at the layer's inner edge (1/s), >= 0 */
     int32_t forward_precision; /* DUFWI_FORWARD_*: arithmetic of the forward (and recompute) steps */
     int32_t kept_segments;   /* gradient calls with checkpoints: how many of the last checkpoint
-                              * segments keep their history from the forward sweep (0 = recompute
-                              * every segment; >= the segment count = keep all, no snapshots) */
+                              * segments keep their history from the forward sweep (at least the
+                              * last one, which costs no memory: 0 and 1 are the same; >= the
+                              * segment count = keep all, no snapshots) */
 } dufwi_problem;
 
 /* Hybrid history (kept_segments = k > 0 with ckpt_interval K > 0): the forward sweep writes the
@@ -97,7 +98,8 @@ typedef struct {
  * segments, then recomputes each earlier segment from its snapshot into the slots the kept
  * segments have freed. The history ring holds max(k, 1) segments, so the workspace grows by
  * (k - 1) K fields of S x (nz + 2P) x pitch floats, less the snapshots of the kept segments, and
- * each kept segment saves one recompute of K steps. The results are bit-identical to keeping
+ * each kept segment saves one recompute of K steps. The last segment is always kept (k >= 1): the
+ * ring holds one segment in any case. The results are bit-identical to keeping
  * every step (the recompute reproduces the forward sweep exactly with FP32 snapshots).
  * dufwi_misfit, dufwi_jvp and the second-order calls ignore it. */
 

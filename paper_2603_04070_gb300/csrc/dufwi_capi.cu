@@ -185,7 +185,9 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     // hybrid history (gradient calls): the last n_keep segments keep the history written by the
     // forward sweep; the recompute of earlier segments reuses their slots once the adjoint has
     // consumed them, so the ring holds max(n_keep, 1) segments
-    L->n_keep = (gradient && L->n_seg > 1) ? std::min(pb->kept_segments, L->n_seg) : 0;
+    // (the last segment always keeps its forward history: its K slots are the ring's anyway, so
+    // kept_segments 0 and 1 lay out and run the same)
+    L->n_keep = (gradient && L->n_seg > 1) ? std::min(std::max(pb->kept_segments, 1), L->n_seg) : 0;
     L->first_kept = L->n_seg - L->n_keep;
     if (L->n_keep > 0) L->n_hist = L->n_keep * L->K;
     if (kind == kLayoutJvp) L->n_hist = 1;

@@ -134,7 +134,7 @@ def test_boundary_and_option_validation():
     ck = d.workspace_size(_problem(d, nt=2001, boundary="cpml", ckpt_interval=50), g, 1)
     ck0 = d.workspace_size(_problem(d, nt=2001, ckpt_interval=50), g, 1)
     field = 2 * (48 + 40) * ((64 + 40 + 7) // 8 * 8) * 4
-    assert ck - ck0 >= (8 + 8 + 40 * 4) * field
+    assert ck - ck0 >= (8 + 8 + 39 * 4) * field              # 40 segments, the last one kept
     with pytest.raises(d.DufwiError) as e:               # no Born step on the staggered operators
         d.jvp_workspace_size(_problem(d, boundary="cpml"), g, 1)
     assert e.value.status == d.ERR_UNSUPPORTED
@@ -317,7 +317,7 @@ def test_compensated_forward_validation_and_sizing():
                 - d.workspace_size(_problem(d, **ck), g, 1))
     gap_fp16 = (d.workspace_size(_problem(d, forward_precision="compensated", snapshot_dtype="fp16", **ck), g, 1)
                 - d.workspace_size(_problem(d, snapshot_dtype="fp16", **ck), g, 1))
-    assert gap_fp32 - gap_fp16 >= 20 * 2 * field
+    assert gap_fp32 - gap_fp16 >= 19 * 2 * field             # 20 segments, the last one kept
     for kw in (dict(boundary="cpml"),):
         with pytest.raises(d.DufwiError) as e:
             d.workspace_size(_problem(d, forward_precision="compensated", **kw), g, 1)
@@ -342,11 +342,13 @@ def test_hybrid_history_workspace_sizing():
     K, nt = 50, 1001                                     # 20 segments
     base = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K), g, 1)
     k1 = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=1), g, 1)
+    assert base == k1                                        # the last segment is always kept
     k5 = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=5), g, 1)
     kall = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=20), g, 1)
     kmore = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, kept_segments=500), g, 1)
     store_all = d.workspace_size(_problem(d, nt=nt, ckpt_interval=0), g, 1)
-    assert abs(k1 - (base - 2 * field)) <= 4096             # one segment's snapshot fewer
+    plain = d.workspace_size(_problem(d, nt=nt, ckpt_interval=K, snapshot_dtype="fp32"), g, 1)
+    assert plain == base
     assert abs(k5 - k1 - 4 * K * field + 4 * 2 * field) <= 4096
     assert kall == kmore
     assert abs(kall - store_all) <= K * field + 4096          # 20 K slots against nt - 1 = 1000 steps
@@ -363,10 +365,10 @@ def test_kept_segments_for_budget_is_the_largest_fit():
     pb = _problem(d, nt=1001, ckpt_interval=50)
     sizes = [d.workspace_size(_problem(d, nt=1001, ckpt_interval=50, kept_segments=k), g, 1) for k in range(21)]
     assert all(a <= b for a, b in zip(sizes[1:], sizes[2:]))
-    for k in (1, 7, 20):
+    for k in (2, 7, 20):
         assert autotune.kept_segments_for_budget(pb, g, 1, sizes[k]) == k
-        if k > 1:
-            assert autotune.kept_segments_for_budget(pb, g, 1, sizes[k] - 1) == k - 1
+        assert autotune.kept_segments_for_budget(pb, g, 1, sizes[k] - 1) == k - 1
+    assert sizes[0] == sizes[1]
     assert autotune.kept_segments_for_budget(pb, g, 1, sizes[1] - 1) == 0
     assert autotune.kept_segments_for_budget(_problem(d, nt=1001, ckpt_interval=0), g, 1, 1 << 40) == 0
 

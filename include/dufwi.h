@@ -285,9 +285,10 @@ int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, c
  *   so      [n_maps][nz][nx] float, device, output
  *   grad    NULL or [n_maps][nz][nx] float, device, output: (dM/dC)^T cd_grad
  *   workspace: device, >= dufwi_second_order_workspace_size bytes.
- * Constant density and the damping layer only: a density map or DUFWI_BOUNDARY_CPML gives
- * DUFWI_ERR_UNSUPPORTED. The launch options (tile height, two-step, persistent) do not apply:
- * every step uses 64 x 32 tiles, one launch per step. */
+ * With a density map all three fields use the staggered variable-density operator of Eq. 1 (the
+ * operator is symmetric, so the adjoint kinds use it as they are). DUFWI_BOUNDARY_CPML and the
+ * compensated forward steps give DUFWI_ERR_UNSUPPORTED. The launch options (tile height,
+ * two-step, persistent) do not apply: every step uses 64 x 32 tiles, one launch per step. */
 int dufwi_second_order_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots,
                                       int32_t n_maps, size_t *bytes);
 int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *density,

@@ -514,7 +514,6 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     // the Born step runs on the variable-density operator, not with the CPML's memory variables;
     // the second-order kernels use the compact Laplacian (constant density) only
     if (c.cpml && (c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
-    if (c.so && density) return DUFWI_ERR_UNSUPPORTED;
     if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
     c.comp = L.comp;
     if (c.comp && (c.cpml || c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
@@ -1566,7 +1565,11 @@ int so_step(Ctx &c, Ring &r, int kind, StepParams p, const SoParams &q, long lon
 {
     SoMaps tm;
     memset(&tm, 0, sizeof(tm));
-    tm.cur_box = r.map[r.cur].box1;
+    tm.cur_box = c.vd ? r.map[r.cur].box2 : r.map[r.cur].box1;   // 80 x 48 (halo 8) for the staggered operator
+    if (c.vd) {
+        tm.bx = c.bx1;
+        tm.bz = c.bz1;
+    }
     tm.out_tile = r.map[r.prv].tile1;
     tm.kap_tile = c.kap1;
     tm.h1 = c.hist1;
@@ -1581,7 +1584,7 @@ int so_step(Ctx &c, Ring &r, int kind, StepParams p, const SoParams &q, long lon
     p.out = r.buf[r.prv];
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
-    CKL(launch_so_step(c.L.radius, kind, tm, p, q, c.st));
+    CKL(launch_so_step(c.L.radius, kind, c.vd, tm, p, q, c.st));
     std::swap(r.cur, r.prv);
     return DUFWI_OK;
 }

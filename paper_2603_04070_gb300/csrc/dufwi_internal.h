@@ -199,6 +199,7 @@ struct CompParams {
 // tensor maps and extra arguments of so_step_kernel (64 x 32 tiles).
 struct SoMaps {
     CUtensorMap cur_box, out_tile, kap_tile;   // the advanced field (box with halo, previous tile), kappa'
+    CUtensorMap bx, bz;                        // variable density: half-point buoyancies (72 x 32, 64 x 40)
     CUtensorMap h1, h2;                        // histories [slot][S]: Lap(U^n), Lap(dU^n)
     CUtensorMap src;                           // Lap(mu^{m+1}) of the current adjoint step [S]
     CUtensorMap dk;                            // dkappa' [n_maps]
@@ -258,7 +259,9 @@ cudaError_t launch_step_cpml(int radius, int mode, const StepMaps &tm, const Cpm
 // Variable-density step (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint, kBorn; 64 x 32 tiles).
 cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
 // One step of the second-order sweeps (kinds kSoBorn, kSoAdj, kSoBornAdj; 64 x 32 tiles).
-cudaError_t launch_so_step(int radius, int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,
+// vd: the staggered variable-density operator (cur_box 80 x 48 with halo 8, buoyancy maps set)
+// instead of the compact Laplacian (cur_box 72 x 40).
+cudaError_t launch_so_step(int radius, int kind, bool vd, const SoMaps &tm, const StepParams &p, const SoParams &q,
                            cudaStream_t st);
 // Second-order term before the fold: a += b - (v / C) g on the padded grid of every shot, with v
 // and C edge-replicated into the absorbing layer.

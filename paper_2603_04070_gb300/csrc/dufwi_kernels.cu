@@ -543,6 +543,110 @@ step_mt_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 
 // </one-step kernel source>
 
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// The staggered operator of Eq. 1, G = D-_x(b_x D+_x u) + D-_z(b_z D+_z u) (unscaled), at the 4 x 4
+// block of cells (lx .. lx + 3, lz .. lz + 3) of a 64 x 32 tile: box is the 80 x 48 field box (column
+// 0 = x0 - 8, row 0 = z0 - 8), bxs the 72 x 32 x-buoyancy tile (column h = half point
+// x0 - 4 + h + 1/2), bzs the 64 x 40 z-buoyancy tile (row j = half point z0 - 4 + j + 1/2), sw the
+// staggered weights. lap receives G, ctr the field at the block's cells.
+template <int R>
+__device__ __forceinline__ void vd_operator_block(const float *box, const float *bxs, const float *bzs, int lx, int lz,
+                                                  const float *sw, float4 (&lap)[4], float4 (&ctr)[4])
+{
+    // The arithmetic runs on packed FP32 pairs (f32x2: the same IEEE operations per lane, in the
+    // same order as the scalar form). Along x the pairs are two neighbouring half points (fluxes)
+    // or two neighbouring cells (divergence), built once per row from shifted copies so that
+    // every packed operand is an aligned register pair; along z they are two columns of a float4.
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float *row = box + (lz + j + kVHalo) * kVBoxX + lx;
+        float w[20];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float4 v = ld4s(row + 4 * c);
+            w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+        }
+        const float *brow = bxs + (lz + j) * kVFxX + lx;
+        float bw[12];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 v = ld4s(brow + 4 * c);
+            bw[4 * c] = v.x; bw[4 * c + 1] = v.y; bw[4 * c + 2] = v.z; bw[4 * c + 3] = v.w;
+        }
+        // flux h (h = 0..10) = bw[h] sum_k s_k (w[h + 4 + k] - w[h + 5 - k]); pairs (h, h + 1), h even
+        float flux[12];
+#pragma unroll
+        for (int h = 0; h < 12; h += 2) {
+            float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                const float2 hi = make_float2(w[h + 4 + k], h + 5 + k < 20 ? w[h + 5 + k] : 0.0f);
+                const float2 lo = make_float2(w[h + 5 - k], w[h + 6 - k]);
+                acc = __ffma2_rn(make_float2(sw[k - 1], sw[k - 1]), __fadd2_rn(hi, neg2(lo)), acc);
+            }
+            const float2 f = __fmul2_rn(make_float2(bw[h], bw[h + 1]), acc);
+            flux[h] = f.x;
+            flux[h + 1] = f.y;
+        }
+        // divergence at cells q = 0..3: sum_k s_k (flux[q + k + 3] - flux[q - k + 4]); pairs (q, q + 1)
+        float2 lxv[2];
+#pragma unroll
+        for (int q = 0; q < 4; q += 2) {
+            float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int k = 1; k <= R; ++k)
+                acc = __ffma2_rn(make_float2(sw[k - 1], sw[k - 1]),
+                                 __fadd2_rn(make_float2(flux[q + k + 3], flux[q + k + 4]),
+                                            neg2(make_float2(flux[q - k + 4], flux[q - k + 5]))),
+                                 acc);
+            lxv[q / 2] = acc;
+        }
+        lap[j] = make_float4(lxv[0].x, lxv[0].y, lxv[1].x, lxv[1].y);
+        ctr[j] = make_float4(w[8], w[9], w[10], w[11]);
+    }
+    {
+        float4 col[18];
+#pragma unroll
+        for (int r = 0; r < 18; ++r) col[r] = ld4s(box + (lz + 1 + r) * kVBoxX + lx + kVHalo);
+        float2 lzv[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lzv[j][0] = lzv[j][1] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int f = 0; f < 11; ++f) {
+            // flux at half-point row lz + f: box rows lz + f + 4 + k and lz + f + 5 - k = col[f + 3 + k], col[f + 4 - k]
+            float2 d[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                const float4 up = col[f + 3 + k], dn = col[f + 4 - k];
+                const float2 sk = make_float2(sw[k - 1], sw[k - 1]);
+                d[0] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.x, up.y), neg2(make_float2(dn.x, dn.y))), d[0]);
+                d[1] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.z, up.w), neg2(make_float2(dn.z, dn.w))), d[1]);
+            }
+            const float4 b = ld4s(bzs + (lz + f) * kTileX + lx);
+            const float2 fl[2] = {__fmul2_rn(make_float2(b.x, b.y), d[0]), __fmul2_rn(make_float2(b.z, b.w), d[1])};
+            // output row j takes +s_k from flux j + k + 3 and -s_k from flux j - k + 4
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int kp_ = f - j - 3, km_ = j + 4 - f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (kp_ >= 1 && kp_ <= R)
+                        lzv[j][h] = __ffma2_rn(make_float2(sw[kp_ - 1], sw[kp_ - 1]), fl[h], lzv[j][h]);
+                    if (km_ >= 1 && km_ <= R)
+                        lzv[j][h] = __ffma2_rn(make_float2(-sw[km_ - 1], -sw[km_ - 1]), fl[h], lzv[j][h]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 a01 = __fadd2_rn(make_float2(lap[j].x, lap[j].y), lzv[j][0]);
+            const float2 a23 = __fadd2_rn(make_float2(lap[j].z, lap[j].w), lzv[j][1]);
+            lap[j] = make_float4(a01.x, a01.y, a23.x, a23.y);
+        }
+    }
+}
+
 // ---- second-order products ---------------------------------------------------------------------
 // For a cotangent w on the channel data and an SoS direction v, the derivative along v of
 // G = (dM/dC)^T w (Eq. 6 for w = 2 (M - M_obs)) follows from differentiating the discrete adjoint
@@ -554,21 +658,26 @@ step_mt_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 // so_step_kernel advances one of the three fields by one step with the extra terms of its kind
 // (SoKind). It is the one-step kernel's tile scheme (64 x 32 tiles, 128 threads, 4 x 4 outputs
 // per thread, one mbarrier for all TMA loads) with more operand tiles and no early loads.
-template <int KIND>
+template <int KIND, bool VD>
 struct SoLayout {
-    static constexpr int kBox = kBoxX * (32 + 2 * kHalo);
+    // the field box: 72 x 40 (halo 4) for the compact Laplacian, 80 x 48 (halo 8) and the two
+    // half-point buoyancy tiles (72 x 32, 64 x 40) for the staggered variable-density operator
+    static constexpr int kBox = VD ? kVBoxX * kVBoxZ : kBoxX * (32 + 2 * kHalo);
+    static constexpr int kB = VD ? kVFxX * kVTileZ + kTileX * kVFzZ : 0;
     static constexpr int kTile = kTileX * 32;
     // prev, kappa' + (Born: Lap(U^n), dkappa'; adjoint: two histories, two sums;
     // Born-adjoint: history, Lap(mu^{m+1}), dkappa', sum)
     static constexpr int kTiles = KIND == kSoBorn ? 4 : 6;
-    static constexpr uint32_t kBytes = (kBox + kTiles * kTile) * sizeof(float);
+    static constexpr uint32_t kBytes = (kBox + kB + kTiles * kTile) * sizeof(float);
 };
 
-template <int R, int KIND>
-__global__ void __launch_bounds__(128, 3)
+template <int R, int KIND, bool VD>
+__global__ void __launch_bounds__(128, VD ? 2 : 3)
 so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoParams q)
 {
-    using SL = SoLayout<KIND>;
+    using SL = SoLayout<KIND, VD>;
+    constexpr int kH = VD ? kVHalo : kHalo;        // halo of the field box
+    constexpr int kSX = VD ? kVBoxX : kBoxX;       // its row stride
     constexpr int TZ = 32;
     extern __shared__ __align__(128) float smem[];
     __shared__ alignas(8) uint64_t bar;
@@ -582,7 +691,9 @@ so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoPa
     const int tx_idx = s % p.n_tx;
     const long long shot_off = static_cast<long long>(s) * p.slice;
     float *box = smem;
-    float *pv = box + SL::kBox;
+    float *fxb = box + SL::kBox;                   // buoyancy tiles (variable density)
+    float *fzb = fxb + (VD ? kVFxX * kVTileZ : 0);
+    float *pv = box + SL::kBox + SL::kB;
     float *kp = pv + SL::kTile;
     float *t0 = kp + SL::kTile;
     float *t1 = t0 + SL::kTile;
@@ -597,7 +708,11 @@ so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoPa
     }
     grid_dependency_wait();
     if (tid == 0) {
-        tma_load_3d(box, &tm.cur_box, &bar, x0 - kHalo, z0 - kHalo, s);
+        tma_load_3d(box, &tm.cur_box, &bar, x0 - kH, z0 - kH, s);
+        if (VD) {
+            tma_load_3d(fxb, &tm.bx, &bar, x0 - kHalo, z0, map);
+            tma_load_3d(fzb, &tm.bz, &bar, x0, z0 - kHalo, map);
+        }
         tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
         tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
         tma_load_4d(t0, &tm.h1, &bar, x0, z0, s, q.h1_slot);
@@ -635,7 +750,10 @@ so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoPa
     if (!wait_tile(&bar, p, tid)) return;
 
     float4 lap[4], ctr[4], nxt[4];
-    lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
+    if (VD)
+        vd_operator_block<R>(box, fxb, fzb, lx, lz, p.sw, lap, ctr);
+    else
+        lap_block<R, kBoxX>(box, kHalo + lx, kHalo + lz, p.c, lap, ctr);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int lo = (lz + j) * kTileX + lx;
@@ -690,7 +808,7 @@ so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoPa
                 continue;
             }
             p.cd[(static_cast<long long>(s) * p.nt + p.step) * p.n_rx + r] =
-                box[(zn - z0 + kHalo) * kBoxX + (xn - x0 + kHalo)];
+                box[(zn - z0 + kH) * kSX + (xn - x0 + kH)];
         }
     }
 }
@@ -754,8 +872,6 @@ __device__ __forceinline__ bool cpml_free_tile(const StepParams &p, int x0, int 
     return x0 - 2 * kHalo >= p.P && x0 + kTileX + 2 * kHalo <= p.P + p.Nx - 1 && z0 - 2 * kHalo >= p.P &&
            z0 + kVTileZ + 2 * kHalo <= p.P + p.Nz - 1;
 }
-
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 template <int MODE>
 struct VdLayout {
@@ -853,100 +969,8 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     // lx .. lx + 10); along z, the half-point rows lz .. lz + 10 of its four columns (box rows
     // lz + 1 .. lz + 18, buoyancy tile rows lz .. lz + 10). Box column/row 0 is x0 - 8 / z0 - 8;
     // x-buoyancy column h is the half point x0 - 4 + h + 1/2, z-buoyancy row j is z0 - 4 + j + 1/2.
-    const float *bxs = fx;
-    const float *bzs = fz;
     float4 lap[4], ctr[4], nxt[4];
-    // The arithmetic runs on packed FP32 pairs (f32x2: the same IEEE operations per lane, in the
-    // same order as the scalar form). Along x the pairs are two neighbouring half points (fluxes)
-    // or two neighbouring cells (divergence), built once per row from shifted copies so that
-    // every packed operand is an aligned register pair; along z they are two columns of a float4.
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float *row = box + (lz + j + kVHalo) * kVBoxX + lx;
-        float w[20];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const float4 v = ld4s(row + 4 * c);
-            w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
-        }
-        const float *brow = bxs + (lz + j) * kVFxX + lx;
-        float bw[12];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float4 v = ld4s(brow + 4 * c);
-            bw[4 * c] = v.x; bw[4 * c + 1] = v.y; bw[4 * c + 2] = v.z; bw[4 * c + 3] = v.w;
-        }
-        // flux h (h = 0..10) = bw[h] sum_k s_k (w[h + 4 + k] - w[h + 5 - k]); pairs (h, h + 1), h even
-        float flux[12];
-#pragma unroll
-        for (int h = 0; h < 12; h += 2) {
-            float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int k = 1; k <= R; ++k) {
-                const float2 hi = make_float2(w[h + 4 + k], h + 5 + k < 20 ? w[h + 5 + k] : 0.0f);
-                const float2 lo = make_float2(w[h + 5 - k], w[h + 6 - k]);
-                acc = __ffma2_rn(make_float2(p.sw[k - 1], p.sw[k - 1]), __fadd2_rn(hi, neg2(lo)), acc);
-            }
-            const float2 f = __fmul2_rn(make_float2(bw[h], bw[h + 1]), acc);
-            flux[h] = f.x;
-            flux[h + 1] = f.y;
-        }
-        // divergence at cells q = 0..3: sum_k s_k (flux[q + k + 3] - flux[q - k + 4]); pairs (q, q + 1)
-        float2 lxv[2];
-#pragma unroll
-        for (int q = 0; q < 4; q += 2) {
-            float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int k = 1; k <= R; ++k)
-                acc = __ffma2_rn(make_float2(p.sw[k - 1], p.sw[k - 1]),
-                                 __fadd2_rn(make_float2(flux[q + k + 3], flux[q + k + 4]),
-                                            neg2(make_float2(flux[q - k + 4], flux[q - k + 5]))),
-                                 acc);
-            lxv[q / 2] = acc;
-        }
-        lap[j] = make_float4(lxv[0].x, lxv[0].y, lxv[1].x, lxv[1].y);
-        ctr[j] = make_float4(w[8], w[9], w[10], w[11]);
-    }
-    {
-        float4 col[18];
-#pragma unroll
-        for (int r = 0; r < 18; ++r) col[r] = ld4s(box + (lz + 1 + r) * kVBoxX + lx + kVHalo);
-        float2 lzv[4][2];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) lzv[j][0] = lzv[j][1] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int f = 0; f < 11; ++f) {
-            // flux at half-point row lz + f: box rows lz + f + 4 + k and lz + f + 5 - k = col[f + 3 + k], col[f + 4 - k]
-            float2 d[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-            for (int k = 1; k <= R; ++k) {
-                const float4 up = col[f + 3 + k], dn = col[f + 4 - k];
-                const float2 sk = make_float2(p.sw[k - 1], p.sw[k - 1]);
-                d[0] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.x, up.y), neg2(make_float2(dn.x, dn.y))), d[0]);
-                d[1] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.z, up.w), neg2(make_float2(dn.z, dn.w))), d[1]);
-            }
-            const float4 b = ld4s(bzs + (lz + f) * kTileX + lx);
-            const float2 fl[2] = {__fmul2_rn(make_float2(b.x, b.y), d[0]), __fmul2_rn(make_float2(b.z, b.w), d[1])};
-            // output row j takes +s_k from flux j + k + 3 and -s_k from flux j - k + 4
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int kp_ = f - j - 3, km_ = j + 4 - f;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (kp_ >= 1 && kp_ <= R)
-                        lzv[j][h] = __ffma2_rn(make_float2(p.sw[kp_ - 1], p.sw[kp_ - 1]), fl[h], lzv[j][h]);
-                    if (km_ >= 1 && km_ <= R)
-                        lzv[j][h] = __ffma2_rn(make_float2(-p.sw[km_ - 1], -p.sw[km_ - 1]), fl[h], lzv[j][h]);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 a01 = __fadd2_rn(make_float2(lap[j].x, lap[j].y), lzv[j][0]);
-            const float2 a23 = __fadd2_rn(make_float2(lap[j].z, lap[j].w), lzv[j][1]);
-            lap[j] = make_float4(a01.x, a01.y, a23.x, a23.y);
-        }
-    }
+    vd_operator_block<R>(box, fx, fz, lx, lz, p.sw, lap, ctr);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int lo = (lz + j) * kTileX + lx;
@@ -2392,12 +2416,12 @@ cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepP
     }
 }
 
-template <int R, int KIND>
+template <int R, int KIND, bool VD>
 static cudaError_t launch_so_step_rk(const SoMaps &tm, const StepParams &p, const SoParams &q, cudaStream_t st)
 {
-    using SL = SoLayout<KIND>;
+    using SL = SoLayout<KIND, VD>;
     static DeviceCache dc;   // shared-memory attributes, set once per device
-    cudaError_t e = configure_kernel(so_step_kernel<R, KIND>, SL::kBytes, dc);
+    cudaError_t e = configure_kernel(so_step_kernel<R, KIND, VD>, SL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + 31) / 32, p.n_maps * p.n_tx);
@@ -2409,32 +2433,39 @@ static cudaError_t launch_so_step_rk(const SoMaps &tm, const StepParams &p, cons
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, so_step_kernel<R, KIND>, tm, p, q);
+    return cudaLaunchKernelEx(&cfg, so_step_kernel<R, KIND, VD>, tm, p, q);
 }
 
-template <int R>
+template <int R, bool VD>
 static cudaError_t launch_so_step_r(int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,
                                     cudaStream_t st)
 {
     switch (kind) {
-    case kSoBorn: return launch_so_step_rk<R, kSoBorn>(tm, p, q, st);
-    case kSoAdj: return launch_so_step_rk<R, kSoAdj>(tm, p, q, st);
-    case kSoBornAdj: return launch_so_step_rk<R, kSoBornAdj>(tm, p, q, st);
+    case kSoBorn: return launch_so_step_rk<R, kSoBorn, VD>(tm, p, q, st);
+    case kSoAdj: return launch_so_step_rk<R, kSoAdj, VD>(tm, p, q, st);
+    case kSoBornAdj: return launch_so_step_rk<R, kSoBornAdj, VD>(tm, p, q, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_so_step(int radius, int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,
+template <bool VD>
+static cudaError_t launch_so_step_v(int radius, int kind, const SoMaps &tm, const StepParams &p, const SoParams &q,
+                                    cudaStream_t st)
+{
+    switch (radius) {
+    case 1: return launch_so_step_r<1, VD>(kind, tm, p, q, st);
+    case 2: return launch_so_step_r<2, VD>(kind, tm, p, q, st);
+    case 3: return launch_so_step_r<3, VD>(kind, tm, p, q, st);
+    case 4: return launch_so_step_r<4, VD>(kind, tm, p, q, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_so_step(int radius, int kind, bool vd, const SoMaps &tm, const StepParams &p, const SoParams &q,
                            cudaStream_t st)
 {
     if (p.tile_z != 32 || p.map_dims) return cudaErrorInvalidValue;
-    switch (radius) {
-    case 1: return launch_so_step_r<1>(kind, tm, p, q, st);
-    case 2: return launch_so_step_r<2>(kind, tm, p, q, st);
-    case 3: return launch_so_step_r<3>(kind, tm, p, q, st);
-    case 4: return launch_so_step_r<4>(kind, tm, p, q, st);
-    default: return cudaErrorInvalidValue;
-    }
+    return vd ? launch_so_step_v<true>(radius, kind, tm, p, q, st) : launch_so_step_v<false>(radius, kind, tm, p, q, st);
 }
 
 cudaError_t launch_hvp_source(const float *cd_sim, const float *cd_obs, const float *dcd, const float *kap,

@@ -503,14 +503,14 @@ def second_order_workspace_size(problem: Problem, geom: Geometry, n_maps: int) -
 def second_order(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, cd_grad: torch.Tensor,
                  dsos: torch.Tensor, *, so: torch.Tensor | None = None, dcd: torch.Tensor | None = None,
                  grad: torch.Tensor | None = None, return_grad: bool = False, workspace: torch.Tensor | None = None,
-                 stream=None, check: bool = False):
+                 stream=None, check: bool = False, density: torch.Tensor | None = None):
     """Second-order product ``so = d/dC[(dM/dC)^T cd_grad] . dsos`` and the Born data
     ``dcd = (dM/dC) dsos`` (``dufwi_second_order``); with ``return_grad`` also
     ``grad = (dM/dC)^T cd_grad``. Returns ``(so, dcd)`` or ``(so, dcd, grad)``.
 
     With ``cd_grad = 2 (M - M_obs)`` the exact Hessian-vector product of the misfit is
-    ``so + 2 (dM/dC)^T dcd``."""
-    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, None)
+    ``so + 2 (dM/dC)^T dcd``. ``density``: optional map (variable-density operator of Eq. 1)."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, density)
     _dev_tensor(cd_grad, "cd_grad", torch.float32, cshape)
     _dev_tensor(dsos, "dsos", torch.float32, sos.shape)
     if so is None:
@@ -530,7 +530,8 @@ def second_order(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geo
         raise DufwiError(ERR_WORKSPACE, "second_order workspace")
     pb = problem.c_struct()
     arr, sh = geom.c_structs()
-    rc = _lib.dufwi_second_order(ctypes.byref(pb), sos.data_ptr(), None, ctypes.byref(arr), wavelet.data_ptr(),
+    rc = _lib.dufwi_second_order(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+                                 ctypes.byref(arr), wavelet.data_ptr(),
                                  ctypes.byref(sh), n_maps, cd_grad.data_ptr(), dsos.data_ptr(), dcd.data_ptr(),
                                  so.data_ptr(), grad.data_ptr() if grad is not None else None, workspace.data_ptr(),
                                  workspace.numel() * workspace.element_size(), _stream(stream))
@@ -543,11 +544,12 @@ def second_order(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geo
 def hvp(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geometry, cd_obs: torch.Tensor,
         dsos: torch.Tensor, *, hv: torch.Tensor | None = None, misfit: torch.Tensor | None = None,
         grad: torch.Tensor | None = None, return_all: bool = False, workspace: torch.Tensor | None = None,
-        stream=None, check: bool = False):
+        stream=None, check: bool = False, density: torch.Tensor | None = None):
     """Exact Hessian-vector product ``H dsos`` of the misfit J = sum (M - M_obs)^2 per map
     (``dufwi_hvp``), one call. With ``return_all`` returns ``(hv, misfit [n_maps] float64,
-    grad)``: the misfit and its gradient come from the same sweeps."""
-    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, None)
+    grad)``: the misfit and its gradient come from the same sweeps. ``density``: optional map
+    (variable-density operator of Eq. 1)."""
+    n_maps, cshape = _common_inputs(problem, sos, wavelet, geom, density)
     _dev_tensor(cd_obs, "cd_obs", torch.float32, cshape)
     _dev_tensor(dsos, "dsos", torch.float32, sos.shape)
     if hv is None:
@@ -569,7 +571,8 @@ def hvp(problem: Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom: Geomet
         raise DufwiError(ERR_WORKSPACE, "hvp workspace")
     pb = problem.c_struct()
     arr, sh = geom.c_structs()
-    rc = _lib.dufwi_hvp(ctypes.byref(pb), sos.data_ptr(), None, ctypes.byref(arr), wavelet.data_ptr(),
+    rc = _lib.dufwi_hvp(ctypes.byref(pb), sos.data_ptr(), density.data_ptr() if density is not None else None,
+                        ctypes.byref(arr), wavelet.data_ptr(),
                         ctypes.byref(sh), n_maps, cd_obs.data_ptr(), dsos.data_ptr(), hv.data_ptr(),
                         misfit.data_ptr() if misfit is not None else None,
                         grad.data_ptr() if grad is not None else None, workspace.data_ptr(),

@@ -170,21 +170,12 @@ def test_exact_hvp_is_symmetric(d):
     assert torch.all((a - b).abs() <= 1e-4 * torch.maximum(a.abs(), b.abs()))
 
 
-def test_second_order_rejects_density_and_third_derivatives(d):
+def test_second_order_rejects_third_derivatives(d):
     from paper_2603_04070_gb300 import autograd
     wl, v = _case(62, nt=120)
     pb = _problem(d, wl)
     geom = d.Geometry.from_workload(wl)
     sos, wav = _cuda(wl.sos_start), _cuda(wl.wavelet)
-    w = torch.zeros((1, wl.n_tx, wl.nt, wl.n_rx), device="cuda")
-    import ctypes
-    arr, sh = geom.c_structs()
-    so = torch.empty_like(sos)
-    ws = torch.empty(d.second_order_workspace_size(pb, geom, 1), dtype=torch.uint8, device="cuda")
-    rc = d._lib.dufwi_second_order(ctypes.byref(pb.c_struct()), sos.data_ptr(), sos.data_ptr(), ctypes.byref(arr),
-                                   wav.data_ptr(), ctypes.byref(sh), 1, w.data_ptr(), _cuda(v).data_ptr(), None,
-                                   so.data_ptr(), None, ws.data_ptr(), ws.numel(), None)
-    assert rc == d.ERR_UNSUPPORTED                      # a density map: no Born step on the staggered operator
     c = sos.clone().requires_grad_(True)
     J = autograd.misfit(pb, c, wav, geom, d.simulate(pb, _cuda(wl.sos_true), wav, geom)).sum()
     (g,) = torch.autograd.grad(J, c, create_graph=True)
@@ -357,3 +348,79 @@ def test_unfolded_end_to_end_gradient_matches_loss_differences(d):
     finally:
         (torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32,
          torch.backends.cudnn.deterministic, torch.backends.cudnn.benchmark) = flags
+
+
+# ------------------------------------------------------------------------------ density maps
+def _density_case(seed, nt=280):
+    wl, v = _case(seed, nt=nt)
+    rho = inputs.density_map(inputs.rng_for(seed + 300), wl.nx, wl.nz, wl.dx)
+    return wl, v, rho
+
+
+def _traces_rho(wl, C, rho):
+    p = _oracle_problem(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return np.stack([oracle.forward(p, np.asarray(C, np.float64), (tix[k], tiz[k]), wl.wavelet.astype(np.float64),
+                                    rix[k], riz[k], rho=rho) for k in range(wl.n_tx)])
+
+
+def _grad_rho(wl, C, M_obs, rho):
+    p = _oracle_problem(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return oracle.misfit_gradient(p, np.asarray(C, np.float64), tix, tiz, wl.wavelet.astype(np.float64), rix, riz,
+                                  np.asarray(M_obs, np.float64), rho=rho)[1]
+
+
+@pytest.mark.parametrize("ckpt", [0, 40])
+def test_second_order_with_density_matches_oracle_differences(d, ckpt):
+    """With a density map (the staggered operator of Eq. 1 in all three fields): the second-order
+    term against the central difference of the oracle's vector-Jacobian product with density, and
+    the Born data and the VJP against the oracle."""
+    wl, v, rho = _density_case(70)
+    C = wl.sos_start[0].astype(np.float64)
+    M_obs = _traces_rho(wl, wl.sos_true[0], rho)
+    w = 2.0 * (_traces_rho(wl, C, rho) - M_obs)
+    h = 0.05
+
+    def vjp(Cx):
+        return _grad_rho(wl, Cx, _traces_rho(wl, Cx, rho) - 0.5 * w, rho)
+
+    ref = (vjp(C + h * v[0]) - vjp(C - h * v[0])) / (2 * h)
+    pb = _problem(d, wl, ckpt_interval=ckpt)
+    pb.c_max = 2000.0
+    geom = d.Geometry.from_workload(wl)
+    so, dcd, g = d.second_order(pb, _cuda(wl.sos_start), _cuda(wl.wavelet), geom, _cuda(w[None]), _cuda(v),
+                                return_grad=True, check=True, density=_cuda(rho[None]))
+    torch.cuda.synchronize()
+    assert rel_l2(so.cpu().numpy()[0], ref) <= SO_TOL
+    assert rel_l2(g.cpu().numpy()[0], vjp(C)) <= GRAD_TOL
+    jv_ref = (_traces_rho(wl, C + h * v[0], rho) - _traces_rho(wl, C - h * v[0], rho)) / (2 * h)
+    assert rel_l2(dcd.cpu().numpy()[0], jv_ref) <= 1e-4
+
+
+def test_exact_hvp_with_density_matches_oracle_and_is_symmetric(d):
+    """dufwi_hvp with a density map against the central difference of the oracle gradient with
+    density (M_obs fixed), its misfit and gradient against dufwi_misfit_gradient with the same map,
+    and <u, H v> = <v, H u>."""
+    wl, v, rho = _density_case(71)
+    C = wl.sos_start[0].astype(np.float64)
+    M_obs = _traces_rho(wl, wl.sos_true[0], rho)
+    h = 0.05
+    ref = (_grad_rho(wl, C + h * v[0], M_obs, rho) - _grad_rho(wl, C - h * v[0], M_obs, rho)) / (2 * h)
+    pb = _problem(d, wl, ckpt_interval=35)
+    pb.c_max = 2000.0
+    geom = d.Geometry.from_workload(wl)
+    sos, wav, obs, r = _cuda(wl.sos_start), _cuda(wl.wavelet), _cuda(M_obs[None]), _cuda(rho[None])
+    hv, J, g = d.hvp(pb, sos, wav, geom, obs, _cuda(v), return_all=True, check=True, density=r)
+    J1, g1 = d.misfit_gradient(pb, sos, wav, geom, obs, density=r)
+    torch.cuda.synchronize()
+    assert rel_l2(hv.cpu().numpy()[0], ref) <= SO_TOL
+    assert torch.equal(J, J1)
+    assert rel_l2(g.cpu().numpy(), g1.cpu().numpy()) <= 1e-6
+    u = _cuda(np.random.default_rng(72).standard_normal(wl.sos_start.shape) * 5.0)
+    hu = d.hvp(pb, sos, wav, geom, obs, u, density=r)
+    a = float((u.double() * hv.double()).sum())
+    b = float((_cuda(v).double() * hu.double()).sum())
+    assert abs(a - b) <= 1e-4 * max(abs(a), abs(b))

@@ -94,13 +94,18 @@ typedef struct {
 
 /* Hybrid history (kept_segments = k > 0 with ckpt_interval K > 0): the forward sweep writes the
  * history Lap(U^n) of the last k segments of K steps as it goes and takes snapshots only at the
- * starts of the earlier ones. The reverse sweep runs the adjoint straight through the kept
+ * starts of the earlier ones and of the first kept one (that one in FP32 whatever snapshot_dtype
+ * says). The reverse sweep runs the adjoint straight through the kept
  * segments, then recomputes each earlier segment from its snapshot into the slots the kept
  * segments have freed. The history ring holds max(k, 1) segments, so the workspace grows by
- * (k - 1) K fields of S x (nz + 2P) x pitch floats, less the snapshots of the kept segments, and
- * each kept segment saves one recompute of K steps. The last segment is always kept (k >= 1): the
- * ring holds one segment in any case. The results are bit-identical to keeping
- * every step (the recompute reproduces the forward sweep exactly with FP32 snapshots).
+ * (k - 1) K fields of S x (nz + 2P) x pitch floats, less the snapshots of the kept segments but
+ * the first, and each kept segment saves one recompute of K steps. The last segment is always kept
+ * (k >= 1): the ring holds one segment in any case. The reverse sweep recomputes the earlier
+ * segments into the first kept segment's slots, so dufwi_backward recomputes that segment too,
+ * from its snapshot: it can run any number of times after one dufwi_forward_save, while
+ * dufwi_misfit_gradient uses the history its own forward sweep has just written. The results are
+ * bit-identical to keeping every step (the recompute reproduces the forward sweep exactly with
+ * FP32 snapshots).
  * dufwi_misfit, dufwi_jvp and the second-order calls ignore it. */
 
 /* Arithmetic of the forward steps (the simulation of Eqs. 2-3, and the recompute of checkpoint

@@ -89,6 +89,7 @@ struct Layout {
     int Nx, Nz, P, nxp, nzp, pitch, radius, S, n_tx, n_rx, n_maps, nt, K, n_seg, n_hist;
     int n_keep;              // gradient calls: last checkpoint segments whose history the forward sweep keeps
     int first_kept;          // n_seg - n_keep: segments before it are recomputed from snapshots
+    int n_snap;              // snapshots taken: segments 0 .. first_kept (0 when every segment is kept)
     long long slice;
     size_t snap_elem;
     // byte offsets into the workspace
@@ -98,6 +99,7 @@ struct Layout {
     size_t o_cm[8], o_cpml;  // CPML: memory variables (two sets of psi_x, psi_z, xi_x, xi_z), coefficient tables
     size_t o_cma[8];         // CPML gradients: the adjoint's memory variables (two sets), apart from the forward's
     size_t o_snapm;          // CPML gradients: FP32 snapshots of the forward memory set read at each segment start
+    size_t o_snapk;          // FP32 snapshot (hi and lo planes when compensated) of the first kept segment's start
     size_t o_flags, o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
         o_f[4], o_m[4], o_grad, o_hist, o_snap, o_scale, o_cd, o_asrc, o_part, total;
     // second-order calls: adjoint and differentiated-adjoint rings, second and third histories,
@@ -189,6 +191,9 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     // kept_segments 0 and 1 lay out and run the same)
     L->n_keep = (gradient && L->n_seg > 1) ? std::min(std::max(pb->kept_segments, 1), L->n_seg) : 0;
     L->first_kept = L->n_seg - L->n_keep;
+    // the first kept segment has a snapshot too: a reverse sweep recomputes the earlier segments
+    // into its slots, so a repeated dufwi_backward recomputes it from there
+    L->n_snap = L->first_kept > 0 ? L->first_kept + 1 : 0;
     if (L->n_keep > 0) L->n_hist = L->n_keep * L->K;
     if (kind == kLayoutJvp) L->n_hist = 1;
     L->snap_elem = pb->snapshot_dtype == DUFWI_SNAP_FP32 ? 4 : 2;
@@ -232,8 +237,8 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         if (gradient) {
             for (int i = 0; i < 8; ++i) L->o_cma[i] = take((size_t)L->S * L->slice * sizeof(float));
             // a recomputed segment restarts from (U^t, U^{t-1}) and the four memory fields read at step t
-            if (L->n_seg > 1 && L->first_kept > 0)
-                L->o_snapm = take((size_t)L->first_kept * 4 * L->S * L->slice * sizeof(float));
+            if (L->n_seg > 1 && L->n_snap > 0)
+                L->o_snapm = take((size_t)L->n_snap * 4 * L->S * L->slice * sizeof(float));
         }
     }
     for (int i = 0; i < 4; ++i) L->o_f[i] = take(field);
@@ -251,9 +256,10 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
         for (int i = 0; i < 4; ++i) L->o_m[i] = take(field);
         L->o_grad = take(field);
         L->o_hist = take(field * (size_t)L->n_hist);
-        if (!store_all && L->first_kept > 0) {   // snapshots of the recomputed segments only
+        if (!store_all && L->n_snap > 0) {   // snapshots of the recomputed segments, and the first kept one's
             L->o_snap = take((size_t)L->first_kept * L->snap_planes * L->S * L->slice * L->snap_elem);
             L->o_scale = take((size_t)L->first_kept * 2 * L->S * sizeof(unsigned));
+            L->o_snapk = take((L->comp ? 4 : 2) * field);   // exact, whatever snapshot_dtype says
         }
         L->o_cd = take(cdb);
         L->o_asrc = take(cdb);
@@ -998,9 +1004,13 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
         const int sg = n / L.K;
         // hybrid history: a kept segment writes its history into its own slots instead of a snapshot
         const bool kept = snapshots && sg >= L.first_kept;
-        if (snapshots && !kept) {
-            char *snap = c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
-            char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
+        if (snapshots && sg < L.n_snap) {
+            // the first kept segment's snapshot is FP32 in every mode: a repeated backward
+            // recomputes that segment, and must reproduce the history the forward sweep wrote
+            const bool exact = sg == L.first_kept;
+            char *snap = exact ? c.at<char>(L.o_snapk)
+                               : c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
+            char *snap_d = snap + (exact ? field : (size_t)L.S * L.slice * L.snap_elem);
             float *cur = rg.buf[rg.cur], *prv = rg.buf[rg.prv];
             if (c.cpml && L.o_snapm) {   // the CPML memory set the next step reads (set mem_par)
                 char *sm = c.at<char>(L.o_snapm) + (size_t)sg * 4 * field;
@@ -1008,10 +1018,10 @@ int forward_sweep(Ctx &c, Ring &rg, const float *wavelet, float *cd, bool store_
                     CK(cudaMemcpyAsync(sm + i * field, c.at<float>(L.o_cm[4 * c.mem_par + i]), field,
                                        cudaMemcpyDeviceToDevice, c.st));
             }
-            if (dtype == DUFWI_SNAP_FP32) {
+            if (dtype == DUFWI_SNAP_FP32 || exact) {
                 CK(cudaMemcpyAsync(snap, cur, field, cudaMemcpyDeviceToDevice, c.st));
                 CK(cudaMemcpyAsync(snap_d, prv, field, cudaMemcpyDeviceToDevice, c.st));
-                if (L.snap_planes == 4) {   // low planes of the compensated field
+                if (L.comp) {   // low planes of the compensated field
                     CK(cudaMemcpyAsync(snap + 2 * field, rg.lo[rg.cur], field, cudaMemcpyDeviceToDevice, c.st));
                     CK(cudaMemcpyAsync(snap + 3 * field, rg.lo[rg.prv], field, cudaMemcpyDeviceToDevice, c.st));
                 }
@@ -1252,7 +1262,10 @@ int gradient_forward(Ctx &c, const float *wavelet)
 
 // Second half: reverse sweep driven by the scaled adjoint source already in the workspace
 // (kappa'_r times dJ/dM), recomputing each checkpoint segment, then the fold into grad.
-int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad, double *grad64 = nullptr)
+// refresh: the first kept segment's history may have been overwritten by an earlier reverse
+// sweep (dufwi_backward), so it is recomputed from its snapshot as well.
+int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad, double *grad64 = nullptr,
+                     bool refresh = false)
 {
     const Layout &L = c.L;
     const size_t field = (size_t)L.S * L.slice * sizeof(float);
@@ -1275,7 +1288,7 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
         const int t1 = store_all ? L.nt - 1 : std::min(t0 + L.K, L.nt - 1);
         // slot of Lap(U^t) is t - h0: a kept segment's own slots, else the ring's first segment
         const int h0 = sg >= L.first_kept ? t0 - (sg - L.first_kept) * L.K : t0;
-        if (!store_all && sg < L.first_kept) {
+        if (!store_all && (sg < L.first_kept || (refresh && sg == L.first_kept && sg < L.n_snap))) {
             NvtxRange range("dufwi recompute segment");
             nl = 0;
             e0 = g_prof.mark(c.st);
@@ -1287,14 +1300,16 @@ int gradient_reverse(Ctx &c, const float *sos, const float *wavelet, float *grad
                     CK(cudaMemcpyAsync(c.at<float>(L.o_cm[4 * c.mem_par + i]), sm + i * field, field,
                                        cudaMemcpyDeviceToDevice, c.st));
             }
-            char *snap = c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
-            char *snap_d = snap + (size_t)L.S * L.slice * L.snap_elem;
+            const bool exact = sg == L.first_kept;
+            const char *snap = exact ? c.at<char>(L.o_snapk)
+                                     : c.at<char>(L.o_snap) + (size_t)sg * L.snap_planes * L.S * L.slice * L.snap_elem;
+            const char *snap_d = snap + (exact ? field : (size_t)L.S * L.slice * L.snap_elem);
             fr.cur = 0;
             fr.prv = 1;
-            if (dtype == DUFWI_SNAP_FP32) {
+            if (dtype == DUFWI_SNAP_FP32 || exact) {
                 CK(cudaMemcpyAsync(fr.buf[0], snap, field, cudaMemcpyDeviceToDevice, c.st));
                 CK(cudaMemcpyAsync(fr.buf[1], snap_d, field, cudaMemcpyDeviceToDevice, c.st));
-                if (L.snap_planes == 4) {
+                if (L.comp) {
                     CK(cudaMemcpyAsync(fr.lo[0], snap + 2 * field, field, cudaMemcpyDeviceToDevice, c.st));
                     CK(cudaMemcpyAsync(fr.lo[1], snap + 3 * field, field, cudaMemcpyDeviceToDevice, c.st));
                 }
@@ -1483,7 +1498,7 @@ int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *densi
     CKL(launch_cotangent_source(cd_grad, c.at<float>(L.o_kap), c.at<int>(L.o_rx), c.at<float>(L.o_asrc), c.status(),
                                 L.S, L.n_tx, L.n_rx, L.nt, L.slice, L.pitch, c.st));
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
-    return gradient_reverse(c, sos, wavelet, grad);
+    return gradient_reverse(c, sos, wavelet, grad, nullptr, true);
 }
 
 int dufwi_jvp_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots, int32_t n_maps, size_t *bytes)

@@ -238,6 +238,35 @@ def test_hybrid_history_with_compressed_snapshots(d):
     assert 0.0 < errs[1] <= errs[0]
 
 
+@pytest.mark.parametrize("kw", [dict(kept_segments=0), dict(kept_segments=3), dict(snapshot_dtype="fp16"),
+                                dict(forward_precision="compensated"), dict(boundary="cpml", pml_alpha=6e6)])
+def test_backward_repeats_after_one_forward_save(d, kw):
+    """dufwi_backward can run any number of times on one dufwi_forward_save workspace: a reverse
+    sweep recomputes earlier segments into the first kept segment's history slots, so each
+    backward recomputes that segment from its own snapshot. Repeated products are bit-identical,
+    and the misfit cotangent gives dufwi_misfit_gradient's gradient bit for bit."""
+    wl = inputs.make_workload("linear_disk", seed=9, nx=64, nz=64, nt=290, n_elem=16, n_tx=2, n_maps=2)
+    M_obs = _observed(wl)
+    pb = _dufwi_problem(d, wl, ckpt_interval=37, **kw)        # 8 segments
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    obs = torch.from_numpy(M_obs).cuda()
+    cd, ws = d.forward_save(pb, sos, wav, geom)
+    q = torch.randn(cd.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(3)) * 1e-9
+    w = 2.0 * (cd - obs)
+    gq1 = d.backward(pb, sos, wav, geom, q, ws, check=True)
+    gw1 = d.backward(pb, sos, wav, geom, w, ws, check=True)
+    gq2 = d.backward(pb, sos, wav, geom, q, ws, check=True)
+    gw2 = d.backward(pb, sos, wav, geom, w, ws, check=True)
+    J, g = d.misfit_gradient(pb, sos, wav, geom, obs)
+    torch.cuda.synchronize()
+    assert torch.equal(gq1, gq2) and torch.equal(gw1, gw2)
+    if kw.get("forward_precision") != "compensated":          # the residual then adds the traces' low parts
+        assert torch.equal(gw1, g)
+    assert float(gq1.abs().max()) > 0.0
+
+
 def test_gradient_batched_maps(d):
     wl = inputs.make_workload("linear_disk", seed=7, nx=70, nz=58, nt=500, n_elem=22, n_tx=3, n_maps=2)
     wl.sos_start = (wl.sos_start + np.random.default_rng(1).uniform(-5, 5, wl.sos_start.shape)).astype(np.float32)

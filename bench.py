@@ -58,6 +58,8 @@ def parse():
                     help="1: one cooperative launch per sweep segment, 0: one launch per step")
     ap.add_argument("--multi-tile", type=int, default=None,
                     help="1: multi-tile one-step kernel (co-resident CTAs, two-stage TMA loads), 0: one tile per CTA")
+    ap.add_argument("--shot-groups", type=int, default=None, choices=[1, 2, 3, 4],
+                    help="shot groups stepped on concurrent streams (default: the autotuner's choice)")
     ap.add_argument("--forward-precision", default="fp32", choices=["fp32", "compensated"],
                     help="forward steps in FP32, or compensated (hi + lo planes, error-free arithmetic)")
     ap.add_argument("--boundary", default="damping", choices=["damping", "cpml"],
@@ -164,31 +166,44 @@ def step_kernel_source_sha256() -> str:
     return hashlib.sha256("".join(parts).encode()).hexdigest()
 
 
-def kernel_traffic(kind: str, key: str = "per_launch_dram_bytes_full_size"):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
-    taken on the current one-step kernel source (else None). key selects the cold-cache figure
-    (ncu's default) or the warm-L2 one (per_launch_dram_bytes_warm_l2)."""
+def effective_groups(dufwi, shots: int) -> int:
+    """Shot groups a gradient call uses with the current options (the two-step, persistent and
+    multi-tile forms step every shot in one launch)."""
+    if any(dufwi.get_option(o) for o in (dufwi.OPT_TWO_STEP, dufwi.OPT_PERSISTENT, dufwi.OPT_MULTI_TILE)):
+        return 1
+    return max(1, min(dufwi.get_option(dufwi.OPT_SHOT_GROUPS), shots))
+
+
+def kernel_traffic(kind: str, key: str = "per_launch_dram_bytes_full_size", shots: int = 16):
+    """DRAM bytes per step of all `shots` shots of the dominant kernel from the committed ncu
+    summary (its per-launch figure scaled by shots / shots_per_launch), if it was taken on the
+    current one-step kernel source (else None). key selects the cold-cache figure (ncu's default)
+    or the warm-L2 one (per_launch_dram_bytes_warm_l2)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if rec.get("step_kernel_source_sha256") != step_kernel_source_sha256():
             return None
-        return rec.get(key, {}).get(kind)
+        v = rec.get(key, {}).get(kind)
+        return None if v is None else v * shots / rec.get("shots_per_launch", 16)
     except Exception:
         return None
 
 
-def scale_traffic():
-    """Per-launch DRAM bytes of the step kernel on the 1024 x 1024 workload (profiles/
-    ncu_traffic_scale.json), if taken on the current one-step kernel source (else None)."""
+def scale_traffic(shots: int = 64):
+    """DRAM bytes per step of all `shots` shots of the step kernel on the 1024 x 1024 workload
+    (profiles/ncu_traffic_scale.json, per-launch figures scaled by shots / shots_per_launch), if
+    taken on the current one-step kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic_scale.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if rec.get("step_kernel_source_sha256") != step_kernel_source_sha256():
             return None
-        return rec.get("per_launch_dram_bytes_full_size")
+        per = rec.get("per_launch_dram_bytes_full_size")
+        f = shots / rec.get("shots_per_launch", 64)
+        return None if per is None else {k: v * f for k, v in per.items()}
     except Exception:
         return None
 
@@ -235,9 +250,10 @@ def measure_scale(dufwi, inputs, dev, flush, stream, peak):
     S = wl.n_tx
     kinds = ["forward", "recompute", "adjoint"]
     dom = max(kinds, key=lambda k: prof[k]["ms"])
-    avg_ms = prof[dom]["ms"] / max(prof[dom]["launches"], 1)
+    G = effective_groups(dufwi, S)
+    avg_ms = prof[dom]["ms"] * G / max(prof[dom]["launches"], 1)       # one step of all shots
     bytes_per_launch = ALGO_BYTES[dom] * cells * S
-    traffic = scale_traffic()
+    traffic = scale_traffic(S)
     rec = {"workload": "scale: %dx%d grid (+%d absorbing cells per side), %d steps, %d elements, %d transmits, "
                        "%d receivers, checkpointed adjoint (every 100 steps, FP16 snapshots)"
                        % (wl.nx, wl.nz, wl.pml, wl.nt, wl.elem_ix.size, wl.n_tx, wl.n_rx),
@@ -245,11 +261,11 @@ def measure_scale(dufwi, inputs, dev, flush, stream, peak):
            "hbm_roofline_frac_40B": GRADIENT_BYTES_PER_CELL * cells * wl.nt * S / (peak * 1e9) / (ms / 1e3),
            "workspace_gb": nbytes / 1e9, "status": dufwi.status_string(status),
            "sweep_ms": {k: prof[k]["ms"] for k in kinds + ["other"]},
-           "dominant": {"kernel": "step_kernel (%s sweep)" % dom, "avg_launch_us": 1e3 * avg_ms,
-                        "algorithmic_bytes_per_launch": bytes_per_launch,
+           "dominant": {"kernel": "step_kernel (%s sweep)" % dom, "avg_step_us": 1e3 * avg_ms, "shot_groups": G,
+                        "algorithmic_bytes_per_step": bytes_per_launch,
                         "achieved_gbs": bytes_per_launch / (avg_ms / 1e3) / 1e9,
                         "frac": bytes_per_launch / (avg_ms / 1e3) / 1e9 / peak,
-                        "dram_bytes_per_launch": traffic.get(dom) if traffic else None}}
+                        "dram_bytes_per_step": traffic.get(dom) if traffic else None}}
     del ws
     return rec
 
@@ -318,6 +334,7 @@ def workload_config(wl, args):
             "tile": [64, 32 if getattr(args, "persistent_used", 0) else args.tile_z_used],
             "two_step": args.two_step_used, "persistent": getattr(args, "persistent_used", 0),
             "multi_tile": getattr(args, "multi_tile_used", 0),
+            "shot_groups": getattr(args, "groups_used", 1),
             "forward_precision": getattr(args, "forward_precision", "fp32"),
             "density": ("variable: water-like background + smooth field + 1-3 rods of 1050-1900 kg/m^3, "
                         "staggered operator" if getattr(args, "density", False) else "constant"),
@@ -344,6 +361,8 @@ def run_ours(args):
         dufwi.set_option(dufwi.OPT_PERSISTENT, args.persistent)
     if args.multi_tile is not None:
         dufwi.set_option(dufwi.OPT_MULTI_TILE, args.multi_tile)
+    if args.shot_groups is not None:
+        dufwi.set_option(dufwi.OPT_SHOT_GROUPS, args.shot_groups)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
@@ -372,7 +391,8 @@ def run_ours(args):
 
     # launch options: tuned on a short gradient probe unless forced on the command line
     tuned = None
-    forced = any(v is not None for v in (args.tile_z, args.two_step, args.persistent, args.multi_tile))
+    forced = any(v is not None for v in (args.tile_z, args.two_step, args.persistent, args.multi_tile,
+                                         args.shot_groups))
     if not forced and not args.no_autotune and not (args.density or args.boundary == "cpml") \
             and args.forward_precision == "fp32":
         from paper_2603_04070_gb300 import autotune
@@ -386,6 +406,7 @@ def run_ours(args):
     args.two_step_used = dufwi.get_option(dufwi.OPT_TWO_STEP)
     args.persistent_used = dufwi.get_option(dufwi.OPT_PERSISTENT)
     args.multi_tile_used = dufwi.get_option(dufwi.OPT_MULTI_TILE)
+    args.groups_used = effective_groups(dufwi, wl.n_maps * wl.n_tx)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -427,7 +448,9 @@ def run_ours(args):
     # variables, which are needed only in the layer cells (the rest of the grid holds zeros)
     layer_frac = 1.0 - (wl.nx * wl.nz) / float(cells)
     extra = (VD_EXTRA_BYTES if (args.density or cpml) else 0) + (32 * layer_frac if cpml else 0)
-    launches_per_unit = 2 if cpml else 1      # a CPML step is two launches (interior tiles, layer tiles)
+    # launches per step: one per shot group (two with the CPML: interior tiles, layer tiles); the
+    # unit of the roofline is one step of every shot, i.e. the group launches of one step together
+    launches_per_unit = (2 if cpml else 1) * args.groups_used
     hbm_frac = (GRADIENT_BYTES_PER_CELL + 2 * extra) * cells * wl.nt * S / (peak * 1e9) / (ms_step / 1e3)
 
     # dominant kernel: the sweep kind with the largest share of device time
@@ -443,12 +466,15 @@ def run_ours(args):
              "vd_step_kernel" if args.density else "step_kernel")
     roofline = {"bound": "hbm", "kernel": "%s (%s sweep)" % (kname, dom), "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if (args.density or cpml) else kernel_traffic(dom),
-                "traffic_warm_l2": None if (args.density or cpml) else kernel_traffic(dom, "per_launch_dram_bytes_warm_l2"),
-                "algorithmic_bytes_per_launch": bytes_per_launch,
-                "unique_bytes_per_launch": unique_per_launch,
+                "traffic": None if (args.density or cpml) else kernel_traffic(dom, shots=S),
+                "traffic_warm_l2": None if (args.density or cpml) else kernel_traffic(
+                    dom, "per_launch_dram_bytes_warm_l2", shots=S),
+                "algorithmic_bytes_per_step": bytes_per_launch,
+                "unique_bytes_per_step": unique_per_launch,
                 "frac_unique_bytes": unique_per_launch / (avg_launch_ms / 1e3) / 1e9 / peak,
-                "avg_launch_us": 1e3 * avg_launch_ms,
+                "avg_step_us": 1e3 * avg_launch_ms, "shot_groups": args.groups_used,
+                "unit_of_work": "one time step of all %d shots (%d concurrent launch%s)"
+                                % (S, launches_per_unit, "" if launches_per_unit == 1 else "es"),
                 "sweep_ms_per_step": {k: prof[k]["ms"] / args.steps for k in kinds + ["other"]},
                 "launches_per_step": {k: prof[k]["launches"] / args.steps for k in kinds + ["other"]}}
 

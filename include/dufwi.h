@@ -427,6 +427,18 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     of the two previous launches wrote (U^{n-1}, kappa', the adjoint's history tile) before it
  *     waits for the previous launch (programmatic dependent launch); 0 requests everything after
  *     the wait. Same results either way.
+ *   DUFWI_OPT_SHOT_GROUPS: 1 to 4 (default 2). A call's shots (maps x transmits) are split into
+ *     this many groups of consecutive shots (at most one group per shot), and each range of time
+ *     steps launches one kernel per group and step, each group on a stream of its own that forks
+ *     from the caller's stream before the range and joins it after. Shots never exchange data, so
+ *     the groups run independently: a group's next step starts while the other group's step
+ *     drains, which fills the SMs that one launch per step leaves idle at its start and end. The
+ *     results are bit-identical for every value. The group streams and their events are created
+ *     on a host thread's first grouped call on a device and kept until the thread exits; while the
+ *     caller's stream is being captured into a CUDA graph they are not created, so a call captured
+ *     before any uncaptured call on that thread and device runs as one group (make one uncaptured
+ *     call first to capture the grouped form). Not used with the two-step, persistent or
+ *     multi-tile forms, the second-order calls, or dufwi_simulate_noalloc.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device
@@ -439,6 +451,7 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
 #define DUFWI_OPT_TEST_STALL 5
 #define DUFWI_OPT_MULTI_TILE 6
 #define DUFWI_OPT_EARLY_LOADS 7
+#define DUFWI_OPT_SHOT_GROUPS 8
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

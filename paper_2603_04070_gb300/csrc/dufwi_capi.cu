@@ -126,6 +126,58 @@ int g_two_step = 0;
 int g_persistent = 0;   // DUFWI_OPT_PERSISTENT: one cooperative launch per sweep segment
 int g_multi_tile = 0;   // DUFWI_OPT_MULTI_TILE: the multi-tile one-step kernel (64 x 32 tiles)
 int g_early = 1;        // DUFWI_OPT_EARLY_LOADS: operands not written by the last two launches requested early
+int g_shot_groups = 2;  // DUFWI_OPT_SHOT_GROUPS: shot groups stepped on concurrent streams
+
+// Streams and events of the shot groups, per host thread and device: created on first use and
+// kept for the thread's lifetime. Calls on different host threads never share an event, so their
+// fork/join orderings cannot mix.
+constexpr int kMaxGroups = 4;
+constexpr int kMaxAuxDevices = 64;
+struct GroupAux {
+    bool ready = false;
+    cudaStream_t st[kMaxGroups] = {};
+    cudaEvent_t fork = nullptr, join[kMaxGroups] = {};
+    ~GroupAux()
+    {
+        if (!ready) return;
+        for (int g = 0; g < kMaxGroups; ++g) {
+            cudaStreamDestroy(st[g]);
+            cudaEventDestroy(join[g]);
+        }
+        cudaEventDestroy(fork);
+    }
+};
+thread_local GroupAux t_group_aux[kMaxAuxDevices];
+
+// The group streams of the current device, or null (the call then steps all its shots as one
+// group). They are not created while the caller's stream is being captured into a graph: a call
+// captured before any uncaptured call on this thread and device runs as one group.
+GroupAux *group_aux(cudaStream_t caller)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxAuxDevices) return nullptr;
+    GroupAux &a = t_group_aux[dev];
+    if (a.ready) return &a;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(caller, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    bool ok = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; ok && g < kMaxGroups; ++g)
+        ok = cudaStreamCreateWithFlags(&a.st[g], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&a.join[g], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (int g = 0; g < kMaxGroups; ++g) {
+            if (a.st[g]) cudaStreamDestroy(a.st[g]);
+            if (a.join[g]) cudaEventDestroy(a.join[g]);
+            a.st[g] = nullptr;
+            a.join[g] = nullptr;
+        }
+        if (a.fork) cudaEventDestroy(a.fork);
+        a.fork = nullptr;
+        return nullptr;
+    }
+    a.ready = true;
+    return &a;
+}
 std::atomic<int> g_test_stall{0};   // DUFWI_OPT_TEST_STALL: the next persistent sweep stalls on purpose
 
 // NVTX range over the host code that enqueues one part of a call (visible in timeline tools).
@@ -434,6 +486,13 @@ struct Ctx {
     bool comp = false;                        // compensated forward steps (hi + lo planes)
     bool multi_tile = false;                  // multi-tile one-step kernel (two-stage TMA pipeline)
     float *cd_lo = nullptr;                   // compensated: low parts of the traces of the current sweep
+    // shot groups: the step launches of a range go to one stream per group, each covering shots
+    // g_s0[g] .. g_s0[g] + g_n[g] - 1, between a fork from and a join into the caller's stream
+    bool allow_groups = true;                 // false: every launch on the caller's stream
+    int groups = 1;
+    int g_s0[kMaxGroups] = {}, g_n[kMaxGroups] = {};
+    GroupAux *aux = nullptr;
+    bool forked = false;
     CompParams cq;                            // compensated: constant arguments of the step
     FieldMaps lomap[2];                       // compensated: maps of the low planes of the forward ring
     CUtensorMap kqh1, kql1;                   // compensated: kappa' / s_R (or / S^2 with density), hi and lo
@@ -529,6 +588,18 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.mem_par = 0;
     c.multi_tile = g_multi_tile != 0 && !c.two_step && !c.persistent && !c.vd && !c.so && !c.comp;
     c.tz = (c.vd || c.persistent || c.so || c.comp || c.multi_tile) ? 32 : g_tile_z;
+    // shot groups for the one-launch-per-step forms (the persistent, two-step and multi-tile forms
+    // walk all shots in one launch; the second-order calls step several rings per time step)
+    c.groups = 1;
+    const int want = std::min(g_shot_groups, L.S);
+    if (want > 1 && c.allow_groups && !c.two_step && !c.persistent && !c.multi_tile && !c.so) {
+        c.aux = group_aux(c.st);
+        if (c.aux) c.groups = want;
+    }
+    for (int g = 0; g < c.groups; ++g) {
+        c.g_s0[g] = (int)((long long)L.S * g / c.groups);
+        c.g_n[g] = (int)((long long)L.S * (g + 1) / c.groups) - c.g_s0[g];
+    }
     const int nrx1 = L.n_rx > 0 ? L.n_rx : 1;
     std::vector<int2> tab1, tab2, tabe;
     std::vector<int> sorted1, sorted2, sortede;
@@ -752,6 +823,30 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     p.rxe_tab = c.at<int2>(L.o_tabe);
     p.rxe_sorted = c.at<int>(L.o_sortede);
     p.n_rxe = L.n_rxe;
+    p.shot0 = 0;
+    p.n_shots = L.S;
+    return DUFWI_OK;
+}
+
+// Fork: the group streams wait for everything enqueued so far on the caller's stream. Join: the
+// caller's stream waits for every group. Ranges of step launches run between the two.
+int fork_groups(Ctx &c)
+{
+    if (c.groups < 2) return DUFWI_OK;
+    CK(cudaEventRecord(c.aux->fork, c.st));
+    for (int g = 0; g < c.groups; ++g) CK(cudaStreamWaitEvent(c.aux->st[g], c.aux->fork, 0));
+    c.forked = true;
+    return DUFWI_OK;
+}
+
+int join_groups(Ctx &c)
+{
+    if (!c.forked) return DUFWI_OK;
+    c.forked = false;
+    for (int g = 0; g < c.groups; ++g) {
+        CK(cudaEventRecord(c.aux->join[g], c.aux->st[g]));
+        CK(cudaStreamWaitEvent(c.st, c.aux->join[g], 0));
+    }
     return DUFWI_OK;
 }
 
@@ -773,9 +868,18 @@ struct Ring {
     }
 };
 
-// One step n -> n+1 (forward modes) or m+1 -> m (adjoint), in place.
+// One step n -> n+1 (forward modes) or m+1 -> m (adjoint), in place, for every shot: inside a
+// forked range one launch per shot group on the group's stream, else one launch on the caller's
+// stream. The ring (and the CPML memory-variable set) rotates once.
 int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
 {
+    const int G = c.forked ? c.groups : 1;
+    auto group = [&](int g, StepParams &q) -> cudaStream_t {
+        if (G == 1) return c.st;
+        q.shot0 = c.g_s0[g];
+        q.n_shots = c.g_n[g];
+        return c.aux->st[g];
+    };
     StepMaps tm;
     memset(&tm, 0, sizeof(tm));
     tm.cur_box = rg.map[rg.cur].box1;
@@ -802,7 +906,11 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
         CompParams q = c.cq;
         q.out_lo = rg.lo[rg.prv];
         q.cd_lo = c.cd_lo;
-        CKL(launch_comp_vd_step(c.L.radius, mode, cm, p, q, c.st));
+        for (int g = 0; g < G; ++g) {
+            StepParams pg = p;
+            const cudaStream_t st = group(g, pg);
+            CKL(launch_comp_vd_step(c.L.radius, mode, cm, pg, q, st));
+        }
         std::swap(rg.cur, rg.prv);
         return DUFWI_OK;
     }
@@ -818,7 +926,11 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
         CompParams q = c.cq;
         q.out_lo = rg.lo[rg.prv];
         q.cd_lo = c.cd_lo;
-        CKL(launch_comp_step(c.L.radius, mode, cm, p, q, c.st));
+        for (int g = 0; g < G; ++g) {
+            StepParams pg = p;
+            const cudaStream_t st = group(g, pg);
+            CKL(launch_comp_step(c.L.radius, mode, cm, pg, q, st));
+        }
         std::swap(rg.cur, rg.prv);
         return DUFWI_OK;
     }
@@ -840,21 +952,33 @@ int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
         const CpmlMaps &cm = adj ? c.cm_adj[par] : c.cm_fwd[par];
         // tiles away from the layer take the staggered kernel (their memory variables stay zero),
         // the others the CPML kernel; both read step n and write disjoint tiles of step n + 1
-        StepParams pi = p, pl = p;
-        pi.tile_class = 1;
-        pl.tile_class = 2;
-        CKL(launch_step_vd(c.L.radius, mode, tm, pi, c.st));
-        CKL(launch_step_cpml(c.L.radius, mode, tm, cm, pl, cp, c.st));
+        for (int g = 0; g < G; ++g) {
+            StepParams pi = p;
+            const cudaStream_t st = group(g, pi);
+            StepParams pl = pi;
+            pi.tile_class = 1;
+            pl.tile_class = 2;
+            CKL(launch_step_vd(c.L.radius, mode, tm, pi, st));
+            CKL(launch_step_cpml(c.L.radius, mode, tm, cm, pl, cp, st));
+        }
         par = w;
     } else if (c.vd) {   // the tile height is 32 here, so tile1, kap1, hist1 and grad1 fit the kernel
         tm.cur_box = rg.map[rg.cur].box2;
         tm.bx_tile = c.bx1;
         tm.bz_tile = c.bz1;
-        CKL(launch_step_vd(c.L.radius, mode, tm, p, c.st));
-    } else if (c.multi_tile) {
+        for (int g = 0; g < G; ++g) {
+            StepParams pg = p;
+            const cudaStream_t st = group(g, pg);
+            CKL(launch_step_vd(c.L.radius, mode, tm, pg, st));
+        }
+    } else if (c.multi_tile) {   // never forked: walks every shot in one launch
         CKL(launch_step_mt(c.L.radius, mode, tm, p, c.st));
     } else {
-        CKL(launch_step(c.L.radius, mode, tm, p, c.st));
+        for (int g = 0; g < G; ++g) {
+            StepParams pg = p;
+            const cudaStream_t st = group(g, pg);
+            CKL(launch_step(c.L.radius, mode, tm, pg, st));
+        }
     }
     std::swap(rg.cur, rg.prv);
     return DUFWI_OK;
@@ -933,22 +1057,24 @@ int forward_range(Ctx &c, Ring &rg, int n0, int n1, int mode, const float *wavel
     p.cd = cd;
     if (c.persistent)
         return sweep(c, rg, mode, p, n0, n1 - n0, hist ? hist + (size_t)(n0 - h0) * hstride : nullptr, 0, nl);
+    int rc = fork_groups(c);
+    if (rc) return rc;
     for (int n = n0; n < n1;) {
         p.step = n;
         p.hist = hist ? hist + (size_t)(n - h0) * hstride : nullptr;
         p.early = (g_early && !c.two_step && n >= n0 + 2) ? 1 : 0;   // the two launches before: steps n-2, n-1
         if (c.two_step && n % 2 == 0 && n + 2 <= n1) {
             p.hist2 = hist ? hist + (size_t)(n + 1 - h0) * hstride : nullptr;
-            int rc = two_steps(c, rg, mode, p, nl);
-            if (rc) return rc;
+            rc = two_steps(c, rg, mode, p, nl);
             n += 2;
         } else {
-            int rc = one_step(c, rg, mode, p, nl);
-            if (rc) return rc;
+            rc = one_step(c, rg, mode, p, nl);
             n += 1;
         }
+        if (rc) break;
     }
-    return DUFWI_OK;
+    const int rj = join_groups(c);
+    return rc ? rc : rj;
 }
 
 // Adjoint steps m = m1 .. m0 (descending), imaging with Lap(U^{m-1}) at history slot m-1-h0.
@@ -959,22 +1085,24 @@ int adjoint_range(Ctx &c, Ring &rg, int m1, int m0, const float *asrc, float *g_
     p.inj_val = asrc;
     p.grad = g_shot;
     if (c.persistent) return sweep(c, rg, kAdjoint, p, m1, m1 - m0 + 1, nullptr, m1 - 1 - h0, nl);
+    int rc = fork_groups(c);
+    if (rc) return rc;
     for (int m = m1; m >= m0;) {
         p.step = m;
         p.hist_slot = m - 1 - h0;
         p.early = (g_early && !c.two_step && m <= m1 - 2) ? 1 : 0;   // the two launches before: m+2, m+1
         if (c.two_step && m % 2 == 0 && m - 1 >= m0) {
             p.hist_slot2 = m - 2 - h0;
-            int rc = two_steps(c, rg, kAdjoint, p, nl);
-            if (rc) return rc;
+            rc = two_steps(c, rg, kAdjoint, p, nl);
             m -= 2;
         } else {
-            int rc = one_step(c, rg, kAdjoint, p, nl);
-            if (rc) return rc;
+            rc = one_step(c, rg, kAdjoint, p, nl);
             m -= 1;
         }
+        if (rc) break;
     }
-    return DUFWI_OK;
+    const int rj = join_groups(c);
+    return rc ? rc : rj;
 }
 
 // Forward sweep from rest over steps [0, nt-1): traces, and either the whole history or the
@@ -1085,6 +1213,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_early = value;
         return DUFWI_OK;
+    case DUFWI_OPT_SHOT_GROUPS:
+        if (value < 1 || value > kMaxGroups) return DUFWI_ERR_INVALID_ARG;
+        g_shot_groups = value;
+        return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL:
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_test_stall = value;
@@ -1101,6 +1233,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     case DUFWI_OPT_PERSISTENT: *value = g_persistent; return DUFWI_OK;
     case DUFWI_OPT_MULTI_TILE: *value = g_multi_tile; return DUFWI_OK;
     case DUFWI_OPT_EARLY_LOADS: *value = g_early; return DUFWI_OK;
+    case DUFWI_OPT_SHOT_GROUPS: *value = g_shot_groups; return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL: *value = g_test_stall.load(); return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;
@@ -1213,9 +1346,22 @@ int dufwi_simulate_sized(const dufwi_problem *pb, const dufwi_map_sizes *sizes, 
                          const dufwi_shots *shots, int32_t n_maps, float *cd, void *workspace,
                          size_t workspace_bytes, void *stream)
 {
+    return dufwi::simulate_impl(pb, sizes, sos, density, arr, wavelet, shots, n_maps, cd, workspace, workspace_bytes,
+                                stream, true);
+}
+
+}  // extern "C"
+
+namespace dufwi {
+
+int simulate_impl(const dufwi_problem *pb, const dufwi_map_sizes *sizes, const float *sos, const float *density,
+                  const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots, int n_maps, float *cd,
+                  void *workspace, size_t workspace_bytes, void *stream, bool allow_groups)
+{
     Ctx c;
     c.pb = pb;
     c.sizes = sizes;
+    c.allow_groups = allow_groups;
     int rc = make_layout(pb, shots, n_maps, kLayoutSimulate, &c.L);
     if (rc) return rc;
     if (!cd && c.L.n_rx > 0) return DUFWI_ERR_INVALID_ARG;
@@ -1231,7 +1377,7 @@ int dufwi_simulate_sized(const dufwi_problem *pb, const dufwi_map_sizes *sizes, 
     return forward_sweep(c, rg, wavelet, cd, false, false);
 }
 
-}  // extern "C"
+}  // namespace dufwi
 
 namespace dufwi {
 namespace {

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(128, 3) comp_step_kernel(const __grid_constant
     __shared__ alignas(8) uint64_t bar;
 
     const int tid = threadIdx.x;
-    const int s = blockIdx.z;
+    const int s = p.shot0 + blockIdx.z;
     const int x0 = blockIdx.x * kTileX;
     const int z0 = blockIdx.y * kCompTileZ;
     const int tx_idx = s % p.n_tx;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(128, 2) comp_vd_step_kernel(const __grid_const
     __shared__ alignas(8) uint64_t bar;
 
     const int tid = threadIdx.x;
-    const int s = blockIdx.z;
+    const int s = p.shot0 + blockIdx.z;
     const int x0 = blockIdx.x * kTileX;
     const int z0 = blockIdx.y * kVTileZ;
     const int tx_idx = s % p.n_tx;
@@ -592,7 +592,7 @@ cudaError_t launch_comp_vd_rm(const CompVdMaps &tm, const StepParams &p, const C
     cudaError_t e = configure_kernel(comp_vd_step_kernel<R, MODE>, kCvBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_maps * p.n_tx);
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_shots);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = kCvBytes;
     cfg.stream = st;
@@ -652,7 +652,7 @@ cudaError_t launch_comp_rm(const CompMaps &tm, const StepParams &p, const CompPa
     cudaError_t e = configure_kernel(comp_step_kernel<R, MODE>, kCompBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kCompTileZ - 1) / kCompTileZ, p.n_maps * p.n_tx);
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kCompTileZ - 1) / kCompTileZ, p.n_shots);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = kCompBytes;
     cfg.stream = st;

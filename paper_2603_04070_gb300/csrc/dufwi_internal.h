@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/dufwi.h"
+
 #include <atomic>
 
 namespace dufwi {
@@ -170,6 +172,7 @@ struct StepParams {
                              // wrote them (set by the host from the third step of a range on)
     int tile_class;          // CPML split: 0 every tile; 1 only tiles whose region grown by 8 cells
                              // lies inside the physical grid (no memory variables); 2 only the others
+    int shot0, n_shots;      // this launch covers shots shot0 .. shot0 + n_shots - 1 (grid.z = n_shots)
 };
 
 // Compensated forward step (comp_step_kernel, 64 x 32 tiles): the field as hi + lo planes of FP32.
@@ -324,5 +327,11 @@ cudaError_t launch_snap_store(const float *cur, const float *prev, void *snap_u,
 cudaError_t launch_snap_load(float *cur, float *prev, const void *snap_u, const void *snap_d,
                              const unsigned *scale_bits, int dtype, int S, long long slice,
                              int nxp, int nzp, int pitch, cudaStream_t st);
+
+// Body of dufwi_simulate_sized. allow_groups false keeps every launch on the caller's stream
+// (no group streams or events are created: the workspace-free entry point allocates nothing).
+int simulate_impl(const dufwi_problem *pb, const dufwi_map_sizes *sizes, const float *sos, const float *density,
+                  const dufwi_array *arr, const float *wavelet, const dufwi_shots *shots, int n_maps, float *cd,
+                  void *workspace, size_t workspace_bytes, void *stream, bool allow_groups);
 
 }  // namespace dufwi

@@ -230,7 +230,7 @@ step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     __shared__ InjList inj;
 
     const int tid = threadIdx.x;
-    const int s = blockIdx.z;
+    const int s = p.shot0 + blockIdx.z;
     const int x0 = blockIdx.x * kTileX;
     const int z0 = blockIdx.y * TZ;
     const int tx_idx = s % p.n_tx;
@@ -684,7 +684,7 @@ so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoPa
     __shared__ InjList inj;
 
     const int tid = threadIdx.x;
-    const int s = blockIdx.z;
+    const int s = p.shot0 + blockIdx.z;
     const int map = s / p.n_tx;
     const int x0 = blockIdx.x * kTileX;
     const int z0 = blockIdx.y * TZ;
@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     __shared__ InjList inj;
 
     const int tid = threadIdx.x;
-    const int s = blockIdx.z;
+    const int s = p.shot0 + blockIdx.z;
     const int x0 = blockIdx.x * kTileX;
     const int z0 = blockIdx.y * TZ;
     const int tx_idx = s % p.n_tx;
@@ -1071,7 +1071,7 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
     __shared__ InjList inj;
 
     const int tid = threadIdx.x;
-    const int s = blockIdx.z;
+    const int s = p.shot0 + blockIdx.z;
     const int x0 = blockIdx.x * kTileX;
     const int z0 = blockIdx.y * TZ;
     const int tx_idx = s % p.n_tx;
@@ -1695,7 +1695,7 @@ step2_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
     __shared__ InjList inj[2];
 
     const int tid = threadIdx.x;
-    const int s = blockIdx.z;
+    const int s = p.shot0 + blockIdx.z;
     const int x0 = blockIdx.x * kTileX;
     const int z0 = blockIdx.y * kPairZ;
     const int tx_idx = s % p.n_tx;
@@ -2150,7 +2150,7 @@ static cudaError_t launch_step_rmt(const StepMaps &tm, const StepParams &p, cuda
     cudaError_t e = configure_kernel(step_kernel<R, MODE, TZ>, TL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + TZ - 1) / TZ, p.n_maps * p.n_tx);
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + TZ - 1) / TZ, p.n_shots);
     cfg.blockDim = dim3(TL::kThreadsPerCta);
     cfg.dynamicSmemBytes = TL::kBytes;
     cfg.stream = st;
@@ -2233,7 +2233,7 @@ static cudaError_t launch_step2_rm(const StepMaps &tm, const StepParams &p, cuda
     cudaError_t e = configure_kernel(step2_kernel<R, MODE>, PL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kPairZ - 1) / kPairZ, p.n_maps * p.n_tx);
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kPairZ - 1) / kPairZ, p.n_shots);
     cfg.blockDim = dim3(kPairThreads);
     cfg.dynamicSmemBytes = PL::kBytes;
     cfg.stream = st;
@@ -2333,7 +2333,7 @@ static cudaError_t launch_step_cpml_rm(const StepMaps &tm, const CpmlMaps &cm, c
     cudaError_t e = configure_kernel(cpml_step_kernel<R, MODE>, CL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_maps * p.n_tx);
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_shots);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = CL::kBytes;
     cfg.stream = st;
@@ -2379,7 +2379,7 @@ static cudaError_t launch_step_vd_rm(const StepMaps &tm, const StepParams &p, cu
     cudaError_t e = configure_kernel(vd_step_kernel<R, MODE>, VL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_maps * p.n_tx);
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_shots);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = VL::kBytes;
     cfg.stream = st;
@@ -2424,7 +2424,7 @@ static cudaError_t launch_so_step_rk(const SoMaps &tm, const StepParams &p, cons
     cudaError_t e = configure_kernel(so_step_kernel<R, KIND, VD>, SL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + 31) / 32, p.n_maps * p.n_tx);
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + 31) / 32, p.n_shots);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = SL::kBytes;
     cfg.stream = st;

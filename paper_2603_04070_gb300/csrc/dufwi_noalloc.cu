@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dufwi.h"
+#include "dufwi_internal.h"
 
 namespace {
 
@@ -58,8 +59,9 @@ extern "C" int dufwi_simulate_noalloc(const dufwi_problem *pb, const float *sos,
     void *scratch = nullptr;
     rc = scratch_address(&scratch);
     if (rc) return rc;
-    return dufwi_simulate(pb, sos, density, arr, wavelet, shots, n_maps, cd, scratch,
-                          (size_t)DUFWI_NOALLOC_SCRATCH_BYTES, stream);
+    // one stream: the shot groups' streams and events would be created on first use
+    return dufwi::simulate_impl(pb, nullptr, sos, density, arr, wavelet, shots, n_maps, cd, scratch,
+                                (size_t)DUFWI_NOALLOC_SCRATCH_BYTES, stream, false);
 }
 
 // The status word is the first int of the scratch array (the layout puts it at offset 0 of every

@@ -34,6 +34,7 @@ OPT_PERSISTENT = 4
 OPT_TEST_STALL = 5
 OPT_MULTI_TILE = 6
 OPT_EARLY_LOADS = 7
+OPT_SHOT_GROUPS = 8
 
 
 class DufwiError(RuntimeError):

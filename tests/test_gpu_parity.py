@@ -697,6 +697,98 @@ def test_gradient_call_captures_in_a_cuda_graph(d):
         del ws
 
 
+@pytest.mark.parametrize("kw", [dict(ckpt_interval=37), dict(ckpt_interval=37, kept_segments=3),
+                                dict(ckpt_interval=37, snapshot_dtype="fp16"), dict(forward_precision="compensated"),
+                                dict(boundary="cpml", pml_alpha=6e6, ckpt_interval=37), dict(density=True),
+                                dict(tile_z=64)])
+def test_shot_groups_are_bit_identical(d, kw):
+    """Shot groups stepped on concurrent streams (DUFWI_OPT_SHOT_GROUPS 1..4, with 2 maps x 3
+    transmits: groups of 3, 2 and 1-2 shots) give the traces, misfit and gradient of one group bit
+    for bit, with checkpoints, the hybrid history, FP16 snapshots, the compensated steps, the
+    CPML, a density map and 64-row tiles."""
+    kw = dict(kw)
+    density = kw.pop("density", False)
+    tile_z = kw.pop("tile_z", 32)
+    wl = inputs.make_workload("linear_disk", seed=12, nx=70, nz=66, nt=260, n_elem=16, n_tx=3, n_maps=2)
+    M_obs = _observed(wl)
+    pb = _dufwi_problem(d, wl, **kw)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    sos[1] += 7.0
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    obs = torch.from_numpy(M_obs).cuda()
+    rho = None
+    if density:
+        rho = torch.from_numpy(np.stack([inputs.density_map(inputs.rng_for(40 + b), wl.nx, wl.nz, wl.dx)
+                                         for b in range(2)]).astype(np.float32)).cuda()
+    g_before, t_before = d.get_option(d.OPT_SHOT_GROUPS), d.get_option(d.OPT_TILE_Z)
+    out = []
+    try:
+        d.set_option(d.OPT_TILE_Z, tile_z)
+        for groups in (1, 2, 3, 4):
+            d.set_option(d.OPT_SHOT_GROUPS, groups)
+            cd = d.simulate(pb, sos, wav, geom, density=rho, check=True)
+            J, g, cd2 = d.misfit_gradient(pb, sos, wav, geom, obs, density=rho, return_cd=True, check=True)
+            torch.cuda.synchronize()
+            out.append((cd, J, g, cd2))
+    finally:
+        d.set_option(d.OPT_SHOT_GROUPS, g_before)
+        d.set_option(d.OPT_TILE_Z, t_before)
+    for o in out[1:]:
+        for a, b in zip(out[0], o):
+            assert torch.equal(a, b)
+    assert float(out[0][2].abs().max()) > 0.0
+
+
+def test_capture_before_any_grouped_call_runs_one_group(d):
+    """On a host thread that has made no uncaptured call yet, the group streams are not created
+    during stream capture: the captured call runs its shots as one group and replays the result
+    of an ordinary (grouped) call bit for bit."""
+    import threading
+    wl = inputs.make_workload("linear_disk", seed=24, nx=60, nz=52, nt=150, n_elem=14, n_tx=4)
+    pb = _dufwi_problem(d, wl, ckpt_interval=30)
+    geom = d.Geometry.from_workload(wl)
+    w = torch.from_numpy(wl.wavelet).cuda()
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    obs = torch.from_numpy(_observed(wl)).cuda()
+    J0, g0 = d.misfit_gradient(pb, sos, w, geom, obs)
+    torch.cuda.synchronize()
+    ws = torch.empty(d.workspace_size(pb, geom, 1), dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(sos)
+    box = {}
+
+    def worker():
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=s):
+                    d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)
+            box["graph"] = graph
+        except Exception as e:          # reported on the main thread
+            box["error"] = e
+
+    try:
+        d.set_option(d.OPT_REUSE_TABLES, 0)
+        # the tables are copied from pageable host memory inside the capture: allowed for a graph
+        # only when they are already in place, so upload them first with an ordinary call
+        d.misfit_gradient(pb, sos, w, geom, obs, misfit=J, grad=g, workspace=ws)
+        torch.cuda.synchronize()
+        d.set_option(d.OPT_REUSE_TABLES, 1)
+        t = threading.Thread(target=worker)
+        t.start()
+        t.join()
+        assert "error" not in box, box.get("error")
+        J.zero_(); g.zero_()
+        box["graph"].replay()
+        torch.cuda.synchronize()
+        assert torch.equal(J, J0) and torch.equal(g, g0)
+    finally:
+        d.set_option(d.OPT_REUSE_TABLES, 0)
+        del ws
+
+
 def _born_case(seed, nt=320):
     wl = inputs.make_workload("linear_disk", seed=seed, nx=58, nz=52, nt=nt, n_elem=14, n_tx=2)
     rng = np.random.default_rng(seed)

@@ -438,7 +438,7 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     caller's stream is being captured into a CUDA graph they are not created, so a call captured
  *     before any uncaptured call on that thread and device runs as one group (make one uncaptured
  *     call first to capture the grouped form). Not used with the two-step, persistent or
- *     multi-tile forms, the second-order calls, or dufwi_simulate_noalloc.
+ *     multi-tile forms, or by dufwi_simulate_noalloc.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device

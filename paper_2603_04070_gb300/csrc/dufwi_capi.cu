@@ -589,10 +589,10 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.multi_tile = g_multi_tile != 0 && !c.two_step && !c.persistent && !c.vd && !c.so && !c.comp;
     c.tz = (c.vd || c.persistent || c.so || c.comp || c.multi_tile) ? 32 : g_tile_z;
     // shot groups for the one-launch-per-step forms (the persistent, two-step and multi-tile forms
-    // walk all shots in one launch; the second-order calls step several rings per time step)
+    // walk all shots in one launch)
     c.groups = 1;
     const int want = std::min(g_shot_groups, L.S);
-    if (want > 1 && c.allow_groups && !c.two_step && !c.persistent && !c.multi_tile && !c.so) {
+    if (want > 1 && c.allow_groups && !c.two_step && !c.persistent && !c.multi_tile) {
         c.aux = group_aux(c.st);
         if (c.aux) c.groups = want;
     }
@@ -839,6 +839,16 @@ int fork_groups(Ctx &c)
     return DUFWI_OK;
 }
 
+// Stream of shot group g of G launches, with q narrowed to the group's shots (G = 1: the caller's
+// stream and every shot).
+cudaStream_t group_stream(Ctx &c, int G, int g, StepParams &q)
+{
+    if (G == 1) return c.st;
+    q.shot0 = c.g_s0[g];
+    q.n_shots = c.g_n[g];
+    return c.aux->st[g];
+}
+
 int join_groups(Ctx &c)
 {
     if (!c.forked) return DUFWI_OK;
@@ -874,12 +884,7 @@ struct Ring {
 int one_step(Ctx &c, Ring &rg, int mode, StepParams p, long long &nl)
 {
     const int G = c.forked ? c.groups : 1;
-    auto group = [&](int g, StepParams &q) -> cudaStream_t {
-        if (G == 1) return c.st;
-        q.shot0 = c.g_s0[g];
-        q.n_shots = c.g_n[g];
-        return c.aux->st[g];
-    };
+    auto group = [&](int g, StepParams &q) { return group_stream(c, G, g, q); };
     StepMaps tm;
     memset(&tm, 0, sizeof(tm));
     tm.cur_box = rg.map[rg.cur].box1;
@@ -1697,15 +1702,18 @@ int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, c
     pb_.inj_node = c.at<int>(L.o_tx);
     pb_.cd = dcd;
     pb_.hist_slot = 0;
-    for (int n = 0; n < L.nt - 1; ++n) {
+    rc = fork_groups(c);
+    if (rc) return rc;
+    for (int n = 0; n < L.nt - 1 && !rc; ++n) {
         // background step n (records U^n, keeps Lap(U^n)), then the Born step n using it
         pf.step = n;
         rc = one_step(c, fr, kFwdSampleHist, pf, nl);
-        if (rc) return rc;
+        if (rc) break;
         pb_.step = n;
         rc = one_step(c, br, kBorn, pb_, nl);
-        if (rc) return rc;
     }
+    const int rj = join_groups(c);
+    if (rc || rj) return rc ? rc : rj;
     if (L.n_rx > 0) {
         CKL(launch_sample(fr.buf[fr.cur], c.at<int>(L.o_rx), bg_cd, L.slice, L.pitch, L.S, L.n_tx, L.n_rx, L.nt,
                           L.nt - 1, c.st));
@@ -1745,7 +1753,12 @@ int so_step(Ctx &c, Ring &r, int kind, StepParams p, const SoParams &q, long lon
     p.out = r.buf[r.prv];
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
-    CKL(launch_so_step(c.L.radius, kind, c.vd, tm, p, q, c.st));
+    const int G = c.forked ? c.groups : 1;
+    for (int g = 0; g < G; ++g) {
+        StepParams pg = p;
+        const cudaStream_t st = group_stream(c, G, g, pg);
+        CKL(launch_so_step(c.L.radius, kind, c.vd, tm, pg, q, st));
+    }
     std::swap(r.cur, r.prv);
     return DUFWI_OK;
 }
@@ -1769,20 +1782,22 @@ int so_forward_range(Ctx &c, Ring &fr, Ring &br, int n0, int n1, int h0, const f
     StepParams pb = c.base;
     pb.smp_node = c.at<int>(L.o_rx);
     pb.cd = dcd;
-    for (int n = n0; n < n1; ++n) {
+    int rc = fork_groups(c);
+    if (rc) return rc;
+    for (int n = n0; n < n1 && !rc; ++n) {
         pf.step = n;
         pf.hist = h1 + (size_t)(n - h0) * hstride;
-        int rc = one_step(c, fr, fmode, pf, nl);
-        if (rc) return rc;
+        rc = one_step(c, fr, fmode, pf, nl);
+        if (rc) break;
         pb.step = n;
         SoParams q;
         memset(&q, 0, sizeof(q));
         q.lap_out = h2 + (size_t)(n - h0) * hstride;
         q.h1_slot = n - h0;
         rc = so_step(c, br, kSoBorn, pb, q, nl);
-        if (rc) return rc;
     }
-    return DUFWI_OK;
+    const int rj = join_groups(c);
+    return rc ? rc : rj;
 }
 
 Ring ring_of(Ctx &c, const size_t *offsets, const FieldMaps *maps)
@@ -1908,7 +1923,9 @@ int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float
         pa.inj_val = asrc;
         StepParams pd = pa;
         pd.inj_val = asrc2;
-        for (int m = t1; m >= t0 + 1; --m) {
+        rc = fork_groups(c);
+        if (rc) return rc;
+        for (int m = t1; m >= t0 + 1 && !rc; --m) {
             pa.step = pd.step = m;
             SoParams qa, qd;
             memset(&qa, 0, sizeof(qa));
@@ -1918,12 +1935,13 @@ int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float
             qa.sum2 = accB;
             qa.h1_slot = qa.h2_slot = m - 1 - t0;
             rc = so_step(c, ar, kSoAdj, pa, qa, nl);
-            if (rc) return rc;
+            if (rc) break;
             qd.sum1 = accA;
             qd.h1_slot = m - 1 - t0;
             rc = so_step(c, dr, kSoBornAdj, pd, qd, nl);
-            if (rc) return rc;
         }
+        const int rj = join_groups(c);
+        if (rc || rj) return rc ? rc : rj;
         g_prof.span(2, e0, g_prof.mark(c.st), nl);
     }
 

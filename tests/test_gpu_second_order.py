@@ -424,3 +424,33 @@ def test_exact_hvp_with_density_matches_oracle_and_is_symmetric(d):
     a = float((u.double() * hv.double()).sum())
     b = float((_cuda(v).double() * hu.double()).sum())
     assert abs(a - b) <= 1e-4 * max(abs(a), abs(b))
+
+
+@pytest.mark.parametrize("with_density", [False, True])
+def test_second_order_calls_are_bit_identical_across_shot_groups(d, with_density):
+    """The Born JVP, the second-order call and dufwi_hvp step their rings per shot group on
+    concurrent streams; 1, 2 and 4 groups (4 shots here) give the same results bit for bit."""
+    wl, v = _case(73, nt=200, n_tx=4)
+    pb = _problem(d, wl, ckpt_interval=45)
+    pb.c_max = 2000.0
+    geom = d.Geometry.from_workload(wl)
+    sos, wav, vv = _cuda(wl.sos_start), _cuda(wl.wavelet), _cuda(v)
+    rho = _cuda(inputs.density_map(inputs.rng_for(75), wl.nx, wl.nz, wl.dx)[None]) if with_density else None
+    obs = d.simulate(pb, _cuda(wl.sos_true), wav, geom, density=rho)
+    w = torch.randn(obs.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(5)) * 1e-6
+    before = d.get_option(d.OPT_SHOT_GROUPS)
+    outs = []
+    try:
+        for groups in (1, 2, 4):
+            d.set_option(d.OPT_SHOT_GROUPS, groups)
+            dcd, cd = d.jvp(pb, sos, wav, geom, vv, density=rho, return_cd=True)
+            so, dcd2, g = d.second_order(pb, sos, wav, geom, w, vv, return_grad=True, check=True, density=rho)
+            hv, J, g2 = d.hvp(pb, sos, wav, geom, obs, vv, return_all=True, check=True, density=rho)
+            torch.cuda.synchronize()
+            outs.append((dcd, cd, so, dcd2, g, hv, J, g2))
+    finally:
+        d.set_option(d.OPT_SHOT_GROUPS, before)
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
+    assert float(outs[0][2].abs().max()) > 0.0 and float(outs[0][5].abs().max()) > 0.0

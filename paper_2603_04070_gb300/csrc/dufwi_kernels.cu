@@ -550,7 +550,41 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 // 0 = x0 - 8, row 0 = z0 - 8), bxs the 72 x 32 x-buoyancy tile (column h = half point
 // x0 - 4 + h + 1/2), bzs the 64 x 40 z-buoyancy tile (row j = half point z0 - 4 + j + 1/2), sw the
 // staggered weights. lap receives G, ctr the field at the block's cells.
+// z-fluxes of a whole 64 x 32 tile, each formed once: F[r] = b_z[r] sum_k s_k (box[r + 4 + k] -
+// box[r + 5 - k]) at the half-point rows r = 0 .. 38 of the z-buoyancy tile (box row 0 is z0 - 8),
+// for the 16 column quads, written over the buoyancy tile (each element is read and then written
+// by the same thread). Thread (quad tid & 15, group tid >> 4) takes rows 5g .. 5g + 4 from a
+// window of 12 box rows. Each flux is the same operations, in the same order, as in the register
+// form of vd_operator_block, so the two forms give identical results.
 template <int R>
+__device__ __forceinline__ void vd_zflux_tile(const float *box, float *bzs, const float *sw, int tid)
+{
+    const int lx = (tid & 15) * 4;
+    const int r0 = 5 * (tid >> 4);
+    float4 col[12];   // box rows r0 + 1 .. r0 + 12
+#pragma unroll
+    for (int i = 0; i < 12; ++i) col[i] = ld4s(box + (r0 + 1 + i) * kVBoxX + lx + kVHalo);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        const int r = r0 + f;
+        if (r > 38) break;   // the last group's fifth row is not read
+        float2 d[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+            const float4 up = col[f + 3 + k], dn = col[f + 4 - k];
+            const float2 sk = make_float2(sw[k - 1], sw[k - 1]);
+            d[0] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.x, up.y), neg2(make_float2(dn.x, dn.y))), d[0]);
+            d[1] = __ffma2_rn(sk, __fadd2_rn(make_float2(up.z, up.w), neg2(make_float2(dn.z, dn.w))), d[1]);
+        }
+        float *bp = bzs + r * kTileX + lx;
+        const float4 b = ld4s(bp);
+        const float2 f0 = __fmul2_rn(make_float2(b.x, b.y), d[0]), f1 = __fmul2_rn(make_float2(b.z, b.w), d[1]);
+        st4s(bp, make_float4(f0.x, f0.y, f1.x, f1.y));
+    }
+}
+
+// ZF: bzs holds the z-fluxes of the tile (vd_zflux_tile) instead of the z-buoyancies.
+template <int R, bool ZF = false>
 __device__ __forceinline__ void vd_operator_block(const float *box, const float *bxs, const float *bzs, int lx, int lz,
                                                   const float *sw, float4 (&lap)[4], float4 (&ctr)[4])
 {
@@ -605,7 +639,33 @@ __device__ __forceinline__ void vd_operator_block(const float *box, const float 
         lap[j] = make_float4(lxv[0].x, lxv[0].y, lxv[1].x, lxv[1].y);
         ctr[j] = make_float4(w[8], w[9], w[10], w[11]);
     }
-    {
+    if (ZF) {   // the tile's z-fluxes are in shared memory: divergence only
+        float2 lzv[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lzv[j][0] = lzv[j][1] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int f = 0; f < 11; ++f) {
+            const float4 F = ld4s(bzs + (lz + f) * kTileX + lx);
+            const float2 fl[2] = {make_float2(F.x, F.y), make_float2(F.z, F.w)};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int kp_ = f - j - 3, km_ = j + 4 - f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (kp_ >= 1 && kp_ <= R)
+                        lzv[j][h] = __ffma2_rn(make_float2(sw[kp_ - 1], sw[kp_ - 1]), fl[h], lzv[j][h]);
+                    if (km_ >= 1 && km_ <= R)
+                        lzv[j][h] = __ffma2_rn(make_float2(-sw[km_ - 1], -sw[km_ - 1]), fl[h], lzv[j][h]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 a01 = __fadd2_rn(make_float2(lap[j].x, lap[j].y), lzv[j][0]);
+            const float2 a23 = __fadd2_rn(make_float2(lap[j].z, lap[j].w), lzv[j][1]);
+            lap[j] = make_float4(a01.x, a01.y, a23.x, a23.y);
+        }
+    } else {
         float4 col[18];
 #pragma unroll
         for (int r = 0; r < 18; ++r) col[r] = ld4s(box + (lz + 1 + r) * kVBoxX + lx + kVHalo);
@@ -969,8 +1029,12 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
     // lx .. lx + 10); along z, the half-point rows lz .. lz + 10 of its four columns (box rows
     // lz + 1 .. lz + 18, buoyancy tile rows lz .. lz + 10). Box column/row 0 is x0 - 8 / z0 - 8;
     // x-buoyancy column h is the half point x0 - 4 + h + 1/2, z-buoyancy row j is z0 - 4 + j + 1/2.
+    // The z-fluxes are formed once per tile into shared memory (over the z-buoyancy tile), the
+    // x-fluxes per block in registers.
     float4 lap[4], ctr[4], nxt[4];
-    vd_operator_block<R>(box, fx, fz, lx, lz, p.sw, lap, ctr);
+    vd_zflux_tile<R>(box, fz, p.sw, tid);
+    __syncthreads();
+    vd_operator_block<R, true>(box, fx, fz, lx, lz, p.sw, lap, ctr);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int lo = (lz + j) * kTileX + lx;

@@ -765,7 +765,22 @@ def measure_linear_disk(dufwi, inputs, dev, flush, stream):
     """The 128 x 128 linear-disk gradient (2000 steps, one transmit, 32 receivers, every step kept):
     ms per gradient with FP32 and with compensated forward steps (the parity-grade form at weak
     residuals). One shot of 168 x 168 padded cells per launch is far below a wave of the GPU, so the
-    time is launch latency."""
+    time is launch latency. The FP32 form runs with the launch options the autotuner picks for this
+    shape (the compensated steps have one form); the caller's options are restored afterwards."""
+    import torch
+    from paper_2603_04070_gb300 import autotune
+    saved = {k: dufwi.get_option(o) for k, o in (("tile_z", dufwi.OPT_TILE_Z), ("two_step", dufwi.OPT_TWO_STEP),
+                                                 ("persistent", dufwi.OPT_PERSISTENT),
+                                                 ("multi_tile", dufwi.OPT_MULTI_TILE),
+                                                 ("early", dufwi.OPT_EARLY_LOADS),
+                                                 ("groups", dufwi.OPT_SHOT_GROUPS))}
+    try:
+        return _measure_linear_disk(dufwi, inputs, autotune, dev, flush, stream)
+    finally:
+        autotune.apply(saved)
+
+
+def _measure_linear_disk(dufwi, inputs, autotune, dev, flush, stream):
     import torch
     wl = inputs.make_workload("linear_disk", seed=1)
     geom = dufwi.Geometry.from_workload(wl)
@@ -777,6 +792,10 @@ def measure_linear_disk(dufwi, inputs, dev, flush, stream):
         pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                            pml_cref=wl.pml_cref, fd_order=wl.fd_order, c_max=wl.c_max, forward_precision=prec)
         obs = dufwi.simulate(pb, torch.from_numpy(wl.sos_true).to(dev), wav, geom)
+        tuned = None
+        if prec == "fp32":
+            t = autotune.tune(pb, sos, wav, geom, gradient=True, cd_obs=obs, steps=400, repeats=2)
+            tuned = {k: t[k] for k in autotune.KNOBS}
         ws = torch.empty(dufwi.workspace_size(pb, geom, 1), dtype=torch.uint8, device=dev)
         J = torch.empty(1, dtype=torch.float64, device=dev)
         g = torch.empty_like(sos)
@@ -817,6 +836,8 @@ def measure_linear_disk(dufwi, inputs, dev, flush, stream):
         rec[prec] = {"ms_per_gradient": ms, "value": 2.0 * wl.padded_cells * wl.nt / (ms / 1e3) / 1e9, "unit": UNIT,
                      "graph_ms_per_gradient": gms,
                      "graph_value": 2.0 * wl.padded_cells * wl.nt / (gms / 1e3) / 1e9}
+        if tuned:
+            rec[prec]["tuned_options"] = tuned
         del graph, ws
     return rec
 

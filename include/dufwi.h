@@ -136,11 +136,11 @@ typedef struct {
  *     is stretched by 1/s, s = 1 + d/(alpha + i omega), through one memory variable per
  *     difference and axis (recursive convolution; alpha = pml_alpha (1 - xi/L)); no damping
  *     term. Supported by dufwi_simulate, dufwi_simulate_noalloc, dufwi_misfit,
- *     dufwi_forward_save/dufwi_backward and dufwi_misfit_gradient, with or without a density map
- *     and with any ckpt_interval: a checkpoint stores the four memory fields read at its step in
- *     FP32 beside (U^t, U^{t-1}), and the adjoint keeps its own memory variables apart from the
- *     forward's; not by the *_sized calls, dufwi_jvp, dufwi_second_order or dufwi_hvp
- *     (DUFWI_ERR_UNSUPPORTED). */
+ *     dufwi_forward_save/dufwi_backward, dufwi_misfit_gradient, dufwi_second_order and dufwi_hvp,
+ *     with or without a density map and with any ckpt_interval: a checkpoint stores the four
+ *     memory fields read at its step in FP32 beside (U^t, U^{t-1}) (and the Born field's beside
+ *     dU in the second-order calls), and each adjoint field keeps its own memory variables; not
+ *     by the *_sized calls or dufwi_jvp (DUFWI_ERR_UNSUPPORTED). */
 #define DUFWI_BOUNDARY_DAMPING 0
 #define DUFWI_BOUNDARY_CPML 1
 
@@ -291,9 +291,13 @@ int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, c
  *   grad    NULL or [n_maps][nz][nx] float, device, output: (dM/dC)^T cd_grad
  *   workspace: device, >= dufwi_second_order_workspace_size bytes.
  * With a density map all three fields use the staggered variable-density operator of Eq. 1 (the
- * operator is symmetric, so the adjoint kinds use it as they are). DUFWI_BOUNDARY_CPML and the
- * compensated forward steps give DUFWI_ERR_UNSUPPORTED. The launch options (tile height,
- * two-step, persistent) do not apply: every step uses 64 x 32 tiles, one launch per step. */
+ * operator is symmetric, so the adjoint kinds use it as they are). With DUFWI_BOUNDARY_CPML Lap is
+ * the stretched operator G of the CPML step (memory variables included), each of U, dU, mu and
+ * dmu has its own memory variables, and in the dmu recursion dkappa' multiplies mu's adjoint
+ * operator term A(mu^{m+1}) (mu^m = 2 mu^{m+1} - mu^{m+2} + kappa' A); tiles away from the
+ * layer run the staggered kernel. The compensated forward steps give DUFWI_ERR_UNSUPPORTED.
+ * The launch options (tile height, two-step, persistent) do not apply: every step uses 64 x 32
+ * tiles, one launch per step and shot group (two with the CPML: interior and layer tiles). */
 int dufwi_second_order_workspace_size(const dufwi_problem *pb, const dufwi_shots *shots,
                                       int32_t n_maps, size_t *bytes);
 int dufwi_second_order(const dufwi_problem *pb, const float *sos, const float *density,

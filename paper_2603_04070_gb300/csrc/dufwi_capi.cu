@@ -98,6 +98,7 @@ struct Layout {
     int n_rxe;               // row length of the grown-tile receiver lists (4 n_rx)
     size_t o_cm[8], o_cpml;  // CPML: memory variables (two sets of psi_x, psi_z, xi_x, xi_z), coefficient tables
     size_t o_cma[8];         // CPML gradients: the adjoint's memory variables (two sets), apart from the forward's
+    size_t o_cmb[8], o_cmd[8];   // CPML second-order calls: the Born field's and dmu's memory variables
     size_t o_snapm;          // CPML gradients: FP32 snapshots of the forward memory set read at each segment start
     size_t o_snapk;          // FP32 snapshot (hi and lo planes when compensated) of the first kept segment's start
     size_t o_flags, o_bx, o_bz, o_dkap, o_status, o_mapdims, o_tx, o_rx, o_tab1, o_sorted1, o_tab2, o_sorted2, o_tabe, o_sortede, o_damp, o_fold, o_kap,
@@ -283,7 +284,7 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     L->o_bx = take((size_t)n_maps * L->slice * sizeof(float));     // buoyancies (density maps only)
     L->o_bz = take((size_t)n_maps * L->slice * sizeof(float));
     if (pb->boundary == DUFWI_BOUNDARY_CPML) {
-        if (kind == kLayoutJvp || kind == kLayoutSecond) return DUFWI_ERR_UNSUPPORTED;   // no Born step
+        if (kind == kLayoutJvp) return DUFWI_ERR_UNSUPPORTED;   // the Born call has no CPML step
         for (int i = 0; i < 8; ++i) L->o_cm[i] = take((size_t)L->S * L->slice * sizeof(float));
         L->o_cpml = take(sizeof(float) * 4 * (size_t)(L->nxp + L->nzp));
         if (gradient) {
@@ -291,6 +292,14 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
             // a recomputed segment restarts from (U^t, U^{t-1}) and the four memory fields read at step t
             if (L->n_seg > 1 && L->n_snap > 0)
                 L->o_snapm = take((size_t)L->n_snap * 4 * L->S * L->slice * sizeof(float));
+        }
+        if (kind == kLayoutSecond) {   // memory variables of mu, dU and dmu; U's and dU's at segment starts
+            for (int i = 0; i < 8; ++i) {
+                L->o_cma[i] = take((size_t)L->S * L->slice * sizeof(float));
+                L->o_cmb[i] = take((size_t)L->S * L->slice * sizeof(float));
+                L->o_cmd[i] = take((size_t)L->S * L->slice * sizeof(float));
+            }
+            if (L->n_seg > 1) L->o_snapm = take((size_t)L->n_seg * 8 * L->S * L->slice * sizeof(float));
         }
     }
     for (int i = 0; i < 4; ++i) L->o_f[i] = take(field);
@@ -499,7 +508,9 @@ struct Ctx {
     CUtensorMap bxl1, bzl1;                   // compensated with density: low parts of the buoyancies
     int mem_par = 0;                          // CPML: which memory-variable set the next forward step reads
     int amem_par = 0;                         // CPML: the same for the adjoint's own sets (gradient calls)
+    int bmem_par = 0, dmem_par = 0;           // CPML second-order calls: the Born field's and dmu's sets
     CpmlMaps cm_fwd[2], cm_adj[2];            // CPML: maps reading set 0 / set 1
+    CpmlMaps cm_born[2], cm_dadj[2];          // CPML second-order calls: dU (forward layout), dmu (adjoint)
     FieldMaps fmap[4], mmap[4];
     CUtensorMap kap1, kap2, hist1, hist2, grad1, grad2, dkap1, bx1, bz1;
     FieldMaps mumap[4], dmumap[4];            // second-order calls: mu and dmu rings
@@ -576,9 +587,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.st = static_cast<cudaStream_t>(stream);
     c.cpml = c.pb->boundary == DUFWI_BOUNDARY_CPML;
     c.vd = density != nullptr || c.cpml;        // the CPML runs on the staggered operator
-    // the Born step runs on the variable-density operator, not with the CPML's memory variables;
-    // the second-order kernels use the compact Laplacian (constant density) only
-    if (c.cpml && (c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
+    // the Born call has no CPML step (the second-order calls run their own kinds on the layer tiles)
+    if (c.cpml && c.jvp) return DUFWI_ERR_UNSUPPORTED;
     if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
     c.comp = L.comp;
     if (c.comp && (c.cpml || c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
@@ -763,7 +773,7 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                 return DUFWI_ERR_CUDA;
             // the adjoint has sets of its own in gradient calls (a recompute between adjoint segments
             // must not overwrite them); chi is read over node boxes with a halo along its axis
-            const size_t *ao = gradient ? L.o_cma : L.o_cm;
+            const size_t *ao = (gradient || c.so) ? L.o_cma : L.o_cm;
             const float *ahx = c.at<float>(ao[4 * k]), *ahz = c.at<float>(ao[4 * k + 1]);
             const float *anx = c.at<float>(ao[4 * k + 2]), *anz = c.at<float>(ao[4 * k + 3]);
             if (tensor_map(&c.cm_adj[k].mem_hx, ahx, L, L.S, 0, kVFxX, kVTileZ) ||
@@ -771,6 +781,21 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                 tensor_map(&c.cm_adj[k].mem_nx, anx, L, L.S, 0, kVBoxX, kVTileZ) ||
                 tensor_map(&c.cm_adj[k].mem_nz, anz, L, L.S, 0, kTileX, kVBoxZ))
                 return DUFWI_ERR_CUDA;
+            if (c.so) {   // the Born field's sets (forward layout) and dmu's (adjoint layout)
+                const float *bhx = c.at<float>(L.o_cmb[4 * k]), *bhz = c.at<float>(L.o_cmb[4 * k + 1]);
+                const float *bnx = c.at<float>(L.o_cmb[4 * k + 2]), *bnz = c.at<float>(L.o_cmb[4 * k + 3]);
+                const float *dhx = c.at<float>(L.o_cmd[4 * k]), *dhz = c.at<float>(L.o_cmd[4 * k + 1]);
+                const float *dnx = c.at<float>(L.o_cmd[4 * k + 2]), *dnz = c.at<float>(L.o_cmd[4 * k + 3]);
+                if (tensor_map(&c.cm_born[k].mem_hx, bhx, L, L.S, 0, kVFxX, kVTileZ) ||
+                    tensor_map(&c.cm_born[k].mem_hz, bhz, L, L.S, 0, kTileX, kVFzZ) ||
+                    tensor_map(&c.cm_born[k].mem_nx, bnx, L, L.S, 0, kTileX, kVTileZ) ||
+                    tensor_map(&c.cm_born[k].mem_nz, bnz, L, L.S, 0, kTileX, kVTileZ) ||
+                    tensor_map(&c.cm_dadj[k].mem_hx, dhx, L, L.S, 0, kVFxX, kVTileZ) ||
+                    tensor_map(&c.cm_dadj[k].mem_hz, dhz, L, L.S, 0, kTileX, kVFzZ) ||
+                    tensor_map(&c.cm_dadj[k].mem_nx, dnx, L, L.S, 0, kVBoxX, kVTileZ) ||
+                    tensor_map(&c.cm_dadj[k].mem_nz, dnz, L, L.S, 0, kTileX, kVBoxZ))
+                    return DUFWI_ERR_CUDA;
+            }
         }
     }
     if (c.jvp) {
@@ -1754,11 +1779,51 @@ int so_step(Ctx &c, Ring &r, int kind, StepParams p, const SoParams &q, long lon
     p.rx_tab = c.at<int2>(c.L.o_tab1);
     p.rx_sorted = c.at<int>(c.L.o_sorted1);
     const int G = c.forked ? c.groups : 1;
-    for (int g = 0; g < G; ++g) {
-        StepParams pg = p;
-        const cudaStream_t st = group_stream(c, G, g, pg);
-        CKL(launch_so_step(c.L.radius, kind, c.vd, tm, pg, q, st));
+    if (!c.cpml) {
+        for (int g = 0; g < G; ++g) {
+            StepParams pg = p;
+            const cudaStream_t st = group_stream(c, G, g, pg);
+            CKL(launch_so_step(c.L.radius, kind, c.vd, tm, pg, q, st));
+        }
+        std::swap(r.cur, r.prv);
+        return DUFWI_OK;
     }
+    // CPML: tiles away from the layer run the staggered second-order kernel, the layer tiles the
+    // CPML kernel's second-order kind with this field's memory-variable set (read set par, write
+    // the other)
+    const Layout &L = c.L;
+    int &par = kind == kSoBorn ? c.bmem_par : kind == kSoAdj ? c.amem_par : c.dmem_par;
+    const size_t *o = kind == kSoBorn ? L.o_cmb : kind == kSoAdj ? L.o_cma : L.o_cmd;
+    const CpmlMaps &cm = kind == kSoBorn ? c.cm_born[par] : kind == kSoAdj ? c.cm_adj[par] : c.cm_dadj[par];
+    const int w = 1 - par;
+    CpmlParams cp;
+    cp.hx_out = c.at<float>(o[4 * w]);
+    cp.hz_out = c.at<float>(o[4 * w + 1]);
+    cp.nx_out = c.at<float>(o[4 * w + 2]);
+    cp.nz_out = c.at<float>(o[4 * w + 3]);
+    cp.cx = c.at<float>(L.o_cpml);
+    cp.cz = cp.cx + 4 * (size_t)L.nxp;
+    StepMaps sm;
+    memset(&sm, 0, sizeof(sm));
+    sm.cur_box = tm.cur_box;
+    sm.out_tile = tm.out_tile;
+    sm.kap_tile = tm.kap_tile;
+    sm.bx_tile = c.bx1;
+    sm.bz_tile = c.bz1;
+    sm.hist_tile = c.hist1;
+    sm.grad_tile = kind == kSoBorn ? c.dkap1 : kind == kSoAdj ? c.so_h2 : c.so_h3;
+    SoParams qc = q;
+    qc.dkap = c.at<float>(L.o_dkap);
+    for (int g = 0; g < G; ++g) {
+        StepParams pi = p;
+        const cudaStream_t st = group_stream(c, G, g, pi);
+        StepParams pl = pi;
+        pi.tile_class = 1;
+        pl.tile_class = 2;
+        CKL(launch_so_step(L.radius, kind, true, tm, pi, q, st));
+        CKL(launch_so_step_cpml(L.radius, kind, sm, cm, pl, cp, qc, st));
+    }
+    par = w;
     std::swap(r.cur, r.prv);
     return DUFWI_OK;
 }
@@ -1855,9 +1920,19 @@ int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float
     CK(cudaMemsetAsync(accA, 0, field, c.st));
     CK(cudaMemsetAsync(accB, 0, field, c.st));
     CK(cudaMemsetAsync(c.at<float>(L.o_hist3), 0, field, c.st));
+    if (c.cpml) {   // every field's memory variables start at zero
+        for (int i = 0; i < 8; ++i) {
+            CK(cudaMemsetAsync(c.at<float>(L.o_cm[i]), 0, field, c.st));
+            CK(cudaMemsetAsync(c.at<float>(L.o_cmb[i]), 0, field, c.st));
+            CK(cudaMemsetAsync(c.at<float>(L.o_cma[i]), 0, field, c.st));
+            CK(cudaMemsetAsync(c.at<float>(L.o_cmd[i]), 0, field, c.st));
+        }
+        c.mem_par = c.bmem_par = c.amem_par = c.dmem_par = 0;
+    }
     g_prof.span(3, e0, g_prof.mark(c.st), nl);
 
-    // forward: background and Born fields together, FP32 snapshots of both at segment starts
+    // forward: background and Born fields together, FP32 snapshots of both at segment starts (with
+    // the CPML also the memory sets U's and dU's next steps read)
     nl = 0;
     e0 = g_prof.mark(c.st);
     float *dcd_out = L.n_rx > 0 ? (dcd ? dcd : c.at<float>(L.o_cd)) : nullptr;
@@ -1871,6 +1946,15 @@ int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float
             CK(cudaMemcpyAsync(snap + field, fr.buf[fr.prv], field, cudaMemcpyDeviceToDevice, c.st));
             CK(cudaMemcpyAsync(snap + 2 * field, br.buf[br.cur], field, cudaMemcpyDeviceToDevice, c.st));
             CK(cudaMemcpyAsync(snap + 3 * field, br.buf[br.prv], field, cudaMemcpyDeviceToDevice, c.st));
+            if (c.cpml) {
+                char *sm = c.at<char>(L.o_snapm) + (size_t)sg * 8 * field;
+                for (int i = 0; i < 4; ++i) {
+                    CK(cudaMemcpyAsync(sm + i * field, c.at<float>(L.o_cm[4 * c.mem_par + i]), field,
+                                       cudaMemcpyDeviceToDevice, c.st));
+                    CK(cudaMemcpyAsync(sm + (4 + i) * field, c.at<float>(L.o_cmb[4 * c.bmem_par + i]), field,
+                                       cudaMemcpyDeviceToDevice, c.st));
+                }
+            }
         }
         rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, cd_bg, dcd_out, nl);
         if (rc) return rc;
@@ -1912,6 +1996,16 @@ int second_order_run(Ctx &c, const float *sos, const float *wavelet, const float
             CK(cudaMemcpyAsync(fr.buf[1], snap + field, field, cudaMemcpyDeviceToDevice, c.st));
             CK(cudaMemcpyAsync(br.buf[0], snap + 2 * field, field, cudaMemcpyDeviceToDevice, c.st));
             CK(cudaMemcpyAsync(br.buf[1], snap + 3 * field, field, cudaMemcpyDeviceToDevice, c.st));
+            if (c.cpml) {   // the memory sets steps t0 of U and dU read: set t0 & 1 of each
+                c.mem_par = c.bmem_par = t0 & 1;
+                const char *sm = c.at<char>(L.o_snapm) + (size_t)sg * 8 * field;
+                for (int i = 0; i < 4; ++i) {
+                    CK(cudaMemcpyAsync(c.at<float>(L.o_cm[4 * c.mem_par + i]), sm + i * field, field,
+                                       cudaMemcpyDeviceToDevice, c.st));
+                    CK(cudaMemcpyAsync(c.at<float>(L.o_cmb[4 * c.bmem_par + i]), sm + (4 + i) * field, field,
+                                       cudaMemcpyDeviceToDevice, c.st));
+                }
+            }
             rc = so_forward_range(c, fr, br, t0, t1, t0, wavelet, nullptr, nullptr, nl);
             if (rc) return rc;
             g_prof.span(1, e0, g_prof.mark(c.st), nl);

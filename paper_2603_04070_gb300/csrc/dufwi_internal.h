@@ -215,6 +215,7 @@ struct SoParams {
     float *sum2;             // adjoint: sum of mu^m Lap(dU^{m-1})
     int h1_slot;             // slot of Lap(U^n) (Born) or Lap(U^{m-1}) (adjoint kinds) in h1
     int h2_slot;             // adjoint: slot of Lap(dU^{m-1}) in h2
+    const float *dkap;       // CPML Born-adjoint (layer tiles): dkappa' [n_maps][nzp][pitch]
 };
 
 // Persistent sweep: n_steps consecutive steps of one sweep in a single cooperative launch. Work
@@ -264,6 +265,13 @@ cudaError_t launch_step_vd(int radius, int mode, const StepMaps &tm, const StepP
 // One step of the second-order sweeps (kinds kSoBorn, kSoAdj, kSoBornAdj; 64 x 32 tiles).
 // vd: the staggered variable-density operator (cur_box 80 x 48 with halo 8, buoyancy maps set)
 // instead of the compact Laplacian (cur_box 72 x 40).
+// Second-order kinds on the CPML layer tiles (p.tile_class 2; the other tiles run launch_so_step
+// with the staggered operator and p.tile_class 1). tm: cur_box (80 x 48 box of the advanced
+// field), out_tile, kap_tile, bx_tile, bz_tile; hist_tile = the first history (4-D); grad_tile =
+// dkappa' (Born), the second history (adjoint, 4-D) or A(mu^{m+1}) (Born-adjoint). cm/cp: the
+// field's own memory-variable set (forward layout for the Born field, adjoint layout otherwise).
+cudaError_t launch_so_step_cpml(int radius, int kind, const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                                const CpmlParams &cp, const SoParams &q, cudaStream_t st);
 cudaError_t launch_so_step(int radius, int kind, bool vd, const SoMaps &tm, const StepParams &p, const SoParams &q,
                            cudaStream_t st);
 // Second-order term before the fold: a += b - (v / C) g on the padded grid of every shot, with v

@@ -707,6 +707,14 @@ __device__ __forceinline__ void vd_operator_block(const float *box, const float 
     }
 }
 
+// CPML split: does the 64 x 32 tile at (x0, z0), grown by 8 cells, lie inside the physical grid
+// (where every CPML coefficient is the identity, so that the memory variables stay zero)?
+__device__ __forceinline__ bool cpml_free_tile(const StepParams &p, int x0, int z0)
+{
+    return x0 - 2 * kHalo >= p.P && x0 + kTileX + 2 * kHalo <= p.P + p.Nx - 1 && z0 - 2 * kHalo >= p.P &&
+           z0 + kVTileZ + 2 * kHalo <= p.P + p.Nz - 1;
+}
+
 // ---- second-order products ---------------------------------------------------------------------
 // For a cotangent w on the channel data and an SoS direction v, the derivative along v of
 // G = (dM/dC)^T w (Eq. 6 for w = 2 (M - M_obs)) follows from differentiating the discrete adjoint
@@ -760,6 +768,7 @@ so_step_kernel(const __grid_constant__ SoMaps tm, const StepParams p, const SoPa
     float *t2 = t1 + SL::kTile;
     float *t3 = t2 + SL::kTile;
     const MapGrid mg = map_grid(p, map);
+    if (VD && p.tile_class == 1 && !cpml_free_tile(p, x0, z0)) return;   // CPML: layer tiles run elsewhere
 
     if (tid == 0) {
         prefetch_tensormap(&tm.cur_box);
@@ -925,14 +934,6 @@ __global__ void so_combine_kernel(float *a, const float *b, const float *g, cons
 // registers, the x fluxes of its four rows and the z fluxes of its four columns that its 4 x 4
 // block needs (11 half points each way, shared-memory reads of 128 bits), their divergence, and
 // runs the common Eq. 2 epilogue.
-// CPML split: does the 64 x 32 tile at (x0, z0), grown by 8 cells, lie inside the physical grid
-// (where every CPML coefficient is the identity, so that the memory variables stay zero)?
-__device__ __forceinline__ bool cpml_free_tile(const StepParams &p, int x0, int z0)
-{
-    return x0 - 2 * kHalo >= p.P && x0 + kTileX + 2 * kHalo <= p.P + p.Nx - 1 && z0 - 2 * kHalo >= p.P &&
-           z0 + kVTileZ + 2 * kHalo <= p.P + p.Nz - 1;
-}
-
 template <int MODE>
 struct VdLayout {
     static constexpr int kBox = kVBoxX * kVBoxZ;
@@ -1102,7 +1103,10 @@ __global__ void __launch_bounds__(128, 4) vd_step_kernel(const __grid_constant__
 //   p = phi + b_rho Fbar,  dbar = b_rho Fbar + a p,  phi <- b p,
 //   mu^n = 2 mu^{n+1} - mu^{n+2} - kappa' D- dbar (+ the scaled residual injections),
 // and the imaging term is again mu^n G^{n-1} with G from the forward sweep's history.
-template <int MODE>
+// SO (0, or 1 + a second-order kind: kSoBorn with the forward arithmetic, kSoAdj and kSoBornAdj
+// with the adjoint's) adds the second-order products' operands: Lap-history tiles t0, t1 in
+// place of the history and sum tiles (the running sums are read from global memory).
+template <int MODE, int SO = 0>
 struct CpmlLayout {
     static constexpr bool kAdj = MODE == kAdjoint;
     static constexpr int kBox = kVBoxX * kVBoxZ;                  // 80 x 48
@@ -1111,9 +1115,11 @@ struct CpmlLayout {
     static constexpr int kTile = kTileX * kVTileZ;                // 64 x 32
     static constexpr int kNx = kAdj ? kVBoxX * kVTileZ : kTile;   // chi: 80 x 32; xi: 64 x 32
     static constexpr int kNz = kAdj ? kTileX * kVBoxZ : kTile;    // chi: 64 x 48; xi: 64 x 32
-    static constexpr int kFloats = kBox + 2 * kBx + 2 * kBz + kNx + kNz + (kAdj ? 4 : 2) * kTile;
+    static constexpr int kFloats = kBox + 2 * kBx + 2 * kBz + kNx + kNz + ((kAdj || SO) ? 4 : 2) * kTile;
     static constexpr uint32_t kBytes = kFloats * sizeof(float);
 };
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
 // (a, b) of a table of 4 rows of length n (a node, b node, a half, b half); identity outside.
 __device__ __forceinline__ float2 cpml_coef(const float *t, int n, int row, int i)
@@ -1122,12 +1128,22 @@ __device__ __forceinline__ float2 cpml_coef(const float *t, int n, int row, int 
     return make_float2(__ldg(t + (row + 0) * n + i), __ldg(t + (row + 1) * n + i));
 }
 
-template <int R, int MODE>
+// Second-order kinds (SO = 1 + kind; see so_step_kernel for the recursions), on the layer tiles:
+//   kSoBorn (MODE kFwdHist): dU^{n+1} = the CPML step on dU (its own memory variables) + dkappa' G(U^n)
+//     with G(U^n) from history slot q.h1_slot (tm.hist_tile) and dkappa' (tm.grad_tile, per map);
+//     writes G(dU^n) to q.lap_out and samples dU^n into p.cd when given.
+//   kSoAdj (MODE kAdjoint): the adjoint CPML step on mu; sums mu^m G(U^{m-1}) into q.sum1 and
+//     mu^m G(dU^{m-1}) into q.sum2 (histories tm.hist_tile slot h1_slot, tm.grad_tile slot
+//     h2_slot); writes its operator term A(mu^{m+1}) (mu^m = 2mu^{m+1} - mu^{m+2} + kappa' A) to
+//     q.lap_out.
+//   kSoBornAdj (MODE kAdjoint): the adjoint CPML step on dmu + dkappa' A(mu^{m+1}) (tm.grad_tile
+//     per shot; dkappa' read from q.dkap); sums dmu^m G(U^{m-1}) into q.sum1.
+template <int R, int MODE, int SO = 0>
 __global__ void __launch_bounds__(128, 2)
 cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ CpmlMaps cm, const StepParams p,
-                 const CpmlParams cp)
+                 const CpmlParams cp, const SoParams q)
 {
-    using CL = CpmlLayout<MODE>;
+    using CL = CpmlLayout<MODE, SO>;
     constexpr bool ADJ = CL::kAdj;
     constexpr int TZ = kVTileZ;
     extern __shared__ __align__(128) float smem[];
@@ -1150,8 +1166,8 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
     float *mnz = mnx + CL::kNx;        // xi / chi, z
     float *pv = mnz + CL::kNz;         // U^{n-1} (mu^{m+2})
     float *kp = pv + CL::kTile;        // kappa'
-    float *hs = kp + CL::kTile;        // adjoint: G^{m-1}
-    float *gg = hs + CL::kTile;        // adjoint: imaging sums
+    float *hs = kp + CL::kTile;        // adjoint: G^{m-1} (second-order kinds: t0)
+    float *gg = hs + CL::kTile;        // adjoint: imaging sums (second-order kinds: t1)
     if (x0 >= p.nxp || z0 >= p.nzp) return;
     if (p.tile_class == 2 && cpml_free_tile(p, x0, z0)) return;    // CPML split: interior tiles run elsewhere
 
@@ -1161,7 +1177,7 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
         prefetch_tensormap(&tm.cur_box);
         mbar_init(&bar, 1);
         mbar_arrive_expect_tx(&bar, CL::kBytes);
-        if (p.early) {
+        if (SO == 0 && p.early) {
             tma_load_3d(bxs, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
             tma_load_3d(bzs, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
@@ -1172,7 +1188,7 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
     grid_dependency_wait();
     if (tid == 0) {
         tma_load_3d(box, &tm.cur_box, &bar, x0 - kVHalo, z0 - kVHalo, s);
-        if (!p.early) {
+        if (SO != 0 || !p.early) {
             tma_load_3d(bxs, &tm.bx_tile, &bar, x0 - kHalo, z0, map);
             tma_load_3d(bzs, &tm.bz_tile, &bar, x0, z0 - kHalo, map);
         }
@@ -1185,20 +1201,33 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
             tma_load_3d(mnx, &cm.mem_nx, &bar, x0, z0, s);
             tma_load_3d(mnz, &cm.mem_nz, &bar, x0, z0, s);
         }
-        if (!p.early) {
+        if (SO != 0) {
             tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
             tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
-            if (ADJ) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            tma_load_4d(hs, &tm.hist_tile, &bar, x0, z0, s, q.h1_slot);
+            if (SO == 1 + kSoBorn) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, map);
+            if (SO == 1 + kSoAdj) tma_load_4d(gg, &tm.grad_tile, &bar, x0, z0, s, q.h2_slot);
+            if (SO == 1 + kSoBornAdj) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
+        } else {
+            if (!p.early) {
+                tma_load_3d(pv, &tm.out_tile, &bar, x0, z0, s);
+                tma_load_3d(kp, &tm.kap_tile, &bar, x0, z0, map);
+                if (ADJ) tma_load_4d_stream(hs, &tm.hist_tile, &bar, x0, z0, s, p.hist_slot);
+            }
+            if (ADJ) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
         }
-        if (ADJ) tma_load_3d(gg, &tm.grad_tile, &bar, x0, z0, s);
     }
     grid_dependents_launch();
 
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     int2 rx_range = make_int2(0, 0);
-    if (MODE != kFwdHist) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
-    gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ, kTileX,
-                            tid, 128);
+    if (MODE != kFwdHist || SO == 1 + kSoBorn) rx_range = __ldg(p.rx_tab + tx_idx * (gridDim.x * gridDim.y) + tile);
+    if (SO == 1 + kSoBorn) {   // the Born field has no point source of its own
+        if (tid == 0) inj.n = 0;
+    } else {
+        gather_injections<MODE>(inj, p, p.rx_sorted, p.n_rx, s, tx_idx, p.step, rx_range, x0, z0, kTileX, TZ,
+                                kTileX, tid, 128);
+    }
     const int lx = (tid & 15) * 4;
     const int lz = (tid >> 4) * 4;
     const int gx = x0 + lx;
@@ -1463,6 +1492,15 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
         const int lo = (lz + j) * kTileX + lx;
         const float4 pp = ld4s(pv + lo), kk = ld4s(kp + lo), u = ctr[j];
         nxt[j] = fma4(kk, opv[j], make_float4(2.f * u.x - pp.x, 2.f * u.y - pp.y, 2.f * u.z - pp.z, 2.f * u.w - pp.w));
+        if (SO == 1 + kSoBorn) nxt[j] = fma4(ld4s(gg + lo), ld4s(hs + lo), nxt[j]);          // + dkappa' G(U^n)
+        if (SO == 1 + kSoBornAdj) {                                                          // + dkappa' A(mu^{m+1})
+            const int gz = z0 + lz + j;
+            const float4 dk = (col_ok && gz < nzp)
+                                  ? ldg4(q.dkap + static_cast<long long>(map) * p.slice +
+                                         static_cast<long long>(gz) * p.pitch + gx)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            nxt[j] = fma4(dk, ld4s(gg + lo), nxt[j]);
+        }
     }
     if (inj.n > 0) {
         __syncthreads();
@@ -1487,14 +1525,21 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
             nv.w = 0.f; lv.w = 0.f;
         }
         const long long o = shot_off + static_cast<long long>(gz) * p.pitch + gx;
+        const int lo = (lz + j) * kTileX + lx;
         st4(p.out + o, nv);
-        if (MODE == kFwdSampleHist || MODE == kFwdHist) st4_stream(p.hist + o, lv);
-        if (MODE == kAdjoint) {
-            const int lo = (lz + j) * kTileX + lx;
-            st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+        if (SO == 0) {
+            if (MODE == kFwdSampleHist || MODE == kFwdHist) st4_stream(p.hist + o, lv);
+            if (MODE == kAdjoint) st4(p.grad + o, fma4(nv, ld4s(hs + lo), ld4s(gg + lo)));
+        } else {
+            if (SO == 1 + kSoBorn || SO == 1 + kSoAdj) st4(q.lap_out + o, lv);
+            if (SO == 1 + kSoAdj) {
+                st4(q.sum1 + o, fma4(nv, ld4s(hs + lo), ldg4(q.sum1 + o)));
+                st4(q.sum2 + o, fma4(nv, ld4s(gg + lo), ldg4(q.sum2 + o)));
+            }
+            if (SO == 1 + kSoBornAdj) st4(q.sum1 + o, fma4(nv, ld4s(hs + lo), ldg4(q.sum1 + o)));
         }
     }
-    if (MODE == kFwdSample || MODE == kFwdSampleHist) {
+    if (MODE == kFwdSample || MODE == kFwdSampleHist || (SO == 1 + kSoBorn && p.cd)) {
         const int cnt = (rx_range.x >= 0 && rx_range.y >= 0 && rx_range.x + rx_range.y <= p.n_rx) ? rx_range.y : 0;
         for (int e = tid; e < cnt; e += 128) {
             const int r = __ldg(p.rx_sorted + tx_idx * p.n_rx + rx_range.x + e);
@@ -2394,7 +2439,7 @@ static cudaError_t launch_step_cpml_rm(const StepMaps &tm, const CpmlMaps &cm, c
 {
     using CL = CpmlLayout<MODE>;
     static DeviceCache dc;   // shared-memory attributes, set once per device
-    cudaError_t e = configure_kernel(cpml_step_kernel<R, MODE>, CL::kBytes, dc);
+    cudaError_t e = configure_kernel(cpml_step_kernel<R, MODE, 0>, CL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_shots);
@@ -2406,7 +2451,56 @@ static cudaError_t launch_step_cpml_rm(const StepMaps &tm, const CpmlMaps &cm, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cpml_step_kernel<R, MODE>, tm, cm, p, cp);
+    SoParams q;
+    memset(&q, 0, sizeof(q));
+    return cudaLaunchKernelEx(&cfg, cpml_step_kernel<R, MODE, 0>, tm, cm, p, cp, q);
+}
+
+template <int R, int KIND>
+static cudaError_t launch_so_step_cpml_rk(const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                                          const CpmlParams &cp, const SoParams &q, cudaStream_t st)
+{
+    constexpr int MODE = KIND == kSoBorn ? kFwdHist : kAdjoint;
+    using CL = CpmlLayout<MODE, 1 + KIND>;
+    static DeviceCache dc;   // shared-memory attributes, set once per device
+    cudaError_t e = configure_kernel(cpml_step_kernel<R, MODE, 1 + KIND>, CL::kBytes, dc);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + kVTileZ - 1) / kVTileZ, p.n_shots);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = CL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cpml_step_kernel<R, MODE, 1 + KIND>, tm, cm, p, cp, q);
+}
+
+template <int R>
+static cudaError_t launch_so_step_cpml_r(int kind, const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                                         const CpmlParams &cp, const SoParams &q, cudaStream_t st)
+{
+    switch (kind) {
+    case kSoBorn: return launch_so_step_cpml_rk<R, kSoBorn>(tm, cm, p, cp, q, st);
+    case kSoAdj: return launch_so_step_cpml_rk<R, kSoAdj>(tm, cm, p, cp, q, st);
+    case kSoBornAdj: return launch_so_step_cpml_rk<R, kSoBornAdj>(tm, cm, p, cp, q, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_so_step_cpml(int radius, int kind, const StepMaps &tm, const CpmlMaps &cm, const StepParams &p,
+                                const CpmlParams &cp, const SoParams &q, cudaStream_t st)
+{
+    if (p.tile_z != kVTileZ || p.map_dims || p.tile_class != 2) return cudaErrorInvalidValue;
+    switch (radius) {
+    case 1: return launch_so_step_cpml_r<1>(kind, tm, cm, p, cp, q, st);
+    case 2: return launch_so_step_cpml_r<2>(kind, tm, cm, p, cp, q, st);
+    case 3: return launch_so_step_cpml_r<3>(kind, tm, cm, p, cp, q, st);
+    case 4: return launch_so_step_cpml_r<4>(kind, tm, cm, p, cp, q, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int R>

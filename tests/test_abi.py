@@ -158,8 +158,9 @@ def test_boundary_and_option_validation():
 
 def test_second_order_workspace_sizing_and_validation():
     """The second-order call keeps two histories: every step with ckpt_interval 0, one segment
-    of each plus four FP32 snapshots per segment otherwise; the staggered operators have no
-    Born step."""
+    of each plus four FP32 snapshots per segment otherwise; with the CPML also the memory
+    variables of its four fields (two sets of four each) and, checkpointed, U's and dU's memory
+    sets at every segment start."""
     d = _lib_module()
     g = _geom(d)
     pb_all = _problem(d, nt=200)
@@ -170,17 +171,19 @@ def test_second_order_workspace_sizing_and_validation():
     assert n_all >= 2 * 199 * field                                  # Lap(U^n), Lap(dU^n) for every step
     assert 2 * 20 * field + 10 * 4 * field <= n_ck < n_all
     assert d.second_order_workspace_size(pb_all, g, 3) > n_all
-    with pytest.raises(d.DufwiError) as e:
-        d.second_order_workspace_size(_problem(d, boundary="cpml"), g, 1)
-    assert e.value.status == d.ERR_UNSUPPORTED
+    c_all = d.second_order_workspace_size(_problem(d, nt=200, boundary="cpml", pml_alpha=6e6), g, 1)
+    c_ck = d.second_order_workspace_size(_problem(d, nt=200, ckpt_interval=20, boundary="cpml", pml_alpha=6e6), g, 1)
+    assert c_all >= n_all + 4 * 8 * field
+    assert c_ck >= n_ck + 4 * 8 * field + 10 * 8 * field
     with pytest.raises(d.DufwiError) as e:
         d.second_order_workspace_size(_problem(d, nt=0), g, 1)
     assert e.value.status == d.ERR_INVALID_ARG
 
 
 def test_second_order_entry_points_reject_bad_arguments_before_device_work():
-    """dufwi_second_order / dufwi_hvp: a missing output or input, or a CPML problem, is reported
-    by the return value before anything touches the device (dummy host pointers suffice)."""
+    """dufwi_second_order / dufwi_hvp: a missing output or input, or a workspace below the layout's
+    size (with the damping layer or the CPML), is reported by the return value before anything
+    touches the device (dummy host pointers suffice)."""
     d = _lib_module()
     g = _geom(d)
     arr, sh = g.c_structs()
@@ -202,10 +205,10 @@ def test_second_order_entry_points_reject_bad_arguments_before_device_work():
                          None, p, 1 << 30, None) == d.ERR_INVALID_ARG
     assert lib.dufwi_hvp(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, None, p, p, None,
                          None, p, 1 << 30, None) == d.ERR_INVALID_ARG
-    # the CPML has no Born step: unsupported, from the layout check
+    # the CPML layout (memory variables of every field) is larger still
     cp = _problem(d, boundary="cpml").c_struct()
     assert lib.dufwi_hvp(ctypes.byref(cp), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, p, p, None,
-                         None, p, 1 << 30, None) == d.ERR_UNSUPPORTED
+                         None, p, 64, None) == d.ERR_WORKSPACE
     # a workspace below the layout's size is rejected before the tables are copied
     assert lib.dufwi_hvp(ctypes.byref(pb), p, None, ctypes.byref(arr), p, ctypes.byref(sh), 1, p, p, p, None,
                          None, p, 64, None) == d.ERR_WORKSPACE

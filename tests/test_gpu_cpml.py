@@ -180,3 +180,76 @@ def test_cpml_unsupported_combinations(d):
     with pytest.raises(d.DufwiError) as e:                      # maps of different sizes
         d.simulate(_pb(d, wl), sos, w, geom, sizes=[(40, 40)])
     assert e.value.status == d.ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------------ second-order products
+SO_TOL = 1e-3     # FP32 second-order sums against an FP64 central difference (h = 0.05 m/s)
+
+
+def _so_case(seed, density):
+    # 124 x 60 keeps tiles that run the staggered kernel (x0 = 64, z0 = 32) beside the layer tiles
+    wl, rho = _case(seed, 124, 60, 300, 20, 2, density=density)
+    v = np.random.default_rng(seed).standard_normal(wl.sos_start.shape) * 5.0
+    return wl, (None if rho is None else rho[0]), v
+
+
+def _grad_o(wl, C, M_obs, rho):
+    p = _op(wl)
+    tix, tiz = wl.tx_nodes()
+    rix, riz = wl.rx_nodes()
+    return oracle.misfit_gradient(p, np.asarray(C, np.float64), tix, tiz, wl.wavelet.astype(np.float64), rix, riz,
+                                  np.asarray(M_obs, np.float64), rho=rho)[1]
+
+
+@pytest.mark.parametrize("ckpt,density", [(0, False), (40, False), (40, True)])
+def test_cpml_second_order_matches_oracle_differences(d, ckpt, density):
+    """dufwi_second_order with the CPML: the second-order term against the central difference of
+    the oracle's vector-Jacobian product with the CPML, the Born data against central differences
+    of the oracle traces, and the VJP against the oracle."""
+    wl, rho, v = _so_case(90, density)
+    C = wl.sos_start[0].astype(np.float64)
+    M_obs = _oracle_traces(wl, wl.sos_true[0], rho)
+    w = 2.0 * (_oracle_traces(wl, C, rho) - M_obs)
+    h = 0.05
+
+    def vjp(Cx):
+        return _grad_o(wl, Cx, _oracle_traces(wl, Cx, rho) - 0.5 * w, rho)
+
+    ref = (vjp(C + h * v[0]) - vjp(C - h * v[0])) / (2 * h)
+    pb = _pb(d, wl, ckpt_interval=ckpt)
+    geom = d.Geometry.from_workload(wl)
+    r = None if rho is None else _t(rho[None].astype(np.float32))
+    so, dcd, g = d.second_order(pb, _t(wl.sos_start), _t(wl.wavelet), geom, _t(w[None].astype(np.float32)),
+                                _t(v.astype(np.float32)), return_grad=True, check=True, density=r)
+    torch.cuda.synchronize()
+    assert rel_l2(so.cpu().numpy()[0], ref) <= SO_TOL
+    assert rel_l2(g.cpu().numpy()[0], vjp(C)) <= GRAD_TOL
+    jv_ref = (_oracle_traces(wl, C + h * v[0], rho) - _oracle_traces(wl, C - h * v[0], rho)) / (2 * h)
+    assert rel_l2(dcd.cpu().numpy()[0], jv_ref) <= 1e-4
+
+
+def test_cpml_exact_hvp_matches_oracle_and_is_symmetric(d):
+    """dufwi_hvp with the CPML against the central difference of the oracle gradient (M_obs fixed),
+    its misfit and gradient against dufwi_misfit_gradient, <u, H v> = <v, H u>, and the checkpointed
+    form (memory variables of U and dU snapshotted with the fields) against keeping every step."""
+    wl, rho, v = _so_case(91, False)
+    C = wl.sos_start[0].astype(np.float64)
+    M_obs = _oracle_traces(wl, wl.sos_true[0], rho)
+    h = 0.05
+    ref = (_grad_o(wl, C + h * v[0], M_obs, rho) - _grad_o(wl, C - h * v[0], M_obs, rho)) / (2 * h)
+    geom = d.Geometry.from_workload(wl)
+    sos, wav, obs, vv = _t(wl.sos_start), _t(wl.wavelet), _t(M_obs[None].astype(np.float32)), _t(v.astype(np.float32))
+    pb = _pb(d, wl, ckpt_interval=35)
+    hv, J, g = d.hvp(pb, sos, wav, geom, obs, vv, return_all=True, check=True)
+    hv0 = d.hvp(_pb(d, wl), sos, wav, geom, obs, vv, check=True)
+    J1, g1 = d.misfit_gradient(pb, sos, wav, geom, obs)
+    torch.cuda.synchronize()
+    assert rel_l2(hv.cpu().numpy()[0], ref) <= SO_TOL
+    assert torch.equal(hv, hv0)
+    assert torch.equal(J, J1)
+    assert rel_l2(g.cpu().numpy(), g1.cpu().numpy()) <= 1e-6
+    u = _t(np.random.default_rng(92).standard_normal(wl.sos_start.shape).astype(np.float32) * 5.0)
+    hu = d.hvp(pb, sos, wav, geom, obs, u)
+    a = float((u.double() * hv.double()).sum())
+    b = float((vv.double() * hu.double()).sum())
+    assert abs(a - b) <= 1e-4 * max(abs(a), abs(b))

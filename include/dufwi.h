@@ -136,11 +136,12 @@ typedef struct {
  *     is stretched by 1/s, s = 1 + d/(alpha + i omega), through one memory variable per
  *     difference and axis (recursive convolution; alpha = pml_alpha (1 - xi/L)); no damping
  *     term. Supported by dufwi_simulate, dufwi_simulate_noalloc, dufwi_misfit,
- *     dufwi_forward_save/dufwi_backward, dufwi_misfit_gradient, dufwi_second_order and dufwi_hvp,
+ *     dufwi_forward_save/dufwi_backward, dufwi_misfit_gradient, dufwi_second_order, dufwi_hvp,
  *     with or without a density map and with any ckpt_interval: a checkpoint stores the four
  *     memory fields read at its step in FP32 beside (U^t, U^{t-1}) (and the Born field's beside
- *     dU in the second-order calls), and each adjoint field keeps its own memory variables; not
- *     by the *_sized calls or dufwi_jvp (DUFWI_ERR_UNSUPPORTED). */
+ *     dU in the second-order calls), and each adjoint field keeps its own memory variables;
+ *     dufwi_jvp too (the Born field with its own memory variables). Not by the *_sized calls
+ *     (DUFWI_ERR_UNSUPPORTED). */
 #define DUFWI_BOUNDARY_DAMPING 0
 #define DUFWI_BOUNDARY_CPML 1
 
@@ -258,7 +259,8 @@ int dufwi_backward(const dufwi_problem *pb, const float *sos, const float *densi
  * dkappa' = 2 kappa' dC / C, with dC extended into the absorbing layer like C. With
  * dufwi_backward this gives Gauss-Newton Hessian-vector products of the misfit,
  * H v = 2 J^T (J v). With a density map both fields use the variable-density operator and
- * Lap is that operator; DUFWI_BOUNDARY_CPML gives DUFWI_ERR_UNSUPPORTED.
+ * Lap is that operator; with DUFWI_BOUNDARY_CPML Lap is the stretched operator G of the CPML
+ * step and dU has memory variables of its own.
  *   dsos   [n_maps][nz][nx] float, device
  *   dcd    [n_maps][n_tx][nt][n_rx] float, device, output
  *   cd     NULL or [n_maps][n_tx][nt][n_rx] float, device, output (the background data)

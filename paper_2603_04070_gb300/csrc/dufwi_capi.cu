@@ -284,7 +284,6 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
     L->o_bx = take((size_t)n_maps * L->slice * sizeof(float));     // buoyancies (density maps only)
     L->o_bz = take((size_t)n_maps * L->slice * sizeof(float));
     if (pb->boundary == DUFWI_BOUNDARY_CPML) {
-        if (kind == kLayoutJvp) return DUFWI_ERR_UNSUPPORTED;   // the Born call has no CPML step
         for (int i = 0; i < 8; ++i) L->o_cm[i] = take((size_t)L->S * L->slice * sizeof(float));
         L->o_cpml = take(sizeof(float) * 4 * (size_t)(L->nxp + L->nzp));
         if (gradient) {
@@ -292,6 +291,10 @@ int make_layout(const dufwi_problem *pb, const dufwi_shots *sh, int n_maps, int 
             // a recomputed segment restarts from (U^t, U^{t-1}) and the four memory fields read at step t
             if (L->n_seg > 1 && L->n_snap > 0)
                 L->o_snapm = take((size_t)L->n_snap * 4 * L->S * L->slice * sizeof(float));
+        }
+        if (kind == kLayoutJvp) {   // the Born field's memory variables, and G(dU^n) (written, not used)
+            for (int i = 0; i < 8; ++i) L->o_cmb[i] = take((size_t)L->S * L->slice * sizeof(float));
+            L->o_hist2 = take((size_t)L->S * L->slice * sizeof(float));
         }
         if (kind == kLayoutSecond) {   // memory variables of mu, dU and dmu; U's and dU's at segment starts
             for (int i = 0; i < 8; ++i) {
@@ -587,8 +590,6 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.st = static_cast<cudaStream_t>(stream);
     c.cpml = c.pb->boundary == DUFWI_BOUNDARY_CPML;
     c.vd = density != nullptr || c.cpml;        // the CPML runs on the staggered operator
-    // the Born call has no CPML step (the second-order calls run their own kinds on the layer tiles)
-    if (c.cpml && c.jvp) return DUFWI_ERR_UNSUPPORTED;
     if (c.cpml && c.sizes) return DUFWI_ERR_UNSUPPORTED;
     c.comp = L.comp;
     if (c.comp && (c.cpml || c.jvp || c.so)) return DUFWI_ERR_UNSUPPORTED;
@@ -781,16 +782,19 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
                 tensor_map(&c.cm_adj[k].mem_nx, anx, L, L.S, 0, kVBoxX, kVTileZ) ||
                 tensor_map(&c.cm_adj[k].mem_nz, anz, L, L.S, 0, kTileX, kVBoxZ))
                 return DUFWI_ERR_CUDA;
-            if (c.so) {   // the Born field's sets (forward layout) and dmu's (adjoint layout)
+            if (c.so || c.jvp) {   // the Born field's sets (forward layout)
                 const float *bhx = c.at<float>(L.o_cmb[4 * k]), *bhz = c.at<float>(L.o_cmb[4 * k + 1]);
                 const float *bnx = c.at<float>(L.o_cmb[4 * k + 2]), *bnz = c.at<float>(L.o_cmb[4 * k + 3]);
-                const float *dhx = c.at<float>(L.o_cmd[4 * k]), *dhz = c.at<float>(L.o_cmd[4 * k + 1]);
-                const float *dnx = c.at<float>(L.o_cmd[4 * k + 2]), *dnz = c.at<float>(L.o_cmd[4 * k + 3]);
                 if (tensor_map(&c.cm_born[k].mem_hx, bhx, L, L.S, 0, kVFxX, kVTileZ) ||
                     tensor_map(&c.cm_born[k].mem_hz, bhz, L, L.S, 0, kTileX, kVFzZ) ||
                     tensor_map(&c.cm_born[k].mem_nx, bnx, L, L.S, 0, kTileX, kVTileZ) ||
-                    tensor_map(&c.cm_born[k].mem_nz, bnz, L, L.S, 0, kTileX, kVTileZ) ||
-                    tensor_map(&c.cm_dadj[k].mem_hx, dhx, L, L.S, 0, kVFxX, kVTileZ) ||
+                    tensor_map(&c.cm_born[k].mem_nz, bnz, L, L.S, 0, kTileX, kVTileZ))
+                    return DUFWI_ERR_CUDA;
+            }
+            if (c.so) {   // dmu's sets (adjoint layout)
+                const float *dhx = c.at<float>(L.o_cmd[4 * k]), *dhz = c.at<float>(L.o_cmd[4 * k + 1]);
+                const float *dnx = c.at<float>(L.o_cmd[4 * k + 2]), *dnz = c.at<float>(L.o_cmd[4 * k + 3]);
+                if (tensor_map(&c.cm_dadj[k].mem_hx, dhx, L, L.S, 0, kVFxX, kVTileZ) ||
                     tensor_map(&c.cm_dadj[k].mem_hz, dhz, L, L.S, 0, kTileX, kVFzZ) ||
                     tensor_map(&c.cm_dadj[k].mem_nx, dnx, L, L.S, 0, kVBoxX, kVTileZ) ||
                     tensor_map(&c.cm_dadj[k].mem_nz, dnz, L, L.S, 0, kTileX, kVBoxZ))
@@ -1607,6 +1611,12 @@ int misfit_gradient_impl(const dufwi_problem *pb, const dufwi_map_sizes *sizes, 
 }  // namespace
 }  // namespace dufwi
 
+namespace dufwi {
+namespace {
+int so_step(Ctx &c, Ring &r, int kind, StepParams p, const SoParams &q, long long &nl);
+}  // namespace
+}  // namespace dufwi
+
 extern "C" {
 
 int dufwi_misfit(const dufwi_problem *pb, const float *sos, const float *density, const dufwi_array *arr,
@@ -1716,6 +1726,13 @@ int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, c
     br.map = c.mmap;
     fr.cur = br.cur = 0;
     fr.prv = br.prv = 1;
+    if (c.cpml) {   // U's and dU's memory variables start at zero
+        for (int i = 0; i < 8; ++i) {
+            CK(cudaMemsetAsync(c.at<float>(L.o_cm[i]), 0, field, c.st));
+            CK(cudaMemsetAsync(c.at<float>(L.o_cmb[i]), 0, field, c.st));
+        }
+        c.mem_par = c.bmem_par = 0;
+    }
     float *bg_cd = cd ? cd : c.at<float>(L.o_cd);
     StepParams pf = c.base, pb_ = c.base;
     pf.inj_node = c.at<int>(L.o_tx);
@@ -1735,7 +1752,15 @@ int dufwi_jvp(const dufwi_problem *pb, const float *sos, const float *density, c
         rc = one_step(c, fr, kFwdSampleHist, pf, nl);
         if (rc) break;
         pb_.step = n;
-        rc = one_step(c, br, kBorn, pb_, nl);
+        if (c.cpml) {   // the Born kind of the second-order calls (its G(dU^n) output is not used)
+            SoParams qb;
+            memset(&qb, 0, sizeof(qb));
+            qb.lap_out = c.at<float>(L.o_hist2);
+            qb.h1_slot = 0;
+            rc = so_step(c, br, kSoBorn, pb_, qb, nl);
+        } else {
+            rc = one_step(c, br, kBorn, pb_, nl);
+        }
     }
     const int rj = join_groups(c);
     if (rc || rj) return rc ? rc : rj;

@@ -174,9 +174,6 @@ def test_cpml_unsupported_combinations(d):
     wl, _ = _case(23, 40, 40, 60, 8, 1)
     geom = d.Geometry.from_workload(wl)
     sos, w = _t(wl.sos_true), _t(wl.wavelet)
-    with pytest.raises(d.DufwiError) as e:                      # Born step
-        d.jvp(_pb(d, wl), sos, w, geom, torch.zeros_like(sos))
-    assert e.value.status == d.ERR_UNSUPPORTED
     with pytest.raises(d.DufwiError) as e:                      # maps of different sizes
         d.simulate(_pb(d, wl), sos, w, geom, sizes=[(40, 40)])
     assert e.value.status == d.ERR_UNSUPPORTED
@@ -253,3 +250,28 @@ def test_cpml_exact_hvp_matches_oracle_and_is_symmetric(d):
     a = float((u.double() * hv.double()).sum())
     b = float((vv.double() * hu.double()).sum())
     assert abs(a - b) <= 1e-4 * max(abs(a), abs(b))
+
+
+@pytest.mark.parametrize("density", [False, True])
+def test_cpml_born_jvp_matches_oracle_differences(d, density):
+    """dufwi_jvp with the CPML (the Born field with its own memory variables, through the CPML
+    kernel's Born kind on the layer tiles) against central differences of the oracle traces, and
+    its background data against the oracle; the JVP and the VJP are transposes."""
+    wl, rho, v = _so_case(93, density)
+    C = wl.sos_true[0].astype(np.float64)
+    h = 0.05
+    ref = (_oracle_traces(wl, C + h * v[0], rho) - _oracle_traces(wl, C - h * v[0], rho)) / (2 * h)
+    pb = _pb(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    r = None if rho is None else _t(rho[None].astype(np.float32))
+    sos, wav, vv = _t(wl.sos_true), _t(wl.wavelet), _t(v.astype(np.float32))
+    dcd, cd = d.jvp(pb, sos, wav, geom, vv, density=r, return_cd=True, check=True)
+    torch.cuda.synchronize()
+    assert rel_l2(dcd.cpu().numpy()[0], ref) <= 1e-4
+    assert rel_l2(cd.cpu().numpy()[0], _oracle_traces(wl, C, rho)) <= TRACE_TOL
+    q = torch.randn(dcd.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(4)) * 1e-9
+    _, ws = d.forward_save(pb, sos, wav, geom, density=r)
+    JTq = d.backward(pb, sos, wav, geom, q, ws, density=r)
+    lhs = float((dcd.double() * q.double()).sum())
+    rhs = float((vv.double() * JTq.double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)

@@ -443,7 +443,8 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     on a host thread's first grouped call on a device and kept until the thread exits; while the
  *     caller's stream is being captured into a CUDA graph they are not created, so a call captured
  *     before any uncaptured call on that thread and device runs as one group (make one uncaptured
- *     call first to capture the grouped form). Not used with the two-step, persistent or
+ *     call first to capture the grouped form). Creating them is a stream and event creation: make
+ *     a thread's first call outside another thread's global-mode stream capture. Not used with the two-step, persistent or
  *     multi-tile forms, or by dufwi_simulate_noalloc.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),

@@ -297,6 +297,7 @@ def run_reference(args):
     args.tile_z_used = 32
     args.two_step_used = 0
     args.persistent_used = 0
+    args.groups_used = 2
     rank, world, _ = dist_env()
     if rank != 0:
         return

@@ -32,7 +32,7 @@ def test_reference_arm_prints_one_complete_json_line(monkeypatch):
     from paper_2603_04070_gb300 import inputs
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     args = bench.parse()
-    args.tile_z_used, args.two_step_used, args.persistent_used = 32, 0, 0
+    args.tile_z_used, args.two_step_used, args.persistent_used, args.groups_used = 32, 0, 0, 2
     wl = inputs.make_workload(args.workload, seed=0, nt=args.nt, n_tx=args.n_tx)
     assert d["config"] == json.loads(json.dumps(bench.workload_config(wl, args)))
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
@@ -54,3 +54,26 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_bench_counts_the_shot_groups_the_library_uses():
+    """The benchmark's roofline divides a sweep's time by its steps through the number of shot
+    groups a call uses: the option's value capped by the shots, and one group for the forms that
+    walk every shot in one launch."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2603_04070_gb300 import dufwi
+    opts = (dufwi.OPT_SHOT_GROUPS, dufwi.OPT_TWO_STEP, dufwi.OPT_PERSISTENT, dufwi.OPT_MULTI_TILE)
+    saved = [dufwi.get_option(o) for o in opts]
+    try:
+        dufwi.set_option(dufwi.OPT_SHOT_GROUPS, 2)
+        assert bench.effective_groups(dufwi, 16) == 2 and bench.effective_groups(dufwi, 1) == 1
+        dufwi.set_option(dufwi.OPT_SHOT_GROUPS, 4)
+        assert bench.effective_groups(dufwi, 3) == 3
+        for o in opts[1:]:
+            dufwi.set_option(o, 1)
+            assert bench.effective_groups(dufwi, 16) == 1
+            dufwi.set_option(o, 0)
+    finally:
+        for o, v in zip(opts, saved):
+            dufwi.set_option(o, v)

@@ -60,6 +60,8 @@ def parse():
                     help="1: multi-tile one-step kernel (co-resident CTAs, two-stage TMA loads), 0: one tile per CTA")
     ap.add_argument("--shot-groups", type=int, default=None, choices=[1, 2, 3, 4],
                     help="shot groups stepped on concurrent streams (default: the autotuner's choice)")
+    ap.add_argument("--min-ctas", type=int, default=None, choices=[4, 5, 6],
+                    help="register-cap variant of the one-step kernel (default: the autotuner's choice)")
     ap.add_argument("--forward-precision", default="fp32", choices=["fp32", "compensated"],
                     help="forward steps in FP32, or compensated (hi + lo planes, error-free arithmetic)")
     ap.add_argument("--boundary", default="damping", choices=["damping", "cpml"],
@@ -336,6 +338,7 @@ def workload_config(wl, args):
             "two_step": args.two_step_used, "persistent": getattr(args, "persistent_used", 0),
             "multi_tile": getattr(args, "multi_tile_used", 0),
             "shot_groups": getattr(args, "groups_used", 1),
+            "min_ctas_per_sm": getattr(args, "min_ctas_used", 5),
             "forward_precision": getattr(args, "forward_precision", "fp32"),
             "density": ("variable: water-like background + smooth field + 1-3 rods of 1050-1900 kg/m^3, "
                         "staggered operator" if getattr(args, "density", False) else "constant"),
@@ -364,6 +367,8 @@ def run_ours(args):
         dufwi.set_option(dufwi.OPT_MULTI_TILE, args.multi_tile)
     if args.shot_groups is not None:
         dufwi.set_option(dufwi.OPT_SHOT_GROUPS, args.shot_groups)
+    if args.min_ctas is not None:
+        dufwi.set_option(dufwi.OPT_MIN_CTAS, args.min_ctas)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
@@ -393,7 +398,7 @@ def run_ours(args):
     # launch options: tuned on a short gradient probe unless forced on the command line
     tuned = None
     forced = any(v is not None for v in (args.tile_z, args.two_step, args.persistent, args.multi_tile,
-                                         args.shot_groups))
+                                         args.shot_groups, args.min_ctas))
     if not forced and not args.no_autotune and not (args.density or args.boundary == "cpml") \
             and args.forward_precision == "fp32":
         from paper_2603_04070_gb300 import autotune
@@ -408,6 +413,7 @@ def run_ours(args):
     args.persistent_used = dufwi.get_option(dufwi.OPT_PERSISTENT)
     args.multi_tile_used = dufwi.get_option(dufwi.OPT_MULTI_TILE)
     args.groups_used = effective_groups(dufwi, wl.n_maps * wl.n_tx)
+    args.min_ctas_used = dufwi.get_option(dufwi.OPT_MIN_CTAS)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -656,7 +662,9 @@ def measure_uneven_batch(dufwi, inputs, autotune, dev, nt, steps, warmup):
     saved = {k: dufwi.get_option(o) for k, o in (("tile_z", dufwi.OPT_TILE_Z), ("two_step", dufwi.OPT_TWO_STEP),
                                                  ("persistent", dufwi.OPT_PERSISTENT),
                                                  ("multi_tile", dufwi.OPT_MULTI_TILE),
-                                                 ("early", dufwi.OPT_EARLY_LOADS))}
+                                                 ("early", dufwi.OPT_EARLY_LOADS),
+                                                 ("groups", dufwi.OPT_SHOT_GROUPS),
+                                                 ("min_ctas", dufwi.OPT_MIN_CTAS))}
     wl, sizes = inputs.uneven_batch(seed=0, nt=nt)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
     geom = dufwi.Geometry.from_workload(wl)
@@ -774,7 +782,8 @@ def measure_linear_disk(dufwi, inputs, dev, flush, stream):
                                                  ("persistent", dufwi.OPT_PERSISTENT),
                                                  ("multi_tile", dufwi.OPT_MULTI_TILE),
                                                  ("early", dufwi.OPT_EARLY_LOADS),
-                                                 ("groups", dufwi.OPT_SHOT_GROUPS))}
+                                                 ("groups", dufwi.OPT_SHOT_GROUPS),
+                                                 ("min_ctas", dufwi.OPT_MIN_CTAS))}
     try:
         return _measure_linear_disk(dufwi, inputs, autotune, dev, flush, stream)
     finally:

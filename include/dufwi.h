@@ -446,6 +446,10 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     call first to capture the grouped form). Creating them is a stream and event creation: make
  *     a thread's first call outside another thread's global-mode stream capture. Not used with the two-step, persistent or
  *     multi-tile forms, or by dufwi_simulate_noalloc.
+ *   DUFWI_OPT_MIN_CTAS: 4, 5 (default) or 6 resident CTAs per SM that the one-step kernel's
+ *     register allocation is compiled for (96 registers at 5; 128 at 4; 80 at 6, with a few
+ *     spills), for the 8th-order stencil with 64 x 32 tiles; other orders and tile heights use
+ *     the build default. Same results for every value.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device
@@ -459,6 +463,7 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
 #define DUFWI_OPT_MULTI_TILE 6
 #define DUFWI_OPT_EARLY_LOADS 7
 #define DUFWI_OPT_SHOT_GROUPS 8
+#define DUFWI_OPT_MIN_CTAS 9
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

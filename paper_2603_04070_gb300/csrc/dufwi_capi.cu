@@ -128,6 +128,7 @@ int g_persistent = 0;   // DUFWI_OPT_PERSISTENT: one cooperative launch per swee
 int g_multi_tile = 0;   // DUFWI_OPT_MULTI_TILE: the multi-tile one-step kernel (64 x 32 tiles)
 int g_early = 1;        // DUFWI_OPT_EARLY_LOADS: operands not written by the last two launches requested early
 int g_shot_groups = 2;  // DUFWI_OPT_SHOT_GROUPS: shot groups stepped on concurrent streams
+int g_min_ctas = 5;     // DUFWI_OPT_MIN_CTAS: register-cap variant of the one-step kernel (4, 5 or 6)
 
 // Streams and events of the shot groups, per host thread and device: created on first use and
 // kept for the thread's lifetime. Calls on different host threads never share an event, so their
@@ -854,6 +855,7 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     p.n_rxe = L.n_rxe;
     p.shot0 = 0;
     p.n_shots = L.S;
+    p.min_ctas = g_min_ctas == 5 ? 0 : g_min_ctas;
     return DUFWI_OK;
 }
 
@@ -1251,6 +1253,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value < 1 || value > kMaxGroups) return DUFWI_ERR_INVALID_ARG;
         g_shot_groups = value;
         return DUFWI_OK;
+    case DUFWI_OPT_MIN_CTAS:
+        if (value < 4 || value > 6) return DUFWI_ERR_INVALID_ARG;
+        g_min_ctas = value;
+        return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL:
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_test_stall = value;
@@ -1268,6 +1274,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     case DUFWI_OPT_MULTI_TILE: *value = g_multi_tile; return DUFWI_OK;
     case DUFWI_OPT_EARLY_LOADS: *value = g_early; return DUFWI_OK;
     case DUFWI_OPT_SHOT_GROUPS: *value = g_shot_groups; return DUFWI_OK;
+    case DUFWI_OPT_MIN_CTAS: *value = g_min_ctas; return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL: *value = g_test_stall.load(); return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;

@@ -173,6 +173,7 @@ struct StepParams {
     int tile_class;          // CPML split: 0 every tile; 1 only tiles whose region grown by 8 cells
                              // lies inside the physical grid (no memory variables); 2 only the others
     int shot0, n_shots;      // this launch covers shots shot0 .. shot0 + n_shots - 1 (grid.z = n_shots)
+    int min_ctas;            // one-step kernel, 8th order, 64 x 32 tiles: register-cap variant (0, 4 or 6)
 };
 
 // Compensated forward step (comp_step_kernel, 64 x 32 tiles): the field as hi + lo planes of FP32.

@@ -220,8 +220,11 @@ __device__ __forceinline__ bool wait_tile(uint64_t *bar, const StepParams &p, in
 // box of U^n and of the 64 x TZ tiles of U^{n-1} and kappa' (and, in the adjoint, of
 // Lap(U^{m-1}) and of the running imaging sum). Many small CTAs stay resident per SM, so the
 // loads of some overlap the arithmetic of others.
-template <int R, int MODE, int TZ>
-__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta, TZ == 32 ? DUFWI_STEP_MIN_CTAS_128 : 4)
+// MINB: resident CTAs per SM asked of the register allocator (0: the build default above; the
+// 64 x 32 form of the 8th-order stencil is also compiled for 4 and 6, a launch option).
+template <int R, int MODE, int TZ, int MINB = 0>
+__global__ void __launch_bounds__(TileLayout<MODE, TZ>::kThreadsPerCta,
+                                  MINB ? MINB : (TZ == 32 ? DUFWI_STEP_MIN_CTAS_128 : 4))
 step_kernel(const __grid_constant__ StepMaps tm, const StepParams p)
 {
     using TL = TileLayout<MODE, TZ>;
@@ -2251,12 +2254,12 @@ __global__ void snap_load_kernel(float *cur, float *prev, const T *su, const T *
 // ---- launchers ------------------------------------------------------------------------------
 
 // <one-step kernel source>
-template <int R, int MODE, int TZ>
+template <int R, int MODE, int TZ, int MINB = 0>
 static cudaError_t launch_step_rmt(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
     using TL = TileLayout<MODE, TZ>;
     static DeviceCache dc;   // shared-memory attributes, set once per device
-    cudaError_t e = configure_kernel(step_kernel<R, MODE, TZ>, TL::kBytes, dc);
+    cudaError_t e = configure_kernel(step_kernel<R, MODE, TZ, MINB>, TL::kBytes, dc);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nxp + kTileX - 1) / kTileX, (p.nzp + TZ - 1) / TZ, p.n_shots);
@@ -2268,12 +2271,16 @@ static cudaError_t launch_step_rmt(const StepMaps &tm, const StepParams &p, cuda
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, step_kernel<R, MODE, TZ>, tm, p);
+    return cudaLaunchKernelEx(&cfg, step_kernel<R, MODE, TZ, MINB>, tm, p);
 }
 
 template <int R, int MODE>
 static cudaError_t launch_step_rm(const StepMaps &tm, const StepParams &p, cudaStream_t st)
 {
+    if constexpr (R == 4) {   // register-cap variants of the 64 x 32 form (p.min_ctas; 0 = default)
+        if (p.tile_z == 32 && p.min_ctas == 4) return launch_step_rmt<R, MODE, 32, 4>(tm, p, st);
+        if (p.tile_z == 32 && p.min_ctas == 6) return launch_step_rmt<R, MODE, 32, 6>(tm, p, st);
+    }
     switch (p.tile_z) {
     case 32: return launch_step_rmt<R, MODE, 32>(tm, p, st);
     case 64: return launch_step_rmt<R, MODE, 64>(tm, p, st);

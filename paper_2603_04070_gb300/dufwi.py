@@ -35,6 +35,7 @@ OPT_TEST_STALL = 5
 OPT_MULTI_TILE = 6
 OPT_EARLY_LOADS = 7
 OPT_SHOT_GROUPS = 8
+OPT_MIN_CTAS = 9
 
 
 class DufwiError(RuntimeError):

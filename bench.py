@@ -62,6 +62,8 @@ def parse():
                     help="shot groups stepped on concurrent streams (default: the autotuner's choice)")
     ap.add_argument("--min-ctas", type=int, default=None, choices=[4, 5, 6],
                     help="register-cap variant of the one-step kernel (default: the autotuner's choice)")
+    ap.add_argument("--cluster", type=int, default=None, choices=[0, 1],
+                    help="1: cluster-resident sweeps for grids that fit (default: the autotuner's choice)")
     ap.add_argument("--forward-precision", default="fp32", choices=["fp32", "compensated"],
                     help="forward steps in FP32, or compensated (hi + lo planes, error-free arithmetic)")
     ap.add_argument("--boundary", default="damping", choices=["damping", "cpml"],
@@ -339,6 +341,7 @@ def workload_config(wl, args):
             "multi_tile": getattr(args, "multi_tile_used", 0),
             "shot_groups": getattr(args, "groups_used", 1),
             "min_ctas_per_sm": getattr(args, "min_ctas_used", 5),
+            "cluster_sweeps": getattr(args, "cluster_used", 0),
             "forward_precision": getattr(args, "forward_precision", "fp32"),
             "density": ("variable: water-like background + smooth field + 1-3 rods of 1050-1900 kg/m^3, "
                         "staggered operator" if getattr(args, "density", False) else "constant"),
@@ -369,6 +372,8 @@ def run_ours(args):
         dufwi.set_option(dufwi.OPT_SHOT_GROUPS, args.shot_groups)
     if args.min_ctas is not None:
         dufwi.set_option(dufwi.OPT_MIN_CTAS, args.min_ctas)
+    if args.cluster is not None:
+        dufwi.set_option(dufwi.OPT_CLUSTER, args.cluster)
     wl = inputs.make_workload(args.workload, seed=rank, nt=args.nt, n_tx=args.n_tx)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=wl.nt, pml_cells=wl.pml, pml_R=wl.pml_R,
                        pml_cref=wl.pml_cref, fd_order=wl.fd_order, snapshot_dtype=args.snapshot,
@@ -398,7 +403,7 @@ def run_ours(args):
     # launch options: tuned on a short gradient probe unless forced on the command line
     tuned = None
     forced = any(v is not None for v in (args.tile_z, args.two_step, args.persistent, args.multi_tile,
-                                         args.shot_groups, args.min_ctas))
+                                         args.shot_groups, args.min_ctas, args.cluster))
     if not forced and not args.no_autotune and not (args.density or args.boundary == "cpml") \
             and args.forward_precision == "fp32":
         from paper_2603_04070_gb300 import autotune
@@ -414,6 +419,7 @@ def run_ours(args):
     args.multi_tile_used = dufwi.get_option(dufwi.OPT_MULTI_TILE)
     args.groups_used = effective_groups(dufwi, wl.n_maps * wl.n_tx)
     args.min_ctas_used = dufwi.get_option(dufwi.OPT_MIN_CTAS)
+    args.cluster_used = dufwi.get_option(dufwi.OPT_CLUSTER)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -664,7 +670,8 @@ def measure_uneven_batch(dufwi, inputs, autotune, dev, nt, steps, warmup):
                                                  ("multi_tile", dufwi.OPT_MULTI_TILE),
                                                  ("early", dufwi.OPT_EARLY_LOADS),
                                                  ("groups", dufwi.OPT_SHOT_GROUPS),
-                                                 ("min_ctas", dufwi.OPT_MIN_CTAS))}
+                                                 ("min_ctas", dufwi.OPT_MIN_CTAS),
+                                                 ("cluster", dufwi.OPT_CLUSTER))}
     wl, sizes = inputs.uneven_batch(seed=0, nt=nt)
     pb = dufwi.Problem(nx=wl.nx, nz=wl.nz, dx=wl.dx, dt=wl.dt, nt=nt, c_max=wl.c_max)
     geom = dufwi.Geometry.from_workload(wl)
@@ -783,7 +790,8 @@ def measure_linear_disk(dufwi, inputs, dev, flush, stream):
                                                  ("multi_tile", dufwi.OPT_MULTI_TILE),
                                                  ("early", dufwi.OPT_EARLY_LOADS),
                                                  ("groups", dufwi.OPT_SHOT_GROUPS),
-                                                 ("min_ctas", dufwi.OPT_MIN_CTAS))}
+                                                 ("min_ctas", dufwi.OPT_MIN_CTAS),
+                                                 ("cluster", dufwi.OPT_CLUSTER))}
     try:
         return _measure_linear_disk(dufwi, inputs, autotune, dev, flush, stream)
     finally:

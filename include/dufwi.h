@@ -450,6 +450,16 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
  *     register allocation is compiled for (96 registers at 5; 128 at 4; 80 at 6, with a few
  *     spills), for the 8th-order stencil with 64 x 32 tiles; other orders and tile heights use
  *     the build default. Same results for every value.
+ *   DUFWI_OPT_CLUSTER: 1 runs each range of time steps (a sweep segment) of the compact
+ *     stencil as one launch of one thread-block cluster of 8 CTAs per shot when the padded grid
+ *     fits the cluster's shared memory (about 300 x 250 padded cells at most; each CTA holds a
+ *     strip of rows and exchanges 4 halo rows per step with its neighbours through distributed
+ *     shared memory, one cluster barrier per step), instead of one launch per step;
+ *     bit-identical results. On GB300 it measured slower than one launch per step with
+ *     programmatic dependent launch on the 128 x 128 and 188 x 188 workloads; it is an
+ *     autotuner candidate. Not used
+ *     with a density map, the CPML, the compensated steps, the Born and second-order calls, the
+ *     *_sized calls or the two-step, persistent and multi-tile forms; 0 (default) otherwise.
  *   DUFWI_OPT_TEST_STALL: test hook for the bounded waits. 1 makes the next persistent sweep
  *     wait on a tile counter that nothing sets; that wait gives up after its time limit (2 s),
  *     the launch ends early with DUFWI_ERR_TIMEOUT in the workspace status word, and the device
@@ -464,6 +474,7 @@ int dufwi_profile_read(double *ms, int64_t *launches, int reset);
 #define DUFWI_OPT_EARLY_LOADS 7
 #define DUFWI_OPT_SHOT_GROUPS 8
 #define DUFWI_OPT_MIN_CTAS 9
+#define DUFWI_OPT_CLUSTER 10
 int dufwi_set_option(int32_t option, int32_t value);
 int dufwi_get_option(int32_t option, int32_t *value);
 

@@ -4,9 +4,11 @@ Launch options: the tile height of the one-step kernel (64 x 32 or 64 x 64), its
 (co-resident CTAs walking the tiles with two-stage TMA loads), early requests of the operands the
 previous two launches did not write (on or off), the number of shot groups stepped on concurrent
 streams (1, 2 or 4), the register-cap variant of the one-step kernel (compiled for 4, 5 or 6
-resident CTAs per SM), two steps per launch, and one persistent launch per sweep segment. For a given problem shape the tuner times a short forward simulation (or, for
-callers whose work is gradients, a short misfit gradient) with each candidate, on the caller's
-device, and keeps the fastest. Results are cached per (GPU name, grid, shots, stencil order): in
+resident CTAs per SM), two steps per launch, one persistent launch per sweep segment, and, for
+grids that fit, one launch of a thread-block cluster per shot and sweep segment. For a given
+problem shape the tuner times a short forward simulation (or, for callers whose work is
+gradients, a short misfit gradient) with each candidate, on the caller's device, and keeps the
+fastest. Results are cached per (GPU name, grid, shots, stencil order): in
 memory, and optionally in a JSON file. The options change speed only: every candidate produces
 bit-identical results (tests check each pair against the default).
 
@@ -25,13 +27,15 @@ import torch
 
 from . import dufwi
 
-_BASE = {"tile_z": 32, "two_step": 0, "persistent": 0, "multi_tile": 0, "early": 1, "groups": 2, "min_ctas": 5}
+_BASE = {"tile_z": 32, "two_step": 0, "persistent": 0, "multi_tile": 0, "early": 1, "groups": 2, "min_ctas": 5,
+         "cluster": 0}
 CANDIDATES = (
     dict(_BASE),
     {**_BASE, "groups": 1},
     {**_BASE, "groups": 4},
     {**_BASE, "min_ctas": 4},
     {**_BASE, "min_ctas": 6},
+    {**_BASE, "cluster": 1},
     {**_BASE, "early": 0},
     {**_BASE, "tile_z": 64},
     {**_BASE, "tile_z": 64, "groups": 1},
@@ -60,6 +64,7 @@ def apply(options: dict):
     dufwi.set_option(dufwi.OPT_EARLY_LOADS, int(options.get("early", 1)))
     dufwi.set_option(dufwi.OPT_SHOT_GROUPS, int(options.get("groups", 2)))
     dufwi.set_option(dufwi.OPT_MIN_CTAS, int(options.get("min_ctas", 5)))
+    dufwi.set_option(dufwi.OPT_CLUSTER, int(options.get("cluster", 0)))
 
 
 def kept_segments_for_budget(problem: dufwi.Problem, geom: dufwi.Geometry, n_maps: int, budget_bytes: int) -> int:

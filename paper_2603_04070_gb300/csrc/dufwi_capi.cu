@@ -129,6 +129,7 @@ int g_multi_tile = 0;   // DUFWI_OPT_MULTI_TILE: the multi-tile one-step kernel 
 int g_early = 1;        // DUFWI_OPT_EARLY_LOADS: operands not written by the last two launches requested early
 int g_shot_groups = 2;  // DUFWI_OPT_SHOT_GROUPS: shot groups stepped on concurrent streams
 int g_min_ctas = 5;     // DUFWI_OPT_MIN_CTAS: register-cap variant of the one-step kernel (4, 5 or 6)
+int g_cluster = 0;      // DUFWI_OPT_CLUSTER: cluster-resident sweeps for grids that fit
 
 // Streams and events of the shot groups, per host thread and device: created on first use and
 // kept for the thread's lifetime. Calls on different host threads never share an event, so their
@@ -498,6 +499,8 @@ struct Ctx {
     bool so = false;                          // second-order call (dufwi_second_order)
     bool comp = false;                        // compensated forward steps (hi + lo planes)
     bool multi_tile = false;                  // multi-tile one-step kernel (two-stage TMA pipeline)
+    bool cluster = false;                     // cluster-resident sweeps (one launch per range and group)
+    int cl_H = 0, cl_lpitch = 0;              // their strip height and shared-memory row stride
     float *cd_lo = nullptr;                   // compensated: low parts of the traces of the current sweep
     // shot groups: the step launches of a range go to one stream per group, each covering shots
     // g_s0[g] .. g_s0[g] + g_n[g] - 1, between a fork from and a join into the caller's stream
@@ -600,6 +603,8 @@ int common_setup(Ctx &c, const float *sos, const float *density, const dufwi_arr
     c.mem_par = 0;
     c.multi_tile = g_multi_tile != 0 && !c.two_step && !c.persistent && !c.vd && !c.so && !c.comp;
     c.tz = (c.vd || c.persistent || c.so || c.comp || c.multi_tile) ? 32 : g_tile_z;
+    c.cluster = g_cluster != 0 && !c.vd && !c.cpml && !c.comp && !c.so && !c.jvp && !c.sizes && !c.two_step &&
+                !c.persistent && !c.multi_tile && cluster_smem_bytes(L.nxp, L.nzp, &c.cl_H, &c.cl_lpitch) > 0;
     // shot groups for the one-launch-per-step forms (the persistent, two-step and multi-tile forms
     // walk all shots in one launch)
     c.groups = 1;
@@ -1079,6 +1084,35 @@ int sweep(Ctx &c, Ring &rg, int mode, StepParams p, int n0, int n, float *hist0,
     return DUFWI_OK;
 }
 
+// A range of k steps in cluster-resident launches (one per shot group), forward from n0 or
+// adjoint from m0 = n0 downwards. The ring ends as k one-step launches would leave it: the last
+// field in buf[cur] and the one before in buf[prv] (cur and prv swapped when k is odd).
+int cluster_range(Ctx &c, Ring &rg, int mode, StepParams p, int n0, int k, float *hist0, long long &nl)
+{
+    if (k <= 0) return DUFWI_OK;
+    ClusterParams cp;
+    memset(&cp, 0, sizeof(cp));
+    cp.cur = rg.buf[rg.cur];
+    cp.prv = rg.buf[rg.prv];
+    const bool odd = k & 1;
+    cp.out_cur = rg.buf[odd ? rg.prv : rg.cur];
+    cp.out_prv = rg.buf[odd ? rg.cur : rg.prv];
+    cp.n_steps = k;
+    cp.step0 = n0;
+    cp.H = c.cl_H;
+    cp.lpitch = c.cl_lpitch;
+    cp.hist0 = hist0;
+    cp.hist_stride = (long long)c.L.S * c.L.slice;
+    const int G = c.forked ? c.groups : 1;
+    for (int g = 0; g < G; ++g) {
+        StepParams pg = p;
+        const cudaStream_t st = group_stream(c, G, g, pg);
+        CKL(launch_cluster_sweep(c.L.radius, mode, pg, cp, st));
+    }
+    if (odd) std::swap(rg.cur, rg.prv);
+    return DUFWI_OK;
+}
+
 // Forward steps n = n0 .. n1-1 (producing U^{n1}). Steps pair up from even n when the two-step
 // kernel is enabled, so every schedule covering a step uses the same grouping. hist: base of the
 // history slots of this range (slot n - h0), or null.
@@ -1095,6 +1129,12 @@ int forward_range(Ctx &c, Ring &rg, int n0, int n1, int mode, const float *wavel
         return sweep(c, rg, mode, p, n0, n1 - n0, hist ? hist + (size_t)(n0 - h0) * hstride : nullptr, 0, nl);
     int rc = fork_groups(c);
     if (rc) return rc;
+    if (c.cluster) {
+        p.step = n0;
+        rc = cluster_range(c, rg, mode, p, n0, n1 - n0, hist ? hist + (size_t)(n0 - h0) * hstride : nullptr, nl);
+        const int rj = join_groups(c);
+        return rc ? rc : rj;
+    }
     for (int n = n0; n < n1;) {
         p.step = n;
         p.hist = hist ? hist + (size_t)(n - h0) * hstride : nullptr;
@@ -1123,6 +1163,13 @@ int adjoint_range(Ctx &c, Ring &rg, int m1, int m0, const float *asrc, float *g_
     if (c.persistent) return sweep(c, rg, kAdjoint, p, m1, m1 - m0 + 1, nullptr, m1 - 1 - h0, nl);
     int rc = fork_groups(c);
     if (rc) return rc;
+    if (c.cluster) {
+        p.step = m1;
+        rc = cluster_range(c, rg, kAdjoint, p, m1, m1 - m0 + 1,
+                           c.at<float>(c.L.o_hist) + (size_t)(m1 - 1 - h0) * c.L.S * c.L.slice, nl);
+        const int rj = join_groups(c);
+        return rc ? rc : rj;
+    }
     for (int m = m1; m >= m0;) {
         p.step = m;
         p.hist_slot = m - 1 - h0;
@@ -1257,6 +1304,10 @@ int dufwi_set_option(int32_t option, int32_t value)
         if (value < 4 || value > 6) return DUFWI_ERR_INVALID_ARG;
         g_min_ctas = value;
         return DUFWI_OK;
+    case DUFWI_OPT_CLUSTER:
+        if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
+        g_cluster = value;
+        return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL:
         if (value != 0 && value != 1) return DUFWI_ERR_INVALID_ARG;
         g_test_stall = value;
@@ -1275,6 +1326,7 @@ int dufwi_get_option(int32_t option, int32_t *value)
     case DUFWI_OPT_EARLY_LOADS: *value = g_early; return DUFWI_OK;
     case DUFWI_OPT_SHOT_GROUPS: *value = g_shot_groups; return DUFWI_OK;
     case DUFWI_OPT_MIN_CTAS: *value = g_min_ctas; return DUFWI_OK;
+    case DUFWI_OPT_CLUSTER: *value = g_cluster; return DUFWI_OK;
     case DUFWI_OPT_TEST_STALL: *value = g_test_stall.load(); return DUFWI_OK;
     case DUFWI_OPT_TWO_STEP: *value = g_two_step; return DUFWI_OK;
     case DUFWI_OPT_REUSE_TABLES: *value = g_reuse_tables; return DUFWI_OK;

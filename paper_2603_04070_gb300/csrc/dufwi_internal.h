@@ -245,8 +245,30 @@ struct SweepParams {
     int stall_tile;          // test hook: this tile's wait can never be met (-1: none)
 };
 
+// Cluster-resident sweep (cluster_sweep_kernel): a range of steps of the compact stencil for
+// grids small enough that one shot's fields fit in the shared memory of a cluster of kClusterCtas
+// CTAs. CTA rank k of the cluster owns the padded rows [k H, (k + 1) H) of its shot; each step
+// copies the 4 halo rows above and below from its neighbours' shared memory (distributed shared
+// memory) and synchronises the cluster once. cur / prv: U^{n0}, U^{n0-1} (mu^{m0+1}, mu^{m0+2})
+// read at the start; out_cur / out_prv receive the last two fields at the end.
+constexpr int kClusterCtas = 8;
+struct ClusterParams {
+    const float *cur, *prv;
+    float *out_cur, *out_prv;
+    int n_steps;             // steps in this launch
+    int step0;               // first step: forward n = step0 + i, adjoint m = step0 - i
+    int H;                   // rows per CTA (a multiple of 4)
+    int lpitch;              // shared-memory row stride (floats): 4 zero columns, nxp rounded to 4, 4 zero columns
+    float *hist0;            // forward with history: Lap(U^{step0}); adjoint: Lap(U^{step0 - 1})
+    long long hist_stride;   // floats between consecutive steps' history slots
+};
+// Shared memory of the cluster form per CTA (bytes) for a padded grid, or 0 when it does not fit.
+size_t cluster_smem_bytes(int nxp, int nzp, int *H, int *lpitch);
+
 // Host launchers (dufwi_kernels.cu). All return cudaGetLastError() of the launch.
 cudaError_t launch_step(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);
+// Cluster-resident sweep of p.n_shots shots (modes kFwdSample, kFwdSampleHist, kFwdHist, kAdjoint).
+cudaError_t launch_cluster_sweep(int radius, int mode, const StepParams &p, const ClusterParams &cp, cudaStream_t st);
 // Multi-tile form of the one-step kernel (64 x 32 tiles, a grid of co-resident CTAs walking all
 // tiles with two-stage TMA loads); same modes and results as launch_step with tile height 32.
 cudaError_t launch_step_mt(int radius, int mode, const StepMaps &tm, const StepParams &p, cudaStream_t st);

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -1124,6 +1125,20 @@ struct CpmlLayout {
 
 __device__ __forceinline__ float4 ldg4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
+// 128-bit global load with an evict-first L2 hint (data read once: the history).
+__device__ __forceinline__ float4 ldg4_stream(const float *p)
+{
+#if DUFWI_L2_HINTS
+    float4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(l2_evict_first_policy()));
+    return v;
+#else
+    return ldg4(p);
+#endif
+}
+
 // (a, b) of a table of 4 rows of length n (a node, b node, a half, b half); identity outside.
 __device__ __forceinline__ float2 cpml_coef(const float *t, int n, int row, int i)
 {
@@ -1556,6 +1571,254 @@ cpml_step_kernel(const __grid_constant__ StepMaps tm, const __grid_constant__ Cp
                 box[(zn - z0 + kVHalo) * kVBoxX + (xn - x0 + kVHalo)];
         }
     }
+}
+
+// ---- cluster-resident sweep --------------------------------------------------------------------
+// For small grids (one shot's fields in the shared memory of kClusterCtas CTAs) a whole range of
+// steps runs in one launch of one cluster per shot. CTA rank k holds rows [k H, (k + 1) H) of the
+// padded grid in three rotating field buffers (the field being read, with 4 halo rows on each
+// side; the previous one; the one being written), kappa' and, in the adjoint, the imaging sum.
+// Each step: copy the halo rows of the field being read from the neighbours' buffers through
+// distributed shared memory, update the owned rows with the one-step kernel's arithmetic (the same
+// Laplacian and Eq. 2 operations in the same order, so the results are bit-identical), apply the
+// point injections in list order, write the history and traces, and synchronise the cluster. The
+// buffer written at step i is read by the neighbours at step i + 1 and overwritten only at step
+// i + 3, after two more cluster barriers, so one barrier per step suffices. Every CTA runs every
+// barrier (no early exit), so the cluster cannot stall on a missing arrival.
+
+// lap_block with a run-time row stride (identical operations).
+template <int R>
+__device__ __forceinline__ void lap_block_rs(const float *src, int sx, int cx, int cz, const float *c,
+                                             float4 (&lap)[4], float4 (&ctr)[4])
+{
+    float4 col[4 + 2 * R];
+#pragma unroll
+    for (int i = 0; i < 4 + 2 * R; ++i) col[i] = ld4s(src + (cz - R + i) * sx + cx);
+    const float2 m4 = make_float2(-4.0f, -4.0f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 lft = ld4s(src + (cz + j) * sx + cx - 4);
+        const float4 rgt = ld4s(src + (cz + j) * sx + cx + 4);
+        const float4 cc = col[R + j];
+        ctr[j] = cc;
+        const float w[12] = {lft.x, lft.y, lft.z, lft.w, cc.x, cc.y, cc.z, cc.w, rgt.x, rgt.y, rgt.z, rgt.w};
+        float2 l[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 u = make_float2(w[4 + 2 * h], w[5 + 2 * h]);
+            const float2 nu4 = __fmul2_rn(m4, u);
+            float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int kk = 1; kk <= R; ++kk) {
+                const float2 xs = (kk & 1)
+                    ? make_float2(w[4 + 2 * h - kk] + w[4 + 2 * h + kk], w[5 + 2 * h - kk] + w[5 + 2 * h + kk])
+                    : __fadd2_rn(make_float2(w[4 + 2 * h - kk], w[5 + 2 * h - kk]),
+                                 make_float2(w[4 + 2 * h + kk], w[5 + 2 * h + kk]));
+                const float4 &cm = col[R + j - kk], &cp = col[R + j + kk];
+                const float2 zs = h == 0 ? __fadd2_rn(make_float2(cm.x, cm.y), make_float2(cp.x, cp.y))
+                                         : __fadd2_rn(make_float2(cm.z, cm.w), make_float2(cp.z, cp.w));
+                acc = __ffma2_rn(make_float2(c[kk], c[kk]), __fadd2_rn(__fadd2_rn(xs, zs), nu4), acc);
+            }
+            l[h] = acc;
+        }
+        lap[j] = make_float4(l[0].x, l[0].y, l[1].x, l[1].y);
+    }
+}
+
+constexpr int kClusterThreads = 256;
+
+constexpr int kClusterList = 128;   // receivers (or the source) inside one CTA's strip
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kClusterThreads, 1)
+cluster_sweep_kernel(const StepParams p, const ClusterParams cp)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(128) float smem[];
+    // receivers sampled (forward) and point injections (source or receivers) inside this strip:
+    // buffer index and receiver number, in list order; the injection values of the current step
+    __shared__ int smp_idx[kClusterList], smp_r[kClusterList], inj_idx[kClusterList], inj_r[kClusterList];
+    __shared__ float inj_v[kClusterList];
+    __shared__ int n_smp, n_inj;
+    const int tid = threadIdx.x;
+    const int rank = static_cast<int>(cl.block_rank());
+    const int s = p.shot0 + blockIdx.y;
+    const int tx_idx = s % p.n_tx;
+    const int map = s / p.n_tx;
+    const long long shot_off = static_cast<long long>(s) * p.slice;
+    const int H = cp.H, lp = cp.lpitch, nxp = p.nxp, nzp = p.nzp;
+    const int z_lo = rank * H;                                  // first owned row
+    const int rows = max(0, min(H, nzp - z_lo));                // owned rows inside the grid
+    const int fsz = (H + 8) * lp;                               // one field buffer, halo rows included
+    float *F[3] = {smem, smem + fsz, smem + 2 * fsz};
+    float *kap = smem + 3 * fsz;                                // H x lp
+    float *G = kap + H * lp;                                    // adjoint imaging sum, H x lp
+    const int nq = (nxp + 3) / 4;                               // float4 columns of a row
+    const MapGrid mg = map_grid(p, map);
+    auto in_strip = [&](int node, int &idx) {
+        const int zn = node >> 16, xn = node & 0xffff;
+        if (node < 0 || zn >= nzp || xn >= nxp) {
+            if (rank == 0) raise_status(p.status, DUFWI_ERR_GEOMETRY);
+            return false;
+        }
+        idx = (zn - z_lo + 4) * lp + 4 + xn;
+        return zn >= z_lo && zn < z_lo + rows;
+    };
+
+    // zero everything (halo rows outside the grid and pad columns stay zero), then load the owned
+    // rows of U^{n0} (buffer 0), U^{n0-1} (buffer 2), kappa' and the running imaging sum
+    for (int i = tid; i < (3 * fsz + 2 * H * lp) / 4; i += kClusterThreads)
+        reinterpret_cast<float4 *>(smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid == 0) {   // the strip's receivers and injections, in list order
+        int m = 0, k = 0, idx = 0;
+        if ((MODE == kFwdSample || MODE == kFwdSampleHist) && p.cd)
+            for (int r = 0; r < p.n_rx; ++r)
+                if (in_strip(__ldg(p.smp_node + tx_idx * p.n_rx + r), idx)) {
+                    if (m < kClusterList) { smp_idx[m] = idx; smp_r[m] = r; }
+                    ++m;
+                }
+        if (MODE == kAdjoint) {
+            for (int r = 0; r < p.n_rx; ++r)
+                if (in_strip(__ldg(p.inj_node + tx_idx * p.n_rx + r), idx)) {
+                    if (k < kClusterList) { inj_idx[k] = idx; inj_r[k] = r; }
+                    ++k;
+                }
+        } else if (in_strip(__ldg(p.inj_node + tx_idx), idx)) {
+            inj_idx[0] = idx;
+            inj_r[0] = 0;
+            k = 1;
+        }
+        if (m > kClusterList || k > kClusterList) raise_status(p.status, DUFWI_ERR_UNSUPPORTED);
+        n_smp = min(m, kClusterList);
+        n_inj = min(k, kClusterList);
+    }
+    __syncthreads();
+    for (int i = tid; i < rows * nq; i += kClusterThreads) {
+        const int r = i / nq, q4 = (i - r * nq) * 4;
+        const long long g = shot_off + static_cast<long long>(z_lo + r) * p.pitch + q4;
+        st4s(F[0] + (r + 4) * lp + 4 + q4, ldg4(cp.cur + g));
+        st4s(F[2] + (r + 4) * lp + 4 + q4, ldg4(cp.prv + g));
+        st4s(kap + r * lp + 4 + q4,
+             ldg4(p.kap + static_cast<long long>(map) * p.slice + static_cast<long long>(z_lo + r) * p.pitch + q4));
+        if (MODE == kAdjoint) st4s(G + r * lp + 4 + q4, ldg4(p.grad + g));
+    }
+    cl.sync();
+
+    constexpr int kHReg = 8;                                    // history prefetch: float4 per thread
+    const bool hreg_ok = rows * nq <= kHReg * kClusterThreads;
+    int ci = 0;                                                 // F[ci] holds the field being read
+    for (int i = 0; i < cp.n_steps; ++i) {
+        const int step = MODE == kAdjoint ? cp.step0 - i : cp.step0 + i;
+        float *cur = F[ci], *prv = F[(ci + 2) % 3], *out = F[(ci + 1) % 3];
+        // requests that do not depend on this step's arithmetic go first: the history rows the
+        // imaging reads (adjoint), this step's injection values, the traces of U^n
+        float4 hreg[kHReg];
+        const float *hm = cp.hist0 - static_cast<long long>(i) * cp.hist_stride + shot_off;
+        if (MODE == kAdjoint && hreg_ok) {
+#pragma unroll
+            for (int j = 0; j < kHReg; ++j) {
+                const int e = tid + j * kClusterThreads;
+                if (e < rows * nq) {
+                    const int r = e / nq, q4 = (e - r * nq) * 4;
+                    hreg[j] = ldg4_stream(hm + static_cast<long long>(z_lo + r) * p.pitch + q4);
+                }
+            }
+        }
+        if (tid < n_inj) {
+            inj_v[tid] = MODE == kAdjoint
+                ? __ldg(p.inj_val + (static_cast<long long>(s) * p.nt + step) * p.n_rx + inj_r[tid])
+                : __fmul_rn(p.inj_scale, __ldg(p.inj_val + static_cast<long long>(p.wav_per_tx ? tx_idx : 0) * p.nt + step));
+        }
+        if (tid < n_smp) p.cd[(static_cast<long long>(s) * p.nt + step) * p.n_rx + smp_r[tid]] = cur[smp_idx[tid]];
+        // halo rows of cur from the neighbours (rows outside the grid stay zero)
+        if (rank > 0) {
+            const float *up = cl.map_shared_rank(cur, rank - 1);
+            for (int e = tid; e < 4 * (lp / 4); e += kClusterThreads) {
+                const int r = e / (lp / 4), q4 = (e - r * (lp / 4)) * 4;
+                st4s(cur + r * lp + q4, *reinterpret_cast<const float4 *>(up + (H + r) * lp + q4));
+            }
+        }
+        if (rank + 1 < static_cast<int>(cl.num_blocks()) && z_lo + H < nzp) {
+            const float *dn = cl.map_shared_rank(cur, rank + 1);
+            for (int e = tid; e < 4 * (lp / 4); e += kClusterThreads) {
+                const int r = e / (lp / 4), q4 = (e - r * (lp / 4)) * 4;
+                st4s(cur + (H + 4 + r) * lp + q4, *reinterpret_cast<const float4 *>(dn + (4 + r) * lp + q4));
+            }
+        }
+        __syncthreads();
+        // update of the owned rows (blocks of 4 x 4; at the grid's last rows the block rows past
+        // nzp are computed and not stored)
+        const int nbr = (rows + 3) / 4;
+        for (int b = tid; b < nbr * nq; b += kClusterThreads) {
+            const int br = b / nq, bq = b - br * nq;
+            const int lz = 4 + 4 * br, lx = 4 + 4 * bq;
+            const int gz0 = z_lo + 4 * br, gx = 4 * bq;
+            float4 lap[4], ctr[4];
+            lap_block_rs<R>(cur, lp, lx, lz, p.c, lap, ctr);
+            const bool interior = region_interior(p, mg, gx, gz0, 4, 4);
+            int xd[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) xd[k] = layer_depth(gx + k, p.P, mg.Nx);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gz = gz0 + j;
+                if (gz >= z_lo + rows) continue;
+                const int lo = (lz + j) * lp + lx;
+                float4 nv = eq2_row(ctr[j], ld4s(prv + lo), ld4s(kap + (lz + j - 4) * lp + lx), lap[j], interior,
+                                    p.damp_tab + layer_depth(gz, p.P, mg.Nz) * (p.P + 1), xd);
+                float4 lv = lap[j];
+                if (gx + 4 > nxp) {   // lanes past the last column stay zero (outside the grid)
+                    if (gx + 1 >= nxp) { nv.y = 0.f; lv.y = 0.f; }
+                    if (gx + 2 >= nxp) { nv.z = 0.f; lv.z = 0.f; }
+                    nv.w = 0.f; lv.w = 0.f;
+                }
+                st4s(out + lo, nv);
+                if (MODE == kFwdSampleHist || MODE == kFwdHist)
+                    st4_stream(cp.hist0 + static_cast<long long>(i) * cp.hist_stride + shot_off +
+                               static_cast<long long>(gz) * p.pitch + gx, lv);
+            }
+        }
+        __syncthreads();
+        // point injections of this step, in list order (thread 0): the product was rounded
+        // before the add, as in the one-step kernel
+        if (tid == 0)
+            for (int e = 0; e < n_inj; ++e) out[inj_idx[e]] = __fadd_rn(out[inj_idx[e]], inj_v[e]);
+        if (MODE == kAdjoint) {   // imaging: G += mu^m Lap(U^{m-1}), with mu^m after the injections
+            __syncthreads();
+            if (hreg_ok) {
+#pragma unroll
+                for (int j = 0; j < kHReg; ++j) {
+                    const int e = tid + j * kClusterThreads;
+                    if (e < rows * nq) {
+                        const int r = e / nq, q4 = (e - r * nq) * 4;
+                        float *gp = G + r * lp + 4 + q4;
+                        st4s(gp, fma4(ld4s(out + (r + 4) * lp + 4 + q4), hreg[j], ld4s(gp)));
+                    }
+                }
+            } else {
+                for (int e = tid; e < rows * nq; e += kClusterThreads) {
+                    const int r = e / nq, q4 = (e - r * nq) * 4;
+                    float *gp = G + r * lp + 4 + q4;
+                    st4s(gp, fma4(ld4s(out + (r + 4) * lp + 4 + q4),
+                                  ldg4(hm + static_cast<long long>(z_lo + r) * p.pitch + q4), ld4s(gp)));
+                }
+            }
+        }
+        cl.sync();
+        ci = (ci + 1) % 3;
+    }
+    // the last two fields (and the imaging sum) back to global memory
+    const float *fc = F[ci], *fp = F[(ci + 2) % 3];
+    for (int i = tid; i < rows * nq; i += kClusterThreads) {
+        const int r = i / nq, q4 = (i - r * nq) * 4;
+        const long long g = shot_off + static_cast<long long>(z_lo + r) * p.pitch + q4;
+        st4(cp.out_cur + g, ld4s(fc + (r + 4) * lp + 4 + q4));
+        st4(cp.out_prv + g, ld4s(fp + (r + 4) * lp + 4 + q4));
+        if (MODE == kAdjoint) st4(p.grad + g, ld4s(G + r * lp + 4 + q4));
+    }
+    // no CTA leaves while a neighbour may still read its buffers
+    cl.sync();
 }
 
 // ---- persistent sweep ---------------------------------------------------------------------------
@@ -2678,6 +2941,67 @@ cudaError_t launch_step_mt(int radius, int mode, const StepMaps &tm, const StepP
 }
 
 // </one-step kernel source>
+
+// Dynamic shared memory of the cluster form at most (the kernel's static lists take about 2 KB
+// of the 227 KB a CTA may use).
+constexpr size_t kClusterSmemMax = 220 * 1024;
+
+size_t cluster_smem_bytes(int nxp, int nzp, int *H, int *lpitch)
+{
+    const int h = ((nzp + kClusterCtas - 1) / kClusterCtas + 3) / 4 * 4;
+    const int lp = (nxp + 3) / 4 * 4 + 8;
+    const size_t bytes = (size_t)(3 * (h + 8) + 2 * h) * lp * sizeof(float);
+    if (H) *H = h;
+    if (lpitch) *lpitch = lp;
+    return bytes <= (size_t)kClusterSmemMax ? bytes : 0;
+}
+
+template <int R, int MODE>
+static cudaError_t launch_cluster_sweep_rm(const StepParams &p, const ClusterParams &cp, cudaStream_t st)
+{
+    int H = 0, lp = 0;
+    const size_t bytes = cluster_smem_bytes(p.nxp, p.nzp, &H, &lp);
+    if (bytes == 0 || H != cp.H || lp != cp.lpitch || p.map_dims) return cudaErrorInvalidValue;
+    static DeviceCache dc;   // shared-memory attributes, set once per device (to the largest size used)
+    cudaError_t e = configure_kernel(cluster_sweep_kernel<R, MODE>, (uint32_t)kClusterSmemMax, dc);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterCtas, p.n_shots);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cluster_sweep_kernel<R, MODE>, p, cp);
+}
+
+template <int R>
+static cudaError_t launch_cluster_sweep_r(int mode, const StepParams &p, const ClusterParams &cp, cudaStream_t st)
+{
+    switch (mode) {
+    case kFwdSample: return launch_cluster_sweep_rm<R, kFwdSample>(p, cp, st);
+    case kFwdSampleHist: return launch_cluster_sweep_rm<R, kFwdSampleHist>(p, cp, st);
+    case kFwdHist: return launch_cluster_sweep_rm<R, kFwdHist>(p, cp, st);
+    case kAdjoint: return launch_cluster_sweep_rm<R, kAdjoint>(p, cp, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_cluster_sweep(int radius, int mode, const StepParams &p, const ClusterParams &cp, cudaStream_t st)
+{
+    switch (radius) {
+    case 1: return launch_cluster_sweep_r<1>(mode, p, cp, st);
+    case 2: return launch_cluster_sweep_r<2>(mode, p, cp, st);
+    case 3: return launch_cluster_sweep_r<3>(mode, p, cp, st);
+    case 4: return launch_cluster_sweep_r<4>(mode, p, cp, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_setup_kappa(const float *sos, const float *density, float *kap, float *bx, float *bz, int *status,
                                int n_maps, int Nx, int Nz, int P, int nxp, int nzp, int pitch, double dt_over_dx,

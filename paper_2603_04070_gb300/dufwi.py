@@ -36,6 +36,7 @@ OPT_MULTI_TILE = 6
 OPT_EARLY_LOADS = 7
 OPT_SHOT_GROUPS = 8
 OPT_MIN_CTAS = 9
+OPT_CLUSTER = 10
 
 
 class DufwiError(RuntimeError):

@@ -149,7 +149,7 @@ def test_boundary_and_option_validation():
     assert d._lib.dufwi_workspace_size(ctypes.byref(bad), ctypes.byref(sh), 1, ctypes.byref(out)) == d.ERR_INVALID_ARG
     for opt, good, badv in ((d.OPT_PERSISTENT, 1, 2), (d.OPT_TEST_STALL, 0, 3), (d.OPT_TILE_Z, 64, 48),
                             (d.OPT_SHOT_GROUPS, 4, 5), (d.OPT_SHOT_GROUPS, 1, 0), (d.OPT_MIN_CTAS, 6, 7),
-                            (d.OPT_MIN_CTAS, 4, 3)):
+                            (d.OPT_MIN_CTAS, 4, 3), (d.OPT_CLUSTER, 1, 2)):
         before = d.get_option(opt)
         with pytest.raises(d.DufwiError):
             d.set_option(opt, badv)
@@ -381,12 +381,12 @@ def test_kept_segments_for_budget_is_the_largest_fit():
 
 def test_autotune_candidates_are_valid_option_sets():
     """Every launch form the tuner times is a set of valid option values (host-side round trip),
-    and applying a set changes only the seven launch options."""
+    and applying a set changes only the eight launch options."""
     from paper_2603_04070_gb300 import autotune
     d = _lib_module()
     opts = {"tile_z": d.OPT_TILE_Z, "two_step": d.OPT_TWO_STEP, "persistent": d.OPT_PERSISTENT,
             "multi_tile": d.OPT_MULTI_TILE, "early": d.OPT_EARLY_LOADS, "groups": d.OPT_SHOT_GROUPS,
-            "min_ctas": d.OPT_MIN_CTAS}
+            "min_ctas": d.OPT_MIN_CTAS, "cluster": d.OPT_CLUSTER}
     assert set(autotune.KNOBS) == set(opts)
     before = {k: d.get_option(o) for k, o in opts.items()}
     reuse = d.get_option(d.OPT_REUSE_TABLES)

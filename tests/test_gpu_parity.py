@@ -740,6 +740,61 @@ def test_shot_groups_are_bit_identical(d, kw):
     assert float(out[0][2].abs().max()) > 0.0
 
 
+@pytest.mark.parametrize("nx,nz,order,kw", [(64, 56, 8, dict()), (64, 56, 8, dict(ckpt_interval=37)),
+                                          (64, 56, 8, dict(ckpt_interval=37, kept_segments=3)),
+                                          (97, 71, 8, dict(ckpt_interval=40)), (60, 52, 4, dict()),
+                                          (128, 128, 8, dict(ckpt_interval=50)), (188, 188, 8, dict())])
+def test_cluster_sweeps_are_bit_identical(d, nx, nz, order, kw):
+    """DUFWI_OPT_CLUSTER: whole ranges of steps in one launch of a cluster of 8 CTAs per shot (the
+    fields in shared memory, halos through distributed shared memory) give the traces, misfit and
+    gradient of one launch per step bit for bit: store-all, checkpointed, the hybrid history, a
+    ragged grid (97 x 71: padded width not a multiple of 4, a partial strip and an empty CTA),
+    order 4, the 128 x 128 configuration and the paper's 188 x 188 grid."""
+    wl = inputs.make_workload("linear_disk", seed=14, nx=nx, nz=nz, nt=230, n_elem=16, n_tx=3, n_maps=2,
+                              fd_order=order)
+    M_obs = _observed(wl)
+    pb = _dufwi_problem(d, wl, **kw)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_start).cuda()
+    sos[1] += 9.0
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    obs = torch.from_numpy(M_obs).cuda()
+    before = d.get_option(d.OPT_CLUSTER)
+    out = []
+    try:
+        for cl in (0, 1):
+            d.set_option(d.OPT_CLUSTER, cl)
+            cd = d.simulate(pb, sos, wav, geom, check=True)
+            J, g, cd2 = d.misfit_gradient(pb, sos, wav, geom, obs, return_cd=True, check=True)
+            torch.cuda.synchronize()
+            out.append((cd, J, g, cd2))
+    finally:
+        d.set_option(d.OPT_CLUSTER, before)
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+    assert float(out[0][2].abs().max()) > 0.0
+
+
+def test_cluster_option_falls_back_on_large_grids(d):
+    """A grid whose fields do not fit a cluster's shared memory runs one launch per step with the
+    option set (same results)."""
+    wl = inputs.make_workload("linear_disk", seed=15, nx=300, nz=280, nt=60, n_elem=16, n_tx=1)
+    pb = _dufwi_problem(d, wl)
+    geom = d.Geometry.from_workload(wl)
+    sos = torch.from_numpy(wl.sos_true).cuda()
+    wav = torch.from_numpy(wl.wavelet).cuda()
+    before = d.get_option(d.OPT_CLUSTER)
+    try:
+        d.set_option(d.OPT_CLUSTER, 0)
+        a = d.simulate(pb, sos, wav, geom)
+        d.set_option(d.OPT_CLUSTER, 1)
+        b = d.simulate(pb, sos, wav, geom, check=True)
+        torch.cuda.synchronize()
+    finally:
+        d.set_option(d.OPT_CLUSTER, before)
+    assert torch.equal(a, b)
+
+
 def test_capture_before_any_grouped_call_runs_one_group(d):
     """On a host thread that has made no uncaptured call yet, the group streams are not created
     during stream capture: the captured call runs its shots as one group and replays the result

@@ -170,6 +170,11 @@ def step_kernel_source_sha256() -> str:
     return hashlib.sha256("".join(parts).encode()).hexdigest()
 
 
+def autotune_cluster_fits(pb) -> bool:
+    from paper_2603_04070_gb300 import autotune
+    return autotune.cluster_fits(pb)
+
+
 def effective_groups(dufwi, shots: int) -> int:
     """Shot groups a gradient call uses with the current options (the two-step, persistent and
     multi-tile forms step every shot in one launch)."""
@@ -419,7 +424,7 @@ def run_ours(args):
     args.multi_tile_used = dufwi.get_option(dufwi.OPT_MULTI_TILE)
     args.groups_used = effective_groups(dufwi, wl.n_maps * wl.n_tx)
     args.min_ctas_used = dufwi.get_option(dufwi.OPT_MIN_CTAS)
-    args.cluster_used = dufwi.get_option(dufwi.OPT_CLUSTER)
+    args.cluster_used = int(bool(dufwi.get_option(dufwi.OPT_CLUSTER)) and autotune_cluster_fits(pb))
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

@@ -56,6 +56,27 @@ def _key(problem: dufwi.Problem, geom: dufwi.Geometry, n_maps: int) -> str:
                                              n_maps * geom.n_tx, geom.n_rx)
 
 
+def cluster_fits(problem: dufwi.Problem) -> bool:
+    """Whether the cluster-resident sweep applies to this grid: one shot's three fields (with 4
+    halo rows per CTA), kappa' and the imaging sum fit 220 KB of shared memory in each of the 8
+    CTAs of a cluster (the library makes the same test; elsewhere the option has no effect)."""
+    nxp, nzp = problem.nx + 2 * problem.pml_cells, problem.nz + 2 * problem.pml_cells
+    h = ((nzp + 7) // 8 + 3) // 4 * 4
+    lp = (nxp + 3) // 4 * 4 + 8
+    return (3 * (h + 8) + 2 * h) * lp * 4 <= 220 * 1024
+
+
+def applicable(options: dict, problem: dufwi.Problem, sizes=None) -> bool:
+    """False for a candidate whose option does nothing for this problem (it would only time the
+    default again): the cluster form on a grid that does not fit or with maps of different sizes,
+    the register-cap variants outside the 8th-order 64 x 32 form."""
+    if options.get("cluster", 0) and (sizes is not None or not cluster_fits(problem)):
+        return False
+    if options.get("min_ctas", 5) != 5 and (problem.fd_order != 8 or options.get("tile_z", 32) != 32):
+        return False
+    return True
+
+
 def apply(options: dict):
     dufwi.set_option(dufwi.OPT_TILE_Z, int(options.get("tile_z", 32)))
     dufwi.set_option(dufwi.OPT_TWO_STEP, int(options.get("two_step", 0)))
@@ -133,6 +154,9 @@ def tune(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom:
             dufwi.simulate(short, sos, w, geom, cd=cd, workspace=ws, sizes=sizes)
     timings = []
     for cand in CANDIDATES:
+        if not applicable(cand, problem, sizes):
+            timings.append(float("inf"))
+            continue
         apply(cand)
         run()                                                                # warm-up
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -144,7 +168,7 @@ def tune(problem: dufwi.Problem, sos: torch.Tensor, wavelet: torch.Tensor, geom:
         timings.append(ev[0].elapsed_time(ev[1]) / repeats)
     best = dict(CANDIDATES[min(range(len(CANDIDATES)), key=lambda i: timings[i])])
     best["ms_per_step"] = min(timings) / nt
-    best["candidates_ms_per_step"] = [t / nt for t in timings]
+    best["candidates_ms_per_step"] = [t / nt if t != float("inf") else None for t in timings]
     best["candidates"] = [dict(c) for c in CANDIDATES]
     apply(best)
     with _lock:

@@ -399,3 +399,23 @@ def test_autotune_candidates_are_valid_option_sets():
     finally:
         autotune.apply(before)
     assert {k: d.get_option(o) for k, o in opts.items()} == before
+
+
+def test_autotune_skips_candidates_that_do_not_apply():
+    """The cluster form applies only to grids whose fields fit a cluster's shared memory (and not
+    to maps of different sizes), the register-cap variants only to the 8th-order 64 x 32 form; the
+    tuner does not time such candidates."""
+    from paper_2603_04070_gb300 import autotune
+    d = _lib_module()
+    small = d.Problem(nx=128, nz=128, dx=1e-4, dt=1e-8, nt=10)
+    ring = d.Problem(nx=188, nz=188, dx=1e-4, dt=1e-8, nt=10)
+    big = d.Problem(nx=512, nz=512, dx=1e-4, dt=1e-8, nt=10)
+    order4 = d.Problem(nx=128, nz=128, dx=1e-4, dt=1e-8, nt=10, fd_order=4)
+    assert autotune.cluster_fits(small) and autotune.cluster_fits(ring) and not autotune.cluster_fits(big)
+    cl = {**autotune._BASE, "cluster": 1}
+    cap = {**autotune._BASE, "min_ctas": 4}
+    assert autotune.applicable(cl, small) and not autotune.applicable(cl, big)
+    assert not autotune.applicable(cl, small, sizes=[(128, 128)])
+    assert autotune.applicable(cap, small) and not autotune.applicable(cap, order4)
+    assert not autotune.applicable({**cap, "tile_z": 64}, small)
+    assert all(autotune.applicable(c, small) for c in autotune.CANDIDATES)

@@ -124,8 +124,8 @@ typedef struct {
  *     Eq. 1 is compensated the same way (integer staggered weights, buoyancies and kappa' as
  *     hi + lo; about 10x the FP32 variable-density step's arithmetic). With the CPML, dufwi_jvp,
  *     dufwi_second_order or dufwi_hvp it returns DUFWI_ERR_UNSUPPORTED. The launch options (tile
- *     height, two steps, persistent sweeps, multi-tile) do not apply: the compensated step runs
- *     one launch per step on 64 x 32 tiles. */
+ *     height, two steps, persistent sweeps, multi-tile, register caps, cluster sweeps) do not
+ *     apply: the compensated step runs one launch per step and shot group on 64 x 32 tiles. */
 #define DUFWI_FORWARD_FP32 0
 #define DUFWI_FORWARD_COMPENSATED 1
 

@@ -36,6 +36,21 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
+def test_binding_constants_match_the_header():
+    """Every DUFWI_OPT_*, DUFWI_ERR_*, DUFWI_SNAP_*, DUFWI_BOUNDARY_* and DUFWI_FORWARD_* value the
+    header defines is the one the binding uses, and every option round-trips through
+    dufwi_get_option."""
+    import re
+    d = _lib_module()
+    header = open(os.path.join(ROOT, "include", "dufwi.h")).read()
+    defs = dict(re.findall(r"#define DUFWI_((?:OPT|ERR)_[A-Z0-9_]+)\s+(-?\d+)", header))
+    assert len([k for k in defs if k.startswith("OPT_")]) >= 10
+    for k, v in defs.items():
+        assert getattr(d, k) == int(v), k
+    for k in (k for k in defs if k.startswith("OPT_")):
+        d.get_option(getattr(d, k))                       # known to the library
+
+
 def test_status_strings_and_version():
     d = _lib_module()
     for code in range(9):

@@ -38,8 +38,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_binding_constants_match_the_header():
     """Every DUFWI_OPT_*, DUFWI_ERR_*, DUFWI_SNAP_*, DUFWI_BOUNDARY_* and DUFWI_FORWARD_* value the
-    header defines is the one the binding uses, and every option round-trips through
-    dufwi_get_option."""
+    header defines is the one the binding uses, and the library knows every option."""
     import re
     d = _lib_module()
     header = open(os.path.join(ROOT, "include", "dufwi.h")).read()
@@ -49,6 +48,11 @@ def test_binding_constants_match_the_header():
         assert getattr(d, k) == int(v), k
     for k in (k for k in defs if k.startswith("OPT_")):
         d.get_option(getattr(d, k))                       # known to the library
+    named = {"SNAP": d.SNAPSHOT_DTYPES, "BOUNDARY": d.BOUNDARIES, "FORWARD": d.FORWARD_PRECISIONS}
+    enums = re.findall(r"#define DUFWI_(SNAP|BOUNDARY|FORWARD)_([A-Z0-9]+)\s+(\d+)", header)
+    assert len(enums) == 7
+    for group, name, v in enums:
+        assert named[group][name.lower()] == int(v), (group, name)
 
 
 def test_status_strings_and_version():

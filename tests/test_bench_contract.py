@@ -77,3 +77,23 @@ def test_bench_counts_the_shot_groups_the_library_uses():
     finally:
         for o, v in zip(opts, saved):
             dufwi.set_option(o, v)
+
+
+def test_committed_traffic_records_match_the_kernel_source():
+    """The committed per-launch DRAM traffic records were taken on the current one-step kernel
+    source (their hash matches), and the benchmark scales them from the captured shots per launch
+    to a step of all shots."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        rec = json.load(f)
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic_scale.json")) as f:
+        rs = json.load(f)
+    sha = bench.step_kernel_source_sha256()
+    assert rec["step_kernel_source_sha256"] == sha and rs["step_kernel_source_sha256"] == sha
+    for kind in ("forward", "recompute", "adjoint"):
+        per = rec["per_launch_dram_bytes_full_size"][kind]
+        assert bench.kernel_traffic(kind, shots=16) == per * 16 / rec["shots_per_launch"]
+        assert bench.scale_traffic(64)[kind] == rs["per_launch_dram_bytes_full_size"][kind] * 64 / rs["shots_per_launch"]
+        # below the algorithmic bytes with warm L2: nothing is re-read from DRAM
+        assert rec["per_launch_dram_bytes_warm_l2"][kind] < rec["algorithmic_bytes_per_launch"][kind]
